@@ -1,0 +1,181 @@
+"""Pins of the oracle's Algorithm 1, divergence and gradients (App. C; eq. (sinkhorn-divergence))."""
+import numpy as np
+import pytest
+
+from oracle.grid import Grid
+from oracle import sinkhorn as sk
+from oracle.gradient import fd_directional, envelope
+from paper_2605_18389_gb300 import inputs
+
+
+def _pair(g, recipe="paper_uniform", seed=7, npairs=1, masses=False):
+    return inputs.pairs(recipe, seed, npairs, g.x, g.nlon, g.a_ring, masses=masses)
+
+
+@pytest.mark.parametrize("tau", [np.inf, 0.5])
+def test_sht_iterates_equal_dense_iterates(tau):
+    # the SHT operator equals H diag(a) (addition theorem), so Alg. 1 driven by either
+    # must produce the same iterates up to rounding
+    g = Grid(12)
+    p, q = _pair(g, npairs=2)
+    ra = sk.sinkhorn(g, p, q, eps=0.1, tau=tau, T=60, C=10, kernel="sht")
+    rb = sk.sinkhorn(g, p, q, eps=0.1, tau=tau, T=60, C=10, kernel="dense")
+    for key in ("u", "v"):
+        np.testing.assert_allclose(ra[key], rb[key], rtol=1e-11)
+    np.testing.assert_allclose(ra["ot"], rb["ot"], rtol=1e-11)
+
+
+def test_balanced_closed_form_infinite_time():
+    # t = 250 => h_l = 0 exactly for l >= 1, K v = <a, v>/4pi; with unit masses the fixed
+    # point is reached after one iteration and OT = eps [sum a p log p + sum a q log q + log 4pi]
+    g = Grid(10)
+    p, q = _pair(g, "vmf3", npairs=2)
+    eps = 1000.0
+    r = sk.sinkhorn(g, p, q, eps=eps, T=3, C=1, delta=0.0)
+    a = g.a
+    exp = eps * (np.sum(a * p * np.log(p), axis=(1, 2)) + np.sum(a * q * np.log(q), axis=(1, 2))
+                 + np.log(4 * np.pi))
+    np.testing.assert_allclose(r["ot"], exp, rtol=1e-12)
+    assert np.all(r["err"] < 1e-14)
+    d = sk.divergence(g, p, q, eps=eps, T=3, C=1)
+    np.testing.assert_allclose(d["S"], 0.0, atol=1e-9 * eps)
+
+
+def test_unbalanced_closed_form_infinite_time():
+    # K v = <a,v>/4pi: the fixed point is u = p^g B^-g, v = q^g A^-g with
+    # log A = (log al - g log be)/(1-g^2), log B = (log be - g log al)/(1-g^2),
+    # al = <a,p^g>/4pi, be = <a,q^g>/4pi, g = tau/(tau+eps); the TI constant vanishes there.
+    g = Grid(8)
+    p, q = _pair(g, "vmf3", npairs=1, masses=True)
+    eps, tau = 1000.0, 700.0
+    gam = tau / (tau + eps)
+    a = g.a
+    al = np.sum(a * p[0] ** gam) / (4 * np.pi)
+    be = np.sum(a * q[0] ** gam) / (4 * np.pi)
+    lA = (np.log(al) - gam * np.log(be)) / (1 - gam * gam)
+    lB = (np.log(be) - gam * np.log(al)) / (1 - gam * gam)
+    u = p[0] ** gam * np.exp(-gam * lB)
+    v = q[0] ** gam * np.exp(-gam * lA)
+    r = sk.sinkhorn(g, p, q, eps=eps, tau=tau, T=400, C=0)
+    np.testing.assert_allclose(r["u"][0], u, rtol=1e-10)
+    np.testing.assert_allclose(r["v"][0], v, rtol=1e-10)
+    ot = np.sum(a * (tau * (1 - u ** (-eps / tau)) * p[0] + tau * (1 - v ** (-eps / tau)) * q[0]))
+    np.testing.assert_allclose(r["ot"][0], ot, rtol=1e-10)
+
+
+def test_balanced_gauge_and_exact_second_marginal():
+    # after every iteration: sum_i u_i = 1 (Alg. 1 gauge) and v (.) K u = q exactly
+    g = Grid(16)
+    p, q = _pair(g)
+    from oracle.sht import heat_apply
+    for T in (1, 2, 5):
+        r = sk.sinkhorn(g, p, q, eps=0.1, T=T, C=0)
+        assert abs(r["u"].sum() - 1.0) < 1e-13
+        np.testing.assert_allclose(r["v"] * heat_apply(g, r["u"], 0.025), q, rtol=1e-11)
+
+
+def test_translation_invariant_step_is_optimal():
+    # the TI step maximises the dual along (phi + c, psi - c); at its optimum
+    # sum a p u^{-eps/tau} = sum a q v^{-eps/tau} after every iteration
+    g = Grid(12)
+    p, q = _pair(g, "vmf3", masses=True)
+    eps, tau = 0.2, 0.3
+    a = g.a
+    for T in (1, 3, 7):
+        r = sk.sinkhorn(g, p, q, eps=eps, tau=tau, T=T, C=0)
+        lhs = np.sum(a * p[0] * r["u"][0] ** (-eps / tau))
+        rhs = np.sum(a * q[0] * r["v"][0] ** (-eps / tau))
+        assert abs(lhs - rhs) < 1e-12 * lhs
+
+
+@pytest.mark.parametrize("tau", [np.inf, 1.0, 0.1])
+def test_dual_objective_nondecreasing(tau):
+    # each half-step maximises the dual in one block and the TI step along translations,
+    # so D = Alg.1-return - eps m(pi) never decreases (K positive at this t)
+    g = Grid(10)
+    p, q = _pair(g, "vmf3", masses=bool(np.isfinite(tau)))   # balanced needs equal masses
+    prev = -np.inf
+    for T in range(1, 12):
+        r = sk.sinkhorn(g, p, q, eps=0.4, tau=tau, T=T, C=0)
+        d = r["ot_dual"][0]
+        assert d >= prev - 1e-12 * abs(d)
+        prev = d
+
+
+def test_balanced_converges_with_exact_marginals():
+    g = Grid(32)
+    p, q = _pair(g)
+    r = sk.sinkhorn(g, p, q, eps=0.1, T=2000, delta=1e-10, C=10)
+    assert r["status"][0] == sk.OK and r["iters"][0] < 2000
+    assert r["err"][0] < 1e-10
+    assert abs(r["mass_pi"][0] - 1.0) < 1e-9
+
+
+def test_divergence_invariants():
+    g = Grid(16)
+    p, q = _pair(g, "vmf3", npairs=3)
+    kw = dict(eps=0.5, T=3000, delta=1e-10, C=10)
+    d1 = sk.divergence(g, p, q, **kw)
+    d2 = sk.divergence(g, q, p, **kw)
+    assert np.all(d1["status"] == sk.OK) and np.all(d2["status"] == sk.OK)
+    np.testing.assert_allclose(d1["S"], d2["S"], rtol=1e-9)
+    assert np.all(d1["S"] > 0)
+    dpp = sk.divergence(g, p, p, **kw)
+    assert np.all(dpp["S"] == 0.0)
+    # balanced + converged: both returned forms agree
+    np.testing.assert_allclose(d1["S"], d1["S_dual"], rtol=1e-8)
+
+
+def test_large_tau_recovers_balanced():
+    g = Grid(12)
+    p, q = _pair(g, "vmf3")
+    kw = dict(eps=0.5, T=600, C=0)
+    sb = sk.divergence(g, p, q, tau=np.inf, **kw)["S"][0]
+    su = sk.divergence(g, p, q, tau=1e8, **kw)["S_dual"][0]
+    assert abs(sb - su) < 1e-5 * abs(sb)
+
+
+def test_breakdown_reported_on_narrow_kernel():
+    # App. C.4: the truncated kernel goes negative; vMF mixtures at nlat 32, t = 1e-2
+    # hit a non-positive K v within a few iterations
+    g = Grid(32)
+    p, q = _pair(g, "vmf3", seed=1001)
+    r = sk.sinkhorn(g, p, q, eps=4e-2, T=50, C=10, delta=1e-10)
+    assert r["status"][0] == sk.NONPOSITIVE
+    assert 1 <= r["iters"][0] <= 10
+    assert np.isnan(r["ot"][0])
+
+
+def test_fd_gradient_matches_envelope():
+    # two independent derivations of dS/dp at convergence (balanced)
+    g = Grid(12)
+    p, q = _pair(g, "vmf3", seed=3)
+    eps = 1.0
+    T = 600
+    ge = envelope(g, p[0], q[0], eps, np.inf, T, delta=1e-13, C=10)
+    rng = np.random.default_rng(5)
+    a = g.a
+    dirs = []
+    for _ in range(4):
+        d = p[0] * rng.normal(size=p[0].shape)
+        d -= np.sum(a * d) / np.sum(a)   # sum a d = 0: balanced needs equal masses
+        dirs.append(d / np.sqrt(np.sum(a * d * d)) * np.sqrt(np.sum(a * p[0] ** 2)))
+    dirs = np.array(dirs)
+    for d in dirs:
+        assert abs(np.sum(a * d)) < 1e-12
+    fd = fd_directional(g, p[0], q[0], eps, np.inf, T, dirs, h=1e-5)
+    env = np.array([np.sum(ge * d) for d in dirs])
+    np.testing.assert_allclose(fd, env, rtol=2e-5, atol=1e-8)
+
+
+def test_unbalanced_fd_gradient_matches_envelope_dual_form():
+    g = Grid(12)
+    p, q = _pair(g, "vmf3", seed=4, masses=True)
+    eps, tau = 1.0, 1.0
+    T = 800
+    ge = envelope(g, p[0], q[0], eps, tau, T, delta=0.0, C=0, form="S_dual")
+    rng = np.random.default_rng(6)
+    dirs = p[0] * rng.normal(size=(3,) + p[0].shape)
+    fd = fd_directional(g, p[0], q[0], eps, tau, T, dirs, h=1e-5, form="S_dual")
+    env = np.array([np.sum(ge * d) for d in dirs])
+    np.testing.assert_allclose(fd, env, rtol=2e-5, atol=1e-8)
