@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the batched heat-kernel Sinkhorn on a 720 x 1440 Gauss-Legendre grid.
+
+One step = one iteration of Algorithm 1 (u-step, v-step, gauge) for every problem of
+the batch, with the marginal check every C = 10 iterations, inside one
+shot_divergence call (8 measure pairs -> 24 OT problems -> 48 heat convolutions of
+all 24 fields per iteration), followed by the final objective and S of every pair.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16x3]
+                    [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (the only other place this
+file runs oracle code besides the cpu_baseline leg).  Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "heat-Sinkhorn iters/s at 720x1440 GL grid, batched; split-prec vs FP32 at 1e-4"
+NLAT, NLON, T_HEAT, PAIRS, CHECK_EVERY = 720, 1440, 1e-4, 8, 10
+EPS = 4.0 * T_HEAT
+RECIPE = "paper_uniform"
+SEED = 5000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--tau", type=float, default=math.inf)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nlat", type=int, default=NLAT, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def config(args, nlat, nlon):
+    return {"workload": f"heat-Sinkhorn divergence, GL {nlat}x{nlon} (lmax {nlat - 1}), t={T_HEAT:g} "
+                        f"(eps={EPS:g}), {PAIRS} pairs -> {3 * PAIRS} OT problems, "
+                        f"{'balanced' if math.isinf(args.tau) else f'tau={args.tau:g}'}, check every "
+                        f"{CHECK_EVERY}",
+            "nlat": nlat, "nlon": nlon, "pairs": PAIRS, "problems": 3 * PAIRS, "t": T_HEAT,
+            "tau": None if math.isinf(args.tau) else args.tau, "precision": args.precision,
+            "fields": f"{RECIPE} (Sec. 4.1 workload: U(0,1) per node, unit mass), seed {SEED}",
+            "l2": "working set > L2 every iteration (fields 2x100 MB, spectra 150 MB, table 0.37 GB)"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) taken while the timed region runs."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm.append(float(f[2]))
+                smax = float(f[3])
+                power.append(float(f[4]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[6:10]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def legendre_flops_per_launch(nlat, lmax, nfields):
+    """Algorithmic FLOPs of ONE Legendre launch (analysis or synthesis) over nfields
+    fields with the hemisphere fold: 2 * (sum over (m,p) blocks of rows) * nh * 2 nfields
+    = 2 * T * ceil(nlat/2) * 2 nfields, T = (lmax+1)(lmax+2)/2."""
+    T = (lmax + 1) * (lmax + 2) // 2
+    nh = (nlat + 1) // 2
+    return 2.0 * T * nh * 2 * nfields
+
+
+def fp32_simt_peak_tflops():
+    """152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2.070 GHz (max SM clock)."""
+    return 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of the workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle.grid import Grid
+    from oracle import sinkhorn as sk
+    from paper_2605_18389_gb300 import inputs
+    og = Grid(args.nlat)
+    og.pbar()
+    p, q = inputs.pairs(RECIPE, SEED, 1, og.x, og.nlon, og.a_ring, dtype=np.float32)
+    p = p.astype(np.float64)
+    q = q.astype(np.float64)
+    # one step = one Alg. 1 iteration of ONE (p,q) problem (a 1/24 sample of a batch step)
+    sk.sinkhorn(og, p, q, EPS, args.tau, T=max(1, args.warmup), C=0)
+    t0 = time.perf_counter()
+    sk.sinkhorn(og, p, q, EPS, args.tau, T=args.steps, C=0)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt / (3 * PAIRS)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(args, og.nlat, og.nlon),
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "iters/s",
+                             "sample": f"each step = 1 Alg. 1 iteration of 1 of the {3 * PAIRS} problems "
+                                       f"(numpy FP64, OpenBLAS on {cores} threads); value = problem-iterations/s "
+                                       f"/ {3 * PAIRS}"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(args, x, w, a_ring):
+    """Oracle on a bounded sample (~10-30 s): 2 iterations of the full 24-problem batch."""
+    from oracle.grid import Grid
+    from oracle import sinkhorn as sk
+    from paper_2605_18389_gb300 import inputs
+    og = Grid(args.nlat)
+    og.pbar()
+    p, q = inputs.pairs(RECIPE, SEED, PAIRS, og.x, og.nlon, og.a_ring, dtype=np.float32)
+    P = np.concatenate([p, p, q]).astype(np.float64)
+    Q = np.concatenate([q, p, q]).astype(np.float64)
+    iters = 2
+    t0 = time.perf_counter()
+    sk.sinkhorn(og, P, Q, EPS, args.tau, T=iters, C=0)
+    dt = time.perf_counter() - t0
+    return {"value": iters / dt, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{iters} Alg. 1 iterations of the full {3 * PAIRS}-problem batch at "
+                      f"{og.nlat}x{og.nlon} (FP64 numpy, OpenBLAS threads = {os.cpu_count()}); "
+                      f"grid/table set-up excluded", "seconds": dt}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2605_18389_gb300 import shot, inputs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        pg = dist
+    prec = shot.SHOT_FP32 if args.precision == "fp32" else shot.SHOT_BF16X3
+    nlat = args.nlat
+    nlon = 2 * nlat
+    g = shot.shot_grid_init(nlat, nlon, -1, prec)
+    x, w, a_ring = shot.shot_grid_nodes(g)
+    p, q = inputs.pairs(RECIPE, SEED + 1000 * rank, PAIRS, x, nlon, a_ring, dtype=np.float32)
+    pt = torch.from_numpy(p).cuda()
+    qt = torch.from_numpy(q).cuda()
+    u3 = torch.empty((3 * PAIRS, nlat, nlon), device="cuda")
+    v3 = torch.empty_like(u3)
+    shot.shot_grid_reserve(g, 3 * PAIRS)
+    kw = dict(tau=args.tau, tol=0.0, check_every=CHECK_EVERY, u3=u3, v3=v3)
+
+    # warm-up (untimed)
+    shot.shot_divergence(g, pt, qt, EPS, max_iter=args.warmup, **kw)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    # timed region: device-resident inputs
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    n0 = shot.shot_launch_count()
+    shot.shot_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc, res = shot.shot_divergence(g, pt, qt, EPS, max_iter=args.steps, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    shot.shot_profile_enable(False)
+    launches = shot.shot_launch_count() - n0
+    barrier()
+    clk = clocks.stop()
+    prof = shot.shot_profile_read()
+    ms = e0.elapsed_time(e1)
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1e3)
+
+    # end to end through the public call with host buffers: H2D of p, q inside the region
+    ph = torch.from_numpy(p).pin_memory()
+    qh = torch.from_numpy(q).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pd = ph.to("cuda", non_blocking=True)
+    qd = qh.to("cuda", non_blocking=True)
+    rc2, res2 = shot.shot_divergence(g, pd, qd, EPS, max_iter=args.steps, **kw)   # S, status -> host
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * args.steps / e2e_s, "unit": "iters/s",
+           "h2d_bytes_per_step": (p.nbytes + q.nbytes) / args.steps,
+           "d2h_bytes_per_step": (res2["S"].nbytes + res2["S_dual"].nbytes + res2["status"].nbytes
+                                  + res2["ot3"].nbytes + res2["iters3"].nbytes) / args.steps}
+
+    # roofline of the dominant kernel over the timed region
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    peaks = measured_peaks()
+    nfields = 3 * PAIRS
+    if dom in ("legendre_analysis", "legendre_synthesis"):
+        fl = legendre_flops_per_launch(nlat, nlat - 1, nfields)
+        achieved = fl / (dom_ms / dom_n / 1e3) / 1e12
+        if prec == shot.SHOT_FP32:
+            peak, bound, unit = fp32_simt_peak_tflops(), "alu", "TFLOP/s"
+            peak_src = "FP32 FFMA peak derived: 152 SMs x 128 lanes x 2 x 2.070 GHz"
+        else:
+            peak, bound, unit = peaks.get("bf16_tflops_sustained", 1700.0), "tensor", "TFLOP/s"
+            peak_src = "bf16 sustained, of measured (MEASURED_PEAKS.json)"
+        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                "algorithmic_per_launch": fl, "launches": dom_n, "avg_launch_ms": dom_ms / dom_n}
+    else:
+        n = nlat * nlon
+        by = nfields * n * 4 * 2.0  # fields in, spectra out (same size), FP32
+        achieved = by / (dom_ms / dom_n / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": "hbm_gbs, of measured",
+                "algorithmic_per_launch": by, "launches": dom_n, "avg_launch_ms": dom_ms / dom_n}
+    share = {k: round(v[0] / sum(x[0] for x in kinds.values()), 4) for k, v in kinds.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config(args, nlat, nlon), "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "roofline": roof, "kernel_share": share,
+            "status": {"rc": int(rc), "S_finite": bool(np.all(np.isfinite(res["S"])))}}
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(args, x, w, a_ring)
+    shot.shot_grid_free(g)
+    if rank == 0:
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * shot.h -- C ABI of the GB300 heat-kernel Sinkhorn library (SHOT: Spherical
+ * Harmonic Optimal Transport).
+ *
+ * The library applies the heat kernel K_t on S^2 to batches of fields sampled on a
+ * Gauss-Legendre (GL) grid and runs Algorithm 1 ("Spherical Harmonic Sinkhorn",
+ * App. C) and the Sinkhorn divergence of eq. (sinkhorn-divergence) on top of it.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - A FIELD is nlat*nlon contiguous float32 values, row-major [nlat][nlon].  Row j
+ *   is the GL ring with x_j = cos(theta_j) DESCENDING (north to south); column k is
+ *   longitude phi_k = 2*pi*k/nlon.  Batches are [batch][nlat][nlon], contiguous.
+ * - The band limit is lmax (degrees 0..lmax, orders 0..lmax, triangular).  The
+ *   default lmax = nlat-1 makes the GL quadrature exact for every product of two
+ *   band-limited fields (App. C.1, "Gauss-Legendre").
+ * - Area weights (App. C.2): every node of ring j has a_j = w_j * 2*pi/nlon with w_j
+ *   the GL weight, so that sum_i a_i = 4*pi.
+ * - Field pointers are DEVICE pointers owned by the caller.  Per-problem scalar
+ *   outputs of the solver calls are HOST pointers (those calls synchronise the
+ *   stream before they return).  shot_heat_apply and the transform calls are
+ *   asynchronous on the given stream.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ * - A grid handle owns its tables and a workspace that grows on demand; calls that
+ *   use the same handle must not run concurrently (serialise them on one stream).
+ * - Every call returns an int status: SHOT_OK (0), a positive warning, or a
+ *   negative error.  No C++ exception crosses this boundary.  shot_last_error()
+ *   gives a message for the calling thread's last error.
+ */
+#ifndef SHOT_H
+#define SHOT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define SHOT_OK                  0
+#define SHOT_WARN_NOT_CONVERGED  1   /* tol > 0 and the marginal check never passed within max_iter */
+#define SHOT_ERR_INVALID_ARG    -1   /* bad size, NULL pointer, eps <= 0, tau <= 0, ... */
+#define SHOT_ERR_CUDA           -2   /* a CUDA runtime call failed (message in shot_last_error) */
+#define SHOT_ERR_OOM            -3   /* device allocation failed */
+#define SHOT_ERR_UNSUPPORTED    -4   /* nlon has a prime factor other than 2, 3, 5, or an unbuilt mode */
+#define SHOT_ERR_NONPOSITIVE    -5   /* some K v <= 0: the update of Alg. 1 is undefined (App. C.4) */
+#define SHOT_ERR_NONFINITE      -6   /* a scaling became inf/NaN (FP32 range exceeded) */
+#define SHOT_ERR_TIMEOUT        -7   /* a bounded device-side wait expired */
+
+/* ---- precision of the Legendre contractions ----------------------------- */
+#define SHOT_FP32    0   /* FP32 SIMT FFMA */
+#define SHOT_BF16X3  1   /* tcgen05 tensor cores, bf16 hi/lo split of both operands, 3 products, FP32 accumulate */
+
+/* ---- source of the associated Legendre values ---------------------------- */
+#define SHOT_TABLE       0   /* precomputed parity-folded table, O(nlat^3) memory */
+
+/* ---- solver flags -------------------------------------------------------- */
+#define SHOT_FLAG_NORM_L1     0x1  /* check sum_i a_i|u_i(Kv)_i - p_i| / sum_i a_i p_i instead of the relative L2 */
+#define SHOT_FLAG_WARM_START  0x2  /* u and v hold the initial scalings instead of 1 */
+
+typedef struct shot_grid_s* shot_grid;
+
+/* Message of the calling thread's last error ("" if none).  Copies at most
+ * len-1 bytes into buf and NUL-terminates; returns the full message length. */
+int shot_last_error(char* buf, int len);
+
+/* Build a GL grid: nodes and weights by Newton's method on P_nlat in FP64 on the
+ * device (App. C.1), area weights (App. C.2) and the orthonormal associated
+ * Legendre table Pbar_lm(x_j) (App. B), folded by parity over the two hemispheres.
+ *   out        receives the handle (host pointer)
+ *   nlat >= 2; nlon >= 2*lmax+1 with prime factors in {2,3,5}; lmax = -1 means nlat-1,
+ *              else 0 <= lmax <= nlat-1
+ *   precision  SHOT_FP32 or SHOT_BF16X3; legendre_mode SHOT_TABLE
+ * Memory: about 2*(lmax+1)(lmax+2)/2 * ceil(nlat/2) * 4 bytes of table (0.37 GB at 720).
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Synchronises `stream`. */
+int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision,
+                   int legendre_mode, void* stream);
+
+/* Release every device resource of the handle (NULL is a no-op). */
+int shot_grid_free(shot_grid g);
+
+/* nlat, nlon, lmax, precision, legendre_mode of the handle (host outputs; any may be NULL). */
+int shot_grid_info(shot_grid g, int* nlat, int* nlon, int* lmax, int* precision, int* legendre_mode);
+
+/* GL nodes x_j (descending) and weights w_j (sum 2) into host arrays of nlat
+ * doubles, and the per-ring area weights a_j = w_j*2*pi/nlon (App. C.2).  Any
+ * pointer may be NULL. */
+int shot_grid_nodes(shot_grid g, double* x, double* w, double* a_ring);
+
+/* Pre-size the workspace for calls on up to `nfields` fields (optional; calls grow it). */
+int shot_grid_reserve(shot_grid g, int nfields);
+
+/* Heat convolution, Sec. 3.2: out = HeatConv(in; h), h_l = exp(-t l(l+1)), for
+ * nfields fields:  ring real-DFT -> per-order Legendre analysis with area weights ->
+ * scaling by h_l -> Legendre synthesis -> inverse ring DFT.
+ *   in, out   device [nfields][nlat][nlon] float32 (may not alias)
+ *   t >= 0    heat time (Alg. 1 uses t = eps/4)
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, OOM, CUDA. */
+int shot_heat_apply(shot_grid g, double t, const float* in, float* out, int nfields, void* stream);
+
+/* Spherical harmonic analysis (App. B: c_lm = <f, Y_lm> by GL quadrature) of nfields
+ * real fields.  coeffs: device float32 [nfields][lmax+1][lmax+1][2] (re, im) with
+ * entry [l][m] for 0 <= m <= l; entries with m > l are written as 0.  Orthonormal
+ * Y_lm with the Condon-Shortley phase.  Asynchronous. */
+int shot_sht_analysis(shot_grid g, const float* in, float* coeffs, int nfields, void* stream);
+
+/* Inverse of shot_sht_analysis for real fields: out = sum_{l,|m|<=l} c_lm Y_lm using
+ * c_{l,-m} = (-1)^m conj(c_lm).  Entries with m > l and Im c_l0 are ignored.  Asynchronous. */
+int shot_sht_synthesis(shot_grid g, const float* coeffs, float* out, int nfields, void* stream);
+
+/* Algorithm 1 (App. C) on `batch` independent problems, each stopping on its own.
+ *   p, q        device [batch][nlat][nlon] float32 marginals (p_i, q_i >= 0)
+ *   eps > 0     entropic parameter; the heat time is t = eps/4 (Alg. 1, step 1)
+ *   tau         marginal penalty; INFINITY = balanced branch, else tau > 0 selects the
+ *               unbalanced branch with the translation-invariant step
+ *   max_iter    T;  tol = delta;  check_every = C (0 disables the periodic check)
+ *   flags       SHOT_FLAG_* ; WARM_START reads u, v as the initial scalings
+ *   u, v        device [batch][nlat][nlon] float32 outputs (inputs with WARM_START)
+ *   ot          host [batch] or NULL: Alg. 1's return (dual form of App. C.2)
+ *   ot_dual     host [batch] or NULL: ot - eps * m(pi)
+ *   mass_pi     host [batch] or NULL: m(pi) = sum_i a_i u_i (K v)_i
+ *   iters       host [batch] or NULL: iterations run (the breakdown iteration on error)
+ *   err         host [batch] or NULL: marginal error of the returned u, v
+ *   status      host [batch] or NULL: per-problem SHOT_OK / SHOT_WARN_NOT_CONVERGED /
+ *               SHOT_ERR_NONPOSITIVE / SHOT_ERR_NONFINITE
+ * Returns the most severe per-problem status (or an argument/CUDA error).
+ * Outputs of a problem that broke down are NaN.  Synchronises `stream`. */
+int shot_sinkhorn(shot_grid g, const float* p, const float* q, int batch,
+                  double eps, double tau, int max_iter, double tol, int check_every, int flags,
+                  float* u, float* v, double* ot, double* ot_dual, double* mass_pi,
+                  int* iters, float* err, int* status, void* stream);
+
+/* Sinkhorn divergence, eq. (sinkhorn-divergence), for `batch` pairs (p_b, q_b):
+ *   S      = OT(p,q) - (OT(p,p) + OT(q,q))/2 + eps/2 (m(p) - m(q))^2  with OT = Alg. 1's return
+ *   S_dual = the same with OT replaced by OT - eps*m(pi) and no mass-difference term
+ * (the two coincide for converged balanced problems).  The 3*batch problems run in
+ * one batch ordered [(p_b,q_b)]_b, [(p_b,p_b)]_b, [(q_b,q_b)]_b.
+ *   S, S_dual, status  host [batch] (S_dual may be NULL)
+ *   u3, v3             device [3*batch][nlat][nlon] or NULL: the scalings of all problems
+ *   ot3, iters3        host [3*batch] or NULL
+ * Other arguments as in shot_sinkhorn.  Synchronises `stream`. */
+int shot_divergence(shot_grid g, const float* p, const float* q, int batch, double eps, double tau,
+                    int max_iter, double tol, int check_every, int flags,
+                    double* S, double* S_dual, int* status,
+                    float* u3, float* v3, double* ot3, int* iters3, void* stream);
+
+/* ---- measurement helpers (no counterpart in the paper) -------------------
+ * shot_launch_count: total number of CUDA kernels this library has launched in the
+ *   process (host counter; *n receives it).
+ * shot_profile_enable(1): from now on every launch is bracketed by two CUDA events on
+ *   its stream; shot_profile_enable(0) stops recording.
+ * shot_profile_read: waits for the recorded events, then writes per kind the summed
+ *   device time in ms and the number of launches, and clears the records.  Kinds:
+ *   0 ring DFT (forward), 1 Legendre analysis, 2 Legendre synthesis,
+ *   3 inverse ring DFT + Sinkhorn epilogue, 4 reductions and small kernels.
+ *   ms, launches: host arrays of nkinds entries. */
+int shot_launch_count(long long* n);
+int shot_profile_enable(int on);
+int shot_profile_read(double* ms, long long* launches, int nkinds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHOT_H */

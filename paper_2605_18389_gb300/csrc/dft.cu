@@ -1,0 +1,281 @@
+// Ring DFTs of the semi-naive SHT and the fused Sinkhorn epilogues.
+//
+// Forward (App. C.1, last paragraph; App. B quadrature): for a field f and ring j,
+//   F_m(j) = sum_k f_jk e^{-i m phi_k},  m = 0..lmax.
+// Rings j (north) and J = nlat-1-j (south) are transformed together as ONE complex
+// sequence z = f_j + i f_J; F_N(m) = (Z(m) + conj Z(N-m))/2, F_S(m) = (Z(m) - conj Z(N-m))/(2i).
+// Because Pbar_lm(-x) = (-1)^{l+m} Pbar_lm(x) and GL nodes are symmetric, the quadrature
+// sum over j splits into an even part (l-m even) over S = a_j (F_N + F_S) and an odd part
+// (l-m odd) over D = a_j (F_N - F_S) on the north half only.  The kernel writes S and D
+// into the (m, parity) blocks X[2m+p][jh][2f + {re,im}].
+//
+// Inverse: the synthesis produces E_m(jh) (even degrees) and O_m(jh) (odd degrees); the
+// north ring has G_N = E + O, the south ring G_S = E - O, and
+//   (K v)(theta_j, phi_k) = Re G_0(j) + 2 Re sum_{m>=1} G_m(j) e^{i m phi_k}
+// is evaluated for both rings by one inverse complex FFT of the Hermitian-extended
+// spectrum Z(m) = G_N(m) + i G_S(m), Z(N-m) = conj G_N(m) + i conj G_S(m).
+// The epilogue then applies Algorithm 1's pointwise step to K v (update, check or
+// final objective) and reduces per-field partial sums (FP64) per ring pair.
+#include "fft.cuh"
+
+namespace shot {
+
+namespace {
+
+constexpr int kThreads = 512;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block reduction of NPART doubles; result valid in thread 0.
+__device__ void block_sum4(double (&acc)[NPART], double* red /* [32*NPART] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NPART; ++i) acc[i] = warp_sum(acc[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) red[wid * NPART + i] = acc[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w)
+#pragma unroll
+      for (int i = 0; i < NPART; ++i) acc[i] += red[w * NPART + i];
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kThreads) k_dft_fwd(
+    const float* __restrict__ in, int nf, int nlat, int nlon, int lmax, int nh,
+    const float* __restrict__ a_ring, const ProbState* __restrict__ ps, int scale_which,
+    float* __restrict__ X, int ldc, FftPlan pl, const float2* __restrict__ tw_g, int FG) {
+  extern __shared__ float2 sm[];
+  const int N = nlon;
+  float2* tw = sm;
+  float2* b0 = sm + N;
+  float2* b1 = b0 + FG * N;
+  const int jh = blockIdx.x;
+  const int f0 = blockIdx.y * FG;
+  const int nfg = min(FG, nf - f0);
+  const int j = jh, J = nlat - 1 - jh;
+
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
+  for (int idx = threadIdx.x; idx < nfg * N; idx += blockDim.x) {
+    const int q = idx / N, k = idx - q * N;
+    const size_t base = (size_t)(f0 + q) * nlat * nlon;
+    const float re = __ldg(in + base + (size_t)j * nlon + k);
+    const float im = (J != j) ? __ldg(in + base + (size_t)J * nlon + k) : 0.f;
+    b0[idx] = make_float2(re, im);
+  }
+  __syncthreads();
+  const float2* Z = fft_smem<false>(b0, b1, tw, pl, nfg, N);
+
+  const float aj = a_ring[j];
+  const int nm = lmax + 1;
+  for (int idx = threadIdx.x; idx < nm * nfg; idx += blockDim.x) {
+    const int m = idx / nfg, q = idx - m * nfg;
+    const int f = f0 + q;
+    float sc = aj;
+    if (scale_which == 1) sc *= (float)ps[f].beta;
+    const float2 zm = Z[q * N + m];
+    const float2 zn = Z[q * N + (m ? N - m : 0)];
+    const float2 FN = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
+    const float2 FS = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
+    const float2 S = make_float2(sc * (FN.x + FS.x), sc * (FN.y + FS.y));
+    const float2 D = make_float2(sc * (FN.x - FS.x), sc * (FN.y - FS.y));
+    *reinterpret_cast<float2*>(X + ((size_t)(2 * m) * nh + jh) * ldc + 2 * f) = S;
+    *reinterpret_cast<float2*>(X + ((size_t)(2 * m + 1) * nh + jh) * ldc + 2 * f) = D;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_idft(
+    const float* __restrict__ Y, int ldc, int nf, int nlat, int nlon, int lmax, int nh,
+    const float* __restrict__ a_ring, FftPlan pl, const float2* __restrict__ tw_g, int FG,
+    EpiParams ep) {
+  extern __shared__ float2 sm[];
+  __shared__ double red[32 * NPART];
+  const int N = nlon;
+  float2* tw = sm;
+  float2* b0 = sm + N;
+  float2* b1 = b0 + FG * N;
+  const int jh = blockIdx.x;
+  const int f0 = blockIdx.y * FG;
+  const int nfg = min(FG, nf - f0);
+  const int j = jh, J = nlat - 1 - jh;
+
+  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
+  // zero the band lmax < m < N - lmax
+  const int nz = N - 2 * lmax - 1;
+  for (int idx = threadIdx.x; idx < nfg * nz; idx += blockDim.x) {
+    const int q = idx / nz, k = idx - q * nz;
+    b0[q * N + lmax + 1 + k] = make_float2(0.f, 0.f);
+  }
+  const int nm = lmax + 1;
+  for (int idx = threadIdx.x; idx < nm * nfg; idx += blockDim.x) {
+    const int m = idx / nfg, q = idx - m * nfg;
+    const int f = f0 + q;
+    const float2 E = *reinterpret_cast<const float2*>(Y + ((size_t)(2 * m) * nh + jh) * ldc + 2 * f);
+    float2 O = make_float2(0.f, 0.f);
+    if (m < lmax) O = *reinterpret_cast<const float2*>(Y + ((size_t)(2 * m + 1) * nh + jh) * ldc + 2 * f);
+    const float2 GN = make_float2(E.x + O.x, E.y + O.y);
+    const float2 GS = make_float2(E.x - O.x, E.y - O.y);
+    if (m == 0) {
+      b0[q * N] = make_float2(GN.x, GS.x);
+    } else {
+      b0[q * N + m] = make_float2(GN.x - GS.y, GN.y + GS.x);
+      b0[q * N + N - m] = make_float2(GN.x + GS.y, GS.x - GN.y);
+    }
+  }
+  __syncthreads();
+  const float2* z = fft_smem<true>(b0, b1, tw, pl, nfg, N);
+
+  const float aj = a_ring[j];
+  const double ajd = (double)aj;
+  const int nrings = (J != j) ? 2 : 1;
+  for (int q = 0; q < nfg; ++q) {
+    const int f = f0 + q;
+    double acc[NPART] = {0.0, 0.0, 0.0, 0.0};
+    const size_t fbase = (size_t)f * nlat * nlon;
+    if (ep.mode == EPI_PLAIN) {
+      for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
+        const int r = idx / N, k = idx - r * N;
+        const float2 zz = z[q * N + k];
+        const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
+        ep.out[o] = r ? zz.y : zz.x;
+      }
+      continue;
+    }
+    ProbState* P = ep.ps + f;
+    if (ep.mode == EPI_UPDATE) {
+      if (!P->active) continue;   // uniform across the block
+      const float* mg = ep.marg[f];
+      for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
+        const int r = idx / N, k = idx - r * N;
+        const float2 zz = z[q * N + k];
+        const float kv = r ? zz.y : zz.x;
+        const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
+        const float pm = __ldg(mg + (size_t)(r ? J : j) * nlon + k);
+        const float ratio = pm / kv;
+        float u;
+        if (ep.balanced) {
+          u = ratio;
+          acc[0] += (double)u;
+        } else {
+          u = powf(ratio, ep.gamma);
+          if (pm > 0.f) acc[0] += ajd * (double)pm * (double)powf(ratio, -ep.eps_over_taueps);
+        }
+        if (!(kv > 0.f)) {
+          if (kv <= 0.f) acc[2] += 1.0;
+          else acc[3] += 1.0;   // NaN
+        }
+        if (!isfinite(u) || !isfinite(kv)) acc[3] += 1.0;
+        ep.out[o] = u;
+      }
+    } else if (ep.mode == EPI_CHECK) {
+      if (!P->active) continue;
+      const float* mg = ep.marg[f];
+      const float al = (float)P->alpha;
+      for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
+        const int r = idx / N, k = idx - r * N;
+        const float2 zz = z[q * N + k];
+        const float kv = r ? zz.y : zz.x;
+        const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
+        const float pm = __ldg(mg + (size_t)(r ? J : j) * nlon + k);
+        const double d = (double)(al * ep.other[o]) * (double)kv - (double)pm;
+        if (ep.norm_l1) {
+          acc[0] += ajd * fabs(d);
+          acc[1] += ajd * (double)pm;
+        } else {
+          acc[0] += d * d;
+          acc[1] += (double)pm * (double)pm;
+        }
+      }
+    } else {  // EPI_FINAL: z = K v_true; ep.other = u buffer, ep.out = v buffer
+      if (P->status < 0) continue;
+      const float* pp = ep.marg[f];
+      const float* qq = ep.marg2[f];
+      const double al = P->alpha, be = P->beta;
+      for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
+        const int r = idx / N, k = idx - r * N;
+        const float2 zz = z[q * N + k];
+        const float kv = r ? zz.y : zz.x;
+        const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
+        const size_t om = (size_t)(r ? J : j) * nlon + k;
+        const float pm = __ldg(pp + om), qm = __ldg(qq + om);
+        const float uu = (float)(al * (double)ep.other[o]);
+        const float vv = (float)(be * (double)ep.out[o]);
+        ep.other[o] = uu;
+        ep.out[o] = vv;
+        const double d = (double)uu * (double)kv - (double)pm;
+        if (ep.norm_l1) {
+          acc[0] += ajd * fabs(d);
+          acc[1] += ajd * (double)pm;
+        } else {
+          acc[0] += d * d;
+          acc[1] += (double)pm * (double)pm;
+        }
+        acc[2] += ajd * (double)uu * (double)kv;
+        const double lu = log((double)uu), lv = log((double)vv);
+        double t;
+        if (ep.balanced) {
+          t = (pm > 0.f ? ep.eps * lu * pm : 0.0) + (qm > 0.f ? ep.eps * lv * qm : 0.0);
+        } else {
+          const double e = -ep.eps / ep.tau;
+          t = (pm > 0.f ? ep.tau * (1.0 - exp(e * lu)) * pm : 0.0) +
+              (qm > 0.f ? ep.tau * (1.0 - exp(e * lv)) * qm : 0.0);
+        }
+        acc[3] += ajd * t;
+      }
+    }
+    block_sum4(acc, red);
+    if (threadIdx.x == 0) {
+      double* pt = ep.part + ((size_t)f * nh + jh) * NPART;
+#pragma unroll
+      for (int i = 0; i < NPART; ++i) pt[i] = acc[i];
+    }
+  }
+}
+
+int pick_fg(int N, int nf) {
+  // shared memory: twiddles + two ping-pong buffers of FG sequences
+  const int budget = 200 * 1024 / 8;
+  int fg = (budget - N) / (2 * N);
+  fg = fg < 1 ? 1 : fg;
+  if (fg > 32) fg = 32;
+  if (fg > nf) fg = nf;
+  return fg;
+}
+
+}  // namespace
+
+int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
+                   float* X, int ldc, cudaStream_t st) {
+  const int FG = pick_fg(g.nlon, nf);
+  const size_t smem = (size_t)(g.nlon + 2 * FG * g.nlon) * sizeof(float2);
+  SHOT_CUDA(cudaFuncSetAttribute(k_dft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(g.nh, (nf + FG - 1) / FG);
+  ProfScope prof(PK_DFT, st);
+  count_launch();
+  k_dft_fwd<<<grid, kThreads, smem, st>>>(in, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, ps, scale_which,
+                                          X, ldc, g.plan, g.tw_d, FG);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
+}
+
+int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
+  const int FG = pick_fg(g.nlon, nf);
+  const size_t smem = (size_t)(g.nlon + 2 * FG * g.nlon) * sizeof(float2);
+  SHOT_CUDA(cudaFuncSetAttribute(k_idft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(g.nh, (nf + FG - 1) / FG);
+  ProfScope prof(PK_IDFT, st);
+  count_launch();
+  k_idft<<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, FG,
+                                       ep);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
+}
+
+}  // namespace shot

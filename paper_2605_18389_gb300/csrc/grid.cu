@@ -1,0 +1,311 @@
+// Grid set-up: Gauss-Legendre nodes and weights, area weights, ring-DFT twiddles, the
+// parity-folded orthonormal associated Legendre table, tile lists and workspaces.
+//
+// FP64 is used on the device only here (nodes, weights, table seeds/recurrence), the
+// values being rounded to FP32 (or split into bf16 hi + lo) for the hot path.
+#include <math.h>
+#include <algorithm>
+
+#include "shot_internal.cuh"
+
+namespace shot {
+
+namespace {
+
+// GL nodes by Newton's method on P_n from cos(pi (k - 1/4)/(n + 1/2)) (App. C.1,
+// "Gauss-Legendre": the latitudes are the roots of P_nlat); w = 2/((1-x^2) P_n'(x)^2).
+// One thread per north-hemisphere node; the south half is its exact mirror.
+__global__ void k_gl_nodes(int n, double* __restrict__ x, double* __restrict__ w) {
+  const int nh = (n + 1) / 2;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nh) return;
+  double xj = cos(M_PI * (j + 0.75) / (n + 0.5));
+  double dp = 1.0;
+  for (int it = 0; it < 60; ++it) {
+    double p0 = 1.0, p1 = xj;
+    for (int l = 2; l <= n; ++l) {
+      const double p2 = ((2 * l - 1) * xj * p1 - (l - 1) * p0) / l;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (n == 1) { p0 = 1.0; p1 = xj; }
+    dp = n * (p0 - xj * p1) / (1.0 - xj * xj);
+    const double dx = p1 / dp;
+    xj -= dx;
+    if (fabs(dx) < 1e-16) break;
+  }
+  {  // derivative at the converged node
+    double p0 = 1.0, p1 = xj;
+    for (int l = 2; l <= n; ++l) {
+      const double p2 = ((2 * l - 1) * xj * p1 - (l - 1) * p0) / l;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (n == 1) { p0 = 1.0; p1 = xj; }
+    dp = n * (p0 - xj * p1) / (1.0 - xj * xj);
+  }
+  if ((n & 1) && j == nh - 1) xj = 0.0;   // the equator node of an odd grid
+  const double wj = 2.0 / ((1.0 - xj * xj) * dp * dp);
+  x[j] = xj;
+  w[j] = wj;
+  x[n - 1 - j] = -xj;
+  w[n - 1 - j] = wj;
+}
+
+__global__ void k_twiddles(int N, float2* __restrict__ tw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  double s, c;
+  sincospi(2.0 * k / N, &s, &c);
+  tw[k] = make_float2((float)c, (float)-s);
+}
+
+__global__ void k_area(int nlat, int nlon, const double* __restrict__ w, float* __restrict__ a) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < nlat) a[j] = (float)(w[j] * (2.0 * M_PI / nlon));
+}
+
+// Orthonormal Pbar_lm(x_jh) (App. B) by the standard recurrences:
+//   Pbar_00 = 1/sqrt(4 pi); Pbar_mm = -sqrt((2m+1)/(2m)) sin(theta) Pbar_{m-1,m-1};
+//   Pbar_{m+1,m} = sqrt(2m+3) x Pbar_mm;
+//   Pbar_lm = a_lm (x Pbar_{l-1,m} - b_lm Pbar_{l-2,m}),
+//   a_lm = sqrt((4l^2-1)/(l^2-m^2)), b_lm = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)).
+// One thread per (m, jh); row l goes to block (m, (l-m) mod 2), row (l-m)/2.
+__global__ void k_pbar(int lmax, int nh, const double* __restrict__ x, const long long* __restrict__ row_off,
+                       int ldt, float* __restrict__ tab, __nv_bfloat16* __restrict__ hi,
+                       __nv_bfloat16* __restrict__ lo) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (j >= nh) return;
+  const double xj = x[j];
+  const double st = sqrt((1.0 - xj) * (1.0 + xj));
+  double pmm = 0.28209479177387814;   // 1/sqrt(4 pi)
+  for (int k = 1; k <= m; ++k) pmm *= -sqrt((2.0 * k + 1.0) / (2.0 * k)) * st;
+  auto store = [&](int l, double val) {
+    const int d = l - m;
+    const int blk = 2 * m + (d & 1);
+    const size_t off = (size_t)(row_off[blk] + (d >> 1)) * ldt + j;
+    if (tab) tab[off] = (float)val;
+    if (hi) {
+      const __nv_bfloat16 h = __double2bfloat16(val);
+      hi[off] = h;
+      lo[off] = __double2bfloat16(val - (double)__bfloat162float(h));
+    }
+  };
+  store(m, pmm);
+  if (m == lmax) return;
+  double p2 = pmm;
+  double p1 = sqrt(2.0 * m + 3.0) * xj * pmm;
+  store(m + 1, p1);
+  for (int l = m + 2; l <= lmax; ++l) {
+    const double ll = (double)l * l, mm = (double)m * m, l1 = (double)(l - 1) * (l - 1);
+    const double a = sqrt((4.0 * ll - 1.0) / (ll - mm));
+    const double b = sqrt((l1 - mm) / (4.0 * l1 - 1.0));
+    const double pl = a * (xj * p1 - b * p2);
+    store(l, pl);
+    p2 = p1;
+    p1 = pl;
+  }
+}
+
+__global__ void k_heat(int lmax, double t, float* __restrict__ h) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l <= lmax) h[l] = (float)exp(-t * (double)l * (double)(l + 1));
+}
+
+// C[row_off[blk] + i][2f + {0,1}]  <->  coeffs[f][l][m][{re,im}],  l = m + p + 2i
+__global__ void k_coeff_gather(int lmax, int nf, const long long* __restrict__ row_off,
+                               const float* __restrict__ C, int ldc, float* __restrict__ coeffs) {
+  const int L = lmax + 1;
+  const size_t total = (size_t)nf * L * L;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(idx % L);
+    const int l = (int)((idx / L) % L);
+    const int f = (int)(idx / ((size_t)L * L));
+    float2 v = make_float2(0.f, 0.f);
+    if (m <= l) {
+      const int d = l - m;
+      const long long row = row_off[2 * m + (d & 1)] + (d >> 1);
+      v = *reinterpret_cast<const float2*>(C + (size_t)row * ldc + 2 * f);
+    }
+    reinterpret_cast<float2*>(coeffs)[idx] = v;
+  }
+}
+
+__global__ void k_coeff_scatter(int lmax, int nf, const long long* __restrict__ row_off,
+                                const float* __restrict__ coeffs, float* __restrict__ C, int ldc) {
+  const int L = lmax + 1;
+  const size_t total = (size_t)nf * L * L;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(idx % L);
+    const int l = (int)((idx / L) % L);
+    const int f = (int)(idx / ((size_t)L * L));
+    if (m > l) continue;
+    float2 v = reinterpret_cast<const float2*>(coeffs)[idx];
+    if (m == 0) v.y = 0.f;
+    const int d = l - m;
+    const long long row = row_off[2 * m + (d & 1)] + (d >> 1);
+    *reinterpret_cast<float2*>(C + (size_t)row * ldc + 2 * f) = v;
+  }
+}
+
+}  // namespace
+
+bool make_fft_plan(int N, FftPlan* pl) {
+  pl->N = N;
+  pl->nst = 0;
+  int n = N;
+  auto push = [&](int r) {
+    if (pl->nst >= 12) return false;
+    pl->R[pl->nst++] = r;
+    n /= r;
+    return true;
+  };
+  while (n % 8 == 0) if (!push(8)) return false;
+  while (n % 4 == 0) if (!push(4)) return false;
+  while (n % 2 == 0) if (!push(2)) return false;
+  while (n % 3 == 0) if (!push(3)) return false;
+  while (n % 5 == 0) if (!push(5)) return false;
+  return n == 1 && N >= 1;
+}
+
+int build_grid_tables(Grid& g, cudaStream_t st) {
+  const int nlat = g.nlat, nh = g.nh, L = g.lmax + 1;
+  SHOT_CUDA(cudaMalloc(&g.x_d, nlat * sizeof(double)));
+  SHOT_CUDA(cudaMalloc(&g.w_d, nlat * sizeof(double)));
+  SHOT_CUDA(cudaMalloc(&g.a_d, nlat * sizeof(float)));
+  SHOT_CUDA(cudaMalloc(&g.tw_d, g.nlon * sizeof(float2)));
+  SHOT_CUDA(cudaMalloc(&g.h_d, L * sizeof(float)));
+  count_launch(5);
+  k_gl_nodes<<<(nh + 127) / 128, 128, 0, st>>>(nlat, g.x_d, g.w_d);
+  k_twiddles<<<(g.nlon + 255) / 256, 256, 0, st>>>(g.nlon, g.tw_d);
+  k_area<<<(nlat + 255) / 256, 256, 0, st>>>(nlat, g.nlon, g.w_d, g.a_d);
+  k_heat<<<(L + 255) / 256, 256, 0, st>>>(g.lmax, 0.0, g.h_d);
+  SHOT_CUDA(cudaGetLastError());
+
+  // blocks (m, p): rows M = (lmax - m - p)/2 + 1 when lmax - m - p >= 0
+  g.nblk = 2 * L;
+  g.M.assign(g.nblk, 0);
+  g.row_off.assign(g.nblk + 1, 0);
+  for (int m = 0; m < L; ++m)
+    for (int p = 0; p < 2; ++p) {
+      const int d = g.lmax - m - p;
+      g.M[2 * m + p] = d >= 0 ? d / 2 + 1 : 0;
+    }
+  for (int b = 0; b < g.nblk; ++b) g.row_off[b + 1] = g.row_off[b] + g.M[b];
+  g.rows_total = g.row_off[g.nblk];
+  g.ldt = (nh + 15) / 16 * 16;
+  SHOT_CUDA(cudaMalloc(&g.M_d, g.nblk * sizeof(int)));
+  SHOT_CUDA(cudaMalloc(&g.row_off_d, (g.nblk + 1) * sizeof(long long)));
+  SHOT_CUDA(cudaMemcpyAsync(g.M_d, g.M.data(), g.nblk * sizeof(int), cudaMemcpyHostToDevice, st));
+  SHOT_CUDA(cudaMemcpyAsync(g.row_off_d, g.row_off.data(), (g.nblk + 1) * sizeof(long long),
+                            cudaMemcpyHostToDevice, st));
+
+  const size_t tab_elems = (size_t)g.rows_total * g.ldt;
+  float* tab = nullptr;
+  __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+  if (g.precision == SHOT_FP32) {
+    SHOT_CUDA(cudaMalloc(&g.tab, tab_elems * sizeof(float)));
+    SHOT_CUDA(cudaMemsetAsync(g.tab, 0, tab_elems * sizeof(float), st));
+    tab = g.tab;
+  } else {
+    SHOT_CUDA(cudaMalloc(&g.tab_hi, tab_elems * sizeof(__nv_bfloat16)));
+    SHOT_CUDA(cudaMalloc(&g.tab_lo, tab_elems * sizeof(__nv_bfloat16)));
+    SHOT_CUDA(cudaMemsetAsync(g.tab_hi, 0, tab_elems * sizeof(__nv_bfloat16), st));
+    SHOT_CUDA(cudaMemsetAsync(g.tab_lo, 0, tab_elems * sizeof(__nv_bfloat16), st));
+    hi = g.tab_hi;
+    lo = g.tab_lo;
+  }
+  dim3 gp((nh + 127) / 128, L);
+  count_launch();
+  k_pbar<<<gp, 128, 0, st>>>(g.lmax, nh, g.x_d, g.row_off_d, g.ldt, tab, hi, lo);
+  SHOT_CUDA(cudaGetLastError());
+
+  // tile lists: analysis tiles cover the rows i of each block, synthesis tiles the nodes
+  std::vector<Tile> ta, ts;
+  for (int b = 0; b < g.nblk; ++b) {
+    for (int r = 0; r < g.M[b]; r += g.bm_ana) ta.push_back({b, r});
+    if (g.M[b] > 0)
+      for (int r = 0; r < nh; r += g.bm_syn) ts.push_back({b, r});
+  }
+  // largest contraction first (synthesis work is proportional to M)
+  std::stable_sort(ts.begin(), ts.end(), [&](const Tile& a, const Tile& b) { return g.M[a.blk] > g.M[b.blk]; });
+  g.ntiles_ana = (int)ta.size();
+  g.ntiles_syn = (int)ts.size();
+  SHOT_CUDA(cudaMalloc(&g.tiles_ana, ta.size() * sizeof(Tile)));
+  SHOT_CUDA(cudaMalloc(&g.tiles_syn, ts.size() * sizeof(Tile)));
+  SHOT_CUDA(cudaMemcpyAsync(g.tiles_ana, ta.data(), ta.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
+  SHOT_CUDA(cudaMemcpyAsync(g.tiles_syn, ts.data(), ts.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
+
+  g.x.resize(nlat);
+  g.w.resize(nlat);
+  g.a_ring.resize(nlat);
+  SHOT_CUDA(cudaMemcpyAsync(g.x.data(), g.x_d, nlat * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SHOT_CUDA(cudaMemcpyAsync(g.w.data(), g.w_d, nlat * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SHOT_CUDA(cudaStreamSynchronize(st));
+  for (int j = 0; j < nlat; ++j) g.a_ring[j] = g.w[j] * (2.0 * M_PI / g.nlon);
+  return SHOT_OK;
+}
+
+int launch_heat_mult(const Grid& g, double t, cudaStream_t st) {
+  const int L = g.lmax + 1;
+  count_launch();
+  k_heat<<<(L + 255) / 256, 256, 0, st>>>(g.lmax, t, g.h_d);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
+}
+
+int launch_coeff_gather(const Grid& g, const float* C, int ldc, int nf, float* coeffs, cudaStream_t st) {
+  count_launch();
+  k_coeff_gather<<<1024, 256, 0, st>>>(g.lmax, nf, g.row_off_d, C, ldc, coeffs);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
+}
+
+int launch_coeff_scatter(const Grid& g, const float* coeffs, int nf, float* C, int ldc, cudaStream_t st) {
+  count_launch();
+  k_coeff_scatter<<<1024, 256, 0, st>>>(g.lmax, nf, g.row_off_d, coeffs, C, ldc);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
+}
+
+int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
+  Workspace& w = g.ws;
+  if (w.dev_int == nullptr) {
+    SHOT_CUDA(cudaMalloc(&w.dev_int, 16 * sizeof(int)));
+    SHOT_CUDA(cudaMallocHost(&w.host_int, 16 * sizeof(int)));
+  }
+  if (nf <= w.nf_cap) return SHOT_OK;
+  SHOT_CUDA(cudaStreamSynchronize(st));
+  cudaFree(w.XY);
+  cudaFree(w.C);
+  cudaFree(w.part);
+  cudaFree(w.probs);
+  cudaFree(w.marg);
+  if (w.host_probs) cudaFreeHost(w.host_probs);
+  w.XY = w.C = nullptr;
+  w.part = nullptr;
+  w.probs = nullptr;
+  w.marg = nullptr;
+  w.host_probs = nullptr;
+  w.nf_cap = 0;
+  const int ldc = (2 * nf + 3) / 4 * 4;
+  const size_t xy = (size_t)g.nblk * g.nh * ldc;
+  const size_t cc = (size_t)g.rows_total * ldc;
+  SHOT_CUDA(cudaMalloc(&w.XY, xy * sizeof(float)));
+  SHOT_CUDA(cudaMalloc(&w.C, cc * sizeof(float)));
+  SHOT_CUDA(cudaMalloc(&w.part, (size_t)nf * g.nh * NPART * sizeof(double)));
+  SHOT_CUDA(cudaMalloc(&w.probs, (size_t)nf * sizeof(ProbState)));
+  SHOT_CUDA(cudaMalloc(&w.marg, (size_t)4 * nf * sizeof(float*)));
+  SHOT_CUDA(cudaMallocHost(&w.host_probs, (size_t)nf * sizeof(ProbState)));
+  // X and C are never read before written except padding columns; keep them finite
+  SHOT_CUDA(cudaMemsetAsync(w.XY, 0, xy * sizeof(float), st));
+  SHOT_CUDA(cudaMemsetAsync(w.C, 0, cc * sizeof(float), st));
+  w.ldc = ldc;
+  w.nf_cap = nf;
+  return SHOT_OK;
+}
+
+}  // namespace shot

@@ -1,0 +1,156 @@
+// Internal declarations shared by the CUDA translation units of the SHOT library.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/shot.h"
+
+namespace shot {
+
+// ---------------------------------------------------------------------------------
+// Error reporting (thread-local message, status codes of shot.h)
+void set_error(const std::string& msg);
+int cuda_status(cudaError_t e, const char* what);   // SHOT_OK or SHOT_ERR_CUDA/OOM + message
+#define SHOT_CUDA(call)                                          \
+  do {                                                           \
+    cudaError_t e_ = (call);                                     \
+    if (e_ != cudaSuccess) return ::shot::cuda_status(e_, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------------------------
+// Launch accounting (prof.cu).  Kinds of shot_profile_read.
+enum ProfKind { PK_DFT = 0, PK_ANALYSIS = 1, PK_SYNTHESIS = 2, PK_IDFT = 3, PK_OTHER = 4, PK_NKINDS = 5 };
+void count_launch(int n = 1);
+class ProfScope {
+ public:
+  ProfScope(int kind, cudaStream_t st);
+  ~ProfScope();
+ private:
+  int kind_;
+  cudaStream_t st_;
+  cudaEvent_t b_ = nullptr, e_ = nullptr;
+};
+
+// ---------------------------------------------------------------------------------
+// Ring FFT plan: nlon = prod R[s], radices in {2,3,4,5,8}, Stockham ordering.
+struct FftPlan {
+  int N;
+  int nst;
+  int R[12];
+};
+bool make_fft_plan(int N, FftPlan* plan);
+
+// ---------------------------------------------------------------------------------
+// Spectral layout.  For order m and parity p (p = (l - m) mod 2) the block (m,p)
+// holds the degrees l = m + p + 2 i, i = 0 .. M_mp - 1, M_mp = (lmax - m - p)/2 + 1.
+//   table   : [block][i][ldt] Pbar_lm(x_jh) at the north-hemisphere nodes jh < nh
+//   X / Y   : [block][jh][ldc] ring spectra folded by parity (see dft.cu)
+//   C       : [row_off[block] + i][ldc] Legendre coefficients
+// ldc >= 2 * nfields (re, im per field), a multiple of 4.
+struct Tile {
+  int blk;    // 2*m + p
+  int r0;     // first row of the tile (i for analysis, jh for synthesis)
+};
+
+struct Workspace {
+  int nf_cap = 0;       // fields the buffers hold
+  int ldc = 0;
+  float* XY = nullptr;  // X (analysis input) and Y (synthesis output) share storage
+  float* C = nullptr;
+  double* part = nullptr;   // per-(field, ring pair) partial sums [nf][nh][NPART]
+  size_t part_cap = 0;
+  void* probs = nullptr;    // ProbState[nf]
+  const float** marg = nullptr;  // device pointer lists [2*nf]
+  float* ubuf = nullptr;    // internal u, v storage for the divergence [3*nf*n] each
+  float* vbuf = nullptr;
+  size_t uv_cap = 0;
+  int* dev_int = nullptr;   // device counters (iteration index, ...)
+  int* host_int = nullptr;  // pinned mirror
+  void* host_probs = nullptr;  // pinned ProbState mirror
+  size_t host_probs_cap = 0;
+};
+
+struct Grid {
+  int nlat = 0, nlon = 0, lmax = 0, nh = 0;
+  int precision = SHOT_FP32, mode = SHOT_TABLE;
+  int dev = 0;
+  FftPlan plan{};
+  // host copies (FP64)
+  std::vector<double> x, w, a_ring;
+  // blocks
+  int nblk = 0;                 // 2*(lmax+1)
+  std::vector<int> M;           // rows per block
+  std::vector<long long> row_off;  // prefix sum of M
+  long long rows_total = 0;
+  int ldt = 0;                  // table row stride (elements), multiple of 16
+  // device
+  double* x_d = nullptr;
+  double* w_d = nullptr;
+  float* a_d = nullptr;         // per-ring area weight (FP32)
+  float2* tw_d = nullptr;       // exp(-2 pi i k / nlon), k < nlon
+  float* h_d = nullptr;         // heat multipliers for the current call, [lmax+1]
+  float* tab = nullptr;         // FP32 folded table
+  __nv_bfloat16* tab_hi = nullptr;  // BF16X3 split table
+  __nv_bfloat16* tab_lo = nullptr;
+  int* M_d = nullptr;
+  long long* row_off_d = nullptr;
+  Tile* tiles_ana = nullptr;
+  Tile* tiles_syn = nullptr;
+  int ntiles_ana = 0, ntiles_syn = 0;
+  int bm_ana = 128, bm_syn = 128;
+  Workspace ws;
+};
+
+// ---------------------------------------------------------------------------------
+// Per-problem solver state (device), see sinkhorn.cu.
+struct ProbState {
+  double alpha;     // u_true = alpha * u_buf
+  double beta;      // v_true = beta  * v_buf
+  double su;        // pending reduction of the u-step (sum u or sum a p u^{-eps/tau})
+  double err;       // last marginal error
+  double ot, ot_dual, mass;
+  int active;
+  int status;
+  int iters;
+  int pad;
+};
+
+// Epilogue modes of the inverse DFT kernel
+enum EpiMode { EPI_PLAIN = 0, EPI_UPDATE = 1, EPI_CHECK = 2, EPI_FINAL = 3 };
+constexpr int NPART = 4;   // partial sums per (field, ring pair)
+
+struct EpiParams {
+  int mode;
+  float* out;                 // EPI_PLAIN: Kv output; EPI_UPDATE: u or v buffer
+  const float* const* marg;   // per-field marginal pointers (p or q)
+  const float* const* marg2;  // EPI_FINAL: the other marginal
+  float* other;               // EPI_CHECK/FINAL: the other scaling buffer (v for the u-side)
+  ProbState* ps;
+  double* part;               // [nf][nh][NPART]
+  int balanced;
+  float gamma;                // tau/(tau+eps)
+  float eps_over_taueps;      // eps/(tau+eps)
+  double eps, tau;
+  int norm_l1;
+  int which;                  // 0: u-step (marginal p), 1: v-step (marginal q)
+};
+
+// ---------------------------------------------------------------------------------
+// Launchers (return SHOT status)
+int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
+                   float* X, int ldc, cudaStream_t st);
+int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
+int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
+int launch_heat_mult(const Grid& g, double t, cudaStream_t st);
+int launch_coeff_gather(const Grid& g, const float* C, int ldc, int nf, float* coeffs, cudaStream_t st);
+int launch_coeff_scatter(const Grid& g, const float* coeffs, int nf, float* C, int ldc, cudaStream_t st);
+int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st);
+int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
+                         cudaStream_t st);
+int build_grid_tables(Grid& g, cudaStream_t st);
+int ensure_workspace(Grid& g, int nf, cudaStream_t st);
+
+}  // namespace shot

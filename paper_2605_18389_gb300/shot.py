@@ -1,0 +1,236 @@
+"""Thin ctypes binding of the SHOT C ABI (include/shot.h).
+
+Argument marshalling only: every step of the computation runs in libshot.so's CUDA
+kernels.  Functions keep the C names; tensors are torch CUDA tensors (float32,
+contiguous) whose device pointers are passed through, and the stream is torch's
+current stream.  If the library is not built the import of any entry point raises:
+there is no CPU fallback.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+SHOT_OK = 0
+SHOT_WARN_NOT_CONVERGED = 1
+SHOT_ERR_INVALID_ARG = -1
+SHOT_ERR_CUDA = -2
+SHOT_ERR_OOM = -3
+SHOT_ERR_UNSUPPORTED = -4
+SHOT_ERR_NONPOSITIVE = -5
+SHOT_ERR_NONFINITE = -6
+SHOT_ERR_TIMEOUT = -7
+
+SHOT_FP32 = 0
+SHOT_BF16X3 = 1
+SHOT_TABLE = 0
+SHOT_FLAG_NORM_L1 = 0x1
+SHOT_FLAG_WARM_START = 0x2
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libshot.so")
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_dbl_p = ctypes.POINTER(ctypes.c_double)
+_c_flt_p = ctypes.POINTER(ctypes.c_float)
+_vp = ctypes.c_void_p
+
+# name -> argtypes (all return int)
+SIGNATURES = {
+    "shot_last_error": [ctypes.c_char_p, ctypes.c_int],
+    "shot_grid_init": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                       ctypes.c_int, _vp],
+    "shot_grid_free": [_vp],
+    "shot_grid_info": [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p],
+    "shot_grid_nodes": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
+    "shot_grid_reserve": [_vp, ctypes.c_int],
+    "shot_heat_apply": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
+    "shot_sht_analysis": [_vp, _vp, _vp, ctypes.c_int, _vp],
+    "shot_sht_synthesis": [_vp, _vp, _vp, ctypes.c_int, _vp],
+    "shot_sinkhorn": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                      ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp, _vp, _c_dbl_p, _c_dbl_p, _c_dbl_p,
+                      _c_int_p, _c_flt_p, _c_int_p, _vp],
+    "shot_divergence": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                        ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_int_p, _vp, _vp,
+                        _c_dbl_p, _c_int_p, _vp],
+    "shot_launch_count": [ctypes.POINTER(ctypes.c_longlong)],
+    "shot_profile_enable": [ctypes.c_int],
+    "shot_profile_read": [_c_dbl_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int],
+}
+
+PROFILE_KINDS = ("ring_dft", "legendre_analysis", "legendre_synthesis", "inverse_dft_epilogue", "other")
+
+_lib = None
+
+
+class ShotError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"SHOT error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libshot.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run __graft_entry__.build()")
+        try:
+            import torch  # noqa: F401  (share torch's CUDA runtime in this process)
+        except ImportError:
+            pass
+        l = ctypes.CDLL(LIB_PATH)
+        for name, args in SIGNATURES.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        _lib = l
+    return _lib
+
+
+def last_error():
+    buf = ctypes.create_string_buffer(1024)
+    lib().shot_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc, allow_positive=True):
+    if rc < 0 or (rc > 0 and not allow_positive):
+        raise ShotError(rc, last_error())
+    return rc
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _dev_ptr(t, name, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous float32")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return _vp(t.data_ptr())
+
+
+def _np_ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+# ---- C-named entry points ---------------------------------------------------------
+
+def shot_grid_init(nlat, nlon=None, lmax=-1, precision=SHOT_FP32, legendre_mode=SHOT_TABLE, stream=None):
+    nlon = 2 * nlat if nlon is None else nlon
+    h = _vp()
+    _check(lib().shot_grid_init(ctypes.byref(h), nlat, nlon, lmax, precision, legendre_mode, _stream(stream)))
+    return h
+
+
+def shot_grid_free(g):
+    return _check(lib().shot_grid_free(g))
+
+
+def shot_grid_info(g):
+    v = [ctypes.c_int() for _ in range(5)]
+    _check(lib().shot_grid_info(g, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("nlat", "nlon", "lmax", "precision", "legendre_mode"), [x.value for x in v]))
+
+
+def shot_grid_nodes(g):
+    nlat = shot_grid_info(g)["nlat"]
+    x, w, a = (np.empty(nlat) for _ in range(3))
+    _check(lib().shot_grid_nodes(g, _np_ptr(x, ctypes.c_double), _np_ptr(w, ctypes.c_double),
+                                 _np_ptr(a, ctypes.c_double)))
+    return x, w, a
+
+
+def shot_grid_reserve(g, nfields):
+    return _check(lib().shot_grid_reserve(g, nfields))
+
+
+def shot_heat_apply(g, t, inp, out, stream=None):
+    nf = inp.shape[0]
+    return _check(lib().shot_heat_apply(g, float(t), _dev_ptr(inp, "in"), _dev_ptr(out, "out", inp.shape),
+                                        nf, _stream(stream)))
+
+
+def shot_sht_analysis(g, inp, coeffs, stream=None):
+    return _check(lib().shot_sht_analysis(g, _dev_ptr(inp, "in"), _dev_ptr(coeffs, "coeffs"), inp.shape[0],
+                                          _stream(stream)))
+
+
+def shot_sht_synthesis(g, coeffs, out, stream=None):
+    return _check(lib().shot_sht_synthesis(g, _dev_ptr(coeffs, "coeffs"), _dev_ptr(out, "out"), out.shape[0],
+                                           _stream(stream)))
+
+
+def shot_sinkhorn(g, p, q, eps, tau=math.inf, max_iter=500, tol=0.0, check_every=10, flags=0, u=None, v=None,
+                  stream=None):
+    """Returns (status_code, dict of per-problem numpy outputs); u, v are filled in place."""
+    import torch
+    B = p.shape[0]
+    if u is None:
+        u = torch.empty_like(p)
+    if v is None:
+        v = torch.empty_like(p)
+    ot, otd, mass = (np.empty(B) for _ in range(3))
+    iters, status = np.empty(B, np.int32), np.empty(B, np.int32)
+    err = np.empty(B, np.float32)
+    rc = _solver_rc(lib().shot_sinkhorn(
+        g, _dev_ptr(p, "p"), _dev_ptr(q, "q", p.shape), B, float(eps), float(tau), int(max_iter), float(tol),
+        int(check_every), int(flags), _dev_ptr(u, "u", p.shape), _dev_ptr(v, "v", p.shape),
+        _np_ptr(ot, ctypes.c_double), _np_ptr(otd, ctypes.c_double), _np_ptr(mass, ctypes.c_double),
+        _np_ptr(iters, ctypes.c_int), _np_ptr(err, ctypes.c_float), _np_ptr(status, ctypes.c_int),
+        _stream(stream)))
+    return rc, dict(u=u, v=v, ot=ot, ot_dual=otd, mass_pi=mass, iters=iters, err=err, status=status)
+
+
+def _solver_rc(rc):
+    """Negative per-problem statuses are results, not call failures, for the solvers."""
+    if rc in (SHOT_ERR_NONPOSITIVE, SHOT_ERR_NONFINITE):
+        return rc
+    return _check(rc)
+
+
+def shot_divergence(g, p, q, eps, tau=math.inf, max_iter=500, tol=0.0, check_every=10, flags=0,
+                    u3=None, v3=None, stream=None):
+    """Returns (status_code, dict with S, S_dual, status, ot3, iters3)."""
+    B = p.shape[0]
+    S, Sd = np.empty(B), np.empty(B)
+    status = np.empty(B, np.int32)
+    ot3 = np.empty(3 * B)
+    it3 = np.empty(3 * B, np.int32)
+    shape3 = (3 * B,) + tuple(p.shape[1:])
+    rc = lib().shot_divergence(
+        g, _dev_ptr(p, "p"), _dev_ptr(q, "q", p.shape), B, float(eps), float(tau), int(max_iter), float(tol),
+        int(check_every), int(flags), _np_ptr(S, ctypes.c_double), _np_ptr(Sd, ctypes.c_double),
+        _np_ptr(status, ctypes.c_int),
+        _dev_ptr(u3, "u3", shape3) if u3 is not None else None,
+        _dev_ptr(v3, "v3", shape3) if v3 is not None else None,
+        _np_ptr(ot3, ctypes.c_double), _np_ptr(it3, ctypes.c_int), _stream(stream))
+    rc = _solver_rc(rc)
+    return rc, dict(S=S, S_dual=Sd, status=status, ot3=ot3, iters3=it3)
+
+
+def shot_launch_count():
+    n = ctypes.c_longlong()
+    _check(lib().shot_launch_count(ctypes.byref(n)))
+    return n.value
+
+
+def shot_profile_enable(on=True):
+    return _check(lib().shot_profile_enable(1 if on else 0))
+
+
+def shot_profile_read():
+    """{kind: (total_ms, launches)} for the launches recorded since the last read."""
+    k = len(PROFILE_KINDS)
+    ms = np.zeros(k)
+    n = np.zeros(k, np.int64)
+    _check(lib().shot_profile_read(_np_ptr(ms, ctypes.c_double), n.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+                                   k))
+    return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(PROFILE_KINDS)}

@@ -1,0 +1,119 @@
+"""GPU parity of Algorithm 1 and the Sinkhorn divergence against the FP64 oracle (C ABI)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.grid import Grid as OGrid
+from oracle import sinkhorn as sk
+from paper_2605_18389_gb300 import inputs
+from tests.gpu_util import rel_max, f32
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from paper_2605_18389_gb300 import shot  # noqa: E402
+
+# FP32 targets: potentials and S within 1e-5 of the FP64 oracle (relative).
+TOL_PHI = 1e-5
+TOL_S = 1e-5
+
+
+@pytest.fixture(scope="module")
+def grid_cache():
+    cache = {}
+
+    def get(nlat):
+        if nlat not in cache:
+            cache[nlat] = (shot.shot_grid_init(nlat), OGrid(nlat))
+        return cache[nlat]
+    yield get
+    for g, _ in cache.values():
+        shot.shot_grid_free(g)
+
+
+def _fields(og, recipe, seed, npairs, masses=False):
+    p, q = inputs.pairs(recipe, seed, npairs, og.x, og.nlon, og.a_ring, masses=masses)
+    p32, p64 = f32(p)
+    q32, q64 = f32(q)
+    return torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), p64, q64
+
+
+def _s_err(s_gpu, s_ref, ot_ref):
+    return np.abs(s_gpu - s_ref) / np.maximum(np.abs(s_ref), 1e-3 * np.abs(ot_ref))
+
+
+@pytest.mark.parametrize("nlat,eps,tau,T", [(16, 0.1, math.inf, 40), (32, 0.1, math.inf, 60),
+                                            (32, 0.1, 1.0, 60), (64, 0.01, 0.1, 30),
+                                            (33, 0.1, math.inf, 30)])
+def test_sinkhorn_fixed_iterations_match_oracle(grid_cache, nlat, eps, tau, T):
+    g, og = grid_cache(nlat)
+    unb = not math.isinf(tau)
+    pt, qt, p, q = _fields(og, "paper_uniform", 1000 + nlat, 3, masses=unb)
+    rc, r = shot.shot_sinkhorn(g, pt, qt, eps, tau, max_iter=T, tol=0.0, check_every=10)
+    ref = sk.sinkhorn(og, p, q, eps, tau, T=T, delta=0.0, C=10)
+    assert rc == 0 and np.all(r["status"] == 0) and np.all(ref["status"] == 0)
+    assert np.all(r["iters"] == T)
+    u, v = r["u"].cpu().numpy(), r["v"].cpu().numpy()
+    for b in range(3):
+        assert rel_max(eps * np.log(u[b]), ref["phi"][b]) < TOL_PHI
+        assert rel_max(eps * np.log(v[b]), ref["psi"][b]) < TOL_PHI
+    np.testing.assert_allclose(r["ot"], ref["ot"], rtol=TOL_PHI)
+    np.testing.assert_allclose(r["mass_pi"], ref["mass_pi"], rtol=1e-5)
+    np.testing.assert_allclose(r["err"], ref["err"], rtol=1e-2, atol=1e-6)
+
+
+def test_sinkhorn_converges_at_same_check(grid_cache):
+    g, og = grid_cache(32)
+    pt, qt, p, q = _fields(og, "paper_uniform", 77, 2)
+    rc, r = shot.shot_sinkhorn(g, pt, qt, 0.1, max_iter=2000, tol=1e-5, check_every=10)
+    ref = sk.sinkhorn(og, p, q, 0.1, T=2000, delta=1e-5, C=10)
+    assert np.all(r["status"] == 0) and np.all(ref["status"] == 0)
+    np.testing.assert_array_equal(r["iters"], ref["iters"])
+    assert np.all(r["err"] < 1e-5)
+
+
+def test_l1_norm_and_not_converged_warning(grid_cache):
+    g, og = grid_cache(16)
+    pt, qt, p, q = _fields(og, "paper_uniform", 5, 1)
+    rc, r = shot.shot_sinkhorn(g, pt, qt, 0.1, max_iter=20, tol=1e-12, check_every=10,
+                               flags=shot.SHOT_FLAG_NORM_L1)
+    ref = sk.sinkhorn(og, p, q, 0.1, T=20, delta=1e-12, C=10, norm="l1")
+    assert rc == shot.SHOT_WARN_NOT_CONVERGED and r["status"][0] == ref["status"][0] == sk.NOT_CONVERGED
+    np.testing.assert_allclose(r["err"], ref["err"], rtol=1e-2)
+
+
+def test_breakdown_reported_at_oracle_iteration(grid_cache):
+    # App. C.4: truncated-kernel negativity; literal vMF inputs at nlat 32, t = 1e-2
+    g, og = grid_cache(32)
+    pt, qt, p, q = _fields(og, "vmf3", 1001, 1)
+    rc, r = shot.shot_sinkhorn(g, pt, qt, 4e-2, max_iter=50, tol=1e-10, check_every=10)
+    ref = sk.sinkhorn(og, p, q, 4e-2, T=50, delta=1e-10, C=10)
+    assert ref["status"][0] == sk.NONPOSITIVE
+    assert rc == shot.SHOT_ERR_NONPOSITIVE and r["status"][0] == shot.SHOT_ERR_NONPOSITIVE
+    assert r["iters"][0] == ref["iters"][0]
+    assert np.isnan(r["ot"][0])
+
+
+@pytest.mark.parametrize("nlat,eps,tau,T,tol", [(16, 0.2, math.inf, 400, 1e-7), (32, 0.1, math.inf, 600, 1e-6),
+                                                (32, 0.1, 1.0, 80, 0.0), (64, 0.01, 10.0, 40, 0.0)])
+def test_divergence_matches_oracle(grid_cache, nlat, eps, tau, T, tol):
+    g, og = grid_cache(nlat)
+    unb = not math.isinf(tau)
+    pt, qt, p, q = _fields(og, "paper_uniform", 2000 + nlat, 2, masses=unb)
+    rc, r = shot.shot_divergence(g, pt, qt, eps, tau, max_iter=T, tol=tol, check_every=10)
+    ref = sk.divergence(og, p, q, eps, tau, T=T, delta=tol, C=10)
+    assert np.all(r["status"] == ref["status"])
+    np.testing.assert_array_equal(r["iters3"], ref["runs"]["iters"])
+    ot_pq = ref["runs"]["ot"][:2]
+    assert np.all(_s_err(r["S"], ref["S"], ot_pq) < TOL_S)
+    assert np.all(_s_err(r["S_dual"], ref["S_dual"], ot_pq) < TOL_S)
+    if not unb:
+        assert np.all(r["S"] > 0)
+
+
+def test_divergence_of_identical_measures_is_zero(grid_cache):
+    g, og = grid_cache(16)
+    pt, qt, p, q = _fields(og, "paper_uniform", 9, 2)
+    rc, r = shot.shot_divergence(g, pt, pt, 0.2, max_iter=100, tol=0.0)
+    assert np.all(r["S"] == 0.0)
