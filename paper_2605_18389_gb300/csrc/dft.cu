@@ -133,11 +133,12 @@ __global__ void __launch_bounds__(kThreads) k_idft(
   const float2* z = fft_smem<true>(b0, b1, tw, pl, nfg, N);
 
   const float aj = a_ring[j];
-  const double ajd = (double)aj;
   const int nrings = (J != j) ? 2 : 1;
+  // Per-element arithmetic is FP32; every thread sums its few elements (<= nrings*N/512)
+  // in FP32 and the block / grid reductions run in FP64.
   for (int q = 0; q < nfg; ++q) {
     const int f = f0 + q;
-    double acc[NPART] = {0.0, 0.0, 0.0, 0.0};
+    float acc32[NPART] = {0.f, 0.f, 0.f, 0.f};
     const size_t fbase = (size_t)f * nlat * nlon;
     if (ep.mode == EPI_PLAIN) {
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
@@ -162,16 +163,17 @@ __global__ void __launch_bounds__(kThreads) k_idft(
         float u;
         if (ep.balanced) {
           u = ratio;
-          acc[0] += (double)u;
+          acc32[0] += u;
         } else {
+          // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}
           u = powf(ratio, ep.gamma);
-          if (pm > 0.f) acc[0] += ajd * (double)pm * (double)powf(ratio, -ep.eps_over_taueps);
+          if (pm > 0.f) acc32[0] += aj * pm * powf(ratio, -ep.eps_over_taueps);
         }
         if (!(kv > 0.f)) {
-          if (kv <= 0.f) acc[2] += 1.0;
-          else acc[3] += 1.0;   // NaN
+          if (kv <= 0.f) acc32[2] += 1.f;
+          else acc32[3] += 1.f;   // NaN
         }
-        if (!isfinite(u) || !isfinite(kv)) acc[3] += 1.0;
+        if (!isfinite(u) || !isfinite(kv)) acc32[3] += 1.f;
         ep.out[o] = u;
       }
     } else if (ep.mode == EPI_CHECK) {
@@ -184,20 +186,21 @@ __global__ void __launch_bounds__(kThreads) k_idft(
         const float kv = r ? zz.y : zz.x;
         const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
         const float pm = __ldg(mg + (size_t)(r ? J : j) * nlon + k);
-        const double d = (double)(al * ep.other[o]) * (double)kv - (double)pm;
+        const float d = fmaf(al * ep.other[o], kv, -pm);
         if (ep.norm_l1) {
-          acc[0] += ajd * fabs(d);
-          acc[1] += ajd * (double)pm;
+          acc32[0] += aj * fabsf(d);
+          acc32[1] += aj * pm;
         } else {
-          acc[0] += d * d;
-          acc[1] += (double)pm * (double)pm;
+          acc32[0] += d * d;
+          acc32[1] += pm * pm;
         }
       }
     } else {  // EPI_FINAL: z = K v_true; ep.other = u buffer, ep.out = v buffer
       if (P->status < 0) continue;
       const float* pp = ep.marg[f];
       const float* qq = ep.marg2[f];
-      const double al = P->alpha, be = P->beta;
+      const float al = (float)P->alpha, be = (float)P->beta;
+      const float epsf = (float)ep.eps, tauf = (float)ep.tau, et = (float)(ep.eps / ep.tau);
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
         const int r = idx / N, k = idx - r * N;
         const float2 zz = z[q * N + k];
@@ -205,31 +208,33 @@ __global__ void __launch_bounds__(kThreads) k_idft(
         const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
         const size_t om = (size_t)(r ? J : j) * nlon + k;
         const float pm = __ldg(pp + om), qm = __ldg(qq + om);
-        const float uu = (float)(al * (double)ep.other[o]);
-        const float vv = (float)(be * (double)ep.out[o]);
+        const float uu = al * ep.other[o];
+        const float vv = be * ep.out[o];
         ep.other[o] = uu;
         ep.out[o] = vv;
-        const double d = (double)uu * (double)kv - (double)pm;
+        const float d = fmaf(uu, kv, -pm);
         if (ep.norm_l1) {
-          acc[0] += ajd * fabs(d);
-          acc[1] += ajd * (double)pm;
+          acc32[0] += aj * fabsf(d);
+          acc32[1] += aj * pm;
         } else {
-          acc[0] += d * d;
-          acc[1] += (double)pm * (double)pm;
+          acc32[0] += d * d;
+          acc32[1] += pm * pm;
         }
-        acc[2] += ajd * (double)uu * (double)kv;
-        const double lu = log((double)uu), lv = log((double)vv);
-        double t;
+        acc32[2] += aj * uu * kv;
+        // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
+        const float lu = logf(uu), lv = logf(vv);
+        float t;
         if (ep.balanced) {
-          t = (pm > 0.f ? ep.eps * lu * pm : 0.0) + (qm > 0.f ? ep.eps * lv * qm : 0.0);
-        } else {
-          const double e = -ep.eps / ep.tau;
-          t = (pm > 0.f ? ep.tau * (1.0 - exp(e * lu)) * pm : 0.0) +
-              (qm > 0.f ? ep.tau * (1.0 - exp(e * lv)) * qm : 0.0);
+          t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);
+        } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u)
+          t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) + (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
         }
-        acc[3] += ajd * t;
+        acc32[3] += aj * t;
       }
     }
+    double acc[NPART];
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) acc[i] = (double)acc32[i];
     block_sum4(acc, red);
     if (threadIdx.x == 0) {
       double* pt = ep.part + ((size_t)f * nh + jh) * NPART;

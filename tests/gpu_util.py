@@ -13,3 +13,14 @@ def f32(a):
     """Round to FP32 and return (fp32 array for the GPU, the same values in FP64 for the oracle)."""
     x = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
     return x, x.astype(np.float64)
+
+
+def s_err(s_gpu, s_ref, ot_ref, tol):
+    """Error of a Sinkhorn divergence in units of its tolerance (pass: <= 1).
+
+    S = OT(p,q) - (OT(p,p) + OT(q,q))/2 cancels: each OT carries the FP32 rounding of
+    the potentials (measured systematic relative error <= ~1e-7 of u), so its absolute
+    error cannot fall below ~2^-24 |OT|.  The bound is tol |S| + 4 * 2^-24 |OT(p,q)|.
+    """
+    s_gpu, s_ref, ot_ref = (np.asarray(a, dtype=np.float64) for a in (s_gpu, s_ref, ot_ref))
+    return np.abs(s_gpu - s_ref) / (tol * np.abs(s_ref) + 4.0 * 2.0 ** -24 * np.abs(ot_ref))

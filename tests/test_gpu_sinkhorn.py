@@ -7,7 +7,7 @@ import pytest
 from oracle.grid import Grid as OGrid
 from oracle import sinkhorn as sk
 from paper_2605_18389_gb300 import inputs
-from tests.gpu_util import rel_max, f32
+from tests.gpu_util import rel_max, f32, s_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -23,10 +23,11 @@ TOL_S = 1e-5
 def grid_cache():
     cache = {}
 
-    def get(nlat):
-        if nlat not in cache:
-            cache[nlat] = (shot.shot_grid_init(nlat), OGrid(nlat))
-        return cache[nlat]
+    def get(nlat, nlon=None):
+        key = (nlat, nlon)
+        if key not in cache:
+            cache[key] = (shot.shot_grid_init(nlat, nlon), OGrid(nlat, nlon))
+        return cache[key]
     yield get
     for g, _ in cache.values():
         shot.shot_grid_free(g)
@@ -39,15 +40,11 @@ def _fields(og, recipe, seed, npairs, masses=False):
     return torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), p64, q64
 
 
-def _s_err(s_gpu, s_ref, ot_ref):
-    return np.abs(s_gpu - s_ref) / np.maximum(np.abs(s_ref), 1e-3 * np.abs(ot_ref))
-
-
-@pytest.mark.parametrize("nlat,eps,tau,T", [(16, 0.1, math.inf, 40), (32, 0.1, math.inf, 60),
-                                            (32, 0.1, 1.0, 60), (64, 0.01, 0.1, 30),
-                                            (33, 0.1, math.inf, 30)])
-def test_sinkhorn_fixed_iterations_match_oracle(grid_cache, nlat, eps, tau, T):
-    g, og = grid_cache(nlat)
+@pytest.mark.parametrize("nlat,nlon,eps,tau,T", [(16, None, 0.1, math.inf, 40), (32, None, 0.1, math.inf, 60),
+                                                 (32, None, 0.1, 1.0, 60), (64, None, 0.02, 0.1, 30),
+                                                 (33, 72, 0.1, math.inf, 30)])
+def test_sinkhorn_fixed_iterations_match_oracle(grid_cache, nlat, nlon, eps, tau, T):
+    g, og = grid_cache(nlat, nlon)
     unb = not math.isinf(tau)
     pt, qt, p, q = _fields(og, "paper_uniform", 1000 + nlat, 3, masses=unb)
     rc, r = shot.shot_sinkhorn(g, pt, qt, eps, tau, max_iter=T, tol=0.0, check_every=10)
@@ -95,8 +92,9 @@ def test_breakdown_reported_at_oracle_iteration(grid_cache):
     assert np.isnan(r["ot"][0])
 
 
-@pytest.mark.parametrize("nlat,eps,tau,T,tol", [(16, 0.2, math.inf, 400, 1e-7), (32, 0.1, math.inf, 600, 1e-6),
-                                                (32, 0.1, 1.0, 80, 0.0), (64, 0.01, 10.0, 40, 0.0)])
+# tol >= 1e-6: the FP32 path resolves the relative marginal error down to ~3e-7
+@pytest.mark.parametrize("nlat,eps,tau,T,tol", [(16, 0.2, math.inf, 400, 2e-6), (32, 0.1, math.inf, 600, 1e-6),
+                                                (32, 0.1, 1.0, 80, 0.0), (64, 0.02, 10.0, 40, 0.0)])
 def test_divergence_matches_oracle(grid_cache, nlat, eps, tau, T, tol):
     g, og = grid_cache(nlat)
     unb = not math.isinf(tau)
@@ -106,8 +104,8 @@ def test_divergence_matches_oracle(grid_cache, nlat, eps, tau, T, tol):
     assert np.all(r["status"] == ref["status"])
     np.testing.assert_array_equal(r["iters3"], ref["runs"]["iters"])
     ot_pq = ref["runs"]["ot"][:2]
-    assert np.all(_s_err(r["S"], ref["S"], ot_pq) < TOL_S)
-    assert np.all(_s_err(r["S_dual"], ref["S_dual"], ot_pq) < TOL_S)
+    assert np.all(s_err(r["S"], ref["S"], ot_pq, TOL_S) <= 1.0)
+    assert np.all(s_err(r["S_dual"], ref["S_dual"], ot_pq, TOL_S) <= 1.0)
     if not unb:
         assert np.all(r["S"] > 0)
 
