@@ -22,36 +22,36 @@ namespace shot {
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = kFftThreads;
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Deterministic block reduction of NPART doubles; result valid in thread 0.
-__device__ void block_sum4(double (&acc)[NPART], double* red /* [32*NPART] */) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NPART; ++i) acc[i] = warp_sum(acc[i]);
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < NPART; ++i) red[wid * NPART + i] = acc[i];
+// Loads rings j (real part) and J = nlat-1-j (imaginary part) of nfg fields into buf.
+__device__ __forceinline__ void load_ring_pairs(const float* __restrict__ in, float2* buf, int f0, int nfg,
+                                                int nlat, int nlon, int j, int J) {
+  const int N = nlon;
+  float* bf = reinterpret_cast<float*>(buf);
+  for (int idx = threadIdx.x; idx < nfg * 2 * N; idx += blockDim.x) {
+    const int q = idx / (2 * N);
+    const int rem = idx - q * 2 * N;
+    const int r = rem / N, k = rem - r * N;
+    const size_t base = (size_t)(f0 + q) * nlat * nlon;
+    float val = 0.f;
+    if (r == 0) val = __ldg(in + base + (size_t)j * nlon + k);
+    else if (J != j) val = __ldg(in + base + (size_t)J * nlon + k);
+    bf[2 * (q * N + k) + r] = val;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < nw; ++w)
-#pragma unroll
-      for (int i = 0; i < NPART; ++i) acc[i] += red[w * NPART + i];
-  }
-  __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) k_dft_fwd(
+template <int FG>
+__global__ void __launch_bounds__(kThreads, 2) k_dft_fwd(
     const float* __restrict__ in, int nf, int nlat, int nlon, int lmax, int nh,
     const float* __restrict__ a_ring, const ProbState* __restrict__ ps, int scale_which,
-    float* __restrict__ X, int ldc, FftPlan pl, const float2* __restrict__ tw_g, int FG) {
+    float* __restrict__ X, int ldc, FftPlan pl, const float2* __restrict__ tw_g) {
   extern __shared__ float2 sm[];
   const int N = nlon;
   float2* tw = sm;
@@ -63,15 +63,9 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd(
   const int j = jh, J = nlat - 1 - jh;
 
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
-  for (int idx = threadIdx.x; idx < nfg * N; idx += blockDim.x) {
-    const int q = idx / N, k = idx - q * N;
-    const size_t base = (size_t)(f0 + q) * nlat * nlon;
-    const float re = __ldg(in + base + (size_t)j * nlon + k);
-    const float im = (J != j) ? __ldg(in + base + (size_t)J * nlon + k) : 0.f;
-    b0[idx] = make_float2(re, im);
-  }
+  load_ring_pairs(in, b0, f0, nfg, nlat, nlon, j, J);
   __syncthreads();
-  const float2* Z = fft_smem<false>(b0, b1, tw, pl, nfg, N);
+  const float2* buf = fft_smem<false>(b0, b1, tw, pl, nfg, N);
 
   const float aj = a_ring[j];
   const int nm = lmax + 1;
@@ -80,8 +74,8 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd(
     const int f = f0 + q;
     float sc = aj;
     if (scale_which == 1) sc *= (float)ps[f].beta;
-    const float2 zm = Z[q * N + m];
-    const float2 zn = Z[q * N + (m ? N - m : 0)];
+    const float2 zm = buf[q * N + m];
+    const float2 zn = buf[q * N + (m ? N - m : 0)];
     const float2 FN = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
     const float2 FS = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
     const float2 S = make_float2(sc * (FN.x + FS.x), sc * (FN.y + FS.y));
@@ -91,16 +85,16 @@ __global__ void __launch_bounds__(kThreads) k_dft_fwd(
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_idft(
+template <int FG>
+__global__ void __launch_bounds__(kThreads, 2) k_idft(
     const float* __restrict__ Y, int ldc, int nf, int nlat, int nlon, int lmax, int nh,
-    const float* __restrict__ a_ring, FftPlan pl, const float2* __restrict__ tw_g, int FG,
-    EpiParams ep) {
+    const float* __restrict__ a_ring, FftPlan pl, const float2* __restrict__ tw_g, EpiParams ep) {
   extern __shared__ float2 sm[];
-  __shared__ double red[32 * NPART];
+  __shared__ float red[kThreads / 32][FG * NPART];
   const int N = nlon;
   float2* tw = sm;
-  float2* b0 = sm + N;
-  float2* b1 = b0 + FG * N;
+  float2* buf = sm + N;
+  float2* b1 = buf + FG * N;
   const int jh = blockIdx.x;
   const int f0 = blockIdx.y * FG;
   const int nfg = min(FG, nf - f0);
@@ -111,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_idft(
   const int nz = N - 2 * lmax - 1;
   for (int idx = threadIdx.x; idx < nfg * nz; idx += blockDim.x) {
     const int q = idx / nz, k = idx - q * nz;
-    b0[q * N + lmax + 1 + k] = make_float2(0.f, 0.f);
+    buf[q * N + lmax + 1 + k] = make_float2(0.f, 0.f);
   }
   const int nm = lmax + 1;
   for (int idx = threadIdx.x; idx < nm * nfg; idx += blockDim.x) {
@@ -123,58 +117,66 @@ __global__ void __launch_bounds__(kThreads) k_idft(
     const float2 GN = make_float2(E.x + O.x, E.y + O.y);
     const float2 GS = make_float2(E.x - O.x, E.y - O.y);
     if (m == 0) {
-      b0[q * N] = make_float2(GN.x, GS.x);
+      buf[q * N] = make_float2(GN.x, GS.x);
     } else {
-      b0[q * N + m] = make_float2(GN.x - GS.y, GN.y + GS.x);
-      b0[q * N + N - m] = make_float2(GN.x + GS.y, GS.x - GN.y);
+      buf[q * N + m] = make_float2(GN.x - GS.y, GN.y + GS.x);
+      buf[q * N + N - m] = make_float2(GN.x + GS.y, GS.x - GN.y);
     }
   }
   __syncthreads();
-  const float2* z = fft_smem<true>(b0, b1, tw, pl, nfg, N);
+  const float2* z = fft_smem<true>(buf, b1, tw, pl, nfg, N);
 
   const float aj = a_ring[j];
   const int nrings = (J != j) ? 2 : 1;
-  // Per-element arithmetic is FP32; every thread sums its few elements (<= nrings*N/512)
-  // in FP32 and the block / grid reductions run in FP64.
-  for (int q = 0; q < nfg; ++q) {
-    const int f = f0 + q;
-    float acc32[NPART] = {0.f, 0.f, 0.f, 0.f};
-    const size_t fbase = (size_t)f * nlat * nlon;
-    if (ep.mode == EPI_PLAIN) {
-      for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
-        const int r = idx / N, k = idx - r * N;
-        const float2 zz = z[q * N + k];
-        const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
-        ep.out[o] = r ? zz.y : zz.x;
-      }
-      continue;
+  if (ep.mode == EPI_PLAIN) {
+    for (int idx = threadIdx.x; idx < nfg * nrings * N; idx += blockDim.x) {
+      const int q = idx / (nrings * N);
+      const int rem = idx - q * nrings * N;
+      const int r = rem / N, k = rem - r * N;
+      const float2 zz = z[q * N + k];
+      ep.out[(size_t)(f0 + q) * nlat * nlon + (size_t)(r ? J : j) * nlon + k] = r ? zz.y : zz.x;
     }
+    return;
+  }
+  // Per-element arithmetic is FP32; every thread sums its few elements (<= nrings*N/512
+  // per field) in FP32, warps reduce in FP32 and the cross-warp / grid sums are FP64.
+  float acc[FG][NPART];
+#pragma unroll
+  for (int q = 0; q < FG; ++q)
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) acc[q][i] = 0.f;
+
+#pragma unroll
+  for (int q = 0; q < FG; ++q) {
+    if (q >= nfg) break;
+    const int f = f0 + q;
+    const size_t fbase = (size_t)f * nlat * nlon;
     ProbState* P = ep.ps + f;
     if (ep.mode == EPI_UPDATE) {
-      if (!P->active) continue;   // uniform across the block
+      if (!P->active) continue;
       const float* mg = ep.marg[f];
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
         const int r = idx / N, k = idx - r * N;
         const float2 zz = z[q * N + k];
         const float kv = r ? zz.y : zz.x;
-        const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
-        const float pm = __ldg(mg + (size_t)(r ? J : j) * nlon + k);
+        const size_t om = (size_t)(r ? J : j) * nlon + k;
+        const float pm = __ldg(mg + om);
         const float ratio = pm / kv;
         float u;
         if (ep.balanced) {
           u = ratio;
-          acc32[0] += u;
+          acc[q][0] += u;
         } else {
           // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}
           u = powf(ratio, ep.gamma);
-          if (pm > 0.f) acc32[0] += aj * pm * powf(ratio, -ep.eps_over_taueps);
+          if (pm > 0.f) acc[q][0] += aj * pm * powf(ratio, -ep.eps_over_taueps);
         }
         if (!(kv > 0.f)) {
-          if (kv <= 0.f) acc32[2] += 1.f;
-          else acc32[3] += 1.f;   // NaN
+          if (kv <= 0.f) acc[q][2] += 1.f;
+          else acc[q][3] += 1.f;   // NaN
         }
-        if (!isfinite(u) || !isfinite(kv)) acc32[3] += 1.f;
-        ep.out[o] = u;
+        if (!isfinite(u) || !isfinite(kv)) acc[q][3] += 1.f;
+        ep.out[fbase + om] = u;
       }
     } else if (ep.mode == EPI_CHECK) {
       if (!P->active) continue;
@@ -184,15 +186,15 @@ __global__ void __launch_bounds__(kThreads) k_idft(
         const int r = idx / N, k = idx - r * N;
         const float2 zz = z[q * N + k];
         const float kv = r ? zz.y : zz.x;
-        const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
-        const float pm = __ldg(mg + (size_t)(r ? J : j) * nlon + k);
-        const float d = fmaf(al * ep.other[o], kv, -pm);
+        const size_t om = (size_t)(r ? J : j) * nlon + k;
+        const float pm = __ldg(mg + om);
+        const float d = fmaf(al * ep.other[fbase + om], kv, -pm);
         if (ep.norm_l1) {
-          acc32[0] += aj * fabsf(d);
-          acc32[1] += aj * pm;
+          acc[q][0] += aj * fabsf(d);
+          acc[q][1] += aj * pm;
         } else {
-          acc32[0] += d * d;
-          acc32[1] += pm * pm;
+          acc[q][0] += d * d;
+          acc[q][1] += pm * pm;
         }
       }
     } else {  // EPI_FINAL: z = K v_true; ep.other = u buffer, ep.out = v buffer
@@ -205,8 +207,8 @@ __global__ void __launch_bounds__(kThreads) k_idft(
         const int r = idx / N, k = idx - r * N;
         const float2 zz = z[q * N + k];
         const float kv = r ? zz.y : zz.x;
-        const size_t o = fbase + (size_t)(r ? J : j) * nlon + k;
         const size_t om = (size_t)(r ? J : j) * nlon + k;
+        const size_t o = fbase + om;
         const float pm = __ldg(pp + om), qm = __ldg(qq + om);
         const float uu = al * ep.other[o];
         const float vv = be * ep.out[o];
@@ -214,73 +216,110 @@ __global__ void __launch_bounds__(kThreads) k_idft(
         ep.out[o] = vv;
         const float d = fmaf(uu, kv, -pm);
         if (ep.norm_l1) {
-          acc32[0] += aj * fabsf(d);
-          acc32[1] += aj * pm;
+          acc[q][0] += aj * fabsf(d);
+          acc[q][1] += aj * pm;
         } else {
-          acc32[0] += d * d;
-          acc32[1] += pm * pm;
+          acc[q][0] += d * d;
+          acc[q][1] += pm * pm;
         }
-        acc32[2] += aj * uu * kv;
+        acc[q][2] += aj * uu * kv;
         // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
         const float lu = logf(uu), lv = logf(vv);
         float t;
         if (ep.balanced) {
           t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);
         } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u)
-          t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) + (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
+          t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
+              (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
         }
-        acc32[3] += aj * t;
+        acc[q][3] += aj * t;
       }
     }
-    double acc[NPART];
+  }
+  // one block reduction for all fields of the CTA
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < NPART; ++i) acc[i] = (double)acc32[i];
-    block_sum4(acc, red);
-    if (threadIdx.x == 0) {
-      double* pt = ep.part + ((size_t)f * nh + jh) * NPART;
+  for (int q = 0; q < FG; ++q)
 #pragma unroll
-      for (int i = 0; i < NPART; ++i) pt[i] = acc[i];
+    for (int i = 0; i < NPART; ++i) {
+      const float v = warp_sum_f(acc[q][i]);
+      if (lane == 0) red[wid][q * NPART + i] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < FG * NPART) {
+    const int q = threadIdx.x / NPART, i = threadIdx.x - q * NPART;
+    if (q < nfg) {
+      const int f = f0 + q;
+      const ProbState* P = ep.ps + f;
+      const bool live = (ep.mode == EPI_FINAL) ? (P->status >= 0) : (P->active != 0);
+      if (live) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += (double)red[w][threadIdx.x];
+        ep.part[((size_t)f * nh + jh) * NPART + i] = t;
+      }
     }
   }
 }
 
 int pick_fg(int N, int nf) {
-  // shared memory: twiddles + two ping-pong buffers of FG sequences
-  const int budget = 200 * 1024 / 8;
-  int fg = (budget - N) / (2 * N);
-  fg = fg < 1 ? 1 : fg;
-  if (fg > 32) fg = 32;
-  if (fg > nf) fg = nf;
+  int fg = 8;
+  while (fg > 1 && (fg * N > kFftCap || fg > nf)) fg >>= 1;
   return fg;
+}
+
+template <int FG>
+int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which, float* X,
+                 int ldc, cudaStream_t st) {
+  const size_t smem = (size_t)(g.nlon + 2 * FG * g.nlon) * sizeof(float2);
+  SHOT_CUDA(cudaFuncSetAttribute(k_dft_fwd<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(g.nh, (nf + FG - 1) / FG);
+  ProfScope prof(PK_DFT, st);
+  count_launch();
+  k_dft_fwd<FG><<<grid, kThreads, smem, st>>>(in, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, ps, scale_which, X,
+                                              ldc, g.plan, g.tw_d);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
+}
+
+template <int FG>
+int launch_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
+  const size_t smem = (size_t)(g.nlon + 2 * FG * g.nlon) * sizeof(float2);
+  SHOT_CUDA(cudaFuncSetAttribute(k_idft<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  dim3 grid(g.nh, (nf + FG - 1) / FG);
+  ProfScope prof(PK_IDFT, st);
+  count_launch();
+  k_idft<FG><<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, ep);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
 }
 
 }  // namespace
 
 int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
                    float* X, int ldc, cudaStream_t st) {
-  const int FG = pick_fg(g.nlon, nf);
-  const size_t smem = (size_t)(g.nlon + 2 * FG * g.nlon) * sizeof(float2);
-  SHOT_CUDA(cudaFuncSetAttribute(k_dft_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(g.nh, (nf + FG - 1) / FG);
-  ProfScope prof(PK_DFT, st);
-  count_launch();
-  k_dft_fwd<<<grid, kThreads, smem, st>>>(in, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, ps, scale_which,
-                                          X, ldc, g.plan, g.tw_d, FG);
-  SHOT_CUDA(cudaGetLastError());
-  return SHOT_OK;
+  if (g.nlon > kFftCap) {
+    set_error("nlon too large for the shared-memory ring FFT");
+    return SHOT_ERR_UNSUPPORTED;
+  }
+  switch (pick_fg(g.nlon, nf)) {
+    case 8: return launch_fwd_t<8>(g, in, nf, ps, scale_which, X, ldc, st);
+    case 4: return launch_fwd_t<4>(g, in, nf, ps, scale_which, X, ldc, st);
+    case 2: return launch_fwd_t<2>(g, in, nf, ps, scale_which, X, ldc, st);
+    default: return launch_fwd_t<1>(g, in, nf, ps, scale_which, X, ldc, st);
+  }
 }
 
 int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
-  const int FG = pick_fg(g.nlon, nf);
-  const size_t smem = (size_t)(g.nlon + 2 * FG * g.nlon) * sizeof(float2);
-  SHOT_CUDA(cudaFuncSetAttribute(k_idft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(g.nh, (nf + FG - 1) / FG);
-  ProfScope prof(PK_IDFT, st);
-  count_launch();
-  k_idft<<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, FG,
-                                       ep);
-  SHOT_CUDA(cudaGetLastError());
-  return SHOT_OK;
+  if (g.nlon > kFftCap) {
+    set_error("nlon too large for the shared-memory ring FFT");
+    return SHOT_ERR_UNSUPPORTED;
+  }
+  switch (pick_fg(g.nlon, nf)) {
+    case 8: return launch_idft_t<8>(g, Y, ldc, nf, ep, st);
+    case 4: return launch_idft_t<4>(g, Y, ldc, nf, ep, st);
+    case 2: return launch_idft_t<2>(g, Y, ldc, nf, ep, st);
+    default: return launch_idft_t<1>(g, Y, ldc, nf, ep, st);
+  }
 }
 
 }  // namespace shot

@@ -90,6 +90,21 @@ __device__ __forceinline__ void bfly5(float2* v) {
   v[3] = csub(a2, b2);
 }
 
+// Threads of an FFT CTA and the most elements (sequences x length) one CTA transforms:
+// two ping-pong buffers of kFftCap complex values plus the twiddles stay under ~110 KB, so
+// two CTAs fit on one SM.
+constexpr int kFftThreads = 512;
+constexpr int kFftCap = 6400;
+
+template <int R, bool INV>
+__device__ __forceinline__ void butterfly(float2* v) {
+  if (R == 2) bfly2<INV>(v);
+  if (R == 3) bfly3<INV>(v);
+  if (R == 4) bfly4<INV>(v[0], v[1], v[2], v[3]);
+  if (R == 5) bfly5<INV>(v);
+  if (R == 8) bfly8<INV>(v);
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst,
                                                const float2* __restrict__ tw, int N, int Ns, int nseq,
@@ -114,20 +129,16 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
       }
       v[r] = x;
     }
-    if (R == 2) bfly2<INV>(v);
-    if (R == 3) bfly3<INV>(v);
-    if (R == 4) bfly4<INV>(v[0], v[1], v[2], v[3]);
-    if (R == 5) bfly5<INV>(v);
-    if (R == 8) bfly8<INV>(v);
+    butterfly<R, INV>(v);
     const int o = (j / Ns) * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[o + r * Ns] = v[r];
   }
 }
 
-// Transforms nseq sequences of length plan.N stored at a[q*ld + k].  b is scratch of the
-// same shape.  Returns the buffer that holds the result (a or b).  All threads of the
-// block must call it; it synchronises internally and before returning.
+// Transforms nseq sequences of length plan.N stored at a[q*ld + k]; b is scratch of the
+// same shape.  Returns the buffer holding the result.  All threads of the block must
+// call it; it synchronises after every stage.
 template <bool INV>
 __device__ float2* fft_smem(float2* a, float2* b, const float2* tw, const FftPlan& pl, int nseq, int ld) {
   int Ns = 1;
