@@ -132,6 +132,56 @@ def fp32_simt_peak_tflops():
     return 152 * 128 * 2 * 2.070e9 / 1e12
 
 
+def algorithmic_work(kind, nlat, nlon, nfields, fp32):
+    """(bytes, flops) one launch of a kernel kind must move / compute at minimum.
+
+    n = nlat*nlon nodes, nh = ceil(nlat/2) ring pairs, T = (lmax+1)(lmax+2)/2 degrees
+    and orders; the folded table holds T*nh entries (4 B in FP32, 2+2 B as bf16 hi/lo).
+    """
+    n = nlat * nlon
+    nh = (nlat + 1) // 2
+    L = nlat
+    T = L * (L + 1) // 2
+    field = nfields * n * 4.0                     # one FP32 field batch
+    spec = 2 * L * nh * 2 * nfields * 4.0         # folded ring spectra X or Y (FP32)
+    coef = T * 2 * nfields * 4.0                  # coefficients (FP32, or bf16 hi+lo)
+    table = T * nh * 4.0
+    if kind == "ring_dft":
+        return field + spec, 0.0
+    if kind == "inverse_dft_epilogue":
+        return spec + 2 * field, 0.0              # Y in, marginal in, scaling out
+    if kind == "legendre_analysis":
+        return table + spec + coef, legendre_flops_per_launch(nlat, L - 1, nfields)
+    if kind == "legendre_synthesis":
+        return table + coef + spec, legendre_flops_per_launch(nlat, L - 1, nfields)
+    return 0.0, 0.0
+
+
+def roofline(kind, avg_ms, nlat, nlon, nfields, fp32):
+    by, fl = algorithmic_work(kind, nlat, nlon, nfields, fp32)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    src = "of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
+    if hbm is None:
+        hbm, src = 6800.0, "of fallback (6.8 TB/s)"
+    s = avg_ms / 1e3
+    if kind.startswith("legendre") and fp32:
+        peak = fp32_simt_peak_tflops()
+        ach = fl / s / 1e12
+        return {"kernel": kind, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "FP32 FFMA, derived: 152 SMs x 128 lanes x 2 FLOP x 2.070 GHz",
+                "algorithmic_per_launch": fl, "avg_launch_ms": avg_ms}
+    ach = by / s / 1e9
+    out = {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+           "traffic": None, "peak_source": src, "algorithmic_per_launch": by, "avg_launch_ms": avg_ms}
+    if kind.startswith("legendre"):
+        bf = peaks.get("bf16_tflops_sustained", 1700.0)
+        out["tensor"] = {"issued_tflops": 3 * fl / s / 1e12, "peak_bf16_tflops": bf,
+                         "frac": 3 * fl / s / 1e12 / bf, "note": "BF16x3 issues 3 MMAs per product"}
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -278,35 +328,16 @@ def main():
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
-    peaks = measured_peaks()
-    nfields = 3 * PAIRS
-    if dom in ("legendre_analysis", "legendre_synthesis"):
-        fl = legendre_flops_per_launch(nlat, nlat - 1, nfields)
-        achieved = fl / (dom_ms / dom_n / 1e3) / 1e12
-        if prec == shot.SHOT_FP32:
-            peak, bound, unit = fp32_simt_peak_tflops(), "alu", "TFLOP/s"
-            peak_src = "FP32 FFMA peak derived: 152 SMs x 128 lanes x 2 x 2.070 GHz"
-        else:
-            peak, bound, unit = peaks.get("bf16_tflops_sustained", 1700.0), "tensor", "TFLOP/s"
-            peak_src = "bf16 sustained, of measured (MEASURED_PEAKS.json)"
-        roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
-                "algorithmic_per_launch": fl, "launches": dom_n, "avg_launch_ms": dom_ms / dom_n}
-    else:
-        n = nlat * nlon
-        by = nfields * n * 4 * 2.0  # fields in, spectra out (same size), FP32
-        achieved = by / (dom_ms / dom_n / 1e3) / 1e9
-        peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": "hbm_gbs, of measured",
-                "algorithmic_per_launch": by, "launches": dom_n, "avg_launch_ms": dom_ms / dom_n}
+    roof = roofline(dom, dom_ms / dom_n, nlat, nlon, 3 * PAIRS, prec == shot.SHOT_FP32)
+    roof["launches"] = dom_n
     share = {k: round(v[0] / sum(x[0] for x in kinds.values()), 4) for k, v in kinds.items()}
+    per_kind = {k: {"avg_launch_ms": round(v[0] / v[1], 5), "launches": v[1]} for k, v in kinds.items()}
 
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config(args, nlat, nlon), "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "roofline": roof, "kernel_share": share,
+            "roofline": roof, "kernel_share": share, "kernels": per_kind,
             "status": {"rc": int(rc), "S_finite": bool(np.all(np.isfinite(res["S"])))}}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args, x, w, a_ring)

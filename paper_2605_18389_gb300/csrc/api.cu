@@ -34,19 +34,18 @@ int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int l
 
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st) {
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st);
-  set_error("precision not built");
-  return SHOT_ERR_UNSUPPORTED;
+  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st) {
   if (g.precision == SHOT_FP32) return launch_analysis_simt(g, nf, X, C, ldc, apply_h, st);
-  set_error("precision not built");
-  return SHOT_ERR_UNSUPPORTED;
+  return launch_legendre_tc(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
 }
 int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st) {
   if (g.precision == SHOT_FP32) return launch_synthesis_simt(g, nf, C, Y, ldc, st);
-  set_error("precision not built");
-  return SHOT_ERR_UNSUPPORTED;
+  int rc = launch_c_to_ct(g, nf, C, ldc, st);
+  if (rc) return rc;
+  return launch_legendre_tc(g, nf, nullptr, nullptr, Y, ldc, false, true, false, st);
 }
 
 namespace {
@@ -280,9 +279,14 @@ int run_sinkhorn(Grid& g, const std::vector<const float*>& P, const std::vector<
   if ((rc = reduce(g, RED_FINAL, nprob, ep, tol, st))) return rc;
   out.ps.resize(nprob);
   SHOT_CUDA(cudaMemcpyAsync(w.host_probs, ps, nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, st));
-  SHOT_CUDA(cudaMemcpyAsync(w.host_int, w.dev_int, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  SHOT_CUDA(cudaMemcpyAsync(w.host_int, w.dev_int, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
   SHOT_CUDA(cudaStreamSynchronize(st));
   memcpy(out.ps.data(), w.host_probs, nprob * sizeof(ProbState));
+  if (w.host_int[4] != 0) {
+    SHOT_CUDA(cudaMemsetAsync(w.dev_int + 4, 0, sizeof(int), st));
+    set_error("a bounded device-side wait expired in a tensor-core kernel");
+    return SHOT_ERR_TIMEOUT;
+  }
   for (auto& p : out.ps) {
     if (p.status == SHOT_OK && p.active) {
       p.iters = w.host_int[0];
@@ -332,7 +336,6 @@ int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision, 
   }
   if (precision != SHOT_FP32 && precision != SHOT_BF16X3) { set_error("unknown precision"); return SHOT_ERR_INVALID_ARG; }
   if (legendre_mode != SHOT_TABLE) { set_error("unknown legendre_mode"); return SHOT_ERR_INVALID_ARG; }
-  if (precision != SHOT_FP32) { set_error("precision not built"); return SHOT_ERR_UNSUPPORTED; }
   FftPlan plan;
   if (!make_fft_plan(nlon, &plan)) { set_error("nlon must factor into 2, 3 and 5"); return SHOT_ERR_UNSUPPORTED; }
   Grid* g = new Grid;
@@ -356,7 +359,8 @@ int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision, 
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->M_d,
+  void* dptr[] = {g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi, g->tabT_lo,
+                  g->ws.ct_hi, g->ws.ct_lo, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};
   for (void* p : dptr)

@@ -73,7 +73,8 @@ __global__ void k_area(int nlat, int nlon, const double* __restrict__ w, float* 
 // One thread per (m, jh); row l goes to block (m, (l-m) mod 2), row (l-m)/2.
 __global__ void k_pbar(int lmax, int nh, const double* __restrict__ x, const long long* __restrict__ row_off,
                        int ldt, float* __restrict__ tab, __nv_bfloat16* __restrict__ hi,
-                       __nv_bfloat16* __restrict__ lo) {
+                       __nv_bfloat16* __restrict__ lo, int ldi, __nv_bfloat16* __restrict__ thi,
+                       __nv_bfloat16* __restrict__ tlo) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (j >= nh) return;
@@ -88,8 +89,12 @@ __global__ void k_pbar(int lmax, int nh, const double* __restrict__ x, const lon
     if (tab) tab[off] = (float)val;
     if (hi) {
       const __nv_bfloat16 h = __double2bfloat16(val);
+      const __nv_bfloat16 l = __double2bfloat16(val - (double)__bfloat162float(h));
       hi[off] = h;
-      lo[off] = __double2bfloat16(val - (double)__bfloat162float(h));
+      lo[off] = l;
+      const size_t offT = ((size_t)blk * nh + j) * ldi + (d >> 1);
+      thi[offT] = h;
+      tlo[offT] = l;
     }
   };
   store(m, pmm);
@@ -206,6 +211,7 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   const size_t tab_elems = (size_t)g.rows_total * g.ldt;
   float* tab = nullptr;
   __nv_bfloat16 *hi = nullptr, *lo = nullptr;
+  g.ldi = (g.M[0] + 7) / 8 * 8;
   if (g.precision == SHOT_FP32) {
     SHOT_CUDA(cudaMalloc(&g.tab, tab_elems * sizeof(float)));
     SHOT_CUDA(cudaMemsetAsync(g.tab, 0, tab_elems * sizeof(float), st));
@@ -217,10 +223,15 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
     SHOT_CUDA(cudaMemsetAsync(g.tab_lo, 0, tab_elems * sizeof(__nv_bfloat16), st));
     hi = g.tab_hi;
     lo = g.tab_lo;
+    const size_t tT = (size_t)g.nblk * nh * g.ldi;
+    SHOT_CUDA(cudaMalloc(&g.tabT_hi, tT * sizeof(__nv_bfloat16)));
+    SHOT_CUDA(cudaMalloc(&g.tabT_lo, tT * sizeof(__nv_bfloat16)));
+    SHOT_CUDA(cudaMemsetAsync(g.tabT_hi, 0, tT * sizeof(__nv_bfloat16), st));
+    SHOT_CUDA(cudaMemsetAsync(g.tabT_lo, 0, tT * sizeof(__nv_bfloat16), st));
   }
   dim3 gp((nh + 127) / 128, L);
   count_launch();
-  k_pbar<<<gp, 128, 0, st>>>(g.lmax, nh, g.x_d, g.row_off_d, g.ldt, tab, hi, lo);
+  k_pbar<<<gp, 128, 0, st>>>(g.lmax, nh, g.x_d, g.row_off_d, g.ldt, tab, hi, lo, g.ldi, g.tabT_hi, g.tabT_lo);
   SHOT_CUDA(cudaGetLastError());
 
   // tile lists: analysis tiles cover the rows i of each block, synthesis tiles the nodes
@@ -275,6 +286,7 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   Workspace& w = g.ws;
   if (w.dev_int == nullptr) {
     SHOT_CUDA(cudaMalloc(&w.dev_int, 16 * sizeof(int)));
+    SHOT_CUDA(cudaMemsetAsync(w.dev_int, 0, 16 * sizeof(int), st));
     SHOT_CUDA(cudaMallocHost(&w.host_int, 16 * sizeof(int)));
   }
   if (nf <= w.nf_cap) return SHOT_OK;
@@ -284,6 +296,10 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   cudaFree(w.part);
   cudaFree(w.probs);
   cudaFree(w.marg);
+  cudaFree(w.ct_hi);
+  cudaFree(w.ct_lo);
+  w.ct_hi = w.ct_lo = nullptr;
+  w.nmma_cap = 0;
   if (w.host_probs) cudaFreeHost(w.host_probs);
   w.XY = w.C = nullptr;
   w.part = nullptr;
@@ -303,6 +319,14 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   // X and C are never read before written except padding columns; keep them finite
   SHOT_CUDA(cudaMemsetAsync(w.XY, 0, xy * sizeof(float), st));
   SHOT_CUDA(cudaMemsetAsync(w.C, 0, cc * sizeof(float), st));
+  if (g.precision == SHOT_BF16X3) {
+    w.nmma_cap = tc_nmma(nf);
+    const size_t ct = (size_t)g.nblk * w.nmma_cap * g.ldi;
+    SHOT_CUDA(cudaMalloc(&w.ct_hi, ct * sizeof(__nv_bfloat16)));
+    SHOT_CUDA(cudaMalloc(&w.ct_lo, ct * sizeof(__nv_bfloat16)));
+    SHOT_CUDA(cudaMemsetAsync(w.ct_hi, 0, ct * sizeof(__nv_bfloat16), st));
+    SHOT_CUDA(cudaMemsetAsync(w.ct_lo, 0, ct * sizeof(__nv_bfloat16), st));
+  }
   w.ldc = ldc;
   w.nf_cap = nf;
   return SHOT_OK;

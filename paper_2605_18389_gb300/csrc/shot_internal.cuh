@@ -67,7 +67,10 @@ struct Workspace {
   float* ubuf = nullptr;    // internal u, v storage for the divergence [3*nf*n] each
   float* vbuf = nullptr;
   size_t uv_cap = 0;
-  int* dev_int = nullptr;   // device counters (iteration index, ...)
+  __nv_bfloat16* ct_hi = nullptr;   // BF16X3: scaled coefficients C^T [blk][nmma_cap][ldi]
+  __nv_bfloat16* ct_lo = nullptr;
+  int nmma_cap = 0;
+  int* dev_int = nullptr;   // device counters: [0] iterations, [1] active, [4] timeout flag
   int* host_int = nullptr;  // pinned mirror
   void* host_probs = nullptr;  // pinned ProbState mirror
   size_t host_probs_cap = 0;
@@ -93,8 +96,11 @@ struct Grid {
   float2* tw_d = nullptr;       // exp(-2 pi i k / nlon), k < nlon
   float* h_d = nullptr;         // heat multipliers for the current call, [lmax+1]
   float* tab = nullptr;         // FP32 folded table
-  __nv_bfloat16* tab_hi = nullptr;  // BF16X3 split table
+  __nv_bfloat16* tab_hi = nullptr;  // BF16X3 split table [row][ldt]
   __nv_bfloat16* tab_lo = nullptr;
+  __nv_bfloat16* tabT_hi = nullptr;  // BF16X3 transposed copy [blk][jh][ldi]
+  __nv_bfloat16* tabT_lo = nullptr;
+  int ldi = 0;                  // row stride of the transposed table (>= max M, multiple of 8)
   int* M_d = nullptr;
   long long* row_off_d = nullptr;
   Tile* tiles_ana = nullptr;
@@ -151,6 +157,10 @@ int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int l
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st);
 int build_grid_tables(Grid& g, cudaStream_t st);
+int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
+                       bool apply_h, cudaStream_t st);
+int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
+int tc_nmma(int nf);
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
 
 }  // namespace shot
