@@ -142,6 +142,25 @@ int shot_divergence(shot_grid g, const float* p, const float* q, int batch, doub
                     double* S, double* S_dual, int* status,
                     float* u3, float* v3, double* ot3, int* iters3, void* stream);
 
+/* ---- heat convolution without device allocation (no counterpart in the paper) ----
+ * For callers that cannot call cudaMalloc where they need K_t: code running while
+ * another component owns the allocator (a pool that must not grow, a framework step
+ * that forbids allocation, a stream another party is capturing into a CUDA graph), or
+ * processes held to a device-memory budget fixed at start-up.  shot_heat_apply may
+ * grow the grid's workspace; this variant never allocates: its scratch (ring spectra
+ * and Legendre coefficients) lives in a fixed file-scope __device__ array of
+ * SHOT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until exit.
+ *   Same arguments and result as shot_heat_apply; SHOT_FP32 grids only.
+ *   Needs (2(lmax+1)ceil(nlat/2) + (lmax+1)(lmax+2)/2) * ldc * 4 bytes with
+ *   ldc = 2*nfields rounded up to a multiple of 4; larger requests return
+ *   SHOT_ERR_INVALID_ARG with the sizes in shot_last_error().
+ *   The first call on a device resolves the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make it before any stream capture.
+ *   All calls share the array: calls whose kernels may overlap on the GPU race and must
+ *   be serialised by the caller.  Asynchronous on `stream`. */
+#define SHOT_NOALLOC_SCRATCH_BYTES (8u << 20)
+int shot_heat_apply_noalloc(shot_grid g, double t, const float* in, float* out, int nfields, void* stream);
+
 /* ---- measurement helpers (no counterpart in the paper) -------------------
  * shot_launch_count: total number of CUDA kernels this library has launched in the
  *   process (host counter; *n receives it).

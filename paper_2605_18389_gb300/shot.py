@@ -53,6 +53,7 @@ SIGNATURES = {
     "shot_divergence": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                         ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_int_p, _vp, _vp,
                         _c_dbl_p, _c_int_p, _vp],
+    "shot_heat_apply_noalloc": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
     "shot_launch_count": [ctypes.POINTER(ctypes.c_longlong)],
     "shot_profile_enable": [ctypes.c_int],
     "shot_profile_read": [_c_dbl_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int],
@@ -156,6 +157,13 @@ def shot_heat_apply(g, t, inp, out, stream=None):
     nf = inp.shape[0]
     return _check(lib().shot_heat_apply(g, float(t), _dev_ptr(inp, "in"), _dev_ptr(out, "out", inp.shape),
                                         nf, _stream(stream)))
+
+
+def shot_heat_apply_noalloc(g, t, inp, out, stream=None):
+    """shot_heat_apply without any device allocation (fixed library-owned scratch)."""
+    nf = inp.shape[0]
+    return _check(lib().shot_heat_apply_noalloc(g, float(t), _dev_ptr(inp, "in"), _dev_ptr(out, "out", inp.shape),
+                                                nf, _stream(stream)))
 
 
 def shot_sht_analysis(g, inp, coeffs, stream=None):
