@@ -35,3 +35,15 @@ UNIT = {"fp32": 2.0 ** -24, "bf16x3": 2.0 ** -16}
 def s_err_prec(s_gpu, s_ref, ot_ref, tol, prec):
     s_gpu, s_ref, ot_ref = (np.asarray(a, dtype=np.float64) for a in (s_gpu, s_ref, ot_ref))
     return np.abs(s_gpu - s_ref) / (tol * np.abs(s_ref) + 4.0 * UNIT[prec] * np.abs(ot_ref))
+
+
+def potentials_err(grid, eps, u, v, phi_ref, psi_ref):
+    """max over problems of the gauge-fixed potential errors (phi~ and psi~ relative to
+    their largest magnitude), phi~ = phi - <a,phi>/4pi, psi~ = psi + <a,phi>/4pi: the
+    potentials of Alg. 1 are defined up to (phi + c, psi - c)."""
+    from oracle.sinkhorn import gauge_fixed
+    phi = eps * np.log(np.asarray(u, dtype=np.float64))
+    psi = eps * np.log(np.asarray(v, dtype=np.float64))
+    gp, gs = gauge_fixed(grid, phi, psi)
+    rp, rs = gauge_fixed(grid, phi_ref, psi_ref)
+    return max(max(rel_max(gp[b], rp[b]), rel_max(gs[b], rs[b])) for b in range(phi.shape[0]))

@@ -7,7 +7,7 @@ import pytest
 from oracle.grid import Grid as OGrid
 from oracle import sinkhorn as sk
 from paper_2605_18389_gb300 import inputs
-from tests.gpu_util import rel_max, f32, s_err
+from tests.gpu_util import rel_max, f32, s_err, potentials_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -52,7 +52,8 @@ def test_sinkhorn_fixed_iterations_match_oracle(grid_cache, nlat, nlon, eps, tau
     assert rc == 0 and np.all(r["status"] == 0) and np.all(ref["status"] == 0)
     assert np.all(r["iters"] == T)
     u, v = r["u"].cpu().numpy(), r["v"].cpu().numpy()
-    for b in range(3):
+    assert potentials_err(og, eps, u, v, ref["phi"], ref["psi"]) < TOL_PHI
+    for b in range(3):   # FP32 also meets the bar without removing the gauge
         assert rel_max(eps * np.log(u[b]), ref["phi"][b]) < TOL_PHI
         assert rel_max(eps * np.log(v[b]), ref["psi"][b]) < TOL_PHI
     np.testing.assert_allclose(r["ot"], ref["ot"], rtol=TOL_PHI)
