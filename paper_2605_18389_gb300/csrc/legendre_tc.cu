@@ -268,26 +268,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_ana_tc(const __grid_
     // producers of the B operand: X[jh][c] FP32 -> bf16 hi/lo, K-major [c][jh] swizzled
     const int pt = threadIdx.x - 128;
     const float* Xb = a.X + (size_t)blk * a.nh * a.ldc;
-    const int c4n = a.nmma / 4;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages, n = kb / kStages;
       if (kb >= kStages && !mbar_wait(&ctl.empty[s], (n - 1) & 1, abort)) break;
       uint8_t* bh = sB_hi + s * bbytes;
       uint8_t* bl = sB_lo + s * bbytes;
-      for (int e = pt; e < kBK * c4n; e += 128) {
-        const int r = e / c4n, c = (e - r * c4n) * 4;
-        const int jh = kb * kBK + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (jh < a.nh && c < a.ncols) v = __ldg(reinterpret_cast<const float4*>(Xb + (size_t)jh * a.ldc + c));
-        const float vv[4] = {v.x, v.y, v.z, v.w};
+      // one task = 8 consecutive nodes of one column -> one 16-byte swizzle chunk of hi and
+      // of lo; a warp's 32 tasks share the nodes and read 32 consecutive columns
+      for (int e = pt; e < 8 * a.nmma; e += 128) {
+        const int r8 = e / a.nmma, c = e - r8 * a.nmma;
+        const int jh0 = kb * kBK + r8 * 8;
+        uint32_t hw[4], lw[4];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const __nv_bfloat16 hi = __float2bfloat16_rn(vv[t]);
-          const __nv_bfloat16 lo = __float2bfloat16_rn(vv[t] - __bfloat162float(hi));
-          const uint32_t o = sw128_offset(c + t, r);
-          *reinterpret_cast<__nv_bfloat16*>(bh + o) = hi;
-          *reinterpret_cast<__nv_bfloat16*>(bl + o) = lo;
+        for (int t = 0; t < 8; t += 2) {
+          float v0 = 0.f, v1 = 0.f;
+          if (c < a.ncols) {
+            if (jh0 + t < a.nh) v0 = __ldg(Xb + (size_t)(jh0 + t) * a.ldc + c);
+            if (jh0 + t + 1 < a.nh) v1 = __ldg(Xb + (size_t)(jh0 + t + 1) * a.ldc + c);
+          }
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+          const float2 hf = __bfloat1622float2(h2);
+          const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+          hw[t / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+          lw[t / 2] = *reinterpret_cast<const uint32_t*>(&l2);
         }
+        const uint32_t o = sw128_offset(c, r8 * 8);
+        *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
       }
       fence_async_smem();
       mbar_arrive(&ctl.fullB[s]);
