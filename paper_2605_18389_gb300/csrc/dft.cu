@@ -35,15 +35,13 @@ __device__ __forceinline__ void load_ring_pairs(const float* __restrict__ in, fl
                                                 int nlat, int nlon, int j, int J) {
   const int N = nlon;
   float* bf = reinterpret_cast<float*>(buf);
-  for (int idx = threadIdx.x; idx < nfg * 2 * N; idx += blockDim.x) {
-    const int q = idx / (2 * N);
-    const int rem = idx - q * 2 * N;
-    const int r = rem / N, k = rem - r * N;
-    const size_t base = (size_t)(f0 + q) * nlat * nlon;
-    float val = 0.f;
-    if (r == 0) val = __ldg(in + base + (size_t)j * nlon + k);
-    else if (J != j) val = __ldg(in + base + (size_t)J * nlon + k);
-    bf[2 * (q * N + k) + r] = val;
+  for (int q = 0; q < nfg; ++q) {
+    const float* fj = in + (size_t)(f0 + q) * nlat * nlon + (size_t)j * nlon;
+    const float* fJ = in + (size_t)(f0 + q) * nlat * nlon + (size_t)J * nlon;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      bf[2 * (q * N + k)] = __ldg(fj + k);
+      bf[2 * (q * N + k) + 1] = (J != j) ? __ldg(fJ + k) : 0.f;
+    }
   }
 }
 
@@ -69,8 +67,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_dft_fwd(
 
   const float aj = a_ring[j];
   const int nm = lmax + 1;
-  for (int idx = threadIdx.x; idx < nm * nfg; idx += blockDim.x) {
-    const int m = idx / nfg, q = idx - m * nfg;
+  for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
+    const int m = idx / FG, q = idx - m * FG;
+    if (q >= nfg) continue;
     const int f = f0 + q;
     float sc = aj;
     if (scale_which == 1) sc *= (float)ps[f].beta;
@@ -103,13 +102,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
   // zero the band lmax < m < N - lmax
   const int nz = N - 2 * lmax - 1;
-  for (int idx = threadIdx.x; idx < nfg * nz; idx += blockDim.x) {
-    const int q = idx / nz, k = idx - q * nz;
-    buf[q * N + lmax + 1 + k] = make_float2(0.f, 0.f);
-  }
+  for (int q = 0; q < nfg; ++q)
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) buf[q * N + lmax + 1 + k] = make_float2(0.f, 0.f);
   const int nm = lmax + 1;
-  for (int idx = threadIdx.x; idx < nm * nfg; idx += blockDim.x) {
-    const int m = idx / nfg, q = idx - m * nfg;
+  for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
+    const int m = idx / FG, q = idx - m * FG;
+    if (q >= nfg) continue;
     const int f = f0 + q;
     const float2 E = *reinterpret_cast<const float2*>(Y + ((size_t)(2 * m) * nh + jh) * ldc + 2 * f);
     float2 O = make_float2(0.f, 0.f);
@@ -129,12 +127,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
   const float aj = a_ring[j];
   const int nrings = (J != j) ? 2 : 1;
   if (ep.mode == EPI_PLAIN) {
-    for (int idx = threadIdx.x; idx < nfg * nrings * N; idx += blockDim.x) {
-      const int q = idx / (nrings * N);
-      const int rem = idx - q * nrings * N;
-      const int r = rem / N, k = rem - r * N;
-      const float2 zz = z[q * N + k];
-      ep.out[(size_t)(f0 + q) * nlat * nlon + (size_t)(r ? J : j) * nlon + k] = r ? zz.y : zz.x;
+    for (int q = 0; q < nfg; ++q) {
+      float* oj = ep.out + (size_t)(f0 + q) * nlat * nlon + (size_t)j * nlon;
+      float* oJ = ep.out + (size_t)(f0 + q) * nlat * nlon + (size_t)J * nlon;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float2 zz = z[q * N + k];
+        oj[k] = zz.x;
+        if (J != j) oJ[k] = zz.y;
+      }
     }
     return;
   }
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       if (!P->active) continue;
       const float* mg = ep.marg[f];
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
-        const int r = idx / N, k = idx - r * N;
+        const int r = idx >= N ? 1 : 0, k = idx - r * N;
         const float2 zz = z[q * N + k];
         const float kv = r ? zz.y : zz.x;
         const size_t om = (size_t)(r ? J : j) * nlon + k;
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       const float* mg = ep.marg[f];
       const float al = (float)P->alpha;
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
-        const int r = idx / N, k = idx - r * N;
+        const int r = idx >= N ? 1 : 0, k = idx - r * N;
         const float2 zz = z[q * N + k];
         const float kv = r ? zz.y : zz.x;
         const size_t om = (size_t)(r ? J : j) * nlon + k;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       const float al = (float)P->alpha, be = (float)P->beta;
       const float epsf = (float)ep.eps, tauf = (float)ep.tau, et = (float)(ep.eps / ep.tau);
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
-        const int r = idx / N, k = idx - r * N;
+        const int r = idx >= N ? 1 : 0, k = idx - r * N;
         const float2 zz = z[q * N + k];
         const float kv = r ? zz.y : zz.x;
         const size_t om = (size_t)(r ? J : j) * nlon + k;

@@ -105,17 +105,24 @@ __device__ __forceinline__ void butterfly(float2* v) {
   if (R == 8) bfly8<INV>(v);
 }
 
+// a / d for 0 <= a < 2^16 and 2 <= d < 2^16 with mul = ceil(2^32 / d) (exact: the
+// error a (mul - 2^32/d) / 2^32 < 2^-16 never crosses an integer); mul == 0 means d == 1.
+__device__ __forceinline__ int fast_div(int a, uint32_t mul) {
+  return mul ? (int)__umulhi((uint32_t)a, mul) : a;
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst,
                                                const float2* __restrict__ tw, int N, int Ns, int nseq,
-                                               int ld) {
+                                               int ld, uint32_t ns_mul, uint32_t nr_mul) {
   const int NR = N / R;
   const int tstep = N / (Ns * R);
   const int total = nseq * NR;
   for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-    const int q = idx / NR;
+    const int q = fast_div(idx, nr_mul);
     const int j = idx - q * NR;
-    const int k = j % Ns;
+    const int jd = fast_div(j, ns_mul);
+    const int k = j - jd * Ns;
     const float2* s = src + q * ld;
     float2* d = dst + q * ld;
     float2 v[R];
@@ -130,7 +137,7 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
       v[r] = x;
     }
     butterfly<R, INV>(v);
-    const int o = (j / Ns) * Ns * R + k;
+    const int o = jd * Ns * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) d[o + r * Ns] = v[r];
   }
@@ -145,11 +152,11 @@ __device__ float2* fft_smem(float2* a, float2* b, const float2* tw, const FftPla
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.R[s];
     switch (R) {
-      case 2: stockham_stage<2, INV>(a, b, tw, pl.N, Ns, nseq, ld); break;
-      case 3: stockham_stage<3, INV>(a, b, tw, pl.N, Ns, nseq, ld); break;
-      case 4: stockham_stage<4, INV>(a, b, tw, pl.N, Ns, nseq, ld); break;
-      case 5: stockham_stage<5, INV>(a, b, tw, pl.N, Ns, nseq, ld); break;
-      default: stockham_stage<8, INV>(a, b, tw, pl.N, Ns, nseq, ld); break;
+      case 2: stockham_stage<2, INV>(a, b, tw, pl.N, Ns, nseq, ld, pl.ns_mul[s], pl.nr_mul[s]); break;
+      case 3: stockham_stage<3, INV>(a, b, tw, pl.N, Ns, nseq, ld, pl.ns_mul[s], pl.nr_mul[s]); break;
+      case 4: stockham_stage<4, INV>(a, b, tw, pl.N, Ns, nseq, ld, pl.ns_mul[s], pl.nr_mul[s]); break;
+      case 5: stockham_stage<5, INV>(a, b, tw, pl.N, Ns, nseq, ld, pl.ns_mul[s], pl.nr_mul[s]); break;
+      default: stockham_stage<8, INV>(a, b, tw, pl.N, Ns, nseq, ld, pl.ns_mul[s], pl.nr_mul[s]); break;
     }
     __syncthreads();
     float2* t = a;

@@ -173,7 +173,16 @@ bool make_fft_plan(int N, FftPlan* pl) {
   while (n % 2 == 0) if (!push(2)) return false;
   while (n % 3 == 0) if (!push(3)) return false;
   while (n % 5 == 0) if (!push(5)) return false;
-  return n == 1 && N >= 1;
+  if (n != 1 || N < 1 || N >= (1 << 16)) return false;
+  // exact division by multiply-high for operands below 2^16
+  auto mul = [](uint32_t d) -> uint32_t { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + d - 1) / d); };
+  int Ns = 1;
+  for (int s = 0; s < pl->nst; ++s) {
+    pl->ns_mul[s] = mul((uint32_t)Ns);
+    pl->nr_mul[s] = mul((uint32_t)(N / pl->R[s]));
+    Ns *= pl->R[s];
+  }
+  return true;
 }
 
 int build_grid_tables(Grid& g, cudaStream_t st) {

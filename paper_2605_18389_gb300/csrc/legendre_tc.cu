@@ -24,7 +24,9 @@ namespace {
 constexpr int kTcThreads = 256;
 constexpr int kBM = 128;          // MMA M
 constexpr int kBK = 64;           // K elements per pipeline stage (one 128-byte swizzle row)
-constexpr int kStages = 2;
+constexpr int kMaxStages = 4;
+constexpr int kStagesAna = 3;   // one CTA per SM (table + X + B tiles)
+constexpr int kStagesSyn = 2;   // two CTAs per SM
 constexpr uint32_t kSpinLimit = 1u << 24;
 constexpr int kATileBytes = kBM * kBK * 2;   // 16 KB
 
@@ -163,9 +165,9 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
 }
 
 struct TcSmem {
-  uint64_t fullA[kStages];
-  uint64_t fullB[kStages];
-  uint64_t empty[kStages];
+  uint64_t fullA[kMaxStages];
+  uint64_t fullB[kMaxStages];
+  uint64_t empty[kMaxStages];
   uint64_t done;
   uint32_t tmem;
   int abort;
@@ -190,8 +192,10 @@ struct AnaArgs {
   int* err;
 };
 
+template <int kStages>
 __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_ana_tc(const __grid_constant__ CUtensorMap tm_hi,
                                                                    const __grid_constant__ CUtensorMap tm_lo,
+                                                                   const __grid_constant__ CUtensorMap tm_x,
                                                                    AnaArgs a) {
   extern __shared__ uint8_t smraw[];
   __shared__ TcSmem ctl;
@@ -201,6 +205,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_ana_tc(const __grid_
   uint8_t* sA_lo = sA_hi + kStages * kATileBytes;
   uint8_t* sB_hi = sA_lo + kStages * kATileBytes;
   uint8_t* sB_lo = sB_hi + kStages * bbytes;
+  const int xbytes = a.nmma * kBK * 4;     // FP32 X tile [64 nodes][nmma columns]
+  uint8_t* sX = sB_lo + kStages * bbytes;
 
   const Tile tl = a.tiles[blockIdx.x];
   const int blk = tl.blk, i0 = tl.r0;
@@ -234,9 +240,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_ana_tc(const __grid_
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % kStages, n = kb / kStages;
         if (kb >= kStages && !mbar_wait(&ctl.empty[s], (n - 1) & 1, abort)) break;
-        mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes);
+        mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + xbytes);
         tma_load_2d(sA_hi + s * kATileBytes, &tm_hi, &ctl.fullA[s], kb * kBK, (int)(ro + i0));
         tma_load_2d(sA_lo + s * kATileBytes, &tm_lo, &ctl.fullA[s], kb * kBK, (int)(ro + i0));
+        tma_load_2d(sX + s * xbytes, &tm_x, &ctl.fullA[s], 0, blk * a.nh + kb * kBK);
         issued = kb + 1;
       }
       for (int kb = issued > kStages ? issued - kStages : 0; kb < issued; ++kb)
@@ -265,27 +272,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_ana_tc(const __grid_
       umma_commit(&ctl.done);
     }
   } else if (warp >= 4) {
-    // producers of the B operand: X[jh][c] FP32 -> bf16 hi/lo, K-major [c][jh] swizzled
+    // producers of the B operand: the FP32 tile X[jh][c] (brought by TMA with the table
+    // tiles) -> bf16 hi/lo, K-major [c][jh], 128-byte swizzled
     const int pt = threadIdx.x - 128;
-    const float* Xb = a.X + (size_t)blk * a.nh * a.ldc;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % kStages, n = kb / kStages;
-      if (kb >= kStages && !mbar_wait(&ctl.empty[s], (n - 1) & 1, abort)) break;
+      if (!mbar_wait(&ctl.fullA[s], n & 1, abort)) break;
+      const float* xs = reinterpret_cast<const float*>(sX + s * xbytes);
       uint8_t* bh = sB_hi + s * bbytes;
       uint8_t* bl = sB_lo + s * bbytes;
-      // one task = 8 consecutive nodes of one column -> one 16-byte swizzle chunk of hi and
-      // of lo; a warp's 32 tasks share the nodes and read 32 consecutive columns
+      // one task = 8 consecutive nodes of one column -> one 16-byte swizzle chunk of hi
+      // and of lo; rows beyond the block's nodes (or columns beyond the fields) are zero
       for (int e = pt; e < 8 * a.nmma; e += 128) {
         const int r8 = e / a.nmma, c = e - r8 * a.nmma;
         const int jh0 = kb * kBK + r8 * 8;
         uint32_t hw[4], lw[4];
 #pragma unroll
         for (int t = 0; t < 8; t += 2) {
-          float v0 = 0.f, v1 = 0.f;
-          if (c < a.ncols) {
-            if (jh0 + t < a.nh) v0 = __ldg(Xb + (size_t)(jh0 + t) * a.ldc + c);
-            if (jh0 + t + 1 < a.nh) v1 = __ldg(Xb + (size_t)(jh0 + t + 1) * a.ldc + c);
-          }
+          float v0 = xs[(r8 * 8 + t) * a.nmma + c];
+          float v1 = xs[(r8 * 8 + t + 1) * a.nmma + c];
+          if (c >= a.ncols || jh0 + t >= a.nh) v0 = 0.f;
+          if (c >= a.ncols || jh0 + t + 1 >= a.nh) v1 = 0.f;
           const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
           const float2 hf = __bfloat1622float2(h2);
           const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
@@ -345,6 +352,7 @@ struct SynArgs {
   int* err;
 };
 
+template <int kStages>
 __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_syn_tc(const __grid_constant__ CUtensorMap ta_hi,
                                                                    const __grid_constant__ CUtensorMap ta_lo,
                                                                    const __grid_constant__ CUtensorMap tb_hi,
@@ -501,7 +509,31 @@ int make_map(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t rows, u
   return SHOT_OK;
 }
 
-size_t tc_smem_bytes(int nmma) { return 1024 + (size_t)kStages * (2 * kATileBytes + 2 * nmma * kBK * 2); }
+// 2-D FP32 tensor [rows][inner] (row stride ld elements), box {box_inner, box_rows}, no swizzle
+int make_map_f32(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t rows, uint64_t ld, uint32_t box_inner,
+                 uint32_t box_rows) {
+  auto enc = get_encode();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled unavailable");
+    return SHOT_ERR_CUDA;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {ld * 4};
+  cuuint32_t box[2] = {box_inner, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled (FP32) failed");
+    return SHOT_ERR_CUDA;
+  }
+  return SHOT_OK;
+}
+
+size_t tc_smem_bytes(int nmma, bool with_x, int stages) {
+  return 1024 + (size_t)stages * (2 * kATileBytes + 2 * nmma * kBK * 2 + (with_x ? nmma * kBK * 4 : 0));
+}
 
 }  // namespace
 
@@ -517,31 +549,38 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     set_error("BF16X3 path supports at most 128 fields per call");
     return SHOT_ERR_UNSUPPORTED;
   }
-  const size_t smem = tc_smem_bytes(nmma);
   int rc;
   if (ana) {
-    CUtensorMap mh, ml;
+    // deepest pipeline (<= 3 stages) whose tiles fit in one CTA's shared memory
+    int stages = kStagesAna;
+    while (stages > 1 && tc_smem_bytes(nmma, true, stages) > 227 * 1024) --stages;
+    const size_t smem = tc_smem_bytes(nmma, true, stages);
+    CUtensorMap mh, ml, mx;
     if ((rc = make_map(&mh, g.tab_hi, g.nh, g.rows_total, g.ldt, kBM))) return rc;
     if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kBM))) return rc;
+    if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
     AnaArgs a{g.tiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma, apply_h ? g.h_d : nullptr,
               w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4};
-    SHOT_CUDA(cudaFuncSetAttribute(k_legendre_ana_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = stages == 3 ? k_legendre_ana_tc<3> : stages == 2 ? k_legendre_ana_tc<2> : k_legendre_ana_tc<1>;
+    SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ProfScope prof(PK_ANALYSIS, st);
     count_launch();
-    k_legendre_ana_tc<<<g.ntiles_ana, kTcThreads, smem, st>>>(mh, ml, a);
+    kern<<<g.ntiles_ana, kTcThreads, smem, st>>>(mh, ml, mx, a);
     SHOT_CUDA(cudaGetLastError());
   }
   if (syn) {
+    const size_t smem = tc_smem_bytes(nmma, false, kStagesSyn);
     CUtensorMap ah, al, bh, bl;
     if ((rc = make_map(&ah, g.tabT_hi, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kBM))) return rc;
     if ((rc = make_map(&al, g.tabT_lo, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kBM))) return rc;
     if ((rc = make_map(&bh, w.ct_hi, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
     if ((rc = make_map(&bl, w.ct_lo, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
     SynArgs a{g.tiles_syn, g.M_d, g.nh, nmma, w.nmma_cap, 2 * nf, ldc, Y, w.dev_int + 4};
-    SHOT_CUDA(cudaFuncSetAttribute(k_legendre_syn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    SHOT_CUDA(cudaFuncSetAttribute(k_legendre_syn_tc<kStagesSyn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem));
     ProfScope prof(PK_SYNTHESIS, st);
     count_launch();
-    k_legendre_syn_tc<<<g.ntiles_syn, kTcThreads, smem, st>>>(ah, al, bh, bl, a);
+    k_legendre_syn_tc<kStagesSyn><<<g.ntiles_syn, kTcThreads, smem, st>>>(ah, al, bh, bl, a);
     SHOT_CUDA(cudaGetLastError());
   }
   return SHOT_OK;

@@ -40,6 +40,8 @@ struct FftPlan {
   int N;
   int nst;
   int R[12];
+  uint32_t ns_mul[12];   // ceil(2^32 / Ns) of stage s (0 when Ns == 1)
+  uint32_t nr_mul[12];   // ceil(2^32 / (N / R)) of stage s (0 when N / R == 1)
 };
 bool make_fft_plan(int N, FftPlan* plan);
 
