@@ -142,6 +142,53 @@ int shot_divergence(shot_grid g, const float* p, const float* q, int batch, doub
                     double* S, double* S_dual, int* status,
                     float* u3, float* v3, double* ot3, int* iters3, void* stream);
 
+/* Many batches of pairs on several grids in one solve (the batched uneven-grid
+ * workload): every set's problems (p_b,q_b), (p_b,p_b), (q_b,q_b) join one Alg. 1 solve
+ * per grid (sets sharing a grid may differ in tau, not in eps); the grids' solves run on
+ * separate streams inside one CUDA graph per block of check_every iterations, replayed
+ * until max_iter or until every problem passed the check.
+ *   sets[i].grid, p, q (device [batch][nlat][nlon]), batch, eps, tau (INFINITY = balanced),
+ *   S, S_dual (may be NULL), status: host [batch] outputs as in shot_divergence.
+ * Each grid's internal u, v storage grows to its problem count.  Returns the most severe
+ * status.  Synchronises `stream`. */
+typedef struct shot_pair_set {
+  shot_grid grid;
+  const float* p;
+  const float* q;
+  int batch;
+  double eps;
+  double tau;
+  double* S;
+  double* S_dual;
+  int* status;
+} shot_pair_set;
+int shot_divergence_multi(const shot_pair_set* sets, int nsets, int max_iter, double tol, int check_every,
+                          int flags, void* stream);
+
+/* Gradient of the Sinkhorn divergence S (the Alg. 1-return form of shot_divergence,
+ * including eps/2 (m(p)-m(q))^2) with respect to the node values of p, as used for the
+ * gradient-based regional attribution of Sec. 4.2.
+ *   mode SHOT_GRAD_UNROLLED: exact reverse-mode derivative of S computed by exactly
+ *        max_iter iterations of Alg. 1 (no early stop), through the gauge and the
+ *        translation-invariant steps; forward states are checkpointed every
+ *        checkpoint_every iterations and recomputed segment by segment.
+ *   mode SHOT_GRAD_ENVELOPE: the potential form, valid at convergence: balanced
+ *        a (.) [phi_pq - (phi_pp + psi_pp)/2] + eps (m(p)-m(q)) a; unbalanced, the
+ *        derivative of S_dual: a (.) [tau(1-e^{-phi_pq/tau}) - (tau(1-e^{-phi_pp/tau}) +
+ *        tau(1-e^{-psi_pp/tau}))/2].
+ *   grad_p  device [batch][nlat][nlon] float32: dS/dp_i (Euclidean; carries the factor
+ *           a_i; balanced S is defined modulo c*a, so compare along directions with
+ *           sum_i a_i d_i = 0)
+ *   S, status host [batch].  Allocates its checkpoint buffers on the device (about
+ *   (max_iter/checkpoint_every + 2 checkpoint_every + 7) * 2 * batch fields).
+ * No derivative is produced for a pair whose iteration broke down (status < 0).
+ * Synchronises `stream`. */
+#define SHOT_GRAD_UNROLLED 0
+#define SHOT_GRAD_ENVELOPE 1
+int shot_divergence_grad(shot_grid g, const float* p, const float* q, int batch, double eps, double tau,
+                         int max_iter, int checkpoint_every, int mode, double* S, float* grad_p, int* status,
+                         void* stream);
+
 /* ---- heat convolution without device allocation (no counterpart in the paper) ----
  * For callers that cannot call cudaMalloc where they need K_t: code running while
  * another component owns the allocator (a pool that must not grow, a framework step

@@ -17,6 +17,8 @@
 
 #include "shot_internal.cuh"
 
+extern "C" int shot_launch_count(long long* n);
+
 namespace shot {
 
 static thread_local std::string t_err;
@@ -61,7 +63,7 @@ __device__ __forceinline__ double wsum(double v) {
 // Fixed-order reduction of the per-ring-pair partial sums and the per-problem scalar
 // steps of Alg. 1 (gauge / TI constant / convergence test / objective).
 __global__ void k_reduce(int mode, int nprob, int nh, const double* __restrict__ part, ProbState* ps,
-                         int* dev_int, int balanced, double eps, double tau, double tol, int norm_l1) {
+                         int* dev_int, double eps, double tol, int norm_l1) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int kdone = dev_int[0];
   for (int f = wid; f < nprob; f += nw) {
@@ -90,11 +92,11 @@ __global__ void k_reduce(int mode, int nprob, int nh, const double* __restrict__
         P->su = s[0];
       } else {
         double al, be;
-        if (balanced) {
+        if (P->balanced) {
           al = 1.0 / P->su;
           be = P->su;
         } else {
-          const double c = 0.5 * tau * (log(P->su) - log(s[0]));
+          const double c = 0.5 * P->tau * (log(P->su) - log(s[0]));
           al = exp(c / eps);
           be = exp(-c / eps);
         }
@@ -130,7 +132,8 @@ __global__ void k_reduce(int mode, int nprob, int nh, const double* __restrict__
   }
 }
 
-__global__ void k_init_probs(int nprob, ProbState* ps, int* dev_int) {
+// per-problem state: tau (INFINITY = balanced) from taus[f], gamma = tau/(tau+eps)
+__global__ void k_init_probs(int nprob, ProbState* ps, int* dev_int, const double* __restrict__ taus, double eps) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f < nprob) {
     ProbState P;
@@ -139,10 +142,14 @@ __global__ void k_init_probs(int nprob, ProbState* ps, int* dev_int) {
     P.su = 0.0;
     P.err = nan("");
     P.ot = P.ot_dual = P.mass = nan("");
+    const double tau = taus[f];
+    P.tau = tau;
+    P.balanced = isinf(tau) ? 1 : 0;
+    P.gamma = P.balanced ? 1.f : (float)(tau / (tau + eps));
+    P.et = P.balanced ? 0.f : (float)(eps / (tau + eps));
     P.active = 1;
     P.status = SHOT_OK;
     P.iters = 0;
-    P.pad = 0;
     ps[f] = P;
   }
   if (f == 0) {
@@ -162,8 +169,11 @@ __global__ void k_field_mass(const float* const* __restrict__ fl, int nlat, int 
   __shared__ double red[32];
   const float* f = fl[blockIdx.x];
   double s = 0.0;
-  for (size_t i = threadIdx.x; i < (size_t)nlat * nlon; i += blockDim.x)
-    s += (double)a_ring[i / nlon] * (double)f[i];
+  for (int j = 0; j < nlat; ++j) {
+    float t = 0.f;
+    for (int k = threadIdx.x; k < nlon; k += blockDim.x) t += f[(size_t)j * nlon + k];
+    s += (double)a_ring[j] * (double)t;
+  }
   s = wsum(s);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -185,11 +195,11 @@ int heat_pipeline(Grid& g, const float* in, int nf, int scale_which, cudaStream_
   return launch_legendre(g, nf, w.XY, w.C, w.XY, w.ldc, st);
 }
 
-int reduce(Grid& g, int mode, int nprob, const EpiParams& ep, double tol, cudaStream_t st) {
+int reduce(Grid& g, int mode, int nprob, double eps, double tol, int norm_l1, cudaStream_t st) {
   ProfScope prof(PK_OTHER, st);
   count_launch();
   k_reduce<<<1, 256, 0, st>>>(mode, nprob, g.nh, g.ws.part, reinterpret_cast<ProbState*>(g.ws.probs),
-                              g.ws.dev_int, ep.balanced, ep.eps, ep.tau, tol, ep.norm_l1);
+                              g.ws.dev_int, eps, tol, norm_l1);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }
@@ -199,102 +209,265 @@ struct SolveOut {
   int kdone = 0;
 };
 
-// Algorithm 1 on nprob problems with marginal lists P (first) and Q (second).
-int run_sinkhorn(Grid& g, const std::vector<const float*>& P, const std::vector<const float*>& Q, double eps,
-                 double tau, int T, double tol, int C, int flags, float* u, float* v, cudaStream_t st,
-                 SolveOut& out) {
-  const int nprob = (int)P.size();
-  int rc = ensure_workspace(g, nprob, st);
-  if (rc) return rc;
+// One Alg. 1 solve on one grid: nprob problems with marginals P (first), Q (second) and
+// per-problem tau; state lives in the grid's workspace, work runs on the grid's stream.
+struct Solve {
+  Grid* g = nullptr;
+  int nprob = 0;
+  double eps = 0, tol = 0;
+  int C = 0, norm_l1 = 0;
+  float *u = nullptr, *v = nullptr;
+  cudaStream_t st = nullptr;
+};
+
+int ensure_stream(Grid& g) {
   Workspace& w = g.ws;
+  if (!w.stream) {
+    SHOT_CUDA(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+    SHOT_CUDA(cudaEventCreateWithFlags(&w.ev0, cudaEventDisableTiming));
+    SHOT_CUDA(cudaEventCreateWithFlags(&w.ev1, cudaEventDisableTiming));
+  }
+  return SHOT_OK;
+}
+
+int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector<const float*>& Q,
+                  const std::vector<double>& taus, double eps, double tol, int C, int flags, float* u, float* v,
+                  cudaStream_t user, Solve& s) {
+  const int nprob = (int)P.size();
+  int rc = ensure_workspace(g, nprob, user);
+  if (rc) return rc;
+  if ((rc = ensure_stream(g))) return rc;
+  Workspace& w = g.ws;
+  s.g = &g;
+  s.nprob = nprob;
+  s.eps = eps;
+  s.tol = tol;
+  s.C = C;
+  s.norm_l1 = (flags & SHOT_FLAG_NORM_L1) ? 1 : 0;
+  s.u = u;
+  s.v = v;
+  s.st = w.stream;
+  // the solver stream starts after everything already queued on the caller's stream
+  SHOT_CUDA(cudaEventRecord(w.ev0, user));
+  SHOT_CUDA(cudaStreamWaitEvent(s.st, w.ev0, 0));
   const size_t n = (size_t)g.nlat * g.nlon;
-  std::vector<const float*> lists(4 * (size_t)nprob);
+  std::vector<const float*> lists(2 * (size_t)nprob);
   for (int i = 0; i < nprob; ++i) {
     lists[i] = P[i];
     lists[nprob + i] = Q[i];
   }
-  SHOT_CUDA(cudaMemcpyAsync(w.marg, lists.data(), 2 * nprob * sizeof(float*), cudaMemcpyHostToDevice, st));
+  SHOT_CUDA(cudaMemcpyAsync(w.marg, lists.data(), 2 * nprob * sizeof(float*), cudaMemcpyHostToDevice, s.st));
+  SHOT_CUDA(cudaMemcpyAsync(w.taus, taus.data(), nprob * sizeof(double), cudaMemcpyHostToDevice, s.st));
   ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   count_launch();
-  k_init_probs<<<(nprob + 127) / 128, 128, 0, st>>>(nprob, ps, w.dev_int);
+  k_init_probs<<<(nprob + 127) / 128, 128, 0, s.st>>>(nprob, ps, w.dev_int, w.taus, eps);
   if (!(flags & SHOT_FLAG_WARM_START)) {
     count_launch(2);
-    k_fill<<<1024, 256, 0, st>>>(u, n * nprob, 1.f);
-    k_fill<<<1024, 256, 0, st>>>(v, n * nprob, 1.f);
+    k_fill<<<1024, 256, 0, s.st>>>(u, n * nprob, 1.f);
+    k_fill<<<1024, 256, 0, s.st>>>(v, n * nprob, 1.f);
   }
   SHOT_CUDA(cudaGetLastError());
-  rc = launch_heat_mult(g, eps / 4.0, st);
-  if (rc) return rc;
+  return launch_heat_mult(g, eps / 4.0, s.st);
+}
 
+EpiParams base_ep(Solve& s) {
+  Workspace& w = s.g->ws;
   EpiParams ep{};
-  ep.ps = ps;
+  ep.ps = reinterpret_cast<ProbState*>(w.probs);
   ep.part = w.part;
-  ep.balanced = isinf(tau) ? 1 : 0;
-  ep.gamma = ep.balanced ? 1.f : (float)(tau / (tau + eps));
-  ep.eps_over_taueps = ep.balanced ? 0.f : (float)(eps / (tau + eps));
-  ep.eps = eps;
-  ep.tau = tau;
-  ep.norm_l1 = (flags & SHOT_FLAG_NORM_L1) ? 1 : 0;
-  const float* const* margP = w.marg;
-  const float* const* margQ = w.marg + nprob;
+  ep.eps = s.eps;
+  ep.norm_l1 = s.norm_l1;
+  return ep;
+}
 
-  int k = 0;
-  for (k = 1; k <= T; ++k) {
-    // u-step: u = p / K(beta v)
-    if ((rc = heat_pipeline(g, v, nprob, 1, st))) return rc;
+// nit iterations of Alg. 1, then (optionally) the marginal check; no host synchronisation
+int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
+  Grid& g = *s.g;
+  Workspace& w = g.ws;
+  const float* const* margP = w.marg;
+  const float* const* margQ = w.marg + s.nprob;
+  EpiParams ep = base_ep(s);
+  int rc;
+  for (int i = 0; i < nit; ++i) {
+    // u-step: u = (p / K(beta v))^gamma
+    if ((rc = heat_pipeline(g, s.v, s.nprob, 1, st))) return rc;
     ep.mode = EPI_UPDATE;
-    ep.out = u;
+    ep.out = s.u;
     ep.marg = margP;
     ep.which = 0;
-    if ((rc = launch_idft(g, w.XY, w.ldc, nprob, ep, st))) return rc;
-    if ((rc = reduce(g, RED_U, nprob, ep, tol, st))) return rc;
-    // v-step: v = q / K u
-    if ((rc = heat_pipeline(g, u, nprob, 0, st))) return rc;
-    ep.out = v;
+    if ((rc = launch_idft(g, w.XY, w.ldc, s.nprob, ep, st))) return rc;
+    if ((rc = reduce(g, RED_U, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
+    // v-step: v = (q / K u)^gamma, then the gauge / translation-invariant scalars
+    if ((rc = heat_pipeline(g, s.u, s.nprob, 0, st))) return rc;
+    ep.out = s.v;
     ep.marg = margQ;
     ep.which = 1;
-    if ((rc = launch_idft(g, w.XY, w.ldc, nprob, ep, st))) return rc;
-    if ((rc = reduce(g, RED_V, nprob, ep, tol, st))) return rc;
-    if (C > 0 && k % C == 0) {
-      if ((rc = heat_pipeline(g, v, nprob, 1, st))) return rc;
-      ep.mode = EPI_CHECK;
-      ep.other = u;
-      ep.marg = margP;
-      if ((rc = launch_idft(g, w.XY, w.ldc, nprob, ep, st))) return rc;
-      if ((rc = reduce(g, RED_CHECK, nprob, ep, tol, st))) return rc;
-      SHOT_CUDA(cudaMemcpyAsync(w.host_int, w.dev_int, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-      SHOT_CUDA(cudaStreamSynchronize(st));
-      if (w.host_int[1] == 0) break;
-    }
+    if ((rc = launch_idft(g, w.XY, w.ldc, s.nprob, ep, st))) return rc;
+    if ((rc = reduce(g, RED_V, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
   }
-  out.kdone = k > T ? T : k;
+  if (check) {
+    if ((rc = heat_pipeline(g, s.v, s.nprob, 1, st))) return rc;
+    ep.mode = EPI_CHECK;
+    ep.other = s.u;
+    ep.marg = margP;
+    if ((rc = launch_idft(g, w.XY, w.ldc, s.nprob, ep, st))) return rc;
+    if ((rc = reduce(g, RED_CHECK, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
+  }
+  return SHOT_OK;
+}
+
+int solve_final_enqueue(Solve& s) {
+  Grid& g = *s.g;
+  Workspace& w = g.ws;
+  EpiParams ep = base_ep(s);
+  int rc;
   // final K v_true for the objective, mass and marginal error; writes u_true, v_true
-  if ((rc = heat_pipeline(g, v, nprob, 1, st))) return rc;
+  if ((rc = heat_pipeline(g, s.v, s.nprob, 1, s.st))) return rc;
   ep.mode = EPI_FINAL;
-  ep.out = v;
-  ep.other = u;
-  ep.marg = margP;
-  ep.marg2 = margQ;
-  if ((rc = launch_idft(g, w.XY, w.ldc, nprob, ep, st))) return rc;
-  if ((rc = reduce(g, RED_FINAL, nprob, ep, tol, st))) return rc;
-  out.ps.resize(nprob);
-  SHOT_CUDA(cudaMemcpyAsync(w.host_probs, ps, nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, st));
-  SHOT_CUDA(cudaMemcpyAsync(w.host_int, w.dev_int, 8 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  SHOT_CUDA(cudaStreamSynchronize(st));
-  memcpy(out.ps.data(), w.host_probs, nprob * sizeof(ProbState));
+  ep.out = s.v;
+  ep.other = s.u;
+  ep.marg = w.marg;
+  ep.marg2 = w.marg + s.nprob;
+  if ((rc = launch_idft(g, w.XY, w.ldc, s.nprob, ep, s.st))) return rc;
+  if ((rc = reduce(g, RED_FINAL, s.nprob, s.eps, s.tol, s.norm_l1, s.st))) return rc;
+  ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
+  SHOT_CUDA(cudaMemcpyAsync(w.host_probs, ps, s.nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, s.st));
+  SHOT_CUDA(cudaMemcpyAsync(w.host_int, w.dev_int, 8 * sizeof(int), cudaMemcpyDeviceToHost, s.st));
+  return SHOT_OK;
+}
+
+int solve_collect(Solve& s, cudaStream_t user, SolveOut& out) {
+  Workspace& w = s.g->ws;
+  SHOT_CUDA(cudaStreamSynchronize(s.st));
+  // the caller's stream continues after the solve
+  SHOT_CUDA(cudaEventRecord(w.ev1, s.st));
+  SHOT_CUDA(cudaStreamWaitEvent(user, w.ev1, 0));
+  out.ps.resize(s.nprob);
+  memcpy(out.ps.data(), w.host_probs, s.nprob * sizeof(ProbState));
+  out.kdone = w.host_int[0];
   if (w.host_int[4] != 0) {
-    SHOT_CUDA(cudaMemsetAsync(w.dev_int + 4, 0, sizeof(int), st));
+    SHOT_CUDA(cudaMemsetAsync(w.dev_int + 4, 0, sizeof(int), s.st));
+    SHOT_CUDA(cudaStreamSynchronize(s.st));
     set_error("a bounded device-side wait expired in a tensor-core kernel");
     return SHOT_ERR_TIMEOUT;
   }
   for (auto& p : out.ps) {
     if (p.status == SHOT_OK && p.active) {
       p.iters = w.host_int[0];
-      if (tol > 0) p.status = SHOT_WARN_NOT_CONVERGED;
+      if (s.tol > 0) p.status = SHOT_WARN_NOT_CONVERGED;
     }
     if (p.status < 0) p.ot = p.ot_dual = p.mass = p.err = nan("");
   }
   return SHOT_OK;
+}
+
+// Blocks of B iterations (B = C when checking, else 10), each captured once into a CUDA
+// graph and replayed; the host polls the number of active problems after every checked
+// block.  Graphs are not used while per-launch profiling is on.
+struct Runner {
+  std::vector<Solve*> sets;
+  cudaStream_t main = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int block = 10;
+  ~Runner() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+};
+
+int enqueue_all(Runner& r, int nit, bool check) {
+  int rc;
+  if (r.sets.size() == 1) return solve_enqueue(*r.sets[0], nit, check, r.main);
+  // fork: every set on its own grid stream, joined back into the main stream
+  for (Solve* s : r.sets) {
+    Workspace& w = s->g->ws;
+    if (s->st == r.main) {
+      if ((rc = solve_enqueue(*s, nit, check, r.main))) return rc;
+      continue;
+    }
+    SHOT_CUDA(cudaEventRecord(w.ev0, r.main));
+    SHOT_CUDA(cudaStreamWaitEvent(w.stream, w.ev0, 0));
+    if ((rc = solve_enqueue(*s, nit, check, w.stream))) return rc;
+    SHOT_CUDA(cudaEventRecord(w.ev1, w.stream));
+    SHOT_CUDA(cudaStreamWaitEvent(r.main, w.ev1, 0));
+  }
+  return SHOT_OK;
+}
+
+int run_blocks(Runner& r, int T) {
+  const int C = r.sets[0]->C;
+  const int B = C > 0 ? C : 10;
+  const bool use_graph = !profiling_on() && T >= 2 * B;
+  int k = 0, rc;
+  long long per_block = 0;
+  // the main stream waits for every set's preparation
+  for (Solve* s : r.sets)
+    if (s->st != r.main) {
+      SHOT_CUDA(cudaEventRecord(s->g->ws.ev0, s->st));
+      SHOT_CUDA(cudaStreamWaitEvent(r.main, s->g->ws.ev0, 0));
+    }
+  while (k < T) {
+    const int nit = (T - k < B) ? T - k : B;
+    const bool check = C > 0 && nit == B;
+    if (use_graph && nit == B) {
+      if (!r.exec) {
+        cudaGraph_t graph = nullptr;
+        long long n0 = 0, n1 = 0;
+        shot_launch_count(&n0);
+        SHOT_CUDA(cudaStreamBeginCapture(r.main, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_all(r, nit, check);
+        cudaError_t e = cudaStreamEndCapture(r.main, &graph);
+        shot_launch_count(&n1);
+        per_block = n1 - n0;
+        count_launch((int)-per_block);   // captured, not launched
+        if (rc) {
+          if (graph) cudaGraphDestroy(graph);
+          return rc;
+        }
+        if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&r.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
+      }
+      count_launch((int)per_block);
+      SHOT_CUDA(cudaGraphLaunch(r.exec, r.main));
+    } else {
+      if ((rc = enqueue_all(r, nit, check))) return rc;
+    }
+    k += nit;
+    if (check) {
+      int active = 0;
+      for (Solve* s : r.sets) {
+        Workspace& w = s->g->ws;
+        SHOT_CUDA(cudaMemcpyAsync(w.host_int + 8, w.dev_int + 1, sizeof(int), cudaMemcpyDeviceToHost, r.main));
+      }
+      SHOT_CUDA(cudaStreamSynchronize(r.main));
+      for (Solve* s : r.sets) active += s->g->ws.host_int[8];
+      if (active == 0) break;
+    }
+  }
+  // every set's stream continues after the blocks
+  for (Solve* s : r.sets)
+    if (s->st != r.main) {
+      SHOT_CUDA(cudaEventRecord(s->g->ws.ev1, r.main));
+      SHOT_CUDA(cudaStreamWaitEvent(s->st, s->g->ws.ev1, 0));
+    }
+  return SHOT_OK;
+}
+
+// Alg. 1 on nprob problems of one grid with marginal lists P (first) and Q (second).
+int run_sinkhorn(Grid& g, const std::vector<const float*>& P, const std::vector<const float*>& Q, double eps,
+                 double tau, int T, double tol, int C, int flags, float* u, float* v, cudaStream_t st,
+                 SolveOut& out) {
+  std::vector<double> taus(P.size(), tau);
+  Solve s;
+  int rc = solve_prepare(g, P, Q, taus, eps, tol, C, flags, u, v, st, s);
+  if (rc) return rc;
+  Runner r;
+  r.sets.push_back(&s);
+  r.main = s.st;
+  if ((rc = run_blocks(r, T))) return rc;
+  if ((rc = solve_final_enqueue(s))) return rc;
+  return solve_collect(s, st, out);
 }
 
 int worst_status(const std::vector<ProbState>& ps) {
@@ -309,6 +482,21 @@ int worst_status(const std::vector<ProbState>& ps) {
 bool finite_pos(double x) { return x > 0.0 && isfinite(x); }
 
 }  // namespace
+
+int run_sinkhorn_public(Grid& g, const std::vector<const float*>& P, const std::vector<const float*>& Q, double eps,
+                        double tau, int T, double tol, int C, int flags, float* u, float* v, cudaStream_t st,
+                        std::vector<ProbState>& out, int* kdone) {
+  SolveOut so;
+  int rc = run_sinkhorn(g, P, Q, eps, tau, T, tol, C, flags, u, v, st, so);
+  if (rc) return rc;
+  out = so.ps;
+  if (kdone) *kdone = so.kdone;
+  return SHOT_OK;
+}
+
+int divergence_grad(Grid& g, const float* p, const float* q, int batch, double eps, double tau, int T, int ck,
+                    int mode, double* S, float* grad, int* status, cudaStream_t st);
+
 }  // namespace shot
 
 using namespace shot;
@@ -365,6 +553,10 @@ int shot_grid_free(shot_grid gh) {
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};
   for (void* p : dptr)
     if (p) cudaFree(p);
+  if (g->ws.taus) cudaFree(g->ws.taus);
+  if (g->ws.stream) cudaStreamDestroy(g->ws.stream);
+  if (g->ws.ev0) cudaEventDestroy(g->ws.ev0);
+  if (g->ws.ev1) cudaEventDestroy(g->ws.ev1);
   if (g->ws.host_int) cudaFreeHost(g->ws.host_int);
   if (g->ws.host_probs) cudaFreeHost(g->ws.host_probs);
   delete g;
@@ -547,6 +739,133 @@ int shot_divergence(shot_grid gh, const float* p, const float* q, int batch, dou
     if (iters3) iters3[i] = so.ps[i].iters;
   }
   return worst_status(so.ps);
+}
+
+int shot_divergence_multi(const shot_pair_set* sets, int nsets, int max_iter, double tol, int check_every,
+                          int flags, void* stream) {
+  if (!sets || nsets < 1 || max_iter < 0 || check_every < 0) {
+    set_error("shot_divergence_multi: bad argument");
+    return SHOT_ERR_INVALID_ARG;
+  }
+  cudaStream_t user = as_stream(stream);
+  // group the sets by grid: one solve per grid with per-problem tau
+  std::vector<Grid*> grids;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < nsets; ++i) {
+    const shot_pair_set& S = sets[i];
+    Grid* g = as_grid(S.grid);
+    int rc = check_solver_args(g, S.p, S.q, S.batch, S.eps, S.tau, max_iter, check_every);
+    if (rc) return rc;
+    if (!S.S || !S.status) { set_error("shot_divergence_multi: S and status are required"); return SHOT_ERR_INVALID_ARG; }
+    size_t k = 0;
+    while (k < grids.size() && grids[k] != g) ++k;
+    if (k == grids.size()) {
+      grids.push_back(g);
+      members.emplace_back();
+    }
+    if (!members[k].empty() && sets[members[k][0]].eps != S.eps) {
+      set_error("shot_divergence_multi: sets sharing a grid must share eps");
+      return SHOT_ERR_INVALID_ARG;
+    }
+    members[k].push_back(i);
+  }
+  const size_t G = grids.size();
+  std::vector<Solve> solves(G);
+  std::vector<std::vector<double>> masses(G);
+  int rc;
+  for (size_t k = 0; k < G; ++k) {
+    Grid& g = *grids[k];
+    const size_t n = (size_t)g.nlat * g.nlon;
+    std::vector<const float*> P, Q, fl;
+    std::vector<double> taus;
+    for (int i : members[k]) {
+      const shot_pair_set& S = sets[i];
+      for (int part = 0; part < 3; ++part)
+        for (int b = 0; b < S.batch; ++b) {
+          const float* pb = S.p + b * n;
+          const float* qb = S.q + b * n;
+          P.push_back(part == 2 ? qb : pb);
+          Q.push_back(part == 0 ? qb : (part == 1 ? pb : qb));
+          taus.push_back(S.tau);
+        }
+      for (int b = 0; b < S.batch; ++b) fl.push_back(S.p + b * n);
+      for (int b = 0; b < S.batch; ++b) fl.push_back(S.q + b * n);
+    }
+    const int np = (int)P.size();
+    if ((rc = ensure_workspace(g, np, user))) return rc;
+    Workspace& w = g.ws;
+    if (w.uv_cap < (size_t)np * n) {
+      SHOT_CUDA(cudaStreamSynchronize(user));
+      cudaFree(w.ubuf);
+      cudaFree(w.vbuf);
+      w.ubuf = w.vbuf = nullptr;
+      w.uv_cap = 0;
+      SHOT_CUDA(cudaMalloc(&w.ubuf, (size_t)np * n * sizeof(float)));
+      SHOT_CUDA(cudaMalloc(&w.vbuf, (size_t)np * n * sizeof(float)));
+      w.uv_cap = (size_t)np * n;
+    }
+    // masses of every field of the grid (FP64), before the solve uses the partial buffer
+    const int nfl = (int)fl.size();
+    const float** fl_d = w.marg + 2 * np;
+    if (nfl > 2 * np) { set_error("internal: mass list too long"); return SHOT_ERR_INVALID_ARG; }
+    SHOT_CUDA(cudaMemcpyAsync(fl_d, fl.data(), nfl * sizeof(float*), cudaMemcpyHostToDevice, user));
+    count_launch();
+    k_field_mass<<<nfl, 256, 0, user>>>(fl_d, g.nlat, g.nlon, g.a_d, w.part);
+    SHOT_CUDA(cudaGetLastError());
+    masses[k].resize(nfl);
+    SHOT_CUDA(cudaMemcpyAsync(masses[k].data(), w.part, nfl * sizeof(double), cudaMemcpyDeviceToHost, user));
+    SHOT_CUDA(cudaStreamSynchronize(user));
+    if ((rc = solve_prepare(g, P, Q, taus, sets[members[k][0]].eps, tol, check_every, flags, w.ubuf, w.vbuf, user,
+                            solves[k])))
+      return rc;
+  }
+  Runner r;
+  for (auto& s : solves) r.sets.push_back(&s);
+  r.main = solves[0].st;
+  if ((rc = run_blocks(r, max_iter))) return rc;
+  int worst = SHOT_OK;
+  for (size_t k = 0; k < G; ++k)
+    if ((rc = solve_final_enqueue(solves[k]))) return rc;
+  for (size_t k = 0; k < G; ++k) {
+    SolveOut so;
+    if ((rc = solve_collect(solves[k], user, so))) return rc;
+    size_t off = 0, moff = 0;
+    for (int i : members[k]) {
+      const shot_pair_set& S = sets[i];
+      const int B = S.batch;
+      for (int b = 0; b < B; ++b) {
+        const ProbState &a = so.ps[off + b], &pp = so.ps[off + B + b], &qq = so.ps[off + 2 * B + b];
+        const double dm = masses[k][moff + b] - masses[k][moff + B + b];
+        S.S[b] = a.ot - 0.5 * (pp.ot + qq.ot) + 0.5 * S.eps * dm * dm;
+        if (S.S_dual) S.S_dual[b] = a.ot_dual - 0.5 * (pp.ot_dual + qq.ot_dual);
+        int ws = SHOT_OK;
+        for (int st3 : {a.status, pp.status, qq.status}) {
+          if (st3 < 0 && (ws >= 0 || st3 < ws)) ws = st3;
+          else if (ws >= 0 && st3 > ws) ws = st3;
+        }
+        S.status[b] = ws;
+        if (ws < 0 && (worst >= 0 || ws < worst)) worst = ws;
+        else if (worst >= 0 && ws > worst) worst = ws;
+      }
+      off += 3 * (size_t)B;
+      moff += 2 * (size_t)B;
+    }
+  }
+  return worst;
+}
+
+int shot_divergence_grad(shot_grid gh, const float* p, const float* q, int batch, double eps, double tau,
+                         int max_iter, int checkpoint_every, int mode, double* S, float* grad_p, int* status,
+                         void* stream) {
+  Grid* g = as_grid(gh);
+  int rc = check_solver_args(g, p, q, batch, eps, tau, max_iter, 0);
+  if (rc) return rc;
+  if (!S || !grad_p || !status || (mode != SHOT_GRAD_UNROLLED && mode != SHOT_GRAD_ENVELOPE)) {
+    set_error("shot_divergence_grad: S, grad_p, status required; mode UNROLLED or ENVELOPE");
+    return SHOT_ERR_INVALID_ARG;
+  }
+  return divergence_grad(*g, p, q, batch, eps, tau, max_iter, checkpoint_every, mode, S, grad_p, status,
+                         as_stream(stream));
 }
 
 }  // extern "C"

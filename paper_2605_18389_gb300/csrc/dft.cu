@@ -155,6 +155,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
     if (ep.mode == EPI_UPDATE) {
       if (!P->active) continue;
       const float* mg = ep.marg[f];
+      const int bal = P->balanced;
+      const float gam = P->gamma, et = P->et;
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
         const int r = idx >= N ? 1 : 0, k = idx - r * N;
         const float2 zz = z[q * N + k];
@@ -163,13 +165,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
         const float pm = __ldg(mg + om);
         const float ratio = pm / kv;
         float u;
-        if (ep.balanced) {
+        if (bal) {
           u = ratio;
           acc[q][0] += u;
         } else {
           // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}
-          u = powf(ratio, ep.gamma);
-          if (pm > 0.f) acc[q][0] += aj * pm * powf(ratio, -ep.eps_over_taueps);
+          u = powf(ratio, gam);
+          if (pm > 0.f) acc[q][0] += aj * pm * powf(ratio, -et);
         }
         if (!(kv > 0.f)) {
           if (kv <= 0.f) acc[q][2] += 1.f;
@@ -202,7 +204,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       const float* pp = ep.marg[f];
       const float* qq = ep.marg2[f];
       const float al = (float)P->alpha, be = (float)P->beta;
-      const float epsf = (float)ep.eps, tauf = (float)ep.tau, et = (float)(ep.eps / ep.tau);
+      const int bal = P->balanced;
+      const float epsf = (float)ep.eps, tauf = (float)P->tau, et = bal ? 0.f : (float)(ep.eps / P->tau);
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
         const int r = idx >= N ? 1 : 0, k = idx - r * N;
         const float2 zz = z[q * N + k];
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
         // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
         const float lu = logf(uu), lv = logf(vv);
         float t;
-        if (ep.balanced) {
+        if (bal) {
           t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);
         } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u)
           t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +

@@ -307,6 +307,8 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   cudaFree(w.marg);
   cudaFree(w.ct_hi);
   cudaFree(w.ct_lo);
+  cudaFree(w.taus);
+  w.taus = nullptr;
   w.ct_hi = w.ct_lo = nullptr;
   w.nmma_cap = 0;
   if (w.host_probs) cudaFreeHost(w.host_probs);
@@ -324,6 +326,7 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   SHOT_CUDA(cudaMalloc(&w.part, (size_t)nf * g.nh * NPART * sizeof(double)));
   SHOT_CUDA(cudaMalloc(&w.probs, (size_t)nf * sizeof(ProbState)));
   SHOT_CUDA(cudaMalloc(&w.marg, (size_t)4 * nf * sizeof(float*)));
+  SHOT_CUDA(cudaMalloc(&w.taus, (size_t)nf * sizeof(double)));
   SHOT_CUDA(cudaMallocHost(&w.host_probs, (size_t)nf * sizeof(ProbState)));
   // X and C are never read before written except padding columns; keep them finite
   SHOT_CUDA(cudaMemsetAsync(w.XY, 0, xy * sizeof(float), st));

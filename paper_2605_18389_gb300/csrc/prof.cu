@@ -36,6 +36,8 @@ cudaEvent_t take_event() {
 
 void count_launch(int n) { g_launches += n; }
 
+bool profiling_on() { return g_on.load() != 0; }
+
 ProfScope::ProfScope(int kind, cudaStream_t st) : kind_(kind), st_(st) {
   if (!g_on.load()) return;
   std::lock_guard<std::mutex> lk(g_mu);

@@ -76,6 +76,9 @@ struct Workspace {
   int* host_int = nullptr;  // pinned mirror
   void* host_probs = nullptr;  // pinned ProbState mirror
   size_t host_probs_cap = 0;
+  double* taus = nullptr;      // per-problem tau (device) [nf]
+  cudaStream_t stream = nullptr;   // internal solver stream (capturable)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 struct Grid {
@@ -120,10 +123,13 @@ struct ProbState {
   double su;        // pending reduction of the u-step (sum u or sum a p u^{-eps/tau})
   double err;       // last marginal error
   double ot, ot_dual, mass;
+  double tau;       // marginal penalty of this problem (INFINITY: balanced)
+  float gamma;      // tau/(tau+eps), 1 when balanced
+  float et;         // eps/(tau+eps), 0 when balanced
+  int balanced;
   int active;
   int status;
   int iters;
-  int pad;
 };
 
 // Epilogue modes of the inverse DFT kernel
@@ -136,15 +142,13 @@ struct EpiParams {
   const float* const* marg;   // per-field marginal pointers (p or q)
   const float* const* marg2;  // EPI_FINAL: the other marginal
   float* other;               // EPI_CHECK/FINAL: the other scaling buffer (v for the u-side)
-  ProbState* ps;
+  ProbState* ps;              // per-problem state incl. tau-derived constants
   double* part;               // [nf][nh][NPART]
-  int balanced;
-  float gamma;                // tau/(tau+eps)
-  float eps_over_taueps;      // eps/(tau+eps)
-  double eps, tau;
+  double eps;
   int norm_l1;
   int which;                  // 0: u-step (marginal p), 1: v-step (marginal q)
 };
+bool profiling_on();
 
 // ---------------------------------------------------------------------------------
 // Launchers (return SHOT status)

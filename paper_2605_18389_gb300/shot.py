@@ -25,6 +25,8 @@ SHOT_ERR_TIMEOUT = -7
 SHOT_FP32 = 0
 SHOT_BF16X3 = 1
 SHOT_TABLE = 0
+SHOT_GRAD_UNROLLED = 0
+SHOT_GRAD_ENVELOPE = 1
 SHOT_FLAG_NORM_L1 = 0x1
 SHOT_FLAG_WARM_START = 0x2
 
@@ -53,6 +55,8 @@ SIGNATURES = {
     "shot_divergence": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                         ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_int_p, _vp, _vp,
                         _c_dbl_p, _c_int_p, _vp],
+    "shot_divergence_grad": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                             ctypes.c_int, ctypes.c_int, _c_dbl_p, _vp, _c_int_p, _vp],
     "shot_heat_apply_noalloc": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
     "shot_launch_count": [ctypes.POINTER(ctypes.c_longlong)],
     "shot_profile_enable": [ctypes.c_int],
@@ -60,6 +64,17 @@ SIGNATURES = {
 }
 
 PROFILE_KINDS = ("ring_dft", "legendre_analysis", "legendre_synthesis", "inverse_dft_epilogue", "other")
+
+
+
+class ShotPairSet(ctypes.Structure):
+    """struct shot_pair_set of include/shot.h."""
+    _fields_ = [("grid", _vp), ("p", _vp), ("q", _vp), ("batch", ctypes.c_int), ("eps", ctypes.c_double),
+                ("tau", ctypes.c_double), ("S", _c_dbl_p), ("S_dual", _c_dbl_p), ("status", _c_int_p)]
+
+
+SIGNATURES["shot_divergence_multi"] = [ctypes.POINTER(ShotPairSet), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, _vp]
 
 _lib = None
 
@@ -242,3 +257,62 @@ def shot_profile_read():
     _check(lib().shot_profile_read(_np_ptr(ms, ctypes.c_double), n.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
                                    k))
     return {name: (float(ms[i]), int(n[i])) for i, name in enumerate(PROFILE_KINDS)}
+
+
+def shot_divergence_grad(g, p, q, eps, tau=math.inf, max_iter=400, checkpoint_every=20, mode=SHOT_GRAD_UNROLLED,
+                         grad=None, stream=None):
+    """Returns (status_code, dict with S, status, grad) where grad = dS/dp (device tensor)."""
+    import torch
+    B = p.shape[0]
+    if grad is None:
+        grad = torch.empty_like(p)
+    S = np.empty(B)
+    status = np.empty(B, np.int32)
+    rc = _solver_rc(lib().shot_divergence_grad(
+        g, _dev_ptr(p, "p"), _dev_ptr(q, "q", p.shape), B, float(eps), float(tau), int(max_iter),
+        int(checkpoint_every), int(mode), _np_ptr(S, ctypes.c_double), _dev_ptr(grad, "grad", p.shape),
+        _np_ptr(status, ctypes.c_int), _stream(stream)))
+    return rc, dict(S=S, status=status, grad=grad)
+
+
+def divergence(g, p, q, eps, tau=math.inf, max_iter=400, checkpoint_every=20, mode=SHOT_GRAD_UNROLLED):
+    """S(p, q) as a differentiable torch function of p (batch of pairs; returns a [batch] tensor).
+
+    The forward runs shot_divergence_grad when p requires a gradient (shot_divergence
+    otherwise); backward scales the stored dS/dp by the incoming gradient.
+    """
+    import torch
+
+    class _Div(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, pp):
+            if pp.requires_grad:
+                rc, r = shot_divergence_grad(g, pp.detach().contiguous(), q, eps, tau, max_iter, checkpoint_every,
+                                             mode)
+                ctx.save_for_backward(r["grad"])
+            else:
+                rc, r = shot_divergence(g, pp.detach().contiguous(), q, eps, tau, max_iter, 0.0, 0)
+            return torch.as_tensor(r["S"], dtype=torch.float64, device=pp.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            (gp,) = ctx.saved_tensors
+            return gp * gout.to(gp.dtype).view(-1, *([1] * (gp.dim() - 1)))
+
+    return _Div.apply(p)
+
+
+def shot_divergence_multi(sets, max_iter=200, tol=0.0, check_every=10, flags=0, stream=None):
+    """sets: list of dicts {grid, p, q, eps, tau}.  Returns (status_code, list of dicts S, S_dual, status)."""
+    arr = (ShotPairSet * len(sets))()
+    outs = []
+    for i, st in enumerate(sets):
+        B = st["p"].shape[0]
+        o = dict(S=np.empty(B), S_dual=np.empty(B), status=np.empty(B, np.int32))
+        outs.append(o)
+        arr[i] = ShotPairSet(st["grid"], _dev_ptr(st["p"], "p"), _dev_ptr(st["q"], "q", st["p"].shape), B,
+                             float(st["eps"]), float(st.get("tau", math.inf)), _np_ptr(o["S"], ctypes.c_double),
+                             _np_ptr(o["S_dual"], ctypes.c_double), _np_ptr(o["status"], ctypes.c_int))
+    rc = _solver_rc(lib().shot_divergence_multi(arr, len(sets), int(max_iter), float(tol), int(check_every),
+                                                int(flags), _stream(stream)))
+    return rc, outs

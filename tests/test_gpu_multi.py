@@ -1,0 +1,73 @@
+"""Batched uneven grids in one solve (shot_divergence_multi) and graph-replayed blocks.
+
+Each set's result must equal the oracle's divergence of that set alone (per-problem tau on
+a shared grid), and the multi-grid solve must equal the single-grid calls.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.grid import Grid as OGrid
+from oracle import sinkhorn as sk
+from paper_2605_18389_gb300 import inputs
+from tests.gpu_util import f32, s_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+from paper_2605_18389_gb300 import shot  # noqa: E402
+
+TOL_S = 1e-5
+
+
+def _set(og, seed, npairs, masses):
+    p, q = inputs.pairs("paper_uniform", seed, npairs, og.x, og.nlon, og.a_ring, masses=masses)
+    p32, p64 = f32(p)
+    q32, q64 = f32(q)
+    return torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), p64, q64
+
+
+def test_multi_grid_sets_match_oracle_and_single_calls():
+    eps, T = 0.02, 40
+    specs = [(16, 1.0), (16, math.inf), (24, 0.1), (32, 10.0)]   # grid nlat, tau
+    grids = {n: (shot.shot_grid_init(n), OGrid(n)) for n in (16, 24, 32)}
+    try:
+        sets, refs, singles = [], [], []
+        for i, (n, tau) in enumerate(specs):
+            g, og = grids[n]
+            pt, qt, p64, q64 = _set(og, 900 + i, 2, not math.isinf(tau))
+            sets.append(dict(grid=g, p=pt, q=qt, eps=eps, tau=tau))
+            refs.append(sk.divergence(og, p64, q64, eps, tau, T=T, delta=0.0, C=10))
+        rc, outs = shot.shot_divergence_multi(sets, max_iter=T, tol=0.0, check_every=10)
+        assert rc >= 0
+        for st, o, ref in zip(sets, outs, refs):
+            assert np.all(o["status"] == 0)
+            ot_pq = ref["runs"]["ot"][: len(o["S"])]
+            assert np.all(s_err(o["S"], ref["S"], ot_pq, TOL_S) <= 1.0), (o["S"], ref["S"])
+            assert np.all(s_err(o["S_dual"], ref["S_dual"], ot_pq, TOL_S) <= 1.0)
+            rc1, r1 = shot.shot_divergence(st["grid"], st["p"], st["q"], eps, st["tau"], max_iter=T, tol=0.0,
+                                           check_every=10)
+            singles.append(r1)
+            np.testing.assert_allclose(o["S"], r1["S"], rtol=1e-6, atol=1e-9)
+    finally:
+        for g, _ in grids.values():
+            shot.shot_grid_free(g)
+
+
+def test_graph_replay_equals_profiled_eager_launches():
+    # blocks are captured into a CUDA graph unless per-launch profiling is on: same numbers
+    og = OGrid(24)
+    g = shot.shot_grid_init(24)
+    try:
+        pt, qt, _, _ = _set(og, 5, 3, False)
+        rc, r_graph = shot.shot_divergence(g, pt, qt, 0.05, max_iter=60, tol=0.0, check_every=10)
+        shot.shot_profile_enable(True)
+        try:
+            rc, r_eager = shot.shot_divergence(g, pt, qt, 0.05, max_iter=60, tol=0.0, check_every=10)
+        finally:
+            shot.shot_profile_enable(False)
+            shot.shot_profile_read()
+        np.testing.assert_array_equal(r_graph["S"], r_eager["S"])
+    finally:
+        shot.shot_grid_free(g)
