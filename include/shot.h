@@ -51,6 +51,9 @@ extern "C" {
 
 /* ---- source of the associated Legendre values ---------------------------- */
 #define SHOT_TABLE       0   /* precomputed parity-folded table, O(nlat^3) memory */
+#define SHOT_RECURRENCE  1   /* values regenerated on the fly by the normalised three-term
+                                recurrence from per-(m, node) seeds: O(nlat^2) memory
+                                (SHOT_FP32 grids) */
 
 /* ---- solver flags -------------------------------------------------------- */
 #define SHOT_FLAG_NORM_L1     0x1  /* check sum_i a_i|u_i(Kv)_i - p_i| / sum_i a_i p_i instead of the relative L2 */
@@ -68,7 +71,7 @@ int shot_last_error(char* buf, int len);
  *   out        receives the handle (host pointer)
  *   nlat >= 2; nlon >= 2*lmax+1 with prime factors in {2,3,5}; lmax = -1 means nlat-1,
  *              else 0 <= lmax <= nlat-1
- *   precision  SHOT_FP32 or SHOT_BF16X3; legendre_mode SHOT_TABLE
+ *   precision  SHOT_FP32 or SHOT_BF16X3; legendre_mode SHOT_TABLE or SHOT_RECURRENCE (FP32)
  * Memory: about 2*(lmax+1)(lmax+2)/2 * ceil(nlat/2) * 4 bytes of table (0.37 GB at 720).
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Synchronises `stream`. */
 int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision,
@@ -207,6 +210,14 @@ int shot_divergence_grad(shot_grid g, const float* p, const float* q, int batch,
  *   be serialised by the caller.  Asynchronous on `stream`. */
 #define SHOT_NOALLOC_SCRATCH_BYTES (8u << 20)
 int shot_heat_apply_noalloc(shot_grid g, double t, const float* in, float* out, int nfields, void* stream);
+
+/* Autotune the launch shapes used for calls on `nfields` fields (fields per ring-DFT and
+ * inverse-DFT CTA, FP32 Legendre tile width, BF16x3 analysis pipeline depth) by timing the
+ * candidates with CUDA events; the solvers do this automatically on their first call for
+ * a field count.  choice: host int[4] or NULL, receives the four selections (0 = the
+ * default).  The choices change no summation order (results are bit-identical).
+ * Allocates one temporary field batch.  Synchronises `stream`. */
+int shot_grid_autotune(shot_grid g, int nfields, int* choice, void* stream);
 
 /* ---- measurement helpers (no counterpart in the paper) -------------------
  * shot_launch_count: total number of CUDA kernels this library has launched in the

@@ -35,15 +35,19 @@ int launch_analysis_simt(const Grid& g, int nf, const float* X, float* C, int ld
 int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st);
 
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st) {
+  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st);
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st);
   return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st) {
+  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
   if (g.precision == SHOT_FP32) return launch_analysis_simt(g, nf, X, C, ldc, apply_h, st);
   return launch_legendre_tc(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
 }
 int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st) {
+  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, nullptr, const_cast<float*>(C), Y, ldc, false, true,
+                                                            false, st);
   if (g.precision == SHOT_FP32) return launch_synthesis_simt(g, nf, C, Y, ldc, st);
   int rc = launch_c_to_ct(g, nf, C, ldc, st);
   if (rc) return rc;
@@ -163,25 +167,41 @@ __global__ void k_fill(float* __restrict__ a, size_t n, float v) {
     a[i] = v;
 }
 
-// mass m(p) = sum_i a_i p_i of every listed field (FP64), one block per field
-__global__ void k_field_mass(const float* const* __restrict__ fl, int nlat, int nlon,
-                             const float* __restrict__ a_ring, double* __restrict__ out) {
-  __shared__ double red[32];
-  const float* f = fl[blockIdx.x];
-  double s = 0.0;
-  for (int j = 0; j < nlat; ++j) {
-    float t = 0.f;
-    for (int k = threadIdx.x; k < nlon; k += blockDim.x) t += f[(size_t)j * nlon + k];
-    s += (double)a_ring[j] * (double)t;
-  }
-  s = wsum(s);
+// mass m(p) = sum_i a_i p_i of every listed field (FP64): per-ring partial sums by a
+// (ring, field) grid, then a fixed-order sum per field
+__global__ void k_field_mass_part(const float* const* __restrict__ fl, int nlat, int nlon,
+                                  const float* __restrict__ a_ring, double* __restrict__ part) {
+  __shared__ float red[32];
+  const int j = blockIdx.x, f = blockIdx.y;
+  const float* row = fl[f] + (size_t)j * nlon;
+  float s = 0.f;
+  for (int k = threadIdx.x; k < nlon; k += blockDim.x) s += row[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
+    float t = 0.f;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    out[blockIdx.x] = t;
+    part[(size_t)f * nlat + j] = (double)a_ring[j] * (double)t;
   }
+}
+
+__global__ void k_field_mass_sum(int nfl, int nlat, const double* __restrict__ part, double* __restrict__ out) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nfl) return;
+  double s = 0.0;
+  for (int j = 0; j < nlat; ++j) s += part[(size_t)f * nlat + j];
+  out[f] = s;
+}
+
+// masses of nfl listed fields into out (device); part needs nfl*nlat doubles
+int field_masses(const Grid& g, const float* const* fl_d, int nfl, double* part, double* out, cudaStream_t st) {
+  count_launch(2);
+  k_field_mass_part<<<dim3(g.nlat, nfl), 256, 0, st>>>(fl_d, g.nlat, g.nlon, g.a_d, part);
+  k_field_mass_sum<<<(nfl + 127) / 128, 128, 0, st>>>(nfl, g.nlat, part, out);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
 }
 
 cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
@@ -267,6 +287,7 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
     k_fill<<<1024, 256, 0, s.st>>>(v, n * nprob, 1.f);
   }
   SHOT_CUDA(cudaGetLastError());
+  if ((rc = autotune(g, nprob, s.st))) return rc;
   return launch_heat_mult(g, eps / 4.0, s.st);
 }
 
@@ -523,7 +544,14 @@ int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision, 
     return SHOT_ERR_INVALID_ARG;
   }
   if (precision != SHOT_FP32 && precision != SHOT_BF16X3) { set_error("unknown precision"); return SHOT_ERR_INVALID_ARG; }
-  if (legendre_mode != SHOT_TABLE) { set_error("unknown legendre_mode"); return SHOT_ERR_INVALID_ARG; }
+  if (legendre_mode != SHOT_TABLE && legendre_mode != SHOT_RECURRENCE) {
+    set_error("unknown legendre_mode");
+    return SHOT_ERR_INVALID_ARG;
+  }
+  if (legendre_mode == SHOT_RECURRENCE && precision != SHOT_FP32) {
+    set_error("SHOT_RECURRENCE is built for SHOT_FP32 grids");
+    return SHOT_ERR_UNSUPPORTED;
+  }
   FftPlan plan;
   if (!make_fft_plan(nlon, &plan)) { set_error("nlon must factor into 2, 3 and 5"); return SHOT_ERR_UNSUPPORTED; }
   Grid* g = new Grid;
@@ -535,6 +563,7 @@ int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision, 
   g->mode = legendre_mode;
   g->plan = plan;
   cudaGetDevice(&g->dev);
+  cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->dev);
   int rc = build_grid_tables(*g, as_stream(stream));
   if (rc) {
     shot_grid_free(reinterpret_cast<shot_grid>(g));
@@ -548,7 +577,7 @@ int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
   void* dptr[] = {g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi, g->tabT_lo,
-                  g->ws.ct_hi, g->ws.ct_lo, g->M_d,
+                  g->ws.ct_hi, g->ws.ct_lo, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};
   for (void* p : dptr)
@@ -711,9 +740,7 @@ int shot_divergence(shot_grid gh, const float* p, const float* q, int batch, dou
   const float** fl_d = w.marg + 2 * np;   // spare room in the pointer area
   double* mass_d = w.part;                  // part is free before the solve
   SHOT_CUDA(cudaMemcpyAsync(fl_d, fl.data(), 2 * batch * sizeof(float*), cudaMemcpyHostToDevice, st));
-  count_launch();
-  k_field_mass<<<2 * batch, 256, 0, st>>>(fl_d, g->nlat, g->nlon, g->a_d, mass_d);
-  SHOT_CUDA(cudaGetLastError());
+  if ((rc = field_masses(*g, fl_d, 2 * batch, w.part + 2 * batch, mass_d, st))) return rc;
   std::vector<double> masses(2 * batch);
   SHOT_CUDA(cudaMemcpyAsync(masses.data(), mass_d, 2 * batch * sizeof(double), cudaMemcpyDeviceToHost, st));
   SHOT_CUDA(cudaStreamSynchronize(st));
@@ -809,9 +836,7 @@ int shot_divergence_multi(const shot_pair_set* sets, int nsets, int max_iter, do
     const float** fl_d = w.marg + 2 * np;
     if (nfl > 2 * np) { set_error("internal: mass list too long"); return SHOT_ERR_INVALID_ARG; }
     SHOT_CUDA(cudaMemcpyAsync(fl_d, fl.data(), nfl * sizeof(float*), cudaMemcpyHostToDevice, user));
-    count_launch();
-    k_field_mass<<<nfl, 256, 0, user>>>(fl_d, g.nlat, g.nlon, g.a_d, w.part);
-    SHOT_CUDA(cudaGetLastError());
+    if ((rc = field_masses(g, fl_d, nfl, w.part + nfl, w.part, user))) return rc;
     masses[k].resize(nfl);
     SHOT_CUDA(cudaMemcpyAsync(masses[k].data(), w.part, nfl * sizeof(double), cudaMemcpyDeviceToHost, user));
     SHOT_CUDA(cudaStreamSynchronize(user));

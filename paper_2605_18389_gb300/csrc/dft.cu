@@ -39,8 +39,8 @@ __device__ __forceinline__ void load_ring_pairs(const float* __restrict__ in, fl
     const float* fj = in + (size_t)(f0 + q) * nlat * nlon + (size_t)j * nlon;
     const float* fJ = in + (size_t)(f0 + q) * nlat * nlon + (size_t)J * nlon;
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
-      bf[2 * (q * N + k)] = __ldg(fj + k);
-      bf[2 * (q * N + k) + 1] = (J != j) ? __ldg(fJ + k) : 0.f;
+      bf[2 * pidx(q * N + k)] = __ldg(fj + k);
+      bf[2 * pidx(q * N + k) + 1] = (J != j) ? __ldg(fJ + k) : 0.f;
     }
   }
 }
@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_dft_fwd(
   const int N = nlon;
   float2* tw = sm;
   float2* b0 = sm + N;
-  float2* b1 = b0 + FG * N;
-  const int jh = blockIdx.x;
-  const int f0 = blockIdx.y * FG;
+  float2* b1 = b0 + padded_len(FG * N);
+  const int jh = blockIdx.y;
+  const int f0 = blockIdx.x * FG;
   const int nfg = min(FG, nf - f0);
   const int j = jh, J = nlat - 1 - jh;
 
@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_dft_fwd(
     const int f = f0 + q;
     float sc = aj;
     if (scale_which == 1) sc *= (float)ps[f].beta;
-    const float2 zm = buf[q * N + m];
-    const float2 zn = buf[q * N + (m ? N - m : 0)];
+    const float2 zm = buf[pidx(q * N + m)];
+    const float2 zn = buf[pidx(q * N + (m ? N - m : 0))];
     const float2 FN = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
     const float2 FS = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
     const float2 S = make_float2(sc * (FN.x + FS.x), sc * (FN.y + FS.y));
@@ -93,9 +93,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
   const int N = nlon;
   float2* tw = sm;
   float2* buf = sm + N;
-  float2* b1 = buf + FG * N;
-  const int jh = blockIdx.x;
-  const int f0 = blockIdx.y * FG;
+  float2* b1 = buf + padded_len(FG * N);
+  const int jh = blockIdx.y;
+  const int f0 = blockIdx.x * FG;
   const int nfg = min(FG, nf - f0);
   const int j = jh, J = nlat - 1 - jh;
 
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
   // zero the band lmax < m < N - lmax
   const int nz = N - 2 * lmax - 1;
   for (int q = 0; q < nfg; ++q)
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) buf[q * N + lmax + 1 + k] = make_float2(0.f, 0.f);
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) buf[pidx(q * N + lmax + 1 + k)] = make_float2(0.f, 0.f);
   const int nm = lmax + 1;
   for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
@@ -115,10 +115,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
     const float2 GN = make_float2(E.x + O.x, E.y + O.y);
     const float2 GS = make_float2(E.x - O.x, E.y - O.y);
     if (m == 0) {
-      buf[q * N] = make_float2(GN.x, GS.x);
+      buf[pidx(q * N)] = make_float2(GN.x, GS.x);
     } else {
-      buf[q * N + m] = make_float2(GN.x - GS.y, GN.y + GS.x);
-      buf[q * N + N - m] = make_float2(GN.x + GS.y, GS.x - GN.y);
+      buf[pidx(q * N + m)] = make_float2(GN.x - GS.y, GN.y + GS.x);
+      buf[pidx(q * N + N - m)] = make_float2(GN.x + GS.y, GS.x - GN.y);
     }
   }
   __syncthreads();
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       float* oj = ep.out + (size_t)(f0 + q) * nlat * nlon + (size_t)j * nlon;
       float* oJ = ep.out + (size_t)(f0 + q) * nlat * nlon + (size_t)J * nlon;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const float2 zz = z[q * N + k];
+        const float2 zz = z[pidx(q * N + k)];
         oj[k] = zz.x;
         if (J != j) oJ[k] = zz.y;
       }
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       const float gam = P->gamma, et = P->et;
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
         const int r = idx >= N ? 1 : 0, k = idx - r * N;
-        const float2 zz = z[q * N + k];
+        const float2 zz = z[pidx(q * N + k)];
         const float kv = r ? zz.y : zz.x;
         const size_t om = (size_t)(r ? J : j) * nlon + k;
         const float pm = __ldg(mg + om);
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       const float al = (float)P->alpha;
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
         const int r = idx >= N ? 1 : 0, k = idx - r * N;
-        const float2 zz = z[q * N + k];
+        const float2 zz = z[pidx(q * N + k)];
         const float kv = r ? zz.y : zz.x;
         const size_t om = (size_t)(r ? J : j) * nlon + k;
         const float pm = __ldg(mg + om);
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       const float epsf = (float)ep.eps, tauf = (float)P->tau, et = bal ? 0.f : (float)(ep.eps / P->tau);
       for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
         const int r = idx >= N ? 1 : 0, k = idx - r * N;
-        const float2 zz = z[q * N + k];
+        const float2 zz = z[pidx(q * N + k)];
         const float kv = r ? zz.y : zz.x;
         const size_t om = (size_t)(r ? J : j) * nlon + k;
         const size_t o = fbase + om;
@@ -273,9 +273,9 @@ int pick_fg(int N, int nf) {
 template <int FG>
 int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which, float* X,
                  int ldc, cudaStream_t st) {
-  const size_t smem = (size_t)(g.nlon + 2 * FG * g.nlon) * sizeof(float2);
+  const size_t smem = (size_t)(g.nlon + 2 * padded_len(FG * g.nlon)) * sizeof(float2);
   SHOT_CUDA(cudaFuncSetAttribute(k_dft_fwd<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(g.nh, (nf + FG - 1) / FG);
+  dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
   ProfScope prof(PK_DFT, st);
   count_launch();
   k_dft_fwd<FG><<<grid, kThreads, smem, st>>>(in, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, ps, scale_which, X,
@@ -286,9 +286,9 @@ int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, in
 
 template <int FG>
 int launch_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
-  const size_t smem = (size_t)(g.nlon + 2 * FG * g.nlon) * sizeof(float2);
+  const size_t smem = (size_t)(g.nlon + 2 * padded_len(FG * g.nlon)) * sizeof(float2);
   SHOT_CUDA(cudaFuncSetAttribute(k_idft<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid(g.nh, (nf + FG - 1) / FG);
+  dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
   ProfScope prof(PK_IDFT, st);
   count_launch();
   k_idft<FG><<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, ep);
@@ -304,7 +304,9 @@ int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, 
     set_error("nlon too large for the shared-memory ring FFT");
     return SHOT_ERR_UNSUPPORTED;
   }
-  switch (pick_fg(g.nlon, nf)) {
+  int fg = pick_fg(g.nlon, nf);
+  if (g.active.nf == nf && g.active.dft_fg > 0 && g.active.dft_fg * g.nlon <= kFftCap) fg = g.active.dft_fg;
+  switch (fg) {
     case 8: return launch_fwd_t<8>(g, in, nf, ps, scale_which, X, ldc, st);
     case 4: return launch_fwd_t<4>(g, in, nf, ps, scale_which, X, ldc, st);
     case 2: return launch_fwd_t<2>(g, in, nf, ps, scale_which, X, ldc, st);
@@ -317,7 +319,9 @@ int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams&
     set_error("nlon too large for the shared-memory ring FFT");
     return SHOT_ERR_UNSUPPORTED;
   }
-  switch (pick_fg(g.nlon, nf)) {
+  int fg = pick_fg(g.nlon, nf);
+  if (g.active.nf == nf && g.active.idft_fg > 0 && g.active.idft_fg * g.nlon <= kFftCap) fg = g.active.idft_fg;
+  switch (fg) {
     case 8: return launch_idft_t<8>(g, Y, ldc, nf, ep, st);
     case 4: return launch_idft_t<4>(g, Y, ldc, nf, ep, st);
     case 2: return launch_idft_t<2>(g, Y, ldc, nf, ep, st);

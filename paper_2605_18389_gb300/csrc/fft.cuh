@@ -105,6 +105,12 @@ __device__ __forceinline__ void butterfly(float2* v) {
   if (R == 8) bfly8<INV>(v);
 }
 
+// Shared-memory index of complex element i of the sequence buffers: one float2 of padding
+// after every 16, which turns the stride-R stores of the early Stockham stages into
+// conflict-free 8-byte accesses.
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4) + 1; }
+
 // a / d for 0 <= a < 2^16 and 2 <= d < 2^16 with mul = ceil(2^32 / d) (exact: the
 // error a (mul - 2^32/d) / 2^32 < 2^-16 never crosses an integer); mul == 0 means d == 1.
 __device__ __forceinline__ int fast_div(int a, uint32_t mul) {
@@ -123,12 +129,10 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
     const int j = idx - q * NR;
     const int jd = fast_div(j, ns_mul);
     const int k = j - jd * Ns;
-    const float2* s = src + q * ld;
-    float2* d = dst + q * ld;
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      float2 x = s[j + r * NR];
+      float2 x = src[pidx(q * ld + j + r * NR)];
       if (r > 0) {
         float2 w = tw[k * r * tstep];
         if (INV) w.y = -w.y;
@@ -139,7 +143,7 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
     butterfly<R, INV>(v);
     const int o = jd * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) d[o + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) dst[pidx(q * ld + o + r * Ns)] = v[r];
   }
 }
 

@@ -221,6 +221,10 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   float* tab = nullptr;
   __nv_bfloat16 *hi = nullptr, *lo = nullptr;
   g.ldi = (g.M[0] + 7) / 8 * 8;
+  if (g.mode == SHOT_RECURRENCE) {
+    int rc = build_recurrence(g, st);
+    if (rc) return rc;
+  } else {
   if (g.precision == SHOT_FP32) {
     SHOT_CUDA(cudaMalloc(&g.tab, tab_elems * sizeof(float)));
     SHOT_CUDA(cudaMemsetAsync(g.tab, 0, tab_elems * sizeof(float), st));
@@ -242,6 +246,7 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   count_launch();
   k_pbar<<<gp, 128, 0, st>>>(g.lmax, nh, g.x_d, g.row_off_d, g.ldt, tab, hi, lo, g.ldi, g.tabT_hi, g.tabT_lo);
   SHOT_CUDA(cudaGetLastError());
+  }
 
   // tile lists: analysis tiles cover the rows i of each block, synthesis tiles the nodes
   std::vector<Tile> ta, ts;

@@ -197,6 +197,11 @@ int launch_pair(const Grid& g, int nf, const float* X, float* C, float* Y, int l
 int dispatch(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
              const float* h, cudaStream_t st) {
   const int ncols = 2 * nf;
+  if (g.active.nf == nf && g.active.simt_bn > 0) {
+    if (g.active.simt_bn == 32) return launch_pair<32>(g, nf, X, C, Y, ldc, ana, syn, h, st);
+    if (g.active.simt_bn == 48) return launch_pair<48>(g, nf, X, C, Y, ldc, ana, syn, h, st);
+    return launch_pair<64>(g, nf, X, C, Y, ldc, ana, syn, h, st);
+  }
   if (ncols <= 32) return launch_pair<32>(g, nf, X, C, Y, ldc, ana, syn, h, st);
   if (ncols <= 48) return launch_pair<48>(g, nf, X, C, Y, ldc, ana, syn, h, st);
   return launch_pair<64>(g, nf, X, C, Y, ldc, ana, syn, h, st);

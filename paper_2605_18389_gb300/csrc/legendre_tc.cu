@@ -168,7 +168,8 @@ struct TcSmem {
   uint64_t fullA[kMaxStages];
   uint64_t fullB[kMaxStages];
   uint64_t empty[kMaxStages];
-  uint64_t done;
+  uint64_t tfull[2];    // accumulator buffer ready for the epilogue
+  uint64_t tempty[2];   // accumulator buffer drained by the epilogue
   uint32_t tmem;
   int abort;
 };
@@ -179,6 +180,7 @@ __device__ __forceinline__ uint8_t* align1k(uint8_t* p) {
 
 struct AnaArgs {
   const Tile* tiles;
+  int ntiles;
   const int* M;
   const long long* row_off;
   int nh;
@@ -192,159 +194,9 @@ struct AnaArgs {
   int* err;
 };
 
-template <int kStages>
-__global__ void __launch_bounds__(kTcThreads, 1) k_legendre_ana_tc(const __grid_constant__ CUtensorMap tm_hi,
-                                                                   const __grid_constant__ CUtensorMap tm_lo,
-                                                                   const __grid_constant__ CUtensorMap tm_x,
-                                                                   AnaArgs a) {
-  extern __shared__ uint8_t smraw[];
-  __shared__ TcSmem ctl;
-  uint8_t* base = align1k(smraw);
-  const int bbytes = a.nmma * kBK * 2;
-  uint8_t* sA_hi = base;
-  uint8_t* sA_lo = sA_hi + kStages * kATileBytes;
-  uint8_t* sB_hi = sA_lo + kStages * kATileBytes;
-  uint8_t* sB_lo = sB_hi + kStages * bbytes;
-  const int xbytes = a.nmma * kBK * 4;     // FP32 X tile [64 nodes][nmma columns]
-  uint8_t* sX = sB_lo + kStages * bbytes;
-
-  const Tile tl = a.tiles[blockIdx.x];
-  const int blk = tl.blk, i0 = tl.r0;
-  const int m = blk >> 1, p = blk & 1;
-  const int M = a.M[blk];
-  const long long ro = a.row_off[blk];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nkb = (a.nh + kBK - 1) / kBK;
-  const uint32_t ncols_alloc = tmem_cols_for(a.nmma);
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&ctl.fullA[s], 1);
-      mbar_init(&ctl.fullB[s], 128);
-      mbar_init(&ctl.empty[s], 1);
-    }
-    mbar_init(&ctl.done, 1);
-    ctl.abort = 0;
-    fence_mbar_init();
-  }
-  if (warp == 1) tmem_alloc(&ctl.tmem, ncols_alloc);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t taddr = ctl.tmem;
-  volatile int* abort = &ctl.abort;
-
-  if (warp == 0) {
-    if (lane == 0) {  // TMA producer of the table tiles (A operand)
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStages, n = kb / kStages;
-        if (kb >= kStages && !mbar_wait(&ctl.empty[s], (n - 1) & 1, abort)) break;
-        mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + xbytes);
-        tma_load_2d(sA_hi + s * kATileBytes, &tm_hi, &ctl.fullA[s], kb * kBK, (int)(ro + i0));
-        tma_load_2d(sA_lo + s * kATileBytes, &tm_lo, &ctl.fullA[s], kb * kBK, (int)(ro + i0));
-        tma_load_2d(sX + s * xbytes, &tm_x, &ctl.fullA[s], 0, blk * a.nh + kb * kBK);
-        issued = kb + 1;
-      }
-      for (int kb = issued > kStages ? issued - kStages : 0; kb < issued; ++kb)
-        mbar_drain(&ctl.fullA[kb % kStages], (kb / kStages) & 1);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = idesc_bf16(kBM, a.nmma);
-      bool ok = true;
-      for (int kb = 0; kb < nkb && ok; ++kb) {
-        const int s = kb % kStages, n = kb / kStages;
-        ok = mbar_wait(&ctl.fullA[s], n & 1, abort) && mbar_wait(&ctl.fullB[s], n & 1, abort);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
-        const uint32_t bh = smem_u32(sB_hi + s * bbytes), bl = smem_u32(sB_lo + s * bbytes);
-#pragma unroll
-        for (int k = 0; k < kBK / 16; ++k) {
-          const uint32_t off = k * 32;
-          umma_bf16(taddr, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bh + off), idesc, (kb | k) != 0);
-          umma_bf16(taddr, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bl + off), idesc, 1);
-          umma_bf16(taddr, desc_sw128_kmajor(al + off), desc_sw128_kmajor(bh + off), idesc, 1);
-        }
-        umma_commit(&ctl.empty[s]);
-      }
-      umma_commit(&ctl.done);
-    }
-  } else if (warp >= 4) {
-    // producers of the B operand: the FP32 tile X[jh][c] (brought by TMA with the table
-    // tiles) -> bf16 hi/lo, K-major [c][jh], 128-byte swizzled
-    const int pt = threadIdx.x - 128;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % kStages, n = kb / kStages;
-      if (!mbar_wait(&ctl.fullA[s], n & 1, abort)) break;
-      const float* xs = reinterpret_cast<const float*>(sX + s * xbytes);
-      uint8_t* bh = sB_hi + s * bbytes;
-      uint8_t* bl = sB_lo + s * bbytes;
-      // one task = 8 consecutive nodes of one column -> one 16-byte swizzle chunk of hi
-      // and of lo; rows beyond the block's nodes (or columns beyond the fields) are zero
-      for (int e = pt; e < 8 * a.nmma; e += 128) {
-        const int r8 = e / a.nmma, c = e - r8 * a.nmma;
-        const int jh0 = kb * kBK + r8 * 8;
-        uint32_t hw[4], lw[4];
-#pragma unroll
-        for (int t = 0; t < 8; t += 2) {
-          float v0 = xs[(r8 * 8 + t) * a.nmma + c];
-          float v1 = xs[(r8 * 8 + t + 1) * a.nmma + c];
-          if (c >= a.ncols || jh0 + t >= a.nh) v0 = 0.f;
-          if (c >= a.ncols || jh0 + t + 1 >= a.nh) v1 = 0.f;
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-          const float2 hf = __bfloat1622float2(h2);
-          const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-          hw[t / 2] = *reinterpret_cast<const uint32_t*>(&h2);
-          lw[t / 2] = *reinterpret_cast<const uint32_t*>(&l2);
-        }
-        const uint32_t o = sw128_offset(c, r8 * 8);
-        *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-        *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-      }
-      fence_async_smem();
-      mbar_arrive(&ctl.fullB[s]);
-    }
-    // epilogue: accumulator rows -> h_l scaling -> bf16 hi/lo C^T (and optional FP32 C)
-    const int q = warp - 4;   // TMEM lane quadrant
-    if (mbar_wait_warp(&ctl.done, 0, abort)) {
-      tc_fence_after();
-      const int row = q * 32 + lane;
-      const int i = i0 + row;
-      const float hl = (a.h && i < M) ? a.h[m + p + 2 * i] : 1.f;
-      for (int c0 = 0; c0 < a.nmma; c0 += 16) {
-        float v[16];
-        tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (i < M) {
-#pragma unroll
-          for (int t = 0; t < 16; ++t) {
-            const int c = c0 + t;
-            if (c < a.ncols) {
-              const float val = v[t] * hl;
-              const __nv_bfloat16 hi = __float2bfloat16_rn(val);
-              const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
-              const size_t o = ((size_t)blk * a.nmma_cap + c) * a.ldi + i;
-              a.ct_hi[o] = hi;
-              a.ct_lo[o] = lo;
-              if (a.cf) a.cf[(size_t)(ro + i) * a.ldc + c] = val;
-            }
-          }
-        }
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(taddr, ncols_alloc);
-  }
-  if (threadIdx.x == 0 && ctl.abort) atomicExch(a.err, SHOT_ERR_TIMEOUT);
-}
-
 struct SynArgs {
   const Tile* tiles;
+  int ntiles;
   const int* M;
   int nh;
   int nmma, nmma_cap, ncols, ldc;
@@ -352,111 +204,223 @@ struct SynArgs {
   int* err;
 };
 
-template <int kStages>
-__global__ void __launch_bounds__(kTcThreads, 1) k_legendre_syn_tc(const __grid_constant__ CUtensorMap ta_hi,
-                                                                   const __grid_constant__ CUtensorMap ta_lo,
-                                                                   const __grid_constant__ CUtensorMap tb_hi,
-                                                                   const __grid_constant__ CUtensorMap tb_lo,
-                                                                   SynArgs a) {
+// Persistent, warp-specialised Legendre GEMM.  Warp 0: TMA producer (runs ahead across
+// tiles); warp 1: MMA issuer; warps 2-3 (analysis only): split the FP32 X tile into the
+// bf16 hi/lo B operand; warps 4-7: epilogue.  The accumulator is double-buffered in TMEM
+// so the epilogue of one tile overlaps the MMAs of the next.
+template <int kStages, bool ANA>
+__global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_constant__ CUtensorMap ta_hi,
+                                                               const __grid_constant__ CUtensorMap ta_lo,
+                                                               const __grid_constant__ CUtensorMap tb_hi,
+                                                               const __grid_constant__ CUtensorMap tb_lo,
+                                                               AnaArgs aa, SynArgs sa) {
   extern __shared__ uint8_t smraw[];
   __shared__ TcSmem ctl;
   uint8_t* base = align1k(smraw);
-  const int bbytes = a.nmma * kBK * 2;
+  const int nmma = ANA ? aa.nmma : sa.nmma;
+  const int nh = ANA ? aa.nh : sa.nh;
+  const int ntiles = ANA ? aa.ntiles : sa.ntiles;
+  const Tile* tiles = ANA ? aa.tiles : sa.tiles;
+  const int* Mr = ANA ? aa.M : sa.M;
+  const int bbytes = nmma * kBK * 2;
+  const int xbytes = ANA ? nmma * kBK * 4 : 0;
   uint8_t* sA_hi = base;
   uint8_t* sA_lo = sA_hi + kStages * kATileBytes;
   uint8_t* sB_hi = sA_lo + kStages * kATileBytes;
   uint8_t* sB_lo = sB_hi + kStages * bbytes;
-
-  const Tile tl = a.tiles[blockIdx.x];
-  const int blk = tl.blk, j0 = tl.r0;
-  const int M = a.M[blk];
+  uint8_t* sX = sB_lo + kStages * bbytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nkb = (M + kBK - 1) / kBK;
-  const uint32_t ncols_alloc = tmem_cols_for(a.nmma);
+  const uint32_t ncols_alloc = tmem_cols_for(nmma);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl.fullA[s], 1);
-      mbar_init(&ctl.fullB[s], 1);
+      mbar_init(&ctl.fullB[s], 64);
       mbar_init(&ctl.empty[s], 1);
     }
-    mbar_init(&ctl.done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl.tfull[b], 1);
+      mbar_init(&ctl.tempty[b], 128);
+    }
     ctl.abort = 0;
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(&ctl.tmem, ncols_alloc);
+  if (warp == 1) tmem_alloc(&ctl.tmem, 2 * ncols_alloc);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t taddr = ctl.tmem;
   volatile int* abort = &ctl.abort;
+  auto nkb_of = [&](int blk) { return ANA ? (nh + kBK - 1) / kBK : (Mr[blk] + kBK - 1) / kBK; };
 
   if (warp == 0) {
-    if (lane == 0) {
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStages, n = kb / kStages;
-        if (kb >= kStages && !mbar_wait(&ctl.empty[s], (n - 1) & 1, abort)) break;
-        mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + 2 * bbytes);
-        tma_load_2d(sA_hi + s * kATileBytes, &ta_hi, &ctl.fullA[s], kb * kBK, blk * a.nh + j0);
-        tma_load_2d(sA_lo + s * kATileBytes, &ta_lo, &ctl.fullA[s], kb * kBK, blk * a.nh + j0);
-        tma_load_2d(sB_hi + s * bbytes, &tb_hi, &ctl.fullA[s], kb * kBK, blk * a.nmma_cap);
-        tma_load_2d(sB_lo + s * bbytes, &tb_lo, &ctl.fullA[s], kb * kBK, blk * a.nmma_cap);
-        issued = kb + 1;
-      }
-      for (int kb = issued > kStages ? issued - kStages : 0; kb < issued; ++kb)
-        mbar_drain(&ctl.fullA[kb % kStages], (kb / kStages) & 1);
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kBM, a.nmma);
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % kStages, n = kb / kStages;
-        if (!mbar_wait(&ctl.fullA[s], n & 1, abort)) break;
-        tc_fence_after();
-        const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
-        const uint32_t bh = smem_u32(sB_hi + s * bbytes), bl = smem_u32(sB_lo + s * bbytes);
-#pragma unroll
-        for (int k = 0; k < kBK / 16; ++k) {
-          const uint32_t off = k * 32;
-          umma_bf16(taddr, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bh + off), idesc, (kb | k) != 0);
-          umma_bf16(taddr, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bl + off), idesc, 1);
-          umma_bf16(taddr, desc_sw128_kmajor(al + off), desc_sw128_kmajor(bh + off), idesc, 1);
-        }
-        umma_commit(&ctl.empty[s]);
-      }
-      umma_commit(&ctl.done);
-    }
-  } else if (warp >= 4) {
-    const int q = warp - 4;
-    if (mbar_wait_warp(&ctl.done, 0, abort)) {
-      tc_fence_after();
-      const int jh = j0 + q * 32 + lane;
-      float* yrow = a.Y + ((size_t)blk * a.nh + jh) * a.ldc;
-      for (int c0 = 0; c0 < a.nmma; c0 += 16) {
-        float v[16];
-        tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-        if (jh < a.nh) {
-          if (c0 + 16 <= a.ncols) {
-#pragma unroll
-            for (int t = 0; t < 16; t += 4)
-              *reinterpret_cast<float4*>(yrow + c0 + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+    if (lane == 0) {  // TMA producer
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const int nkb = nkb_of(tl.blk);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % kStages, n = it / kStages;
+          if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
+          if (ANA) {
+            mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + xbytes);
+            const int y = (int)(aa.row_off[tl.blk] + tl.r0);
+            tma_load_2d(sA_hi + s * kATileBytes, &ta_hi, &ctl.fullA[s], kb * kBK, y);
+            tma_load_2d(sA_lo + s * kATileBytes, &ta_lo, &ctl.fullA[s], kb * kBK, y);
+            tma_load_2d(sX + s * xbytes, &tb_hi, &ctl.fullA[s], 0, tl.blk * nh + kb * kBK);
           } else {
-#pragma unroll
-            for (int t = 0; t < 16; ++t)
-              if (c0 + t < a.ncols) yrow[c0 + t] = v[t];
+            mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + 2 * bbytes);
+            const int y = tl.blk * nh + tl.r0;
+            tma_load_2d(sA_hi + s * kATileBytes, &ta_hi, &ctl.fullA[s], kb * kBK, y);
+            tma_load_2d(sA_lo + s * kATileBytes, &ta_lo, &ctl.fullA[s], kb * kBK, y);
+            tma_load_2d(sB_hi + s * bbytes, &tb_hi, &ctl.fullA[s], kb * kBK, tl.blk * sa.nmma_cap);
+            tma_load_2d(sB_lo + s * bbytes, &tb_lo, &ctl.fullA[s], kb * kBK, tl.blk * sa.nmma_cap);
           }
         }
       }
+      // let this CTA's copies land before it can exit
+      for (int k = it > kStages ? it - kStages : 0; k < it; ++k)
+        mbar_drain(&ctl.fullA[k % kStages], (k / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = idesc_bf16(kBM, nmma);
+      int it = 0, lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+        const Tile tl = tiles[t];
+        const int nkb = nkb_of(tl.blk);
+        const int acc = lt & 1, u = lt >> 1;
+        if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (u - 1) & 1, abort))) break;
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % kStages, n = it / kStages;
+          ok = mbar_wait(&ctl.fullA[s], n & 1, abort);
+          if (ok && ANA) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
+          const uint32_t bh = smem_u32(sB_hi + s * bbytes), bl = smem_u32(sB_lo + s * bbytes);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            const uint32_t off = k * 32;
+            umma_bf16(d, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bh + off), idesc, (kb | k) != 0);
+            umma_bf16(d, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bl + off), idesc, 1);
+            umma_bf16(d, desc_sw128_kmajor(al + off), desc_sw128_kmajor(bh + off), idesc, 1);
+          }
+          umma_commit(&ctl.empty[s]);
+        }
+        umma_commit(&ctl.tfull[acc]);
+      }
+    }
+  } else if (warp < 4) {
+    if (ANA) {
+      // split the FP32 X tile (TMA, with the table tiles) into bf16 hi/lo, K-major [c][jh]
+      const int pt = threadIdx.x - 64;
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const Tile tl = tiles[t];
+        const int nkb = nkb_of(tl.blk);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % kStages, n = it / kStages;
+          if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
+          const float* xs = reinterpret_cast<const float*>(sX + s * xbytes);
+          uint8_t* bh = sB_hi + s * bbytes;
+          uint8_t* bl = sB_lo + s * bbytes;
+          // one task = 8 consecutive nodes of one column -> one 16-byte swizzle chunk of hi
+          // and of lo; rows beyond the block's nodes (or columns beyond the fields) are zero
+          for (int e = pt; e < 8 * nmma; e += 64) {
+            const int r8 = e / nmma, c = e - r8 * nmma;
+            const int jh0 = kb * kBK + r8 * 8;
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+              float v0 = xs[(r8 * 8 + q) * nmma + c];
+              float v1 = xs[(r8 * 8 + q + 1) * nmma + c];
+              if (c >= aa.ncols || jh0 + q >= nh) v0 = 0.f;
+              if (c >= aa.ncols || jh0 + q + 1 >= nh) v1 = 0.f;
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+              const float2 hf = __bfloat1622float2(h2);
+              const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+              hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+              lw[q / 2] = *reinterpret_cast<const uint32_t*>(&l2);
+            }
+            const uint32_t o = sw128_offset(c, r8 * 8);
+            *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          }
+          fence_async_smem();
+          mbar_arrive(&ctl.fullB[s]);
+        }
+      }
+    }
+  } else {
+    // epilogue: drain the accumulator of every tile of this CTA
+    const int q = warp - 4;   // TMEM lane quadrant
+    int lt = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+      const Tile tl = tiles[t];
+      const int acc = lt & 1, u = lt >> 1;
+      if (!mbar_wait_warp(&ctl.tfull[acc], u & 1, abort)) break;
+      tc_fence_after();
+      const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc) + ((uint32_t)(q * 32) << 16);
+      const int row = tl.r0 + q * 32 + lane;
+      if (ANA) {
+        const int blk = tl.blk, m = blk >> 1, p = blk & 1;
+        const int M = Mr[blk];
+        const long long ro = aa.row_off[blk];
+        const float hl = (aa.h && row < M) ? aa.h[m + p + 2 * row] : 1.f;
+        for (int c0 = 0; c0 < nmma; c0 += 16) {
+          float v[16];
+          tmem_ld16(d + (uint32_t)c0, v);
+          if (row < M) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int c = c0 + e;
+              if (c < aa.ncols) {
+                const float val = v[e] * hl;
+                const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+                const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
+                const size_t o = ((size_t)blk * aa.nmma_cap + c) * aa.ldi + row;
+                aa.ct_hi[o] = hi;
+                aa.ct_lo[o] = lo;
+                if (aa.cf) aa.cf[(size_t)(ro + row) * aa.ldc + c] = val;
+              }
+            }
+          }
+        }
+      } else {
+        float* yrow = sa.Y + ((size_t)tl.blk * nh + row) * sa.ldc;
+        for (int c0 = 0; c0 < nmma; c0 += 16) {
+          float v[16];
+          tmem_ld16(d + (uint32_t)c0, v);
+          if (row < nh) {
+            if (c0 + 16 <= sa.ncols) {
+#pragma unroll
+              for (int e = 0; e < 16; e += 4)
+                *reinterpret_cast<float4*>(yrow + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (c0 + e < sa.ncols) yrow[c0 + e] = v[e];
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&ctl.tempty[acc]);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(taddr, ncols_alloc);
+    tmem_dealloc(taddr, 2 * ncols_alloc);
   }
-  if (threadIdx.x == 0 && ctl.abort) atomicExch(a.err, SHOT_ERR_TIMEOUT);
+  if (threadIdx.x == 0 && ctl.abort) atomicExch(ANA ? aa.err : sa.err, SHOT_ERR_TIMEOUT);
 }
 
 // FP32 coefficients C[row_off + i][ldc] -> bf16 hi/lo C^T[blk][nmma_cap][ldi] (synthesis input)
@@ -550,22 +514,27 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     return SHOT_ERR_UNSUPPORTED;
   }
   int rc;
+  AnaArgs aa{};
+  SynArgs sa{};
   if (ana) {
     // deepest pipeline (<= 3 stages) whose tiles fit in one CTA's shared memory
     int stages = kStagesAna;
+    if (g.active.nf == nf && g.active.tc_stages > 0) stages = g.active.tc_stages;
     while (stages > 1 && tc_smem_bytes(nmma, true, stages) > 227 * 1024) --stages;
     const size_t smem = tc_smem_bytes(nmma, true, stages);
     CUtensorMap mh, ml, mx;
     if ((rc = make_map(&mh, g.tab_hi, g.nh, g.rows_total, g.ldt, kBM))) return rc;
     if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kBM))) return rc;
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
-    AnaArgs a{g.tiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma, apply_h ? g.h_d : nullptr,
-              w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4};
-    auto kern = stages == 3 ? k_legendre_ana_tc<3> : stages == 2 ? k_legendre_ana_tc<2> : k_legendre_ana_tc<1>;
+    aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma,
+                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4};
+    auto kern = stages == 3 ? k_legendre_tc<3, true> : stages == 2 ? k_legendre_tc<2, true> : k_legendre_tc<1, true>;
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int per_sm = smem <= 113 * 1024 ? 2 : 1;
+    const int grid = g.ntiles_ana < per_sm * g.num_sms ? g.ntiles_ana : per_sm * g.num_sms;
     ProfScope prof(PK_ANALYSIS, st);
     count_launch();
-    kern<<<g.ntiles_ana, kTcThreads, smem, st>>>(mh, ml, mx, a);
+    kern<<<grid, kTcThreads, smem, st>>>(mh, ml, mx, mx, aa, sa);
     SHOT_CUDA(cudaGetLastError());
   }
   if (syn) {
@@ -575,12 +544,14 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map(&al, g.tabT_lo, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kBM))) return rc;
     if ((rc = make_map(&bh, w.ct_hi, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
     if ((rc = make_map(&bl, w.ct_lo, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
-    SynArgs a{g.tiles_syn, g.M_d, g.nh, nmma, w.nmma_cap, 2 * nf, ldc, Y, w.dev_int + 4};
-    SHOT_CUDA(cudaFuncSetAttribute(k_legendre_syn_tc<kStagesSyn>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem));
+    sa = SynArgs{g.tiles_syn, g.ntiles_syn, g.M_d, g.nh, nmma, w.nmma_cap, 2 * nf, ldc, Y, w.dev_int + 4};
+    auto kern = k_legendre_tc<kStagesSyn, false>;
+    SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int per_sm = smem <= 113 * 1024 ? 2 : 1;
+    const int grid = g.ntiles_syn < per_sm * g.num_sms ? g.ntiles_syn : per_sm * g.num_sms;
     ProfScope prof(PK_SYNTHESIS, st);
     count_launch();
-    k_legendre_syn_tc<kStagesSyn><<<g.ntiles_syn, kTcThreads, smem, st>>>(ah, al, bh, bl, a);
+    kern<<<grid, kTcThreads, smem, st>>>(ah, al, bh, bl, aa, sa);
     SHOT_CUDA(cudaGetLastError());
   }
   return SHOT_OK;

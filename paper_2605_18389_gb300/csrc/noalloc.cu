@@ -26,7 +26,7 @@
 
 namespace shot {
 
-int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
+int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
 
 namespace {
 
@@ -87,7 +87,7 @@ extern "C" int shot_heat_apply_noalloc(shot_grid gh, double t, const float* in, 
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if ((rc = launch_heat_mult(*g, t, st))) return rc;
   if ((rc = launch_dft_fwd(*g, in, nfields, nullptr, 0, X, ldc, st))) return rc;
-  if ((rc = launch_legendre_simt(*g, nfields, X, C, X, ldc, st))) return rc;
+  if ((rc = launch_legendre(*g, nfields, X, C, X, ldc, st))) return rc;
   EpiParams ep{};
   ep.mode = EPI_PLAIN;
   ep.out = out;

@@ -81,10 +81,22 @@ struct Workspace {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
+// Tunable launch shapes for one field count (0 = the built-in default).
+struct Tuning {
+  int nf = 0;
+  int dft_fg = 0;      // fields per ring-DFT CTA (1, 2, 4, 8)
+  int idft_fg = 0;     // fields per inverse-DFT CTA
+  int simt_bn = 0;     // FP32 Legendre tile width (32, 48, 64)
+  int tc_stages = 0;   // BF16x3 analysis pipeline depth (1..3)
+};
+
 struct Grid {
   int nlat = 0, nlon = 0, lmax = 0, nh = 0;
+  std::vector<Tuning> tuning;   // per field count, filled by the autotuner
+  Tuning active;                // the entry in force for the current launch sequence
   int precision = SHOT_FP32, mode = SHOT_TABLE;
   int dev = 0;
+  int num_sms = 148;
   FftPlan plan{};
   // host copies (FP64)
   std::vector<double> x, w, a_ring;
@@ -106,6 +118,11 @@ struct Grid {
   __nv_bfloat16* tabT_hi = nullptr;  // BF16X3 transposed copy [blk][jh][ldi]
   __nv_bfloat16* tabT_lo = nullptr;
   int ldi = 0;                  // row stride of the transposed table (>= max M, multiple of 8)
+  // SHOT_RECURRENCE: seeds per (m, node) and recurrence coefficients (O(n) memory)
+  void* rec_seeds = nullptr;
+  void* rec_coef = nullptr;
+  long long* rec_coef_off = nullptr;
+  float* rec_x = nullptr;
   int* M_d = nullptr;
   long long* row_off_d = nullptr;
   Tile* tiles_ana = nullptr;
@@ -163,9 +180,13 @@ int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int l
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st);
 int build_grid_tables(Grid& g, cudaStream_t st);
+int autotune(Grid& g, int nf, cudaStream_t st);   // selects g.active for nf (tunes on first use)
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
                        bool apply_h, cudaStream_t st);
 int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
+int build_recurrence(Grid& g, cudaStream_t st);
+int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
+                        bool apply_h, cudaStream_t st);
 int tc_nmma(int nf);
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
 

@@ -25,6 +25,7 @@ SHOT_ERR_TIMEOUT = -7
 SHOT_FP32 = 0
 SHOT_BF16X3 = 1
 SHOT_TABLE = 0
+SHOT_RECURRENCE = 1
 SHOT_GRAD_UNROLLED = 0
 SHOT_GRAD_ENVELOPE = 1
 SHOT_FLAG_NORM_L1 = 0x1
@@ -58,6 +59,7 @@ SIGNATURES = {
     "shot_divergence_grad": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                              ctypes.c_int, ctypes.c_int, _c_dbl_p, _vp, _c_int_p, _vp],
     "shot_heat_apply_noalloc": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
+    "shot_grid_autotune": [_vp, ctypes.c_int, _c_int_p, _vp],
     "shot_launch_count": [ctypes.POINTER(ctypes.c_longlong)],
     "shot_profile_enable": [ctypes.c_int],
     "shot_profile_read": [_c_dbl_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int],
@@ -316,3 +318,10 @@ def shot_divergence_multi(sets, max_iter=200, tol=0.0, check_every=10, flags=0, 
     rc = _solver_rc(lib().shot_divergence_multi(arr, len(sets), int(max_iter), float(tol), int(check_every),
                                                 int(flags), _stream(stream)))
     return rc, outs
+
+
+def shot_grid_autotune(g, nfields, stream=None):
+    """Tune (or look up) the launch shapes for nfields; returns dict of the four choices."""
+    ch = np.zeros(4, np.int32)
+    _check(lib().shot_grid_autotune(g, int(nfields), _np_ptr(ch, ctypes.c_int), _stream(stream)))
+    return dict(zip(("dft_fg", "idft_fg", "simt_bn", "tc_stages"), [int(x) for x in ch]))

@@ -83,7 +83,8 @@ def test_unrolled_gradient_config4_structure():
 
 
 def test_envelope_gradient_matches_oracle_envelope():
-    nlat, eps, T = 16, 0.5, 600
+    # converged problems (marginal error ~1e-15 in FP64): the envelope formula applies
+    nlat, eps, T = 16, 1.0, 400
     og = OGrid(nlat)
     g = shot.shot_grid_init(nlat)
     try:

@@ -29,7 +29,7 @@ def _set(og, seed, npairs, masses):
 
 
 def test_multi_grid_sets_match_oracle_and_single_calls():
-    eps, T = 0.02, 40
+    eps, T = 0.1, 40   # well-posed on all four grids (the oracle breaks down at eps 0.02 on nlat 16)
     specs = [(16, 1.0), (16, math.inf), (24, 0.1), (32, 10.0)]   # grid nlat, tau
     grids = {n: (shot.shot_grid_init(n), OGrid(n)) for n in (16, 24, 32)}
     try:
