@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--legendre", default="table", choices=["table", "recurrence"])
     ap.add_argument("--tau", type=float, default=math.inf)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nlat", type=int, default=NLAT, help=argparse.SUPPRESS)
@@ -54,15 +55,14 @@ def config(args, nlat, nlon):
                         f"{CHECK_EVERY}",
             "nlat": nlat, "nlon": nlon, "pairs": PAIRS, "problems": 3 * PAIRS, "t": T_HEAT,
             "tau": None if math.isinf(args.tau) else args.tau, "precision": args.precision,
+            "legendre": args.legendre,
             "fields": f"{RECIPE} (Sec. 4.1 workload: U(0,1) per node, unit mass), seed {SEED}",
             "l2": "working set > L2 every iteration (fields 2x100 MB, spectra 150 MB, table 0.37 GB)"}
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2605_18389_gb300 import dist as sd
+    return sd.env()
 
 
 class ClockSampler:
@@ -249,6 +249,7 @@ def main():
         return run_reference(args)
     import torch
     from paper_2605_18389_gb300 import shot, inputs
+    from paper_2605_18389_gb300 import dist as sd
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -260,9 +261,10 @@ def main():
     prec = shot.SHOT_FP32 if args.precision == "fp32" else shot.SHOT_BF16X3
     nlat = args.nlat
     nlon = 2 * nlat
-    g = shot.shot_grid_init(nlat, nlon, -1, prec)
+    mode = shot.SHOT_TABLE if args.legendre == "table" else shot.SHOT_RECURRENCE
+    g = shot.shot_grid_init(nlat, nlon, -1, prec, mode)
     x, w, a_ring = shot.shot_grid_nodes(g)
-    p, q = inputs.pairs(RECIPE, SEED + 1000 * rank, PAIRS, x, nlon, a_ring, dtype=np.float32)
+    p, q = inputs.pairs(RECIPE, sd.pair_seed(SEED, rank), PAIRS, x, nlon, a_ring, dtype=np.float32)
     pt = torch.from_numpy(p).cuda()
     qt = torch.from_numpy(q).cuda()
     u3 = torch.empty((3 * PAIRS, nlat, nlon), device="cuda")
@@ -297,12 +299,8 @@ def main():
     barrier()
     clk = clocks.stop()
     prof = shot.shot_profile_read()
-    ms = e0.elapsed_time(e1)
-    if pg is not None:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1e3)
+    ms = sd.max_over_ranks(e0.elapsed_time(e1), device="cuda")
+    value = sd.job_throughput(args.steps, ms / 1e3, ws)
 
     # end to end through the public call with host buffers: H2D of p, q inside the region
     ph = torch.from_numpy(p).pin_memory()
@@ -314,12 +312,8 @@ def main():
     qd = qh.to("cuda", non_blocking=True)
     rc2, res2 = shot.shot_divergence(g, pd, qd, EPS, max_iter=args.steps, **kw)   # S, status -> host
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * args.steps / e2e_s, "unit": "iters/s",
+    e2e_s = sd.max_over_ranks(time.perf_counter() - t0, device="cuda")
+    e2e = {"value": sd.job_throughput(args.steps, e2e_s, ws), "unit": "iters/s",
            "h2d_bytes_per_step": (p.nbytes + q.nbytes) / args.steps,
            "d2h_bytes_per_step": (res2["S"].nbytes + res2["S_dual"].nbytes + res2["status"].nbytes
                                   + res2["ot3"].nbytes + res2["iters3"].nbytes) / args.steps}

@@ -192,6 +192,15 @@ int shot_divergence_grad(shot_grid g, const float* p, const float* q, int batch,
                          int max_iter, int checkpoint_every, int mode, double* S, float* grad_p, int* status,
                          void* stream);
 
+/* Regional attribution of a divergence gradient (Sec. 4.2, App. E): the field form
+ * g_i = grad_p_i / a_i centred by its area-weighted mean, then the area-weighted RMS
+ * sqrt(sum_R a (g - mean)^2 / sum_R a) over the bands R = Tropics (|lat| < 23.5 deg),
+ * ITCZ (|lat| < 10), NH mid-latitudes (30..60 N), SH mid-latitudes (30..60 S), Arctic (> 66.5 N).
+ *   grad_p  device [batch][nlat][nlon] float32 (as written by shot_divergence_grad)
+ *   rms     host [batch][5] in that band order (NaN for a band without nodes)
+ * Synchronises `stream`. */
+int shot_regional_rms(shot_grid g, const float* grad_p, int batch, double* rms, void* stream);
+
 /* ---- heat convolution without device allocation (no counterpart in the paper) ----
  * For callers that cannot call cudaMalloc where they need K_t: code running while
  * another component owns the allocator (a pool that must not grow, a framework step

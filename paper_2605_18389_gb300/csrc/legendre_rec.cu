@@ -6,9 +6,11 @@
 // l_s >= m with |Pbar_{l_s m}(x_jh)| >= 2^-100 and the FP64-computed values
 // Pbar_{l_s m}, Pbar_{l_s+1, m} (rounded to FP32); below l_s the functions are < 2^-100
 // (they underflow in FP32 near the poles at high m) and are taken as 0.  From the seed the
-// normalised three-term recurrence of App. B runs in FP32:
+// normalised three-term recurrence of App. B runs in double-float arithmetic (every value
+// and coefficient an unevaluated FP32 pair hi + lo, ~44 significant bits; a plain FP32
+// recurrence drifts by ~1e-7 per degree, 5e-5 at degree 719):
 //   Pbar_lm = a_lm (x Pbar_{l-1,m} - b_lm Pbar_{l-2,m}),
-// with a_lm, b_lm from a (lmax+1)(lmax+2)/2 coefficient table.
+// with a_lm, b_lm from a (lmax+1)(lmax+2)/2 coefficient table (FP64 rounded to pairs).
 //   analysis:  a CTA owns (m, parity, 48-column tile); it marches l in chunks, its threads
 //              generating 32 rows of the parity into shared memory per chunk, and contracts
 //              them against the X tile (also in shared memory), times h_l.
@@ -26,12 +28,34 @@ constexpr int kRN = 48;     // columns per CTA
 
 struct Seed {
   int ls;
-  float p0, p1;
+  float p0h, p0l, p1h, p1l;
 };
 
-// generate the next value of the recurrence for node state (pm2, pm1) at degree l
-__device__ __forceinline__ float rec_step(float x, float pm1, float pm2, float a, float b) {
-  return a * fmaf(x, pm1, -b * pm2);
+// double-float helpers (Dekker/Knuth error-free transformations with FMA); the _rn
+// intrinsics are never contracted, which the transformations rely on
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float s = __fadd_rn(p, e);
+  return DF{s, __fsub_rn(e, __fsub_rn(s, p))};
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+  const float s = __fsub_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  float e = __fsub_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fadd_rn(b.h, bb));
+  e = __fadd_rn(e, __fsub_rn(a.l, b.l));
+  const float t = __fadd_rn(s, e);
+  return DF{t, __fsub_rn(e, __fsub_rn(t, s))};
+}
+
+// next value of the recurrence from (Pbar_{l-1}, Pbar_{l-2}) with ab = (a_h, a_l, b_h, b_l)
+__device__ __forceinline__ DF rec_step(DF x, DF pm1, DF pm2, float4 ab) {
+  return df_mul(DF{ab.x, ab.y}, df_sub(df_mul(x, pm1), df_mul(DF{ab.z, ab.w}, pm2)));
 }
 
 // Analysis, one CTA per (m, parity, column tile): C[i][c] = h_l sum_jh Pbar_lm(x_jh) X[jh][c].
@@ -39,9 +63,9 @@ __device__ __forceinline__ float rec_step(float x, float pm1, float pm2, float a
 constexpr int kAnaThreads = 256;
 
 template <int NPT>
-__global__ void __launch_bounds__(kAnaThreads) k_ana_rec(int lmax, int nh, const float* __restrict__ xf,
+__global__ void __launch_bounds__(kAnaThreads) k_ana_rec(int lmax, int nh, const float2* __restrict__ xf,
                                                          const Seed* __restrict__ seeds,
-                                                         const float2* __restrict__ coef,
+                                                         const float4* __restrict__ coef,
                                                          const long long* __restrict__ coef_off,
                                                          const int* __restrict__ Mrows,
                                                          const long long* __restrict__ row_off,
@@ -60,22 +84,23 @@ __global__ void __launch_bounds__(kAnaThreads) k_ana_rec(int lmax, int nh, const
     const int k = idx / kRN, c = idx - k * kRN;
     Xs[idx] = (n0 + c < ncols) ? Xb[(size_t)k * ldc + n0 + c] : 0.f;
   }
-  float st1[NPT], st2[NPT], xs[NPT], s0[NPT], s1[NPT];
+  DF st1[NPT], st2[NPT], xs[NPT], s0[NPT], s1[NPT];
   int ls[NPT];
 #pragma unroll
   for (int r = 0; r < NPT; ++r) {
     const int jh = threadIdx.x + r * kAnaThreads;
-    st1[r] = st2[r] = xs[r] = s0[r] = s1[r] = 0.f;
+    st1[r] = st2[r] = xs[r] = s0[r] = s1[r] = DF{0.f, 0.f};
     ls[r] = 1 << 30;
     if (jh < nh) {
       const Seed sd = seeds[(size_t)m * nh + jh];
-      xs[r] = xf[jh];
+      const float2 xx = xf[jh];
+      xs[r] = DF{xx.x, xx.y};
       ls[r] = sd.ls;
-      s0[r] = sd.p0;
-      s1[r] = sd.p1;
+      s0[r] = DF{sd.p0h, sd.p0l};
+      s1[r] = DF{sd.p1h, sd.p1l};
     }
   }
-  const float2* cf = coef + coef_off[m];   // (a, b) for l = m .. lmax at index l - m
+  const float4* cf = coef + coef_off[m];   // (a_h, a_l, b_h, b_l) for l = m .. lmax at index l - m
   // contraction tile: row tr (32 rows), 6 columns from tc*6 (8 groups over 48)
   const int tr = threadIdx.x >> 3, tc = threadIdx.x & 7;
   int l = m;                                 // next degree to generate
@@ -86,20 +111,20 @@ __global__ void __launch_bounds__(kAnaThreads) k_ana_rec(int lmax, int nh, const
     // marches every degree (both parities) up to the last of them
     const int lend = m + p + 2 * (i0 + rows - 1);
     for (; l <= lend; ++l) {
-      const float2 ab = cf[l - m];
+      const float4 ab = cf[l - m];
       const bool keep = ((l - m) & 1) == p;
       const int row = ((l - m - p) >> 1) - i0;
 #pragma unroll
       for (int r = 0; r < NPT; ++r) {
-        float v;
-        if (l < ls[r]) v = 0.f;
+        DF v;
+        if (l < ls[r]) v = DF{0.f, 0.f};
         else if (l == ls[r]) v = s0[r];
         else if (l == ls[r] + 1) v = s1[r];
-        else v = rec_step(xs[r], st1[r], st2[r], ab.x, ab.y);
+        else v = rec_step(xs[r], st1[r], st2[r], ab);
         st2[r] = st1[r];
         st1[r] = v;
         const int jh = threadIdx.x + r * kAnaThreads;
-        if (keep && jh < nh) Ps[(size_t)jh * kRB + row] = v;
+        if (keep && jh < nh) Ps[(size_t)jh * kRB + row] = v.h;
       }
     }
     __syncthreads();
@@ -129,9 +154,9 @@ __global__ void __launch_bounds__(kAnaThreads) k_ana_rec(int lmax, int nh, const
 }
 
 // Synthesis: Y[jh][c] = sum_i Pbar_lm(x_jh) C[i][c] for block (m, p); a thread owns a node
-__global__ void __launch_bounds__(kRecThreads) k_syn_rec(int lmax, int nh, const float* __restrict__ xf,
+__global__ void __launch_bounds__(kRecThreads) k_syn_rec(int lmax, int nh, const float2* __restrict__ xf,
                                                          const Seed* __restrict__ seeds,
-                                                         const float2* __restrict__ coef,
+                                                         const float4* __restrict__ coef,
                                                          const long long* __restrict__ coef_off,
                                                          const int* __restrict__ Mrows,
                                                          const long long* __restrict__ row_off,
@@ -153,23 +178,22 @@ __global__ void __launch_bounds__(kRecThreads) k_syn_rec(int lmax, int nh, const
   __syncthreads();
   if (jh >= nh) return;
   const Seed sd = seeds[(size_t)m * nh + jh];
-  const float x = xf[jh];
-  const float2* cf = coef + coef_off[m];
+  const float2 xx = xf[jh];
+  const DF x{xx.x, xx.y};
+  const float4* cf = coef + coef_off[m];
   float acc[kRN];
 #pragma unroll
   for (int c = 0; c < kRN; ++c) acc[c] = 0.f;
-  float st1 = 0.f, st2 = 0.f;
+  DF st1{0.f, 0.f}, st2{0.f, 0.f};
   const int lend = m + p + 2 * (M - 1);
   for (int l = (sd.ls > m ? sd.ls : m); l <= lend; ++l) {
-    float v;
-    if (l == sd.ls) v = sd.p0;
-    else if (l == sd.ls + 1) v = sd.p1;
-    else {
-      const float2 ab = cf[l - m];
-      v = rec_step(x, st1, st2, ab.x, ab.y);
-    }
+    DF vv;
+    if (l == sd.ls) vv = DF{sd.p0h, sd.p0l};
+    else if (l == sd.ls + 1) vv = DF{sd.p1h, sd.p1l};
+    else vv = rec_step(x, st1, st2, cf[l - m]);
     st2 = st1;
-    st1 = v;
+    st1 = vv;
+    const float v = vv.h;
     if (((l - m) & 1) == p) {
       const float4* cr = reinterpret_cast<const float4*>(Cs + (size_t)((l - m - p) >> 1) * kRN);
 #pragma unroll
@@ -189,12 +213,17 @@ __global__ void __launch_bounds__(kRecThreads) k_syn_rec(int lmax, int nh, const
 }
 
 // seeds (FP64 recurrence from l = m until |Pbar| >= 2^-100) and the coefficient table
+__device__ __forceinline__ float2 split_df(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 __global__ void k_rec_seeds(int lmax, int nh, const double* __restrict__ x, Seed* __restrict__ seeds,
-                            float* __restrict__ xf) {
+                            float2* __restrict__ xf) {
   const int jh = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (jh >= nh) return;
-  if (m == 0) xf[jh] = (float)x[jh];
+  if (m == 0) xf[jh] = split_df(x[jh]);
   const double xj = x[jh];
   const double st = sqrt((1.0 - xj) * (1.0 + xj));
   const double thr = 7.888609052210118e-31;   // 2^-100
@@ -216,19 +245,23 @@ __global__ void k_rec_seeds(int lmax, int nh, const double* __restrict__ x, Seed
   }
   Seed s;
   s.ls = (fabs(p2) < thr) ? (1 << 30) : l;
-  s.p0 = (float)p2;
-  s.p1 = (float)p1;
+  const float2 a0 = split_df(p2), a1 = split_df(p1);
+  s.p0h = a0.x;
+  s.p0l = a0.y;
+  s.p1h = a1.x;
+  s.p1l = a1.y;
   seeds[(size_t)m * nh + jh] = s;
 }
 
-__global__ void k_rec_coef(int lmax, const long long* __restrict__ coef_off, float2* __restrict__ coef) {
+__global__ void k_rec_coef(int lmax, const long long* __restrict__ coef_off, float4* __restrict__ coef) {
   const int m = blockIdx.x;
   for (int l = m + threadIdx.x; l <= lmax; l += blockDim.x) {
-    float2 ab = make_float2(0.f, 0.f);
+    float4 ab = make_float4(0.f, 0.f, 0.f, 0.f);
     if (l >= m + 2) {
       const double ll = (double)l * l, mm = (double)m * m, l1 = (double)(l - 1) * (l - 1);
-      ab.x = (float)sqrt((4.0 * ll - 1.0) / (ll - mm));
-      ab.y = (float)sqrt((l1 - mm) / (4.0 * l1 - 1.0));
+      const float2 a = split_df(sqrt((4.0 * ll - 1.0) / (ll - mm)));
+      const float2 b = split_df(sqrt((l1 - mm) / (4.0 * l1 - 1.0)));
+      ab = make_float4(a.x, a.y, b.x, b.y);
     }
     coef[coef_off[m] + (l - m)] = ab;
   }
@@ -242,13 +275,14 @@ int build_recurrence(Grid& g, cudaStream_t st) {
   for (int m = 0; m < L; ++m) off[m + 1] = off[m] + (L - m);
   SHOT_CUDA(cudaMalloc(&g.rec_coef_off, (L + 1) * sizeof(long long)));
   SHOT_CUDA(cudaMemcpyAsync(g.rec_coef_off, off.data(), (L + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
-  SHOT_CUDA(cudaMalloc(&g.rec_coef, off[L] * sizeof(float2)));
+  SHOT_CUDA(cudaMalloc(&g.rec_coef, off[L] * sizeof(float4)));
   SHOT_CUDA(cudaMalloc(&g.rec_seeds, (size_t)L * g.nh * sizeof(Seed)));
-  SHOT_CUDA(cudaMalloc(&g.rec_x, (size_t)g.nh * sizeof(float)));
+  SHOT_CUDA(cudaMalloc(&g.rec_x, (size_t)g.nh * sizeof(float2)));
   count_launch(2);
-  k_rec_coef<<<L, 256, 0, st>>>(g.lmax, g.rec_coef_off, reinterpret_cast<float2*>(g.rec_coef));
+  k_rec_coef<<<L, 256, 0, st>>>(g.lmax, g.rec_coef_off, reinterpret_cast<float4*>(g.rec_coef));
   dim3 gs((g.nh + 127) / 128, L);
-  k_rec_seeds<<<gs, 128, 0, st>>>(g.lmax, g.nh, g.x_d, reinterpret_cast<Seed*>(g.rec_seeds), g.rec_x);
+  k_rec_seeds<<<gs, 128, 0, st>>>(g.lmax, g.nh, g.x_d, reinterpret_cast<Seed*>(g.rec_seeds),
+                                  reinterpret_cast<float2*>(g.rec_x));
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }
@@ -273,8 +307,9 @@ int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* 
     ProfScope prof(PK_ANALYSIS, st);
     count_launch();
     kern<<<dim3(g.nblk, ncol_tiles), kAnaThreads, smem, st>>>(
-        g.lmax, g.nh, g.rec_x, reinterpret_cast<const Seed*>(g.rec_seeds), reinterpret_cast<const float2*>(g.rec_coef),
-        g.rec_coef_off, g.M_d, g.row_off_d, X, ldc, ncols, apply_h ? g.h_d : nullptr, C);
+        g.lmax, g.nh, reinterpret_cast<const float2*>(g.rec_x), reinterpret_cast<const Seed*>(g.rec_seeds),
+        reinterpret_cast<const float4*>(g.rec_coef), g.rec_coef_off, g.M_d, g.row_off_d, X, ldc, ncols,
+        apply_h ? g.h_d : nullptr, C);
     SHOT_CUDA(cudaGetLastError());
   }
   if (syn) {
@@ -283,8 +318,8 @@ int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* 
     ProfScope prof(PK_SYNTHESIS, st);
     count_launch();
     k_syn_rec<<<dim3(g.nblk, (g.nh + kRecThreads - 1) / kRecThreads, ncol_tiles), kRecThreads, smem, st>>>(
-        g.lmax, g.nh, g.rec_x, reinterpret_cast<const Seed*>(g.rec_seeds), reinterpret_cast<const float2*>(g.rec_coef),
-        g.rec_coef_off, g.M_d, g.row_off_d, C, ldc, ncols, Y);
+        g.lmax, g.nh, reinterpret_cast<const float2*>(g.rec_x), reinterpret_cast<const Seed*>(g.rec_seeds),
+        reinterpret_cast<const float4*>(g.rec_coef), g.rec_coef_off, g.M_d, g.row_off_d, C, ldc, ncols, Y);
     SHOT_CUDA(cudaGetLastError());
   }
   return SHOT_OK;

@@ -503,6 +503,12 @@ size_t tc_smem_bytes(int nmma, bool with_x, int stages) {
 
 int tc_nmma(int nf) { return (2 * nf + 15) / 16 * 16; }
 
+static int host_tmem_cols(int n) {
+  int c = 32;
+  while (c < n) c <<= 1;
+  return c;
+}
+
 int tc_supported_fields(int nf) { return tc_nmma(nf) <= 256; }
 
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
@@ -530,7 +536,8 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
                  apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4};
     auto kern = stages == 3 ? k_legendre_tc<3, true> : stages == 2 ? k_legendre_tc<2, true> : k_legendre_tc<1, true>;
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int per_sm = smem <= 113 * 1024 ? 2 : 1;
+    // CTAs per SM: both shared memory and the 512 TMEM columns (two accumulators each) must fit
+    const int per_sm = (smem <= 113 * 1024 && 2 * 2 * host_tmem_cols(nmma) <= 512) ? 2 : 1;
     const int grid = g.ntiles_ana < per_sm * g.num_sms ? g.ntiles_ana : per_sm * g.num_sms;
     ProfScope prof(PK_ANALYSIS, st);
     count_launch();
@@ -547,7 +554,8 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     sa = SynArgs{g.tiles_syn, g.ntiles_syn, g.M_d, g.nh, nmma, w.nmma_cap, 2 * nf, ldc, Y, w.dev_int + 4};
     auto kern = k_legendre_tc<kStagesSyn, false>;
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int per_sm = smem <= 113 * 1024 ? 2 : 1;
+    // CTAs per SM: both shared memory and the 512 TMEM columns (two accumulators each) must fit
+    const int per_sm = (smem <= 113 * 1024 && 2 * 2 * host_tmem_cols(nmma) <= 512) ? 2 : 1;
     const int grid = g.ntiles_syn < per_sm * g.num_sms ? g.ntiles_syn : per_sm * g.num_sms;
     ProfScope prof(PK_SYNTHESIS, st);
     count_launch();

@@ -58,6 +58,7 @@ SIGNATURES = {
                         _c_dbl_p, _c_int_p, _vp],
     "shot_divergence_grad": [_vp, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                              ctypes.c_int, ctypes.c_int, _c_dbl_p, _vp, _c_int_p, _vp],
+    "shot_regional_rms": [_vp, _vp, ctypes.c_int, _c_dbl_p, _vp],
     "shot_heat_apply_noalloc": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
     "shot_grid_autotune": [_vp, ctypes.c_int, _c_int_p, _vp],
     "shot_launch_count": [ctypes.POINTER(ctypes.c_longlong)],
@@ -325,3 +326,14 @@ def shot_grid_autotune(g, nfields, stream=None):
     ch = np.zeros(4, np.int32)
     _check(lib().shot_grid_autotune(g, int(nfields), _np_ptr(ch, ctypes.c_int), _stream(stream)))
     return dict(zip(("dft_fg", "idft_fg", "simt_bn", "tc_stages"), [int(x) for x in ch]))
+
+
+REGIONS = ("tropics", "itcz", "nh_midlat", "sh_midlat", "arctic")
+
+
+def shot_regional_rms(g, grad, stream=None):
+    """[batch, 5] area-weighted RMS of the centred gradient field per latitude band."""
+    B = grad.shape[0]
+    out = np.empty((B, 5))
+    _check(lib().shot_regional_rms(g, _dev_ptr(grad, "grad"), B, _np_ptr(out, ctypes.c_double), _stream(stream)))
+    return out

@@ -179,3 +179,26 @@ def test_unbalanced_fd_gradient_matches_envelope_dual_form():
     fd = fd_directional(g, p[0], q[0], eps, tau, T, dirs, h=1e-5, form="S_dual")
     env = np.array([np.sum(ge * d) for d in dirs])
     np.testing.assert_allclose(fd, env, rtol=2e-5, atol=1e-8)
+
+
+def test_regional_rms_invariants():
+    # invariance to the additive constant of the potentials (centring), linear scaling,
+    # hemispheric mirror symmetry, and a closed form for a field that is constant on rings
+    from oracle.regional import regional_rms, band_masks
+    g = Grid(90)
+    a = g.a
+    rng = np.random.default_rng(0)
+    f = rng.normal(size=(g.nlat, g.nlon))
+    r0 = regional_rms(g, a * f)
+    np.testing.assert_allclose(regional_rms(g, a * (f + 3.7)), r0, rtol=1e-12)
+    np.testing.assert_allclose(regional_rms(g, a * 2.5 * f), 2.5 * r0, rtol=1e-12)
+    sym = f + f[::-1]                         # mirror-symmetric field: equal mid-latitude bands
+    rs = regional_rms(g, a * sym)
+    assert abs(rs[2] - rs[3]) < 1e-12 * rs[2]
+    # ring-constant field g = lat: centred mean 0 (odd); band RMS = weighted RMS of lat over the band
+    lat = g.lat_deg
+    rl = regional_rms(g, a * np.repeat(lat[:, None], g.nlon, axis=1))
+    for k, m in enumerate(band_masks(lat)):
+        w = g.w * m
+        exp = np.sqrt(np.sum(w * lat ** 2) / np.sum(w))
+        assert abs(rl[k] - exp) < 1e-10 * exp
