@@ -30,14 +30,16 @@ int cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? SHOT_ERR_OOM : SHOT_ERR_CUDA;
 }
 
-int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
+int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
+                         const ProbState* colscale);
 int launch_analysis_simt(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h, cudaStream_t st);
 int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st);
 
-int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st) {
-  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st);
-  if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st);
-  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st);
+int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
+                    const ProbState* colscale) {
+  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st, colscale);
+  if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st, colscale);
+  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st, colscale);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st) {
@@ -288,7 +290,9 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
   }
   SHOT_CUDA(cudaGetLastError());
   if ((rc = autotune(g, nprob, s.st))) return rc;
-  return launch_heat_mult(g, eps / 4.0, s.st);
+  if ((rc = launch_heat_mult(g, eps / 4.0, s.st))) return rc;
+  // spectra of the starting v (unscaled; the analysis applies beta per column)
+  return launch_dft_fwd(g, v, nprob, nullptr, 0, w.XY, w.ldc, s.st);
 }
 
 EpiParams base_ep(Solve& s) {
@@ -301,37 +305,43 @@ EpiParams base_ep(Solve& s) {
   return ep;
 }
 
-// nit iterations of Alg. 1, then (optionally) the marginal check; no host synchronisation
+// nit iterations of Alg. 1, then (optionally) the marginal check; no host synchronisation.
+// X always holds the unscaled ring spectra of the scaling the next heat convolution needs:
+// each half-step's inverse DFT also transforms the scaling it has just produced (fused),
+// and the gauge factor beta of v is applied per column by the next Legendre analysis.
 int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
   Grid& g = *s.g;
   Workspace& w = g.ws;
   const float* const* margP = w.marg;
   const float* const* margQ = w.marg + s.nprob;
+  ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   EpiParams ep = base_ep(s);
   int rc;
   for (int i = 0; i < nit; ++i) {
-    // u-step: u = (p / K(beta v))^gamma
-    if ((rc = heat_pipeline(g, s.v, s.nprob, 1, st))) return rc;
+    // u-step: u = (p / K(beta v))^gamma, and X := F(u)
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, ps))) return rc;
     ep.mode = EPI_UPDATE;
     ep.out = s.u;
     ep.marg = margP;
     ep.which = 0;
-    if ((rc = launch_idft(g, w.XY, w.ldc, s.nprob, ep, st))) return rc;
+    ep.xout = w.XY;
+    if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
     if ((rc = reduce(g, RED_U, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
-    // v-step: v = (q / K u)^gamma, then the gauge / translation-invariant scalars
-    if ((rc = heat_pipeline(g, s.u, s.nprob, 0, st))) return rc;
+    // v-step: v = (q / K u)^gamma, X := F(v); then the gauge / translation-invariant scalars
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr))) return rc;
     ep.out = s.v;
     ep.marg = margQ;
     ep.which = 1;
-    if ((rc = launch_idft(g, w.XY, w.ldc, s.nprob, ep, st))) return rc;
+    if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
     if ((rc = reduce(g, RED_V, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
   }
-  if (check) {
-    if ((rc = heat_pipeline(g, s.v, s.nprob, 1, st))) return rc;
+  if (check) {   // K(beta v) from the spectra X, which stay for the next u-step
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, ps))) return rc;
     ep.mode = EPI_CHECK;
     ep.other = s.u;
     ep.marg = margP;
-    if ((rc = launch_idft(g, w.XY, w.ldc, s.nprob, ep, st))) return rc;
+    ep.xout = nullptr;
+    if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
     if ((rc = reduce(g, RED_CHECK, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
   }
   return SHOT_OK;
@@ -341,17 +351,17 @@ int solve_final_enqueue(Solve& s) {
   Grid& g = *s.g;
   Workspace& w = g.ws;
   EpiParams ep = base_ep(s);
+  ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   int rc;
   // final K v_true for the objective, mass and marginal error; writes u_true, v_true
-  if ((rc = heat_pipeline(g, s.v, s.nprob, 1, s.st))) return rc;
+  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st, ps))) return rc;
   ep.mode = EPI_FINAL;
   ep.out = s.v;
   ep.other = s.u;
   ep.marg = w.marg;
   ep.marg2 = w.marg + s.nprob;
-  if ((rc = launch_idft(g, w.XY, w.ldc, s.nprob, ep, s.st))) return rc;
+  if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, s.st))) return rc;
   if ((rc = reduce(g, RED_FINAL, s.nprob, s.eps, s.tol, s.norm_l1, s.st))) return rc;
-  ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   SHOT_CUDA(cudaMemcpyAsync(w.host_probs, ps, s.nprob * sizeof(ProbState), cudaMemcpyDeviceToHost, s.st));
   SHOT_CUDA(cudaMemcpyAsync(w.host_int, w.dev_int, 8 * sizeof(int), cudaMemcpyDeviceToHost, s.st));
   return SHOT_OK;
@@ -576,7 +586,8 @@ int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision, 
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi, g->tabT_lo,
+  void* dptr[] = {g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi,
+                  g->tabT_lo,
                   g->ws.ct_hi, g->ws.ct_lo, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};

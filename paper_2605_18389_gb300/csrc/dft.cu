@@ -45,6 +45,31 @@ __device__ __forceinline__ void load_ring_pairs(const float* __restrict__ in, fl
   }
 }
 
+// Two-for-one unpack of the transformed ring pair (j north, J south) and the parity fold:
+// F_N(m) = (Z(m) + conj Z(N-m))/2, F_S(m) = (Z(m) - conj Z(N-m))/(2i);
+// S = a_j (F_N + F_S) -> block (m, even), D = a_j (F_N - F_S) -> block (m, odd).
+template <int FG>
+__device__ __forceinline__ void unpack_fold_store(const float2* buf, int nfg, int f0, int N, int lmax, int nh, int jh,
+                                                  float aj, const ProbState* __restrict__ ps, int scale_which,
+                                                  float* __restrict__ X, int ldc) {
+  const int nm = lmax + 1;
+  for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
+    const int m = idx / FG, q = idx - m * FG;
+    if (q >= nfg) continue;
+    const int f = f0 + q;
+    float sc = aj;
+    if (scale_which == 1) sc *= (float)ps[f].beta;
+    const float2 zm = buf[pidx(q * N + m)];
+    const float2 zn = buf[pidx(q * N + (m ? N - m : 0))];
+    const float2 FN = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
+    const float2 FS = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
+    const float2 S = make_float2(sc * (FN.x + FS.x), sc * (FN.y + FS.y));
+    const float2 D = make_float2(sc * (FN.x - FS.x), sc * (FN.y - FS.y));
+    *reinterpret_cast<float2*>(X + ((size_t)(2 * m) * nh + jh) * ldc + 2 * f) = S;
+    *reinterpret_cast<float2*>(X + ((size_t)(2 * m + 1) * nh + jh) * ldc + 2 * f) = D;
+  }
+}
+
 template <int FG>
 __global__ void __launch_bounds__(kThreads, 2) k_dft_fwd(
     const float* __restrict__ in, int nf, int nlat, int nlon, int lmax, int nh,
@@ -65,23 +90,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_dft_fwd(
   __syncthreads();
   const float2* buf = fft_smem<false>(b0, b1, tw, pl, nfg, N);
 
-  const float aj = a_ring[j];
-  const int nm = lmax + 1;
-  for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
-    const int m = idx / FG, q = idx - m * FG;
-    if (q >= nfg) continue;
-    const int f = f0 + q;
-    float sc = aj;
-    if (scale_which == 1) sc *= (float)ps[f].beta;
-    const float2 zm = buf[pidx(q * N + m)];
-    const float2 zn = buf[pidx(q * N + (m ? N - m : 0))];
-    const float2 FN = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
-    const float2 FS = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
-    const float2 S = make_float2(sc * (FN.x + FS.x), sc * (FN.y + FS.y));
-    const float2 D = make_float2(sc * (FN.x - FS.x), sc * (FN.y - FS.y));
-    *reinterpret_cast<float2*>(X + ((size_t)(2 * m) * nh + jh) * ldc + 2 * f) = S;
-    *reinterpret_cast<float2*>(X + ((size_t)(2 * m + 1) * nh + jh) * ldc + 2 * f) = D;
-  }
+  unpack_fold_store<FG>(buf, nfg, f0, N, lmax, nh, jh, a_ring[j], ps, scale_which, X, ldc);
 }
 
 template <int FG>
@@ -123,6 +132,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
   }
   __syncthreads();
   const float2* z = fft_smem<true>(buf, b1, tw, pl, nfg, N);
+  float2* other = (z == buf) ? b1 : buf;   // input of the fused forward transform
 
   const float aj = a_ring[j];
   const int nrings = (J != j) ? 2 : 1;
@@ -153,7 +163,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
     const size_t fbase = (size_t)f * nlat * nlon;
     ProbState* P = ep.ps + f;
     if (ep.mode == EPI_UPDATE) {
-      if (!P->active) continue;
+      if (!P->active) {
+        if (ep.xout) {   // frozen problem: transform the stored scaling
+          for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
+            const int r = idx >= N ? 1 : 0, k = idx - r * N;
+            const float u = ep.out[fbase + (size_t)(r ? J : j) * nlon + k];
+            float2* ob = other + pidx(q * N + k);
+            if (r == 0) {
+              if (nrings == 1) *ob = make_float2(u, 0.f);
+              else ob->x = u;
+            } else {
+              ob->y = u;
+            }
+          }
+        }
+        continue;
+      }
       const float* mg = ep.marg[f];
       const int bal = P->balanced;
       const float gam = P->gamma, et = P->et;
@@ -179,6 +204,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
         }
         if (!isfinite(u) || !isfinite(kv)) acc[q][3] += 1.f;
         ep.out[fbase + om] = u;
+        if (ep.xout) {
+          float2* ob = other + pidx(q * N + k);
+          if (r == 0) {
+            if (nrings == 1) *ob = make_float2(u, 0.f);
+            else ob->x = u;
+          } else {
+            ob->y = u;
+          }
+        }
       }
     } else if (ep.mode == EPI_CHECK) {
       if (!P->active) continue;
@@ -261,6 +295,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
         ep.part[((size_t)f * nh + jh) * NPART + i] = t;
       }
     }
+  }
+  if (ep.mode == EPI_UPDATE && ep.xout) {
+    // the new scaling of this ring pair is in `other`: transform it for the next half-step
+    __syncthreads();
+    const float2* zf = fft_smem<false>(other, const_cast<float2*>(z), tw, pl, nfg, N);
+    unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc);
   }
 }
 

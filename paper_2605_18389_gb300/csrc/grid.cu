@@ -306,6 +306,8 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   if (nf <= w.nf_cap) return SHOT_OK;
   SHOT_CUDA(cudaStreamSynchronize(st));
   cudaFree(w.XY);
+  cudaFree(w.Yb);
+  w.Yb = nullptr;
   cudaFree(w.C);
   cudaFree(w.part);
   cudaFree(w.probs);
@@ -327,6 +329,8 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   const size_t xy = (size_t)g.nblk * g.nh * ldc;
   const size_t cc = (size_t)g.rows_total * ldc;
   SHOT_CUDA(cudaMalloc(&w.XY, xy * sizeof(float)));
+  SHOT_CUDA(cudaMalloc(&w.Yb, xy * sizeof(float)));
+  SHOT_CUDA(cudaMemsetAsync(w.Yb, 0, xy * sizeof(float), st));
   SHOT_CUDA(cudaMalloc(&w.C, cc * sizeof(float)));
   SHOT_CUDA(cudaMalloc(&w.part, (size_t)nf * g.nh * NPART * sizeof(double)));
   SHOT_CUDA(cudaMalloc(&w.probs, (size_t)nf * sizeof(ProbState)));

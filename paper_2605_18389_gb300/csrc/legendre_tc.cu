@@ -192,6 +192,7 @@ struct AnaArgs {
   int nmma_cap, ldi;
   float* cf;           // optional FP32 [row_off + i][ldc]
   int* err;
+  const ProbState* colscale;   // per-field factor of unscaled spectra (or nullptr)
 };
 
 struct SynArgs {
@@ -381,7 +382,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
             for (int e = 0; e < 16; ++e) {
               const int c = c0 + e;
               if (c < aa.ncols) {
-                const float val = v[e] * hl;
+                const float val = v[e] * hl * (aa.colscale ? (float)aa.colscale[c >> 1].beta : 1.f);
                 const __nv_bfloat16 hi = __float2bfloat16_rn(val);
                 const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
                 const size_t o = ((size_t)blk * aa.nmma_cap + c) * aa.ldi + row;
@@ -512,7 +513,7 @@ static int host_tmem_cols(int n) {
 int tc_supported_fields(int nf) { return tc_nmma(nf) <= 256; }
 
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                       bool apply_h, cudaStream_t st) {
+                       bool apply_h, cudaStream_t st, const ProbState* colscale) {
   const Workspace& w = g.ws;
   const int nmma = tc_nmma(nf);
   if (nmma > 256 || nmma > w.nmma_cap) {
@@ -533,7 +534,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kBM))) return rc;
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
     aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma,
-                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4};
+                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4, colscale};
     auto kern = stages == 3 ? k_legendre_tc<3, true> : stages == 2 ? k_legendre_tc<2, true> : k_legendre_tc<1, true>;
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: both shared memory and the 512 TMEM columns (two accumulators each) must fit

@@ -26,7 +26,6 @@
 
 namespace shot {
 
-int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
 
 namespace {
 

@@ -12,7 +12,6 @@
 namespace shot {
 namespace {
 
-constexpr int kBands = 5;
 
 // per (ring, field): sum_k g and sum_k g^2 of the field form g = grad / a_j
 __global__ void k_ring_moments(int nlat, int nlon, const float* __restrict__ grad, const float* __restrict__ a_ring,

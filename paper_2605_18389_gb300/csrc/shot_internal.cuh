@@ -61,6 +61,7 @@ struct Workspace {
   int nf_cap = 0;       // fields the buffers hold
   int ldc = 0;
   float* XY = nullptr;  // X (analysis input) and Y (synthesis output) share storage
+  float* Yb = nullptr;  // the solver keeps X and Y apart: X survives for the next K application
   float* C = nullptr;
   double* part = nullptr;   // per-(field, ring pair) partial sums [nf][nh][NPART]
   size_t part_cap = 0;
@@ -164,6 +165,8 @@ struct EpiParams {
   double eps;
   int norm_l1;
   int which;                  // 0: u-step (marginal p), 1: v-step (marginal q)
+  float* xout;                // EPI_UPDATE: when set, the CTA also ring-transforms the new
+                              // scaling (unscaled) into the folded spectra xout[.][jh][ldc]
 };
 bool profiling_on();
 
@@ -172,7 +175,8 @@ bool profiling_on();
 int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
                    float* X, int ldc, cudaStream_t st);
 int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
-int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
+int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
+                    const ProbState* colscale = nullptr);
 int launch_heat_mult(const Grid& g, double t, cudaStream_t st);
 int launch_coeff_gather(const Grid& g, const float* C, int ldc, int nf, float* coeffs, cudaStream_t st);
 int launch_coeff_scatter(const Grid& g, const float* coeffs, int nf, float* C, int ldc, cudaStream_t st);
@@ -182,11 +186,11 @@ int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ld
 int build_grid_tables(Grid& g, cudaStream_t st);
 int autotune(Grid& g, int nf, cudaStream_t st);   // selects g.active for nf (tunes on first use)
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                       bool apply_h, cudaStream_t st);
+                       bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
 int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
 int build_recurrence(Grid& g, cudaStream_t st);
 int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
-                        bool apply_h, cudaStream_t st);
+                        bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
 int tc_nmma(int nf);
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
 
