@@ -1,8 +1,10 @@
-"""Gauss-Legendre grid on S^2 (oracle, FP64).  Test infrastructure only.
+"""Iso-latitude grids on S^2 (oracle, FP64).  Test infrastructure only.
 
 Paper: App. C.1 "Gauss-Legendre": the latitudinal samples are the roots of the
-Legendre polynomial P_nlat; longitudes are equispaced.  App. C.2: area weights
-a with a^T 1 = 4 pi, so that int f dsigma ~ a^T f.
+Legendre polynomial P_nlat; "Equiangular ... Clenshaw-Curtis": equally spaced
+colatitudes including both poles, weighted by Clenshaw-Curtis quadrature (the
+paper's main runtime grid, Sec. 4.1); longitudes are equispaced in both.
+App. C.2: area weights a with a^T 1 = 4 pi, so that int f dsigma ~ a^T f.
 
 Conventions (a reading, the paper fixes none): ring j runs north -> south, so
 x_j = cos(theta_j) is DESCENDING; column k has phi_k = 2 pi k / nlon.  The area
@@ -47,16 +49,52 @@ def gauss_legendre(nlat):
     return x, w
 
 
-class Grid:
-    """An nlat x nlon Gauss-Legendre grid, degrees 0..lmax (default nlat-1)."""
+def clenshaw_curtis(nlat):
+    """Nodes x_j = cos(pi j / N), N = nlat - 1 (descending, both poles included),
+    and the Clenshaw-Curtis weights, from their definition: integrate the
+    degree-N polynomial that interpolates f at the nodes.
 
-    def __init__(self, nlat, nlon=None, lmax=None):
+    In the Chebyshev basis the interpolant is sum''_k c_k T_k(x) with
+    c_k = (2/N) sum''_j f_j cos(k j pi / N) (a double prime halves the first and
+    last terms), and int_{-1}^{1} T_k = 2/(1 - k^2) for even k, 0 for odd k.
+    Collecting the coefficient of f_j gives w_j.  Exact for polynomials of
+    degree <= N.
+    """
+    if nlat < 2:
+        raise ValueError("a Clenshaw-Curtis grid needs nlat >= 2")
+    N = nlat - 1
+    j = np.arange(N + 1)
+    x = np.cos(np.pi * j / N)
+    x[N - j[: (N + 1) // 2]] = -x[j[: (N + 1) // 2]]     # exact mirror symmetry
+    if N % 2 == 0:
+        x[N // 2] = 0.0
+    half = np.where((j == 0) | (j == N), 0.5, 1.0)
+    w = np.zeros(N + 1)
+    for k in range(0, N + 1, 2):
+        ck = (2.0 / N) * half * np.cos(np.pi * ((k * j) % (2 * N)) / N)   # d c_k / d f_j
+        wk = 0.5 if k in (0, N) else 1.0
+        w += wk * ck * (2.0 / (1.0 - k * k))
+    w = 0.5 * (w + w[::-1])      # symmetric in exact arithmetic; make it so bitwise
+    return x, w
+
+
+QUADRATURES = {"gl": gauss_legendre, "cc": clenshaw_curtis}
+
+
+class Grid:
+    """An nlat x nlon iso-latitude grid, degrees 0..lmax (default nlat-1).
+
+    quadrature: "gl" (Gauss-Legendre) or "cc" (equiangular, Clenshaw-Curtis).
+    """
+
+    def __init__(self, nlat, nlon=None, lmax=None, quadrature="gl"):
         self.nlat = int(nlat)
         self.nlon = int(nlon) if nlon is not None else 2 * self.nlat
         self.lmax = int(lmax) if lmax is not None else self.nlat - 1
         if self.nlon < 2 * self.lmax + 1:
             raise ValueError("nlon must be >= 2*lmax+1")
-        self.x, self.w = gauss_legendre(self.nlat)
+        self.quadrature = quadrature
+        self.x, self.w = QUADRATURES[quadrature](self.nlat)
         self.theta = np.arccos(self.x)
         self.phi = 2.0 * np.pi * np.arange(self.nlon) / self.nlon
         self.a_ring = self.w * (2.0 * np.pi / self.nlon)

@@ -88,3 +88,16 @@ def test_wrong_gauge_direction_caught(monkeypatch):
     r = sk.sinkhorn(g, p, q, eps=0.1, T=1, C=0)
     monkeypatch.setattr(sk.np, "sum", orig_sum)
     assert abs(r["u"].sum() - 1.0) > 1e-3
+
+
+def test_cc_endpoint_halving_dropped_caught():
+    # Clenshaw-Curtis without halving the end terms of the cosine sums: the pins'
+    # exactness check (int x^2 = 2/3 on 9 nodes) must fail
+    from oracle.grid import clenshaw_curtis
+    x, _ = clenshaw_curtis(9)
+    N = 8
+    j = np.arange(N + 1)
+    w = np.zeros(N + 1)
+    for k in range(0, N + 1, 2):
+        w += (2.0 / N) * np.cos(np.pi * k * j / N) * (2.0 / (1.0 - k * k)) * (0.5 if k in (0, N) else 1.0)
+    assert abs(np.sum(w * x ** 2) - 2.0 / 3.0) > 1e-3
