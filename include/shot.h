@@ -55,6 +55,11 @@ extern "C" {
                                 recurrence from per-(m, node) seeds: O(nlat^2) memory
                                 (SHOT_FP32 grids) */
 
+/* ---- latitudinal quadrature (App. C.1) ----------------------------------- */
+#define SHOT_QUAD_GAUSS_LEGENDRE  0  /* nodes = roots of P_nlat; exact to degree 2 nlat - 1 */
+#define SHOT_QUAD_CLENSHAW_CURTIS 1  /* equiangular theta_j = pi j/(nlat-1), both poles included,
+                                        Clenshaw-Curtis weights; exact to degree nlat - 1 */
+
 /* ---- solver flags -------------------------------------------------------- */
 #define SHOT_FLAG_NORM_L1     0x1  /* check sum_i a_i|u_i(Kv)_i - p_i| / sum_i a_i p_i instead of the relative L2 */
 #define SHOT_FLAG_WARM_START  0x2  /* u and v hold the initial scalings instead of 1 */
@@ -77,13 +82,29 @@ int shot_last_error(char* buf, int len);
 int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision,
                    int legendre_mode, void* stream);
 
+/* Same as shot_grid_init with a choice of latitudinal quadrature (App. C.1):
+ *   quadrature  SHOT_QUAD_GAUSS_LEGENDRE (what shot_grid_init builds) or
+ *               SHOT_QUAD_CLENSHAW_CURTIS: the equiangular grid the paper runs its
+ *               timings on (Sec. 4.1), ring j at colatitude pi j/(nlat-1) (ring 0 the
+ *               north pole, ring nlat-1 the south pole), weights
+ *               w_j = (c_j/N)(1 - sum_{k=1}^{N/2} b_k cos(2 pi k j/N)/(4k^2-1)), N = nlat-1,
+ *               c_j = 1 at the poles and 2 elsewhere, b_k = 1 for k = N/2 and 2 otherwise,
+ *               computed in FP64 on the device.  The heat operator on any node set is
+ *               H diag(a) (the addition theorem), so lmax may go up to nlat-1 as on GL;
+ *               the analysis is an exact inverse of the synthesis only when
+ *               2*lmax <= nlat-1.  Every field-shaped argument of the other calls has the
+ *               same [nlat][nlon] layout on either quadrature.
+ * Other arguments, memory and errors as shot_grid_init; nlat >= 3 for Clenshaw-Curtis. */
+int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int lmax, int precision,
+                        int legendre_mode, void* stream);
+
 /* Release every device resource of the handle (NULL is a no-op). */
 int shot_grid_free(shot_grid g);
 
 /* nlat, nlon, lmax, precision, legendre_mode of the handle (host outputs; any may be NULL). */
 int shot_grid_info(shot_grid g, int* nlat, int* nlon, int* lmax, int* precision, int* legendre_mode);
 
-/* GL nodes x_j (descending) and weights w_j (sum 2) into host arrays of nlat
+/* Nodes x_j = cos(theta_j) (descending) and quadrature weights w_j (sum 2) into host arrays of nlat
  * doubles, and the per-ring area weights a_j = w_j*2*pi/nlon (App. C.2).  Any
  * pointer may be NULL. */
 int shot_grid_nodes(shot_grid g, double* x, double* w, double* a_ring);

@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
+
 #include "shot_internal.cuh"
 
 extern "C" int shot_launch_count(long long* n);
@@ -39,6 +41,10 @@ int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, i
                     const ProbState* colscale) {
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st, colscale);
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st, colscale);
+  if (g.fused_heat) {
+    const int rc = launch_heat_tc(g, nf, X, Y, ldc, st, colscale);
+    if (rc != SHOT_ERR_UNSUPPORTED) return rc;
+  }
   return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st, colscale);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
@@ -67,74 +73,109 @@ __device__ __forceinline__ double wsum(double v) {
 }
 
 // Fixed-order reduction of the per-ring-pair partial sums and the per-problem scalar
-// steps of Alg. 1 (gauge / TI constant / convergence test / objective).
-__global__ void k_reduce(int mode, int nprob, int nh, const double* __restrict__ part, ProbState* ps,
-                         int* dev_int, double eps, double tol, int norm_l1) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// steps of Alg. 1 (gauge / TI constant / convergence test / objective).  One block per
+// problem; the last block to finish (ticket in dev_int[12], reset by that block) counts
+// the problems still active and advances the iteration counter.
+constexpr int kRedThreads = 128;
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int nh, const double* __restrict__ part,
+                                                        ProbState* ps, int* dev_int, double eps, double tol,
+                                                        int norm_l1) {
+  __shared__ double red[kRedThreads / 32][NPART];
+  __shared__ int last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int f = blockIdx.x;
   const int kdone = dev_int[0];
-  for (int f = wid; f < nprob; f += nw) {
-    ProbState* P = ps + f;
-    const bool skip = (mode == RED_FINAL) ? (P->status < 0) : (P->active == 0);
-    if (skip) continue;
+  ProbState* P = ps + f;
+  const bool skip = (mode == RED_FINAL) ? (P->status < 0) : (P->active == 0);
+  if (!skip) {
     double s[NPART] = {0.0, 0.0, 0.0, 0.0};
-    for (int j = lane; j < nh; j += 32) {
-      const double* pt = part + ((size_t)f * nh + j) * NPART;
-#pragma unroll
-      for (int i = 0; i < NPART; ++i) s[i] += pt[i];
+    const double4* pf = reinterpret_cast<const double4*>(part + (size_t)f * nh * NPART);
+    for (int j = threadIdx.x; j < nh; j += kRedThreads) {
+      const double4 a = pf[j];
+      s[0] += a.x;
+      s[1] += a.y;
+      s[2] += a.z;
+      s[3] += a.w;
     }
 #pragma unroll
     for (int i = 0; i < NPART; ++i) s[i] = wsum(s[i]);
-    if (lane != 0) continue;
-    if (mode == RED_U || mode == RED_V) {
-      if (s[2] > 0.0) {
-        P->status = SHOT_ERR_NONPOSITIVE;
-        P->active = 0;
-        P->iters = kdone + 1;
-      } else if (s[3] > 0.0) {
-        P->status = SHOT_ERR_NONFINITE;
-        P->active = 0;
-        P->iters = kdone + 1;
-      } else if (mode == RED_U) {
-        P->su = s[0];
-      } else {
-        double al, be;
-        if (P->balanced) {
-          al = 1.0 / P->su;
-          be = P->su;
-        } else {
-          const double c = 0.5 * P->tau * (log(P->su) - log(s[0]));
-          al = exp(c / eps);
-          be = exp(-c / eps);
-        }
-        if (!(isfinite(al) && isfinite(be) && al > 0.0 && be > 0.0)) {
+    if (lane == 0)
+#pragma unroll
+      for (int i = 0; i < NPART; ++i) red[wid][i] = s[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int i = 0; i < NPART; ++i) {
+        double t = 0.0;
+        for (int w = 0; w < kRedThreads / 32; ++w) t += red[w][i];
+        s[i] = t;
+      }
+      if (mode == RED_U || mode == RED_V) {
+        if (s[2] > 0.0) {
+          P->status = SHOT_ERR_NONPOSITIVE;
+          P->active = 0;
+          P->iters = kdone + 1;
+        } else if (s[3] > 0.0) {
           P->status = SHOT_ERR_NONFINITE;
           P->active = 0;
           P->iters = kdone + 1;
+        } else if (mode == RED_U) {
+          P->su = s[0];
         } else {
-          P->alpha = al;
-          P->beta = be;
+          double al, be;
+          if (P->balanced) {
+            al = 1.0 / P->su;
+            be = P->su;
+          } else {
+            const double c = 0.5 * P->tau * (log(P->su) - log(s[0]));
+            al = exp(c / eps);
+            be = exp(-c / eps);
+          }
+          if (!(isfinite(al) && isfinite(be) && al > 0.0 && be > 0.0)) {
+            P->status = SHOT_ERR_NONFINITE;
+            P->active = 0;
+            P->iters = kdone + 1;
+          } else {
+            P->alpha = al;
+            P->beta = be;
+          }
         }
+      } else if (mode == RED_CHECK) {
+        const double e = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
+        P->err = e;
+        if (e < tol) {
+          P->active = 0;
+          P->iters = kdone;
+        }
+      } else {
+        P->err = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
+        P->mass = s[2];
+        P->ot = s[3];
+        P->ot_dual = s[3] - eps * s[2];
       }
-    } else if (mode == RED_CHECK) {
-      const double e = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
-      P->err = e;
-      if (e < tol) {
-        P->active = 0;
-        P->iters = kdone;
-      }
-    } else {
-      P->err = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
-      P->mass = s[2];
-      P->ot = s[3];
-      P->ot_dual = s[3] - eps * s[2];
     }
   }
+  // last block: count the active problems (all blocks' updates are visible after the fence)
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = (atomicAdd(&dev_int[12], 1) == nprob - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  int na = 0;
+  for (int g = threadIdx.x; g < nprob; g += kRedThreads) na += *(volatile int*)&ps[g].active;
+  na = __reduce_add_sync(0xffffffffu, na);
+  __shared__ int wna[kRedThreads / 32];
+  if (lane == 0) wna[wid] = na;
   __syncthreads();
   if (threadIdx.x == 0) {
+    int t = 0;
+    for (int w = 0; w < kRedThreads / 32; ++w) t += wna[w];
     if (mode == RED_V) dev_int[0] = kdone + 1;
-    int na = 0;
-    for (int f = 0; f < nprob; ++f) na += ps[f].active;
-    dev_int[1] = na;
+    dev_int[1] = t;
+    dev_int[12] = 0;
   }
 }
 
@@ -161,6 +202,7 @@ __global__ void k_init_probs(int nprob, ProbState* ps, int* dev_int, const doubl
   if (f == 0) {
     dev_int[0] = 0;
     dev_int[1] = nprob;
+    dev_int[12] = 0;   // k_reduce's ticket
   }
 }
 
@@ -220,7 +262,7 @@ int heat_pipeline(Grid& g, const float* in, int nf, int scale_which, cudaStream_
 int reduce(Grid& g, int mode, int nprob, double eps, double tol, int norm_l1, cudaStream_t st) {
   ProfScope prof(PK_OTHER, st);
   count_launch();
-  k_reduce<<<1, 256, 0, st>>>(mode, nprob, g.nh, g.ws.part, reinterpret_cast<ProbState*>(g.ws.probs),
+  k_reduce<<<nprob, kRedThreads, 0, st>>>(mode, nprob, g.nh, g.ws.part, reinterpret_cast<ProbState*>(g.ws.probs),
                               g.ws.dev_int, eps, tol, norm_l1);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
@@ -546,8 +588,21 @@ int shot_last_error(char* buf, int len) {
 
 int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision, int legendre_mode,
                    void* stream) {
+  return shot_grid_init_quad(out, SHOT_QUAD_GAUSS_LEGENDRE, nlat, nlon, lmax, precision, legendre_mode, stream);
+}
+
+int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int lmax, int precision,
+                        int legendre_mode, void* stream) {
   if (!out) { set_error("out is NULL"); return SHOT_ERR_INVALID_ARG; }
   *out = nullptr;
+  if (quadrature != SHOT_QUAD_GAUSS_LEGENDRE && quadrature != SHOT_QUAD_CLENSHAW_CURTIS) {
+    set_error("unknown quadrature");
+    return SHOT_ERR_INVALID_ARG;
+  }
+  if (quadrature == SHOT_QUAD_CLENSHAW_CURTIS && nlat < 3) {
+    set_error("a Clenshaw-Curtis grid needs nlat >= 3");
+    return SHOT_ERR_INVALID_ARG;
+  }
   if (lmax == -1) lmax = nlat - 1;
   if (nlat < 2 || lmax < 0 || lmax > nlat - 1 || nlon < 2 * lmax + 1) {
     set_error("need nlat >= 2, 0 <= lmax <= nlat-1, nlon >= 2*lmax+1");
@@ -571,6 +626,11 @@ int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision, 
   g->nh = (nlat + 1) / 2;
   g->precision = precision;
   g->mode = legendre_mode;
+  g->quad = quadrature;
+  {  // SHOT_FUSED_HEAT=1 selects the fused per-order analysis + synthesis kernel (BF16X3)
+    const char* e = getenv("SHOT_FUSED_HEAT");
+    g->fused_heat = (e && e[0] == '1') ? 1 : 0;
+  }
   g->plan = plan;
   cudaGetDevice(&g->dev);
   cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->dev);
@@ -586,7 +646,7 @@ int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision, 
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi,
+  void* dptr[] = {g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi,
                   g->tabT_lo,
                   g->ws.ct_hi, g->ws.ct_lo, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,

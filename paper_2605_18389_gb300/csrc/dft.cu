@@ -23,6 +23,19 @@ namespace shot {
 namespace {
 
 constexpr int kThreads = kFftThreads;
+constexpr int kEpiBatch = 6;   // longitudes per thread whose marginal values are loaded together
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -33,15 +46,12 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // Loads rings j (real part) and J = nlat-1-j (imaginary part) of nfg fields into buf.
 __device__ __forceinline__ void load_ring_pairs(const float* __restrict__ in, float2* buf, int f0, int nfg,
                                                 int nlat, int nlon, int j, int J) {
-  const int N = nlon;
-  float* bf = reinterpret_cast<float*>(buf);
+  const int N = nlon, ld = seq_ld(N);
   for (int q = 0; q < nfg; ++q) {
     const float* fj = in + (size_t)(f0 + q) * nlat * nlon + (size_t)j * nlon;
     const float* fJ = in + (size_t)(f0 + q) * nlat * nlon + (size_t)J * nlon;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-      bf[2 * pidx(q * N + k)] = __ldg(fj + k);
-      bf[2 * pidx(q * N + k) + 1] = (J != j) ? __ldg(fJ + k) : 0.f;
-    }
+    for (int k = threadIdx.x; k < N; k += blockDim.x)
+      buf[q * ld + k] = make_float2(__ldg(fj + k), (J != j) ? __ldg(fJ + k) : 0.f);
   }
 }
 
@@ -52,15 +62,15 @@ template <int FG>
 __device__ __forceinline__ void unpack_fold_store(const float2* buf, int nfg, int f0, int N, int lmax, int nh, int jh,
                                                   float aj, const ProbState* __restrict__ ps, int scale_which,
                                                   float* __restrict__ X, int ldc) {
-  const int nm = lmax + 1;
+  const int nm = lmax + 1, ld = seq_ld(N);
   for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
     if (q >= nfg) continue;
     const int f = f0 + q;
     float sc = aj;
     if (scale_which == 1) sc *= (float)ps[f].beta;
-    const float2 zm = buf[pidx(q * N + m)];
-    const float2 zn = buf[pidx(q * N + (m ? N - m : 0))];
+    const float2 zm = buf[q * ld + m];
+    const float2 zn = buf[q * ld + (m ? N - m : 0)];
     const float2 FN = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
     const float2 FS = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
     const float2 S = make_float2(sc * (FN.x + FS.x), sc * (FN.y + FS.y));
@@ -71,15 +81,15 @@ __device__ __forceinline__ void unpack_fold_store(const float2* buf, int nfg, in
 }
 
 template <int FG>
-__global__ void __launch_bounds__(kThreads, 2) k_dft_fwd(
+__global__ void __launch_bounds__(kThreads, 3) k_dft_fwd(
     const float* __restrict__ in, int nf, int nlat, int nlon, int lmax, int nh,
     const float* __restrict__ a_ring, const ProbState* __restrict__ ps, int scale_which,
     float* __restrict__ X, int ldc, FftPlan pl, const float2* __restrict__ tw_g) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   const int N = nlon;
-  float2* tw = sm;
-  float2* b0 = sm + N;
-  float2* b1 = b0 + padded_len(FG * N);
+  float2* b0 = sm;
+  float2* b1 = b0 + FG * seq_ld(N);
+  float2* tw = b1 + FG * seq_ld(N);
   const int jh = blockIdx.y;
   const int f0 = blockIdx.x * FG;
   const int nfg = min(FG, nf - f0);
@@ -88,68 +98,87 @@ __global__ void __launch_bounds__(kThreads, 2) k_dft_fwd(
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
   load_ring_pairs(in, b0, f0, nfg, nlat, nlon, j, J);
   __syncthreads();
-  const float2* buf = fft_smem<false>(b0, b1, tw, pl, nfg, N);
+  const float2* buf = fft_smem<false>(b0, b1, tw, pl, nfg);
 
   unpack_fold_store<FG>(buf, nfg, f0, N, lmax, nh, jh, a_ring[j], ps, scale_which, X, ldc);
 }
 
 template <int FG>
-__global__ void __launch_bounds__(kThreads, 2) k_idft(
+__global__ void __launch_bounds__(kThreads, 3) k_idft(
     const float* __restrict__ Y, int ldc, int nf, int nlat, int nlon, int lmax, int nh,
     const float* __restrict__ a_ring, FftPlan pl, const float2* __restrict__ tw_g, EpiParams ep) {
-  extern __shared__ float2 sm[];
+  extern __shared__ __align__(16) float2 sm[];
   __shared__ float red[kThreads / 32][FG * NPART];
   const int N = nlon;
-  float2* tw = sm;
-  float2* buf = sm + N;
-  float2* b1 = buf + padded_len(FG * N);
+  const int ld = seq_ld(N);
+  float2* buf = sm;
+  float2* b1 = buf + FG * ld;
+  float2* tw = b1 + FG * ld;
   const int jh = blockIdx.y;
   const int f0 = blockIdx.x * FG;
   const int nfg = min(FG, nf - f0);
   const int j = jh, J = nlat - 1 - jh;
 
+  // Gather this ring pair's spectra of the CTA's fields, E_m and O_m for every order (the
+  // (2m+1) block of m = lmax is empty), into b1 with asynchronous copies: all of them are
+  // in flight at once.  Row (blk, jh) holds the fields' (re, im) pairs contiguously; a
+  // field group of even size starts on a 16-byte boundary (ldc is a multiple of 4), and
+  // reading up to the next even field stays inside the row.
+  float2* stg = b1;   // stg[blk * FG + q]
+  const int nblk_v = 2 * lmax + 1;
+  if (FG % 2 == 0) {
+    constexpr int ch = FG / 2;
+    for (int e = threadIdx.x; e < nblk_v * ch; e += blockDim.x) {
+      const int blk = e / ch, c = e - blk * ch;
+      if (2 * c < nfg) cp_async16(stg + blk * FG + 2 * c, Y + ((size_t)blk * nh + jh) * ldc + 2 * f0 + 4 * c);
+    }
+  } else {
+    for (int blk = threadIdx.x; blk < nblk_v; blk += blockDim.x)
+      cp_async8(stg + blk * FG, Y + ((size_t)blk * nh + jh) * ldc + 2 * f0);
+  }
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
   // zero the band lmax < m < N - lmax
   const int nz = N - 2 * lmax - 1;
   for (int q = 0; q < nfg; ++q)
-    for (int k = threadIdx.x; k < nz; k += blockDim.x) buf[pidx(q * N + lmax + 1 + k)] = make_float2(0.f, 0.f);
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) buf[q * ld + lmax + 1 + k] = make_float2(0.f, 0.f);
+  cp_async_wait_all();
+  __syncthreads();
   const int nm = lmax + 1;
   for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
     if (q >= nfg) continue;
-    const int f = f0 + q;
-    const float2 E = *reinterpret_cast<const float2*>(Y + ((size_t)(2 * m) * nh + jh) * ldc + 2 * f);
-    float2 O = make_float2(0.f, 0.f);
-    if (m < lmax) O = *reinterpret_cast<const float2*>(Y + ((size_t)(2 * m + 1) * nh + jh) * ldc + 2 * f);
+    const float2 E = stg[(2 * m) * FG + q];
+    const float2 O = (m < lmax) ? stg[(2 * m + 1) * FG + q] : make_float2(0.f, 0.f);
     const float2 GN = make_float2(E.x + O.x, E.y + O.y);
     const float2 GS = make_float2(E.x - O.x, E.y - O.y);
     if (m == 0) {
-      buf[pidx(q * N)] = make_float2(GN.x, GS.x);
+      buf[q * ld] = make_float2(GN.x, GS.x);
     } else {
-      buf[pidx(q * N + m)] = make_float2(GN.x - GS.y, GN.y + GS.x);
-      buf[pidx(q * N + N - m)] = make_float2(GN.x + GS.y, GS.x - GN.y);
+      buf[q * ld + m] = make_float2(GN.x - GS.y, GN.y + GS.x);
+      buf[q * ld + N - m] = make_float2(GN.x + GS.y, GS.x - GN.y);
     }
   }
   __syncthreads();
-  const float2* z = fft_smem<true>(buf, b1, tw, pl, nfg, N);
+  const float2* z = fft_smem<true>(buf, b1, tw, pl, nfg);
   float2* other = (z == buf) ? b1 : buf;   // input of the fused forward transform
 
   const float aj = a_ring[j];
-  const int nrings = (J != j) ? 2 : 1;
+  const bool two = (J != j);   // false only for the equator ring of an odd grid
   if (ep.mode == EPI_PLAIN) {
     for (int q = 0; q < nfg; ++q) {
       float* oj = ep.out + (size_t)(f0 + q) * nlat * nlon + (size_t)j * nlon;
       float* oJ = ep.out + (size_t)(f0 + q) * nlat * nlon + (size_t)J * nlon;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const float2 zz = z[pidx(q * N + k)];
+        const float2 zz = z[q * ld + k];
         oj[k] = zz.x;
-        if (J != j) oJ[k] = zz.y;
+        if (two) oJ[k] = zz.y;
       }
     }
     return;
   }
-  // Per-element arithmetic is FP32; every thread sums its few elements (<= nrings*N/512
-  // per field) in FP32, warps reduce in FP32 and the cross-warp / grid sums are FP64.
+  // Per-element arithmetic is FP32; every thread sums its few elements (<= 2N/512 per
+  // field) in FP32, warps reduce in FP32 and the cross-warp / grid sums are FP64.  A
+  // thread takes longitude k of both rings of the pair.
   float acc[FG][NPART];
 #pragma unroll
   for (int q = 0; q < FG; ++q)
@@ -161,76 +190,82 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
     if (q >= nfg) break;
     const int f = f0 + q;
     const size_t fbase = (size_t)f * nlat * nlon;
+    const size_t rj = (size_t)j * nlon, rJ = (size_t)J * nlon;   // ring offsets within a field
+    float* outf = ep.out + fbase;
+    float* othf = ep.other ? ep.other + fbase : nullptr;
     ProbState* P = ep.ps + f;
     if (ep.mode == EPI_UPDATE) {
       if (!P->active) {
         if (ep.xout) {   // frozen problem: transform the stored scaling
-          for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
-            const int r = idx >= N ? 1 : 0, k = idx - r * N;
-            const float u = ep.out[fbase + (size_t)(r ? J : j) * nlon + k];
-            float2* ob = other + pidx(q * N + k);
-            if (r == 0) {
-              if (nrings == 1) *ob = make_float2(u, 0.f);
-              else ob->x = u;
-            } else {
-              ob->y = u;
-            }
-          }
+          for (int k = threadIdx.x; k < N; k += blockDim.x)
+            other[q * ld + k] = make_float2(outf[rj + k], two ? outf[rJ + k] : 0.f);
         }
         continue;
       }
       const float* mg = ep.marg[f];
       const int bal = P->balanced;
       const float gam = P->gamma, et = P->et;
-      for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
-        const int r = idx >= N ? 1 : 0, k = idx - r * N;
-        const float2 zz = z[pidx(q * N + k)];
-        const float kv = r ? zz.y : zz.x;
-        const size_t om = (size_t)(r ? J : j) * nlon + k;
-        const float pm = __ldg(mg + om);
-        const float ratio = pm / kv;
-        float u;
-        if (bal) {
-          u = ratio;
-          acc[q][0] += u;
-        } else {
-          // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}
-          u = powf(ratio, gam);
-          if (pm > 0.f) acc[q][0] += aj * pm * powf(ratio, -et);
+      for (int k0 = threadIdx.x; k0 < N; k0 += kEpiBatch * kThreads) {
+        // the marginal values of all this thread's longitudes first, then the arithmetic
+        float pv[kEpiBatch][2];
+#pragma unroll
+        for (int b = 0; b < kEpiBatch; ++b) {
+          const int k = k0 + b * kThreads;
+          pv[b][0] = (k < N) ? __ldg(mg + rj + k) : 0.f;
+          pv[b][1] = (k < N && two) ? __ldg(mg + rJ + k) : 0.f;
         }
-        if (!(kv > 0.f)) {
-          if (kv <= 0.f) acc[q][2] += 1.f;
-          else acc[q][3] += 1.f;   // NaN
-        }
-        if (!isfinite(u) || !isfinite(kv)) acc[q][3] += 1.f;
-        ep.out[fbase + om] = u;
-        if (ep.xout) {
-          float2* ob = other + pidx(q * N + k);
-          if (r == 0) {
-            if (nrings == 1) *ob = make_float2(u, 0.f);
-            else ob->x = u;
-          } else {
-            ob->y = u;
+#pragma unroll
+        for (int b = 0; b < kEpiBatch; ++b) {
+          const int k = k0 + b * kThreads;
+          if (k >= N) break;
+          const float2 zz = z[q * ld + k];
+          float u2[2];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            if (r == 1 && !two) { u2[1] = 0.f; break; }
+            const float kv = r ? zz.y : zz.x;
+            const float pm = pv[b][r];
+            const float ratio = pm / kv;
+            float u;
+            if (bal) {
+              u = ratio;
+              acc[q][0] += u;
+            } else {
+              // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}
+              u = powf(ratio, gam);
+              if (pm > 0.f) acc[q][0] += aj * pm * powf(ratio, -et);
+            }
+            if (!(kv > 0.f)) {
+              if (kv <= 0.f) acc[q][2] += 1.f;
+              else acc[q][3] += 1.f;   // NaN
+            }
+            if (!isfinite(u) || !isfinite(kv)) acc[q][3] += 1.f;
+            outf[(r ? rJ : rj) + k] = u;
+            u2[r] = u;
           }
+          if (ep.xout) other[q * ld + k] = make_float2(u2[0], u2[1]);
         }
       }
     } else if (ep.mode == EPI_CHECK) {
       if (!P->active) continue;
       const float* mg = ep.marg[f];
       const float al = (float)P->alpha;
-      for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
-        const int r = idx >= N ? 1 : 0, k = idx - r * N;
-        const float2 zz = z[pidx(q * N + k)];
-        const float kv = r ? zz.y : zz.x;
-        const size_t om = (size_t)(r ? J : j) * nlon + k;
-        const float pm = __ldg(mg + om);
-        const float d = fmaf(al * ep.other[fbase + om], kv, -pm);
-        if (ep.norm_l1) {
-          acc[q][0] += aj * fabsf(d);
-          acc[q][1] += aj * pm;
-        } else {
-          acc[q][0] += d * d;
-          acc[q][1] += pm * pm;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float2 zz = z[q * ld + k];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (r == 1 && !two) break;
+          const float kv = r ? zz.y : zz.x;
+          const size_t o = (r ? rJ : rj) + k;
+          const float pm = __ldg(mg + o);
+          const float d = fmaf(al * othf[o], kv, -pm);
+          if (ep.norm_l1) {
+            acc[q][0] += aj * fabsf(d);
+            acc[q][1] += aj * pm;
+          } else {
+            acc[q][0] += d * d;
+            acc[q][1] += pm * pm;
+          }
         }
       }
     } else {  // EPI_FINAL: z = K v_true; ep.other = u buffer, ep.out = v buffer
@@ -240,36 +275,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
       const float al = (float)P->alpha, be = (float)P->beta;
       const int bal = P->balanced;
       const float epsf = (float)ep.eps, tauf = (float)P->tau, et = bal ? 0.f : (float)(ep.eps / P->tau);
-      for (int idx = threadIdx.x; idx < nrings * N; idx += blockDim.x) {
-        const int r = idx >= N ? 1 : 0, k = idx - r * N;
-        const float2 zz = z[pidx(q * N + k)];
-        const float kv = r ? zz.y : zz.x;
-        const size_t om = (size_t)(r ? J : j) * nlon + k;
-        const size_t o = fbase + om;
-        const float pm = __ldg(pp + om), qm = __ldg(qq + om);
-        const float uu = al * ep.other[o];
-        const float vv = be * ep.out[o];
-        ep.other[o] = uu;
-        ep.out[o] = vv;
-        const float d = fmaf(uu, kv, -pm);
-        if (ep.norm_l1) {
-          acc[q][0] += aj * fabsf(d);
-          acc[q][1] += aj * pm;
-        } else {
-          acc[q][0] += d * d;
-          acc[q][1] += pm * pm;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float2 zz = z[q * ld + k];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (r == 1 && !two) break;
+          const float kv = r ? zz.y : zz.x;
+          const size_t o = (r ? rJ : rj) + k;
+          const float pm = __ldg(pp + o), qm = __ldg(qq + o);
+          const float uu = al * othf[o];
+          const float vv = be * outf[o];
+          othf[o] = uu;
+          outf[o] = vv;
+          const float d = fmaf(uu, kv, -pm);
+          if (ep.norm_l1) {
+            acc[q][0] += aj * fabsf(d);
+            acc[q][1] += aj * pm;
+          } else {
+            acc[q][0] += d * d;
+            acc[q][1] += pm * pm;
+          }
+          acc[q][2] += aj * uu * kv;
+          // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
+          const float lu = logf(uu), lv = logf(vv);
+          float t;
+          if (bal) {
+            t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);
+          } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u)
+            t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
+                (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
+          }
+          acc[q][3] += aj * t;
         }
-        acc[q][2] += aj * uu * kv;
-        // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
-        const float lu = logf(uu), lv = logf(vv);
-        float t;
-        if (bal) {
-          t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);
-        } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u)
-          t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
-              (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
-        }
-        acc[q][3] += aj * t;
       }
     }
   }
@@ -299,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft(
   if (ep.mode == EPI_UPDATE && ep.xout) {
     // the new scaling of this ring pair is in `other`: transform it for the next half-step
     __syncthreads();
-    const float2* zf = fft_smem<false>(other, const_cast<float2*>(z), tw, pl, nfg, N);
+    const float2* zf = fft_smem<false>(other, const_cast<float2*>(z), tw, pl, nfg);
     unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc);
   }
 }
@@ -313,7 +350,7 @@ int pick_fg(int N, int nf) {
 template <int FG>
 int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which, float* X,
                  int ldc, cudaStream_t st) {
-  const size_t smem = (size_t)(g.nlon + 2 * padded_len(FG * g.nlon)) * sizeof(float2);
+  const size_t smem = (size_t)(g.nlon + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
   SHOT_CUDA(cudaFuncSetAttribute(k_dft_fwd<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
   ProfScope prof(PK_DFT, st);
@@ -326,7 +363,8 @@ int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, in
 
 template <int FG>
 int launch_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
-  const size_t smem = (size_t)(g.nlon + 2 * padded_len(FG * g.nlon)) * sizeof(float2);
+  // two sequence buffers (the second also stages the gathered spectra) and the twiddles
+  const size_t smem = (size_t)(g.nlon + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
   SHOT_CUDA(cudaFuncSetAttribute(k_idft<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
   ProfScope prof(PK_IDFT, st);

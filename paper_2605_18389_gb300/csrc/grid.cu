@@ -5,6 +5,9 @@
 // values being rounded to FP32 (or split into bf16 hi + lo) for the hot path.
 #include <math.h>
 #include <algorithm>
+#include <cmath>
+#include <functional>
+#include <vector>
 
 #include "shot_internal.cuh"
 
@@ -52,12 +55,32 @@ __global__ void k_gl_nodes(int n, double* __restrict__ x, double* __restrict__ w
   w[n - 1 - j] = wj;
 }
 
-__global__ void k_twiddles(int N, float2* __restrict__ tw) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  double s, c;
-  sincospi(2.0 * k / N, &s, &c);
-  tw[k] = make_float2((float)c, (float)-s);
+// Equiangular Clenshaw-Curtis nodes x_j = cos(pi j/N), N = n-1, both poles included
+// (App. C.1, "Equiangular ... Clenshaw-Curtis"), and the closed-form weights of the
+// degree-N interpolatory rule on them:
+//   w_j = (c_j/N) (1 - sum_{k=1}^{floor(N/2)} b_k cos(2 pi k j / N) / (4k^2 - 1)),
+// c_j = 1 for j in {0, N} else 2, b_k = 1 for k = N/2 else 2.  The cosine argument is
+// reduced exactly (k j mod N) before sincospi.  One thread per north-half node; the
+// south half is its exact mirror.
+__global__ void k_cc_nodes(int n, double* __restrict__ x, double* __restrict__ w) {
+  const int nh = (n + 1) / 2;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nh) return;
+  const int N = n - 1;
+  double xj = cospi((double)j / N);
+  if (2 * j == N) xj = 0.0;   // the equator ring of an odd grid
+  double s = 0.0;
+  for (int k = 1; 2 * k <= N; ++k) {
+    const long long r = ((long long)k * j) % N;
+    const double bk = (2 * k == N) ? 1.0 : 2.0;
+    s += bk * cospi(2.0 * (double)r / N) / (4.0 * k * k - 1.0);
+  }
+  const double cj = (j == 0) ? 1.0 : 2.0;
+  const double wj = cj / N * (1.0 - s);
+  x[j] = xj;
+  w[j] = wj;
+  x[n - 1 - j] = -xj;
+  w[n - 1 - j] = wj;
 }
 
 __global__ void k_area(int nlat, int nlon, const double* __restrict__ w, float* __restrict__ a) {
@@ -158,31 +181,85 @@ __global__ void k_coeff_scatter(int lmax, int nf, const long long* __restrict__ 
 
 }  // namespace
 
+// Factorisation of the ring length into the radices the shared-memory FFT has
+// butterflies for.  Fewest stages first; then the bank conflicts of the first stage's
+// stores (lanes at a stride of R complex values: conflict-free for odd R, gcd(2R, 32)/2-way
+// otherwise), which puts an odd radix first when there is one and otherwise the smallest;
+// then the smallest largest radix (registers).
 bool make_fft_plan(int N, FftPlan* pl) {
-  pl->N = N;
-  pl->nst = 0;
-  int n = N;
-  auto push = [&](int r) {
-    if (pl->nst >= 12) return false;
-    pl->R[pl->nst++] = r;
-    n /= r;
-    return true;
+  if (N < 1 || N >= (1 << 16)) return false;
+  static const int kRad[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+  const int nrad = (int)(sizeof(kRad) / sizeof(kRad[0]));
+  auto order = [](std::vector<int> f) {
+    std::vector<int> odd, even;
+    for (int r : f) (r & 1 ? odd : even).push_back(r);
+    std::sort(odd.rbegin(), odd.rend());
+    std::sort(even.begin(), even.end());
+    odd.insert(odd.end(), even.begin(), even.end());
+    return odd;
   };
-  while (n % 8 == 0) if (!push(8)) return false;
-  while (n % 4 == 0) if (!push(4)) return false;
-  while (n % 2 == 0) if (!push(2)) return false;
-  while (n % 3 == 0) if (!push(3)) return false;
-  while (n % 5 == 0) if (!push(5)) return false;
-  if (n != 1 || N < 1 || N >= (1 << 16)) return false;
+  auto cost = [](const std::vector<int>& f) {
+    if (f.empty()) return 0.0;
+    int g = 2 * f[0], b = 32;
+    while (b) { const int t = g % b; g = b; b = t; }
+    const int deg = (f[0] & 1) ? 1 : g / 2;
+    const int mx = *std::max_element(f.begin(), f.end());
+    return (double)f.size() + 0.15 * (deg - 1) + 0.01 * mx;
+  };
+  std::vector<int> best, cur;
+  double best_cost = 1e30;
+  bool found = false;
+  // multisets in non-increasing radix-table order
+  std::function<void(int, int)> dfs = [&](int n, int from) {
+    if (n == 1) {
+      const std::vector<int> f = order(cur);
+      const double c = cost(f);
+      if (!found || c < best_cost) { best = f; best_cost = c; found = true; }
+      return;
+    }
+    if ((int)cur.size() >= 16) return;
+    for (int i = from; i < nrad; ++i)
+      if (n % kRad[i] == 0) {
+        cur.push_back(kRad[i]);
+        dfs(n / kRad[i], i);
+        cur.pop_back();
+      }
+  };
+  dfs(N, 0);
+  if (!found) return false;
+  pl->N = N;
+  pl->nst = (int)best.size();
   // exact division by multiply-high for operands below 2^16
   auto mul = [](uint32_t d) -> uint32_t { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + d - 1) / d); };
-  int Ns = 1;
+  int Ns = 1, off = 0;
   for (int s = 0; s < pl->nst; ++s) {
+    pl->R[s] = best[s];
+    pl->tw_off[s] = off;
     pl->ns_mul[s] = mul((uint32_t)Ns);
     pl->nr_mul[s] = mul((uint32_t)(N / pl->R[s]));
+    if (s > 0) off += (pl->R[s] - 1) * Ns;
     Ns *= pl->R[s];
   }
   return true;
+}
+
+void fft_plan_twiddles(const FftPlan& pl, std::vector<float2>& tw) {
+  const int N = pl.N;
+  tw.assign(N, make_float2(1.f, 0.f));
+  int Ns = 1;
+  for (int s = 0; s < pl.nst; ++s) {
+    const int R = pl.R[s];
+    if (s > 0) {
+      const long long tstep = N / (Ns * R);
+      for (int r = 1; r < R; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          const long long e = ((long long)k * r * tstep) % N;   // exact index reduction
+          const double a = 2.0 * M_PI * (double)e / N;
+          tw[pl.tw_off[s] + (r - 1) * Ns + k] = make_float2((float)std::cos(a), (float)-std::sin(a));
+        }
+    }
+    Ns *= R;
+  }
 }
 
 int build_grid_tables(Grid& g, cudaStream_t st) {
@@ -192,12 +269,20 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   SHOT_CUDA(cudaMalloc(&g.a_d, nlat * sizeof(float)));
   SHOT_CUDA(cudaMalloc(&g.tw_d, g.nlon * sizeof(float2)));
   SHOT_CUDA(cudaMalloc(&g.h_d, L * sizeof(float)));
-  count_launch(5);
-  k_gl_nodes<<<(nh + 127) / 128, 128, 0, st>>>(nlat, g.x_d, g.w_d);
-  k_twiddles<<<(g.nlon + 255) / 256, 256, 0, st>>>(g.nlon, g.tw_d);
+  count_launch(3);
+  if (g.quad == SHOT_QUAD_CLENSHAW_CURTIS)
+    k_cc_nodes<<<(nh + 127) / 128, 128, 0, st>>>(nlat, g.x_d, g.w_d);
+  else
+    k_gl_nodes<<<(nh + 127) / 128, 128, 0, st>>>(nlat, g.x_d, g.w_d);
   k_area<<<(nlat + 255) / 256, 256, 0, st>>>(nlat, g.nlon, g.w_d, g.a_d);
   k_heat<<<(L + 255) / 256, 256, 0, st>>>(g.lmax, 0.0, g.h_d);
   SHOT_CUDA(cudaGetLastError());
+  {
+    std::vector<float2> tw;
+    fft_plan_twiddles(g.plan, tw);
+    SHOT_CUDA(cudaMemcpyAsync(g.tw_d, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    SHOT_CUDA(cudaStreamSynchronize(st));   // tw is a local
+  }
 
   // blocks (m, p): rows M = (lmax - m - p)/2 + 1 when lmax - m - p >= 0
   g.nblk = 2 * L;
@@ -254,6 +339,18 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
     for (int r = 0; r < g.M[b]; r += g.bm_ana) ta.push_back({b, r});
     if (g.M[b] > 0)
       for (int r = 0; r < nh; r += g.bm_syn) ts.push_back({b, r});
+  }
+  {  // blocks with rows, largest first, for the fused heat kernel
+    std::vector<int> ord;
+    for (int b = 0; b < g.nblk; ++b)
+      if (g.M[b] > 0) ord.push_back(b);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return g.M[a] > g.M[b]; });
+    g.nwork = (int)ord.size();
+    g.nmt_max = (g.M[0] + g.bm_ana - 1) / g.bm_ana;
+    g.kc_max = (g.M[0] + 63) / 64;
+    SHOT_CUDA(cudaMalloc(&g.blk_order_d, ord.size() * sizeof(int)));
+    SHOT_CUDA(cudaMemcpyAsync(g.blk_order_d, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    SHOT_CUDA(cudaStreamSynchronize(st));   // ord is a local
   }
   // largest contraction first (synthesis work is proportional to M)
   std::stable_sort(ts.begin(), ts.end(), [&](const Tile& a, const Tile& b) { return g.M[a.blk] > g.M[b.blk]; });

@@ -151,6 +151,22 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Shared-memory matrix descriptor: MN-major operand (the M or N index contiguous), 128-byte
+// swizzle.  The tile is a stack of 1 KB atoms of 8 K-rows x 64 MN elements; lbo is the
+// byte distance between atoms along MN, sbo between the 8-row groups along K.
+__device__ __forceinline__ uint64_t desc_sw128_mnmajor(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// kind::f16 instruction descriptor with an MN-major A operand (B K-major)
+__host__ __device__ constexpr uint32_t idesc_bf16_amn(int M, int N) { return idesc_bf16(M, N) | (1u << 15); }
+
 __device__ __forceinline__ uint32_t tmem_cols_for(int n) {
   uint32_t c = 32;
   while ((int)c < n) c <<= 1;
@@ -424,6 +440,339 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
   if (threadIdx.x == 0 && ctl.abort) atomicExch(ANA ? aa.err : sa.err, SHOT_ERR_TIMEOUT);
 }
 
+
+// ---------------------------------------------------------------------------------
+// Fused heat application per (m, parity) block: the analysis of the block (all its
+// 128-row tiles), h_l and the per-field gauge factor in the epilogue, the coefficients
+// kept in shared memory as the bf16 hi/lo B operand, then the synthesis of the block
+// (all its 128-node tiles) with the SAME table tiles read as an MN-major A operand:
+//   analysis   C[i][c] = h_l sum_jh Pbar[i][jh] X[jh][c]      A = Pbar (K = jh contiguous)
+//   synthesis  Y[jh][c] = sum_i Pbar[i][jh] C[i][c]            A = Pbar^T (M = jh contiguous)
+// The second read of each table tile comes shortly after the first, from L2, so the table
+// streams from HBM once per heat application, and no coefficients go through global memory.
+// Roles as in k_legendre_tc; a persistent CTA takes whole blocks, largest first, in
+// snake order over the grid.
+constexpr int kMaxSlots = 8;   // TMEM accumulators per CTA (analysis tiles + synthesis tiles)
+
+struct HeatTcSmem {
+  uint64_t full[kMaxStages];
+  uint64_t fullB[kMaxStages];
+  uint64_t empty[kMaxStages];
+  uint64_t afull[kMaxSlots], aempty[kMaxSlots];
+  uint64_t sfull[kMaxSlots], sempty[kMaxSlots];
+  uint64_t cready;
+  uint32_t tmem;
+  int abort;
+};
+
+struct HeatArgs {
+  const int* order;   // blocks with rows, largest first
+  int nwork;
+  const int* M;
+  const long long* row_off;
+  int nh, ldc, ncols, nmma;
+  int nmt_max;        // 128-row tiles of the largest block
+  int kc_max;         // 64-row chunks of the largest block
+  const float* h;     // h_l or nullptr
+  const ProbState* colscale;
+  float* Y;           // [blk][jh][ldc]
+  int* err;
+};
+
+__device__ __forceinline__ int heat_work(int r, int c, int G) { return r * G + ((r & 1) ? G - 1 - c : c); }
+
+template <int kStages>
+__global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant__ CUtensorMap t_hi,
+                                                           const __grid_constant__ CUtensorMap t_lo,
+                                                           const __grid_constant__ CUtensorMap t_x, HeatArgs ha) {
+  extern __shared__ uint8_t smraw[];
+  __shared__ HeatTcSmem ctl;
+  uint8_t* base = align1k(smraw);
+  const int nmma = ha.nmma, nh = ha.nh;
+  const int bbytes = nmma * kBK * 2;
+  const int xbytes = nmma * kBK * 4;
+  const int sbytes = 2 * kATileBytes + xbytes + 2 * bbytes;   // one pipeline stage
+  const int cbytes = nmma * 128;                              // one 64-row chunk of C (hi or lo)
+  uint8_t* cbuf_hi = base + kStages * sbytes;
+  uint8_t* cbuf_lo = cbuf_hi + ha.kc_max * cbytes;
+  auto sA_hi = [&](int s) { return base + s * sbytes; };
+  auto sA_lo = [&](int s) { return base + s * sbytes + kATileBytes; };
+  auto sX = [&](int s) { return base + s * sbytes + 2 * kATileBytes; };
+  auto sB_hi = [&](int s) { return base + s * sbytes + 2 * kATileBytes + xbytes; };
+  auto sB_lo = [&](int s) { return base + s * sbytes + 2 * kATileBytes + xbytes + bbytes; };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ncols_alloc = tmem_cols_for(nmma);
+  const int nnt = (nh + kBM - 1) / kBM;
+  const int nkbA = (nh + kBK - 1) / kBK;
+  const int G = gridDim.x;
+  const int rounds = (ha.nwork + G - 1) / G;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&ctl.full[s], 1);
+      mbar_init(&ctl.fullB[s], 64);
+      mbar_init(&ctl.empty[s], 1);
+    }
+    for (int b = 0; b < kMaxSlots; ++b) {
+      mbar_init(&ctl.afull[b], 1);
+      mbar_init(&ctl.aempty[b], 128);
+      mbar_init(&ctl.sfull[b], 1);
+      mbar_init(&ctl.sempty[b], 128);
+    }
+    mbar_init(&ctl.cready, 128);
+    ctl.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl.tmem, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = ctl.tmem;
+  volatile int* abort = &ctl.abort;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int it = 0;
+      bool ok = true;
+      for (int r = 0; r < rounds && ok; ++r) {
+        const int w = heat_work(r, blockIdx.x, G);
+        if (w >= ha.nwork) continue;
+        const int blk = ha.order[w];
+        const int M = ha.M[blk];
+        const int ro = (int)ha.row_off[blk];
+        const int nmt = (M + kBM - 1) / kBM, nkbS = (M + kBK - 1) / kBK;
+        for (int mt = 0; mt < nmt && ok; ++mt)
+          for (int kb = 0; kb < nkbA; ++kb, ++it) {
+            const int s = it % kStages, n = it / kStages;
+            if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
+            mbar_arrive_expect_tx(&ctl.full[s], 2 * kATileBytes + xbytes);
+            const int y = ro + mt * kBM, x = kb * kBK;
+            tma_load_2d(sA_hi(s), &t_hi, &ctl.full[s], x, y);
+            tma_load_2d(sA_hi(s) + kATileBytes / 2, &t_hi, &ctl.full[s], x, y + 64);
+            tma_load_2d(sA_lo(s), &t_lo, &ctl.full[s], x, y);
+            tma_load_2d(sA_lo(s) + kATileBytes / 2, &t_lo, &ctl.full[s], x, y + 64);
+            tma_load_2d(sX(s), &t_x, &ctl.full[s], 0, blk * nh + kb * kBK);
+          }
+        for (int nt = 0; nt < nnt && ok; ++nt)
+          for (int kb = 0; kb < nkbS; ++kb, ++it) {
+            const int s = it % kStages, n = it / kStages;
+            if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
+            mbar_arrive_expect_tx(&ctl.full[s], 2 * kATileBytes);
+            const int y = ro + kb * kBK, x = nt * kBM;
+            tma_load_2d(sA_hi(s), &t_hi, &ctl.full[s], x, y);
+            tma_load_2d(sA_hi(s) + kATileBytes / 2, &t_hi, &ctl.full[s], x + 64, y);
+            tma_load_2d(sA_lo(s), &t_lo, &ctl.full[s], x, y);
+            tma_load_2d(sA_lo(s) + kATileBytes / 2, &t_lo, &ctl.full[s], x + 64, y);
+          }
+      }
+      for (int k = it > kStages ? it - kStages : 0; k < it; ++k)
+        mbar_drain(&ctl.full[k % kStages], (k / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t id_a = idesc_bf16(kBM, nmma);       // analysis: both operands K-major
+      const uint32_t id_s = idesc_bf16_amn(kBM, nmma);   // synthesis: A (table) MN-major
+      int it = 0, nb = 0;
+      int ause[kMaxSlots] = {0}, suse[kMaxSlots] = {0};
+      bool ok = true;
+      for (int r = 0; r < rounds && ok; ++r) {
+        const int w = heat_work(r, blockIdx.x, G);
+        if (w >= ha.nwork) continue;
+        const int blk = ha.order[w];
+        const int M = ha.M[blk];
+        const int nmt = (M + kBM - 1) / kBM, nkbS = (M + kBK - 1) / kBK;
+        for (int mt = 0; mt < nmt && ok; ++mt) {
+          if (ause[mt] > 0 && !(ok = mbar_wait(&ctl.aempty[mt], (ause[mt] - 1) & 1, abort))) break;
+          tc_fence_after();
+          const uint32_t d = taddr + (uint32_t)(mt * ncols_alloc);
+          for (int kb = 0; kb < nkbA; ++kb, ++it) {
+            const int s = it % kStages, n = it / kStages;
+            ok = mbar_wait(&ctl.full[s], n & 1, abort);
+            if (ok) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
+            const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k) {
+              const uint32_t off = k * 32;
+              umma_bf16(d, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bh + off), id_a, (kb | k) != 0);
+              umma_bf16(d, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bl + off), id_a, 1);
+              umma_bf16(d, desc_sw128_kmajor(al + off), desc_sw128_kmajor(bh + off), id_a, 1);
+            }
+            umma_commit(&ctl.empty[s]);
+          }
+          if (!ok) break;
+          umma_commit(&ctl.afull[mt]);
+          ++ause[mt];
+        }
+        if (!ok) break;
+        // the coefficients of this block must be in shared memory
+        if (!(ok = mbar_wait(&ctl.cready, nb & 1, abort))) break;
+        tc_fence_after();
+        const uint32_t ch = smem_u32(cbuf_hi), cl = smem_u32(cbuf_lo);
+        for (int nt = 0; nt < nnt && ok; ++nt) {
+          const int slot = ha.nmt_max + nt;
+          if (suse[nt] > 0 && !(ok = mbar_wait(&ctl.sempty[nt], (suse[nt] - 1) & 1, abort))) break;
+          tc_fence_after();
+          const uint32_t d = taddr + (uint32_t)(slot * ncols_alloc);
+          for (int kb = 0; kb < nkbS; ++kb, ++it) {
+            const int s = it % kStages, n = it / kStages;
+            ok = mbar_wait(&ctl.full[s], n & 1, abort);
+            if (ok) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);   // keeps the stage phases aligned
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k) {
+              // A: 16 K-rows (two 8-row groups, 1 KB apart) of two 64-node atoms (8 KB apart)
+              const uint64_t a_h = desc_sw128_mnmajor(ah + k * 2048, kATileBytes / 2, 1024);
+              const uint64_t a_l = desc_sw128_mnmajor(al + k * 2048, kATileBytes / 2, 1024);
+              const uint32_t boff = (uint32_t)(kb * cbytes + k * 32);
+              const uint64_t b_h = desc_sw128_kmajor(ch + boff), b_l = desc_sw128_kmajor(cl + boff);
+              umma_bf16(d, a_h, b_h, id_s, (kb | k) != 0);
+              umma_bf16(d, a_h, b_l, id_s, 1);
+              umma_bf16(d, a_l, b_h, id_s, 1);
+            }
+            umma_commit(&ctl.empty[s]);
+          }
+          if (!ok) break;
+          umma_commit(&ctl.sfull[nt]);
+          ++suse[nt];
+        }
+        ++nb;
+      }
+    }
+  } else if (warp < 4) {
+    // split the FP32 X tile of every analysis stage into bf16 hi/lo, K-major [c][jh]; every
+    // stage (analysis or synthesis) is released to the MMA issuer through fullB
+    const int pt = threadIdx.x - 64;
+    int it = 0;
+    bool ok = true;
+    for (int r = 0; r < rounds && ok; ++r) {
+      const int w = heat_work(r, blockIdx.x, G);
+      if (w >= ha.nwork) continue;
+      const int blk = ha.order[w];
+      const int M = ha.M[blk];
+      const int nmt = (M + kBM - 1) / kBM, nkbS = (M + kBK - 1) / kBK;
+      for (int mt = 0; mt < nmt && ok; ++mt)
+        for (int kb = 0; kb < nkbA; ++kb, ++it) {
+          const int s = it % kStages, n = it / kStages;
+          if (!(ok = mbar_wait(&ctl.full[s], n & 1, abort))) break;
+          const float* xs = reinterpret_cast<const float*>(sX(s));
+          uint8_t* bh = sB_hi(s);
+          uint8_t* bl = sB_lo(s);
+          for (int e = pt; e < 8 * nmma; e += 64) {
+            const int r8 = e / nmma, c = e - r8 * nmma;
+            const int jh0 = kb * kBK + r8 * 8;
+            uint32_t hw[4], lw[4];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+              float v0 = xs[(r8 * 8 + q) * nmma + c];
+              float v1 = xs[(r8 * 8 + q + 1) * nmma + c];
+              if (c >= ha.ncols || jh0 + q >= nh) v0 = 0.f;
+              if (c >= ha.ncols || jh0 + q + 1 >= nh) v1 = 0.f;
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+              const float2 hf = __bfloat1622float2(h2);
+              const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+              hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+              lw[q / 2] = *reinterpret_cast<const uint32_t*>(&l2);
+            }
+            const uint32_t o = sw128_offset(c, r8 * 8);
+            *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+          }
+          fence_async_smem();
+          mbar_arrive(&ctl.fullB[s]);
+        }
+      // synthesis stages carry no X, but every stage completes one fullB phase, so that the
+      // phase count of each stage's barriers stays the same for every role
+      for (int k = 0; k < nnt * nkbS && ok; ++k, ++it) {
+        const int s = it % kStages, n = it / kStages;
+        if (!(ok = mbar_wait(&ctl.full[s], n & 1, abort))) break;
+        mbar_arrive(&ctl.fullB[s]);
+      }
+    }
+  } else {
+    // epilogue: coefficients into shared memory, then the synthesis output to Y
+    const int q = warp - 4;   // TMEM lane quadrant
+    int ause[kMaxSlots] = {0}, suse[kMaxSlots] = {0};
+    bool ok = true;
+    for (int r = 0; r < rounds && ok; ++r) {
+      const int w = heat_work(r, blockIdx.x, G);
+      if (w >= ha.nwork) continue;
+      const int blk = ha.order[w];
+      const int M = ha.M[blk];
+      const int m = blk >> 1, p = blk & 1;
+      const int nmt = (M + kBM - 1) / kBM, kext = ((M + kBK - 1) / kBK) * kBK;
+      for (int mt = 0; mt < nmt; ++mt) {
+        if (!(ok = mbar_wait_warp(&ctl.afull[mt], ause[mt] & 1, abort))) break;
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(mt * ncols_alloc) + ((uint32_t)(q * 32) << 16);
+        const int i = mt * kBM + q * 32 + lane;   // degree row within the block
+        const float hl = (i < M) ? (ha.h ? ha.h[m + p + 2 * i] : 1.f) : 0.f;
+        const uint32_t cb = (uint32_t)((i >> 6) * cbytes);
+        for (int c0 = 0; c0 < nmma; c0 += 16) {
+          float v[16];
+          tmem_ld16(d + (uint32_t)c0, v);
+          if (i < kext) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int c = c0 + e;
+              float val = 0.f;
+              if (c < ha.ncols) val = v[e] * hl * (ha.colscale ? (float)ha.colscale[c >> 1].beta : 1.f);
+              const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+              const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
+              const uint32_t o = cb + sw128_offset(c, i & 63);
+              *reinterpret_cast<__nv_bfloat16*>(cbuf_hi + o) = hi;
+              *reinterpret_cast<__nv_bfloat16*>(cbuf_lo + o) = lo;
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&ctl.aempty[mt]);
+        ++ause[mt];
+      }
+      if (!ok) break;
+      fence_async_smem();   // the generic-proxy writes of C become visible to the MMAs
+      mbar_arrive(&ctl.cready);
+      for (int nt = 0; nt < nnt; ++nt) {
+        if (!(ok = mbar_wait_warp(&ctl.sfull[nt], suse[nt] & 1, abort))) break;
+        tc_fence_after();
+        const int slot = ha.nmt_max + nt;
+        const uint32_t d = taddr + (uint32_t)(slot * ncols_alloc) + ((uint32_t)(q * 32) << 16);
+        const int jh = nt * kBM + q * 32 + lane;
+        float* yrow = ha.Y + ((size_t)blk * nh + jh) * ha.ldc;
+        for (int c0 = 0; c0 < nmma; c0 += 16) {
+          float v[16];
+          tmem_ld16(d + (uint32_t)c0, v);
+          if (jh < nh) {
+            if (c0 + 16 <= ha.ncols) {
+#pragma unroll
+              for (int e = 0; e < 16; e += 4)
+                *reinterpret_cast<float4*>(yrow + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (c0 + e < ha.ncols) yrow[c0 + e] = v[e];
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&ctl.sempty[nt]);
+        ++suse[nt];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 512);
+  }
+  if (threadIdx.x == 0 && ctl.abort) atomicExch(ha.err, SHOT_ERR_TIMEOUT);
+}
+
 // FP32 coefficients C[row_off + i][ldc] -> bf16 hi/lo C^T[blk][nmma_cap][ldi] (synthesis input)
 __global__ void k_c_to_ct(int nblk, const int* __restrict__ Mrows, const long long* __restrict__ row_off,
                           const float* __restrict__ C, int ldc, int ncols, __nv_bfloat16* __restrict__ hi,
@@ -563,6 +912,41 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     kern<<<grid, kTcThreads, smem, st>>>(ah, al, bh, bl, aa, sa);
     SHOT_CUDA(cudaGetLastError());
   }
+  return SHOT_OK;
+}
+
+// Fused analysis + synthesis (k_heat_tc) for the solver's heat applications.  Returns
+// SHOT_ERR_UNSUPPORTED (without launching) when the configuration does not fit: more than
+// 32 fields, TMEM slots, or shared memory; the caller then runs the two-kernel path.
+int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
+                   const ProbState* colscale) {
+  const Workspace& w = g.ws;
+  const int nmma = tc_nmma(nf);
+  if (nmma > 64 || g.nwork == 0) return SHOT_ERR_UNSUPPORTED;
+  const int ncols_alloc = host_tmem_cols(nmma);
+  const int nnt = (g.nh + kBM - 1) / kBM;
+  if (g.nmt_max + nnt > 512 / ncols_alloc || g.nmt_max + nnt > kMaxSlots) return SHOT_ERR_UNSUPPORTED;
+  const size_t sbytes = 2 * kATileBytes + (size_t)nmma * kBK * 4 + 2 * (size_t)nmma * kBK * 2;
+  const size_t cbytes = (size_t)nmma * 128;
+  int stages = 3;
+  while (stages > 2 && 1024 + stages * sbytes + 2 * g.kc_max * cbytes > 227 * 1024) --stages;
+  size_t smem = 1024 + stages * sbytes + 2 * g.kc_max * cbytes;
+  if (smem > 227 * 1024) return SHOT_ERR_UNSUPPORTED;
+  if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: it allocates all 512 TMEM columns
+  int rc;
+  CUtensorMap mh, ml, mx;
+  if ((rc = make_map(&mh, g.tab_hi, g.nh, g.rows_total, g.ldt, 64))) return rc;
+  if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, 64))) return rc;
+  if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
+  HeatArgs ha{g.blk_order_d, g.nwork, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma, g.nmt_max, g.kc_max,
+              g.h_d, colscale, Y, w.dev_int + 4};
+  auto kern = stages == 3 ? k_heat_tc<3> : k_heat_tc<2>;
+  SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = g.nwork < g.num_sms ? g.nwork : g.num_sms;
+  ProfScope prof(PK_ANALYSIS, st);
+  count_launch();
+  kern<<<grid, kTcThreads, smem, st>>>(mh, ml, mx, ha);
+  SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }
 

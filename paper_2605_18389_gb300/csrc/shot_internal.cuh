@@ -39,11 +39,14 @@ class ProfScope {
 struct FftPlan {
   int N;
   int nst;
-  int R[12];
-  uint32_t ns_mul[12];   // ceil(2^32 / Ns) of stage s (0 when Ns == 1)
-  uint32_t nr_mul[12];   // ceil(2^32 / (N / R)) of stage s (0 when N / R == 1)
+  int R[16];
+  int tw_off[16];        // offset of stage s's twiddles ((R - 1) x Ns, r-major) in the table
+  uint32_t ns_mul[16];   // ceil(2^32 / Ns) of stage s (0 when Ns == 1)
+  uint32_t nr_mul[16];   // ceil(2^32 / (N / R)) of stage s (0 when N / R == 1)
 };
 bool make_fft_plan(int N, FftPlan* plan);
+// the plan's stage twiddles W_N^{k r N/(Ns R)} (forward sign), N complex values
+void fft_plan_twiddles(const FftPlan& plan, std::vector<float2>& tw);
 
 // ---------------------------------------------------------------------------------
 // Spectral layout.  For order m and parity p (p = (l - m) mod 2) the block (m,p)
@@ -95,7 +98,7 @@ struct Grid {
   int nlat = 0, nlon = 0, lmax = 0, nh = 0;
   std::vector<Tuning> tuning;   // per field count, filled by the autotuner
   Tuning active;                // the entry in force for the current launch sequence
-  int precision = SHOT_FP32, mode = SHOT_TABLE;
+  int precision = SHOT_FP32, mode = SHOT_TABLE, quad = SHOT_QUAD_GAUSS_LEGENDRE;
   int dev = 0;
   int num_sms = 148;
   FftPlan plan{};
@@ -128,6 +131,9 @@ struct Grid {
   long long* row_off_d = nullptr;
   Tile* tiles_ana = nullptr;
   Tile* tiles_syn = nullptr;
+  int* blk_order_d = nullptr;   // blocks with rows, largest first (fused heat kernel)
+  int nwork = 0, nmt_max = 0, kc_max = 0;
+  int fused_heat = 0;           // BF16X3 table grids: fused analysis + synthesis kernel
   int ntiles_ana = 0, ntiles_syn = 0;
   int bm_ana = 128, bm_syn = 128;
   Workspace ws;
@@ -192,6 +198,8 @@ int build_recurrence(Grid& g, cudaStream_t st);
 int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
                         bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
 int tc_nmma(int nf);
+int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
+                   const ProbState* colscale);
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
 
 }  // namespace shot

@@ -28,6 +28,8 @@ SHOT_TABLE = 0
 SHOT_RECURRENCE = 1
 SHOT_GRAD_UNROLLED = 0
 SHOT_GRAD_ENVELOPE = 1
+SHOT_QUAD_GAUSS_LEGENDRE = 0
+SHOT_QUAD_CLENSHAW_CURTIS = 1
 SHOT_FLAG_NORM_L1 = 0x1
 SHOT_FLAG_WARM_START = 0x2
 
@@ -43,6 +45,8 @@ SIGNATURES = {
     "shot_last_error": [ctypes.c_char_p, ctypes.c_int],
     "shot_grid_init": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                        ctypes.c_int, _vp],
+    "shot_grid_init_quad": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_int, ctypes.c_int, _vp],
     "shot_grid_free": [_vp],
     "shot_grid_info": [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p],
     "shot_grid_nodes": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
@@ -146,6 +150,15 @@ def shot_grid_init(nlat, nlon=None, lmax=-1, precision=SHOT_FP32, legendre_mode=
     nlon = 2 * nlat if nlon is None else nlon
     h = _vp()
     _check(lib().shot_grid_init(ctypes.byref(h), nlat, nlon, lmax, precision, legendre_mode, _stream(stream)))
+    return h
+
+
+def shot_grid_init_quad(quadrature, nlat, nlon=None, lmax=-1, precision=SHOT_FP32, legendre_mode=SHOT_TABLE,
+                        stream=None):
+    nlon = 2 * nlat if nlon is None else nlon
+    h = _vp()
+    _check(lib().shot_grid_init_quad(ctypes.byref(h), quadrature, nlat, nlon, lmax, precision, legendre_mode,
+                                     _stream(stream)))
     return h
 
 
