@@ -6,8 +6,11 @@ the batch, with the marginal check every C = 10 iterations, inside one
 shot_divergence call (8 measure pairs -> 24 OT problems -> 48 heat convolutions of
 all 24 fields per iteration), followed by the final objective and S of every pair.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|bf16x3]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp32]
                     [--impl ours|reference]
+
+The headline is the split-precision (BF16x3) form; the same run also times the plain FP32
+form on the same fields and reports the speedup and the S agreement between the two.
 
 --impl reference times the FP64 CPU oracle on the host cores (the only other place this
 file runs oracle code besides the cpu_baseline leg).  Prints one JSON line on rank 0.
@@ -40,7 +43,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison pass")
     ap.add_argument("--legendre", default="table", choices=["table", "recurrence"])
     ap.add_argument("--tau", type=float, default=math.inf)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -228,6 +232,31 @@ def run_reference(args):
     return 0
 
 
+def fp32_compare(args, shot, torch, quad, nlat, nlon, mode, pt, qt, S_split):
+    """The plain FP32 form on the same fields and steps (graph path, CUDA events): its
+    iters/s, the split form's speedup over it, and the relative S difference."""
+    g = shot.shot_grid_init_quad(quad, nlat, nlon, -1, shot.SHOT_FP32, mode)
+    shot.shot_grid_reserve(g, 3 * PAIRS)
+    u3 = torch.empty((3 * PAIRS, nlat, nlon), device="cuda")
+    v3 = torch.empty_like(u3)
+    kw = dict(tau=args.tau, tol=0.0, check_every=CHECK_EVERY, u3=u3, v3=v3)
+    shot.shot_divergence(g, pt, qt, EPS, max_iter=args.warmup, **kw)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, res = shot.shot_divergence(g, pt, qt, EPS, max_iter=args.steps, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    shot.shot_grid_free(g)
+    v32 = args.steps / (ms / 1e3)
+    S32 = np.asarray(res["S"], dtype=np.float64)
+    rel = float(np.max(np.abs(np.asarray(S_split) - S32) / np.maximum(np.abs(S32), 1e-300)))
+    return {"value": v32, "unit": "iters/s", "ms_per_step": ms / args.steps,
+            "split_speedup": None, "S_max_rel_diff": rel}
+
+
 def cpu_baseline(args, x, w, a_ring):
     """Oracle on a bounded sample (~10-30 s): 2 iterations of the full 24-problem batch."""
     from oracle.grid import Grid
@@ -340,12 +369,20 @@ def main():
     share = {k: round(v[0] / sum(x[0] for x in kinds.values()), 4) for k, v in kinds.items()}
     per_kind = {k: {"avg_launch_ms": round(v[0] / v[1], 5), "launches": v[1]} for k, v in kinds.items()}
 
+    compare = None
+    if args.precision == "bf16x3" and not args.no_compare and ws == 1:
+        compare = fp32_compare(args, shot, torch, quad, nlat, nlon, mode, pt, qt, res["S"])
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "bf16x3 (bf16 hi/lo products, f32 accumulate; f32 elsewhere)",
+            "data": "synthetic",
             "config": config(args, nlat, nlon), "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "roofline": roof, "kernel_share": share, "kernels": per_kind,
             "status": {"rc": int(rc), "S_finite": bool(np.all(np.isfinite(res["S"])))}}
+    if compare is not None:
+        compare["split_speedup"] = value / compare["value"]
+        line["fp32_compare"] = compare
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(args, x, w, a_ring)
     shot.shot_grid_free(g)

@@ -249,6 +249,28 @@ int shot_heat_apply_noalloc(shot_grid g, double t, const float* in, float* out, 
  * Allocates one temporary field batch.  Synchronises `stream`. */
 int shot_grid_autotune(shot_grid g, int nfields, int* choice, void* stream);
 
+/* ---- heat convolution vs explicit matrix convolution -----------------------
+ * The comparison of App. "Convolution on S^2": the matrix convolution applies the
+ * unnormalised geodesic Gibbs kernel K_eps(x, y) = exp(-d(x, y)^2 / eps), which
+ * integrates over the sphere to C(eps); by Varadhan's formula the heat kernel at
+ * t = eps/4 is close to K_eps / C(eps), so the heat output is rescaled by C(eps) before
+ * the two are compared.
+ *
+ * shot_gibbs_normaliser: C(eps) = 2 pi int_0^pi exp(-theta^2/eps) sin(theta) dtheta
+ *   (host computation, composite Simpson's rule).  eps > 0; *C receives the value.
+ * shot_gibbs_apply: out[f][i] = sum_j a_j exp(-d(x_i, x_j)^2 / eps) in[f][j] with the
+ *   grid's area weights a (App. C.2) and d the great-circle distance, evaluated pair by
+ *   pair in FP32 (O(n^2) per field, nothing of size n^2 stored; meant for the small grids
+ *   of the comparison).  in, out: device [nfields][nlat][nlon] FP32, distinct.
+ *   Asynchronous on `stream`; the first call on a grid also builds its node vectors.
+ * shot_conv_compare: for each field, the mean over the grid nodes of
+ *   |C(eps) (H_{eps/4} in)_i - (K_eps in)_i| into mae[f] (host array of nfields doubles);
+ *   allocates and frees its two temporary field batches; synchronises `stream`.
+ * Errors: INVALID_ARG (eps <= 0, NULL pointers, nfields < 1, in == out), OOM, CUDA. */
+int shot_gibbs_normaliser(double eps, double* C);
+int shot_gibbs_apply(shot_grid g, double eps, const float* in, float* out, int nfields, void* stream);
+int shot_conv_compare(shot_grid g, double eps, const float* in, int nfields, double* mae, void* stream);
+
 /* ---- measurement helpers (no counterpart in the paper) -------------------
  * shot_launch_count: total number of CUDA kernels this library has launched in the
  *   process (host counter; *n receives it).

@@ -37,15 +37,20 @@ int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float*
 int launch_analysis_simt(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h, cudaStream_t st);
 int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st);
 
+int spectra_split(const Grid& g, int nf, int ldc) {
+  return (g.split_spectra && g.precision == SHOT_BF16X3 && g.mode == SHOT_TABLE && tc_nmma(nf) <= 64 &&
+          ldc % 8 == 0) ? 1 : 0;
+}
+
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
-                    const ProbState* colscale) {
+                    const ProbState* colscale, int xsplit) {
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st, colscale);
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st, colscale);
   if (g.fused_heat) {
-    const int rc = launch_heat_tc(g, nf, X, Y, ldc, st, colscale);
+    const int rc = launch_heat_tc(g, nf, X, Y, ldc, st, colscale, xsplit);
     if (rc != SHOT_ERR_UNSUPPORTED) return rc;
   }
-  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st, colscale);
+  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st, colscale, xsplit);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st) {
@@ -282,6 +287,7 @@ struct Solve {
   int C = 0, norm_l1 = 0;
   float *u = nullptr, *v = nullptr;
   cudaStream_t st = nullptr;
+  int xs = 0;   // spectra kept as bf16 hi/lo (tensor-core operand format)
 };
 
 int ensure_stream(Grid& g) {
@@ -334,7 +340,8 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
   if ((rc = autotune(g, nprob, s.st))) return rc;
   if ((rc = launch_heat_mult(g, eps / 4.0, s.st))) return rc;
   // spectra of the starting v (unscaled; the analysis applies beta per column)
-  return launch_dft_fwd(g, v, nprob, nullptr, 0, w.XY, w.ldc, s.st);
+  s.xs = spectra_split(g, nprob, w.ldc);
+  return launch_dft_fwd(g, v, nprob, nullptr, 0, w.XY, w.ldc, s.st, s.xs);
 }
 
 EpiParams base_ep(Solve& s) {
@@ -344,6 +351,7 @@ EpiParams base_ep(Solve& s) {
   ep.part = w.part;
   ep.eps = s.eps;
   ep.norm_l1 = s.norm_l1;
+  ep.xsplit = s.xs;
   return ep;
 }
 
@@ -361,7 +369,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
   int rc;
   for (int i = 0; i < nit; ++i) {
     // u-step: u = (p / K(beta v))^gamma, and X := F(u)
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, ps))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, ps, s.xs))) return rc;
     ep.mode = EPI_UPDATE;
     ep.out = s.u;
     ep.marg = margP;
@@ -370,7 +378,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
     if ((rc = reduce(g, RED_U, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
     // v-step: v = (q / K u)^gamma, X := F(v); then the gauge / translation-invariant scalars
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
     ep.out = s.v;
     ep.marg = margQ;
     ep.which = 1;
@@ -378,7 +386,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     if ((rc = reduce(g, RED_V, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
   }
   if (check) {   // K(beta v) from the spectra X, which stay for the next u-step
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, ps))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, ps, s.xs))) return rc;
     ep.mode = EPI_CHECK;
     ep.other = s.u;
     ep.marg = margP;
@@ -396,7 +404,7 @@ int solve_final_enqueue(Solve& s) {
   ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   int rc;
   // final K v_true for the objective, mass and marginal error; writes u_true, v_true
-  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st, ps))) return rc;
+  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st, ps, s.xs))) return rc;
   ep.mode = EPI_FINAL;
   ep.out = s.v;
   ep.other = s.u;
@@ -627,9 +635,12 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
   g->precision = precision;
   g->mode = legendre_mode;
   g->quad = quadrature;
-  {  // SHOT_FUSED_HEAT=1 selects the fused per-order analysis + synthesis kernel (BF16X3)
+  {  // SHOT_FUSED_HEAT=1 selects the fused per-order analysis + synthesis kernel (BF16X3);
+     // SHOT_SPLIT_SPECTRA=1 has the solver keep bf16 hi/lo spectra on BF16X3 grids
     const char* e = getenv("SHOT_FUSED_HEAT");
     g->fused_heat = (e && e[0] == '1') ? 1 : 0;
+    e = getenv("SHOT_SPLIT_SPECTRA");
+    g->split_spectra = (e && e[0] == '1') ? 1 : 0;
   }
   g->plan = plan;
   cudaGetDevice(&g->dev);
@@ -646,7 +657,7 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi,
+  void* dptr[] = {g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi,
                   g->tabT_lo,
                   g->ws.ct_hi, g->ws.ct_lo, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,

@@ -329,10 +329,6 @@ __global__ void k_g_mass_diff(int nlat, int nlon, const float* __restrict__ p, c
 
 }  // namespace
 
-int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which, float* X, int ldc,
-                   cudaStream_t st);
-int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
-
 // out = K (beta (.) in) (beta per problem from ps when ps != nullptr)
 static int heat_fields(Grid& g, const float* in, float* out, int nf, const ProbState* ps, cudaStream_t st) {
   Workspace& w = g.ws;

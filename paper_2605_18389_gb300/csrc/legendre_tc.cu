@@ -180,6 +180,40 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
          (uint32_t)(k & 7) * 2u;
 }
 
+// B operand of the analysis, MN-major (N = columns contiguous): nmma columns in atoms of 64
+// (8 KB apart, 128-byte rows, one row per node).
+__host__ __device__ constexpr int mn_atoms(int nmma) { return (nmma + 63) / 64; }
+
+// Splits the FP32 spectra tile xs[64 nodes][nmma] (TMA, row-major) into bf16 hi and lo in
+// the MN-major layout above.  One task = 8 consecutive columns of one node: one 16-byte
+// swizzled chunk of hi and one of lo.  Nodes past the block (jh0 + r >= nh) and columns
+// past the fields are zero.  64 threads (pt = 0..63).
+__device__ __forceinline__ void split_x_mn(const float* xs, int nmma, int ncols, int jh0, int nh, uint8_t* bh,
+                                           uint8_t* bl, int pt) {
+  const int ch = nmma >> 3;
+  for (int e = pt; e < 64 * ch; e += 64) {
+    const int r = e / ch, c0 = (e - r * ch) * 8;
+    const float4 a = *reinterpret_cast<const float4*>(xs + r * nmma + c0);
+    const float4 b = *reinterpret_cast<const float4*>(xs + r * nmma + c0 + 4);
+    float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    const bool row_ok = jh0 + r < nh;
+    uint32_t hw[4], lw[4];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      const float v0 = (row_ok && c0 + q < ncols) ? v[q] : 0.f;
+      const float v1 = (row_ok && c0 + q + 1 < ncols) ? v[q + 1] : 0.f;
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+      const float2 hf = __bfloat1622float2(h2);
+      const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+      hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+      lw[q / 2] = *reinterpret_cast<const uint32_t*>(&l2);
+    }
+    const uint32_t o = (uint32_t)((c0 >> 6) * (64 * 64 * 2)) + sw128_offset(r, c0 & 63);
+    *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
 struct TcSmem {
   uint64_t fullA[kMaxStages];
   uint64_t fullB[kMaxStages];
@@ -225,7 +259,12 @@ struct SynArgs {
 // tiles); warp 1: MMA issuer; warps 2-3 (analysis only): split the FP32 X tile into the
 // bf16 hi/lo B operand; warps 4-7: epilogue.  The accumulator is double-buffered in TMEM
 // so the epilogue of one tile overlaps the MMAs of the next.
-template <int kStages, bool ANA>
+// XS (analysis only): the spectra come as bf16 hi/lo arrays [blk nh + jh][ldc] and are
+// loaded by TMA as an MN-major B operand (64 columns x 64 nodes per box); the split warps
+// are idle.
+constexpr int kXsBoxBytes = 64 * 64 * 2;
+
+template <int kStages, bool ANA, bool XS = false>
 __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_constant__ CUtensorMap ta_hi,
                                                                const __grid_constant__ CUtensorMap ta_lo,
                                                                const __grid_constant__ CUtensorMap tb_hi,
@@ -239,8 +278,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
   const int ntiles = ANA ? aa.ntiles : sa.ntiles;
   const Tile* tiles = ANA ? aa.tiles : sa.tiles;
   const int* Mr = ANA ? aa.M : sa.M;
-  const int bbytes = nmma * kBK * 2;
-  const int xbytes = ANA ? nmma * kBK * 4 : 0;
+  const int bbytes = ANA ? mn_atoms(nmma) * kXsBoxBytes : nmma * kBK * 2;
+  const int xbytes = (ANA && !XS) ? nmma * kBK * 4 : 0;
   uint8_t* sA_hi = base;
   uint8_t* sA_lo = sA_hi + kStages * kATileBytes;
   uint8_t* sB_hi = sA_lo + kStages * kATileBytes;
@@ -280,7 +319,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
           if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
-          if (ANA) {
+          if (ANA && XS) {
+            mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + 2 * kXsBoxBytes);
+            const int y = (int)(aa.row_off[tl.blk] + tl.r0);
+            tma_load_2d(sA_hi + s * kATileBytes, &ta_hi, &ctl.fullA[s], kb * kBK, y);
+            tma_load_2d(sA_lo + s * kATileBytes, &ta_lo, &ctl.fullA[s], kb * kBK, y);
+            tma_load_2d(sB_hi + s * bbytes, &tb_hi, &ctl.fullA[s], 0, tl.blk * nh + kb * kBK);
+            tma_load_2d(sB_lo + s * bbytes, &tb_lo, &ctl.fullA[s], 0, tl.blk * nh + kb * kBK);
+          } else if (ANA) {
             mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + xbytes);
             const int y = (int)(aa.row_off[tl.blk] + tl.r0);
             tma_load_2d(sA_hi + s * kATileBytes, &ta_hi, &ctl.fullA[s], kb * kBK, y);
@@ -302,7 +348,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t idesc = idesc_bf16(kBM, nmma);
+      // analysis: B (spectra) MN-major; synthesis: B (C^T) K-major
+      const uint32_t idesc = ANA ? (idesc_bf16(kBM, nmma) | (1u << 16)) : idesc_bf16(kBM, nmma);
       int it = 0, lt = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
@@ -315,7 +362,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
           ok = mbar_wait(&ctl.fullA[s], n & 1, abort);
-          if (ok && ANA) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);
+          if (ok && ANA && !XS) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);
           if (!ok) break;
           tc_fence_after();
           const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
@@ -323,9 +370,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k) {
             const uint32_t off = k * 32;
-            umma_bf16(d, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bh + off), idesc, (kb | k) != 0);
-            umma_bf16(d, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bl + off), idesc, 1);
-            umma_bf16(d, desc_sw128_kmajor(al + off), desc_sw128_kmajor(bh + off), idesc, 1);
+            uint64_t b_h, b_l;
+            if (ANA) {   // 16 K-rows = two 8-row groups of the MN-major atoms
+              b_h = desc_sw128_mnmajor(bh + k * 2048, kXsBoxBytes, 1024);
+              b_l = desc_sw128_mnmajor(bl + k * 2048, kXsBoxBytes, 1024);
+            } else {
+              b_h = desc_sw128_kmajor(bh + off);
+              b_l = desc_sw128_kmajor(bl + off);
+            }
+            umma_bf16(d, desc_sw128_kmajor(ah + off), b_h, idesc, (kb | k) != 0);
+            umma_bf16(d, desc_sw128_kmajor(ah + off), b_l, idesc, 1);
+            umma_bf16(d, desc_sw128_kmajor(al + off), b_h, idesc, 1);
           }
           umma_commit(&ctl.empty[s]);
         }
@@ -333,8 +388,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
       }
     }
   } else if (warp < 4) {
-    if (ANA) {
-      // split the FP32 X tile (TMA, with the table tiles) into bf16 hi/lo, K-major [c][jh]
+    if (ANA && !XS) {
+      // split the FP32 X tile (TMA, with the table tiles) into bf16 hi/lo, MN-major [jh][c]
       const int pt = threadIdx.x - 64;
       int it = 0;
       bool ok = true;
@@ -344,31 +399,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
           if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
-          const float* xs = reinterpret_cast<const float*>(sX + s * xbytes);
-          uint8_t* bh = sB_hi + s * bbytes;
-          uint8_t* bl = sB_lo + s * bbytes;
-          // one task = 8 consecutive nodes of one column -> one 16-byte swizzle chunk of hi
-          // and of lo; rows beyond the block's nodes (or columns beyond the fields) are zero
-          for (int e = pt; e < 8 * nmma; e += 64) {
-            const int r8 = e / nmma, c = e - r8 * nmma;
-            const int jh0 = kb * kBK + r8 * 8;
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int q = 0; q < 8; q += 2) {
-              float v0 = xs[(r8 * 8 + q) * nmma + c];
-              float v1 = xs[(r8 * 8 + q + 1) * nmma + c];
-              if (c >= aa.ncols || jh0 + q >= nh) v0 = 0.f;
-              if (c >= aa.ncols || jh0 + q + 1 >= nh) v1 = 0.f;
-              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-              const float2 hf = __bfloat1622float2(h2);
-              const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-              hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
-              lw[q / 2] = *reinterpret_cast<const uint32_t*>(&l2);
-            }
-            const uint32_t o = sw128_offset(c, r8 * 8);
-            *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-          }
+          split_x_mn(reinterpret_cast<const float*>(sX + s * xbytes), nmma, aa.ncols, kb * kBK, nh,
+                     sB_hi + s * bbytes, sB_lo + s * bbytes, pt);
           fence_async_smem();
           mbar_arrive(&ctl.fullB[s]);
         }
@@ -481,16 +513,17 @@ struct HeatArgs {
 
 __device__ __forceinline__ int heat_work(int r, int c, int G) { return r * G + ((r & 1) ? G - 1 - c : c); }
 
-template <int kStages>
+template <int kStages, bool XS>
 __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant__ CUtensorMap t_hi,
                                                            const __grid_constant__ CUtensorMap t_lo,
-                                                           const __grid_constant__ CUtensorMap t_x, HeatArgs ha) {
+                                                           const __grid_constant__ CUtensorMap t_x,
+                                                           const __grid_constant__ CUtensorMap t_x2, HeatArgs ha) {
   extern __shared__ uint8_t smraw[];
   __shared__ HeatTcSmem ctl;
   uint8_t* base = align1k(smraw);
   const int nmma = ha.nmma, nh = ha.nh;
-  const int bbytes = nmma * kBK * 2;
-  const int xbytes = nmma * kBK * 4;
+  const int bbytes = mn_atoms(nmma) * kXsBoxBytes;   // analysis B, MN-major
+  const int xbytes = XS ? 0 : nmma * kBK * 4;
   const int sbytes = 2 * kATileBytes + xbytes + 2 * bbytes;   // one pipeline stage
   const int cbytes = nmma * 128;                              // one 64-row chunk of C (hi or lo)
   uint8_t* cbuf_hi = base + kStages * sbytes;
@@ -545,13 +578,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
           for (int kb = 0; kb < nkbA; ++kb, ++it) {
             const int s = it % kStages, n = it / kStages;
             if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
-            mbar_arrive_expect_tx(&ctl.full[s], 2 * kATileBytes + xbytes);
+            mbar_arrive_expect_tx(&ctl.full[s], 2 * kATileBytes + (XS ? 2 * kXsBoxBytes : xbytes));
             const int y = ro + mt * kBM, x = kb * kBK;
             tma_load_2d(sA_hi(s), &t_hi, &ctl.full[s], x, y);
             tma_load_2d(sA_hi(s) + kATileBytes / 2, &t_hi, &ctl.full[s], x, y + 64);
             tma_load_2d(sA_lo(s), &t_lo, &ctl.full[s], x, y);
             tma_load_2d(sA_lo(s) + kATileBytes / 2, &t_lo, &ctl.full[s], x, y + 64);
-            tma_load_2d(sX(s), &t_x, &ctl.full[s], 0, blk * nh + kb * kBK);
+            if (XS) {
+              tma_load_2d(sB_hi(s), &t_x, &ctl.full[s], 0, blk * nh + kb * kBK);
+              tma_load_2d(sB_lo(s), &t_x2, &ctl.full[s], 0, blk * nh + kb * kBK);
+            } else {
+              tma_load_2d(sX(s), &t_x, &ctl.full[s], 0, blk * nh + kb * kBK);
+            }
           }
         for (int nt = 0; nt < nnt && ok; ++nt)
           for (int kb = 0; kb < nkbS; ++kb, ++it) {
@@ -570,7 +608,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      const uint32_t id_a = idesc_bf16(kBM, nmma);       // analysis: both operands K-major
+      // analysis: A K-major; B K-major (split in shared memory) or MN-major (XS, from TMA)
+      const uint32_t id_a = idesc_bf16(kBM, nmma) | (1u << 16);
       const uint32_t id_s = idesc_bf16_amn(kBM, nmma);   // synthesis: A (table) MN-major
       int it = 0, nb = 0;
       int ause[kMaxSlots] = {0}, suse[kMaxSlots] = {0};
@@ -588,7 +627,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
           for (int kb = 0; kb < nkbA; ++kb, ++it) {
             const int s = it % kStages, n = it / kStages;
             ok = mbar_wait(&ctl.full[s], n & 1, abort);
-            if (ok) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);
+            if (ok && !XS) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);
             if (!ok) break;
             tc_fence_after();
             const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
@@ -596,9 +635,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k) {
               const uint32_t off = k * 32;
-              umma_bf16(d, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bh + off), id_a, (kb | k) != 0);
-              umma_bf16(d, desc_sw128_kmajor(ah + off), desc_sw128_kmajor(bl + off), id_a, 1);
-              umma_bf16(d, desc_sw128_kmajor(al + off), desc_sw128_kmajor(bh + off), id_a, 1);
+              const uint64_t b_h = desc_sw128_mnmajor(bh + k * 2048, kXsBoxBytes, 1024);
+              const uint64_t b_l = desc_sw128_mnmajor(bl + k * 2048, kXsBoxBytes, 1024);
+              umma_bf16(d, desc_sw128_kmajor(ah + off), b_h, id_a, (kb | k) != 0);
+              umma_bf16(d, desc_sw128_kmajor(ah + off), b_l, id_a, 1);
+              umma_bf16(d, desc_sw128_kmajor(al + off), b_h, id_a, 1);
             }
             umma_commit(&ctl.empty[s]);
           }
@@ -619,7 +660,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
           for (int kb = 0; kb < nkbS; ++kb, ++it) {
             const int s = it % kStages, n = it / kStages;
             ok = mbar_wait(&ctl.full[s], n & 1, abort);
-            if (ok) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);   // keeps the stage phases aligned
+            if (ok && !XS) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);   // keeps the stage phases aligned
             if (!ok) break;
             tc_fence_after();
             const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
@@ -645,10 +686,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
     }
   } else if (warp < 4) {
     // split the FP32 X tile of every analysis stage into bf16 hi/lo, K-major [c][jh]; every
-    // stage (analysis or synthesis) is released to the MMA issuer through fullB
+    // stage (analysis or synthesis) is released to the MMA issuer through fullB (not used
+    // with XS: the spectra arrive split)
     const int pt = threadIdx.x - 64;
     int it = 0;
-    bool ok = true;
+    bool ok = !XS;
     for (int r = 0; r < rounds && ok; ++r) {
       const int w = heat_work(r, blockIdx.x, G);
       if (w >= ha.nwork) continue;
@@ -659,29 +701,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
         for (int kb = 0; kb < nkbA; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
           if (!(ok = mbar_wait(&ctl.full[s], n & 1, abort))) break;
-          const float* xs = reinterpret_cast<const float*>(sX(s));
-          uint8_t* bh = sB_hi(s);
-          uint8_t* bl = sB_lo(s);
-          for (int e = pt; e < 8 * nmma; e += 64) {
-            const int r8 = e / nmma, c = e - r8 * nmma;
-            const int jh0 = kb * kBK + r8 * 8;
-            uint32_t hw[4], lw[4];
-#pragma unroll
-            for (int q = 0; q < 8; q += 2) {
-              float v0 = xs[(r8 * 8 + q) * nmma + c];
-              float v1 = xs[(r8 * 8 + q + 1) * nmma + c];
-              if (c >= ha.ncols || jh0 + q >= nh) v0 = 0.f;
-              if (c >= ha.ncols || jh0 + q + 1 >= nh) v1 = 0.f;
-              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-              const float2 hf = __bfloat1622float2(h2);
-              const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-              hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
-              lw[q / 2] = *reinterpret_cast<const uint32_t*>(&l2);
-            }
-            const uint32_t o = sw128_offset(c, r8 * 8);
-            *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-            *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-          }
+          split_x_mn(reinterpret_cast<const float*>(sX(s)), nmma, ha.ncols, kb * kBK, nh, sB_hi(s), sB_lo(s), pt);
           fence_async_smem();
           mbar_arrive(&ctl.fullB[s]);
         }
@@ -845,8 +865,11 @@ int make_map_f32(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t row
   return SHOT_OK;
 }
 
+// with_x: analysis (MN-major B of mn_atoms(nmma) 8 KB atoms, plus the FP32 spectra tile);
+// otherwise synthesis (K-major B of nmma rows)
 size_t tc_smem_bytes(int nmma, bool with_x, int stages) {
-  return 1024 + (size_t)stages * (2 * kATileBytes + 2 * nmma * kBK * 2 + (with_x ? nmma * kBK * 4 : 0));
+  const size_t b = with_x ? (size_t)mn_atoms(nmma) * kXsBoxBytes : (size_t)nmma * kBK * 2;
+  return 1024 + (size_t)stages * (2 * kATileBytes + 2 * b + (with_x ? nmma * kBK * 4 : 0));
 }
 
 }  // namespace
@@ -862,7 +885,7 @@ static int host_tmem_cols(int n) {
 int tc_supported_fields(int nf) { return tc_nmma(nf) <= 256; }
 
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                       bool apply_h, cudaStream_t st, const ProbState* colscale) {
+                       bool apply_h, cudaStream_t st, const ProbState* colscale, int xsplit) {
   const Workspace& w = g.ws;
   const int nmma = tc_nmma(nf);
   if (nmma > 256 || nmma > w.nmma_cap) {
@@ -872,7 +895,32 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
   int rc;
   AnaArgs aa{};
   SynArgs sa{};
-  if (ana) {
+  if (ana && xsplit) {
+    // spectra already split (bf16 hi/lo [blk nh + jh][ldc]): B by TMA, four stages
+    if (nmma > 64 || ldc % 8 != 0) {
+      set_error("split spectra need at most 32 fields and ldc a multiple of 8");
+      return SHOT_ERR_UNSUPPORTED;
+    }
+    const __nv_bfloat16* Xh = reinterpret_cast<const __nv_bfloat16*>(X);
+    const __nv_bfloat16* Xl = Xh + (size_t)g.nblk * g.nh * ldc;
+    constexpr int stages = 4;
+    const size_t smem = 1024 + (size_t)stages * (2 * kATileBytes + 2 * kXsBoxBytes);
+    CUtensorMap mh, ml, xh, xl;
+    if ((rc = make_map(&mh, g.tab_hi, g.nh, g.rows_total, g.ldt, kBM))) return rc;
+    if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kBM))) return rc;
+    if ((rc = make_map(&xh, Xh, ldc, (uint64_t)g.nblk * g.nh, ldc, kBK))) return rc;
+    if ((rc = make_map(&xl, Xl, ldc, (uint64_t)g.nblk * g.nh, ldc, kBK))) return rc;
+    aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, nullptr, ldc, 2 * nf, nmma,
+                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4, colscale};
+    auto kern = k_legendre_tc<stages, true, true>;
+    SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int per_sm = (smem <= 113 * 1024 && 2 * 2 * host_tmem_cols(nmma) <= 512) ? 2 : 1;
+    const int grid = g.ntiles_ana < per_sm * g.num_sms ? g.ntiles_ana : per_sm * g.num_sms;
+    ProfScope prof(PK_ANALYSIS, st);
+    count_launch();
+    kern<<<grid, kTcThreads, smem, st>>>(mh, ml, xh, xl, aa, sa);
+    SHOT_CUDA(cudaGetLastError());
+  } else if (ana) {
     // deepest pipeline (<= 3 stages) whose tiles fit in one CTA's shared memory
     int stages = kStagesAna;
     if (g.active.nf == nf && g.active.tc_stages > 0) stages = g.active.tc_stages;
@@ -919,14 +967,16 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
 // SHOT_ERR_UNSUPPORTED (without launching) when the configuration does not fit: more than
 // 32 fields, TMEM slots, or shared memory; the caller then runs the two-kernel path.
 int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
-                   const ProbState* colscale) {
+                   const ProbState* colscale, int xsplit) {
   const Workspace& w = g.ws;
   const int nmma = tc_nmma(nf);
   if (nmma > 64 || g.nwork == 0) return SHOT_ERR_UNSUPPORTED;
   const int ncols_alloc = host_tmem_cols(nmma);
   const int nnt = (g.nh + kBM - 1) / kBM;
   if (g.nmt_max + nnt > 512 / ncols_alloc || g.nmt_max + nnt > kMaxSlots) return SHOT_ERR_UNSUPPORTED;
-  const size_t sbytes = 2 * kATileBytes + (size_t)nmma * kBK * 4 + 2 * (size_t)nmma * kBK * 2;
+  if (xsplit && ldc % 8 != 0) return SHOT_ERR_UNSUPPORTED;
+  const size_t sbytes = 2 * kATileBytes + 2 * (size_t)mn_atoms(nmma) * kXsBoxBytes +
+                        (xsplit ? 0 : (size_t)nmma * kBK * 4);
   const size_t cbytes = (size_t)nmma * 128;
   int stages = 3;
   while (stages > 2 && 1024 + stages * sbytes + 2 * g.kc_max * cbytes > 227 * 1024) --stages;
@@ -934,18 +984,27 @@ int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cud
   if (smem > 227 * 1024) return SHOT_ERR_UNSUPPORTED;
   if (smem < 120 * 1024) smem = 120 * 1024;   // one CTA per SM: it allocates all 512 TMEM columns
   int rc;
-  CUtensorMap mh, ml, mx;
+  CUtensorMap mh, ml, mx, mx2;
   if ((rc = make_map(&mh, g.tab_hi, g.nh, g.rows_total, g.ldt, 64))) return rc;
   if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, 64))) return rc;
-  if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
+  if (xsplit) {
+    const __nv_bfloat16* Xh = reinterpret_cast<const __nv_bfloat16*>(X);
+    const __nv_bfloat16* Xl = Xh + (size_t)g.nblk * g.nh * ldc;
+    if ((rc = make_map(&mx, Xh, ldc, (uint64_t)g.nblk * g.nh, ldc, kBK))) return rc;
+    if ((rc = make_map(&mx2, Xl, ldc, (uint64_t)g.nblk * g.nh, ldc, kBK))) return rc;
+  } else {
+    if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
+    mx2 = mx;
+  }
   HeatArgs ha{g.blk_order_d, g.nwork, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma, g.nmt_max, g.kc_max,
               g.h_d, colscale, Y, w.dev_int + 4};
-  auto kern = stages == 3 ? k_heat_tc<3> : k_heat_tc<2>;
+  auto kern = xsplit ? (stages == 3 ? k_heat_tc<3, true> : k_heat_tc<2, true>)
+                     : (stages == 3 ? k_heat_tc<3, false> : k_heat_tc<2, false>);
   SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int grid = g.nwork < g.num_sms ? g.nwork : g.num_sms;
   ProfScope prof(PK_ANALYSIS, st);
   count_launch();
-  kern<<<grid, kTcThreads, smem, st>>>(mh, ml, mx, ha);
+  kern<<<grid, kTcThreads, smem, st>>>(mh, ml, mx, mx2, ha);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }

@@ -134,6 +134,8 @@ struct Grid {
   int* blk_order_d = nullptr;   // blocks with rows, largest first (fused heat kernel)
   int nwork = 0, nmt_max = 0, kc_max = 0;
   int fused_heat = 0;           // BF16X3 table grids: fused analysis + synthesis kernel
+  int split_spectra = 0;        // BF16X3 table grids: the solver keeps bf16 hi/lo spectra
+  void* xyz_d = nullptr;        // node unit vectors (float4), made on first use
   int ntiles_ana = 0, ntiles_syn = 0;
   int bm_ana = 128, bm_syn = 128;
   Workspace ws;
@@ -173,16 +175,19 @@ struct EpiParams {
   int which;                  // 0: u-step (marginal p), 1: v-step (marginal q)
   float* xout;                // EPI_UPDATE: when set, the CTA also ring-transforms the new
                               // scaling (unscaled) into the folded spectra xout[.][jh][ldc]
+  int xsplit;                 // xout as bf16 hi/lo arrays (tensor-core operand) instead of FP32
 };
 bool profiling_on();
 
 // ---------------------------------------------------------------------------------
 // Launchers (return SHOT status)
 int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
-                   float* X, int ldc, cudaStream_t st);
+                   float* X, int ldc, cudaStream_t st, int xsplit = 0);
 int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
-                    const ProbState* colscale = nullptr);
+                    const ProbState* colscale = nullptr, int xsplit = 0);
+// whether the solver keeps its spectra as bf16 hi/lo (BF16X3 table grids, <= 32 fields)
+int spectra_split(const Grid& g, int nf, int ldc);
 int launch_heat_mult(const Grid& g, double t, cudaStream_t st);
 int launch_coeff_gather(const Grid& g, const float* C, int ldc, int nf, float* coeffs, cudaStream_t st);
 int launch_coeff_scatter(const Grid& g, const float* coeffs, int nf, float* C, int ldc, cudaStream_t st);
@@ -192,14 +197,14 @@ int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ld
 int build_grid_tables(Grid& g, cudaStream_t st);
 int autotune(Grid& g, int nf, cudaStream_t st);   // selects g.active for nf (tunes on first use)
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                       bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
+                       bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr, int xsplit = 0);
 int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
 int build_recurrence(Grid& g, cudaStream_t st);
 int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
                         bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
 int tc_nmma(int nf);
 int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
-                   const ProbState* colscale);
+                   const ProbState* colscale, int xsplit = 0);
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
 
 }  // namespace shot

@@ -61,6 +61,8 @@ RECIPES = {
     "vmf8": ("vmf", dict(ncomp=8, kappa_lo=10.0, kappa_hi=200.0)),
     "vmf8_zonal": ("vmf", dict(ncomp=8, kappa_lo=10.0, kappa_hi=200.0, zonal=True)),
     "vmf32": ("vmf", dict(ncomp=32, kappa_lo=50.0, kappa_hi=2000.0)),
+    # the heat-vs-matrix convolution comparison: one vMF density, kappa = 10, random mean
+    "vmf_k10": ("vmf", dict(ncomp=1, kappa_lo=10.0, kappa_hi=10.0, floor=0.0)),
 }
 
 

@@ -48,6 +48,9 @@ SIGNATURES = {
     "shot_grid_init_quad": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.c_int, ctypes.c_int, _vp],
     "shot_grid_free": [_vp],
+    "shot_gibbs_normaliser": [ctypes.c_double, _c_dbl_p],
+    "shot_gibbs_apply": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
+    "shot_conv_compare": [_vp, ctypes.c_double, _vp, ctypes.c_int, _c_dbl_p, _vp],
     "shot_grid_info": [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p],
     "shot_grid_nodes": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
     "shot_grid_reserve": [_vp, ctypes.c_int],
@@ -160,6 +163,25 @@ def shot_grid_init_quad(quadrature, nlat, nlon=None, lmax=-1, precision=SHOT_FP3
     _check(lib().shot_grid_init_quad(ctypes.byref(h), quadrature, nlat, nlon, lmax, precision, legendre_mode,
                                      _stream(stream)))
     return h
+
+
+def shot_gibbs_normaliser(eps):
+    c = ctypes.c_double()
+    _check(lib().shot_gibbs_normaliser(eps, ctypes.byref(c)))
+    return c.value
+
+
+def shot_gibbs_apply(g, eps, inp, out, stream=None):
+    return _check(lib().shot_gibbs_apply(g, eps, _dev_ptr(inp, "in"), _dev_ptr(out, "out"), inp.shape[0],
+                                         _stream(stream)))
+
+
+def shot_conv_compare(g, eps, inp, stream=None):
+    """Per-field mean |C(eps) H_{eps/4} f - K_eps f| over the grid nodes (numpy array)."""
+    mae = np.empty(inp.shape[0])
+    _check(lib().shot_conv_compare(g, eps, _dev_ptr(inp, "in"), inp.shape[0], _np_ptr(mae, ctypes.c_double),
+                                   _stream(stream)))
+    return mae
 
 
 def shot_grid_free(g):

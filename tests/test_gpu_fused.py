@@ -26,7 +26,7 @@ def _grid(monkeypatch, fused, nlat, nlon=None, lmax=-1, quad=shot.SHOT_QUAD_GAUS
 
 
 @pytest.mark.parametrize("nlat,nlon,lmax,nf,t", [(8, None, -1, 1, 0.1), (32, None, -1, 3, 0.01),
-                                                 (33, 72, -1, 2, 0.02), (65, 130, -1, 24, 3e-3),
+                                                 (33, 72, -1, 2, 0.02), (65, 135, -1, 24, 3e-3),
                                                  (180, None, -1, 5, 1e-3), (20, 45, 13, 3, 0.05),
                                                  (256, None, -1, 32, 1e-3), (64, None, -1, 40, 3e-3)])
 def test_fused_heat_apply_matches_oracle(monkeypatch, nlat, nlon, lmax, nf, t):
@@ -56,10 +56,10 @@ def test_fused_agrees_with_two_kernel_path(monkeypatch, nlat, nf):
 
 
 def test_fused_cc_grid(monkeypatch):
-    g = _grid(monkeypatch, True, 33, 66, -1, shot.SHOT_QUAD_CLENSHAW_CURTIS)
-    og = OGrid(33, 66, quadrature="cc")
-    f, f64 = f32(np.random.default_rng(5).uniform(size=(4, 33, 66)))
-    out = torch.empty((4, 33, 66), device="cuda")
+    g = _grid(monkeypatch, True, 33, 72, -1, shot.SHOT_QUAD_CLENSHAW_CURTIS)
+    og = OGrid(33, 72, quadrature="cc")
+    f, f64 = f32(np.random.default_rng(5).uniform(size=(4, 33, 72)))
+    out = torch.empty((4, 33, 72), device="cuda")
     shot.shot_heat_apply(g, 0.01, torch.from_numpy(f).cuda(), out)
     shot.shot_grid_free(g)
     assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, 0.01)) < TOL
@@ -89,3 +89,21 @@ def test_fused_720_full_size(monkeypatch):
     shot.shot_heat_apply(g, 1e-4, torch.from_numpy(f).cuda(), out)
     shot.shot_grid_free(g)
     assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, 1e-4)) < TOL
+
+
+@pytest.mark.parametrize("fused,split", [(False, False), (False, True), (True, False), (True, True)])
+def test_spectra_formats_agree_with_oracle(monkeypatch, fused, split):
+    # the solver's spectra as FP32 (split in shared memory) or as bf16 hi/lo written by the
+    # inverse DFT (TMA'd as an MN-major operand), with the two-kernel or the fused path
+    monkeypatch.setenv("SHOT_SPLIT_SPECTRA", "1" if split else "0")
+    g = _grid(monkeypatch, fused, 40)
+    og = OGrid(40)
+    p, q = inputs.pairs("paper_uniform", 7040, 3, og.x, og.nlon, og.a_ring)
+    p32, p64 = f32(p)
+    q32, q64 = f32(q)
+    rc, r = shot.shot_divergence(g, torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), 0.05,
+                                 max_iter=50, tol=0.0, check_every=10)
+    shot.shot_grid_free(g)
+    ref = sk.divergence(og, p64, q64, 0.05, T=50, delta=0.0, C=10)
+    assert np.all(r["status"] == 0) and np.all(ref["status"] == 0)
+    assert np.all(s_err_prec(r["S"], ref["S"], ref["runs"]["ot"][:3], TOL, "bf16x3") <= 1.0)

@@ -101,3 +101,23 @@ def test_cc_endpoint_halving_dropped_caught():
     for k in range(0, N + 1, 2):
         w += (2.0 / N) * np.cos(np.pi * k * j / N) * (2.0 / (1.0 - k * k)) * (0.5 if k in (0, N) else 1.0)
     assert abs(np.sum(w * x ** 2) - 2.0 / 3.0) > 1e-3
+
+
+def test_normaliser_without_jacobian_caught(monkeypatch):
+    # C(eps) integrated without the sin(theta) surface element: the small-eps series pin
+    # (C = pi eps - pi eps^2 / 6 + ...) must fail
+    from scipy import integrate
+    eps = 1e-2
+    bad = 2 * np.pi * integrate.quad(lambda th: np.exp(-th * th / eps), 0.0, np.pi)[0]
+    series = 2 * np.pi * (eps / 2 - eps ** 2 / 12 + eps ** 3 / 120)
+    assert abs(bad - series) > 1e-3
+
+
+def test_gibbs_without_area_weights_caught():
+    # matrix convolution that forgets a_j: its row sums no longer approach C(eps)
+    from oracle import convolution as cv
+    g = Grid(24, quadrature="cc")
+    X = g.xyz.reshape(-1, 3)
+    d = cv.geodesic(X[:1, None, :], X[None, :, :])[0]
+    bad_rowsum = np.exp(-d * d / 0.5).sum()
+    assert abs(bad_rowsum / cv.gibbs_normaliser(0.5) - 1.0) > 1e-2
