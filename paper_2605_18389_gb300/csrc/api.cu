@@ -300,6 +300,8 @@ int ensure_stream(Grid& g) {
   return SHOT_OK;
 }
 
+EpiParams base_ep(Solve& s);
+
 int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector<const float*>& Q,
                   const std::vector<double>& taus, double eps, double tol, int C, int flags, float* u, float* v,
                   cudaStream_t user, Solve& s) {
@@ -337,10 +339,16 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
     k_fill<<<1024, 256, 0, s.st>>>(v, n * nprob, 1.f);
   }
   SHOT_CUDA(cudaGetLastError());
-  if ((rc = autotune(g, nprob, s.st))) return rc;
+  s.xs = spectra_split(g, nprob, w.ldc);
+  {  // tune the launch shapes on the solver's own form of the inverse DFT
+    EpiParams up = base_ep(s);
+    up.mode = EPI_UPDATE;
+    up.marg = w.marg;
+    up.xout = w.XY;
+    if ((rc = autotune(g, nprob, s.st, &up))) return rc;
+  }
   if ((rc = launch_heat_mult(g, eps / 4.0, s.st))) return rc;
   // spectra of the starting v (unscaled; the analysis applies beta per column)
-  s.xs = spectra_split(g, nprob, w.ldc);
   return launch_dft_fwd(g, v, nprob, nullptr, 0, w.XY, w.ldc, s.st, s.xs);
 }
 
@@ -657,8 +665,7 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo, g->tabT_hi,
-                  g->tabT_lo,
+  void* dptr[] = {g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo,
                   g->ws.ct_hi, g->ws.ct_lo, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};

@@ -31,7 +31,9 @@ int time_ms(float* out, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, const s
 
 }  // namespace
 
-int autotune(Grid& g, int nf, cudaStream_t st) {
+// upd: when given (the solver), the inverse DFT is timed in the solver's form (Sinkhorn
+// update + forward transform of the new scaling) rather than as a plain transform.
+int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd) {
   for (const Tuning& t : g.tuning)
     if (t.nf == nf) {
       g.active = t;
@@ -85,7 +87,12 @@ int autotune(Grid& g, int nf, cudaStream_t st) {
     if (fg <= nf && fg * g.nlon <= 6400) fgs.push_back(fg);
   if (fgs.empty()) fgs.push_back(1);
   auto run_fwd = [&]() { return launch_dft_fwd(g, fld, nf, nullptr, 0, w.XY, w.ldc, st); };
-  auto run_inv = [&]() { return launch_idft(g, w.XY, w.ldc, nf, ep, st); };
+  EpiParams ep_upd{};
+  if (upd) {
+    ep_upd = *upd;
+    ep_upd.out = fld;
+  }
+  auto run_inv = [&]() { return launch_idft(g, w.XY, w.ldc, nf, upd ? ep_upd : ep, st); };
   auto run_leg = [&]() { return launch_legendre(g, nf, w.XY, w.C, w.XY, w.ldc, st); };
   auto pick_vec = [&](int* slot, const std::vector<int>& c, const std::function<int()>& fn) -> int {
     float best = FLT_MAX;

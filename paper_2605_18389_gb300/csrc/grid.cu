@@ -96,8 +96,7 @@ __global__ void k_area(int nlat, int nlon, const double* __restrict__ w, float* 
 // One thread per (m, jh); row l goes to block (m, (l-m) mod 2), row (l-m)/2.
 __global__ void k_pbar(int lmax, int nh, const double* __restrict__ x, const long long* __restrict__ row_off,
                        int ldt, float* __restrict__ tab, __nv_bfloat16* __restrict__ hi,
-                       __nv_bfloat16* __restrict__ lo, int ldi, __nv_bfloat16* __restrict__ thi,
-                       __nv_bfloat16* __restrict__ tlo) {
+                       __nv_bfloat16* __restrict__ lo) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (j >= nh) return;
@@ -115,9 +114,6 @@ __global__ void k_pbar(int lmax, int nh, const double* __restrict__ x, const lon
       const __nv_bfloat16 l = __double2bfloat16(val - (double)__bfloat162float(h));
       hi[off] = h;
       lo[off] = l;
-      const size_t offT = ((size_t)blk * nh + j) * ldi + (d >> 1);
-      thi[offT] = h;
-      tlo[offT] = l;
     }
   };
   store(m, pmm);
@@ -321,15 +317,10 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
     SHOT_CUDA(cudaMemsetAsync(g.tab_lo, 0, tab_elems * sizeof(__nv_bfloat16), st));
     hi = g.tab_hi;
     lo = g.tab_lo;
-    const size_t tT = (size_t)g.nblk * nh * g.ldi;
-    SHOT_CUDA(cudaMalloc(&g.tabT_hi, tT * sizeof(__nv_bfloat16)));
-    SHOT_CUDA(cudaMalloc(&g.tabT_lo, tT * sizeof(__nv_bfloat16)));
-    SHOT_CUDA(cudaMemsetAsync(g.tabT_hi, 0, tT * sizeof(__nv_bfloat16), st));
-    SHOT_CUDA(cudaMemsetAsync(g.tabT_lo, 0, tT * sizeof(__nv_bfloat16), st));
   }
   dim3 gp((nh + 127) / 128, L);
   count_launch();
-  k_pbar<<<gp, 128, 0, st>>>(g.lmax, nh, g.x_d, g.row_off_d, g.ldt, tab, hi, lo, g.ldi, g.tabT_hi, g.tabT_lo);
+  k_pbar<<<gp, 128, 0, st>>>(g.lmax, nh, g.x_d, g.row_off_d, g.ldt, tab, hi, lo);
   SHOT_CUDA(cudaGetLastError());
   }
 

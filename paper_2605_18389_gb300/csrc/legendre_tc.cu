@@ -5,10 +5,12 @@
 //   synthesis  Y[jh][c] = sum_i Pbar_lm(x_jh) C[i][c]               (K = degrees i)
 // Both operands are split into bf16 hi + lo (v = hi + lo, |lo| <= 2^-9 |v|) and the
 // product is accumulated in FP32 in tensor memory as A_hi B_hi + A_hi B_lo + A_lo B_hi
-// (the lo*lo term, ~2^-18 relative, is dropped).  Operands are K-major, 128-byte
-// swizzled in shared memory: the table tiles come by TMA (the synthesis reads a
-// transposed copy of the table so that its A operand is K-major as well); the analysis
-// B operand (the FP32 ring spectra X) is split and transposed by four producer warps.
+// (the lo*lo term, ~2^-18 relative, is dropped).  Operands are 128-byte swizzled in
+// shared memory.  The table [i][jh] (jh contiguous) comes by TMA and serves both
+// contractions: K-major A of the analysis (K = jh), MN-major A of the synthesis (M = jh).
+// The analysis B operand (the FP32 ring spectra X, [jh][c]) is split into hi/lo by two
+// warps in the MN-major layout it already has (or arrives split, bf16 hi/lo, by TMA); the
+// synthesis B operand is C^T (K-major, bf16 hi/lo, written by the analysis epilogue).
 // One elected thread issues tcgen05.mma (M = 128, N = 2*nfields rounded to 16, K = 16);
 // tcgen05.commit releases the pipeline stages; four warps read the accumulator with
 // tcgen05.ld for the epilogue.  Every mbarrier wait is bounded; on expiry the CTA
@@ -249,6 +251,7 @@ struct SynArgs {
   const Tile* tiles;
   int ntiles;
   const int* M;
+  const long long* row_off;
   int nh;
   int nmma, nmma_cap, ncols, ldc;
   float* Y;   // [blk][jh][ldc]
@@ -333,10 +336,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
             tma_load_2d(sA_lo + s * kATileBytes, &ta_lo, &ctl.fullA[s], kb * kBK, y);
             tma_load_2d(sX + s * xbytes, &tb_hi, &ctl.fullA[s], 0, tl.blk * nh + kb * kBK);
           } else {
+            // A = the table's rows i (K) of this K-chunk, nodes r0 .. r0+127 (M, contiguous):
+            // two 64-node boxes 8 KB apart, read as an MN-major operand
             mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + 2 * bbytes);
-            const int y = tl.blk * nh + tl.r0;
-            tma_load_2d(sA_hi + s * kATileBytes, &ta_hi, &ctl.fullA[s], kb * kBK, y);
-            tma_load_2d(sA_lo + s * kATileBytes, &ta_lo, &ctl.fullA[s], kb * kBK, y);
+            const int y = (int)sa.row_off[tl.blk] + kb * kBK;
+            tma_load_2d(sA_hi + s * kATileBytes, &ta_hi, &ctl.fullA[s], tl.r0, y);
+            tma_load_2d(sA_hi + s * kATileBytes + kATileBytes / 2, &ta_hi, &ctl.fullA[s], tl.r0 + 64, y);
+            tma_load_2d(sA_lo + s * kATileBytes, &ta_lo, &ctl.fullA[s], tl.r0, y);
+            tma_load_2d(sA_lo + s * kATileBytes + kATileBytes / 2, &ta_lo, &ctl.fullA[s], tl.r0 + 64, y);
             tma_load_2d(sB_hi + s * bbytes, &tb_hi, &ctl.fullA[s], kb * kBK, tl.blk * sa.nmma_cap);
             tma_load_2d(sB_lo + s * bbytes, &tb_lo, &ctl.fullA[s], kb * kBK, tl.blk * sa.nmma_cap);
           }
@@ -348,8 +355,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      // analysis: B (spectra) MN-major; synthesis: B (C^T) K-major
-      const uint32_t idesc = ANA ? (idesc_bf16(kBM, nmma) | (1u << 16)) : idesc_bf16(kBM, nmma);
+      // analysis: A (table) K-major, B (spectra) MN-major; synthesis: A (table) MN-major,
+      // B (C^T) K-major
+      const uint32_t idesc = ANA ? (idesc_bf16(kBM, nmma) | (1u << 16)) : idesc_bf16_amn(kBM, nmma);
       int it = 0, lt = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
@@ -378,9 +386,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
               b_h = desc_sw128_kmajor(bh + off);
               b_l = desc_sw128_kmajor(bl + off);
             }
-            umma_bf16(d, desc_sw128_kmajor(ah + off), b_h, idesc, (kb | k) != 0);
-            umma_bf16(d, desc_sw128_kmajor(ah + off), b_l, idesc, 1);
-            umma_bf16(d, desc_sw128_kmajor(al + off), b_h, idesc, 1);
+            uint64_t a_h, a_l;
+            if (ANA) {
+              a_h = desc_sw128_kmajor(ah + off);
+              a_l = desc_sw128_kmajor(al + off);
+            } else {   // 16 K-rows (two 8-row groups) of two 64-node atoms
+              a_h = desc_sw128_mnmajor(ah + k * 2048, kATileBytes / 2, 1024);
+              a_l = desc_sw128_mnmajor(al + k * 2048, kATileBytes / 2, 1024);
+            }
+            umma_bf16(d, a_h, b_h, idesc, (kb | k) != 0);
+            umma_bf16(d, a_h, b_l, idesc, 1);
+            umma_bf16(d, a_l, b_h, idesc, 1);
           }
           umma_commit(&ctl.empty[s]);
         }
@@ -945,11 +961,11 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
   if (syn) {
     const size_t smem = tc_smem_bytes(nmma, false, kStagesSyn);
     CUtensorMap ah, al, bh, bl;
-    if ((rc = make_map(&ah, g.tabT_hi, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kBM))) return rc;
-    if ((rc = make_map(&al, g.tabT_lo, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kBM))) return rc;
+    if ((rc = make_map(&ah, g.tab_hi, g.nh, g.rows_total, g.ldt, 64))) return rc;
+    if ((rc = make_map(&al, g.tab_lo, g.nh, g.rows_total, g.ldt, 64))) return rc;
     if ((rc = make_map(&bh, w.ct_hi, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
     if ((rc = make_map(&bl, w.ct_lo, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
-    sa = SynArgs{g.tiles_syn, g.ntiles_syn, g.M_d, g.nh, nmma, w.nmma_cap, 2 * nf, ldc, Y, w.dev_int + 4};
+    sa = SynArgs{g.tiles_syn, g.ntiles_syn, g.M_d, g.row_off_d, g.nh, nmma, w.nmma_cap, 2 * nf, ldc, Y, w.dev_int + 4};
     auto kern = k_legendre_tc<kStagesSyn, false>;
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: both shared memory and the 512 TMEM columns (two accumulators each) must fit

@@ -119,9 +119,7 @@ struct Grid {
   float* tab = nullptr;         // FP32 folded table
   __nv_bfloat16* tab_hi = nullptr;  // BF16X3 split table [row][ldt]
   __nv_bfloat16* tab_lo = nullptr;
-  __nv_bfloat16* tabT_hi = nullptr;  // BF16X3 transposed copy [blk][jh][ldi]
-  __nv_bfloat16* tabT_lo = nullptr;
-  int ldi = 0;                  // row stride of the transposed table (>= max M, multiple of 8)
+  int ldi = 0;                  // row stride of C^T (>= the largest block, multiple of 8)
   // SHOT_RECURRENCE: seeds per (m, node) and recurrence coefficients (O(n) memory)
   void* rec_seeds = nullptr;
   void* rec_coef = nullptr;
@@ -195,7 +193,8 @@ int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int l
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st);
 int build_grid_tables(Grid& g, cudaStream_t st);
-int autotune(Grid& g, int nf, cudaStream_t st);   // selects g.active for nf (tunes on first use)
+// selects g.active for nf (tunes on first use)
+int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd = nullptr);
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
                        bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr, int xsplit = 0);
 int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
