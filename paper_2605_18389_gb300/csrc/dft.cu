@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
             if (r == 1 && !two) { u2[1] = 0.f; break; }
             const float kv = r ? zz.y : zz.x;
             const float pm = pv[b][r];
-            const float ratio = pm / kv;
+            const float ratio = __fdividef(pm, kv);   // MUFU reciprocal + multiply, <= 2 ulp
             float u;
             if (bal) {
               u = ratio;
