@@ -136,11 +136,13 @@ def sinkhorn(grid, p, q, eps, tau=np.inf, T=500, delta=0.0, C=10, norm="l2",
         mass = np.sum(a * u * kv, axis=(1, 2))
         phi = eps * np.log(u)
         psi = eps * np.log(v)
+        # a node with zero marginal contributes its limit, 0 (where p = 0, u = 0 and phi = -inf)
         if balanced:
-            ot = np.sum(a * (phi * p + psi * q), axis=(1, 2))
+            tp, tq = phi * p, psi * q
         else:
-            ot = np.sum(a * (tau * (1.0 - np.exp(-phi / tau)) * p
-                             + tau * (1.0 - np.exp(-psi / tau)) * q), axis=(1, 2))
+            tp = tau * (1.0 - np.exp(-phi / tau)) * p
+            tq = tau * (1.0 - np.exp(-psi / tau)) * q
+        ot = np.sum(a * (np.where(p > 0, tp, 0.0) + np.where(q > 0, tq, 0.0)), axis=(1, 2))
     broke = status < 0
     for arr in (err, mass, ot):
         arr[broke] = np.nan

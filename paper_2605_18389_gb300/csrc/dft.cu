@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_dft_fwd(
   unpack_fold_store<FG>(buf, nfg, f0, N, lmax, nh, jh, a_ring[j], ps, scale_which, X, ldc, xsplit);
 }
 
-template <int FG>
+template <int FG, class PL = RuntimePlan>
 __global__ void __launch_bounds__(kThreads, 3) k_idft(
     const float* __restrict__ Y, int ldc, int nf, int nlat, int nlon, int lmax, int nh,
     const float* __restrict__ a_ring, FftPlan pl, const float2* __restrict__ tw_g, EpiParams ep) {
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
     }
   }
   __syncthreads();
-  const float2* z = fft_smem<true>(buf, b1, tw, pl, nfg);
+  const float2* z = fft_smem_plan<true, PL>(buf, b1, tw, pl, nfg);
   float2* other = (z == buf) ? b1 : buf;   // input of the fused forward transform
 
   const float aj = a_ring[j];
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
   if (ep.mode == EPI_UPDATE && ep.xout) {
     // the new scaling of this ring pair is in `other`: transform it for the next half-step
     __syncthreads();
-    const float2* zf = fft_smem<false>(other, const_cast<float2*>(z), tw, pl, nfg);
+    const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw, pl, nfg);
     unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc, ep.xsplit);
   }
 }
@@ -376,18 +376,26 @@ int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, in
   return SHOT_OK;
 }
 
-template <int FG>
+template <int FG, class PL = RuntimePlan>
 int launch_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
   // two sequence buffers (the second also stages the gathered spectra) and the twiddles
   const size_t smem = (size_t)(g.nlon + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
-  SHOT_CUDA(cudaFuncSetAttribute(k_idft<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  SHOT_CUDA(cudaFuncSetAttribute(k_idft<FG, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
   ProfScope prof(PK_IDFT, st);
   count_launch();
-  k_idft<FG><<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, ep);
+  k_idft<FG, PL><<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, ep);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }
+
+// the runtime plan equals the compile-time one (same N and radices in the same order)
+template <class PL>
+bool plan_is(const FftPlan& p) {
+  return p.N == PL::N && p.nst == 3 && p.R[0] == PL::R0 && p.R[1] == PL::R1 && p.R[2] == PL::R2;
+}
+using Plan1440 = CtPlan<1440, 15, 8, 12>;   // 720 x 1440 grids
+using Plan1024 = CtPlan<1024, 4, 16, 16>;   // 512 x 1024 grids
 
 }  // namespace
 
@@ -414,6 +422,12 @@ int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams&
   }
   int fg = pick_fg(g.nlon, nf);
   if (g.active.nf == nf && g.active.idft_fg > 0 && g.active.idft_fg * g.nlon <= kFftCap) fg = g.active.idft_fg;
+  if (fg == 2 || fg == 4) {   // plans compiled for the common ring lengths
+    if (plan_is<Plan1440>(g.plan))
+      return fg == 2 ? launch_idft_t<2, Plan1440>(g, Y, ldc, nf, ep, st) : launch_idft_t<4, Plan1440>(g, Y, ldc, nf, ep, st);
+    if (plan_is<Plan1024>(g.plan))
+      return fg == 2 ? launch_idft_t<2, Plan1024>(g, Y, ldc, nf, ep, st) : launch_idft_t<4, Plan1024>(g, Y, ldc, nf, ep, st);
+  }
   switch (fg) {
     case 8: return launch_idft_t<8>(g, Y, ldc, nf, ep, st);
     case 4: return launch_idft_t<4>(g, Y, ldc, nf, ep, st);

@@ -291,4 +291,62 @@ __device__ float2* fft_smem(float2* a, float2* b, const float2* tw, const FftPla
   return a;
 }
 
+// ---- plans fixed at compile time ---------------------------------------------------
+// The same Stockham stages with N, the radices and the spans as template constants: the
+// divisions by N/R and Ns become multiply-shifts and every load, twiddle and store offset an
+// immediate.  CtPlan<0> is the runtime plan.
+template <int N_, int R0_ = 1, int R1_ = 1, int R2_ = 1>
+struct CtPlan {
+  static constexpr int N = N_, R0 = R0_, R1 = R1_, R2 = R2_;
+};
+using RuntimePlan = CtPlan<0>;
+
+template <int R, bool INV, int N, int NS, int TWOFF>
+__device__ __forceinline__ void stockham_stage_ct(const float2* __restrict__ src, float2* __restrict__ dst,
+                                                  const float2* __restrict__ tw, int nseq) {
+  constexpr int NR = N / R, LD = N + 1;
+  const int total = nseq * NR;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int q = idx / NR;
+    const int j = idx - q * NR;
+    const int jd = j / NS;
+    const int k = j - jd * NS;
+    const float2* s = src + q * LD + j;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = s[r * NR];
+    if constexpr (NS > 1) {
+      const float2* tws = tw + TWOFF + k;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = INV ? cmulc(v[r], tws[(r - 1) * NS]) : cmul(v[r], tws[(r - 1) * NS]);
+    }
+    butterfly<R, INV>(v);
+    float2* d = dst + q * LD + jd * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) d[r * NS] = v[out_reg<R>(r)];
+  }
+}
+
+// three-stage compile-time plan; the twiddle table layout is the runtime plan's (stage s at
+// sum over earlier stages s' >= 1 of (R_s' - 1) Ns_s')
+template <bool INV, class PL>
+__device__ float2* fft_smem_ct(float2* a, float2* b, const float2* tw, int nseq) {
+  constexpr int N = PL::N, R0 = PL::R0, R1 = PL::R1, R2 = PL::R2;
+  static_assert(R0 * R1 * R2 == N, "plan radices must multiply to N");
+  stockham_stage_ct<R0, INV, N, 1, 0>(a, b, tw, nseq);
+  __syncthreads();
+  stockham_stage_ct<R1, INV, N, R0, 0>(b, a, tw, nseq);
+  __syncthreads();
+  stockham_stage_ct<R2, INV, N, R0 * R1, (R1 - 1) * R0>(a, b, tw, nseq);
+  __syncthreads();
+  return b;
+}
+
+template <bool INV, class PL>
+__device__ __forceinline__ float2* fft_smem_plan(float2* a, float2* b, const float2* tw, const FftPlan& pl,
+                                                 int nseq) {
+  if constexpr (PL::N == 0) return fft_smem<INV>(a, b, tw, pl, nseq);
+  else return fft_smem_ct<INV, PL>(a, b, tw, nseq);
+}
+
 }  // namespace shot

@@ -29,7 +29,8 @@ constexpr int kBK = 64;           // K elements per pipeline stage (one 128-byte
 constexpr int kMaxStages = 4;
 constexpr int kStagesAna = 3;   // one CTA per SM (table + X + B tiles)
 constexpr int kStagesSyn = 2;   // two CTAs per SM
-constexpr uint32_t kSpinLimit = 1u << 24;
+// Every wait is bounded by the SM clock: after ~2^30 cycles (~0.5 s at 2 GHz) it gives up.
+constexpr long long kWaitCycles = 1LL << 30;
 constexpr int kATileBytes = kBM * kBK * 2;   // 16 KB
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -44,24 +45,27 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t byte
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
-__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+// One potentially blocking probe: mbarrier.try_wait suspends the thread in hardware for a
+// bounded, system-dependent time, so waiting roles do not take issue slots from the working
+// ones the way a test_wait spin does.
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
       : "r"(smem_u32(b)), "r"(parity)
       : "memory");
   return ok != 0;
 }
+
 // Bounded wait that ignores the abort flag: used to let this CTA's own TMA copies land
 // before it exits.
 __device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
-    if (mbar_test(b, parity)) return;
-    if ((it & 255u) == 255u) __nanosleep(32);
-  }
+  const long long t0 = clock64();
+  while (!mbar_try(b, parity))
+    if (clock64() - t0 > kWaitCycles) return;
 }
 
 // Warp-uniform bounded wait: lane 0 waits, the verdict is broadcast to the warp (the
@@ -69,13 +73,15 @@ __device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort);
 
 // Bounded wait for the phase of the given parity.  Returns false (and raises the CTA's
-// abort flag) when the limit expires or another role already aborted.
+// abort flag) when the clock limit expires or another role already aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
-    if (mbar_test(b, parity)) return true;
-    if ((it & 255u) == 255u) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(b, parity)) return true;
+    if ((it & 15u) == 0) {
       if (*abort) return false;
-      __nanosleep(32);
+      if (clock64() - t0 > kWaitCycles) break;
     }
   }
   *abort = 1;
@@ -275,8 +281,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
                                                                AnaArgs aa, SynArgs sa) {
   extern __shared__ uint8_t smraw[];
   __shared__ TcSmem ctl;
+  __shared__ float cscale[256];   // analysis: per-column factor (gauge beta) as FP32
   uint8_t* base = align1k(smraw);
   const int nmma = ANA ? aa.nmma : sa.nmma;
+  if (ANA)
+    for (int c = threadIdx.x; c < nmma; c += blockDim.x)
+      cscale[c] = (aa.colscale && c < aa.ncols) ? (float)aa.colscale[c >> 1].beta : 1.f;
   const int nh = ANA ? aa.nh : sa.nh;
   const int ntiles = ANA ? aa.ntiles : sa.ntiles;
   const Tile* tiles = ANA ? aa.tiles : sa.tiles;
@@ -446,7 +456,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
             for (int e = 0; e < 16; ++e) {
               const int c = c0 + e;
               if (c < aa.ncols) {
-                const float val = v[e] * hl * (aa.colscale ? (float)aa.colscale[c >> 1].beta : 1.f);
+                const float val = v[e] * hl * cscale[c];
                 const __nv_bfloat16 hi = __float2bfloat16_rn(val);
                 const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
                 const size_t o = ((size_t)blk * aa.nmma_cap + c) * aa.ldi + row;
@@ -536,8 +546,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
                                                            const __grid_constant__ CUtensorMap t_x2, HeatArgs ha) {
   extern __shared__ uint8_t smraw[];
   __shared__ HeatTcSmem ctl;
+  __shared__ float cscale[256];
   uint8_t* base = align1k(smraw);
   const int nmma = ha.nmma, nh = ha.nh;
+  for (int c = threadIdx.x; c < nmma; c += blockDim.x)
+    cscale[c] = (ha.colscale && c < ha.ncols) ? (float)ha.colscale[c >> 1].beta : 1.f;
   const int bbytes = mn_atoms(nmma) * kXsBoxBytes;   // analysis B, MN-major
   const int xbytes = XS ? 0 : nmma * kBK * 4;
   const int sbytes = 2 * kATileBytes + xbytes + 2 * bbytes;   // one pipeline stage
@@ -756,7 +769,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
             for (int e = 0; e < 16; ++e) {
               const int c = c0 + e;
               float val = 0.f;
-              if (c < ha.ncols) val = v[e] * hl * (ha.colscale ? (float)ha.colscale[c >> 1].beta : 1.f);
+              if (c < ha.ncols) val = v[e] * hl * cscale[c];
               const __nv_bfloat16 hi = __float2bfloat16_rn(val);
               const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
               const uint32_t o = cb + sw128_offset(c, i & 63);
@@ -940,6 +953,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     // deepest pipeline (<= 3 stages) whose tiles fit in one CTA's shared memory
     int stages = kStagesAna;
     if (g.active.nf == nf && g.active.tc_stages > 0) stages = g.active.tc_stages;
+    if (g.tc_stages_override > 0) stages = g.tc_stages_override;
     while (stages > 1 && tc_smem_bytes(nmma, true, stages) > 227 * 1024) --stages;
     const size_t smem = tc_smem_bytes(nmma, true, stages);
     CUtensorMap mh, ml, mx;

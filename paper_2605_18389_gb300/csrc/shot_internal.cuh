@@ -133,6 +133,7 @@ struct Grid {
   int nwork = 0, nmt_max = 0, kc_max = 0;
   int fused_heat = 0;           // BF16X3 table grids: fused analysis + synthesis kernel
   int split_spectra = 0;        // BF16X3 table grids: the solver keeps bf16 hi/lo spectra
+  int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core analysis (0 = tuned)
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use
   int ntiles_ana = 0, ntiles_syn = 0;
   int bm_ana = 128, bm_syn = 128;

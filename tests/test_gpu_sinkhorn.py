@@ -116,3 +116,24 @@ def test_divergence_of_identical_measures_is_zero(grid_cache):
     pt, qt, p, q = _fields(og, "paper_uniform", 9, 2)
     rc, r = shot.shot_divergence(g, pt, pt, 0.2, max_iter=100, tol=0.0)
     assert np.all(r["S"] == 0.0)
+
+
+@pytest.mark.parametrize("tau", [math.inf, 1.0])
+def test_divergence_with_zero_marginal_entries(grid_cache, tau):
+    # p vanishes on a polar cap and q on a longitude sector: those nodes give u = 0 (v = 0)
+    # and contribute their limit 0 to the objective (a reading of the paper's dual form)
+    g, og = grid_cache(24)
+    rng = np.random.default_rng(24)
+    p, q = rng.uniform(size=(2, 2, og.nlat, og.nlon))
+    p[:, : og.nlat // 3] = 0.0
+    q[:, :, : og.nlon // 4] = 0.0
+    p /= np.sum(og.a * p, axis=(1, 2))[:, None, None]
+    q /= np.sum(og.a * q, axis=(1, 2))[:, None, None]
+    p32, p64 = f32(p)
+    q32, q64 = f32(q)
+    rc, r = shot.shot_divergence(g, torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), 0.2, tau,
+                                 max_iter=60, tol=0.0, check_every=10)
+    ref = sk.divergence(og, p64, q64, 0.2, tau, T=60, delta=0.0, C=10)
+    assert np.all(r["status"] == 0) and np.all(ref["status"] == 0)
+    assert np.all(np.isfinite(r["S"])) and np.all(np.isfinite(ref["S"]))
+    assert np.all(s_err(r["S"], ref["S"], ref["runs"]["ot"][:2], TOL_S) <= 1.0)

@@ -202,3 +202,20 @@ def test_regional_rms_invariants():
         w = g.w * m
         exp = np.sqrt(np.sum(w * lat ** 2) / np.sum(w))
         assert abs(rl[k] - exp) < 1e-10 * exp
+
+
+def test_zero_marginal_entries_are_the_limit_of_a_vanishing_floor():
+    # a node with p_i = 0 contributes its limit 0 to the objective: S with exact zeros
+    # equals the limit of S with a floor delta -> 0 (the iterates are continuous in p there)
+    g = Grid(10)
+    rng = np.random.default_rng(4)
+    p, q = rng.uniform(size=(2, g.nlat, g.nlon))
+    p[: g.nlat // 3] = 0.0                      # a polar cap without mass
+    q[:, : g.nlon // 4] = 0.0
+    def norm(f):
+        return f / np.sum(g.a * f)
+    S0 = sk.divergence(g, norm(p), norm(q), 0.5, T=200, C=0)["S"][0]
+    assert np.isfinite(S0)
+    Ss = [sk.divergence(g, norm(p + d), norm(q + d), 0.5, T=200, C=0)["S"][0] for d in (1e-6, 1e-8)]
+    assert abs(Ss[1] - S0) < 1e-5 * abs(S0) + 1e-9
+    assert abs(Ss[0] - S0) > abs(Ss[1] - S0)
