@@ -42,6 +42,8 @@ NONFINITE = -6
 def _kernel(grid, eps, kernel):
     t = eps / 4.0
     if kernel == "sht":
+        if hasattr(grid, "heat_apply"):   # grids with their own ring layout (HEALPix)
+            return lambda f: grid.heat_apply(f, t)
         return lambda f: heat_apply(grid, f, t)
     if kernel == "dense":
         K = kernel_matrix(grid, t)

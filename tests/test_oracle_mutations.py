@@ -121,3 +121,12 @@ def test_gibbs_without_area_weights_caught():
     d = cv.geodesic(X[:1, None, :], X[None, :, :])[0]
     bad_rowsum = np.exp(-d * d / 0.5).sum()
     assert abs(bad_rowsum / cv.gibbs_normaliser(0.5) - 1.0) > 1e-2
+
+
+def test_healpix_longitude_offset_dropped_caught():
+    # rings without their half-pixel longitude offset: the base-resolution pin fails
+    from oracle.healpix import HealpixGrid
+    g = HealpixGrid(1)
+    bad = 2 * np.pi * (np.arange(g.npix) - g.off[g.ring_of]) / g.npx[g.ring_of]
+    ph = np.sort(bad.reshape(3, 4) % (2 * np.pi), axis=1)
+    assert np.abs(ph[0] - (np.pi / 4 + np.pi / 2 * np.arange(4))).max() > 0.5
