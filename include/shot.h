@@ -59,6 +59,8 @@ extern "C" {
 #define SHOT_QUAD_GAUSS_LEGENDRE  0  /* nodes = roots of P_nlat; exact to degree 2 nlat - 1 */
 #define SHOT_QUAD_CLENSHAW_CURTIS 1  /* equiangular theta_j = pi j/(nlat-1), both poles included,
                                         Clenshaw-Curtis weights; exact to degree nlat - 1 */
+#define SHOT_QUAD_HEALPIX         2  /* HEALPix rings (shot_grid_init_healpix): equal-area pixels,
+                                        no exact quadrature */
 
 /* ---- solver flags -------------------------------------------------------- */
 #define SHOT_FLAG_NORM_L1     0x1  /* check sum_i a_i|u_i(Kv)_i - p_i| / sum_i a_i p_i instead of the relative L2 */
@@ -97,6 +99,31 @@ int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision,
  * Other arguments, memory and errors as shot_grid_init; nlat >= 3 for Clenshaw-Curtis. */
 int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int lmax, int precision,
                         int legendre_mode, void* stream);
+
+/* Build a HEALPix grid (App. C.1 "HEALPix"): N = 12 nside^2 equal-area pixels on 4 nside - 1
+ * iso-latitude rings.  Ring i (north to south, k = i + 1 mirrored into the north half) has
+ *   polar cap k < nside:  z = 1 - k^2/(3 nside^2), 4k pixels, first pixel at phi0 = pi/(4k);
+ *   belt nside <= k <= 2 nside: z = 4/3 - 2k/(3 nside), 4 nside pixels,
+ *                         phi0 = pi (2 - s)/(4 nside), s = (k - nside + 1) mod 2;
+ * pixel j of a ring at phi0 + 2 pi j / n (the HEALPix pixel centres; the cyclic order in a
+ * ring starts at phi0), every pixel with area 4 pi / N.  Fields are flat FP32 arrays of the N
+ * pixels in ring order ([batch][N] wherever the other calls say [batch][nlat][nlon]).  There is
+ * no exact quadrature: the heat operator is H diag(a) on the pixel centres (addition theorem).
+ *   nside in 1..4096; lmax = -1 means 3 nside - 1, else 0 <= lmax <= 4 nside - 2;
+ *   precision, legendre_mode as shot_grid_init.  shot_grid_info reports nlat = 4 nside - 1
+ *   rings and nlon = 4 nside (the longest ring).
+ * Supported on HEALPix grids: shot_heat_apply(_noalloc), shot_sht_analysis/synthesis,
+ * shot_sinkhorn, shot_divergence(_multi), shot_gibbs_apply, shot_conv_compare; the gradient and
+ * the regional attribution return SHOT_ERR_UNSUPPORTED.  Errors: INVALID_ARG, UNSUPPORTED,
+ * OOM, CUDA.  Synchronises `stream`. */
+int shot_grid_init_healpix(shot_grid* out, int nside, int lmax, int precision, int legendre_mode, void* stream);
+
+/* Number of nodes of one field (nlat * nlon, or 12 nside^2 on HEALPix) into *npix. */
+int shot_grid_npix(shot_grid g, long long* npix);
+
+/* Ring geometry into host arrays of nlat entries (any may be NULL): nodes per ring, offset of
+ * the ring's first node within a field, longitude of that node (0 on GL/CC grids). */
+int shot_grid_rings(shot_grid g, int* len, long long* off, double* phi0);
 
 /* Release every device resource of the handle (NULL is a no-op). */
 int shot_grid_free(shot_grid g);

@@ -55,7 +55,7 @@ def gibbs_apply(grid, f, eps, rows=1024):
 def conv_mae(grid, f, eps):
     """Mean absolute error between C(eps) * heat convolution at t = eps/4 and the matrix
     convolution, per field."""
-    h = sht.heat_apply(grid, f, eps / 4.0)
+    h = grid.heat_apply(f, eps / 4.0) if hasattr(grid, "heat_apply") else sht.heat_apply(grid, f, eps / 4.0)
     k = gibbs_apply(grid, f, eps)
     d = np.abs(gibbs_normaliser(eps) * h - k)
     return d.reshape(d.shape[:-2] + (-1,)).mean(axis=-1)

@@ -39,7 +39,7 @@ int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int l
 
 int spectra_split(const Grid& g, int nf, int ldc) {
   return (g.split_spectra && g.precision == SHOT_BF16X3 && g.mode == SHOT_TABLE && tc_nmma(nf) <= 64 &&
-          ldc % 8 == 0) ? 1 : 0;
+          ldc % 8 == 0 && g.quad != SHOT_QUAD_HEALPIX) ? 1 : 0;
 }
 
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
@@ -218,13 +218,15 @@ __global__ void k_fill(float* __restrict__ a, size_t n, float v) {
 
 // mass m(p) = sum_i a_i p_i of every listed field (FP64): per-ring partial sums by a
 // (ring, field) grid, then a fixed-order sum per field
-__global__ void k_field_mass_part(const float* const* __restrict__ fl, int nlat, int nlon,
-                                  const float* __restrict__ a_ring, double* __restrict__ part) {
+__global__ void k_field_mass_part(const float* const* __restrict__ fl, int nlat, const int* __restrict__ rlen,
+                                  const long long* __restrict__ roff, const float* __restrict__ a_ring,
+                                  double* __restrict__ part) {
   __shared__ float red[32];
   const int j = blockIdx.x, f = blockIdx.y;
-  const float* row = fl[f] + (size_t)j * nlon;
+  const float* row = fl[f] + roff[j];
+  const int n = rlen[j];
   float s = 0.f;
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x) s += row[k];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s += row[k];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -247,7 +249,7 @@ __global__ void k_field_mass_sum(int nfl, int nlat, const double* __restrict__ p
 // masses of nfl listed fields into out (device); part needs nfl*nlat doubles
 int field_masses(const Grid& g, const float* const* fl_d, int nfl, double* part, double* out, cudaStream_t st) {
   count_launch(2);
-  k_field_mass_part<<<dim3(g.nlat, nfl), 256, 0, st>>>(fl_d, g.nlat, g.nlon, g.a_d, part);
+  k_field_mass_part<<<dim3(g.nlat, nfl), 256, 0, st>>>(fl_d, g.nlat, g.ring_len_d, g.ring_off_d, g.a_d, part);
   k_field_mass_sum<<<(nfl + 127) / 128, 128, 0, st>>>(nfl, g.nlat, part, out);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
@@ -322,7 +324,7 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
   // the solver stream starts after everything already queued on the caller's stream
   SHOT_CUDA(cudaEventRecord(w.ev0, user));
   SHOT_CUDA(cudaStreamWaitEvent(s.st, w.ev0, 0));
-  const size_t n = (size_t)g.nlat * g.nlon;
+  const size_t n = g.npix;
   std::vector<const float*> lists(2 * (size_t)nprob);
   for (int i = 0; i < nprob; ++i) {
     lists[i] = P[i];
@@ -664,10 +666,67 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
   return SHOT_OK;
 }
 
+int shot_grid_init_healpix(shot_grid* out, int nside, int lmax, int precision, int legendre_mode, void* stream) {
+  if (!out) { set_error("out is NULL"); return SHOT_ERR_INVALID_ARG; }
+  *out = nullptr;
+  if (nside < 1 || nside > 4096) { set_error("need 1 <= nside <= 4096"); return SHOT_ERR_INVALID_ARG; }
+  const int nr = 4 * nside - 1;
+  if (lmax == -1) lmax = 3 * nside - 1;
+  if (lmax < 0 || lmax > nr - 1) { set_error("need 0 <= lmax <= 4 nside - 2"); return SHOT_ERR_INVALID_ARG; }
+  if (precision != SHOT_FP32 && precision != SHOT_BF16X3) { set_error("unknown precision"); return SHOT_ERR_INVALID_ARG; }
+  if (legendre_mode != SHOT_TABLE && legendre_mode != SHOT_RECURRENCE) {
+    set_error("unknown legendre_mode");
+    return SHOT_ERR_INVALID_ARG;
+  }
+  if (legendre_mode == SHOT_RECURRENCE && precision != SHOT_FP32) {
+    set_error("SHOT_RECURRENCE is built for SHOT_FP32 grids");
+    return SHOT_ERR_UNSUPPORTED;
+  }
+  Grid* g = new Grid;
+  g->nlat = nr;
+  g->nlon = 4 * nside;   // the longest ring
+  g->lmax = lmax;
+  g->nh = (nr + 1) / 2;
+  g->nside = nside;
+  g->precision = precision;
+  g->mode = legendre_mode;
+  g->quad = SHOT_QUAD_HEALPIX;
+  g->plan.N = 0;
+  g->plan.nst = 0;
+  cudaGetDevice(&g->dev);
+  cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->dev);
+  int rc = build_grid_tables(*g, as_stream(stream));
+  if (rc) {
+    shot_grid_free(reinterpret_cast<shot_grid>(g));
+    return rc;
+  }
+  *out = reinterpret_cast<shot_grid>(g);
+  return SHOT_OK;
+}
+
+int shot_grid_npix(shot_grid gh, long long* npix) {
+  Grid* g = as_grid(gh);
+  if (!g || !npix) { set_error("shot_grid_npix: bad argument"); return SHOT_ERR_INVALID_ARG; }
+  *npix = (long long)g->npix;
+  return SHOT_OK;
+}
+
+int shot_grid_rings(shot_grid gh, int* len, long long* off, double* phi0) {
+  Grid* g = as_grid(gh);
+  if (!g) { set_error("shot_grid_rings: bad handle"); return SHOT_ERR_INVALID_ARG; }
+  for (int i = 0; i < g->nlat; ++i) {
+    if (len) len[i] = g->ring_len[i];
+    if (off) off[i] = g->ring_off[i];
+    if (phi0)
+      phi0[i] = g->quad == SHOT_QUAD_HEALPIX ? M_PI * g->ring_phase[i].first / g->ring_phase[i].second : 0.0;
+  }
+  return SHOT_OK;
+}
+
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo,
+  void* dptr[] = {g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo,
                   g->ws.ct_hi, g->ws.ct_lo, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};
@@ -772,7 +831,7 @@ int shot_sinkhorn(shot_grid gh, const float* p, const float* q, int batch, doubl
   int rc = check_solver_args(g, p, q, batch, eps, tau, max_iter, check_every);
   if (rc) return rc;
   if (!u || !v) { set_error("u, v are required"); return SHOT_ERR_INVALID_ARG; }
-  const size_t n = (size_t)g->nlat * g->nlon;
+  const size_t n = g->npix;
   std::vector<const float*> P(batch), Q(batch);
   for (int b = 0; b < batch; ++b) {
     P[b] = p + b * n;
@@ -801,7 +860,7 @@ int shot_divergence(shot_grid gh, const float* p, const float* q, int batch, dou
   if (rc) return rc;
   if (!S || !status) { set_error("S and status are required"); return SHOT_ERR_INVALID_ARG; }
   cudaStream_t st = as_stream(stream);
-  const size_t n = (size_t)g->nlat * g->nlon;
+  const size_t n = g->npix;
   const int np = 3 * batch;
   if ((rc = ensure_workspace(*g, np, st))) return rc;
   Workspace& w = g->ws;
@@ -893,7 +952,7 @@ int shot_divergence_multi(const shot_pair_set* sets, int nsets, int max_iter, do
   int rc;
   for (size_t k = 0; k < G; ++k) {
     Grid& g = *grids[k];
-    const size_t n = (size_t)g.nlat * g.nlon;
+    const size_t n = g.npix;
     std::vector<const float*> P, Q, fl;
     std::vector<double> taus;
     for (int i : members[k]) {
@@ -979,6 +1038,10 @@ int shot_divergence_grad(shot_grid gh, const float* p, const float* q, int batch
   if (!S || !grad_p || !status || (mode != SHOT_GRAD_UNROLLED && mode != SHOT_GRAD_ENVELOPE)) {
     set_error("shot_divergence_grad: S, grad_p, status required; mode UNROLLED or ENVELOPE");
     return SHOT_ERR_INVALID_ARG;
+  }
+  if (g->quad == SHOT_QUAD_HEALPIX) {
+    set_error("shot_divergence_grad: not built for HEALPix grids");
+    return SHOT_ERR_UNSUPPORTED;
   }
   return divergence_grad(*g, p, q, batch, eps, tau, max_iter, checkpoint_every, mode, S, grad_p, status,
                          as_stream(stream));

@@ -50,7 +50,7 @@ int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd) {
   cudaEvent_t e0, e1;
   SHOT_CUDA(cudaEventCreate(&e0));
   SHOT_CUDA(cudaEventCreate(&e1));
-  const size_t n = (size_t)g.nlat * g.nlon;
+  const size_t n = g.npix;
   // the solver buffers hold no state yet: use the caller-independent workspace only
   float* fld = nullptr;
   cudaError_t ce = cudaMalloc(&fld, (size_t)nf * n * sizeof(float));

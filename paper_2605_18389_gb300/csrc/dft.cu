@@ -17,13 +17,13 @@
 // The epilogue then applies Algorithm 1's pointwise step to K v (update, check or
 // final objective) and reduces per-field partial sums (FP64) per ring pair.
 #include "fft.cuh"
+#include "epilogue.cuh"
 
 namespace shot {
 
 namespace {
 
 constexpr int kThreads = kFftThreads;
-constexpr int kEpiBatch = 6;   // longitudes per thread whose marginal values are loaded together
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
@@ -37,11 +37,6 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // Loads rings j (real part) and J = nlat-1-j (imaginary part) of nfg fields into buf.
 __device__ __forceinline__ void load_ring_pairs(const float* __restrict__ in, float2* buf, int f0, int nfg,
@@ -141,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
   // reading up to the next even field stays inside the row.
   float2* stg = b1;   // stg[blk * FG + q]
   const int nblk_v = 2 * lmax + 1;
-  if (FG % 2 == 0) {
+  if constexpr (FG % 2 == 0) {
     constexpr int ch = FG / 2;
     for (int e = threadIdx.x; e < nblk_v * ch; e += blockDim.x) {
       const int blk = e / ch, c = e - blk * ch;
@@ -179,175 +174,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
 
   const float aj = a_ring[j];
   const bool two = (J != j);   // false only for the equator ring of an odd grid
-  if (ep.mode == EPI_PLAIN) {
-    for (int q = 0; q < nfg; ++q) {
-      float* oj = ep.out + (size_t)(f0 + q) * nlat * nlon + (size_t)j * nlon;
-      float* oJ = ep.out + (size_t)(f0 + q) * nlat * nlon + (size_t)J * nlon;
-      for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const float2 zz = z[q * ld + k];
-        oj[k] = zz.x;
-        if (two) oJ[k] = zz.y;
-      }
-    }
-    return;
-  }
-  // Per-element arithmetic is FP32; every thread sums its few elements (<= 2N/512 per
-  // field) in FP32, warps reduce in FP32 and the cross-warp / grid sums are FP64.  A
-  // thread takes longitude k of both rings of the pair.
-  float acc[FG][NPART];
-#pragma unroll
-  for (int q = 0; q < FG; ++q)
-#pragma unroll
-    for (int i = 0; i < NPART; ++i) acc[q][i] = 0.f;
-
-#pragma unroll
-  for (int q = 0; q < FG; ++q) {
-    if (q >= nfg) break;
-    const int f = f0 + q;
-    const size_t fbase = (size_t)f * nlat * nlon;
-    const size_t rj = (size_t)j * nlon, rJ = (size_t)J * nlon;   // ring offsets within a field
-    float* outf = ep.out + fbase;
-    float* othf = ep.other ? ep.other + fbase : nullptr;
-    ProbState* P = ep.ps + f;
-    if (ep.mode == EPI_UPDATE) {
-      if (!P->active) {
-        if (ep.xout) {   // frozen problem: transform the stored scaling
-          for (int k = threadIdx.x; k < N; k += blockDim.x)
-            other[q * ld + k] = make_float2(outf[rj + k], two ? outf[rJ + k] : 0.f);
-        }
-        continue;
-      }
-      const float* mg = ep.marg[f];
-      const int bal = P->balanced;
-      const float gam = P->gamma, et = P->et;
-      for (int k0 = threadIdx.x; k0 < N; k0 += kEpiBatch * kThreads) {
-        // the marginal values of all this thread's longitudes first, then the arithmetic
-        float pv[kEpiBatch][2];
-#pragma unroll
-        for (int b = 0; b < kEpiBatch; ++b) {
-          const int k = k0 + b * kThreads;
-          pv[b][0] = (k < N) ? __ldg(mg + rj + k) : 0.f;
-          pv[b][1] = (k < N && two) ? __ldg(mg + rJ + k) : 0.f;
-        }
-#pragma unroll
-        for (int b = 0; b < kEpiBatch; ++b) {
-          const int k = k0 + b * kThreads;
-          if (k >= N) break;
-          const float2 zz = z[q * ld + k];
-          float u2[2];
-#pragma unroll
-          for (int r = 0; r < 2; ++r) {
-            if (r == 1 && !two) { u2[1] = 0.f; break; }
-            const float kv = r ? zz.y : zz.x;
-            const float pm = pv[b][r];
-            const float ratio = __fdividef(pm, kv);   // MUFU reciprocal + multiply, <= 2 ulp
-            float u;
-            if (bal) {
-              u = ratio;
-              acc[q][0] += u;
-            } else {
-              // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}
-              u = powf(ratio, gam);
-              if (pm > 0.f) acc[q][0] += aj * pm * powf(ratio, -et);
-            }
-            if (!(kv > 0.f)) {
-              if (kv <= 0.f) acc[q][2] += 1.f;
-              else acc[q][3] += 1.f;   // NaN
-            }
-            if (!isfinite(u) || !isfinite(kv)) acc[q][3] += 1.f;
-            outf[(r ? rJ : rj) + k] = u;
-            u2[r] = u;
-          }
-          if (ep.xout) other[q * ld + k] = make_float2(u2[0], u2[1]);
-        }
-      }
-    } else if (ep.mode == EPI_CHECK) {
-      if (!P->active) continue;
-      const float* mg = ep.marg[f];
-      const float al = (float)P->alpha;
-      for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const float2 zz = z[q * ld + k];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          if (r == 1 && !two) break;
-          const float kv = r ? zz.y : zz.x;
-          const size_t o = (r ? rJ : rj) + k;
-          const float pm = __ldg(mg + o);
-          const float d = fmaf(al * othf[o], kv, -pm);
-          if (ep.norm_l1) {
-            acc[q][0] += aj * fabsf(d);
-            acc[q][1] += aj * pm;
-          } else {
-            acc[q][0] += d * d;
-            acc[q][1] += pm * pm;
-          }
-        }
-      }
-    } else {  // EPI_FINAL: z = K v_true; ep.other = u buffer, ep.out = v buffer
-      if (P->status < 0) continue;
-      const float* pp = ep.marg[f];
-      const float* qq = ep.marg2[f];
-      const float al = (float)P->alpha, be = (float)P->beta;
-      const int bal = P->balanced;
-      const float epsf = (float)ep.eps, tauf = (float)P->tau, et = bal ? 0.f : (float)(ep.eps / P->tau);
-      for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const float2 zz = z[q * ld + k];
-#pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          if (r == 1 && !two) break;
-          const float kv = r ? zz.y : zz.x;
-          const size_t o = (r ? rJ : rj) + k;
-          const float pm = __ldg(pp + o), qm = __ldg(qq + o);
-          const float uu = al * othf[o];
-          const float vv = be * outf[o];
-          othf[o] = uu;
-          outf[o] = vv;
-          const float d = fmaf(uu, kv, -pm);
-          if (ep.norm_l1) {
-            acc[q][0] += aj * fabsf(d);
-            acc[q][1] += aj * pm;
-          } else {
-            acc[q][0] += d * d;
-            acc[q][1] += pm * pm;
-          }
-          acc[q][2] += aj * uu * kv;
-          // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
-          const float lu = logf(uu), lv = logf(vv);
-          float t;
-          if (bal) {
-            t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);
-          } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u)
-            t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
-                (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
-          }
-          acc[q][3] += aj * t;
-        }
-      }
-    }
-  }
-  // one block reduction for all fields of the CTA
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < FG; ++q)
-#pragma unroll
-    for (int i = 0; i < NPART; ++i) {
-      const float v = warp_sum_f(acc[q][i]);
-      if (lane == 0) red[wid][q * NPART + i] = v;
-    }
-  __syncthreads();
-  if (threadIdx.x < FG * NPART) {
-    const int q = threadIdx.x / NPART, i = threadIdx.x - q * NPART;
-    if (q < nfg) {
-      const int f = f0 + q;
-      const ProbState* P = ep.ps + f;
-      const bool live = (ep.mode == EPI_FINAL) ? (P->status >= 0) : (P->active != 0);
-      if (live) {
-        double t = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) t += (double)red[w][threadIdx.x];
-        ep.part[((size_t)f * nh + jh) * NPART + i] = t;
-      }
-    }
-  }
+  ring_pair_epilogue<FG, kThreads>(z, other, ld, N, nfg, f0, (size_t)nlat * nlon, (size_t)j * nlon,
+                                   (size_t)J * nlon, two, aj, nh, jh, ep, red);
+  if (ep.mode == EPI_PLAIN) return;
   if (ep.mode == EPI_UPDATE && ep.xout) {
     // the new scaling of this ring pair is in `other`: transform it for the next half-step
     __syncthreads();
@@ -401,6 +230,13 @@ using Plan1024 = CtPlan<1024, 4, 16, 16>;   // 512 x 1024 grids
 
 int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
                    float* X, int ldc, cudaStream_t st, int xsplit) {
+  if (g.quad == SHOT_QUAD_HEALPIX) {
+    if (scale_which || xsplit) {
+      set_error("HEALPix ring transform: no per-field scaling, FP32 spectra only");
+      return SHOT_ERR_UNSUPPORTED;
+    }
+    return launch_hp_dft_fwd(g, in, nf, X, ldc, st);
+  }
   if (g.nlon > kFftCap) {
     set_error("nlon too large for the shared-memory ring FFT");
     return SHOT_ERR_UNSUPPORTED;
@@ -416,6 +252,7 @@ int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, 
 }
 
 int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
+  if (g.quad == SHOT_QUAD_HEALPIX) return launch_hp_idft(g, Y, ldc, nf, ep, st);
   if (g.nlon > kFftCap) {
     set_error("nlon too large for the shared-memory ring FFT");
     return SHOT_ERR_UNSUPPORTED;

@@ -1,0 +1,203 @@
+// The Sinkhorn epilogue of the inverse ring transform, shared by the rectangular grids'
+// FFT kernel and the HEALPix ring kernel.
+//
+// z holds K v on the ring pair (real part: ring j, imaginary part: ring J; nseq = nfg
+// sequences of N longitudes at stride ld); the epilogue applies Algorithm 1's pointwise step
+// of the given mode and reduces the per-field partial sums of the pair into
+// ep.part[f][jh][NPART]:
+//   EPI_PLAIN   out = K v
+//   EPI_UPDATE  u = p / Kv (balanced) or (p / Kv)^{tau/(tau+eps)}; sums: sum u (gauge) or
+//               sum a p u^{-eps/tau} (translation-invariant step), non-positive and
+//               non-finite counts; when ep.xout is set the new scaling is also written
+//               into `other` (u_j + i u_J) for the forward transform that follows
+//   EPI_CHECK   |u Kv - p| sums for the marginal error (L2 or L1, App. C.3)
+//   EPI_FINAL   u_true, v_true, the marginal error, m(pi) and the dual objective
+// Field f occupies out[f * fstride ...]; rings j and J start at rj and rJ within a field.
+#pragma once
+#include "shot_internal.cuh"
+
+namespace shot {
+
+__device__ __forceinline__ float epi_warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int FG, int NT>
+__device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* other, int ld, int N, int nfg, int f0,
+                                                   size_t fstride, size_t rj, size_t rJ, bool two, float aj,
+                                                   int nh, int jh, const EpiParams& ep,
+                                                   float (*red)[FG * NPART]) {
+  constexpr int kEpiBatch = 6;   // longitudes per thread whose marginal values are loaded together
+  if (ep.mode == EPI_PLAIN) {
+    for (int q = 0; q < nfg; ++q) {
+      float* oj = ep.out + (size_t)(f0 + q) * fstride + rj;
+      float* oJ = ep.out + (size_t)(f0 + q) * fstride + rJ;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float2 zz = z[q * ld + k];
+        oj[k] = zz.x;
+        if (two) oJ[k] = zz.y;
+      }
+    }
+    return;
+  }
+  // Per-element arithmetic is FP32; every thread sums its few elements (<= 2N/512 per
+  // field) in FP32, warps reduce in FP32 and the cross-warp / grid sums are FP64.  A
+  // thread takes longitude k of both rings of the pair.
+  float acc[FG][NPART];
+#pragma unroll
+  for (int q = 0; q < FG; ++q)
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) acc[q][i] = 0.f;
+
+#pragma unroll
+  for (int q = 0; q < FG; ++q) {
+    if (q >= nfg) break;
+    const int f = f0 + q;
+    const size_t fbase = (size_t)f * fstride;
+    float* outf = ep.out + fbase;
+    float* othf = ep.other ? ep.other + fbase : nullptr;
+    ProbState* P = ep.ps + f;
+    if (ep.mode == EPI_UPDATE) {
+      if (!P->active) {
+        if (ep.xout) {   // frozen problem: transform the stored scaling
+          for (int k = threadIdx.x; k < N; k += blockDim.x)
+            other[q * ld + k] = make_float2(outf[rj + k], two ? outf[rJ + k] : 0.f);
+        }
+        continue;
+      }
+      const float* mg = ep.marg[f];
+      const int bal = P->balanced;
+      const float gam = P->gamma, et = P->et;
+      for (int k0 = threadIdx.x; k0 < N; k0 += kEpiBatch * NT) {
+        // the marginal values of all this thread's longitudes first, then the arithmetic
+        float pv[kEpiBatch][2];
+#pragma unroll
+        for (int b = 0; b < kEpiBatch; ++b) {
+          const int k = k0 + b * NT;
+          pv[b][0] = (k < N) ? __ldg(mg + rj + k) : 0.f;
+          pv[b][1] = (k < N && two) ? __ldg(mg + rJ + k) : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < kEpiBatch; ++b) {
+          const int k = k0 + b * NT;
+          if (k >= N) break;
+          const float2 zz = z[q * ld + k];
+          float u2[2];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            if (r == 1 && !two) { u2[1] = 0.f; break; }
+            const float kv = r ? zz.y : zz.x;
+            const float pm = pv[b][r];
+            const float ratio = __fdividef(pm, kv);   // MUFU reciprocal + multiply, <= 2 ulp
+            float u;
+            if (bal) {
+              u = ratio;
+              acc[q][0] += u;
+            } else {
+              // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}
+              u = powf(ratio, gam);
+              if (pm > 0.f) acc[q][0] += aj * pm * powf(ratio, -et);
+            }
+            if (!(kv > 0.f)) {
+              if (kv <= 0.f) acc[q][2] += 1.f;
+              else acc[q][3] += 1.f;   // NaN
+            }
+            if (!isfinite(u) || !isfinite(kv)) acc[q][3] += 1.f;
+            outf[(r ? rJ : rj) + k] = u;
+            u2[r] = u;
+          }
+          if (ep.xout) other[q * ld + k] = make_float2(u2[0], u2[1]);
+        }
+      }
+    } else if (ep.mode == EPI_CHECK) {
+      if (!P->active) continue;
+      const float* mg = ep.marg[f];
+      const float al = (float)P->alpha;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float2 zz = z[q * ld + k];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (r == 1 && !two) break;
+          const float kv = r ? zz.y : zz.x;
+          const size_t o = (r ? rJ : rj) + k;
+          const float pm = __ldg(mg + o);
+          const float d = fmaf(al * othf[o], kv, -pm);
+          if (ep.norm_l1) {
+            acc[q][0] += aj * fabsf(d);
+            acc[q][1] += aj * pm;
+          } else {
+            acc[q][0] += d * d;
+            acc[q][1] += pm * pm;
+          }
+        }
+      }
+    } else {  // EPI_FINAL: z = K v_true; ep.other = u buffer, ep.out = v buffer
+      if (P->status < 0) continue;
+      const float* pp = ep.marg[f];
+      const float* qq = ep.marg2[f];
+      const float al = (float)P->alpha, be = (float)P->beta;
+      const int bal = P->balanced;
+      const float epsf = (float)ep.eps, tauf = (float)P->tau, et = bal ? 0.f : (float)(ep.eps / P->tau);
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const float2 zz = z[q * ld + k];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          if (r == 1 && !two) break;
+          const float kv = r ? zz.y : zz.x;
+          const size_t o = (r ? rJ : rj) + k;
+          const float pm = __ldg(pp + o), qm = __ldg(qq + o);
+          const float uu = al * othf[o];
+          const float vv = be * outf[o];
+          othf[o] = uu;
+          outf[o] = vv;
+          const float d = fmaf(uu, kv, -pm);
+          if (ep.norm_l1) {
+            acc[q][0] += aj * fabsf(d);
+            acc[q][1] += aj * pm;
+          } else {
+            acc[q][0] += d * d;
+            acc[q][1] += pm * pm;
+          }
+          acc[q][2] += aj * uu * kv;
+          // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
+          const float lu = logf(uu), lv = logf(vv);
+          float t;
+          if (bal) {
+            t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);
+          } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u)
+            t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
+                (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
+          }
+          acc[q][3] += aj * t;
+        }
+      }
+    }
+  }
+  // one block reduction for all fields of the CTA
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < FG; ++q)
+#pragma unroll
+    for (int i = 0; i < NPART; ++i) {
+      const float v = epi_warp_sum(acc[q][i]);
+      if (lane == 0) red[wid][q * NPART + i] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < FG * NPART) {
+    const int q = threadIdx.x / NPART, i = threadIdx.x - q * NPART;
+    if (q < nfg) {
+      const int f = f0 + q;
+      const ProbState* P = ep.ps + f;
+      const bool live = (ep.mode == EPI_FINAL) ? (P->status >= 0) : (P->active != 0);
+      if (live) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += (double)red[w][threadIdx.x];
+        ep.part[((size_t)f * nh + jh) * NPART + i] = t;
+      }
+    }
+  }
+}
+
+}  // namespace shot

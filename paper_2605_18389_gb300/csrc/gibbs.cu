@@ -107,8 +107,22 @@ double gibbs_normaliser_host(double eps) {
 
 int ensure_xyz(Grid& g, cudaStream_t st) {
   if (g.xyz_d) return SHOT_OK;
-  const int n = g.nlat * g.nlon;
+  const int n = (int)g.npix;
   SHOT_CUDA(cudaMalloc(&g.xyz_d, (size_t)n * sizeof(float4)));
+  if (g.quad == SHOT_QUAD_HEALPIX) {   // ring lengths and longitude offsets vary: host, FP64
+    std::vector<float4> v((size_t)n);
+    for (int i = 0; i < g.nlat; ++i) {
+      const double z = g.x[i], st_ = std::sqrt((1.0 - z) * (1.0 + z));
+      const double phi0 = M_PI * g.ring_phase[i].first / g.ring_phase[i].second;
+      for (int k = 0; k < g.ring_len[i]; ++k) {
+        const double ph = phi0 + 2.0 * M_PI * k / g.ring_len[i];
+        v[(size_t)g.ring_off[i] + k] = make_float4((float)(st_ * std::cos(ph)), (float)(st_ * std::sin(ph)), (float)z, 0.f);
+      }
+    }
+    SHOT_CUDA(cudaMemcpyAsync(g.xyz_d, v.data(), v.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+    SHOT_CUDA(cudaStreamSynchronize(st));   // v is a local
+    return SHOT_OK;
+  }
   count_launch();
   k_node_xyz<<<(n + 255) / 256, 256, 0, st>>>(g.nlat, g.nlon, g.x_d, reinterpret_cast<float4*>(g.xyz_d));
   SHOT_CUDA(cudaGetLastError());
@@ -118,10 +132,12 @@ int ensure_xyz(Grid& g, cudaStream_t st) {
 int launch_gibbs(Grid& g, double eps, const float* in, float* out, int nf, cudaStream_t st) {
   int rc = ensure_xyz(g, st);
   if (rc) return rc;
-  const int n = g.nlat * g.nlon;
+  const int n = (int)g.npix;
+  // node j's area weight is a_ring[j / ring width]: HEALPix pixels all have the same area
+  const int width = g.quad == SHOT_QUAD_HEALPIX ? n : g.nlon;
   for (int f0 = 0; f0 < nf; f0 += kGF) {
     count_launch();
-    k_gibbs<<<(n + kGT - 1) / kGT, kGT, 0, st>>>(n, g.nlon, reinterpret_cast<const float4*>(g.xyz_d), g.a_d,
+    k_gibbs<<<(n + kGT - 1) / kGT, kGT, 0, st>>>(n, width, reinterpret_cast<const float4*>(g.xyz_d), g.a_d,
                                                  (float)(1.0 / eps), in, out, nf, f0);
     SHOT_CUDA(cudaGetLastError());
   }
@@ -159,7 +175,7 @@ extern "C" int shot_conv_compare(shot_grid gh, double eps, const float* in, int 
     return SHOT_ERR_INVALID_ARG;
   }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int n = g->nlat * g->nlon;
+  const int n = (int)g->npix;
   const int nblk = 64;
   float *h = nullptr, *k = nullptr;
   double* part = nullptr;

@@ -265,20 +265,44 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   SHOT_CUDA(cudaMalloc(&g.a_d, nlat * sizeof(float)));
   SHOT_CUDA(cudaMalloc(&g.tw_d, g.nlon * sizeof(float2)));
   SHOT_CUDA(cudaMalloc(&g.h_d, L * sizeof(float)));
-  count_launch(3);
-  if (g.quad == SHOT_QUAD_CLENSHAW_CURTIS)
-    k_cc_nodes<<<(nh + 127) / 128, 128, 0, st>>>(nlat, g.x_d, g.w_d);
-  else
-    k_gl_nodes<<<(nh + 127) / 128, 128, 0, st>>>(nlat, g.x_d, g.w_d);
-  k_area<<<(nlat + 255) / 256, 256, 0, st>>>(nlat, g.nlon, g.w_d, g.a_d);
-  k_heat<<<(L + 255) / 256, 256, 0, st>>>(g.lmax, 0.0, g.h_d);
-  SHOT_CUDA(cudaGetLastError());
-  {
+  if (g.quad == SHOT_QUAD_HEALPIX) {
+    // closed-form ring geometry on the host (FP64), then to the device
+    healpix_geometry(g, g.nside);
+    std::vector<float> af(g.a_ring.begin(), g.a_ring.end());
+    SHOT_CUDA(cudaMemcpyAsync(g.x_d, g.x.data(), nlat * sizeof(double), cudaMemcpyHostToDevice, st));
+    SHOT_CUDA(cudaMemcpyAsync(g.w_d, g.w.data(), nlat * sizeof(double), cudaMemcpyHostToDevice, st));
+    SHOT_CUDA(cudaMemcpyAsync(g.a_d, af.data(), nlat * sizeof(float), cudaMemcpyHostToDevice, st));
+    std::vector<int2> ph(nlat);
+    for (int i = 0; i < nlat; ++i) ph[i] = make_int2(g.ring_phase[i].first, g.ring_phase[i].second);
+    SHOT_CUDA(cudaMalloc(&g.ring_phase_d, nlat * sizeof(int2)));
+    SHOT_CUDA(cudaMemcpyAsync(g.ring_phase_d, ph.data(), nlat * sizeof(int2), cudaMemcpyHostToDevice, st));
+    SHOT_CUDA(cudaStreamSynchronize(st));   // af, ph are locals
+    count_launch();
+    k_heat<<<(L + 255) / 256, 256, 0, st>>>(g.lmax, 0.0, g.h_d);
+    SHOT_CUDA(cudaGetLastError());
+  } else {
+    count_launch(3);
+    if (g.quad == SHOT_QUAD_CLENSHAW_CURTIS)
+      k_cc_nodes<<<(nh + 127) / 128, 128, 0, st>>>(nlat, g.x_d, g.w_d);
+    else
+      k_gl_nodes<<<(nh + 127) / 128, 128, 0, st>>>(nlat, g.x_d, g.w_d);
+    k_area<<<(nlat + 255) / 256, 256, 0, st>>>(nlat, g.nlon, g.w_d, g.a_d);
+    k_heat<<<(L + 255) / 256, 256, 0, st>>>(g.lmax, 0.0, g.h_d);
+    SHOT_CUDA(cudaGetLastError());
     std::vector<float2> tw;
     fft_plan_twiddles(g.plan, tw);
     SHOT_CUDA(cudaMemcpyAsync(g.tw_d, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
     SHOT_CUDA(cudaStreamSynchronize(st));   // tw is a local
+    g.ring_len.assign(nlat, g.nlon);
+    g.ring_off.assign(nlat + 1, 0);
+    for (int i = 0; i < nlat; ++i) g.ring_off[i + 1] = g.ring_off[i] + g.nlon;
+    g.npix = (size_t)nlat * g.nlon;
   }
+  SHOT_CUDA(cudaMalloc(&g.ring_len_d, nlat * sizeof(int)));
+  SHOT_CUDA(cudaMalloc(&g.ring_off_d, (nlat + 1) * sizeof(long long)));
+  SHOT_CUDA(cudaMemcpyAsync(g.ring_len_d, g.ring_len.data(), nlat * sizeof(int), cudaMemcpyHostToDevice, st));
+  SHOT_CUDA(cudaMemcpyAsync(g.ring_off_d, g.ring_off.data(), (nlat + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+                            st));
 
   // blocks (m, p): rows M = (lmax - m - p)/2 + 1 when lmax - m - p >= 0
   g.nblk = 2 * L;
@@ -352,13 +376,16 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   SHOT_CUDA(cudaMemcpyAsync(g.tiles_ana, ta.data(), ta.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
   SHOT_CUDA(cudaMemcpyAsync(g.tiles_syn, ts.data(), ts.size() * sizeof(Tile), cudaMemcpyHostToDevice, st));
 
-  g.x.resize(nlat);
-  g.w.resize(nlat);
-  g.a_ring.resize(nlat);
-  SHOT_CUDA(cudaMemcpyAsync(g.x.data(), g.x_d, nlat * sizeof(double), cudaMemcpyDeviceToHost, st));
-  SHOT_CUDA(cudaMemcpyAsync(g.w.data(), g.w_d, nlat * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (g.quad != SHOT_QUAD_HEALPIX) {   // nodes and weights were made on the device
+    g.x.resize(nlat);
+    g.w.resize(nlat);
+    g.a_ring.resize(nlat);
+    SHOT_CUDA(cudaMemcpyAsync(g.x.data(), g.x_d, nlat * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SHOT_CUDA(cudaMemcpyAsync(g.w.data(), g.w_d, nlat * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SHOT_CUDA(cudaStreamSynchronize(st));
+    for (int j = 0; j < nlat; ++j) g.a_ring[j] = g.w[j] * (2.0 * M_PI / g.nlon);
+  }
   SHOT_CUDA(cudaStreamSynchronize(st));
-  for (int j = 0; j < nlat; ++j) g.a_ring[j] = g.w[j] * (2.0 * M_PI / g.nlon);
   return SHOT_OK;
 }
 

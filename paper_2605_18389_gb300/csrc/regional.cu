@@ -57,6 +57,10 @@ extern "C" int shot_regional_rms(shot_grid gh, const float* grad_p, int batch, d
     set_error("shot_regional_rms: bad argument");
     return SHOT_ERR_INVALID_ARG;
   }
+  if (g->quad == SHOT_QUAD_HEALPIX) {
+    set_error("shot_regional_rms: not built for HEALPix grids");
+    return SHOT_ERR_UNSUPPORTED;
+  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   double* mom = nullptr;
   SHOT_CUDA(cudaMalloc(&mom, (size_t)batch * g->nlat * 2 * sizeof(double)));

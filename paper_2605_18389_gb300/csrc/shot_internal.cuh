@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/shot.h"
@@ -135,6 +136,17 @@ struct Grid {
   int split_spectra = 0;        // BF16X3 table grids: the solver keeps bf16 hi/lo spectra
   int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core analysis (0 = tuned)
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use
+  // ring geometry (every grid): ring i holds ring_len[i] nodes starting at ring_off[i] of a
+  // field of npix nodes; HEALPix rings also carry the longitude of their first pixel,
+  // phi0 = pi * ring_phase.first / ring_phase.second
+  int nside = 0;
+  size_t npix = 0;
+  std::vector<int> ring_len;
+  std::vector<long long> ring_off;
+  std::vector<std::pair<int, int>> ring_phase;
+  int* ring_len_d = nullptr;
+  long long* ring_off_d = nullptr;
+  int2* ring_phase_d = nullptr;
   int ntiles_ana = 0, ntiles_syn = 0;
   int bm_ana = 128, bm_syn = 128;
   Workspace ws;
@@ -206,5 +218,9 @@ int tc_nmma(int nf);
 int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
                    const ProbState* colscale, int xsplit = 0);
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
+// HEALPix
+void healpix_geometry(Grid& g, int nside);
+int launch_hp_dft_fwd(const Grid& g, const float* in, int nf, float* X, int ldc, cudaStream_t st);
+int launch_hp_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
 
 }  // namespace shot

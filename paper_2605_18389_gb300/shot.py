@@ -30,6 +30,7 @@ SHOT_GRAD_UNROLLED = 0
 SHOT_GRAD_ENVELOPE = 1
 SHOT_QUAD_GAUSS_LEGENDRE = 0
 SHOT_QUAD_CLENSHAW_CURTIS = 1
+SHOT_QUAD_HEALPIX = 2
 SHOT_FLAG_NORM_L1 = 0x1
 SHOT_FLAG_WARM_START = 0x2
 
@@ -47,6 +48,9 @@ SIGNATURES = {
                        ctypes.c_int, _vp],
     "shot_grid_init_quad": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.c_int, ctypes.c_int, _vp],
+    "shot_grid_init_healpix": [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp],
+    "shot_grid_npix": [_vp, ctypes.POINTER(ctypes.c_longlong)],
+    "shot_grid_rings": [_vp, _c_int_p, ctypes.POINTER(ctypes.c_longlong), _c_dbl_p],
     "shot_grid_free": [_vp],
     "shot_gibbs_normaliser": [ctypes.c_double, _c_dbl_p],
     "shot_gibbs_apply": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
@@ -182,6 +186,28 @@ def shot_conv_compare(g, eps, inp, stream=None):
     _check(lib().shot_conv_compare(g, eps, _dev_ptr(inp, "in"), inp.shape[0], _np_ptr(mae, ctypes.c_double),
                                    _stream(stream)))
     return mae
+
+
+def shot_grid_init_healpix(nside, lmax=-1, precision=SHOT_FP32, legendre_mode=SHOT_TABLE, stream=None):
+    h = _vp()
+    _check(lib().shot_grid_init_healpix(ctypes.byref(h), nside, lmax, precision, legendre_mode, _stream(stream)))
+    return h
+
+
+def shot_grid_npix(g):
+    n = ctypes.c_longlong()
+    _check(lib().shot_grid_npix(g, ctypes.byref(n)))
+    return n.value
+
+
+def shot_grid_rings(g):
+    nr = shot_grid_info(g)["nlat"]
+    ln = np.empty(nr, np.int32)
+    off = np.empty(nr, np.int64)
+    ph = np.empty(nr)
+    _check(lib().shot_grid_rings(g, _np_ptr(ln, ctypes.c_int), _np_ptr(off, ctypes.c_longlong),
+                                 _np_ptr(ph, ctypes.c_double)))
+    return ln, off, ph
 
 
 def shot_grid_free(g):
