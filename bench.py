@@ -49,21 +49,69 @@ def parse():
     ap.add_argument("--tau", type=float, default=math.inf)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nlat", type=int, default=NLAT, help=argparse.SUPPRESS)
-    ap.add_argument("--quadrature", default="gl", choices=["gl", "cc"],
-                    help="latitudinal quadrature (cc: the equiangular Clenshaw-Curtis grid); the "
-                         "headline line is gl")
-    return ap.parse_args()
+    ap.add_argument("--quadrature", default="gl", choices=["gl", "cc", "healpix"],
+                    help="grid (cc: equiangular Clenshaw-Curtis; healpix: HEALPix rings, with --nside); "
+                         "the headline line is gl")
+    ap.add_argument("--nside", type=int, default=64, help="HEALPix resolution (the paper's climate grid: 64)")
+    ap.add_argument("--t", type=float, default=None,
+                    help="heat time t = eps/4 (default 1e-4; the climate setting eps = 0.01 is t = 2.5e-3)")
+    args = ap.parse_args()
+    global T_HEAT, EPS
+    if args.t is not None:
+        T_HEAT = args.t
+        EPS = 4.0 * T_HEAT
+    return args
+
+
+def grid_dims(args):
+    """(rings, longest ring, nodes per field) of the benchmarked grid."""
+    if args.quadrature == "healpix":
+        return 4 * args.nside - 1, 4 * args.nside, 12 * args.nside * args.nside
+    return args.nlat, 2 * args.nlat, args.nlat * 2 * args.nlat
+
+
+def oracle_grid(args):
+    if args.quadrature == "healpix":
+        from oracle.healpix import HealpixGrid
+        return HealpixGrid(args.nside)
+    from oracle.grid import Grid
+    return Grid(args.nlat, quadrature=args.quadrature)
+
+
+def oracle_nodes(og):
+    """(x, nlon, a_ring) of an oracle GL/CC grid; None for HEALPix (fields drawn per pixel)."""
+    return (og.x, og.nlon, og.a_ring) if hasattr(og, "nlon") else None
+
+
+def bench_fields(args, og_or_nodes, npairs, base_seed, dtype=np.float32):
+    """The workload's p, q: U(0,1) per node with unit mass (Sec. 4.1), on the grid's nodes;
+    HEALPix fields are flat [pairs, 1, N] (oracle layout)."""
+    from paper_2605_18389_gb300 import inputs
+    if args.quadrature == "healpix":
+        npix = 12 * args.nside * args.nside
+        area = 4.0 * np.pi / npix
+        def one(seed):
+            f = np.random.default_rng(seed).uniform(size=npix)
+            return (f / (area * f.sum()))[None]
+        p = np.stack([one([base_seed, 2 * i]) for i in range(npairs)]).astype(dtype)
+        q = np.stack([one([base_seed, 2 * i + 1]) for i in range(npairs)]).astype(dtype)
+        return p, q
+    x, nlon, a_ring = og_or_nodes
+    return inputs.pairs(RECIPE, base_seed, npairs, x, nlon, a_ring, dtype=dtype)
 
 
 def config(args, nlat, nlon):
-    quad = "GL" if args.quadrature == "gl" else "Clenshaw-Curtis"
-    return {"workload": f"heat-Sinkhorn divergence, {quad} {nlat}x{nlon} (lmax {nlat - 1}), t={T_HEAT:g} "
+    quad = {"gl": "GL", "cc": "Clenshaw-Curtis", "healpix": "HEALPix"}[args.quadrature]
+    shape = (f"nside {args.nside} ({12 * args.nside ** 2} pixels, lmax {3 * args.nside - 1})"
+             if args.quadrature == "healpix" else f"{nlat}x{nlon} (lmax {nlat - 1})")
+    return {"workload": f"heat-Sinkhorn divergence, {quad} {shape}, t={T_HEAT:g} "
                         f"(eps={EPS:g}), {PAIRS} pairs -> {3 * PAIRS} OT problems, "
                         f"{'balanced' if math.isinf(args.tau) else f'tau={args.tau:g}'}, check every "
                         f"{CHECK_EVERY}",
             "nlat": nlat, "nlon": nlon, "pairs": PAIRS, "problems": 3 * PAIRS, "t": T_HEAT,
             "tau": None if math.isinf(args.tau) else args.tau, "precision": args.precision,
             "legendre": args.legendre, "quadrature": args.quadrature,
+            "nside": args.nside if args.quadrature == "healpix" else None,
             "fields": f"{RECIPE} (Sec. 4.1 workload: U(0,1) per node, unit mass), seed {SEED}",
             "l2": "working set > L2 every iteration (fields 2x100 MB, spectra 150 MB, table 0.37 GB)"}
 
@@ -140,15 +188,15 @@ def fp32_simt_peak_tflops():
     return 152 * 128 * 2 * 2.070e9 / 1e12
 
 
-def algorithmic_work(kind, nlat, nlon, nfields, fp32):
+def algorithmic_work(kind, nlat, npix, lmax, nfields, fp32):
     """(bytes, flops) one launch of a kernel kind must move / compute at minimum.
 
-    n = nlat*nlon nodes, nh = ceil(nlat/2) ring pairs, T = (lmax+1)(lmax+2)/2 degrees
+    npix nodes per field, nh = ceil(nlat/2) ring pairs, T = (lmax+1)(lmax+2)/2 degrees
     and orders; the folded table holds T*nh entries (4 B in FP32, 2+2 B as bf16 hi/lo).
     """
-    n = nlat * nlon
+    n = npix
     nh = (nlat + 1) // 2
-    L = nlat
+    L = lmax + 1
     T = L * (L + 1) // 2
     field = nfields * n * 4.0                     # one FP32 field batch
     spec = 2 * L * nh * 2 * nfields * 4.0         # folded ring spectra X or Y (FP32)
@@ -160,14 +208,14 @@ def algorithmic_work(kind, nlat, nlon, nfields, fp32):
         # the fused half-step form: Y in, marginal in, new scaling out, its spectra X out
         return 2 * spec + 2 * field, 0.0
     if kind == "legendre_analysis":
-        return table + spec + coef, legendre_flops_per_launch(nlat, L - 1, nfields)
+        return table + spec + coef, legendre_flops_per_launch(nlat, lmax, nfields)
     if kind == "legendre_synthesis":
-        return table + coef + spec, legendre_flops_per_launch(nlat, L - 1, nfields)
+        return table + coef + spec, legendre_flops_per_launch(nlat, lmax, nfields)
     return 0.0, 0.0
 
 
-def roofline(kind, avg_ms, nlat, nlon, nfields, fp32):
-    by, fl = algorithmic_work(kind, nlat, nlon, nfields, fp32)
+def roofline(kind, avg_ms, nlat, npix, lmax, nfields, fp32):
+    by, fl = algorithmic_work(kind, nlat, npix, lmax, nfields, fp32)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     src = "of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
@@ -204,12 +252,10 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    from oracle.grid import Grid
     from oracle import sinkhorn as sk
-    from paper_2605_18389_gb300 import inputs
-    og = Grid(args.nlat, quadrature=args.quadrature)
+    og = oracle_grid(args)
     og.pbar()
-    p, q = inputs.pairs(RECIPE, SEED, 1, og.x, og.nlon, og.a_ring, dtype=np.float32)
+    p, q = bench_fields(args, oracle_nodes(og), 1, SEED)
     p = p.astype(np.float64)
     q = q.astype(np.float64)
     # one step = one Alg. 1 iteration of ONE (p,q) problem (a 1/24 sample of a batch step)
@@ -222,7 +268,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config(args, og.nlat, og.nlon),
+            "config": config(args, *grid_dims(args)[:2]),
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "iters/s",
                              "sample": f"each step = 1 Alg. 1 iteration of 1 of the {3 * PAIRS} problems "
                                        f"(numpy FP64, OpenBLAS on {cores} threads); value = problem-iterations/s "
@@ -232,12 +278,19 @@ def run_reference(args):
     return 0
 
 
+def make_grid(shot, args, prec, mode):
+    if args.quadrature == "healpix":
+        return shot.shot_grid_init_healpix(args.nside, -1, prec, mode)
+    quad = shot.SHOT_QUAD_GAUSS_LEGENDRE if args.quadrature == "gl" else shot.SHOT_QUAD_CLENSHAW_CURTIS
+    return shot.shot_grid_init_quad(quad, args.nlat, 2 * args.nlat, -1, prec, mode)
+
+
 def fp32_compare(args, shot, torch, quad, nlat, nlon, mode, pt, qt, S_split):
     """The plain FP32 form on the same fields and steps (graph path, CUDA events): its
     iters/s, the split form's speedup over it, and the relative S difference."""
-    g = shot.shot_grid_init_quad(quad, nlat, nlon, -1, shot.SHOT_FP32, mode)
+    g = make_grid(shot, args, shot.SHOT_FP32, mode)
     shot.shot_grid_reserve(g, 3 * PAIRS)
-    u3 = torch.empty((3 * PAIRS, nlat, nlon), device="cuda")
+    u3 = torch.empty((3 * PAIRS,) + tuple(pt.shape[1:]), device="cuda")
     v3 = torch.empty_like(u3)
     kw = dict(tau=args.tau, tol=0.0, check_every=CHECK_EVERY, u3=u3, v3=v3)
     shot.shot_divergence(g, pt, qt, EPS, max_iter=args.warmup, **kw)
@@ -263,12 +316,10 @@ def fp32_compare(args, shot, torch, quad, nlat, nlon, mode, pt, qt, S_split):
 
 def cpu_baseline(args, x, w, a_ring):
     """Oracle on a bounded sample (~10-30 s): 2 iterations of the full 24-problem batch."""
-    from oracle.grid import Grid
     from oracle import sinkhorn as sk
-    from paper_2605_18389_gb300 import inputs
-    og = Grid(args.nlat, quadrature=args.quadrature)
+    og = oracle_grid(args)
     og.pbar()
-    p, q = inputs.pairs(RECIPE, SEED, PAIRS, og.x, og.nlon, og.a_ring, dtype=np.float32)
+    p, q = bench_fields(args, oracle_nodes(og), PAIRS, SEED)
     P = np.concatenate([p, p, q]).astype(np.float64)
     Q = np.concatenate([q, p, q]).astype(np.float64)
     iters = 2
@@ -276,8 +327,8 @@ def cpu_baseline(args, x, w, a_ring):
     sk.sinkhorn(og, P, Q, EPS, args.tau, T=iters, C=0)
     dt = time.perf_counter() - t0
     return {"value": iters / dt, "unit": "iters/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{iters} Alg. 1 iterations of the full {3 * PAIRS}-problem batch at "
-                      f"{og.nlat}x{og.nlon} (FP64 numpy, OpenBLAS threads = {os.cpu_count()}); "
+            "sample": f"{iters} Alg. 1 iterations of the full {3 * PAIRS}-problem batch on the same "
+                      f"grid (FP64 numpy, OpenBLAS threads = {os.cpu_count()}); "
                       f"grid/table set-up excluded", "seconds": dt}
 
 
@@ -297,16 +348,15 @@ def main():
         dist.init_process_group("nccl")
         pg = dist
     prec = shot.SHOT_FP32 if args.precision == "fp32" else shot.SHOT_BF16X3
-    nlat = args.nlat
-    nlon = 2 * nlat
+    nlat, nlon, npix = grid_dims(args)
     mode = shot.SHOT_TABLE if args.legendre == "table" else shot.SHOT_RECURRENCE
-    quad = shot.SHOT_QUAD_GAUSS_LEGENDRE if args.quadrature == "gl" else shot.SHOT_QUAD_CLENSHAW_CURTIS
-    g = shot.shot_grid_init_quad(quad, nlat, nlon, -1, prec, mode)
+    quad = None
+    g = make_grid(shot, args, prec, mode)
     x, w, a_ring = shot.shot_grid_nodes(g)
-    p, q = inputs.pairs(RECIPE, sd.pair_seed(SEED, rank), PAIRS, x, nlon, a_ring, dtype=np.float32)
+    p, q = bench_fields(args, (x, nlon, a_ring), PAIRS, sd.pair_seed(SEED, rank))
     pt = torch.from_numpy(p).cuda()
     qt = torch.from_numpy(q).cuda()
-    u3 = torch.empty((3 * PAIRS, nlat, nlon), device="cuda")
+    u3 = torch.empty((3 * PAIRS,) + tuple(pt.shape[1:]), device="cuda")
     v3 = torch.empty_like(u3)
     shot.shot_grid_reserve(g, 3 * PAIRS)
     kw = dict(tau=args.tau, tol=0.0, check_every=CHECK_EVERY, u3=u3, v3=v3)
@@ -366,7 +416,8 @@ def main():
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
-    roof = roofline(dom, dom_ms / dom_n, nlat, nlon, 3 * PAIRS, prec == shot.SHOT_FP32)
+    lmax = 3 * args.nside - 1 if args.quadrature == "healpix" else nlat - 1
+    roof = roofline(dom, dom_ms / dom_n, nlat, npix, lmax, 3 * PAIRS, prec == shot.SHOT_FP32)
     roof["launches"] = dom_n
     roof["timing"] = ("CUDA events around every launch on the solver's stream, over a second "
                       "pass of the timed K steps")

@@ -651,6 +651,8 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     g->fused_heat = (e && e[0] == '1') ? 1 : 0;
     e = getenv("SHOT_SPLIT_SPECTRA");
     g->split_spectra = (e && e[0] == '1') ? 1 : 0;
+    e = getenv("SHOT_ANA_ROWS");   // 1: the row-tiled tensor-core analysis instead of the transposed one
+    g->ana_rowmajor = (e && e[0] == '1') ? 1 : 0;
     e = getenv("SHOT_TC_STAGES");   // 1..3 fixes the analysis pipeline depth instead of the autotuner
     g->tc_stages_override = (e && e[0] >= '1' && e[0] <= '3') ? e[0] - '0' : 0;
   }
@@ -726,7 +728,7 @@ int shot_grid_rings(shot_grid gh, int* len, long long* off, double* phi0) {
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo,
+  void* dptr[] = {g->tiles_ana_t, g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo,
                   g->ws.ct_hi, g->ws.ct_lo, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};

@@ -367,6 +367,21 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
     SHOT_CUDA(cudaMemcpyAsync(g.blk_order_d, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     SHOT_CUDA(cudaStreamSynchronize(st));   // ord is a local
   }
+  {  // transposed analysis: each block's rows in at most 256-row runs of near-equal size
+    std::vector<TileR> tr;
+    for (int b = 0; b < g.nblk; ++b) {
+      const int M = g.M[b];
+      if (M <= 0) continue;
+      const int parts = (M + 255) / 256;
+      const int per = ((M + parts - 1) / parts + 31) / 32 * 32;
+      for (int r0 = 0; r0 < M; r0 += per) tr.push_back({b, r0, std::min(per, M - r0)});
+    }
+    std::stable_sort(tr.begin(), tr.end(), [](const TileR& a, const TileR& b) { return a.rows > b.rows; });
+    g.ntiles_ana_t = (int)tr.size();
+    SHOT_CUDA(cudaMalloc(&g.tiles_ana_t, tr.size() * sizeof(TileR)));
+    SHOT_CUDA(cudaMemcpyAsync(g.tiles_ana_t, tr.data(), tr.size() * sizeof(TileR), cudaMemcpyHostToDevice, st));
+    SHOT_CUDA(cudaStreamSynchronize(st));   // tr is a local
+  }
   // largest contraction first (synthesis work is proportional to M)
   std::stable_sort(ts.begin(), ts.end(), [&](const Tile& a, const Tile& b) { return g.M[a.blk] > g.M[b.blk]; });
   g.ntiles_ana = (int)ta.size();

@@ -500,6 +500,221 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
 
 
 // ---------------------------------------------------------------------------------
+// Transposed analysis: C^T[c][i] = h_l sum_jh X[jh][c] Pbar[i][jh], i.e. D = A B with
+//   A = X^T  (M = 128 lanes: the spectra columns c, only 2 nf of them filled; K = jh),
+//             MN-major in shared memory, split into hi/lo by two warps (same layout as the
+//             analysis B operand of k_legendre_tc);
+//   B = Pbar (N = the tile's degree rows, up to 256 in 32-row TMA boxes; K = jh), K-major.
+// A tile is a run of at most 256 degree rows of one block, so a block wastes < 32 rows to
+// padding (an M = 128 row tiling wastes ~64), and the epilogue holds 16 consecutive degrees
+// of one column per tcgen05.ld: C^T rows are written as 32-byte vectors, directly in the
+// K-major layout the synthesis reads.  Only used by the heat application (no FP32 C).
+constexpr int kRowBox = 32;           // degree rows per TMA box
+constexpr int kRowBoxBytes = kRowBox * kBK * 2;   // 4 KB
+
+struct AnaTArgs {
+  const TileR* tiles;
+  int ntiles;
+  const long long* row_off;
+  const int* M;
+  int nh;
+  const float* X;
+  int ldc, ncols, nmma;
+  const float* h;
+  const ProbState* colscale;
+  __nv_bfloat16* ct_hi;
+  __nv_bfloat16* ct_lo;
+  int nmma_cap, ldi;
+  int* err;
+};
+
+template <int kStages>
+__global__ void __launch_bounds__(kTcThreads, 1) k_ana_tc_t(const __grid_constant__ CUtensorMap t_hi,
+                                                            const __grid_constant__ CUtensorMap t_lo,
+                                                            const __grid_constant__ CUtensorMap t_x, AnaTArgs aa) {
+  extern __shared__ uint8_t smraw[];
+  __shared__ TcSmem ctl;
+  __shared__ float cscale[256];
+  uint8_t* base = align1k(smraw);
+  const int nmma = aa.nmma, nh = aa.nh;
+  constexpr int kBTile = 256 * kBK * 2;          // table tile (hi or lo), 256 rows
+  constexpr int kATile = 2 * kXsBoxBytes;        // X^T (hi or lo): two 64-column atoms
+  const int xbytes = nmma * kBK * 4;
+  const int sbytes = 2 * kBTile + 2 * kATile + xbytes;
+  auto sB_hi = [&](int s) { return base + s * sbytes; };
+  auto sB_lo = [&](int s) { return base + s * sbytes + kBTile; };
+  auto sA_hi = [&](int s) { return base + s * sbytes + 2 * kBTile; };
+  auto sA_lo = [&](int s) { return base + s * sbytes + 2 * kBTile + kATile; };
+  auto sX = [&](int s) { return base + s * sbytes + 2 * kBTile + 2 * kATile; };
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr uint32_t kAccCols = 256;
+  const int nkb = (nh + kBK - 1) / kBK;
+
+  for (int c = threadIdx.x; c < 128; c += blockDim.x)
+    cscale[c] = (aa.colscale && c < aa.ncols) ? (float)aa.colscale[c >> 1].beta : 1.f;
+  // the A atoms of columns 64..127 hold only zeros (2 nf <= 64): clear them once
+  for (int s = 0; s < kStages; ++s)
+    for (int o = threadIdx.x * 16; o < kXsBoxBytes; o += blockDim.x * 16) {
+      *reinterpret_cast<uint4*>(sA_hi(s) + kXsBoxBytes + o) = make_uint4(0, 0, 0, 0);
+      *reinterpret_cast<uint4*>(sA_lo(s) + kXsBoxBytes + o) = make_uint4(0, 0, 0, 0);
+    }
+  fence_async_smem();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&ctl.fullA[s], 1);
+      mbar_init(&ctl.fullB[s], 64);
+      mbar_init(&ctl.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl.tfull[b], 1);
+      mbar_init(&ctl.tempty[b], 128);
+    }
+    ctl.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl.tmem, 2 * kAccCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = ctl.tmem;
+  volatile int* abort = &ctl.abort;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < aa.ntiles && ok; t += gridDim.x) {
+        const TileR tl = aa.tiles[t];
+        const int nbox = (tl.rows + kRowBox - 1) / kRowBox;
+        const int y0 = (int)aa.row_off[tl.blk] + tl.r0;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % kStages, n = it / kStages;
+          if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
+          mbar_arrive_expect_tx(&ctl.fullA[s], 2 * nbox * kRowBoxBytes + xbytes);
+          for (int b = 0; b < nbox; ++b) {
+            tma_load_2d(sB_hi(s) + b * kRowBoxBytes, &t_hi, &ctl.fullA[s], kb * kBK, y0 + b * kRowBox);
+            tma_load_2d(sB_lo(s) + b * kRowBoxBytes, &t_lo, &ctl.fullA[s], kb * kBK, y0 + b * kRowBox);
+          }
+          tma_load_2d(sX(s), &t_x, &ctl.fullA[s], 0, tl.blk * nh + kb * kBK);
+        }
+      }
+      for (int k = it > kStages ? it - kStages : 0; k < it; ++k)
+        mbar_drain(&ctl.fullA[k % kStages], (k / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      int it = 0, lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < aa.ntiles && ok; t += gridDim.x, ++lt) {
+        const TileR tl = aa.tiles[t];
+        const int nrow = (tl.rows + kRowBox - 1) / kRowBox * kRowBox;   // N, a multiple of 32
+        const uint32_t idesc = idesc_bf16_amn(kBM, nrow);
+        const int acc = lt & 1, u = lt >> 1;
+        if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (u - 1) & 1, abort))) break;
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(acc * kAccCols);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % kStages, n = it / kStages;
+          ok = mbar_wait(&ctl.fullA[s], n & 1, abort);
+          if (ok) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
+          const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k) {
+            // A: 16 K-rows (jh) of the two 64-column atoms; B: the table rows, K-major
+            const uint64_t a_h = desc_sw128_mnmajor(ah + k * 2048, kXsBoxBytes, 1024);
+            const uint64_t a_l = desc_sw128_mnmajor(al + k * 2048, kXsBoxBytes, 1024);
+            const uint64_t b_h = desc_sw128_kmajor(bh + k * 32), b_l = desc_sw128_kmajor(bl + k * 32);
+            umma_bf16(d, a_h, b_h, idesc, (kb | k) != 0);
+            umma_bf16(d, a_h, b_l, idesc, 1);
+            umma_bf16(d, a_l, b_h, idesc, 1);
+          }
+          umma_commit(&ctl.empty[s]);
+        }
+        if (!ok) break;
+        umma_commit(&ctl.tfull[acc]);
+      }
+    }
+  } else if (warp < 4) {
+    // split the FP32 spectra tile (TMA) into the A operand X^T, hi/lo, MN-major
+    const int pt = threadIdx.x - 64;
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < aa.ntiles && ok; t += gridDim.x) {
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = it % kStages, n = it / kStages;
+        if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
+        split_x_mn(reinterpret_cast<const float*>(sX(s)), nmma, aa.ncols, kb * kBK, nh, sA_hi(s), sA_lo(s), pt);
+        fence_async_smem();
+        mbar_arrive(&ctl.fullB[s]);
+      }
+    }
+  } else {
+    // epilogue: lane c of quadrant q holds column 32 q + lane; 16 degree rows per load
+    const int q = warp - 4;
+    const int c = q * 32 + lane;
+    const bool qlive = q * 32 < aa.ncols;   // warp-uniform
+    const float cs = cscale[c];
+    int lt = 0;
+    for (int t = blockIdx.x; t < aa.ntiles; t += gridDim.x, ++lt) {
+      const TileR tl = aa.tiles[t];
+      const int acc = lt & 1, u = lt >> 1;
+      if (!mbar_wait_warp(&ctl.tfull[acc], u & 1, abort)) break;
+      tc_fence_after();
+      if (qlive) {
+        const int blk = tl.blk, m = blk >> 1, p = blk & 1;
+        const uint32_t d = taddr + (uint32_t)(acc * kAccCols) + ((uint32_t)(q * 32) << 16);
+        const size_t row0 = ((size_t)blk * aa.nmma_cap + c) * aa.ldi + tl.r0;
+        for (int i0 = 0; i0 < tl.rows; i0 += 16) {
+          float v[16];
+          tmem_ld16(d + (uint32_t)i0, v);
+          if (c < aa.ncols) {
+            uint32_t hw[8], lw[8];
+#pragma unroll
+            for (int e = 0; e < 16; e += 2) {
+              const int i = tl.r0 + i0 + e;
+              const float h0 = aa.h ? aa.h[m + p + 2 * i] : 1.f;
+              const float h1 = aa.h ? aa.h[m + p + 2 * (i + 1)] : 1.f;
+              const float v0 = v[e] * h0 * cs, v1 = v[e + 1] * h1 * cs;
+              const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+              const float2 hf = __bfloat1622float2(h2);
+              const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+              hw[e / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+              lw[e / 2] = *reinterpret_cast<const uint32_t*>(&l2);
+            }
+            __nv_bfloat16* dh = aa.ct_hi + row0 + i0;
+            __nv_bfloat16* dl = aa.ct_lo + row0 + i0;
+            if (i0 + 16 <= tl.rows) {   // 32-byte aligned: ldi, r0 and i0 are multiples of 8
+              reinterpret_cast<uint4*>(dh)[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+              reinterpret_cast<uint4*>(dh)[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
+              reinterpret_cast<uint4*>(dl)[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+              reinterpret_cast<uint4*>(dl)[1] = make_uint4(lw[4], lw[5], lw[6], lw[7]);
+            } else {   // the block's last rows: rows past M stay zero for the synthesis
+              for (int e = 0; e < tl.rows - i0; ++e) {
+                const uint32_t wh = hw[e / 2], wl = lw[e / 2];
+                dh[e] = __ushort_as_bfloat16((unsigned short)((e & 1) ? (wh >> 16) : (wh & 0xFFFFu)));
+                dl[e] = __ushort_as_bfloat16((unsigned short)((e & 1) ? (wl >> 16) : (wl & 0xFFFFu)));
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&ctl.tempty[acc]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 2 * kAccCols);
+  }
+  if (threadIdx.x == 0 && ctl.abort) atomicExch(aa.err, SHOT_ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------------
 // Fused heat application per (m, parity) block: the analysis of the block (all its
 // 128-row tiles), h_l and the per-field gauge factor in the epilogue, the coefficients
 // kept in shared memory as the bf16 hi/lo B operand, then the synthesis of the block
@@ -924,7 +1139,23 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
   int rc;
   AnaArgs aa{};
   SynArgs sa{};
-  if (ana && xsplit) {
+  if (ana && !Cf && !xsplit && nmma <= 64 && g.ntiles_ana_t > 0 && !g.ana_rowmajor) {
+    // transposed analysis (fields on M, degree rows on N), C^T written by the epilogue
+    constexpr int stages = 2;
+    const size_t smem = 1024 + (size_t)stages * (2 * 256 * kBK * 2 + 2 * 2 * kXsBoxBytes + (size_t)nmma * kBK * 4);
+    CUtensorMap mh, ml, mx;
+    if ((rc = make_map(&mh, g.tab_hi, g.nh, g.rows_total, g.ldt, kRowBox))) return rc;
+    if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kRowBox))) return rc;
+    if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
+    AnaTArgs ta{g.tiles_ana_t, g.ntiles_ana_t, g.row_off_d, g.M_d, g.nh, X, ldc, 2 * nf, nmma,
+                apply_h ? g.h_d : nullptr, colscale, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, w.dev_int + 4};
+    SHOT_CUDA(cudaFuncSetAttribute(k_ana_tc_t<stages>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = g.ntiles_ana_t < g.num_sms ? g.ntiles_ana_t : g.num_sms;
+    ProfScope prof(PK_ANALYSIS, st);
+    count_launch();
+    k_ana_tc_t<stages><<<grid, kTcThreads, smem, st>>>(mh, ml, mx, ta);
+    SHOT_CUDA(cudaGetLastError());
+  } else if (ana && xsplit) {
     // spectra already split (bf16 hi/lo [blk nh + jh][ldc]): B by TMA, four stages
     if (nmma > 64 || ldc % 8 != 0) {
       set_error("split spectra need at most 32 fields and ldc a multiple of 8");

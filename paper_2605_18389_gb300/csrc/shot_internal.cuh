@@ -60,6 +60,10 @@ struct Tile {
   int blk;    // 2*m + p
   int r0;     // first row of the tile (i for analysis, jh for synthesis)
 };
+// a run of degree rows of one block for the transposed tensor-core analysis (rows <= 256)
+struct TileR {
+  int blk, r0, rows;
+};
 
 struct Workspace {
   int nf_cap = 0;       // fields the buffers hold
@@ -131,10 +135,14 @@ struct Grid {
   Tile* tiles_ana = nullptr;
   Tile* tiles_syn = nullptr;
   int* blk_order_d = nullptr;   // blocks with rows, largest first (fused heat kernel)
+  TileR* tiles_ana_t = nullptr;  // transposed analysis tiles, largest first
+  int ntiles_ana_t = 0;
   int nwork = 0, nmt_max = 0, kc_max = 0;
   int fused_heat = 0;           // BF16X3 table grids: fused analysis + synthesis kernel
   int split_spectra = 0;        // BF16X3 table grids: the solver keeps bf16 hi/lo spectra
   int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core analysis (0 = tuned)
+  int ana_rowmajor = 0;         // SHOT_ANA_ROWS=1: degree rows on M (128-row tiles) instead of the
+                                // transposed analysis
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use
   // ring geometry (every grid): ring i holds ring_len[i] nodes starting at ring_off[i] of a
   // field of npix nodes; HEALPix rings also carry the longitude of their first pixel,
