@@ -674,9 +674,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ana_tc_t(const __grid_constan
             uint32_t hw[8], lw[8];
 #pragma unroll
             for (int e = 0; e < 16; e += 2) {
-              const int i = tl.r0 + i0 + e;
-              const float h0 = aa.h ? aa.h[m + p + 2 * i] : 1.f;
-              const float h1 = aa.h ? aa.h[m + p + 2 * (i + 1)] : 1.f;
+              const int i = tl.r0 + i0 + e;   // rows past the tile (i0 + e >= rows) are not stored
+              const float h0 = (aa.h && i0 + e < tl.rows) ? aa.h[m + p + 2 * i] : 1.f;
+              const float h1 = (aa.h && i0 + e + 1 < tl.rows) ? aa.h[m + p + 2 * (i + 1)] : 1.f;
               const float v0 = v[e] * h0 * cs, v1 = v[e + 1] * h1 * cs;
               const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
               const float2 hf = __bfloat1622float2(h2);
@@ -686,7 +686,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ana_tc_t(const __grid_constan
             }
             __nv_bfloat16* dh = aa.ct_hi + row0 + i0;
             __nv_bfloat16* dl = aa.ct_lo + row0 + i0;
-            if (i0 + 16 <= tl.rows) {   // 32-byte aligned: ldi, r0 and i0 are multiples of 8
+            if (i0 + 16 <= tl.rows) {   // 16-byte aligned: ldi, r0 and i0 are multiples of 8
               reinterpret_cast<uint4*>(dh)[0] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
               reinterpret_cast<uint4*>(dh)[1] = make_uint4(hw[4], hw[5], hw[6], hw[7]);
               reinterpret_cast<uint4*>(dl)[0] = make_uint4(lw[0], lw[1], lw[2], lw[3]);
@@ -1139,7 +1139,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
   int rc;
   AnaArgs aa{};
   SynArgs sa{};
-  if (ana && !Cf && !xsplit && nmma <= 64 && g.ntiles_ana_t > 0 && !g.ana_rowmajor) {
+  if (ana && !Cf && !xsplit && nmma <= 64 && g.ntiles_ana_t > 0 && g.ana_transposed) {
     // transposed analysis (fields on M, degree rows on N), C^T written by the epilogue
     constexpr int stages = 2;
     const size_t smem = 1024 + (size_t)stages * (2 * 256 * kBK * 2 + 2 * 2 * kXsBoxBytes + (size_t)nmma * kBK * 4);

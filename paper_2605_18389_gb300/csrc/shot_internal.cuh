@@ -141,8 +141,8 @@ struct Grid {
   int fused_heat = 0;           // BF16X3 table grids: fused analysis + synthesis kernel
   int split_spectra = 0;        // BF16X3 table grids: the solver keeps bf16 hi/lo spectra
   int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core analysis (0 = tuned)
-  int ana_rowmajor = 0;         // SHOT_ANA_ROWS=1: degree rows on M (128-row tiles) instead of the
-                                // transposed analysis
+  int ana_transposed = 0;       // SHOT_ANA_TRANSPOSED=1: fields on M, degree rows on N (k_ana_tc_t)
+                                // instead of 128-row tiles of degrees on M
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use
   // ring geometry (every grid): ring i holds ring_len[i] nodes starting at ring_off[i] of a
   // field of npix nodes; HEALPix rings also carry the longitude of their first pixel,

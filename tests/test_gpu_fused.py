@@ -107,3 +107,24 @@ def test_spectra_formats_agree_with_oracle(monkeypatch, fused, split):
     ref = sk.divergence(og, p64, q64, 0.05, T=50, delta=0.0, C=10)
     assert np.all(r["status"] == 0) and np.all(ref["status"] == 0)
     assert np.all(s_err_prec(r["S"], ref["S"], ref["runs"]["ot"][:3], TOL, "bf16x3") <= 1.0)
+
+
+@pytest.mark.parametrize("nlat,nf", [(33, 3), (96, 24)])
+def test_transposed_analysis_matches_oracle(monkeypatch, nlat, nf):
+    # the opt-in transposed analysis (fields on M, degree rows on N): same heat operator
+    monkeypatch.setenv("SHOT_ANA_TRANSPOSED", "1")
+    g = _grid(monkeypatch, False, nlat)
+    og = OGrid(nlat)
+    f, f64 = f32(np.random.default_rng(nlat * 3).uniform(size=(nf, og.nlat, og.nlon)))
+    out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
+    shot.shot_heat_apply(g, 3e-3, torch.from_numpy(f).cuda(), out)
+    p, q = inputs.pairs("paper_uniform", 9000 + nlat, 2, og.x, og.nlon, og.a_ring)
+    p32, p64 = f32(p)
+    q32, q64 = f32(q)
+    rc, r = shot.shot_divergence(g, torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), 0.05,
+                                 max_iter=40, tol=0.0, check_every=10)
+    shot.shot_grid_free(g)
+    assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, 3e-3)) < TOL
+    ref = sk.divergence(og, p64, q64, 0.05, T=40, delta=0.0, C=10)
+    assert np.all(r["status"] == 0) and np.all(ref["status"] == 0)
+    assert np.all(s_err_prec(r["S"], ref["S"], ref["runs"]["ot"][:2], TOL, "bf16x3") <= 1.0)
