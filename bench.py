@@ -214,6 +214,13 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields, fp32):
     return 0.0, 0.0
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
+# capture of this file's 720 x 1440, 24-field BF16x3 run (20 steps); valid only for that workload
+# and the kernels as captured.
+NCU_TRAFFIC = {("inverse_dft_epilogue", False): 321.9e6, ("legendre_analysis", False): 532.4e6,
+               ("legendre_synthesis", False): 521.8e6}
+
+
 def roofline(kind, avg_ms, nlat, npix, lmax, nfields, fp32):
     by, fl = algorithmic_work(kind, nlat, npix, lmax, nfields, fp32)
     peaks = measured_peaks()
@@ -230,8 +237,9 @@ def roofline(kind, avg_ms, nlat, npix, lmax, nfields, fp32):
                 "peak_source": "FP32 FFMA, derived: 152 SMs x 128 lanes x 2 FLOP x 2.070 GHz",
                 "algorithmic_per_launch": fl, "avg_launch_ms": avg_ms}
     ach = by / s / 1e9
+    traffic = NCU_TRAFFIC.get((kind, fp32)) if (nlat, npix, nfields) == (720, 720 * 1440, 24) else None
     out = {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-           "traffic": None, "peak_source": src, "algorithmic_per_launch": by, "avg_launch_ms": avg_ms}
+           "traffic": traffic, "peak_source": src, "algorithmic_per_launch": by, "avg_launch_ms": avg_ms}
     if kind.startswith("legendre"):
         bf = peaks.get("bf16_tflops_sustained", 1700.0)
         out["tensor"] = {"issued_tflops": 3 * fl / s / 1e12, "peak_bf16_tflops": bf,
