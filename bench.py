@@ -6,11 +6,12 @@ the batch, with the marginal check every C = 10 iterations, inside one
 shot_divergence call (8 measure pairs -> 24 OT problems -> 48 heat convolutions of
 all 24 fields per iteration), followed by the final objective and S of every pair.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp32]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|tf32x3|fp32]
                     [--impl ours|reference]
 
 The headline is the split-precision (BF16x3) form; the same run also times the plain FP32
-form on the same fields and reports the speedup and the S agreement between the two.
+form on the same fields and reports the speedup and the S agreement between the two
+(also for --precision tf32x3, the tf32 hi/lo split at FP32-class accuracy).
 
 --impl reference times the FP64 CPU oracle on the host cores (the only other place this
 file runs oracle code besides the cpu_baseline leg).  Prints one JSON line on rank 0.
@@ -31,6 +32,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "heat-Sinkhorn iters/s at 720x1440 GL grid, batched; split-prec vs FP32 at 1e-4"
+DTYPE = {"fp32": "f32", "bf16x3": "bf16x3 (bf16 hi/lo products, f32 accumulate; f32 elsewhere)",
+         "tf32x3": "tf32x3 (tf32 hi/lo products, f32 accumulate; f32 elsewhere)"}
 NLAT, NLON, T_HEAT, PAIRS, CHECK_EVERY = 720, 1440, 1e-4, 8, 10
 EPS = 4.0 * T_HEAT
 RECIPE = "paper_uniform"
@@ -43,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp32"])
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp32"])
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison pass")
     ap.add_argument("--legendre", default="table", choices=["table", "recurrence"])
     ap.add_argument("--tau", type=float, default=math.inf)
@@ -188,11 +191,12 @@ def fp32_simt_peak_tflops():
     return 152 * 128 * 2 * 2.070e9 / 1e12
 
 
-def algorithmic_work(kind, nlat, npix, lmax, nfields, fp32):
+def algorithmic_work(kind, nlat, npix, lmax, nfields):
     """(bytes, flops) one launch of a kernel kind must move / compute at minimum.
 
     npix nodes per field, nh = ceil(nlat/2) ring pairs, T = (lmax+1)(lmax+2)/2 degrees
-    and orders; the folded table holds T*nh entries (4 B in FP32, 2+2 B as bf16 hi/lo).
+    and orders; the folded table holds T*nh entries (4 B in FP32 and TF32x3, 2+2 B as bf16
+    hi/lo), read once per launch in every precision.
     """
     n = npix
     nh = (nlat + 1) // 2
@@ -215,14 +219,15 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields, fp32):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu --set full
-# capture of this file's 720 x 1440, 24-field BF16x3 run (20 steps); valid only for that workload
-# and the kernels as captured.
-NCU_TRAFFIC = {("inverse_dft_epilogue", False): 321.9e6, ("legendre_analysis", False): 532.4e6,
-               ("legendre_synthesis", False): 521.8e6}
+# capture of this file's 720 x 1440, 24-field BF16x3 run (20 steps); valid only for that workload,
+# precision and the kernels as captured.
+NCU_TRAFFIC = {("inverse_dft_epilogue", "bf16x3"): 321.9e6, ("legendre_analysis", "bf16x3"): 532.4e6,
+               ("legendre_synthesis", "bf16x3"): 521.8e6}
 
 
-def roofline(kind, avg_ms, nlat, npix, lmax, nfields, fp32):
-    by, fl = algorithmic_work(kind, nlat, npix, lmax, nfields, fp32)
+def roofline(kind, avg_ms, nlat, npix, lmax, nfields, prec):
+    by, fl = algorithmic_work(kind, nlat, npix, lmax, nfields)
+    fp32 = prec == "fp32"
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
     src = "of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)"
@@ -237,13 +242,18 @@ def roofline(kind, avg_ms, nlat, npix, lmax, nfields, fp32):
                 "peak_source": "FP32 FFMA, derived: 152 SMs x 128 lanes x 2 FLOP x 2.070 GHz",
                 "algorithmic_per_launch": fl, "avg_launch_ms": avg_ms}
     ach = by / s / 1e9
-    traffic = NCU_TRAFFIC.get((kind, fp32)) if (nlat, npix, nfields) == (720, 720 * 1440, 24) else None
+    traffic = NCU_TRAFFIC.get((kind, prec)) if (nlat, npix, nfields) == (720, 720 * 1440, 24) else None
     out = {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
            "traffic": traffic, "peak_source": src, "algorithmic_per_launch": by, "avg_launch_ms": avg_ms}
     if kind.startswith("legendre"):
         bf = peaks.get("bf16_tflops_sustained", 1700.0)
-        out["tensor"] = {"issued_tflops": 3 * fl / s / 1e12, "peak_bf16_tflops": bf,
-                         "frac": 3 * fl / s / 1e12 / bf, "note": "BF16x3 issues 3 MMAs per product"}
+        if prec == "tf32x3":   # dense TF32 runs at half the bf16 rate (nominal 1.1 vs 2.25 PFLOP/s)
+            out["tensor"] = {"issued_tflops": 3 * fl / s / 1e12, "peak_tf32_tflops": bf / 2,
+                             "frac": 3 * fl / s / 1e12 / (bf / 2),
+                             "note": "TF32x3 issues 3 MMAs per product; peak = measured bf16 x 1/2"}
+        else:
+            out["tensor"] = {"issued_tflops": 3 * fl / s / 1e12, "peak_bf16_tflops": bf,
+                             "frac": 3 * fl / s / 1e12 / bf, "note": "BF16x3 issues 3 MMAs per product"}
     return out
 
 
@@ -355,7 +365,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
         pg = dist
-    prec = shot.SHOT_FP32 if args.precision == "fp32" else shot.SHOT_BF16X3
+    prec = {"fp32": shot.SHOT_FP32, "bf16x3": shot.SHOT_BF16X3, "tf32x3": shot.SHOT_TF32X3}[args.precision]
     nlat, nlon, npix = grid_dims(args)
     mode = shot.SHOT_TABLE if args.legendre == "table" else shot.SHOT_RECURRENCE
     quad = None
@@ -425,7 +435,7 @@ def main():
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
     lmax = 3 * args.nside - 1 if args.quadrature == "healpix" else nlat - 1
-    roof = roofline(dom, dom_ms / dom_n, nlat, npix, lmax, 3 * PAIRS, prec == shot.SHOT_FP32)
+    roof = roofline(dom, dom_ms / dom_n, nlat, npix, lmax, 3 * PAIRS, args.precision)
     roof["launches"] = dom_n
     roof["timing"] = ("CUDA events around every launch on the solver's stream, over a second "
                       "pass of the timed K steps")
@@ -433,12 +443,12 @@ def main():
     per_kind = {k: {"avg_launch_ms": round(v[0] / v[1], 5), "launches": v[1]} for k, v in kinds.items()}
 
     compare = None
-    if args.precision == "bf16x3" and not args.no_compare and ws == 1:
+    if args.precision != "fp32" and not args.no_compare and ws == 1:
         compare = fp32_compare(args, shot, torch, quad, nlat, nlon, mode, pt, qt, res["S"])
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision == "fp32" else "bf16x3 (bf16 hi/lo products, f32 accumulate; f32 elsewhere)",
+            "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": config(args, nlat, nlon), "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "roofline": roof, "kernel_share": share, "kernels": per_kind,

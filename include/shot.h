@@ -48,6 +48,8 @@ extern "C" {
 /* ---- precision of the Legendre contractions ----------------------------- */
 #define SHOT_FP32    0   /* FP32 SIMT FFMA */
 #define SHOT_BF16X3  1   /* tcgen05 tensor cores, bf16 hi/lo split of both operands, 3 products, FP32 accumulate */
+#define SHOT_TF32X3  2   /* tcgen05 tensor cores, tf32 hi/lo split of both operands, 3 products, FP32 accumulate;
+                            ~2^-21 relative per product; keeps a second, transposed FP32 table */
 
 /* ---- source of the associated Legendre values ---------------------------- */
 #define SHOT_TABLE       0   /* precomputed parity-folded table, O(nlat^3) memory */
@@ -78,8 +80,9 @@ int shot_last_error(char* buf, int len);
  *   out        receives the handle (host pointer)
  *   nlat >= 2; nlon >= 2*lmax+1 with prime factors in {2,3,5}; lmax = -1 means nlat-1,
  *              else 0 <= lmax <= nlat-1
- *   precision  SHOT_FP32 or SHOT_BF16X3; legendre_mode SHOT_TABLE or SHOT_RECURRENCE (FP32)
- * Memory: about 2*(lmax+1)(lmax+2)/2 * ceil(nlat/2) * 4 bytes of table (0.37 GB at 720).
+ *   precision  SHOT_FP32, SHOT_BF16X3 or SHOT_TF32X3; legendre_mode SHOT_TABLE or SHOT_RECURRENCE (FP32)
+ * Memory: about 2*(lmax+1)(lmax+2)/2 * ceil(nlat/2) * 4 bytes of table (0.37 GB at 720);
+ *   SHOT_TF32X3 adds the transposed copy, 2(lmax+1) ceil(nlat/2) ceil(M_max/8)*8 * 4 bytes (0.75 GB at 720).
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Synchronises `stream`. */
 int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision,
                    int legendre_mode, void* stream);

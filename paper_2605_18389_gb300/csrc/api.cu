@@ -46,6 +46,7 @@ int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, i
                     const ProbState* colscale, int xsplit) {
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st, colscale);
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st, colscale);
+  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st, colscale);
   if (g.fused_heat) {
     const int rc = launch_heat_tc(g, nf, X, Y, ldc, st, colscale, xsplit);
     if (rc != SHOT_ERR_UNSUPPORTED) return rc;
@@ -56,12 +57,18 @@ int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ld
                          cudaStream_t st) {
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
   if (g.precision == SHOT_FP32) return launch_analysis_simt(g, nf, X, C, ldc, apply_h, st);
+  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
   return launch_legendre_tc(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
 }
 int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st) {
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, nullptr, const_cast<float*>(C), Y, ldc, false, true,
                                                             false, st);
   if (g.precision == SHOT_FP32) return launch_synthesis_simt(g, nf, C, Y, ldc, st);
+  if (g.precision == SHOT_TF32X3) {
+    const int rc = launch_c_to_ct32(g, nf, C, ldc, st);
+    if (rc) return rc;
+    return launch_legendre_tf32(g, nf, nullptr, nullptr, Y, ldc, false, true, false, st);
+  }
   int rc = launch_c_to_ct(g, nf, C, ldc, st);
   if (rc) return rc;
   return launch_legendre_tc(g, nf, nullptr, nullptr, Y, ldc, false, true, false, st);
@@ -626,7 +633,10 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     set_error("need nlat >= 2, 0 <= lmax <= nlat-1, nlon >= 2*lmax+1");
     return SHOT_ERR_INVALID_ARG;
   }
-  if (precision != SHOT_FP32 && precision != SHOT_BF16X3) { set_error("unknown precision"); return SHOT_ERR_INVALID_ARG; }
+  if (precision != SHOT_FP32 && precision != SHOT_BF16X3 && precision != SHOT_TF32X3) {
+    set_error("unknown precision");
+    return SHOT_ERR_INVALID_ARG;
+  }
   if (legendre_mode != SHOT_TABLE && legendre_mode != SHOT_RECURRENCE) {
     set_error("unknown legendre_mode");
     return SHOT_ERR_INVALID_ARG;
@@ -675,7 +685,10 @@ int shot_grid_init_healpix(shot_grid* out, int nside, int lmax, int precision, i
   const int nr = 4 * nside - 1;
   if (lmax == -1) lmax = 3 * nside - 1;
   if (lmax < 0 || lmax > nr - 1) { set_error("need 0 <= lmax <= 4 nside - 2"); return SHOT_ERR_INVALID_ARG; }
-  if (precision != SHOT_FP32 && precision != SHOT_BF16X3) { set_error("unknown precision"); return SHOT_ERR_INVALID_ARG; }
+  if (precision != SHOT_FP32 && precision != SHOT_BF16X3 && precision != SHOT_TF32X3) {
+    set_error("unknown precision");
+    return SHOT_ERR_INVALID_ARG;
+  }
   if (legendre_mode != SHOT_TABLE && legendre_mode != SHOT_RECURRENCE) {
     set_error("unknown legendre_mode");
     return SHOT_ERR_INVALID_ARG;
@@ -728,8 +741,8 @@ int shot_grid_rings(shot_grid gh, int* len, long long* off, double* phi0) {
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->tiles_ana_t, g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tab_hi, g->tab_lo,
-                  g->ws.ct_hi, g->ws.ct_lo, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
+  void* dptr[] = {g->tiles_ana_t, g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tabT, g->tab_hi, g->tab_lo,
+                  g->ws.ct_hi, g->ws.ct_lo, g->ws.ct32, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};
   for (void* p : dptr)

@@ -94,9 +94,10 @@ __global__ void k_area(int nlat, int nlon, const double* __restrict__ w, float* 
 //   Pbar_lm = a_lm (x Pbar_{l-1,m} - b_lm Pbar_{l-2,m}),
 //   a_lm = sqrt((4l^2-1)/(l^2-m^2)), b_lm = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)).
 // One thread per (m, jh); row l goes to block (m, (l-m) mod 2), row (l-m)/2.
+// tabT (optional): the same values at [blk][jh][ldi] (degrees contiguous).
 __global__ void k_pbar(int lmax, int nh, const double* __restrict__ x, const long long* __restrict__ row_off,
                        int ldt, float* __restrict__ tab, __nv_bfloat16* __restrict__ hi,
-                       __nv_bfloat16* __restrict__ lo) {
+                       __nv_bfloat16* __restrict__ lo, float* __restrict__ tabT, int ldi) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (j >= nh) return;
@@ -109,6 +110,7 @@ __global__ void k_pbar(int lmax, int nh, const double* __restrict__ x, const lon
     const int blk = 2 * m + (d & 1);
     const size_t off = (size_t)(row_off[blk] + (d >> 1)) * ldt + j;
     if (tab) tab[off] = (float)val;
+    if (tabT) tabT[((size_t)blk * nh + j) * ldi + (d >> 1)] = (float)val;
     if (hi) {
       const __nv_bfloat16 h = __double2bfloat16(val);
       const __nv_bfloat16 l = __double2bfloat16(val - (double)__bfloat162float(h));
@@ -330,10 +332,17 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
     int rc = build_recurrence(g, st);
     if (rc) return rc;
   } else {
-  if (g.precision == SHOT_FP32) {
+  float* tabT = nullptr;
+  if (g.precision == SHOT_FP32 || g.precision == SHOT_TF32X3) {
     SHOT_CUDA(cudaMalloc(&g.tab, tab_elems * sizeof(float)));
     SHOT_CUDA(cudaMemsetAsync(g.tab, 0, tab_elems * sizeof(float), st));
     tab = g.tab;
+    if (g.precision == SHOT_TF32X3) {
+      const size_t tt = (size_t)g.nblk * nh * g.ldi;
+      SHOT_CUDA(cudaMalloc(&g.tabT, tt * sizeof(float)));
+      SHOT_CUDA(cudaMemsetAsync(g.tabT, 0, tt * sizeof(float), st));
+      tabT = g.tabT;
+    }
   } else {
     SHOT_CUDA(cudaMalloc(&g.tab_hi, tab_elems * sizeof(__nv_bfloat16)));
     SHOT_CUDA(cudaMalloc(&g.tab_lo, tab_elems * sizeof(__nv_bfloat16)));
@@ -344,7 +353,7 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   }
   dim3 gp((nh + 127) / 128, L);
   count_launch();
-  k_pbar<<<gp, 128, 0, st>>>(g.lmax, nh, g.x_d, g.row_off_d, g.ldt, tab, hi, lo);
+  k_pbar<<<gp, 128, 0, st>>>(g.lmax, nh, g.x_d, g.row_off_d, g.ldt, tab, hi, lo, tabT, g.ldi);
   SHOT_CUDA(cudaGetLastError());
   }
 
@@ -444,6 +453,8 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   cudaFree(w.marg);
   cudaFree(w.ct_hi);
   cudaFree(w.ct_lo);
+  cudaFree(w.ct32);
+  w.ct32 = nullptr;
   cudaFree(w.taus);
   w.taus = nullptr;
   w.ct_hi = w.ct_lo = nullptr;
@@ -477,6 +488,12 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
     SHOT_CUDA(cudaMalloc(&w.ct_lo, ct * sizeof(__nv_bfloat16)));
     SHOT_CUDA(cudaMemsetAsync(w.ct_hi, 0, ct * sizeof(__nv_bfloat16), st));
     SHOT_CUDA(cudaMemsetAsync(w.ct_lo, 0, ct * sizeof(__nv_bfloat16), st));
+  }
+  if (g.precision == SHOT_TF32X3) {
+    w.nmma_cap = tc_nmma(nf);
+    const size_t ct = (size_t)g.nblk * w.nmma_cap * g.ldi;
+    SHOT_CUDA(cudaMalloc(&w.ct32, ct * sizeof(float)));
+    SHOT_CUDA(cudaMemsetAsync(w.ct32, 0, ct * sizeof(float), st));
   }
   w.ldc = ldc;
   w.nf_cap = nf;

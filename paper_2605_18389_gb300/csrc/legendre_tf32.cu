@@ -1,0 +1,368 @@
+// Per-order Legendre contractions on the tensor cores in split TF32 (TF32x3).
+//
+// Same contractions as the other paths (App. C.1 semi-naive SHT; Sec. 3.2 h_l scaling):
+//   analysis   C[i][c] = h_l sum_jh Pbar_lm(x_jh) X[jh][c]        (K = nodes jh)
+//   synthesis  Y[jh][c] = sum_i Pbar_lm(x_jh) C[i][c]               (K = degrees i)
+// Every FP32 operand v is split into two TF32 values: hi = v with its 13 low mantissa bits
+// cleared, lo = v - hi (exact in FP32; the tensor core reads it as TF32 as well).  The
+// product is accumulated in FP32 in tensor memory as A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (tcgen05.mma kind::tf32, K = 8 per instruction); the dropped lo*lo term and the TF32
+// reading of lo leave ~2^-21 relative error per product, against ~2^-16 for BF16x3.  The
+// HBM traffic is that of the BF16x3 path: the table is read once as FP32 (4 bytes an entry,
+// as bf16 hi + lo) and split in shared memory.
+//
+// Both operands are K-major, 128-byte swizzled, 32 FP32 values (one swizzle row) per
+// pipeline stage along K:
+//   analysis   A = table tile [128 degree rows][32 nodes]        (TMA, the table [i][jh])
+//              B = X^T [columns][32 nodes]                        (transposed from the FP32
+//                                                                  spectra tile in smem)
+//   synthesis  A = transposed table tile [128 nodes][32 degrees]  (TMA, a second copy of the
+//                                                                  table laid out [blk][jh][i])
+//              B = C^T [columns][32 degrees]                      (TMA, FP32 C^T written by
+//                                                                  the analysis epilogue)
+// kind::tf32 is used with K-major operands only, hence the transposed table copy.
+// Warp roles: 0 TMA producer, 1 MMA issuer, 2-7 split (six warps: the table tile alone is
+// 16 KB per stage), 8-11 epilogue over a double-buffered accumulator.  Every mbarrier wait
+// is bounded; on expiry the CTA records SHOT_ERR_TIMEOUT and still frees its tensor memory.
+#include "tc_ptx.cuh"
+
+namespace shot {
+namespace {
+
+constexpr int kT32Threads = 384;
+constexpr int kSplitThreads = 192;               // warps 2..7
+constexpr int kTK = 32;                          // K per stage (one 128-byte row of FP32)
+constexpr int kTTile = kBM * kTK * 4;            // 16 KB: 128 rows x 32 FP32
+constexpr int kT32MaxStages = 4;
+constexpr uint32_t kTf32Mask = 0xFFFFE000u;      // sign, exponent and 10 stored mantissa bits
+
+__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+// Instruction descriptor, kind::tf32: TF32 A and B (format 2), FP32 accumulator, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & kTf32Mask); }
+
+// byte offset of FP32 element (row, k) in a K-major 128B-swizzled tile with 32-element rows
+__device__ __forceinline__ uint32_t sw128_offset32(int row, int k) {
+  const uint32_t chunk = (uint32_t)(k >> 2);   // 16-byte chunk (4 values) within the row
+  return (uint32_t)(row >> 3) * 1024u + (uint32_t)(row & 7) * 128u + ((chunk ^ (uint32_t)(row & 7)) << 4) +
+         (uint32_t)(k & 3) * 4u;
+}
+
+// Element-wise split of a tile (the swizzle does not matter): raw -> hi (in place), lo.
+__device__ __forceinline__ void split_inplace(uint8_t* raw, uint8_t* lo, int nbytes, int pt) {
+  for (int o = pt * 16; o < nbytes; o += kSplitThreads * 16) {
+    const float4 v = *reinterpret_cast<const float4*>(raw + o);
+    const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+    *reinterpret_cast<float4*>(raw + o) = h;
+    *reinterpret_cast<float4*>(lo + o) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+  }
+}
+
+// X^T operand: xs[32 nodes][nmma] (row-major FP32, by TMA) -> hi/lo [c][32 nodes], K-major
+// SW128.  One task = 4 consecutive nodes of one column (one 16-byte chunk); nodes past the
+// block (jh0 + k >= nh) and columns past the fields are zero.
+__device__ __forceinline__ void split_xt(const float* xs, int nmma, int ncols, int jh0, int nh, uint8_t* bh,
+                                         uint8_t* bl, int pt) {
+  for (int e = pt; e < nmma * (kTK / 4); e += kSplitThreads) {
+    const int c = e % nmma, k4 = (e / nmma) * 4;
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (c < ncols && jh0 + k4 + q < nh) ? xs[(k4 + q) * nmma + c] : 0.f;
+    const float4 h = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
+    const uint32_t o = sw128_offset32(c, k4);
+    *reinterpret_cast<float4*>(bh + o) = h;
+    *reinterpret_cast<float4*>(bl + o) = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
+  }
+}
+
+struct T32Args {
+  const Tile* tiles;
+  int ntiles;
+  const int* M;
+  const long long* row_off;
+  int nh, ldc, ncols, nmma;
+  const float* h;             // analysis: h_l, or nullptr
+  const ProbState* colscale;  // analysis: per-field factor (gauge beta) of unscaled spectra, or nullptr
+  float* ct;                  // analysis output: C^T [blk][nmma_cap][ldi] FP32
+  float* cf;                  // analysis output (optional): C [row_off + i][ldc] FP32
+  int nmma_cap, ldi;
+  float* Y;                   // synthesis output [blk][jh][ldc]
+  int* err;
+};
+
+// Persistent, warp-specialised TF32x3 Legendre GEMM (roles in the file header).  Stage s
+// holds [A hi (TMA'd raw, split in place)][A lo][B hi][B lo][X raw (analysis)].
+template <int kStages, bool ANA>
+__global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_constant__ CUtensorMap ta,
+                                                                  const __grid_constant__ CUtensorMap tb,
+                                                                  T32Args a) {
+  extern __shared__ uint8_t smraw[];
+  __shared__ TcSmem ctl;
+  __shared__ float cscale[256];
+  uint8_t* base = align1k(smraw);
+  const int nmma = a.nmma, nh = a.nh;
+  const int bbytes = nmma * kTK * 4;   // one B tile (hi or lo); the analysis X tile has the same size
+  const int sbytes = 2 * kTTile + (ANA ? 3 : 2) * bbytes;
+  auto sA_hi = [&](int s) { return base + s * sbytes; };
+  auto sA_lo = [&](int s) { return base + s * sbytes + kTTile; };
+  auto sB_hi = [&](int s) { return base + s * sbytes + 2 * kTTile; };
+  auto sB_lo = [&](int s) { return base + s * sbytes + 2 * kTTile + bbytes; };
+  auto sX = [&](int s) { return base + s * sbytes + 2 * kTTile + 2 * bbytes; };
+  if (ANA)
+    for (int c = threadIdx.x; c < nmma; c += blockDim.x)
+      cscale[c] = (a.colscale && c < a.ncols) ? (float)a.colscale[c >> 1].beta : 1.f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ncols_alloc = tmem_cols_for(nmma);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&ctl.fullA[s], 1);
+      mbar_init(&ctl.fullB[s], kSplitThreads);
+      mbar_init(&ctl.empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl.tfull[b], 1);
+      mbar_init(&ctl.tempty[b], 128);
+    }
+    ctl.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl.tmem, 2 * ncols_alloc);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = ctl.tmem;
+  volatile int* abort = &ctl.abort;
+  auto nkb_of = [&](int blk) { return ANA ? (nh + kTK - 1) / kTK : (a.M[blk] + kTK - 1) / kTK; };
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer, runs ahead across tiles
+      int it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        const Tile tl = a.tiles[t];
+        const int nkb = nkb_of(tl.blk);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % kStages, n = it / kStages;
+          if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
+          mbar_arrive_expect_tx(&ctl.fullA[s], kTTile + bbytes);
+          if (ANA) {   // table rows i of the tile x nodes of this K-chunk; spectra rows = nodes
+            tma_load_2d(sA_hi(s), &ta, &ctl.fullA[s], kb * kTK, (int)(a.row_off[tl.blk] + tl.r0));
+            tma_load_2d(sX(s), &tb, &ctl.fullA[s], 0, tl.blk * nh + kb * kTK);
+          } else {     // transposed table: nodes of the tile x degrees of this K-chunk; C^T rows = columns
+            tma_load_2d(sA_hi(s), &ta, &ctl.fullA[s], kb * kTK, tl.blk * nh + tl.r0);
+            tma_load_2d(sB_hi(s), &tb, &ctl.fullA[s], kb * kTK, tl.blk * a.nmma_cap);
+          }
+        }
+      }
+      // let this CTA's copies land before it can exit
+      for (int k = it > kStages ? it - kStages : 0; k < it; ++k)
+        mbar_drain(&ctl.fullA[k % kStages], (k / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer: every operand it reads was written by the split warps
+      const uint32_t idesc = idesc_tf32(kBM, nmma);
+      int it = 0, lt = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++lt) {
+        const Tile tl = a.tiles[t];
+        const int nkb = nkb_of(tl.blk);
+        const int acc = lt & 1, u = lt >> 1;
+        if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (u - 1) & 1, abort))) break;
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % kStages, n = it / kStages;
+          if (!(ok = mbar_wait(&ctl.fullB[s], n & 1, abort))) break;
+          tc_fence_after();
+          const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
+          const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
+#pragma unroll
+          for (int k = 0; k < kTK / 8; ++k) {   // 8 TF32 = 32 bytes per instruction
+            const uint32_t off = k * 32;
+            const uint64_t a_h = desc_sw128_kmajor(ah + off), a_l = desc_sw128_kmajor(al + off);
+            const uint64_t b_h = desc_sw128_kmajor(bh + off), b_l = desc_sw128_kmajor(bl + off);
+            umma_tf32(d, a_h, b_h, idesc, (kb | k) != 0);
+            umma_tf32(d, a_h, b_l, idesc, 1);
+            umma_tf32(d, a_l, b_h, idesc, 1);
+          }
+          umma_commit(&ctl.empty[s]);
+        }
+        if (!ok) break;
+        umma_commit(&ctl.tfull[acc]);
+      }
+    }
+  } else if (warp < 8) {
+    // split warps: table tile in place -> hi, lo; analysis: X -> X^T hi/lo; synthesis: C^T in place
+    const int pt = threadIdx.x - 64;
+    int it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      const Tile tl = a.tiles[t];
+      const int nkb = nkb_of(tl.blk);
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = it % kStages, n = it / kStages;
+        if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
+        split_inplace(sA_hi(s), sA_lo(s), kTTile, pt);
+        if (ANA)
+          split_xt(reinterpret_cast<const float*>(sX(s)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s), pt);
+        else
+          split_inplace(sB_hi(s), sB_lo(s), bbytes, pt);
+        fence_async_smem();
+        mbar_arrive(&ctl.fullB[s]);
+      }
+    }
+  } else {
+    // epilogue: drain the accumulator of every tile of this CTA (warp 8 + q reads lanes 32q..)
+    const int q = warp - 8;
+    int lt = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
+      const Tile tl = a.tiles[t];
+      const int acc = lt & 1, u = lt >> 1;
+      if (!mbar_wait_warp(&ctl.tfull[acc], u & 1, abort)) break;
+      tc_fence_after();
+      const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc) + ((uint32_t)(q * 32) << 16);
+      const int row = tl.r0 + q * 32 + lane;
+      if (ANA) {
+        const int blk = tl.blk, m = blk >> 1, p = blk & 1;
+        const int M = a.M[blk];
+        const long long ro = a.row_off[blk];
+        const float hl = (a.h && row < M) ? a.h[m + p + 2 * row] : 1.f;
+        for (int c0 = 0; c0 < nmma; c0 += 16) {
+          float v[16];
+          tmem_ld16(d + (uint32_t)c0, v);
+          if (row < M) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int c = c0 + e;
+              if (c < a.ncols) {
+                const float val = v[e] * hl * cscale[c];
+                a.ct[((size_t)blk * a.nmma_cap + c) * a.ldi + row] = val;
+                if (a.cf) a.cf[(size_t)(ro + row) * a.ldc + c] = val;
+              }
+            }
+          }
+        }
+      } else {
+        float* yrow = a.Y + ((size_t)tl.blk * nh + row) * a.ldc;
+        for (int c0 = 0; c0 < nmma; c0 += 16) {
+          float v[16];
+          tmem_ld16(d + (uint32_t)c0, v);
+          if (row < nh) {
+            if (c0 + 16 <= a.ncols) {
+#pragma unroll
+              for (int e = 0; e < 16; e += 4)
+                *reinterpret_cast<float4*>(yrow + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+            } else {
+#pragma unroll
+              for (int e = 0; e < 16; ++e)
+                if (c0 + e < a.ncols) yrow[c0 + e] = v[e];
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&ctl.tempty[acc]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 2 * ncols_alloc);
+  }
+  if (threadIdx.x == 0 && ctl.abort) atomicExch(a.err, SHOT_ERR_TIMEOUT);
+}
+
+// FP32 coefficients C[row_off + i][ldc] -> C^T[blk][nmma_cap][ldi] (synthesis-only input)
+__global__ void k_c_to_ct32(const int* __restrict__ Mrows, const long long* __restrict__ row_off,
+                            const float* __restrict__ C, int ldc, int ncols, float* __restrict__ ct, int nmma_cap,
+                            int ldi) {
+  const int blk = blockIdx.x;
+  const int M = Mrows[blk];
+  const long long ro = row_off[blk];
+  for (int idx = threadIdx.x; idx < M * ncols; idx += blockDim.x) {
+    const int c = idx / M, i = idx - c * M;
+    ct[((size_t)blk * nmma_cap + c) * ldi + i] = C[(size_t)(ro + i) * ldc + c];
+  }
+}
+
+size_t tf32_smem_bytes(int nmma, bool ana, int stages) {
+  return 1024 + (size_t)stages * (2 * kTTile + (ana ? 3 : 2) * (size_t)nmma * kTK * 4);
+}
+
+}  // namespace
+
+int tf32_nmma(int nf) { return (2 * nf + 15) / 16 * 16; }
+
+int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
+                         bool apply_h, cudaStream_t st, const ProbState* colscale) {
+  const Workspace& w = g.ws;
+  const int nmma = tf32_nmma(nf);
+  if (nmma > 256 || nmma > w.nmma_cap || !w.ct32 || !g.tab || !g.tabT) {
+    set_error("TF32X3 path supports at most 128 fields per call");
+    return SHOT_ERR_UNSUPPORTED;
+  }
+  int rc;
+  // deepest pipeline (<= 4 stages) whose tiles fit in one CTA's shared memory, with 2 KB
+  // left for the static control block
+  auto pick = [&](bool a_) {
+    int s = kT32MaxStages;
+    while (s > 1 && tf32_smem_bytes(nmma, a_, s) + 2048 > 227 * 1024) --s;
+    return s;
+  };
+  auto launch = [&](bool a_, const CUtensorMap& ma, const CUtensorMap& mb, const T32Args& args, int ntiles) -> int {
+    const int stages = pick(a_);
+    const size_t smem = tf32_smem_bytes(nmma, a_, stages);
+    auto kern = a_ ? (stages == 4 ? k_legendre_tf32<4, true> : stages == 3 ? k_legendre_tf32<3, true>
+                      : stages == 2 ? k_legendre_tf32<2, true> : k_legendre_tf32<1, true>)
+                   : (stages == 4 ? k_legendre_tf32<4, false> : stages == 3 ? k_legendre_tf32<3, false>
+                      : stages == 2 ? k_legendre_tf32<2, false> : k_legendre_tf32<1, false>);
+    SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = ntiles < g.num_sms ? ntiles : g.num_sms;
+    ProfScope prof(a_ ? PK_ANALYSIS : PK_SYNTHESIS, st);
+    count_launch();
+    kern<<<grid, kT32Threads, smem, st>>>(ma, mb, args);
+    SHOT_CUDA(cudaGetLastError());
+    return SHOT_OK;
+  };
+  if (ana) {
+    CUtensorMap ma, mx;
+    if ((rc = make_map_f32(&ma, g.tab, g.nh, g.rows_total, g.ldt, kTK, kBM, true))) return rc;
+    if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kTK))) return rc;
+    const T32Args args{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma,
+                       apply_h ? g.h_d : nullptr, colscale, w.ct32, Cf, w.nmma_cap, g.ldi, nullptr, w.dev_int + 4};
+    if ((rc = launch(true, ma, mx, args, g.ntiles_ana))) return rc;
+  }
+  if (syn) {
+    CUtensorMap ma, mb;
+    if ((rc = make_map_f32(&ma, g.tabT, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kTK, kBM, true))) return rc;
+    if ((rc = make_map_f32(&mb, w.ct32, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, kTK, nmma, true))) return rc;
+    const T32Args args{g.tiles_syn, g.ntiles_syn, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma,
+                       nullptr, nullptr, nullptr, nullptr, w.nmma_cap, g.ldi, Y, w.dev_int + 4};
+    if ((rc = launch(false, ma, mb, args, g.ntiles_syn))) return rc;
+  }
+  return SHOT_OK;
+}
+
+int launch_c_to_ct32(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st) {
+  const Workspace& w = g.ws;
+  count_launch();
+  k_c_to_ct32<<<g.nblk, 256, 0, st>>>(g.M_d, g.row_off_d, C, ldc, 2 * nf, w.ct32, w.nmma_cap, g.ldi);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
+}
+
+}  // namespace shot

@@ -80,6 +80,7 @@ struct Workspace {
   size_t uv_cap = 0;
   __nv_bfloat16* ct_hi = nullptr;   // BF16X3: scaled coefficients C^T [blk][nmma_cap][ldi]
   __nv_bfloat16* ct_lo = nullptr;
+  float* ct32 = nullptr;            // TF32X3: scaled coefficients C^T [blk][nmma_cap][ldi], FP32
   int nmma_cap = 0;
   int* dev_int = nullptr;   // device counters: [0] iterations, [1] active, [4] timeout flag
   int* host_int = nullptr;  // pinned mirror
@@ -121,7 +122,8 @@ struct Grid {
   float* a_d = nullptr;         // per-ring area weight (FP32)
   float2* tw_d = nullptr;       // exp(-2 pi i k / nlon), k < nlon
   float* h_d = nullptr;         // heat multipliers for the current call, [lmax+1]
-  float* tab = nullptr;         // FP32 folded table
+  float* tab = nullptr;         // FP32 folded table [row][ldt] (FP32 and TF32X3 grids)
+  float* tabT = nullptr;        // TF32X3: the table transposed per block, [blk][jh][ldi], zero for i >= M
   __nv_bfloat16* tab_hi = nullptr;  // BF16X3 split table [row][ldt]
   __nv_bfloat16* tab_lo = nullptr;
   int ldi = 0;                  // row stride of C^T (>= the largest block, multiple of 8)
@@ -219,6 +221,9 @@ int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd = nullptr);
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
                        bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr, int xsplit = 0);
 int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
+int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
+                         bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
+int launch_c_to_ct32(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
 int build_recurrence(Grid& g, cudaStream_t st);
 int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
                         bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);

@@ -24,6 +24,7 @@ SHOT_ERR_TIMEOUT = -7
 
 SHOT_FP32 = 0
 SHOT_BF16X3 = 1
+SHOT_TF32X3 = 2
 SHOT_TABLE = 0
 SHOT_RECURRENCE = 1
 SHOT_GRAD_UNROLLED = 0

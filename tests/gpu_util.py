@@ -26,10 +26,11 @@ def s_err(s_gpu, s_ref, ot_ref, tol):
     return np.abs(s_gpu - s_ref) / (tol * np.abs(s_ref) + 4.0 * 2.0 ** -24 * np.abs(ot_ref))
 
 
-# Unit roundoff of the Legendre contractions per precision: FP32 FFMA (2^-24) and the
-# bf16 hi/lo split with three products (dropped lo*lo term and the rounding of lo:
-# <= 3 * 2^-18 per product, taken as 2^-16).
-UNIT = {"fp32": 2.0 ** -24, "bf16x3": 2.0 ** -16}
+# Unit roundoff of the Legendre contractions per precision: FP32 FFMA (2^-24), the bf16
+# hi/lo split with three products (dropped lo*lo term and the rounding of lo: <= 3 * 2^-18
+# per product, taken as 2^-16) and the tf32 hi/lo split with three products (dropped lo*lo
+# and lo read as TF32: <= 3 * 2^-22 per product, taken as 2^-20).
+UNIT = {"fp32": 2.0 ** -24, "bf16x3": 2.0 ** -16, "tf32x3": 2.0 ** -20}
 
 
 def s_err_prec(s_gpu, s_ref, ot_ref, tol, prec):

@@ -15,8 +15,8 @@ torch = pytest.importorskip("torch")
 
 from paper_2605_18389_gb300 import shot  # noqa: E402
 
-PREC = {"fp32": shot.SHOT_FP32, "bf16x3": shot.SHOT_BF16X3}
-TOL = {"fp32": 2e-5, "bf16x3": 2e-4}
+PREC = {"fp32": shot.SHOT_FP32, "bf16x3": shot.SHOT_BF16X3, "tf32x3": shot.SHOT_TF32X3}
+TOL = {"fp32": 2e-5, "bf16x3": 2e-4, "tf32x3": 2e-5}
 
 
 def _grid(nside, lmax=-1, prec="fp32", mode=shot.SHOT_TABLE):
@@ -39,7 +39,7 @@ def test_geometry_matches_oracle(nside):
     shot.shot_grid_free(g)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "tf32x3"])
 @pytest.mark.parametrize("nside,lmax,nf,t", [(1, -1, 1, 0.2), (2, -1, 3, 0.05), (4, -1, 5, 0.02),
                                              (8, 11, 2, 0.01), (16, -1, 24, 3e-3)])
 def test_heat_apply_matches_oracle(prec, nside, lmax, nf, t):
