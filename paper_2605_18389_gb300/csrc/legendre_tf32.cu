@@ -61,29 +61,57 @@ __device__ __forceinline__ uint32_t sw128_offset32(int row, int k) {
 }
 
 // Element-wise split of a tile (the swizzle does not matter): raw -> hi (in place), lo.
+// Each thread loads kSplitBatch chunks before it stores any, so the loads overlap.
+constexpr int kSplitBatch = 6;   // 16 KB / (192 threads x 16 B) = 5.3 chunks per thread
 __device__ __forceinline__ void split_inplace(uint8_t* raw, uint8_t* lo, int nbytes, int pt) {
-  for (int o = pt * 16; o < nbytes; o += kSplitThreads * 16) {
-    const float4 v = *reinterpret_cast<const float4*>(raw + o);
-    const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-    *reinterpret_cast<float4*>(raw + o) = h;
-    *reinterpret_cast<float4*>(lo + o) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+  for (int base = 0; base < nbytes; base += kSplitBatch * kSplitThreads * 16) {
+    float4 v[kSplitBatch];
+#pragma unroll
+    for (int i = 0; i < kSplitBatch; ++i) {
+      const int o = base + (pt + i * kSplitThreads) * 16;
+      if (o < nbytes) v[i] = *reinterpret_cast<const float4*>(raw + o);
+    }
+#pragma unroll
+    for (int i = 0; i < kSplitBatch; ++i) {
+      const int o = base + (pt + i * kSplitThreads) * 16;
+      if (o < nbytes) {
+        const float4 h = make_float4(tf32_hi(v[i].x), tf32_hi(v[i].y), tf32_hi(v[i].z), tf32_hi(v[i].w));
+        *reinterpret_cast<float4*>(raw + o) = h;
+        *reinterpret_cast<float4*>(lo + o) = make_float4(v[i].x - h.x, v[i].y - h.y, v[i].z - h.z, v[i].w - h.w);
+      }
+    }
   }
 }
 
 // X^T operand: xs[32 nodes][nmma] (row-major FP32, by TMA) -> hi/lo [c][32 nodes], K-major
 // SW128.  One task = 4 consecutive nodes of one column (one 16-byte chunk); nodes past the
 // block (jh0 + k >= nh) and columns past the fields are zero.
+// Two tasks per thread are loaded before either is stored.
 __device__ __forceinline__ void split_xt(const float* xs, int nmma, int ncols, int jh0, int nh, uint8_t* bh,
                                          uint8_t* bl, int pt) {
-  for (int e = pt; e < nmma * (kTK / 4); e += kSplitThreads) {
-    const int c = e % nmma, k4 = (e / nmma) * 4;
-    float v[4];
+  const int ntask = nmma * (kTK / 4);
+  for (int e0 = pt; e0 < ntask; e0 += 2 * kSplitThreads) {
+    float v[2][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = (c < ncols && jh0 + k4 + q < nh) ? xs[(k4 + q) * nmma + c] : 0.f;
-    const float4 h = make_float4(tf32_hi(v[0]), tf32_hi(v[1]), tf32_hi(v[2]), tf32_hi(v[3]));
-    const uint32_t o = sw128_offset32(c, k4);
-    *reinterpret_cast<float4*>(bh + o) = h;
-    *reinterpret_cast<float4*>(bl + o) = make_float4(v[0] - h.x, v[1] - h.y, v[2] - h.z, v[3] - h.w);
+    for (int b = 0; b < 2; ++b) {
+      const int e = e0 + b * kSplitThreads;
+      const int c = e % nmma, k4 = (e / nmma) * 4;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        v[b][q] = (e < ntask && c < ncols && jh0 + k4 + q < nh) ? xs[(k4 + q) * nmma + c] : 0.f;
+    }
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      const int e = e0 + b * kSplitThreads;
+      if (e < ntask) {
+        const int c = e % nmma, k4 = (e / nmma) * 4;
+        const float4 h = make_float4(tf32_hi(v[b][0]), tf32_hi(v[b][1]), tf32_hi(v[b][2]), tf32_hi(v[b][3]));
+        const uint32_t o = sw128_offset32(c, k4);
+        *reinterpret_cast<float4*>(bh + o) = h;
+        *reinterpret_cast<float4*>(bl + o) =
+            make_float4(v[b][0] - h.x, v[b][1] - h.y, v[b][2] - h.z, v[b][3] - h.w);
+      }
+    }
   }
 }
 
@@ -124,7 +152,12 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
     for (int c = threadIdx.x; c < nmma; c += blockDim.x)
       cscale[c] = (a.colscale && c < a.ncols) ? (float)a.colscale[c >> 1].beta : 1.f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t ncols_alloc = tmem_cols_for(nmma);
+  // B hi and B lo are adjacent in shared memory, so for 2 nmma <= 256 they form one operand
+  // of N = 2 nmma: A_hi [B_hi | B_lo] and A_lo B_hi are two MMAs per K step instead of three
+  // (one fewer read of the A tile); the accumulator then holds two halves that the epilogue adds.
+  const bool bcat = 2 * nmma <= 256;
+  const int nacc = bcat ? 2 * nmma : nmma;
+  const uint32_t ncols_alloc = tmem_cols_for(nacc);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -173,7 +206,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer: every operand it reads was written by the split warps
-      const uint32_t idesc = idesc_tf32(kBM, nmma);
+      const uint32_t idesc = idesc_tf32(kBM, nmma), idesc2 = idesc_tf32(kBM, nacc);
       int it = 0, lt = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++lt) {
@@ -194,9 +227,14 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
             const uint32_t off = k * 32;
             const uint64_t a_h = desc_sw128_kmajor(ah + off), a_l = desc_sw128_kmajor(al + off);
             const uint64_t b_h = desc_sw128_kmajor(bh + off), b_l = desc_sw128_kmajor(bl + off);
-            umma_tf32(d, a_h, b_h, idesc, (kb | k) != 0);
-            umma_tf32(d, a_h, b_l, idesc, 1);
-            umma_tf32(d, a_l, b_h, idesc, 1);
+            if (bcat) {   // b_h spans B_hi and B_lo (2 nmma rows)
+              umma_tf32(d, a_h, b_h, idesc2, (kb | k) != 0);
+              umma_tf32(d, a_l, b_h, idesc, 1);
+            } else {
+              umma_tf32(d, a_h, b_h, idesc, (kb | k) != 0);
+              umma_tf32(d, a_h, b_l, idesc, 1);
+              umma_tf32(d, a_l, b_h, idesc, 1);
+            }
           }
           umma_commit(&ctl.empty[s]);
         }
@@ -243,6 +281,12 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         for (int c0 = 0; c0 < nmma; c0 += 16) {
           float v[16];
           tmem_ld16(d + (uint32_t)c0, v);
+          if (bcat) {   // + A_hi B_lo, accumulated in the second half
+            float w[16];
+            tmem_ld16(d + (uint32_t)(nmma + c0), w);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] += w[e];
+          }
           if (row < M) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -260,6 +304,12 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         for (int c0 = 0; c0 < nmma; c0 += 16) {
           float v[16];
           tmem_ld16(d + (uint32_t)c0, v);
+          if (bcat) {   // + A_hi B_lo, accumulated in the second half
+            float w[16];
+            tmem_ld16(d + (uint32_t)(nmma + c0), w);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] += w[e];
+          }
           if (row < nh) {
             if (c0 + 16 <= a.ncols) {
 #pragma unroll

@@ -52,7 +52,8 @@ def test_tf32x3_grid_reports_precision(grid_cache):
 @pytest.mark.parametrize("nlat,nlon,lmax,nf,quad", [(8, None, -1, 1, "gl"), (32, None, -1, 3, "gl"),
                                                     (33, 72, -1, 2, "gl"), (64, None, -1, 24, "gl"),
                                                     (180, None, -1, 5, "gl"), (20, 45, 13, 3, "gl"),
-                                                    (32, None, -1, 128, "gl"), (65, 135, -1, 4, "cc"),
+                                                    (32, None, -1, 128, "gl"), (48, None, -1, 40, "gl"),
+                                                    (65, 135, -1, 4, "cc"),
                                                     (300, None, -1, 2, "gl")])
 def test_tf32x3_analysis_matches_oracle(grid_cache, nlat, nlon, lmax, nf, quad):
     g, og = grid_cache(nlat, nlon, lmax, quad)
@@ -68,7 +69,8 @@ def test_tf32x3_analysis_matches_oracle(grid_cache, nlat, nlon, lmax, nf, quad):
 
 @pytest.mark.parametrize("nlat,nlon,lmax,nf,quad", [(8, None, -1, 1, "gl"), (32, None, -1, 5, "gl"),
                                                     (180, None, -1, 2, "gl"), (20, 45, 13, 3, "gl"),
-                                                    (65, 135, -1, 4, "cc"), (64, None, -1, 100, "gl")])
+                                                    (65, 135, -1, 4, "cc"), (64, None, -1, 100, "gl"),
+                                                    (48, None, -1, 64, "gl")])
 def test_tf32x3_synthesis_matches_oracle(grid_cache, nlat, nlon, lmax, nf, quad):
     g, og = grid_cache(nlat, nlon, lmax, quad)
     L = og.lmax + 1
