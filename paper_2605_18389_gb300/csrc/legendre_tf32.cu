@@ -132,7 +132,7 @@ struct T32Args {
 
 // Persistent, warp-specialised TF32x3 Legendre GEMM (roles in the file header).  Stage s
 // holds [A hi (TMA'd raw, split in place)][A lo][B hi][B lo][X raw (analysis)].
-template <int kStages, bool ANA>
+template <int kStages, bool ANA, bool BCAT>
 __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_constant__ CUtensorMap ta,
                                                                   const __grid_constant__ CUtensorMap tb,
                                                                   T32Args a) {
@@ -152,10 +152,11 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
     for (int c = threadIdx.x; c < nmma; c += blockDim.x)
       cscale[c] = (a.colscale && c < a.ncols) ? (float)a.colscale[c >> 1].beta : 1.f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // B hi and B lo are adjacent in shared memory, so for 2 nmma <= 256 they form one operand
-  // of N = 2 nmma: A_hi [B_hi | B_lo] and A_lo B_hi are two MMAs per K step instead of three
-  // (one fewer read of the A tile); the accumulator then holds two halves that the epilogue adds.
-  const bool bcat = 2 * nmma <= 256;
+  // BCAT (2 nmma <= 256): B hi and B lo are adjacent in shared memory and form one operand
+  // of N = 2 nmma, so A_hi [B_hi | B_lo] and A_lo B_hi are two MMAs per K step instead of
+  // three (one fewer read of the A tile); the accumulator then holds two halves that the
+  // epilogue adds.
+  constexpr bool bcat = BCAT;
   const int nacc = bcat ? 2 * nmma : nmma;
   const uint32_t ncols_alloc = tmem_cols_for(nacc);
 
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
             const uint32_t off = k * 32;
             const uint64_t a_h = desc_sw128_kmajor(ah + off), a_l = desc_sw128_kmajor(al + off);
             const uint64_t b_h = desc_sw128_kmajor(bh + off), b_l = desc_sw128_kmajor(bl + off);
-            if (bcat) {   // b_h spans B_hi and B_lo (2 nmma rows)
+            if constexpr (BCAT) {   // b_h spans B_hi and B_lo (2 nmma rows)
               umma_tf32(d, a_h, b_h, idesc2, (kb | k) != 0);
               umma_tf32(d, a_l, b_h, idesc, 1);
             } else {
@@ -281,7 +282,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         for (int c0 = 0; c0 < nmma; c0 += 16) {
           float v[16];
           tmem_ld16(d + (uint32_t)c0, v);
-          if (bcat) {   // + A_hi B_lo, accumulated in the second half
+          if constexpr (BCAT) {   // + A_hi B_lo, accumulated in the second half
             float w[16];
             tmem_ld16(d + (uint32_t)(nmma + c0), w);
 #pragma unroll
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         for (int c0 = 0; c0 < nmma; c0 += 16) {
           float v[16];
           tmem_ld16(d + (uint32_t)c0, v);
-          if (bcat) {   // + A_hi B_lo, accumulated in the second half
+          if constexpr (BCAT) {   // + A_hi B_lo, accumulated in the second half
             float w[16];
             tmem_ld16(d + (uint32_t)(nmma + c0), w);
 #pragma unroll
@@ -376,10 +377,15 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
   auto launch = [&](bool a_, const CUtensorMap& ma, const CUtensorMap& mb, const T32Args& args, int ntiles) -> int {
     const int stages = pick(a_);
     const size_t smem = tf32_smem_bytes(nmma, a_, stages);
-    auto kern = a_ ? (stages == 4 ? k_legendre_tf32<4, true> : stages == 3 ? k_legendre_tf32<3, true>
-                      : stages == 2 ? k_legendre_tf32<2, true> : k_legendre_tf32<1, true>)
-                   : (stages == 4 ? k_legendre_tf32<4, false> : stages == 3 ? k_legendre_tf32<3, false>
-                      : stages == 2 ? k_legendre_tf32<2, false> : k_legendre_tf32<1, false>);
+    const bool bc = 2 * nmma <= 256;
+    auto kern = bc ? (a_ ? (stages == 4 ? k_legendre_tf32<4, true, true> : stages == 3 ? k_legendre_tf32<3, true, true>
+                            : stages == 2 ? k_legendre_tf32<2, true, true> : k_legendre_tf32<1, true, true>)
+                         : (stages == 4 ? k_legendre_tf32<4, false, true> : stages == 3 ? k_legendre_tf32<3, false, true>
+                            : stages == 2 ? k_legendre_tf32<2, false, true> : k_legendre_tf32<1, false, true>))
+                   : (a_ ? (stages == 4 ? k_legendre_tf32<4, true, false> : stages == 3 ? k_legendre_tf32<3, true, false>
+                            : stages == 2 ? k_legendre_tf32<2, true, false> : k_legendre_tf32<1, true, false>)
+                         : (stages == 4 ? k_legendre_tf32<4, false, false> : stages == 3 ? k_legendre_tf32<3, false, false>
+                            : stages == 2 ? k_legendre_tf32<2, false, false> : k_legendre_tf32<1, false, false>));
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = ntiles < g.num_sms ? ntiles : g.num_sms;
     ProfScope prof(a_ ? PK_ANALYSIS : PK_SYNTHESIS, st);
