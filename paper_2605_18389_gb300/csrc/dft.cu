@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
     const float* __restrict__ a_ring, FftPlan pl, const float2* __restrict__ tw_g, EpiParams ep) {
   extern __shared__ __align__(16) float2 sm[];
   __shared__ float red[kThreads / 32][FG * NPART];
+  __shared__ EpiField fi[FG];
   const int N = nlon;
   const int ld = seq_ld(N);
   float2* buf = sm;
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
     for (int blk = threadIdx.x; blk < nblk_v; blk += blockDim.x)
       cp_async8(stg + blk * FG, Y + ((size_t)blk * nh + jh) * ldc + 2 * f0);
   }
+  epi_fields_load<FG>(ep, f0, nfg, fi);
   for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
   // zero the band lmax < m < N - lmax
   const int nz = N - 2 * lmax - 1;
@@ -153,6 +155,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
     for (int k = threadIdx.x; k < nz; k += blockDim.x) buf[q * ld + lmax + 1 + k] = make_float2(0.f, 0.f);
   cp_async_wait_all();
   __syncthreads();
+  epi_prefetch_marginals<FG>(ep, fi, nfg, (size_t)j * nlon, (size_t)(nlat - 1 - jh) * nlon, nlat - 1 - jh != jh, N);
   const int nm = lmax + 1;
   for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
@@ -175,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
   const float aj = a_ring[j];
   const bool two = (J != j);   // false only for the equator ring of an odd grid
   ring_pair_epilogue<FG, kThreads>(z, other, ld, N, nfg, f0, (size_t)nlat * nlon, (size_t)j * nlon,
-                                   (size_t)J * nlon, two, aj, nh, jh, ep, red);
+                                   (size_t)J * nlon, two, aj, nh, jh, ep, red, fi);
   if (ep.mode == EPI_PLAIN) return;
   if (ep.mode == EPI_UPDATE && ep.xout) {
     // the new scaling of this ring pair is in `other`: transform it for the next half-step

@@ -18,6 +18,54 @@
 
 namespace shot {
 
+// Per-field state the epilogue needs, read into shared memory by epi_fields_load at the start
+// of the kernel (while the spectra gather is in flight), so that the epilogue does not wait on
+// the chain problem state -> marginal pointer -> marginal values.
+struct EpiField {
+  const float* marg;   // p (u-step) or q (v-step) of the field
+  int live;            // EPI_FINAL: status >= 0; otherwise active
+  int balanced;
+  float gamma, et;
+};
+
+// Threads 0..FG-1 fill fi[q] for the CTA's fields f0 + q (q < nfg).
+template <int FG>
+__device__ __forceinline__ void epi_fields_load(const EpiParams& ep, int f0, int nfg, EpiField* fi) {
+  const int q = threadIdx.x;
+  if (q < FG && q < nfg && ep.mode != EPI_PLAIN) {
+    const ProbState* P = ep.ps + f0 + q;
+    EpiField e;
+    e.marg = ep.marg[f0 + q];
+    e.live = (ep.mode == EPI_FINAL) ? (P->status >= 0) : (P->active != 0);
+    e.balanced = P->balanced;
+    e.gamma = P->gamma;
+    e.et = P->et;
+    fi[q] = e;
+  }
+}
+
+// After fi is visible to the block: asks L2 for the marginal rows j and J of the CTA's live
+// fields (UPDATE and CHECK modes), one 128-byte line per thread, so that the epilogue's loads
+// hit L2 instead of waiting on DRAM after the inverse transform.
+template <int FG>
+__device__ __forceinline__ void epi_prefetch_marginals(const EpiParams& ep, const EpiField* fi, int nfg, size_t rj,
+                                                       size_t rJ, bool two, int N) {
+  if (ep.mode != EPI_UPDATE && ep.mode != EPI_CHECK) return;
+  const int lines = (N + 31) / 32 + 1;   // a row of N floats spans at most this many 128-byte lines
+  const int per_field = 2 * lines;
+  for (int t = threadIdx.x; t < nfg * per_field; t += blockDim.x) {
+    const int q = t / per_field, r = t - q * per_field;
+    if (!fi[q].live) continue;
+    const int ring = r / lines, l = r - ring * lines;
+    if (ring == 1 && !two) continue;
+    const float* row = fi[q].marg + (ring ? rJ : rj);
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(row) & ~uintptr_t(127);
+    const uintptr_t a = a0 + (uintptr_t)l * 128;
+    if (a < reinterpret_cast<uintptr_t>(row + N))
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+  }
+}
+
 __device__ __forceinline__ float epi_warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -28,7 +76,7 @@ template <int FG, int NT>
 __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* other, int ld, int N, int nfg, int f0,
                                                    size_t fstride, size_t rj, size_t rJ, bool two, float aj,
                                                    int nh, int jh, const EpiParams& ep,
-                                                   float (*red)[FG * NPART]) {
+                                                   float (*red)[FG * NPART], const EpiField* fi) {
   constexpr int kEpiBatch = 6;   // longitudes per thread whose marginal values are loaded together
   if (ep.mode == EPI_PLAIN) {
     for (int q = 0; q < nfg; ++q) {
@@ -58,18 +106,18 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
     const size_t fbase = (size_t)f * fstride;
     float* outf = ep.out + fbase;
     float* othf = ep.other ? ep.other + fbase : nullptr;
-    ProbState* P = ep.ps + f;
+    const EpiField F = fi[q];
     if (ep.mode == EPI_UPDATE) {
-      if (!P->active) {
+      if (!F.live) {
         if (ep.xout) {   // frozen problem: transform the stored scaling
           for (int k = threadIdx.x; k < N; k += blockDim.x)
             other[q * ld + k] = make_float2(outf[rj + k], two ? outf[rJ + k] : 0.f);
         }
         continue;
       }
-      const float* mg = ep.marg[f];
-      const int bal = P->balanced;
-      const float gam = P->gamma, et = P->et;
+      const float* mg = F.marg;
+      const int bal = F.balanced;
+      const float gam = F.gamma, et = F.et;
       for (int k0 = threadIdx.x; k0 < N; k0 += kEpiBatch * NT) {
         // the marginal values of all this thread's longitudes first, then the arithmetic
         float pv[kEpiBatch][2];
@@ -112,9 +160,9 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
         }
       }
     } else if (ep.mode == EPI_CHECK) {
-      if (!P->active) continue;
-      const float* mg = ep.marg[f];
-      const float al = (float)P->alpha;
+      if (!F.live) continue;
+      const float* mg = F.marg;
+      const float al = (float)ep.ps[f].alpha;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const float2 zz = z[q * ld + k];
 #pragma unroll
@@ -134,7 +182,8 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
         }
       }
     } else {  // EPI_FINAL: z = K v_true; ep.other = u buffer, ep.out = v buffer
-      if (P->status < 0) continue;
+      if (!F.live) continue;
+      const ProbState* P = ep.ps + f;
       const float* pp = ep.marg[f];
       const float* qq = ep.marg2[f];
       const float al = (float)P->alpha, be = (float)P->beta;
@@ -189,9 +238,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
     const int q = threadIdx.x / NPART, i = threadIdx.x - q * NPART;
     if (q < nfg) {
       const int f = f0 + q;
-      const ProbState* P = ep.ps + f;
-      const bool live = (ep.mode == EPI_FINAL) ? (P->status >= 0) : (P->active != 0);
-      if (live) {
+      if (fi[q].live) {
         double t = 0.0;
         for (int w = 0; w < NT / 32; ++w) t += (double)red[w][threadIdx.x];
         ep.part[((size_t)f * nh + jh) * NPART + i] = t;

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_idft(const float* __restrict_
                                                         int nh, float area, EpiParams ep) {
   extern __shared__ __align__(16) float2 sm[];
   __shared__ float red[kHpThreads / 32][FG * NPART];
+  __shared__ EpiField fi[FG];
   const int jh = blockIdx.y, f0 = blockIdx.x * FG;
   const int nfg = min(FG, nf - f0);
   const int j = jh, J = nrings - 1 - jh;
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_idft(const float* __restrict_
   float2* ph = tw + n;           // [lmax + 1]
   float2* gn = ph + nm;          // [lmax + 1][FG]  G_N = E + O
   float2* gs = gn + nm * FG;     // [lmax + 1][FG]  G_S = E - O
+  epi_fields_load<FG>(ep, f0, nfg, fi);
   ring_tables(tw, ph, n, rphase[j], lmax);
   for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
@@ -172,7 +174,7 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_idft(const float* __restrict_
   __syncthreads();
   const bool two = (J != j);
   ring_pair_epilogue<FG, kHpThreads>(zb, za, n, n, nfg, f0, npix, (size_t)roff[j], (size_t)roff[J], two, area, nh,
-                                     jh, ep, red);
+                                     jh, ep, red, fi);
   if (ep.mode == EPI_PLAIN) return;
   if (ep.mode == EPI_UPDATE && ep.xout) {   // the new scaling is in za: transform it
     __syncthreads();
