@@ -143,6 +143,7 @@ struct Grid {
   int fused_heat = 0;           // BF16X3 table grids: fused analysis + synthesis kernel
   int split_spectra = 0;        // BF16X3 table grids: the solver keeps bf16 hi/lo spectra
   int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core analysis (0 = tuned)
+  int idft_nonpersistent = 0;   // SHOT_IDFT_PERSISTENT=0: update half-steps use the one-item-per-CTA k_idft
   int ana_transposed = 0;       // SHOT_ANA_TRANSPOSED=1: fields on M, degree rows on N (k_ana_tc_t)
                                 // instead of 128-row tiles of degrees on M
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use

@@ -141,3 +141,35 @@ def test_divergence_with_zero_marginal_entries(grid_cache, tau):
     assert np.all(r["status"] == 0) and np.all(ref["status"] == 0)
     assert np.all(np.isfinite(r["S"])) and np.all(np.isfinite(ref["S"]))
     assert np.all(s_err(r["S"], ref["S"], ref["runs"]["ot"][:2], TOL_S) <= 1.0)
+
+
+@pytest.mark.parametrize("nlat,pairs,tau", [(256, 8, math.inf), (75, 3, 1.0), (45, 1, math.inf)])
+def test_persistent_update_kernel_matches_one_item_per_cta(nlat, pairs, tau):
+    """The solver's update half-steps run in a persistent kernel that prefetches the next
+    (ring pair, field group) item's spectra and marginals; the per-item arithmetic is that of
+    the one-item-per-CTA kernel (SHOT_IDFT_PERSISTENT=0), so u, v and S agree bit for bit.
+    Sizes: several items per CTA (256), an odd grid with an equator ring (75, 45), a partial
+    field group (3 problems)."""
+    import os
+    og = OGrid(nlat)
+    p, q = inputs.pairs("paper_uniform", 4000 + nlat, pairs, og.x, og.nlon, og.a_ring,
+                        masses=not math.isinf(tau))
+    pt = torch.from_numpy(p.astype(np.float32)).cuda()
+    qt = torch.from_numpy(q.astype(np.float32)).cuda()
+    res = []
+    for flag in ("1", "0"):
+        os.environ["SHOT_IDFT_PERSISTENT"] = flag
+        try:
+            g = shot.shot_grid_init(nlat)
+        finally:
+            del os.environ["SHOT_IDFT_PERSISTENT"]
+        try:
+            u3 = torch.empty((3 * pairs, og.nlat, og.nlon), device="cuda")
+            v3 = torch.empty_like(u3)
+            rc, r = shot.shot_divergence(g, pt, qt, 0.05, tau, max_iter=40, tol=0.0, check_every=10, u3=u3, v3=v3)
+            assert rc == 0
+            res.append((u3.cpu().numpy(), v3.cpu().numpy(), np.asarray(r["S"])))
+        finally:
+            shot.shot_grid_free(g)
+    for a, b in zip(res[0], res[1]):
+        np.testing.assert_array_equal(a, b)
