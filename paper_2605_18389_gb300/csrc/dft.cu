@@ -192,94 +192,61 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
 // Persistent form of k_idft for the solver's update half-steps (EPI_UPDATE with the fused
 // forward transform of the new scaling).  A CTA walks over items (ring pair jh, field group)
 // item = blockIdx.x + i gridDim.x, consecutive items covering the field groups of one ring
-// pair.  While it transforms one item, cp.async brings the next item's inputs into shared
-// memory: its spectra rows (issued after this item's unpack) and its marginal rows (issued
-// after this item's epilogue), so neither the gather nor the update waits on DRAM.  Two CTAs
-// per SM (~101 KB of shared memory each at 1440 longitudes and two fields).
-__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem)
-               : "memory");
-}
+// pair.  Right after it has unpacked one item's spectra it starts the cp.async gather of the
+// next item's spectra rows into a staging area and asks L2 for the next item's marginal rows,
+// so that neither the gather nor the update waits on DRAM.  The stage twiddles are read
+// through L1 (every CTA reads the same N values) rather than copied into shared memory, which
+// keeps three CTAs per SM (~68 KB each at 1440 longitudes and two fields).
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// shared-memory layout of k_idft_p (bytes): [buf][b1] sequences, twiddles, spectra staging,
-// marginal staging; each part 16-byte aligned
+// shared-memory layout of k_idft_p (bytes): [buf][b1] sequences, then the spectra staging
+// area, 16-byte aligned
 struct IdftPLayout {
-  size_t stg, mst, total;
+  size_t stg, total;
 };
 __host__ __device__ inline IdftPLayout idft_p_layout(int FG, int N, int lmax) {
-  auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
   IdftPLayout L;
-  L.stg = up16((size_t)(2 * FG * seq_ld(N) + N) * sizeof(float2));
-  L.mst = L.stg + up16((size_t)(2 * lmax + 1) * FG * sizeof(float2));
-  L.total = L.mst + (size_t)FG * 2 * N * sizeof(float);
+  L.stg = ((size_t)2 * FG * seq_ld(N) * sizeof(float2) + 15) / 16 * 16;
+  L.total = L.stg + (size_t)(2 * lmax + 1) * FG * sizeof(float2);
   return L;
 }
 
 template <int FG, class PL = RuntimePlan>
-__global__ void __launch_bounds__(kThreads, 2) k_idft_p(
+__global__ void __launch_bounds__(kThreads, 3) k_idft_p(
     const float* __restrict__ Y, int ldc, int nf, int nlat, int nlon, int lmax, int nh,
     const float* __restrict__ a_ring, FftPlan pl, const float2* __restrict__ tw_g, EpiParams ep, int ngroups) {
   extern __shared__ __align__(16) float2 sm[];
   __shared__ float red[kThreads / 32][FG * NPART];
   __shared__ EpiField fi[2][FG];
   const int N = nlon, ld = seq_ld(N);
-  const IdftPLayout lay = idft_p_layout(FG, N, lmax);
   float2* buf = sm;
   float2* b1 = buf + FG * ld;
-  float2* tw = b1 + FG * ld;
-  float2* stg = reinterpret_cast<float2*>(reinterpret_cast<uint8_t*>(sm) + lay.stg);   // [blk][FG]
-  float* mst = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(sm) + lay.mst);    // [FG][2][N]
+  float2* stg = reinterpret_cast<float2*>(reinterpret_cast<uint8_t*>(sm) + idft_p_layout(FG, N, lmax).stg);
   const int nblk_v = 2 * lmax + 1;   // the (2m+1) block of m = lmax is empty
   const int nitems = ngroups * nh;
-  const bool vec4 = (N % 4) == 0;    // marginal rows start on 16-byte boundaries (if the fields do)
 
   auto item_geom = [&](int item, int& jh, int& f0, int& nfg) {
     jh = item / ngroups;
     f0 = (item - jh * ngroups) * FG;
     nfg = min(FG, nf - f0);
   };
-  auto issue_Y = [&](int item) {
-    if (item < nitems) {
-      int jh, f0, nfg;
-      item_geom(item, jh, f0, nfg);
-      if constexpr (FG % 2 == 0) {
-        constexpr int ch = FG / 2;
-        for (int e = threadIdx.x; e < nblk_v * ch; e += blockDim.x) {
-          const int blk = e / ch, c = e - blk * ch;
-          if (2 * c < nfg) cp_async16(stg + blk * FG + 2 * c, Y + ((size_t)blk * nh + jh) * ldc + 2 * f0 + 4 * c);
-        }
-      } else {
-        for (int blk = threadIdx.x; blk < nblk_v; blk += blockDim.x)
-          cp_async8(stg + blk * FG, Y + ((size_t)blk * nh + jh) * ldc + 2 * f0);
+  auto issue_Y = [&](int item) {   // spectra rows E_m, O_m of the item's fields -> stg[blk][FG]
+    if (item >= nitems) return;
+    int jh, f0, nfg;
+    item_geom(item, jh, f0, nfg);
+    if constexpr (FG % 2 == 0) {
+      constexpr int ch = FG / 2;
+      for (int e = threadIdx.x; e < nblk_v * ch; e += blockDim.x) {
+        const int blk = e / ch, c = e - blk * ch;
+        if (2 * c < nfg) cp_async16(stg + blk * FG + 2 * c, Y + ((size_t)blk * nh + jh) * ldc + 2 * f0 + 4 * c);
       }
-    }
-    cp_async_commit();
-  };
-  auto issue_M = [&](int item, const EpiField* F) {
-    if (item < nitems) {
-      int jh, f0, nfg;
-      item_geom(item, jh, f0, nfg);
-      const int j = jh, J = nlat - 1 - jh;
-      for (int q = 0; q < nfg; ++q) {
-        if (!F[q].live) continue;
-        for (int r = 0; r < 2; ++r) {
-          if (r == 1 && J == j) break;
-          const float* src = F[q].marg + (size_t)(r ? J : j) * nlon;
-          float* dst = mst + (2 * q + r) * N;
-          if (vec4 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
-            for (int k = threadIdx.x * 4; k < N; k += blockDim.x * 4) cp_async16(dst + k, src + k);
-          } else {
-            for (int k = threadIdx.x; k < N; k += blockDim.x) cp_async4(dst + k, src + k);
-          }
-        }
-      }
+    } else {
+      for (int blk = threadIdx.x; blk < nblk_v; blk += blockDim.x)
+        cp_async8(stg + blk * FG, Y + ((size_t)blk * nh + jh) * ldc + 2 * f0);
     }
     cp_async_commit();
   };
 
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
   int item = blockIdx.x, slot = 0;
   if (item < nitems) {
     int jh, f0, nfg;
@@ -288,13 +255,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft_p(
   }
   issue_Y(item);
   __syncthreads();
-  issue_M(item, fi[0]);
+  if (item < nitems) {
+    int jh, f0, nfg;
+    item_geom(item, jh, f0, nfg);
+    epi_prefetch_marginals<FG>(ep, fi[0], nfg, (size_t)jh * nlon, (size_t)(nlat - 1 - jh) * nlon,
+                               nlat - 1 - jh != jh, N);
+  }
   while (item < nitems) {
     const int next = item + gridDim.x;
     int jh, f0, nfg;
     item_geom(item, jh, f0, nfg);
     const int j = jh, J = nlat - 1 - jh;
-    cp_async_wait_one();   // this item's spectra (its marginals may still be in flight)
+    cp_async_wait_all();   // this item's spectra
     __syncthreads();
     const int nz = N - 2 * lmax - 1;   // the band lmax < m < N - lmax is zero
     for (int q = 0; q < nfg; ++q)
@@ -321,17 +293,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_idft_p(
       epi_fields_load<FG>(ep, fn, nn, fi[slot ^ 1]);
     }
     issue_Y(next);
-    const float2* z = fft_smem_plan<true, PL>(buf, b1, tw, pl, nfg);
+    const float2* z = fft_smem_plan<true, PL>(buf, b1, tw_g, pl, nfg);
     float2* other = (z == buf) ? b1 : buf;
-    cp_async_wait_one();   // this item's marginals (the next item's spectra may be in flight)
-    __syncthreads();
+    if (next < nitems) {   // fi[slot ^ 1] is visible after the transform's barriers
+      int jn, fn, nn;
+      item_geom(next, jn, fn, nn);
+      epi_prefetch_marginals<FG>(ep, fi[slot ^ 1], nn, (size_t)jn * nlon, (size_t)(nlat - 1 - jn) * nlon,
+                                 nlat - 1 - jn != jn, N);
+    }
     const float aj = a_ring[j];
     const bool two = (J != j);
     ring_pair_epilogue<FG, kThreads>(z, other, ld, N, nfg, f0, (size_t)nlat * nlon, (size_t)j * nlon,
-                                     (size_t)J * nlon, two, aj, nh, jh, ep, red, fi[slot], mst);
-    issue_M(next, fi[slot ^ 1]);   // the epilogue's reduction barrier follows its last marginal read
+                                     (size_t)J * nlon, two, aj, nh, jh, ep, red, fi[slot]);
     __syncthreads();
-    const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw, pl, nfg);
+    const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw_g, pl, nfg);
     unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc, ep.xsplit);
     item = next;
     slot ^= 1;
@@ -378,7 +353,7 @@ int launch_idft_p_t(const Grid& g, const float* Y, int ldc, int nf, const EpiPar
   SHOT_CUDA(cudaFuncSetAttribute(k_idft_p<FG, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int ngroups = (nf + FG - 1) / FG;
   const int nitems = ngroups * g.nh;
-  const int grid = nitems < 2 * g.num_sms ? nitems : 2 * g.num_sms;
+  const int grid = nitems < 3 * g.num_sms ? nitems : 3 * g.num_sms;
   ProfScope prof(PK_IDFT, st);
   count_launch();
   k_idft_p<FG, PL><<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, ep,
@@ -428,7 +403,7 @@ int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams&
   }
   // the solver's update half-steps: persistent kernel with the next item's inputs prefetched
   if (ep.mode == EPI_UPDATE && ep.xout && !g.idft_nonpersistent && nf >= 2 &&
-      idft_p_layout(2, g.nlon, g.lmax).total <= 113 * 1024) {
+      idft_p_layout(2, g.nlon, g.lmax).total <= 74 * 1024) {
     if (plan_is<Plan1440>(g.plan)) return launch_idft_p_t<2, Plan1440>(g, Y, ldc, nf, ep, st);
     if (plan_is<Plan1024>(g.plan)) return launch_idft_p_t<2, Plan1024>(g, Y, ldc, nf, ep, st);
     return launch_idft_p_t<2>(g, Y, ldc, nf, ep, st);

@@ -13,8 +13,6 @@
 //   EPI_CHECK   |u Kv - p| sums for the marginal error (L2 or L1, App. C.3)
 //   EPI_FINAL   u_true, v_true, the marginal error, m(pi) and the dual objective
 // Field f occupies out[f * fstride ...]; rings j and J start at rj and rJ within a field.
-// mstage (UPDATE only, optional): the marginal rows already staged in shared memory,
-// [field q][ring (j, J)][N], instead of being read from ep.marg.
 #pragma once
 #include "shot_internal.cuh"
 
@@ -78,8 +76,7 @@ template <int FG, int NT>
 __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* other, int ld, int N, int nfg, int f0,
                                                    size_t fstride, size_t rj, size_t rJ, bool two, float aj,
                                                    int nh, int jh, const EpiParams& ep,
-                                                   float (*red)[FG * NPART], const EpiField* fi,
-                                                   const float* mstage = nullptr) {
+                                                   float (*red)[FG * NPART], const EpiField* fi) {
   constexpr int kEpiBatch = 6;   // longitudes per thread whose marginal values are loaded together
   if (ep.mode == EPI_PLAIN) {
     for (int q = 0; q < nfg; ++q) {
@@ -127,13 +124,8 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
 #pragma unroll
         for (int b = 0; b < kEpiBatch; ++b) {
           const int k = k0 + b * NT;
-          if (mstage) {   // staged in shared memory: [q][ring][N]
-            pv[b][0] = (k < N) ? mstage[(2 * q) * N + k] : 0.f;
-            pv[b][1] = (k < N && two) ? mstage[(2 * q + 1) * N + k] : 0.f;
-          } else {
-            pv[b][0] = (k < N) ? __ldg(mg + rj + k) : 0.f;
-            pv[b][1] = (k < N && two) ? __ldg(mg + rJ + k) : 0.f;
-          }
+          pv[b][0] = (k < N) ? __ldg(mg + rj + k) : 0.f;
+          pv[b][1] = (k < N && two) ? __ldg(mg + rJ + k) : 0.f;
         }
 #pragma unroll
         for (int b = 0; b < kEpiBatch; ++b) {
