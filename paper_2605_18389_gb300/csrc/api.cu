@@ -665,8 +665,8 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     g->ana_transposed = (e && e[0] == '1') ? 1 : 0;
     e = getenv("SHOT_IDFT_PERSISTENT");   // 0: one item per CTA for the update half-steps too
     g->idft_nonpersistent = (e && e[0] == '0') ? 1 : 0;
-    e = getenv("SHOT_TC_STAGES");   // 1..3 fixes the analysis pipeline depth instead of the autotuner
-    g->tc_stages_override = (e && e[0] >= '1' && e[0] <= '3') ? e[0] - '0' : 0;
+    e = getenv("SHOT_TC_STAGES");   // 1..4 fixes the analysis pipeline depth instead of the autotuner
+    g->tc_stages_override = (e && e[0] >= '1' && e[0] <= '4') ? e[0] - '0' : 0;
   }
   g->plan = plan;
   cudaGetDevice(&g->dev);

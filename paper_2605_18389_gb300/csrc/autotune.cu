@@ -115,7 +115,7 @@ int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd) {
   if (!rc) rc = pick_vec(&t.dft_fg, fgs, run_fwd);
   if (!rc) rc = pick_vec(&t.idft_fg, fgs, run_inv);
   if (!rc && g.mode == SHOT_TABLE && g.precision == SHOT_FP32) rc = pick(&t.simt_bn, {32, 48, 64}, run_leg);
-  if (!rc && g.mode == SHOT_TABLE && g.precision == SHOT_BF16X3) rc = pick(&t.tc_stages, {1, 2, 3}, run_leg);
+  if (!rc && g.mode == SHOT_TABLE && g.precision == SHOT_BF16X3) rc = pick(&t.tc_stages, {2, 3, 4}, run_leg);
   cudaStreamSynchronize(st);
   cudaFree(fld);
   cudaEventDestroy(e0);

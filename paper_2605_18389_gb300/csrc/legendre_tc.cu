@@ -111,11 +111,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
   const int* Mr = ANA ? aa.M : sa.M;
   const int bbytes = ANA ? mn_atoms(nmma) * kXsBoxBytes : nmma * kBK * 2;
   const int xbytes = (ANA && !XS) ? nmma * kBK * 4 : 0;
+  // Analysis from FP32 spectra: the split B operand lives in its own ring of two buffers
+  // (released by the MMAs), so the TMA ring holds only what streams from memory (table tiles
+  // and the FP32 spectra tile) and can run one stage deeper in the same shared memory.
+  constexpr bool kBRing = ANA && !XS;
+  constexpr int nB = kBRing ? 2 : kStages;
   uint8_t* sA_hi = base;
   uint8_t* sA_lo = sA_hi + kStages * kATileBytes;
   uint8_t* sB_hi = sA_lo + kStages * kATileBytes;
-  uint8_t* sB_lo = sB_hi + kStages * bbytes;
-  uint8_t* sX = sB_lo + kStages * bbytes;
+  uint8_t* sB_lo = sB_hi + nB * bbytes;
+  uint8_t* sX = sB_lo + nB * bbytes;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t ncols_alloc = tmem_cols_for(nmma);
 
@@ -128,6 +133,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl.tfull[b], 1);
       mbar_init(&ctl.tempty[b], 128);
+      mbar_init(&ctl.bempty[b], 1);
     }
     ctl.abort = 0;
     fence_mbar_init();
@@ -197,12 +203,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
         const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
+          const int sb = kBRing ? (it & 1) : s;   // B buffer of this iteration
           ok = mbar_wait(&ctl.fullA[s], n & 1, abort);
-          if (ok && ANA && !XS) ok = mbar_wait(&ctl.fullB[s], n & 1, abort);
+          if (ok && kBRing) ok = mbar_wait(&ctl.fullB[sb], (it >> 1) & 1, abort);
           if (!ok) break;
           tc_fence_after();
           const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
-          const uint32_t bh = smem_u32(sB_hi + s * bbytes), bl = smem_u32(sB_lo + s * bbytes);
+          const uint32_t bh = smem_u32(sB_hi + sb * bbytes), bl = smem_u32(sB_lo + sb * bbytes);
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k) {
             const uint32_t off = k * 32;
@@ -227,6 +234,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
             umma_bf16(d, a_l, b_h, idesc, 1);
           }
           umma_commit(&ctl.empty[s]);
+          if (kBRing) umma_commit(&ctl.bempty[sb]);
         }
         umma_commit(&ctl.tfull[acc]);
       }
@@ -242,11 +250,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
         const int nkb = nkb_of(tl.blk);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
+          const int sb = it & 1;
           if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
+          // the MMAs of iteration it - 2 have finished reading this B buffer
+          if (it >= 2 && !(ok = mbar_wait(&ctl.bempty[sb], ((it >> 1) - 1) & 1, abort))) break;
           split_x_mn(reinterpret_cast<const float*>(sX + s * xbytes), nmma, aa.ncols, kb * kBK, nh,
-                     sB_hi + s * bbytes, sB_lo + s * bbytes, pt);
+                     sB_hi + sb * bbytes, sB_lo + sb * bbytes, pt);
           fence_async_smem();
-          mbar_arrive(&ctl.fullB[s]);
+          mbar_arrive(&ctl.fullB[sb]);
         }
       }
     }
@@ -875,8 +886,10 @@ __global__ void k_c_to_ct(int nblk, const int* __restrict__ Mrows, const long lo
 // with_x: analysis (MN-major B of mn_atoms(nmma) 8 KB atoms, plus the FP32 spectra tile);
 // otherwise synthesis (K-major B of nmma rows)
 size_t tc_smem_bytes(int nmma, bool with_x, int stages) {
-  const size_t b = with_x ? (size_t)mn_atoms(nmma) * kXsBoxBytes : (size_t)nmma * kBK * 2;
-  return 1024 + (size_t)stages * (2 * kATileBytes + 2 * b + (with_x ? nmma * kBK * 4 : 0));
+  if (with_x)   // analysis: table tiles and the FP32 spectra tile per stage, B in a ring of two
+    return 1024 + (size_t)stages * (2 * kATileBytes + (size_t)nmma * kBK * 4) +
+           2 * 2 * (size_t)mn_atoms(nmma) * kXsBoxBytes;
+  return 1024 + (size_t)stages * (2 * kATileBytes + 2 * (size_t)nmma * kBK * 2);
 }
 
 }  // namespace
@@ -948,7 +961,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     int stages = kStagesAna;
     if (g.active.nf == nf && g.active.tc_stages > 0) stages = g.active.tc_stages;
     if (g.tc_stages_override > 0) stages = g.tc_stages_override;
-    while (stages > 1 && tc_smem_bytes(nmma, true, stages) > 227 * 1024) --stages;
+    while (stages > 1 && tc_smem_bytes(nmma, true, stages) + 1024 > 227 * 1024) --stages;
     const size_t smem = tc_smem_bytes(nmma, true, stages);
     CUtensorMap mh, ml, mx;
     if ((rc = make_map(&mh, g.tab_hi, g.nh, g.rows_total, g.ldt, kBM))) return rc;
@@ -956,7 +969,10 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
     aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma,
                  apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4, colscale};
-    auto kern = stages == 3 ? k_legendre_tc<3, true> : stages == 2 ? k_legendre_tc<2, true> : k_legendre_tc<1, true>;
+    auto kern = stages == 4   ? k_legendre_tc<4, true>
+                : stages == 3 ? k_legendre_tc<3, true>
+                : stages == 2 ? k_legendre_tc<2, true>
+                              : k_legendre_tc<1, true>;
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: both shared memory and the 512 TMEM columns (two accumulators each) must fit
     const int per_sm = (smem <= 113 * 1024 && 2 * 2 * host_tmem_cols(nmma) <= 512) ? 2 : 1;

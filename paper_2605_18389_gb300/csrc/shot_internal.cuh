@@ -97,7 +97,7 @@ struct Tuning {
   int dft_fg = 0;      // fields per ring-DFT CTA (1, 2, 4, 8)
   int idft_fg = 0;     // fields per inverse-DFT CTA
   int simt_bn = 0;     // FP32 Legendre tile width (32, 48, 64)
-  int tc_stages = 0;   // BF16x3 analysis pipeline depth (1..3)
+  int tc_stages = 0;   // BF16x3 analysis pipeline depth (1..4)
 };
 
 struct Grid {

@@ -118,3 +118,27 @@ def test_bf16x3_divergence_matches_oracle(grid_cache, nlat, eps, tau, T, tol):
     ot_pq = ref["runs"]["ot"][:2]
     assert np.all(s_err_prec(r["S"], ref["S"], ot_pq, TOL, "bf16x3") <= 1.0)
     assert np.all(s_err_prec(r["S_dual"], ref["S_dual"], ot_pq, TOL, "bf16x3") <= 1.0)
+
+
+@pytest.mark.parametrize("nlat,nf", [(96, 24), (64, 40), (40, 64)])
+def test_bf16x3_analysis_pipeline_depths_agree(monkeypatch, nlat, nf):
+    """The tensor-core analysis at every pipeline depth (SHOT_TC_STAGES=1..4; the split spectra
+    operand in its own ring of two buffers) matches the oracle, and the depths agree bit for
+    bit: the K order of the accumulation does not depend on the depth.  Depths that do not fit
+    in shared memory for the field count fall back to the deepest one that does."""
+    og = OGrid(nlat)
+    f, f64 = f32(np.random.default_rng(nlat + 7 * nf).uniform(size=(nf, og.nlat, og.nlon)))
+    ref = osht.heat_apply(og, f64, 2e-3)
+    outs = []
+    for depth in ("1", "2", "3", "4"):
+        monkeypatch.setenv("SHOT_TC_STAGES", depth)
+        g = shot.shot_grid_init(nlat, None, -1, shot.SHOT_BF16X3)
+        try:
+            out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
+            shot.shot_heat_apply(g, 2e-3, torch.from_numpy(f).cuda(), out)
+            outs.append(out.cpu().numpy())
+        finally:
+            shot.shot_grid_free(g)
+    assert rel_max(outs[0], ref) < TOL
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
