@@ -27,30 +27,47 @@ __host__ __device__ constexpr int mn_atoms(int nmma) { return (nmma + 63) / 64; 
 // Splits the FP32 spectra tile xs[64 nodes][nmma] (TMA, row-major) into bf16 hi and lo in
 // the MN-major layout above.  One task = 8 consecutive columns of one node: one 16-byte
 // swizzled chunk of hi and one of lo.  Nodes past the block (jh0 + r >= nh) and columns
-// past the fields are zero.  64 threads (pt = 0..63).
+// past the fields are zero.  nt threads (pt = 0..nt-1); each loads two tasks before it
+// stores either, so the shared-memory loads overlap.
 __device__ __forceinline__ void split_x_mn(const float* xs, int nmma, int ncols, int jh0, int nh, uint8_t* bh,
-                                           uint8_t* bl, int pt) {
+                                           uint8_t* bl, int pt, int nt = 64) {
   const int ch = nmma >> 3;
-  for (int e = pt; e < 64 * ch; e += 64) {
-    const int r = e / ch, c0 = (e - r * ch) * 8;
-    const float4 a = *reinterpret_cast<const float4*>(xs + r * nmma + c0);
-    const float4 b = *reinterpret_cast<const float4*>(xs + r * nmma + c0 + 4);
-    float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    const bool row_ok = jh0 + r < nh;
-    uint32_t hw[4], lw[4];
+  const int ntask = 64 * ch;
+  for (int e0 = pt; e0 < ntask; e0 += 2 * nt) {
+    float4 ld[2][2];
 #pragma unroll
-    for (int q = 0; q < 8; q += 2) {
-      const float v0 = (row_ok && c0 + q < ncols) ? v[q] : 0.f;
-      const float v1 = (row_ok && c0 + q + 1 < ncols) ? v[q + 1] : 0.f;
-      const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
-      const float2 hf = __bfloat1622float2(h2);
-      const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
-      hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
-      lw[q / 2] = *reinterpret_cast<const uint32_t*>(&l2);
+    for (int i = 0; i < 2; ++i) {
+      const int e = e0 + i * nt;
+      if (e < ntask) {
+        const int r = e / ch, c0 = (e - r * ch) * 8;
+        ld[i][0] = *reinterpret_cast<const float4*>(xs + r * nmma + c0);
+        ld[i][1] = *reinterpret_cast<const float4*>(xs + r * nmma + c0 + 4);
+      }
     }
-    const uint32_t o = (uint32_t)((c0 >> 6) * (64 * 64 * 2)) + sw128_offset(r, c0 & 63);
-    *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-    *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int e = e0 + i * nt;
+      if (e >= ntask) break;
+      const int r = e / ch, c0 = (e - r * ch) * 8;
+      const float4 a = ld[i][0];
+      const float4 b = ld[i][1];
+      float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+      const bool row_ok = jh0 + r < nh;
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int q = 0; q < 8; q += 2) {
+        const float v0 = (row_ok && c0 + q < ncols) ? v[q] : 0.f;
+        const float v1 = (row_ok && c0 + q + 1 < ncols) ? v[q + 1] : 0.f;
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h2);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+        lw[q / 2] = *reinterpret_cast<const uint32_t*>(&l2);
+      }
+      const uint32_t o = (uint32_t)((c0 >> 6) * (64 * 64 * 2)) + sw128_offset(r, c0 & 63);
+      *reinterpret_cast<uint4*>(bh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>(bl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
   }
 }
 
@@ -91,8 +108,15 @@ struct SynArgs {
 // are idle.
 constexpr int kXsBoxBytes = 64 * 64 * 2;
 
+// Analysis from FP32 spectra runs six converter warps (2-7) and its epilogue on warps 8-11
+// (384 threads); the other forms keep two converter slots (2-3) and warps 4-7 (256 threads).
+template <bool ANA, bool XS>
+__host__ __device__ constexpr int tc_conv_warps() { return (ANA && !XS) ? 6 : 2; }
+template <bool ANA, bool XS>
+__host__ __device__ constexpr int tc_threads() { return 32 * (4 + tc_conv_warps<ANA, XS>()); }
+
 template <int kStages, bool ANA, bool XS = false>
-__global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_constant__ CUtensorMap ta_hi,
+__global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const __grid_constant__ CUtensorMap ta_hi,
                                                                const __grid_constant__ CUtensorMap ta_lo,
                                                                const __grid_constant__ CUtensorMap tb_hi,
                                                                const __grid_constant__ CUtensorMap tb_lo,
@@ -124,10 +148,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t ncols_alloc = tmem_cols_for(nmma);
 
+  constexpr int kConv = 32 * tc_conv_warps<ANA, XS>();   // converter threads
+  constexpr int kEpiWarp0 = 2 + tc_conv_warps<ANA, XS>();
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl.fullA[s], 1);
-      mbar_init(&ctl.fullB[s], 64);
+      mbar_init(&ctl.fullB[s], kConv);
       mbar_init(&ctl.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -239,7 +265,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
         umma_commit(&ctl.tfull[acc]);
       }
     }
-  } else if (warp < 4) {
+  } else if (warp < kEpiWarp0) {
     if (ANA && !XS) {
       // split the FP32 X tile (TMA, with the table tiles) into bf16 hi/lo, MN-major [jh][c]
       const int pt = threadIdx.x - 64;
@@ -255,7 +281,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
           // the MMAs of iteration it - 2 have finished reading this B buffer
           if (it >= 2 && !(ok = mbar_wait(&ctl.bempty[sb], ((it >> 1) - 1) & 1, abort))) break;
           split_x_mn(reinterpret_cast<const float*>(sX + s * xbytes), nmma, aa.ncols, kb * kBK, nh,
-                     sB_hi + sb * bbytes, sB_lo + sb * bbytes, pt);
+                     sB_hi + sb * bbytes, sB_lo + sb * bbytes, pt, kConv);
           fence_async_smem();
           mbar_arrive(&ctl.fullB[sb]);
         }
@@ -263,7 +289,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_legendre_tc(const __grid_cons
     }
   } else {
     // epilogue: drain the accumulator of every tile of this CTA
-    const int q = warp - 4;   // TMEM lane quadrant
+    const int q = warp - kEpiWarp0;   // TMEM lane quadrant (warp % 4)
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const Tile tl = tiles[t];
@@ -979,7 +1005,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     const int grid = g.ntiles_ana < per_sm * g.num_sms ? g.ntiles_ana : per_sm * g.num_sms;
     ProfScope prof(PK_ANALYSIS, st);
     count_launch();
-    kern<<<grid, kTcThreads, smem, st>>>(mh, ml, mx, mx, aa, sa);
+    kern<<<grid, tc_threads<true, false>(), smem, st>>>(mh, ml, mx, mx, aa, sa);
     SHOT_CUDA(cudaGetLastError());
   }
   if (syn) {
