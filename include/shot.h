@@ -142,12 +142,24 @@ int shot_grid_nodes(shot_grid g, double* x, double* w, double* a_ring);
 /* Pre-size the workspace for calls on up to `nfields` fields (optional; calls grow it). */
 int shot_grid_reserve(shot_grid g, int nfields);
 
+/* Device-side status of the asynchronous calls on this grid.  Every wait inside the
+ * tensor-core kernels is bounded (about 0.5 s of SM clock); one that expires makes its CTA
+ * stop, release its tensor memory and raise a flag in the grid's workspace.  The solver
+ * entry points (shot_sinkhorn, shot_divergence, shot_divergence_grad) read the flag
+ * themselves; the asynchronous transforms (shot_heat_apply, shot_sht_analysis,
+ * shot_sht_synthesis) cannot without synchronising, so their caller checks here:
+ * synchronises `stream`, returns SHOT_ERR_TIMEOUT if the flag is set (and clears it), else
+ * SHOT_OK.  Not part of the paper's method: a check on the device path.
+ * Errors: INVALID_ARG (NULL grid), CUDA, TIMEOUT. */
+int shot_grid_check(shot_grid g, void* stream);
+
 /* Heat convolution, Sec. 3.2: out = HeatConv(in; h), h_l = exp(-t l(l+1)), for
  * nfields fields:  ring real-DFT -> per-order Legendre analysis with area weights ->
  * scaling by h_l -> Legendre synthesis -> inverse ring DFT.
  *   in, out   device [nfields][nlat][nlon] float32 (may not alias)
  *   t >= 0    heat time (Alg. 1 uses t = eps/4)
- * Asynchronous on `stream`.  Errors: INVALID_ARG, OOM, CUDA. */
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, OOM, CUDA; a device-side timeout is
+ * reported by shot_grid_check. */
 int shot_heat_apply(shot_grid g, double t, const float* in, float* out, int nfields, void* stream);
 
 /* Spherical harmonic analysis (App. B: c_lm = <f, Y_lm> by GL quadrature) of nfields

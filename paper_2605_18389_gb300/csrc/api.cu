@@ -787,6 +787,22 @@ int shot_grid_reserve(shot_grid gh, int nfields) {
   return ensure_workspace(*g, nfields, 0);
 }
 
+int shot_grid_check(shot_grid gh, void* stream) {
+  Grid* g = as_grid(gh);
+  if (!g) { set_error("shot_grid_check: bad grid"); return SHOT_ERR_INVALID_ARG; }
+  cudaStream_t st = as_stream(stream);
+  SHOT_CUDA(cudaStreamSynchronize(st));
+  if (!g->ws.dev_int) return SHOT_OK;   // nothing has run on this grid yet
+  int flag = 0;
+  SHOT_CUDA(cudaMemcpy(&flag, g->ws.dev_int + 4, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    SHOT_CUDA(cudaMemset(g->ws.dev_int + 4, 0, sizeof(int)));
+    set_error("a bounded device-side wait expired in a tensor-core kernel");
+    return SHOT_ERR_TIMEOUT;
+  }
+  return SHOT_OK;
+}
+
 int shot_heat_apply(shot_grid gh, double t, const float* in, float* out, int nfields, void* stream) {
   Grid* g = as_grid(gh);
   if (!g || !in || !out || nfields < 1 || !(t >= 0.0) || in == out) {

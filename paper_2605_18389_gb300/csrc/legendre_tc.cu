@@ -113,7 +113,8 @@ constexpr int kXsBoxBytes = 64 * 64 * 2;
 template <bool ANA, bool XS>
 __host__ __device__ constexpr int tc_conv_warps() { return (ANA && !XS) ? 6 : 2; }
 template <bool ANA, bool XS>
-__host__ __device__ constexpr int tc_threads() { return 32 * (4 + tc_conv_warps<ANA, XS>()); }
+__host__ __device__ constexpr int tc_threads() { return 32 * (2 + tc_conv_warps<ANA, XS>() + 4); }
+static_assert(tc_threads<true, false>() == 384 && tc_threads<false, false>() == kTcThreads, "warp roles");
 
 template <int kStages, bool ANA, bool XS = false>
 __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const __grid_constant__ CUtensorMap ta_hi,
@@ -153,9 +154,9 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl.fullA[s], 1);
-      mbar_init(&ctl.fullB[s], kConv);
       mbar_init(&ctl.empty[s], 1);
     }
+    for (int s = 0; s < (kStages > nB ? kStages : nB); ++s) mbar_init(&ctl.fullB[s], kConv);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl.tfull[b], 1);
       mbar_init(&ctl.tempty[b], 128);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "shot_grid_info": [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p],
     "shot_grid_nodes": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
     "shot_grid_reserve": [_vp, ctypes.c_int],
+    "shot_grid_check": [_vp, _vp],
     "shot_heat_apply": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
     "shot_sht_analysis": [_vp, _vp, _vp, ctypes.c_int, _vp],
     "shot_sht_synthesis": [_vp, _vp, _vp, ctypes.c_int, _vp],
@@ -231,6 +232,12 @@ def shot_grid_nodes(g):
 
 def shot_grid_reserve(g, nfields):
     return _check(lib().shot_grid_reserve(g, nfields))
+
+
+def shot_grid_check(g, stream=None):
+    """Synchronises the stream; raises ShotError(SHOT_ERR_TIMEOUT) if a bounded device-side
+    wait expired in a kernel on this grid since the last check."""
+    return _check(lib().shot_grid_check(g, _stream(stream)))
 
 
 def shot_heat_apply(g, t, inp, out, stream=None):

@@ -46,6 +46,7 @@ def test_bf16x3_analysis_matches_oracle(grid_cache, nlat, nlon, lmax, nf):
     f, f64 = f32(np.random.default_rng(nlat + nf).normal(size=(nf, og.nlat, og.nlon)))
     c = torch.empty((nf, L, L, 2), device="cuda")
     shot.shot_sht_analysis(g, torch.from_numpy(f).cuda(), c)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
     got = c.cpu().numpy()
     ref = osht.analysis(og, f64)
     assert rel_max(got[..., 0], ref.real) < TOL
@@ -64,6 +65,7 @@ def test_bf16x3_synthesis_matches_oracle(grid_cache, nlat, nlon, lmax, nf):
     c[:, :, 0, 1] = 0
     out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
     shot.shot_sht_synthesis(g, torch.from_numpy(c).cuda(), out)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
     ref = osht.synthesis(og, c[..., 0].astype(np.float64) + 1j * c[..., 1].astype(np.float64))
     assert rel_max(out.cpu().numpy(), ref) < TOL
 
@@ -74,6 +76,7 @@ def test_bf16x3_heat_apply_matches_oracle(grid_cache, nlat, nf, t):
     f, f64 = f32(np.random.default_rng(nlat).uniform(size=(nf, og.nlat, og.nlon)))
     out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
     shot.shot_heat_apply(g, t, torch.from_numpy(f).cuda(), out)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
     assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, t)) < TOL
 
 
@@ -83,6 +86,7 @@ def test_bf16x3_heat_apply_720_full_size(grid_cache):
     f, f64 = f32(np.random.default_rng(7200).uniform(size=(nf, 720, 1440)))
     out = torch.empty((nf, 720, 1440), device="cuda")
     shot.shot_heat_apply(g, 1e-4, torch.from_numpy(f).cuda(), out)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
     got = out.cpu().numpy()
     ref = osht.heat_apply(og, f64[:3], 1e-4)   # the oracle on a sample of the batch
     assert rel_max(got[:3], ref) < TOL
@@ -136,6 +140,7 @@ def test_bf16x3_analysis_pipeline_depths_agree(monkeypatch, nlat, nf):
         try:
             out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
             shot.shot_heat_apply(g, 2e-3, torch.from_numpy(f).cuda(), out)
+            shot.shot_grid_check(g)   # no bounded device-side wait expired
             outs.append(out.cpu().numpy())
         finally:
             shot.shot_grid_free(g)

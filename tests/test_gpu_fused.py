@@ -36,6 +36,7 @@ def test_fused_heat_apply_matches_oracle(monkeypatch, nlat, nlon, lmax, nf, t):
     f, f64 = f32(np.random.default_rng(17 * nlat + nf).uniform(size=(nf, og.nlat, og.nlon)))
     out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
     shot.shot_heat_apply(g, t, torch.from_numpy(f).cuda(), out)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
     shot.shot_grid_free(g)
     assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, t)) < TOL
 
@@ -49,6 +50,7 @@ def test_fused_agrees_with_two_kernel_path(monkeypatch, nlat, nf):
         g = _grid(monkeypatch, fused, nlat)
         out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
         shot.shot_heat_apply(g, 2e-3, torch.from_numpy(f).cuda(), out)
+        shot.shot_grid_check(g)   # no bounded device-side wait expired
         shot.shot_grid_free(g)
         outs.append(out.cpu().numpy())
     # same products and the same accumulation order per tile: agreement far below the tolerance
@@ -61,6 +63,7 @@ def test_fused_cc_grid(monkeypatch):
     f, f64 = f32(np.random.default_rng(5).uniform(size=(4, 33, 72)))
     out = torch.empty((4, 33, 72), device="cuda")
     shot.shot_heat_apply(g, 0.01, torch.from_numpy(f).cuda(), out)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
     shot.shot_grid_free(g)
     assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, 0.01)) < TOL
 
@@ -87,6 +90,7 @@ def test_fused_720_full_size(monkeypatch):
     f, f64 = f32(np.random.default_rng(720).uniform(size=(3, 720, 1440)))
     out = torch.empty((3, 720, 1440), device="cuda")
     shot.shot_heat_apply(g, 1e-4, torch.from_numpy(f).cuda(), out)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
     shot.shot_grid_free(g)
     assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, 1e-4)) < TOL
 
@@ -118,6 +122,7 @@ def test_transposed_analysis_matches_oracle(monkeypatch, nlat, nf):
     f, f64 = f32(np.random.default_rng(nlat * 3).uniform(size=(nf, og.nlat, og.nlon)))
     out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
     shot.shot_heat_apply(g, 3e-3, torch.from_numpy(f).cuda(), out)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
     p, q = inputs.pairs("paper_uniform", 9000 + nlat, 2, og.x, og.nlon, og.a_ring)
     p32, p64 = f32(p)
     q32, q64 = f32(q)
