@@ -136,11 +136,12 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
   const int* Mr = ANA ? aa.M : sa.M;
   const int bbytes = ANA ? mn_atoms(nmma) * kXsBoxBytes : nmma * kBK * 2;
   const int xbytes = (ANA && !XS) ? nmma * kBK * 4 : 0;
-  // Analysis from FP32 spectra: the split B operand lives in its own ring of two buffers
-  // (released by the MMAs), so the TMA ring holds only what streams from memory (table tiles
-  // and the FP32 spectra tile) and can run one stage deeper in the same shared memory.
+  // Analysis from FP32 spectra: the split B operand lives in its own ring of kBRingDepth
+  // buffers (released by the MMAs), so the TMA ring holds only what streams from memory
+  // (table tiles and the FP32 spectra tile) and can run one stage deeper in the same shared
+  // memory.
   constexpr bool kBRing = ANA && !XS;
-  constexpr int nB = kBRing ? 2 : kStages;
+  constexpr int nB = kBRing ? kBRingDepth : kStages;
   uint8_t* sA_hi = base;
   uint8_t* sA_lo = sA_hi + kStages * kATileBytes;
   uint8_t* sB_hi = sA_lo + kStages * kATileBytes;
@@ -160,8 +161,8 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl.tfull[b], 1);
       mbar_init(&ctl.tempty[b], 128);
-      mbar_init(&ctl.bempty[b], 1);
     }
+    for (int b = 0; b < kBRingDepth; ++b) mbar_init(&ctl.bempty[b], 1);
     ctl.abort = 0;
     fence_mbar_init();
   }
@@ -230,9 +231,9 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
         const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
-          const int sb = kBRing ? (it & 1) : s;   // B buffer of this iteration
+          const int sb = kBRing ? (it % kBRingDepth) : s;   // B buffer of this iteration
           ok = mbar_wait(&ctl.fullA[s], n & 1, abort);
-          if (ok && kBRing) ok = mbar_wait(&ctl.fullB[sb], (it >> 1) & 1, abort);
+          if (ok && kBRing) ok = mbar_wait(&ctl.fullB[sb], (it / kBRingDepth) & 1, abort);
           if (!ok) break;
           tc_fence_after();
           const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
@@ -277,10 +278,10 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
         const int nkb = nkb_of(tl.blk);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
-          const int sb = it & 1;
+          const int sb = it % kBRingDepth, nb = it / kBRingDepth;
           if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
-          // the MMAs of iteration it - 2 have finished reading this B buffer
-          if (it >= 2 && !(ok = mbar_wait(&ctl.bempty[sb], ((it >> 1) - 1) & 1, abort))) break;
+          // the MMAs of iteration it - kBRingDepth have finished reading this B buffer
+          if (nb > 0 && !(ok = mbar_wait(&ctl.bempty[sb], (nb - 1) & 1, abort))) break;
           split_x_mn(reinterpret_cast<const float*>(sX + s * xbytes), nmma, aa.ncols, kb * kBK, nh,
                      sB_hi + sb * bbytes, sB_lo + sb * bbytes, pt, kConv);
           fence_async_smem();
@@ -913,9 +914,9 @@ __global__ void k_c_to_ct(int nblk, const int* __restrict__ Mrows, const long lo
 // with_x: analysis (MN-major B of mn_atoms(nmma) 8 KB atoms, plus the FP32 spectra tile);
 // otherwise synthesis (K-major B of nmma rows)
 size_t tc_smem_bytes(int nmma, bool with_x, int stages) {
-  if (with_x)   // analysis: table tiles and the FP32 spectra tile per stage, B in a ring of two
+  if (with_x)   // analysis: table tiles and the FP32 spectra tile per stage, B in its own ring
     return 1024 + (size_t)stages * (2 * kATileBytes + (size_t)nmma * kBK * 4) +
-           2 * 2 * (size_t)mn_atoms(nmma) * kXsBoxBytes;
+           kBRingDepth * 2 * (size_t)mn_atoms(nmma) * kXsBoxBytes;
   return 1024 + (size_t)stages * (2 * kATileBytes + 2 * (size_t)nmma * kBK * 2);
 }
 
