@@ -116,7 +116,7 @@ template <bool ANA, bool XS>
 __host__ __device__ constexpr int tc_threads() { return 32 * (2 + tc_conv_warps<ANA, XS>() + 4); }
 static_assert(tc_threads<true, false>() == 384 && tc_threads<false, false>() == kTcThreads, "warp roles");
 
-template <int kStages, bool ANA, bool XS = false>
+template <int kStages, bool ANA, bool XS = false, int kBR = 2>
 __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const __grid_constant__ CUtensorMap ta_hi,
                                                                const __grid_constant__ CUtensorMap ta_lo,
                                                                const __grid_constant__ CUtensorMap tb_hi,
@@ -136,12 +136,12 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
   const int* Mr = ANA ? aa.M : sa.M;
   const int bbytes = ANA ? mn_atoms(nmma) * kXsBoxBytes : nmma * kBK * 2;
   const int xbytes = (ANA && !XS) ? nmma * kBK * 4 : 0;
-  // Analysis from FP32 spectra: the split B operand lives in its own ring of kBRingDepth
+  // Analysis from FP32 spectra: the split B operand lives in its own ring of kBR
   // buffers (released by the MMAs), so the TMA ring holds only what streams from memory
   // (table tiles and the FP32 spectra tile) and can run one stage deeper in the same shared
   // memory.
   constexpr bool kBRing = ANA && !XS;
-  constexpr int nB = kBRing ? kBRingDepth : kStages;
+  constexpr int nB = kBRing ? kBR : kStages;
   uint8_t* sA_hi = base;
   uint8_t* sA_lo = sA_hi + kStages * kATileBytes;
   uint8_t* sB_hi = sA_lo + kStages * kATileBytes;
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
       mbar_init(&ctl.tfull[b], 1);
       mbar_init(&ctl.tempty[b], 128);
     }
-    for (int b = 0; b < kBRingDepth; ++b) mbar_init(&ctl.bempty[b], 1);
+    for (int b = 0; b < kBR; ++b) mbar_init(&ctl.bempty[b], 1);
     ctl.abort = 0;
     fence_mbar_init();
   }
@@ -231,9 +231,9 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
         const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
-          const int sb = kBRing ? (it % kBRingDepth) : s;   // B buffer of this iteration
+          const int sb = kBRing ? (it % kBR) : s;   // B buffer of this iteration
           ok = mbar_wait(&ctl.fullA[s], n & 1, abort);
-          if (ok && kBRing) ok = mbar_wait(&ctl.fullB[sb], (it / kBRingDepth) & 1, abort);
+          if (ok && kBRing) ok = mbar_wait(&ctl.fullB[sb], (it / kBR) & 1, abort);
           if (!ok) break;
           tc_fence_after();
           const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
@@ -278,9 +278,9 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
         const int nkb = nkb_of(tl.blk);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
-          const int sb = it % kBRingDepth, nb = it / kBRingDepth;
+          const int sb = it % kBR, nb = it / kBR;
           if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
-          // the MMAs of iteration it - kBRingDepth have finished reading this B buffer
+          // the MMAs of iteration it - kBR have finished reading this B buffer
           if (nb > 0 && !(ok = mbar_wait(&ctl.bempty[sb], (nb - 1) & 1, abort))) break;
           split_x_mn(reinterpret_cast<const float*>(sX + s * xbytes), nmma, aa.ncols, kb * kBK, nh,
                      sB_hi + sb * bbytes, sB_lo + sb * bbytes, pt, kConv);
@@ -913,10 +913,10 @@ __global__ void k_c_to_ct(int nblk, const int* __restrict__ Mrows, const long lo
 
 // with_x: analysis (MN-major B of mn_atoms(nmma) 8 KB atoms, plus the FP32 spectra tile);
 // otherwise synthesis (K-major B of nmma rows)
-size_t tc_smem_bytes(int nmma, bool with_x, int stages) {
-  if (with_x)   // analysis: table tiles and the FP32 spectra tile per stage, B in its own ring
+size_t tc_smem_bytes(int nmma, bool with_x, int stages, int br = 2) {
+  if (with_x)   // analysis: table tiles and the FP32 spectra tile per stage, B in a ring of br buffers
     return 1024 + (size_t)stages * (2 * kATileBytes + (size_t)nmma * kBK * 4) +
-           kBRingDepth * 2 * (size_t)mn_atoms(nmma) * kXsBoxBytes;
+           (size_t)br * 2 * (size_t)mn_atoms(nmma) * kXsBoxBytes;
   return 1024 + (size_t)stages * (2 * kATileBytes + 2 * (size_t)nmma * kBK * 2);
 }
 
@@ -989,18 +989,24 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     int stages = kStagesAna;
     if (g.active.nf == nf && g.active.tc_stages > 0) stages = g.active.tc_stages;
     if (g.tc_stages_override > 0) stages = g.tc_stages_override;
-    while (stages > 1 && tc_smem_bytes(nmma, true, stages) + 1024 > 227 * 1024) --stages;
-    const size_t smem = tc_smem_bytes(nmma, true, stages);
+    // split spectra ring: three buffers when they fit beside at least two TMA stages
+    const int br = (tc_smem_bytes(nmma, true, 2, 3) + 1024 <= 227 * 1024) ? 3 : 2;
+    while (stages > 1 && tc_smem_bytes(nmma, true, stages, br) + 1024 > 227 * 1024) --stages;
+    const size_t smem = tc_smem_bytes(nmma, true, stages, br);
     CUtensorMap mh, ml, mx;
     if ((rc = make_map(&mh, g.tab_hi, g.nh, g.rows_total, g.ldt, kBM))) return rc;
     if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kBM))) return rc;
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
     aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma,
                  apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4, colscale};
-    auto kern = stages == 4   ? k_legendre_tc<4, true>
-                : stages == 3 ? k_legendre_tc<3, true>
-                : stages == 2 ? k_legendre_tc<2, true>
-                              : k_legendre_tc<1, true>;
+    auto kern = br == 3 ? (stages == 4   ? k_legendre_tc<4, true, false, 3>
+                           : stages == 3 ? k_legendre_tc<3, true, false, 3>
+                           : stages == 2 ? k_legendre_tc<2, true, false, 3>
+                                         : k_legendre_tc<1, true, false, 3>)
+                        : (stages == 4   ? k_legendre_tc<4, true, false, 2>
+                           : stages == 3 ? k_legendre_tc<3, true, false, 2>
+                           : stages == 2 ? k_legendre_tc<2, true, false, 2>
+                                         : k_legendre_tc<1, true, false, 2>);
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: both shared memory and the 512 TMEM columns (two accumulators each) must fit
     const int per_sm = (smem <= 113 * 1024 && 2 * 2 * host_tmem_cols(nmma) <= 512) ? 2 : 1;

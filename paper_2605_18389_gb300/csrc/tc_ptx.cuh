@@ -17,7 +17,6 @@ constexpr int kBM = 128;          // MMA M
 constexpr int kBK = 64;           // K elements per pipeline stage (one 128-byte swizzle row)
 constexpr int kMaxStages = 4;
 constexpr int kStagesAna = 4;   // one CTA per SM (table + X tiles per stage, B in its own ring)
-constexpr int kBRingDepth = 3;  // split spectra operand buffers of the analysis
 constexpr int kStagesSyn = 2;   // two CTAs per SM
 // Every wait is bounded by the SM clock: after ~2^30 cycles (~0.5 s at 2 GHz) it gives up.
 constexpr long long kWaitCycles = 1LL << 30;
@@ -184,7 +183,7 @@ struct TcSmem {
   uint64_t empty[kMaxStages];
   uint64_t tfull[2];    // accumulator buffer ready for the epilogue
   uint64_t tempty[2];   // accumulator buffer drained by the epilogue
-  uint64_t bempty[4];   // analysis B buffer read by the MMAs (B ring)
+  uint64_t bempty[3];   // analysis B buffer read by the MMAs (B ring of up to three)
   uint32_t tmem;
   int abort;
 };
