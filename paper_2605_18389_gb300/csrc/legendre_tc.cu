@@ -116,7 +116,7 @@ template <bool ANA, bool XS>
 __host__ __device__ constexpr int tc_threads() { return 32 * (2 + tc_conv_warps<ANA, XS>() + 4); }
 static_assert(tc_threads<true, false>() == 384 && tc_threads<false, false>() == kTcThreads, "warp roles");
 
-template <int kStages, bool ANA, bool XS = false, int kBR = 2>
+template <int kStages, bool ANA, bool XS = false, int kBR = 2, bool BCAT = false>
 __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const __grid_constant__ CUtensorMap ta_hi,
                                                                const __grid_constant__ CUtensorMap ta_lo,
                                                                const __grid_constant__ CUtensorMap tb_hi,
@@ -140,15 +140,27 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
   // buffers (released by the MMAs), so the TMA ring holds only what streams from memory
   // (table tiles and the FP32 spectra tile) and can run one stage deeper in the same shared
   // memory.
+  // Each ring buffer holds the hi atoms followed by the lo atoms, so that for up to 128
+  // columns (BCAT) [B_hi | B_lo] is one MN-major operand of N = 2 x 64 x atoms: a K step is
+  // then A_hi [B_hi | B_lo] + A_lo B_hi, two MMAs instead of three (the A tile is read from
+  // shared memory twice instead of three times), and the epilogue adds the accumulator's
+  // second half.  Pad columns of the atoms stay zero.
   constexpr bool kBRing = ANA && !XS;
   constexpr int nB = kBRing ? kBR : kStages;
+  const int bstride = kBRing ? 2 * bbytes : bbytes;   // between the B buffers
   uint8_t* sA_hi = base;
   uint8_t* sA_lo = sA_hi + kStages * kATileBytes;
   uint8_t* sB_hi = sA_lo + kStages * kATileBytes;
-  uint8_t* sB_lo = sB_hi + nB * bbytes;
-  uint8_t* sX = sB_lo + nB * bbytes;
+  uint8_t* sB_lo = kBRing ? sB_hi + bbytes : sB_hi + nB * bbytes;
+  uint8_t* sX = sB_hi + 2 * nB * bbytes;
+  const int ncat = 2 * 64 * mn_atoms(nmma);   // N of [B_hi | B_lo] (BCAT)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t ncols_alloc = tmem_cols_for(nmma);
+  const uint32_t ncols_alloc = tmem_cols_for(BCAT ? ncat : nmma);
+  if (kBRing) {   // the atoms' pad columns are never written by the converter: zero them once
+    for (int o = threadIdx.x * 16; o < 2 * nB * bbytes; o += blockDim.x * 16)
+      *reinterpret_cast<uint4*>(sB_hi + o) = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
+  }
 
   constexpr int kConv = 32 * tc_conv_warps<ANA, XS>();   // converter threads
   constexpr int kEpiWarp0 = 2 + tc_conv_warps<ANA, XS>();
@@ -220,6 +232,7 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
       // analysis: A (table) K-major, B (spectra) MN-major; synthesis: A (table) MN-major,
       // B (C^T) K-major
       const uint32_t idesc = ANA ? (idesc_bf16(kBM, nmma) | (1u << 16)) : idesc_bf16_amn(kBM, nmma);
+      const uint32_t idesc_cat = idesc_bf16(kBM, BCAT ? ncat : nmma) | (1u << 16);
       int it = 0, lt = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
@@ -237,7 +250,7 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
           if (!ok) break;
           tc_fence_after();
           const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
-          const uint32_t bh = smem_u32(sB_hi + sb * bbytes), bl = smem_u32(sB_lo + sb * bbytes);
+          const uint32_t bh = smem_u32(sB_hi + sb * bstride), bl = smem_u32(sB_lo + sb * bstride);
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k) {
             const uint32_t off = k * 32;
@@ -257,9 +270,14 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
               a_h = desc_sw128_mnmajor(ah + k * 2048, kATileBytes / 2, 1024);
               a_l = desc_sw128_mnmajor(al + k * 2048, kATileBytes / 2, 1024);
             }
-            umma_bf16(d, a_h, b_h, idesc, (kb | k) != 0);
-            umma_bf16(d, a_h, b_l, idesc, 1);
-            umma_bf16(d, a_l, b_h, idesc, 1);
+            if constexpr (BCAT) {   // b_h starts [B_hi | B_lo]
+              umma_bf16(d, a_h, b_h, idesc_cat, (kb | k) != 0);
+              umma_bf16(d, a_l, b_h, idesc, 1);
+            } else {
+              umma_bf16(d, a_h, b_h, idesc, (kb | k) != 0);
+              umma_bf16(d, a_h, b_l, idesc, 1);
+              umma_bf16(d, a_l, b_h, idesc, 1);
+            }
           }
           umma_commit(&ctl.empty[s]);
           if (kBRing) umma_commit(&ctl.bempty[sb]);
@@ -283,7 +301,7 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
           // the MMAs of iteration it - kBR have finished reading this B buffer
           if (nb > 0 && !(ok = mbar_wait(&ctl.bempty[sb], (nb - 1) & 1, abort))) break;
           split_x_mn(reinterpret_cast<const float*>(sX + s * xbytes), nmma, aa.ncols, kb * kBK, nh,
-                     sB_hi + sb * bbytes, sB_lo + sb * bbytes, pt, kConv);
+                     sB_hi + sb * bstride, sB_lo + sb * bstride, pt, kConv);
           fence_async_smem();
           mbar_arrive(&ctl.fullB[sb]);
         }
@@ -308,6 +326,12 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
         for (int c0 = 0; c0 < nmma; c0 += 16) {
           float v[16];
           tmem_ld16(d + (uint32_t)c0, v);
+          if constexpr (BCAT) {   // + A_hi B_lo from the second half
+            float w[16];
+            tmem_ld16(d + (uint32_t)(ncat / 2 + c0), w);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) v[e] += w[e];
+          }
           if (row < M) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -999,17 +1023,28 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
     aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma,
                  apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4, colscale};
-    auto kern = br == 3 ? (stages == 4   ? k_legendre_tc<4, true, false, 3>
-                           : stages == 3 ? k_legendre_tc<3, true, false, 3>
-                           : stages == 2 ? k_legendre_tc<2, true, false, 3>
-                                         : k_legendre_tc<1, true, false, 3>)
-                        : (stages == 4   ? k_legendre_tc<4, true, false, 2>
-                           : stages == 3 ? k_legendre_tc<3, true, false, 2>
-                           : stages == 2 ? k_legendre_tc<2, true, false, 2>
-                                         : k_legendre_tc<1, true, false, 2>);
+    // [B_hi | B_lo] as one operand up to 128 columns (N = 2 x 64 x atoms <= 256)
+    const bool bcat = 2 * 64 * mn_atoms(nmma) <= 256;
+    auto kern = bcat ? (br == 3 ? (stages == 4   ? k_legendre_tc<4, true, false, 3, true>
+                                   : stages == 3 ? k_legendre_tc<3, true, false, 3, true>
+                                   : stages == 2 ? k_legendre_tc<2, true, false, 3, true>
+                                                 : k_legendre_tc<1, true, false, 3, true>)
+                                : (stages == 4   ? k_legendre_tc<4, true, false, 2, true>
+                                   : stages == 3 ? k_legendre_tc<3, true, false, 2, true>
+                                   : stages == 2 ? k_legendre_tc<2, true, false, 2, true>
+                                                 : k_legendre_tc<1, true, false, 2, true>))
+                     : (br == 3 ? (stages == 4   ? k_legendre_tc<4, true, false, 3>
+                                   : stages == 3 ? k_legendre_tc<3, true, false, 3>
+                                   : stages == 2 ? k_legendre_tc<2, true, false, 3>
+                                                 : k_legendre_tc<1, true, false, 3>)
+                                : (stages == 4   ? k_legendre_tc<4, true, false, 2>
+                                   : stages == 3 ? k_legendre_tc<3, true, false, 2>
+                                   : stages == 2 ? k_legendre_tc<2, true, false, 2>
+                                                 : k_legendre_tc<1, true, false, 2>));
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: both shared memory and the 512 TMEM columns (two accumulators each) must fit
-    const int per_sm = (smem <= 113 * 1024 && 2 * 2 * host_tmem_cols(nmma) <= 512) ? 2 : 1;
+    const int acc_cols = host_tmem_cols(bcat ? 2 * 64 * mn_atoms(nmma) : nmma);
+    const int per_sm = (smem <= 113 * 1024 && 2 * 2 * acc_cols <= 512) ? 2 : 1;
     const int grid = g.ntiles_ana < per_sm * g.num_sms ? g.ntiles_ana : per_sm * g.num_sms;
     ProfScope prof(PK_ANALYSIS, st);
     count_launch();
