@@ -71,6 +71,68 @@ __device__ __forceinline__ void split_x_mn(const float* xs, int nmma, int ncols,
   }
 }
 
+// The same split with each thread's tasks fixed for the whole kernel: the offsets into the
+// FP32 tile and into the atoms, the task's node and its valid-column mask are computed once
+// (the tasks are the same at every stage), so a stage costs only the loads, the conversions
+// and the stores.  Up to kXcTasks tasks per thread (64 x nmma/8 <= kXcTasks x threads).
+constexpr int kXcTasks = 4;
+struct XConv {
+  int xoff[kXcTasks];     // float offset of the task's 8 values in the FP32 tile (-1: no task)
+  uint32_t so[kXcTasks];  // byte offset of its 16-byte chunk in the hi (and lo) atoms
+  int r[kXcTasks];        // node within the 64-node chunk
+  uint32_t cm[kXcTasks];  // bit q: column c0 + q < ncols
+
+  __device__ __forceinline__ void init(int nmma, int ncols, int pt, int nt) {
+    const int ch = nmma >> 3, ntask = 64 * ch;
+#pragma unroll
+    for (int i = 0; i < kXcTasks; ++i) {
+      const int e = pt + i * nt;
+      xoff[i] = -1;
+      so[i] = 0;
+      r[i] = 0;
+      cm[i] = 0;
+      if (e < ntask) {
+        const int rr = e / ch, c0 = (e - rr * ch) * 8;
+        xoff[i] = rr * nmma + c0;
+        so[i] = (uint32_t)((c0 >> 6) * (64 * 64 * 2)) + sw128_offset(rr, c0 & 63);
+        r[i] = rr;
+        uint32_t m = 0;
+        for (int q = 0; q < 8; ++q) m |= (c0 + q < ncols) ? (1u << q) : 0u;
+        cm[i] = m;
+      }
+    }
+  }
+
+  __device__ __forceinline__ void run(const float* xs, int jh0, int nh, uint8_t* bh, uint8_t* bl) const {
+    float4 a[kXcTasks], b[kXcTasks];
+#pragma unroll
+    for (int i = 0; i < kXcTasks; ++i)
+      if (xoff[i] >= 0) {
+        a[i] = *reinterpret_cast<const float4*>(xs + xoff[i]);
+        b[i] = *reinterpret_cast<const float4*>(xs + xoff[i] + 4);
+      }
+#pragma unroll
+    for (int i = 0; i < kXcTasks; ++i) {
+      if (xoff[i] < 0) continue;
+      const uint32_t m = (jh0 + r[i] < nh) ? cm[i] : 0u;
+      const float v[8] = {a[i].x, a[i].y, a[i].z, a[i].w, b[i].x, b[i].y, b[i].z, b[i].w};
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int q = 0; q < 8; q += 2) {
+        const float v0 = (m >> q) & 1u ? v[q] : 0.f;
+        const float v1 = (m >> (q + 1)) & 1u ? v[q + 1] : 0.f;
+        const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+        const float2 hf = __bfloat1622float2(h2);
+        const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
+        hw[q / 2] = *reinterpret_cast<const uint32_t*>(&h2);
+        lw[q / 2] = *reinterpret_cast<const uint32_t*>(&l2);
+      }
+      *reinterpret_cast<uint4*>(bh + so[i]) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>(bl + so[i]) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  }
+};
+
 struct AnaArgs {
   const Tile* tiles;
   int ntiles;
@@ -289,6 +351,9 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
     if (ANA && !XS) {
       // split the FP32 X tile (TMA, with the table tiles) into bf16 hi/lo, MN-major [jh][c]
       const int pt = threadIdx.x - 64;
+      const bool pre = 64 * (nmma >> 3) <= kXcTasks * kConv;   // the tasks fit the fixed plan
+      XConv xc;
+      xc.init(pre ? nmma : 0, aa.ncols, pt, kConv);
       int it = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -300,8 +365,12 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
           if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
           // the MMAs of iteration it - kBR have finished reading this B buffer
           if (nb > 0 && !(ok = mbar_wait(&ctl.bempty[sb], (nb - 1) & 1, abort))) break;
-          split_x_mn(reinterpret_cast<const float*>(sX + s * xbytes), nmma, aa.ncols, kb * kBK, nh,
-                     sB_hi + sb * bstride, sB_lo + sb * bstride, pt, kConv);
+          if (pre)
+            xc.run(reinterpret_cast<const float*>(sX + s * xbytes), kb * kBK, nh, sB_hi + sb * bstride,
+                   sB_lo + sb * bstride);
+          else
+            split_x_mn(reinterpret_cast<const float*>(sX + s * xbytes), nmma, aa.ncols, kb * kBK, nh,
+                       sB_hi + sb * bstride, sB_lo + sb * bstride, pt, kConv);
           fence_async_smem();
           mbar_arrive(&ctl.fullB[sb]);
         }
