@@ -170,13 +170,14 @@ struct SynArgs {
 // are idle.
 constexpr int kXsBoxBytes = 64 * 64 * 2;
 
-// Analysis from FP32 spectra runs six converter warps (2-7) and its epilogue on warps 8-11
-// (384 threads); the other forms keep two converter slots (2-3) and warps 4-7 (256 threads).
+// Analysis from FP32 spectra runs eight converter warps (2-9, two on each SM sub-partition)
+// and its epilogue on warps 10-13 (448 threads); the other forms keep two converter slots
+// (2-3) and warps 4-7 (256 threads).
 template <bool ANA, bool XS>
-__host__ __device__ constexpr int tc_conv_warps() { return (ANA && !XS) ? 6 : 2; }
+__host__ __device__ constexpr int tc_conv_warps() { return (ANA && !XS) ? 8 : 2; }
 template <bool ANA, bool XS>
 __host__ __device__ constexpr int tc_threads() { return 32 * (2 + tc_conv_warps<ANA, XS>() + 4); }
-static_assert(tc_threads<true, false>() == 384 && tc_threads<false, false>() == kTcThreads, "warp roles");
+static_assert(tc_threads<true, false>() == 448 && tc_threads<false, false>() == kTcThreads, "warp roles");
 
 template <int kStages, bool ANA, bool XS = false, int kBR = 2, bool BCAT = false>
 __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const __grid_constant__ CUtensorMap ta_hi,
