@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
     }
   } else {
     // epilogue: drain the accumulator of every tile of this CTA
-    const int q = warp - kEpiWarp0;   // TMEM lane quadrant (warp % 4)
+    const int q = warp & 3;   // a warp reaches only TMEM lanes 32 (warp % 4) .. 32 (warp % 4) + 31
     int lt = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const Tile tl = tiles[t];
