@@ -144,9 +144,12 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
               u = ratio;
               acc[q][0] += u;
             } else {
-              // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}
-              u = powf(ratio, gam);
-              if (pm > 0.f) acc[q][0] += aj * pm * powf(ratio, -et);
+              // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}: both powers from one
+              // base-2 logarithm of the ratio (hardware log2/exp2, ~2^-21 absolute in the exponent;
+              // ratio = 0 gives u = 0, and p = 0 contributes nothing to the sum)
+              const float l2 = __log2f(ratio);
+              u = exp2f(gam * l2);
+              if (pm > 0.f) acc[q][0] += aj * pm * exp2f(-et * l2);
             }
             if (!(kv > 0.f)) {
               if (kv <= 0.f) acc[q][2] += 1.f;
