@@ -743,7 +743,7 @@ int shot_grid_rings(shot_grid gh, int* len, long long* off, double* phi0) {
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->tiles_ana_t, g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tabT, g->tab_hi, g->tab_lo,
+  void* dptr[] = {g->tiles_ana_t, g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->hp_plan_d, g->ring_plan_d, g->hp_tw_d, g->hp_tw_base_d, g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tabT, g->tab_hi, g->tab_lo,
                   g->ws.ct_hi, g->ws.ct_lo, g->ws.ct32, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};

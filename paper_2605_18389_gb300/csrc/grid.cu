@@ -278,7 +278,40 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
     for (int i = 0; i < nlat; ++i) ph[i] = make_int2(g.ring_phase[i].first, g.ring_phase[i].second);
     SHOT_CUDA(cudaMalloc(&g.ring_phase_d, nlat * sizeof(int2)));
     SHOT_CUDA(cudaMemcpyAsync(g.ring_phase_d, ph.data(), nlat * sizeof(int2), cudaMemcpyHostToDevice, st));
-    SHOT_CUDA(cudaStreamSynchronize(st));   // af, ph are locals
+    // ring FFT plans: one per distinct length with factors 2, 3, 5 only
+    std::vector<FftPlan> plans;
+    std::vector<int> ring_plan(nlat, -1), tw_base;
+    std::vector<float2> tw_all;
+    for (int i = 0; i < nlat; ++i) {
+      const int n = g.ring_len[i];
+      int pi = -1;
+      for (size_t k = 0; k < plans.size(); ++k)
+        if (plans[k].N == n) pi = (int)k;
+      if (pi < 0) {
+        FftPlan pl;
+        if (make_fft_plan(n, &pl)) {
+          std::vector<float2> tw;
+          fft_plan_twiddles(pl, tw);
+          pi = (int)plans.size();
+          plans.push_back(pl);
+          tw_base.push_back((int)tw_all.size());
+          tw_all.insert(tw_all.end(), tw.begin(), tw.end());
+        }
+      }
+      ring_plan[i] = pi;
+    }
+    SHOT_CUDA(cudaMalloc(&g.ring_plan_d, nlat * sizeof(int)));
+    SHOT_CUDA(cudaMemcpyAsync(g.ring_plan_d, ring_plan.data(), nlat * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!plans.empty()) {
+      SHOT_CUDA(cudaMalloc(&g.hp_plan_d, plans.size() * sizeof(FftPlan)));
+      SHOT_CUDA(cudaMalloc(&g.hp_tw_d, tw_all.size() * sizeof(float2)));
+      SHOT_CUDA(cudaMalloc(&g.hp_tw_base_d, tw_base.size() * sizeof(int)));
+      SHOT_CUDA(cudaMemcpyAsync(g.hp_plan_d, plans.data(), plans.size() * sizeof(FftPlan), cudaMemcpyHostToDevice, st));
+      SHOT_CUDA(cudaMemcpyAsync(g.hp_tw_d, tw_all.data(), tw_all.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+      SHOT_CUDA(cudaMemcpyAsync(g.hp_tw_base_d, tw_base.data(), tw_base.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                st));
+    }
+    SHOT_CUDA(cudaStreamSynchronize(st));   // af, ph, the plans and tables are locals
     count_launch();
     k_heat<<<(L + 255) / 256, 256, 0, st>>>(g.lmax, 0.0, g.h_d);
     SHOT_CUDA(cudaGetLastError());

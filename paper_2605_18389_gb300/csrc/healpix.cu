@@ -9,8 +9,10 @@
 // the other grids and the Legendre stage is shared with them unchanged.
 //
 // A ring's length n_i is 4k, not always a product of 2, 3 and 5, and the band limit
-// (3 nside - 1 by default) exceeds n_i / 2 on the polar rings, so the ring transforms are
-// direct DFTs in shared memory with the aliasing made explicit:
+// (3 nside - 1 by default) exceeds n_i / 2 on the polar rings.  The ring transforms run the
+// shared-memory Stockham FFT of the rectangular grids on the rings whose length factors into
+// 2, 3 and 5 (all equatorial-belt rings at the usual nside = 2^k, and many polar rings) and a
+// direct DFT in shared memory on the others, with the aliasing made explicit:
 //   forward  F_m = e^{-i m phi0} D_{m mod n},   D_k = sum_j f_j e^{-2 pi i k j / n}
 //   inverse  f_j = sum_k Z_k e^{2 pi i k j / n},
 //            Z_k = sum_{m = -lmax..lmax, m = k mod n} e^{i m phi0} G_m,   G_{-m} = conj G_m.
@@ -19,6 +21,7 @@
 #include <vector>
 
 #include "epilogue.cuh"
+#include "fft.cuh"
 
 namespace shot {
 namespace {
@@ -38,8 +41,10 @@ __device__ __forceinline__ float2 half_turns(long long r, int d) {
   return make_float2(c, s);
 }
 
-// ring constants: twiddles tw[t] = e^{-2 pi i t / n}; phases ph[m] = e^{i m phi0}
+// ring constants: twiddles tw[t] = e^{-2 pi i t / n} (direct DFT rings; tw may be null);
+// phases ph[m] = e^{i m phi0}
 __device__ __forceinline__ void ring_tables(float2* tw, float2* ph, int n, int2 phase, int lmax) {
+  if (tw)
   for (int t = threadIdx.x; t < n; t += blockDim.x) {
     const float2 e = half_turns(2LL * t, n);
     tw[t] = make_float2(e.x, -e.y);
@@ -48,12 +53,14 @@ __device__ __forceinline__ void ring_tables(float2* tw, float2* ph, int n, int2 
     for (int m = threadIdx.x; m <= lmax; m += blockDim.x) ph[m] = half_turns((long long)m * phase.x, phase.y);
 }
 
-// D[q][k] = sum_t zin[q][t] tw[k t mod n] (forward, conj = false) or with conj(tw) (inverse)
+// D[q][k] = sum_t zin[q][t] tw[k t mod n] (forward, conj = false) or with conj(tw) (inverse);
+// sequences at a stride of ld
 template <bool INV>
-__device__ __forceinline__ void direct_dft(const float2* zin, float2* zout, const float2* tw, int n, int nseq) {
+__device__ __forceinline__ void direct_dft(const float2* zin, float2* zout, const float2* tw, int n, int ld,
+                                           int nseq) {
   for (int idx = threadIdx.x; idx < nseq * n; idx += blockDim.x) {
     const int q = idx / n, k = idx - q * n;
-    const float2* s = zin + q * n;
+    const float2* s = zin + q * ld;
     float re = 0.f, im = 0.f;
     int e = 0;
     for (int t = 0; t < n; ++t) {
@@ -65,19 +72,36 @@ __device__ __forceinline__ void direct_dft(const float2* zin, float2* zout, cons
       e += k;
       if (e >= n) e -= n;
     }
-    zout[q * n + k] = make_float2(re, im);
+    zout[q * ld + k] = make_float2(re, im);
   }
+}
+
+// The ring transform of nseq sequences (stride seq_ld(n)) in a, b as scratch: the FFT when
+// the ring has a plan (pi >= 0), else the direct DFT with the twiddles tw.  Returns the buffer
+// holding the result.  All threads call it; it synchronises before returning.
+template <bool INV>
+__device__ __forceinline__ float2* ring_transform(float2* a, float2* b, const float2* tw, int n, int nseq, int pi,
+                                                  const FftPlan* __restrict__ plans,
+                                                  const float2* __restrict__ tw_all, const int* __restrict__ tw_base) {
+  if (pi >= 0) {
+    const FftPlan pl = plans[pi];
+    return fft_smem<INV>(a, b, tw_all + tw_base[pi], pl, nseq);
+  }
+  direct_dft<INV>(a, b, tw, n, seq_ld(n), nseq);
+  __syncthreads();
+  return b;
 }
 
 // from the transformed ring pair D: S = a (F_N + F_S), D = a (F_N - F_S) for m <= lmax into X
 template <int FG>
 __device__ __forceinline__ void hp_unpack_store(const float2* D, const float2* ph, int n, int nfg, int f0, int lmax,
                                                 int nh, int jh, float aj, float* __restrict__ X, int ldc) {
+  const int ld = seq_ld(n);
   for (int idx = threadIdx.x; idx < (lmax + 1) * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
     if (q >= nfg) continue;
     const int k = m % n, kk = (n - k) % n;
-    const float2 zm = D[q * n + k], zn = D[q * n + kk];
+    const float2 zm = D[q * ld + k], zn = D[q * ld + kk];
     float2 FN = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
     float2 FS = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
     const float2 e = make_float2(ph[m].x, -ph[m].y);   // e^{-i m phi0}
@@ -96,26 +120,29 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_fwd(const float* __restrict__
                                                        const int* __restrict__ rlen,
                                                        const long long* __restrict__ roff,
                                                        const int2* __restrict__ rphase, int nrings, int lmax, int nh,
-                                                       float area, float* __restrict__ X, int ldc) {
+                                                       float area, float* __restrict__ X, int ldc,
+                                                       const int* __restrict__ rplan, const FftPlan* __restrict__ plans,
+                                                       const float2* __restrict__ tw_all,
+                                                       const int* __restrict__ tw_base) {
   extern __shared__ __align__(16) float2 sm[];
   const int jh = blockIdx.y, f0 = blockIdx.x * FG;
   const int nfg = min(FG, nf - f0);
   const int j = jh, J = nrings - 1 - jh;
-  const int n = rlen[j];
-  float2* zb = sm;               // [FG][n]
-  float2* db = zb + FG * n;      // [FG][n]
-  float2* tw = db + FG * n;      // [n]
+  const int n = rlen[j], ld = seq_ld(n);
+  const int pi = rplan[j];
+  float2* zb = sm;               // [FG][ld]
+  float2* db = zb + FG * ld;     // [FG][ld]
+  float2* tw = db + FG * ld;     // [n] (direct DFT rings)
   float2* ph = tw + n;           // [lmax + 1]
-  ring_tables(tw, ph, n, rphase[j], lmax);
+  ring_tables(pi >= 0 ? nullptr : tw, ph, n, rphase[j], lmax);
   for (int q = 0; q < nfg; ++q) {
     const float* fj = in + (size_t)(f0 + q) * npix + roff[j];
     const float* fJ = in + (size_t)(f0 + q) * npix + roff[J];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) zb[q * n + k] = make_float2(fj[k], J != j ? fJ[k] : 0.f);
+    for (int k = threadIdx.x; k < n; k += blockDim.x) zb[q * ld + k] = make_float2(fj[k], J != j ? fJ[k] : 0.f);
   }
   __syncthreads();
-  direct_dft<false>(zb, db, tw, n, nfg);
-  __syncthreads();
-  hp_unpack_store<FG>(db, ph, n, nfg, f0, lmax, nh, jh, area, X, ldc);
+  const float2* D = ring_transform<false>(zb, db, tw, n, nfg, pi, plans, tw_all, tw_base);
+  hp_unpack_store<FG>(D, ph, n, nfg, f0, lmax, nh, jh, area, X, ldc);
 }
 
 template <int FG>
@@ -123,23 +150,28 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_idft(const float* __restrict_
                                                         const int* __restrict__ rlen,
                                                         const long long* __restrict__ roff,
                                                         const int2* __restrict__ rphase, int nrings, int lmax,
-                                                        int nh, float area, EpiParams ep) {
+                                                        int nh, float area, EpiParams ep,
+                                                        const int* __restrict__ rplan,
+                                                        const FftPlan* __restrict__ plans,
+                                                        const float2* __restrict__ tw_all,
+                                                        const int* __restrict__ tw_base) {
   extern __shared__ __align__(16) float2 sm[];
   __shared__ float red[kHpThreads / 32][FG * NPART];
   __shared__ EpiField fi[FG];
   const int jh = blockIdx.y, f0 = blockIdx.x * FG;
   const int nfg = min(FG, nf - f0);
   const int j = jh, J = nrings - 1 - jh;
-  const int n = rlen[j];
+  const int n = rlen[j], ld = seq_ld(n);
+  const int pi = rplan[j];
   const int nm = lmax + 1;
-  float2* za = sm;               // [FG][n]  spectra Z, later the new scaling
-  float2* zb = za + FG * n;      // [FG][n]  K v on the ring pair
-  float2* tw = zb + FG * n;      // [n]
+  float2* za = sm;               // [FG][ld]  spectra Z
+  float2* zb = za + FG * ld;     // [FG][ld]
+  float2* tw = zb + FG * ld;     // [n] (direct DFT rings)
   float2* ph = tw + n;           // [lmax + 1]
   float2* gn = ph + nm;          // [lmax + 1][FG]  G_N = E + O
   float2* gs = gn + nm * FG;     // [lmax + 1][FG]  G_S = E - O
   epi_fields_load<FG>(ep, f0, nfg, fi);
-  ring_tables(tw, ph, n, rphase[j], lmax);
+  ring_tables(pi >= 0 ? nullptr : tw, ph, n, rphase[j], lmax);
   for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
     float2 E = make_float2(0.f, 0.f), O = make_float2(0.f, 0.f);
@@ -167,26 +199,27 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_idft(const float* __restrict_
       re += t.x;
       im += t.y;
     }
-    za[q * n + k] = make_float2(re, im);
+    za[q * ld + k] = make_float2(re, im);
   }
   __syncthreads();
-  direct_dft<true>(za, zb, tw, n, nfg);
-  __syncthreads();
+  float2* z = ring_transform<true>(za, zb, tw, n, nfg, pi, plans, tw_all, tw_base);   // K v on the ring pair
+  float2* other = (z == za) ? zb : za;   // receives the new scaling
   const bool two = (J != j);
-  ring_pair_epilogue<FG, kHpThreads>(zb, za, n, n, nfg, f0, npix, (size_t)roff[j], (size_t)roff[J], two, area, nh,
-                                     jh, ep, red, fi);
+  ring_pair_epilogue<FG, kHpThreads>(z, other, ld, n, nfg, f0, npix, (size_t)roff[j], (size_t)roff[J], two, area,
+                                     nh, jh, ep, red, fi);
   if (ep.mode == EPI_PLAIN) return;
-  if (ep.mode == EPI_UPDATE && ep.xout) {   // the new scaling is in za: transform it
+  if (ep.mode == EPI_UPDATE && ep.xout) {   // transform the new scaling
     __syncthreads();
-    direct_dft<false>(za, zb, tw, n, nfg);
-    __syncthreads();
-    hp_unpack_store<FG>(zb, ph, n, nfg, f0, lmax, nh, jh, area, ep.xout, ldc);
+    const float2* D = ring_transform<false>(other, z, tw, n, nfg, pi, plans, tw_all, tw_base);
+    hp_unpack_store<FG>(D, ph, n, nfg, f0, lmax, nh, jh, area, ep.xout, ldc);
   }
 }
 
-size_t hp_fwd_smem(int fg, int n, int lmax) { return (size_t)(2 * fg * n + n + lmax + 1) * sizeof(float2); }
+size_t hp_fwd_smem(int fg, int n, int lmax) {
+  return (size_t)(2 * fg * seq_ld(n) + n + lmax + 1) * sizeof(float2);
+}
 size_t hp_idft_smem(int fg, int n, int lmax) {
-  return (size_t)(2 * fg * n + n + (lmax + 1) * (1 + 2 * fg)) * sizeof(float2);
+  return (size_t)(2 * fg * seq_ld(n) + n + (lmax + 1) * (1 + 2 * fg)) * sizeof(float2);
 }
 
 int hp_pick_fg(const Grid& g, int nf, bool inverse) {
@@ -204,7 +237,8 @@ int hp_fwd_t(const Grid& g, const float* in, int nf, float* X, int ldc, cudaStre
   ProfScope prof(PK_DFT, st);
   count_launch();
   k_hp_fwd<FG><<<dim3((nf + FG - 1) / FG, g.nh), kHpThreads, smem, st>>>(
-      in, nf, g.npix, g.ring_len_d, g.ring_off_d, g.ring_phase_d, g.nlat, g.lmax, g.nh, (float)g.a_ring[0], X, ldc);
+      in, nf, g.npix, g.ring_len_d, g.ring_off_d, g.ring_phase_d, g.nlat, g.lmax, g.nh, (float)g.a_ring[0], X, ldc,
+      g.ring_plan_d, g.hp_plan_d, g.hp_tw_d, g.hp_tw_base_d);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }
@@ -216,7 +250,8 @@ int hp_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& e
   ProfScope prof(PK_IDFT, st);
   count_launch();
   k_hp_idft<FG><<<dim3((nf + FG - 1) / FG, g.nh), kHpThreads, smem, st>>>(
-      Y, ldc, nf, g.npix, g.ring_len_d, g.ring_off_d, g.ring_phase_d, g.nlat, g.lmax, g.nh, (float)g.a_ring[0], ep);
+      Y, ldc, nf, g.npix, g.ring_len_d, g.ring_off_d, g.ring_phase_d, g.nlat, g.lmax, g.nh, (float)g.a_ring[0], ep,
+      g.ring_plan_d, g.hp_plan_d, g.hp_tw_d, g.hp_tw_base_d);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }

@@ -158,6 +158,13 @@ struct Grid {
   int* ring_len_d = nullptr;
   long long* ring_off_d = nullptr;
   int2* ring_phase_d = nullptr;
+  // HEALPix: FFT plans for the ring lengths that factor into 2, 3 and 5 (the other rings use
+  // direct DFTs); ring_plan_d[i] = plan index or -1, each plan's stage twiddles at
+  // hp_tw_d + hp_tw_base_d[plan]
+  FftPlan* hp_plan_d = nullptr;
+  int* ring_plan_d = nullptr;
+  float2* hp_tw_d = nullptr;
+  int* hp_tw_base_d = nullptr;
   int ntiles_ana = 0, ntiles_syn = 0;
   int bm_ana = 128, bm_syn = 128;
   Workspace ws;
