@@ -40,7 +40,7 @@ extern "C" {
 #define SHOT_ERR_INVALID_ARG    -1   /* bad size, NULL pointer, eps <= 0, tau <= 0, ... */
 #define SHOT_ERR_CUDA           -2   /* a CUDA runtime call failed (message in shot_last_error) */
 #define SHOT_ERR_OOM            -3   /* device allocation failed */
-#define SHOT_ERR_UNSUPPORTED    -4   /* nlon has a prime factor other than 2, 3, 5, or an unbuilt mode */
+#define SHOT_ERR_UNSUPPORTED    -4   /* nlon beyond the ring FFT (> 6400 longitudes), or an unbuilt mode */
 #define SHOT_ERR_NONPOSITIVE    -5   /* some K v <= 0: the update of Alg. 1 is undefined (App. C.4) */
 #define SHOT_ERR_NONFINITE      -6   /* a scaling became inf/NaN (FP32 range exceeded) */
 #define SHOT_ERR_TIMEOUT        -7   /* a bounded device-side wait expired */
@@ -78,7 +78,8 @@ int shot_last_error(char* buf, int len);
  * device (App. C.1), area weights (App. C.2) and the orthonormal associated
  * Legendre table Pbar_lm(x_j) (App. B), folded by parity over the two hemispheres.
  *   out        receives the handle (host pointer)
- *   nlat >= 2; nlon >= 2*lmax+1 with prime factors in {2,3,5}; lmax = -1 means nlat-1,
+ *   nlat >= 2; 2*lmax+1 <= nlon <= 6400 (any factorisation: prime factors above 5 run generic
+ *              O(p)-per-output FFT stages, so 2,3,5-smooth nlon are fastest); lmax = -1 means nlat-1,
  *              else 0 <= lmax <= nlat-1
  *   precision  SHOT_FP32, SHOT_BF16X3 or SHOT_TF32X3; legendre_mode SHOT_TABLE or SHOT_RECURRENCE (FP32)
  * Memory: about 2*(lmax+1)(lmax+2)/2 * ceil(nlat/2) * 4 bytes of table (0.37 GB at 720);

@@ -646,7 +646,7 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     return SHOT_ERR_UNSUPPORTED;
   }
   FftPlan plan;
-  if (!make_fft_plan(nlon, &plan)) { set_error("nlon must factor into 2, 3 and 5"); return SHOT_ERR_UNSUPPORTED; }
+  if (!make_fft_plan(nlon, &plan)) { set_error("no ring FFT plan for this nlon (too long)"); return SHOT_ERR_UNSUPPORTED; }
   Grid* g = new Grid;
   g->nlat = nlat;
   g->nlon = nlon;

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_dft_fwd(
   const int nfg = min(FG, nf - f0);
   const int j = jh, J = nlat - 1 - jh;
 
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
+  for (int k = threadIdx.x; k < fft_tw_len(pl); k += blockDim.x) tw[k] = tw_g[k];
   load_ring_pairs(in, b0, f0, nfg, nlat, nlon, j, J);
   __syncthreads();
   const float2* buf = fft_smem<false>(b0, b1, tw, pl, nfg);
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
       cp_async8(stg + blk * FG, Y + ((size_t)blk * nh + jh) * ldc + 2 * f0);
   }
   epi_fields_load<FG>(ep, f0, nfg, fi);
-  for (int k = threadIdx.x; k < N; k += blockDim.x) tw[k] = tw_g[k];
+  for (int k = threadIdx.x; k < fft_tw_len(pl); k += blockDim.x) tw[k] = tw_g[k];
   // zero the band lmax < m < N - lmax
   const int nz = N - 2 * lmax - 1;
   for (int q = 0; q < nfg; ++q)
@@ -323,7 +323,7 @@ int pick_fg(int N, int nf) {
 template <int FG>
 int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which, float* X,
                  int ldc, cudaStream_t st, int xsplit) {
-  const size_t smem = (size_t)(g.nlon + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
+  const size_t smem = (size_t)(fft_tw_len(g.plan) + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
   SHOT_CUDA(cudaFuncSetAttribute(k_dft_fwd<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
   ProfScope prof(PK_DFT, st);
@@ -337,7 +337,7 @@ int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, in
 template <int FG, class PL = RuntimePlan>
 int launch_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
   // two sequence buffers (the second also stages the gathered spectra) and the twiddles
-  const size_t smem = (size_t)(g.nlon + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
+  const size_t smem = (size_t)(fft_tw_len(g.plan) + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
   SHOT_CUDA(cudaFuncSetAttribute(k_idft<FG, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
   ProfScope prof(PK_IDFT, st);

@@ -7,7 +7,9 @@
 // applies an R-point DFT and writes output r to out[(j div Ns) Ns R + (j mod Ns) + r Ns].
 //
 // Radices go up to 16 so that the rings of the usual grids take three stages
-// (1440 = 9 * 10 * 16).  The composite radices (6, 9, 10, 12, 15, 16) run as two
+// (1440 = 9 * 10 * 16); a prime factor above 5 becomes a stage of its own with a generic
+// butterfly (O(R) work per output, roots of unity from the plan's table), so any ring
+// length has a plan.  The composite radices (6, 9, 10, 12, 15, 16) run as two
 // register-resident levels of 2-, 3-, 4- and 5-point DFTs (Cooley-Tukey inside the
 // butterfly) whose internal twiddles are compile-time constants.  The stage twiddles come
 // from a per-stage table, r-major, so that consecutive lanes read consecutive entries.
@@ -258,6 +260,44 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
   }
 }
 
+// Stage with a radix that has no compiled butterfly (a prime above 5): each task computes one
+// output r of butterfly j, sum_t v_t W_R^{r t}, with v_t the stage-twiddled input t and the
+// roots W_R^e from the plan's table; O(R) work per output.  Tasks run r-major over the
+// butterflies, so consecutive threads read consecutive inputs.
+template <bool INV>
+__device__ __noinline__ void stockham_stage_generic(const float2* __restrict__ src, float2* __restrict__ dst,
+                                                    const float2* __restrict__ tws, const float2* __restrict__ roots,
+                                                    int N, int R, int Ns, int nseq, uint32_t ns_mul,
+                                                    uint32_t nr_mul) {
+  const int NR = N / R;
+  const int ld = seq_ld(N);
+  const int total = nseq * N;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int qr = fast_div(idx, nr_mul);   // q R + r
+    const int j = idx - qr * NR;
+    const int q = qr / R, r = qr - q * R;
+    const int jd = fast_div(j, ns_mul);
+    const int k = j - jd * Ns;
+    const float2* s = src + q * ld + j;
+    float re = 0.f, im = 0.f;
+    int e = 0;   // r t mod R
+    for (int t = 0; t < R; ++t) {
+      float2 v = s[t * NR];
+      if (Ns > 1 && t > 0) {
+        const float2 w = tws[(t - 1) * Ns + k];
+        v = INV ? cmulc(v, w) : cmul(v, w);
+      }
+      const float2 w = roots[e];
+      v = INV ? cmulc(v, w) : cmul(v, w);
+      re += v.x;
+      im += v.y;
+      e += r;
+      if (e >= R) e -= R;
+    }
+    dst[q * ld + jd * Ns * R + k + r * Ns] = make_float2(re, im);
+  }
+}
+
 // Transforms nseq sequences of length plan.N stored at a[q * seq_ld(N) + k]; b is
 // scratch of the same shape; tw holds the plan's stage twiddles (forward sign).  Returns
 // the buffer holding the result.  All threads of the block must call it; it
@@ -280,7 +320,10 @@ __device__ float2* fft_smem(float2* a, float2* b, const float2* tw, const FftPla
       case 10: stockham_stage<10, INV>(a, b, tws, pl.N, Ns, nseq, nsm, nrm); break;
       case 12: stockham_stage<12, INV>(a, b, tws, pl.N, Ns, nseq, nsm, nrm); break;
       case 15: stockham_stage<15, INV>(a, b, tws, pl.N, Ns, nseq, nsm, nrm); break;
-      default: stockham_stage<16, INV>(a, b, tws, pl.N, Ns, nseq, nsm, nrm); break;
+      case 16: stockham_stage<16, INV>(a, b, tws, pl.N, Ns, nseq, nsm, nrm); break;
+      default:
+        stockham_stage_generic<INV>(a, b, tws, tw + pl.root_off[s], pl.N, R, Ns, nseq, nsm, nrm);
+        break;
     }
     __syncthreads();
     float2* t = a;

@@ -186,6 +186,22 @@ __global__ void k_coeff_scatter(int lmax, int nf, const long long* __restrict__ 
 // then the smallest largest radix (registers).
 bool make_fft_plan(int N, FftPlan* pl) {
   if (N < 1 || N >= (1 << 16)) return false;
+  // prime factors above 5 become generic stages, placed first (their stage twiddles are 1)
+  std::vector<int> gen;
+  {
+    int m = N;
+    for (int p : {2, 3, 5})
+      while (m % p == 0) m /= p;
+    for (int p = 7; (long long)p * p <= m; p += 2)
+      while (m % p == 0) {
+        gen.push_back(p);
+        m /= p;
+      }
+    if (m > 1) gen.push_back(m);
+    std::sort(gen.rbegin(), gen.rend());
+    for (int p : gen) N /= p;   // the 2,3,5-smooth part goes to the radix search below
+  }
+  const int Nfull = [&] { int t = N; for (int p : gen) t *= p; return t; }();
   static const int kRad[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
   const int nrad = (int)(sizeof(kRad) / sizeof(kRad[0]));
   auto order = [](std::vector<int> f) {
@@ -225,14 +241,22 @@ bool make_fft_plan(int N, FftPlan* pl) {
   };
   dfs(N, 0);
   if (!found) return false;
+  best.insert(best.begin(), gen.begin(), gen.end());
+  if (best.size() > 16) return false;
+  N = Nfull;
   pl->N = N;
   pl->nst = (int)best.size();
   // exact division by multiply-high for operands below 2^16
   auto mul = [](uint32_t d) -> uint32_t { return d <= 1 ? 0u : (uint32_t)((((uint64_t)1 << 32) + d - 1) / d); };
-  int Ns = 1, off = 0;
+  int Ns = 1, off = 0, roff = N;
   for (int s = 0; s < pl->nst; ++s) {
     pl->R[s] = best[s];
     pl->tw_off[s] = off;
+    pl->root_off[s] = 0;
+    if (!fft_radix_compiled(best[s])) {
+      pl->root_off[s] = roff;
+      roff += best[s];
+    }
     pl->ns_mul[s] = mul((uint32_t)Ns);
     pl->nr_mul[s] = mul((uint32_t)(N / pl->R[s]));
     if (s > 0) off += (pl->R[s] - 1) * Ns;
@@ -243,7 +267,16 @@ bool make_fft_plan(int N, FftPlan* pl) {
 
 void fft_plan_twiddles(const FftPlan& pl, std::vector<float2>& tw) {
   const int N = pl.N;
-  tw.assign(N, make_float2(1.f, 0.f));
+  size_t total = N;
+  for (int s = 0; s < pl.nst; ++s)
+    if (!fft_radix_compiled(pl.R[s])) total = std::max(total, (size_t)pl.root_off[s] + pl.R[s]);
+  tw.assign(total, make_float2(1.f, 0.f));
+  for (int s = 0; s < pl.nst; ++s)   // roots W_R^e of the generic stages
+    if (!fft_radix_compiled(pl.R[s]))
+      for (int e = 0; e < pl.R[s]; ++e) {
+        const double a = 2.0 * M_PI * (double)e / pl.R[s];
+        tw[pl.root_off[s] + e] = make_float2((float)std::cos(a), (float)-std::sin(a));
+      }
   int Ns = 1;
   for (int s = 0; s < pl.nst; ++s) {
     const int R = pl.R[s];
@@ -265,7 +298,7 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   SHOT_CUDA(cudaMalloc(&g.x_d, nlat * sizeof(double)));
   SHOT_CUDA(cudaMalloc(&g.w_d, nlat * sizeof(double)));
   SHOT_CUDA(cudaMalloc(&g.a_d, nlat * sizeof(float)));
-  SHOT_CUDA(cudaMalloc(&g.tw_d, g.nlon * sizeof(float2)));
+  SHOT_CUDA(cudaMalloc(&g.tw_d, (size_t)std::max(fft_tw_len(g.plan), g.nlon) * sizeof(float2)));
   SHOT_CUDA(cudaMalloc(&g.h_d, L * sizeof(float)));
   if (g.quad == SHOT_QUAD_HEALPIX) {
     // closed-form ring geometry on the host (FP64), then to the device

@@ -42,11 +42,26 @@ struct FftPlan {
   int nst;
   int R[16];
   int tw_off[16];        // offset of stage s's twiddles ((R - 1) x Ns, r-major) in the table
+  int root_off[16];      // stages with a radix outside {2..6, 8, 9, 10, 12, 15, 16} (primes > 5):
+                         // offset of the R roots W_R^e (forward sign) in the table, else 0
   uint32_t ns_mul[16];   // ceil(2^32 / Ns) of stage s (0 when Ns == 1)
   uint32_t nr_mul[16];   // ceil(2^32 / (N / R)) of stage s (0 when N / R == 1)
 };
+// radices with a compiled butterfly; any other radix runs the generic O(R) per output stage
+__host__ __device__ inline bool fft_radix_compiled(int R) {
+  return R == 2 || R == 3 || R == 4 || R == 5 || R == 6 || R == 8 || R == 9 || R == 10 || R == 12 || R == 15 ||
+         R == 16;
+}
+// entries of the plan's twiddle table (N, plus the roots of its generic stages)
+__host__ __device__ inline int fft_tw_len(const FftPlan& p) {
+  int t = p.N;
+  for (int s = 0; s < p.nst; ++s)
+    if (!fft_radix_compiled(p.R[s]) && p.root_off[s] + p.R[s] > t) t = p.root_off[s] + p.R[s];
+  return t;
+}
 bool make_fft_plan(int N, FftPlan* plan);
-// the plan's stage twiddles W_N^{k r N/(Ns R)} (forward sign), N complex values
+// the plan's stage twiddles W_N^{k r N/(Ns R)} (forward sign), then the roots of its generic
+// stages: N + (sum of their radices) complex values
 void fft_plan_twiddles(const FftPlan& plan, std::vector<float2>& tw);
 
 // ---------------------------------------------------------------------------------
@@ -120,7 +135,7 @@ struct Grid {
   double* x_d = nullptr;
   double* w_d = nullptr;
   float* a_d = nullptr;         // per-ring area weight (FP32)
-  float2* tw_d = nullptr;       // exp(-2 pi i k / nlon), k < nlon
+  float2* tw_d = nullptr;       // the ring FFT plan's twiddle table, fft_tw_len(plan) entries
   float* h_d = nullptr;         // heat multipliers for the current call, [lmax+1]
   float* tab = nullptr;         // FP32 folded table [row][ldt] (FP32 and TF32X3 grids)
   float* tabT = nullptr;        // TF32X3: the table transposed per block, [blk][jh][ldi], zero for i >= M

@@ -112,3 +112,23 @@ def test_heat_apply_rejects_bad_arguments(grid_cache):
         shot.shot_grid_init(8, 14)      # nlon < 2 lmax + 1
     with pytest.raises(shot.ShotError):
         shot.shot_grid_init(8, 17 * 2)  # prime factor 17
+
+
+# Ring lengths with prime factors above 5 run a generic FFT stage per such prime (O(p) work
+# per output; the roots of unity tabulated in the plan): 42 = 2*3*7, 66 = 2*3*11,
+# 98 = 2*7^2, 130 = 2*5*13, 362 = 2*181 (a prime radix of 181).
+@pytest.mark.parametrize("nlat,nlon,nf", [(21, 42, 3), (33, 66, 2), (49, 98, 4), (65, 130, 24), (181, 362, 2)])
+def test_any_ring_length_heat_and_sht_match_oracle(grid_cache, nlat, nlon, nf):
+    g, og = grid_cache(nlat, nlon)
+    L = og.lmax + 1
+    rng = np.random.default_rng(nlon + nf)
+    f, f64 = f32(rng.uniform(size=(nf, og.nlat, og.nlon)))
+    out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
+    shot.shot_heat_apply(g, 2e-3, torch.from_numpy(f).cuda(), out)
+    assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, 2e-3)) < TOL_SHT
+    c = torch.empty((nf, L, L, 2), device="cuda")
+    shot.shot_sht_analysis(g, torch.from_numpy(f).cuda(), c)
+    ref = osht.analysis(og, f64)
+    got = c.cpu().numpy()
+    assert rel_max(got[..., 0], ref.real) < TOL_SHT
+    assert rel_max(got[..., 1], ref.imag) < TOL_SHT

@@ -173,3 +173,23 @@ def test_persistent_update_kernel_matches_one_item_per_cta(nlat, pairs, tau):
             shot.shot_grid_free(g)
     for a, b in zip(res[0], res[1]):
         np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_sinkhorn_on_ring_length_with_prime_13(prec):
+    """nlon = 130 = 2*5*13: the solver's fused transforms run the generic radix-13 stage."""
+    nlat, eps, T = 65, 0.05, 40
+    og = OGrid(nlat)
+    g = shot.shot_grid_init(nlat, None, -1, shot.SHOT_FP32 if prec == "fp32" else shot.SHOT_BF16X3)
+    try:
+        p, q = inputs.pairs("paper_uniform", 130, 2, og.x, og.nlon, og.a_ring)
+        p32, p64 = f32(p)
+        q32, q64 = f32(q)
+        rc, r = shot.shot_sinkhorn(g, torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), eps,
+                                   max_iter=T, tol=0.0, check_every=10)
+        ref = sk.sinkhorn(og, p64, q64, eps, math.inf, T=T, delta=0.0, C=10)
+        assert rc == 0 and np.all(r["status"] == 0)
+        u, v = r["u"].cpu().numpy(), r["v"].cpu().numpy()
+        assert potentials_err(og, eps, u, v, ref["phi"], ref["psi"]) < (TOL_PHI if prec == "fp32" else 1e-4)
+    finally:
+        shot.shot_grid_free(g)
