@@ -646,7 +646,10 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     return SHOT_ERR_UNSUPPORTED;
   }
   FftPlan plan;
-  if (!make_fft_plan(nlon, &plan)) { set_error("no ring FFT plan for this nlon (too long)"); return SHOT_ERR_UNSUPPORTED; }
+  if (nlon > kFftCap || !make_fft_plan(nlon, &plan)) {
+    set_error("nlon above the shared-memory ring FFT's 6400 longitudes");
+    return SHOT_ERR_UNSUPPORTED;
+  }
   Grid* g = new Grid;
   g->nlat = nlat;
   g->nlon = nlon;

@@ -215,11 +215,9 @@ __host__ __device__ constexpr int out_reg(int k) {
 }
 
 // Threads of an FFT CTA (launched with at least three CTAs per SM in mind: <= 80
-// registers, enough for the radix-16 butterfly without spills) and the most elements
-// (sequences x length) one CTA transforms: two ping-pong buffers of kFftCap complex values
-// plus the twiddles stay under ~110 KB, so at least two CTAs fit on one SM.
+// registers, enough for the radix-16 butterfly without spills); kFftCap (the most elements,
+// sequences x length, one CTA transforms) is declared with the grid types.
 constexpr int kFftThreads = 256;
-constexpr int kFftCap = 6400;
 
 // stride of consecutive sequences in the CTA's buffers
 __host__ __device__ constexpr int seq_ld(int N) { return N + 1; }

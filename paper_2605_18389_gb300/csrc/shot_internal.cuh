@@ -37,6 +37,11 @@ class ProfScope {
 
 // ---------------------------------------------------------------------------------
 // Ring FFT plan: nlon = prod R[s], radices in {2,3,4,5,8}, Stockham ordering.
+// The most elements (sequences x length) one ring-FFT CTA transforms: two ping-pong buffers
+// of kFftCap complex values plus the twiddles stay under ~110 KB (at least two CTAs per SM);
+// also the longest ring a grid may have.
+constexpr int kFftCap = 6400;
+
 struct FftPlan {
   int N;
   int nst;

@@ -111,7 +111,7 @@ def test_heat_apply_rejects_bad_arguments(grid_cache):
     with pytest.raises(shot.ShotError):
         shot.shot_grid_init(8, 14)      # nlon < 2 lmax + 1
     with pytest.raises(shot.ShotError):
-        shot.shot_grid_init(8, 17 * 2)  # prime factor 17
+        shot.shot_grid_init(8, 6402)    # longer than the shared-memory ring FFT takes
 
 
 # Ring lengths with prime factors above 5 run a generic FFT stage per such prime (O(p) work
