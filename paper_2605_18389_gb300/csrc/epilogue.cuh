@@ -151,11 +151,13 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
               u = exp2f(gam * l2);
               if (pm > 0.f) acc[q][0] += aj * pm * exp2f(-et * l2);
             }
-            if (!(kv > 0.f)) {
+            // one test on the common path: K v positive and finite, u finite (NaN fails each
+            // comparison); the rare failures are sorted into non-positive (first in the status
+            // precedence) and non-finite
+            if (!(kv > 0.f && kv < INFINITY && fabsf(u) < INFINITY)) {
               if (kv <= 0.f) acc[q][2] += 1.f;
-              else acc[q][3] += 1.f;   // NaN
+              else acc[q][3] += 1.f;   // NaN or infinite K v, or u overflowed
             }
-            if (!isfinite(u) || !isfinite(kv)) acc[q][3] += 1.f;
             outf[(r ? rJ : rj) + k] = u;
             u2[r] = u;
           }
