@@ -21,16 +21,18 @@
 //              B = C^T [columns][32 degrees]                      (TMA, FP32 C^T written by
 //                                                                  the analysis epilogue)
 // kind::tf32 is used with K-major operands only, hence the transposed table copy.
-// Warp roles: 0 TMA producer, 1 MMA issuer, 2-7 split (six warps: the table tile alone is
-// 16 KB per stage), 8-11 epilogue over a double-buffered accumulator.  Every mbarrier wait
+// Warp roles: 0 TMA producer, 1 MMA issuer, 2-9 split (eight warps, two per SM sub-partition:
+// the table tile alone is 16 KB per stage), 10-13 epilogue over a double-buffered accumulator
+// (a warp reads the TMEM lane quadrant warp % 4).  Every mbarrier wait
 // is bounded; on expiry the CTA records SHOT_ERR_TIMEOUT and still frees its tensor memory.
 #include "tc_ptx.cuh"
 
 namespace shot {
 namespace {
 
-constexpr int kT32Threads = 384;
-constexpr int kSplitThreads = 192;               // warps 2..7
+constexpr int kSplitWarps = 8;                   // warps 2..9 (two per SM sub-partition)
+constexpr int kSplitThreads = 32 * kSplitWarps;
+constexpr int kT32Threads = 32 * (2 + kSplitWarps + 4);   // + TMA, MMA and four epilogue warps
 constexpr int kTK = 32;                          // K per stage (one 128-byte row of FP32)
 constexpr int kTTile = kBM * kTK * 4;            // 16 KB: 128 rows x 32 FP32
 constexpr int kT32MaxStages = 4;
@@ -62,7 +64,7 @@ __device__ __forceinline__ uint32_t sw128_offset32(int row, int k) {
 
 // Element-wise split of a tile (the swizzle does not matter): raw -> hi (in place), lo.
 // Each thread loads kSplitBatch chunks before it stores any, so the loads overlap.
-constexpr int kSplitBatch = 6;   // 16 KB / (192 threads x 16 B) = 5.3 chunks per thread
+constexpr int kSplitBatch = 4;   // 16 KB / (256 threads x 16 B) = 4 chunks per thread
 __device__ __forceinline__ void split_inplace(uint8_t* raw, uint8_t* lo, int nbytes, int pt) {
   for (int base = 0; base < nbytes; base += kSplitBatch * kSplitThreads * 16) {
     float4 v[kSplitBatch];
@@ -114,6 +116,48 @@ __device__ __forceinline__ void split_xt(const float* xs, int nmma, int ncols, i
     }
   }
 }
+
+// The X^T split with each thread's tasks fixed for the whole kernel (they are the same at every
+// stage): the tile offsets of the four node values, the chunk's offset in the swizzled B tile and
+// whether the column is a field column; a stage then only loads, splits and stores.
+constexpr int kXtTasks = 4;   // nmma x 8 tasks <= 4 x 256 threads (nmma <= 128)
+struct XtPlan {
+  int c[kXtTasks];         // column (-1: no task)
+  int k4[kXtTasks];        // first of the task's four nodes within the 32-node chunk
+  uint32_t o[kXtTasks];    // byte offset of the 16-byte chunk in the hi (and lo) tile
+  __device__ __forceinline__ void init(int nmma, int pt) {
+    const int ntask = nmma * (kTK / 4);
+#pragma unroll
+    for (int i = 0; i < kXtTasks; ++i) {
+      const int e = pt + i * kSplitThreads;
+      c[i] = -1;
+      k4[i] = 0;
+      o[i] = 0;
+      if (e < ntask) {
+        c[i] = e % nmma;
+        k4[i] = (e / nmma) * 4;
+        o[i] = sw128_offset32(c[i], k4[i]);
+      }
+    }
+  }
+  __device__ __forceinline__ void run(const float* xs, int nmma, int ncols, int jh0, int nh, uint8_t* bh,
+                                      uint8_t* bl) const {
+    float v[kXtTasks][4];
+#pragma unroll
+    for (int i = 0; i < kXtTasks; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        v[i][q] = (c[i] >= 0 && c[i] < ncols && jh0 + k4[i] + q < nh) ? xs[(k4[i] + q) * nmma + c[i]] : 0.f;
+#pragma unroll
+    for (int i = 0; i < kXtTasks; ++i) {
+      if (c[i] < 0) continue;
+      const float4 h = make_float4(tf32_hi(v[i][0]), tf32_hi(v[i][1]), tf32_hi(v[i][2]), tf32_hi(v[i][3]));
+      *reinterpret_cast<float4*>(bh + o[i]) = h;
+      *reinterpret_cast<float4*>(bl + o[i]) =
+          make_float4(v[i][0] - h.x, v[i][1] - h.y, v[i][2] - h.z, v[i][3] - h.w);
+    }
+  }
+};
 
 struct T32Args {
   const Tile* tiles;
@@ -243,9 +287,12 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         umma_commit(&ctl.tfull[acc]);
       }
     }
-  } else if (warp < 8) {
+  } else if (warp < 2 + kSplitWarps) {
     // split warps: table tile in place -> hi, lo; analysis: X -> X^T hi/lo; synthesis: C^T in place
     const int pt = threadIdx.x - 64;
+    const bool pre = ANA && nmma * (kTK / 4) <= kXtTasks * kSplitThreads;
+    XtPlan xp;
+    xp.init(pre ? nmma : 0, pt);
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
@@ -255,7 +302,9 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         const int s = it % kStages, n = it / kStages;
         if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
         split_inplace(sA_hi(s), sA_lo(s), kTTile, pt);
-        if (ANA)
+        if (ANA && pre)
+          xp.run(reinterpret_cast<const float*>(sX(s)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s));
+        else if (ANA)
           split_xt(reinterpret_cast<const float*>(sX(s)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s), pt);
         else
           split_inplace(sB_hi(s), sB_lo(s), bbytes, pt);
@@ -265,7 +314,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
     }
   } else {
     // epilogue: drain the accumulator of every tile of this CTA (warp 8 + q reads lanes 32q..)
-    const int q = warp - 8;
+    const int q = warp & 3;   // a warp reaches only TMEM lanes 32 (warp % 4) ..
     int lt = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
       const Tile tl = a.tiles[t];
