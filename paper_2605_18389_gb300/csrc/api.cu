@@ -47,6 +47,10 @@ int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, i
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st, colscale);
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st, colscale);
   if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st, colscale);
+  if (g.merged_heat && !xsplit) {
+    const int rc = launch_heat_merged(g, nf, X, Y, ldc, st, colscale);
+    if (rc != SHOT_ERR_UNSUPPORTED) return rc;
+  }
   if (g.fused_heat) {
     const int rc = launch_heat_tc(g, nf, X, Y, ldc, st, colscale, xsplit);
     if (rc != SHOT_ERR_UNSUPPORTED) return rc;
@@ -668,6 +672,8 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     g->ana_transposed = (e && e[0] == '1') ? 1 : 0;
     e = getenv("SHOT_IDFT_PERSISTENT");   // 0: one item per CTA for the update half-steps too
     g->idft_nonpersistent = (e && e[0] == '0') ? 1 : 0;
+    e = getenv("SHOT_MERGED_HEAT");   // 1: analysis + synthesis of a heat application in one persistent kernel
+    g->merged_heat = (e && e[0] == '1') ? 1 : 0;
     e = getenv("SHOT_TC_STAGES");   // 1..4 fixes the analysis pipeline depth instead of the autotuner
     g->tc_stages_override = (e && e[0] >= '1' && e[0] <= '4') ? e[0] - '0' : 0;
   }

@@ -988,6 +988,322 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
   if (threadIdx.x == 0 && ctl.abort) atomicExch(ha.err, SHOT_ERR_TIMEOUT);
 }
 
+// ---------------------------------------------------------------------------------
+// Merged heat kernel: each persistent CTA owns whole (m, p) blocks and runs both contractions
+// for them, the coefficients C^T going through global memory (L2) as in the two-kernel path:
+//   analysis  C^T = h_l Pbar X   (block b's table rows from DRAM, the split spectra operand
+//                                 built by eight converter warps as in k_legendre_tc)
+//   synthesis Y = Pbar^T C       (the same table rows again, shortly after: from L2)
+// Units run in the order A1, A2, S1, A3, S2, ..., Ak, S(k-1), Sk (A = analysis of a block,
+// S = its synthesis), so that the write-back of a block's coefficients (epilogue -> global ->
+// TMA) is hidden behind the next block's analysis.  The producer loads a synthesis unit's C^T
+// only after the epilogue has stored it: the epilogue threads fence their global stores for the
+// async proxy and arrive on cready[i & 1] (two barriers alternate, so a producer wait never
+// sees a phase two blocks ahead).  Up to 32 fields ([B_hi | B_lo] as one operand of N = 128).
+struct MergedArgs {
+  const int* order;   // blocks with rows, largest first
+  int nwork;
+  const int* M;
+  const long long* row_off;
+  int nh, ldc, ncols, nmma;
+  const float* h;                 // h_l
+  const ProbState* colscale;      // per-field factor of unscaled spectra, or nullptr
+  __nv_bfloat16* ct_hi;           // C^T [blk][nmma_cap][ldi] (hi, lo)
+  __nv_bfloat16* ct_lo;
+  int nmma_cap, ldi;
+  float* Y;                       // [blk][jh][ldc]
+  int* err;
+};
+
+struct MergedSmem {
+  uint64_t full[kMaxStages], empty[kMaxStages];
+  uint64_t fullB[3], bempty[3];   // split spectra ring
+  uint64_t tfull[2], tempty[2];
+  uint64_t cready[2];
+  uint32_t tmem;
+  int abort;
+};
+
+// unit u of a CTA with k blocks: (block index within the CTA's list, synthesis?)
+__device__ __forceinline__ void merged_unit(int u, int k, int& i, bool& syn) {
+  if (u == 0) { i = 0; syn = false; }
+  else if (u == 2 * k - 1) { i = k - 1; syn = true; }
+  else if (u & 1) { i = (u + 1) / 2; syn = false; }
+  else { i = u / 2 - 1; syn = true; }
+}
+
+constexpr int kMgConvWarps = 8;
+constexpr int kMgThreads = 32 * (2 + kMgConvWarps + 4);
+constexpr int kMgBR = 3;
+
+template <int kStages>
+__global__ void __launch_bounds__(kMgThreads, 1) k_heat_merged(
+    const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,   // table, 128-row boxes
+    const __grid_constant__ CUtensorMap ts_hi, const __grid_constant__ CUtensorMap ts_lo,   // table, 64-row boxes
+    const __grid_constant__ CUtensorMap tx,                                                  // FP32 spectra
+    const __grid_constant__ CUtensorMap tc_hi, const __grid_constant__ CUtensorMap tc_lo,   // C^T
+    MergedArgs a) {
+  extern __shared__ uint8_t smraw[];
+  __shared__ MergedSmem ctl;
+  __shared__ float cscale[256];
+  uint8_t* base = align1k(smraw);
+  const int nmma = a.nmma, nh = a.nh;
+  const int bbytes = mn_atoms(nmma) * kXsBoxBytes;   // analysis B atoms (hi or lo)
+  const int xbytes = nmma * kBK * 4;                 // FP32 spectra tile = synthesis C^T hi + lo
+  const int sbytes = 2 * kATileBytes + xbytes;
+  auto sA_hi = [&](int s) { return base + s * sbytes; };
+  auto sA_lo = [&](int s) { return base + s * sbytes + kATileBytes; };
+  auto sX = [&](int s) { return base + s * sbytes + 2 * kATileBytes; };   // ana: X; syn: C^T hi then lo
+  uint8_t* sB = base + kStages * sbytes;                                   // ring: [hi atoms][lo atoms]
+  const int ncat = 2 * 64 * mn_atoms(nmma);
+  const uint32_t ncols_alloc = tmem_cols_for(ncat);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int kConv = 32 * kMgConvWarps;
+  constexpr int kEpiWarp0 = 2 + kMgConvWarps;
+  const int G = gridDim.x;
+  const int rounds = (a.nwork + G - 1) / G;
+  int kblk = 0;   // blocks of this CTA
+  for (int r = 0; r < rounds; ++r)
+    if (heat_work(r, blockIdx.x, G) < a.nwork) ++kblk;
+  auto blk_of = [&](int i) { return a.order[heat_work(i, blockIdx.x, G)]; };
+  const int nunits = 2 * kblk;
+  const int nkbA = (nh + kBK - 1) / kBK;
+  const int nnt = (nh + kBM - 1) / kBM;
+
+  for (int c = threadIdx.x; c < nmma; c += blockDim.x)
+    cscale[c] = (a.colscale && c < a.ncols) ? (float)a.colscale[c >> 1].beta : 1.f;
+  for (int o = threadIdx.x * 16; o < kMgBR * 2 * bbytes; o += blockDim.x * 16)   // pad columns stay zero
+    *reinterpret_cast<uint4*>(sB + o) = make_uint4(0, 0, 0, 0);
+  fence_async_smem();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&ctl.full[s], 1);
+      mbar_init(&ctl.empty[s], 1);
+    }
+    for (int b = 0; b < kMgBR; ++b) {
+      mbar_init(&ctl.fullB[b], kConv);
+      mbar_init(&ctl.bempty[b], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl.tfull[b], 1);
+      mbar_init(&ctl.tempty[b], 128);
+      mbar_init(&ctl.cready[b], 128);
+    }
+    ctl.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&ctl.tmem, 2 * ncols_alloc);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = ctl.tmem;
+  volatile int* abort = &ctl.abort;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int it = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        int i;
+        bool syn;
+        merged_unit(u, kblk, i, syn);
+        const int blk = blk_of(i), M = a.M[blk], ro = (int)a.row_off[blk];
+        if (!syn) {
+          const int nmt = (M + kBM - 1) / kBM;
+          for (int mt = 0; mt < nmt && ok; ++mt)
+            for (int kb = 0; kb < nkbA; ++kb, ++it) {
+              const int s = it % kStages, n = it / kStages;
+              if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
+              mbar_arrive_expect_tx(&ctl.full[s], 2 * kATileBytes + xbytes);
+              tma_load_2d(sA_hi(s), &ta_hi, &ctl.full[s], kb * kBK, ro + mt * kBM);
+              tma_load_2d(sA_lo(s), &ta_lo, &ctl.full[s], kb * kBK, ro + mt * kBM);
+              tma_load_2d(sX(s), &tx, &ctl.full[s], 0, blk * nh + kb * kBK);
+            }
+        } else {
+          // the block's coefficients are in global memory once its analysis epilogue arrived
+          if (!(ok = mbar_wait(&ctl.cready[i & 1], (i >> 1) & 1, abort))) break;
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+          const int nkbS = (M + kBK - 1) / kBK;
+          for (int nt = 0; nt < nnt && ok; ++nt)
+            for (int kb = 0; kb < nkbS; ++kb, ++it) {
+              const int s = it % kStages, n = it / kStages;
+              if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
+              mbar_arrive_expect_tx(&ctl.full[s], 2 * kATileBytes + xbytes);
+              const int y = ro + kb * kBK, x = nt * kBM;
+              tma_load_2d(sA_hi(s), &ts_hi, &ctl.full[s], x, y);
+              tma_load_2d(sA_hi(s) + kATileBytes / 2, &ts_hi, &ctl.full[s], x + 64, y);
+              tma_load_2d(sA_lo(s), &ts_lo, &ctl.full[s], x, y);
+              tma_load_2d(sA_lo(s) + kATileBytes / 2, &ts_lo, &ctl.full[s], x + 64, y);
+              tma_load_2d(sX(s), &tc_hi, &ctl.full[s], kb * kBK, blk * a.nmma_cap);
+              tma_load_2d(sX(s) + nmma * kBK * 2, &tc_lo, &ctl.full[s], kb * kBK, blk * a.nmma_cap);
+            }
+        }
+      }
+      for (int k = it > kStages ? it - kStages : 0; k < it; ++k)
+        mbar_drain(&ctl.full[k % kStages], (k / kStages) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t id_ana = idesc_bf16(kBM, nmma) | (1u << 16);   // B MN-major
+      const uint32_t id_cat = idesc_bf16(kBM, ncat) | (1u << 16);
+      const uint32_t id_syn = idesc_bf16_amn(kBM, nmma);            // A MN-major
+      int it = 0, ia = 0, lt = 0;
+      bool ok = true;
+      for (int u = 0; u < nunits && ok; ++u) {
+        int i;
+        bool syn;
+        merged_unit(u, kblk, i, syn);
+        const int blk = blk_of(i), M = a.M[blk];
+        const int ntile = syn ? nnt : (M + kBM - 1) / kBM;
+        const int nkb = syn ? (M + kBK - 1) / kBK : nkbA;
+        for (int tile = 0; tile < ntile && ok; ++tile, ++lt) {
+          const int acc = lt & 1, uu = lt >> 1;
+          if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (uu - 1) & 1, abort))) break;
+          tc_fence_after();
+          const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
+          for (int kb = 0; kb < nkb; ++kb, ++it) {
+            const int s = it % kStages, n = it / kStages;
+            const int sb = ia % kMgBR;
+            ok = mbar_wait(&ctl.full[s], n & 1, abort);
+            if (ok && !syn) ok = mbar_wait(&ctl.fullB[sb], (ia / kMgBR) & 1, abort);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
+            if (!syn) {
+              const uint32_t bh = smem_u32(sB + sb * 2 * bbytes);
+#pragma unroll
+              for (int k = 0; k < kBK / 16; ++k) {
+                const uint64_t b_cat = desc_sw128_mnmajor(bh + k * 2048, kXsBoxBytes, 1024);
+                umma_bf16(d, desc_sw128_kmajor(ah + k * 32), b_cat, id_cat, (kb | k) != 0);
+                umma_bf16(d, desc_sw128_kmajor(al + k * 32), b_cat, id_ana, 1);
+              }
+              umma_commit(&ctl.empty[s]);
+              umma_commit(&ctl.bempty[sb]);
+              ++ia;
+            } else {
+              const uint32_t bh = smem_u32(sX(s)), bl = bh + (uint32_t)(nmma * kBK * 2);
+#pragma unroll
+              for (int k = 0; k < kBK / 16; ++k) {
+                const uint64_t a_h = desc_sw128_mnmajor(ah + k * 2048, kATileBytes / 2, 1024);
+                const uint64_t a_l = desc_sw128_mnmajor(al + k * 2048, kATileBytes / 2, 1024);
+                const uint64_t b_h = desc_sw128_kmajor(bh + k * 32), b_l = desc_sw128_kmajor(bl + k * 32);
+                umma_bf16(d, a_h, b_h, id_syn, (kb | k) != 0);
+                umma_bf16(d, a_h, b_l, id_syn, 1);
+                umma_bf16(d, a_l, b_h, id_syn, 1);
+              }
+              umma_commit(&ctl.empty[s]);
+            }
+          }
+          if (!ok) break;
+          umma_commit(&ctl.tfull[acc]);
+        }
+      }
+    }
+  } else if (warp < kEpiWarp0) {
+    // converters: the analysis stages' FP32 spectra tiles -> [B_hi | B_lo] ring buffers
+    const int pt = threadIdx.x - 64;
+    XConv xc;
+    xc.init(nmma, a.ncols, pt, kConv);
+    int it = 0, ia = 0;
+    bool ok = true;
+    for (int u = 0; u < nunits && ok; ++u) {
+      int i;
+      bool syn;
+      merged_unit(u, kblk, i, syn);
+      const int blk = blk_of(i), M = a.M[blk];
+      if (syn) {   // the synthesis stages take their operands straight from TMA
+        it += nnt * ((M + kBK - 1) / kBK);
+        continue;
+      }
+      const int nmt = (M + kBM - 1) / kBM;
+      for (int mt = 0; mt < nmt && ok; ++mt)
+        for (int kb = 0; kb < nkbA; ++kb, ++it, ++ia) {
+          const int s = it % kStages, n = it / kStages;
+          const int sb = ia % kMgBR, nb = ia / kMgBR;
+          if (!(ok = mbar_wait(&ctl.full[s], n & 1, abort))) break;
+          if (nb > 0 && !(ok = mbar_wait(&ctl.bempty[sb], (nb - 1) & 1, abort))) break;
+          uint8_t* bh = sB + sb * 2 * bbytes;
+          xc.run(reinterpret_cast<const float*>(sX(s)), kb * kBK, nh, bh, bh + bbytes);
+          fence_async_smem();
+          mbar_arrive(&ctl.fullB[sb]);
+        }
+    }
+  } else {
+    // epilogue: analysis tiles -> C^T (bf16 hi/lo, global), synthesis tiles -> Y
+    const int q = warp & 3;   // a warp reaches only TMEM lanes 32 (warp % 4) ..
+    int lt = 0;
+    bool ok = true;
+    for (int u = 0; u < nunits && ok; ++u) {
+      int i;
+      bool syn;
+      merged_unit(u, kblk, i, syn);
+      const int blk = blk_of(i), M = a.M[blk];
+      const int m = blk >> 1, p = blk & 1;
+      const int ntile = syn ? nnt : (M + kBM - 1) / kBM;
+      for (int tile = 0; tile < ntile; ++tile, ++lt) {
+        const int acc = lt & 1, uu = lt >> 1;
+        if (!(ok = mbar_wait_warp(&ctl.tfull[acc], uu & 1, abort))) break;
+        tc_fence_after();
+        const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc) + ((uint32_t)(q * 32) << 16);
+        const int row = tile * kBM + q * 32 + lane;
+        if (!syn) {
+          const float hl = (a.h && row < M) ? a.h[m + p + 2 * row] : 1.f;
+          for (int c0 = 0; c0 < nmma; c0 += 16) {
+            float v[16], w[16];
+            tmem_ld16(d + (uint32_t)c0, v);
+            tmem_ld16(d + (uint32_t)(ncat / 2 + c0), w);   // + A_hi B_lo
+            if (row < M) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const int c = c0 + e;
+                if (c < a.ncols) {
+                  const float val = (v[e] + w[e]) * hl * cscale[c];
+                  const __nv_bfloat16 hi = __float2bfloat16_rn(val);
+                  const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
+                  const size_t o = ((size_t)blk * a.nmma_cap + c) * a.ldi + row;
+                  a.ct_hi[o] = hi;
+                  a.ct_lo[o] = lo;
+                }
+              }
+            }
+          }
+        } else {
+          float* yrow = a.Y + ((size_t)blk * nh + row) * a.ldc;
+          for (int c0 = 0; c0 < nmma; c0 += 16) {
+            float v[16];
+            tmem_ld16(d + (uint32_t)c0, v);
+            if (row < nh) {
+              if (c0 + 16 <= a.ncols) {
+#pragma unroll
+                for (int e = 0; e < 16; e += 4)
+                  *reinterpret_cast<float4*>(yrow + c0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+              } else {
+#pragma unroll
+                for (int e = 0; e < 16; ++e)
+                  if (c0 + e < a.ncols) yrow[c0 + e] = v[e];
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&ctl.tempty[acc]);
+      }
+      if (ok && !syn) {   // this block's C^T is stored: hand it to the producer's TMA loads
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        mbar_arrive(&ctl.cready[i & 1]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(taddr, 2 * ncols_alloc);
+  }
+  if (threadIdx.x == 0 && ctl.abort) atomicExch(a.err, SHOT_ERR_TIMEOUT);
+}
+
 // FP32 coefficients C[row_off + i][ldc] -> bf16 hi/lo C^T[blk][nmma_cap][ldi] (synthesis input)
 __global__ void k_c_to_ct(int nblk, const int* __restrict__ Mrows, const long long* __restrict__ row_off,
                           const float* __restrict__ C, int ldc, int ncols, __nv_bfloat16* __restrict__ hi,
@@ -1184,6 +1500,40 @@ int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cud
   ProfScope prof(PK_ANALYSIS, st);
   count_launch();
   kern<<<grid, kTcThreads, smem, st>>>(mh, ml, mx, mx2, ha);
+  SHOT_CUDA(cudaGetLastError());
+  return SHOT_OK;
+}
+
+// Merged heat kernel (k_heat_merged) for the BF16X3 heat applications, up to 32 fields with
+// FP32 spectra.  Returns SHOT_ERR_UNSUPPORTED (without launching) otherwise.
+int launch_heat_merged(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
+                       const ProbState* colscale) {
+  const Workspace& w = g.ws;
+  const int nmma = tc_nmma(nf);
+  if (nmma > 64 || g.nwork == 0 || nmma > w.nmma_cap) return SHOT_ERR_UNSUPPORTED;
+  const size_t sbytes = 2 * kATileBytes + (size_t)nmma * kBK * 4;
+  const size_t ring = (size_t)kMgBR * 2 * mn_atoms(nmma) * kXsBoxBytes;
+  int stages = kMaxStages;
+  while (stages > 2 && 1024 + stages * sbytes + ring + 2048 > 227 * 1024) --stages;
+  const size_t smem = 1024 + stages * sbytes + ring;
+  if (smem + 2048 > 227 * 1024) return SHOT_ERR_UNSUPPORTED;
+  int rc;
+  CUtensorMap ah, al, sh, sl, mx, ch, cl;
+  if ((rc = make_map(&ah, g.tab_hi, g.nh, g.rows_total, g.ldt, kBM))) return rc;
+  if ((rc = make_map(&al, g.tab_lo, g.nh, g.rows_total, g.ldt, kBM))) return rc;
+  if ((rc = make_map(&sh, g.tab_hi, g.nh, g.rows_total, g.ldt, 64))) return rc;
+  if ((rc = make_map(&sl, g.tab_lo, g.nh, g.rows_total, g.ldt, 64))) return rc;
+  if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
+  if ((rc = make_map(&ch, w.ct_hi, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
+  if ((rc = make_map(&cl, w.ct_lo, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
+  MergedArgs ma{g.blk_order_d, g.nwork, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma, g.h_d, colscale,
+                w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Y, w.dev_int + 4};
+  auto kern = stages == 4 ? k_heat_merged<4> : stages == 3 ? k_heat_merged<3> : k_heat_merged<2>;
+  SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = g.nwork < g.num_sms ? g.nwork : g.num_sms;
+  ProfScope prof(PK_ANALYSIS, st);
+  count_launch();
+  kern<<<grid, kMgThreads, smem, st>>>(ah, al, sh, sl, mx, ch, cl, ma);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }

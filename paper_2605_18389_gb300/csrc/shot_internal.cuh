@@ -161,6 +161,7 @@ struct Grid {
   int ntiles_ana_t = 0;
   int nwork = 0, nmt_max = 0, kc_max = 0;
   int fused_heat = 0;           // BF16X3 table grids: fused analysis + synthesis kernel
+  int merged_heat = 0;          // SHOT_MERGED_HEAT=1: BF16X3 heat applications in k_heat_merged
   int split_spectra = 0;        // BF16X3 table grids: the solver keeps bf16 hi/lo spectra
   int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core analysis (0 = tuned)
   int idft_nonpersistent = 0;   // SHOT_IDFT_PERSISTENT=0: update half-steps use the one-item-per-CTA k_idft
@@ -249,6 +250,8 @@ int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd = nullptr);
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
                        bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr, int xsplit = 0);
 int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
+int launch_heat_merged(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
+                       const ProbState* colscale);
 int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
                          bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
 int launch_c_to_ct32(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);

@@ -133,3 +133,56 @@ def test_transposed_analysis_matches_oracle(monkeypatch, nlat, nf):
     ref = sk.divergence(og, p64, q64, 0.05, T=40, delta=0.0, C=10)
     assert np.all(r["status"] == 0) and np.all(ref["status"] == 0)
     assert np.all(s_err_prec(r["S"], ref["S"], ref["runs"]["ot"][:2], TOL, "bf16x3") <= 1.0)
+
+
+def _merged_grid(monkeypatch, merged, nlat, nlon=None, lmax=-1):
+    monkeypatch.setenv("SHOT_MERGED_HEAT", "1" if merged else "0")
+    return shot.shot_grid_init(nlat, nlon, lmax, shot.SHOT_BF16X3)
+
+
+@pytest.mark.parametrize("nlat,nlon,lmax,nf,t", [(8, None, -1, 1, 0.1), (33, 72, -1, 2, 0.02),
+                                                 (64, None, -1, 24, 3e-3), (180, None, -1, 5, 1e-3),
+                                                 (20, 45, 13, 3, 0.05), (256, None, -1, 32, 1e-3)])
+def test_merged_heat_apply_matches_oracle(monkeypatch, nlat, nlon, lmax, nf, t):
+    """Analysis and synthesis of each block in one persistent CTA (SHOT_MERGED_HEAT=1)."""
+    g = _merged_grid(monkeypatch, True, nlat, nlon, lmax)
+    og = OGrid(nlat, nlon, None if lmax == -1 else lmax)
+    f, f64 = f32(np.random.default_rng(23 * nlat + nf).uniform(size=(nf, og.nlat, og.nlon)))
+    out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
+    shot.shot_heat_apply(g, t, torch.from_numpy(f).cuda(), out)
+    shot.shot_grid_check(g)   # no bounded device-side wait expired
+    shot.shot_grid_free(g)
+    assert rel_max(out.cpu().numpy(), osht.heat_apply(og, f64, t)) < TOL
+
+
+@pytest.mark.parametrize("nlat,nf", [(96, 24), (180, 7), (720, 24)])
+def test_merged_agrees_with_two_kernel_path_bitwise(monkeypatch, nlat, nf):
+    """The merged kernel issues the two-kernel path's MMAs in the same K order and the same
+    epilogue arithmetic: the heat applications agree bit for bit."""
+    og = OGrid(nlat)
+    f = np.random.default_rng(nlat).uniform(size=(nf, og.nlat, og.nlon)).astype(np.float32)
+    outs = []
+    for merged in (True, False):
+        g = _merged_grid(monkeypatch, merged, nlat)
+        out = torch.empty((nf, og.nlat, og.nlon), device="cuda")
+        shot.shot_heat_apply(g, 1e-3, torch.from_numpy(f).cuda(), out)
+        shot.shot_grid_check(g)
+        outs.append(out.cpu().numpy())
+        shot.shot_grid_free(g)
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_merged_divergence_matches_oracle(monkeypatch):
+    nlat, eps, tau, T = 64, 0.02, 1.0, 30
+    g = _merged_grid(monkeypatch, True, nlat)
+    og = OGrid(nlat)
+    p, q = inputs.pairs("paper_uniform", 2400, 2, og.x, og.nlon, og.a_ring, masses=True)
+    p32, p64 = f32(p)
+    q32, q64 = f32(q)
+    rc, r = shot.shot_divergence(g, torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), eps, tau,
+                                 max_iter=T, tol=0.0, check_every=10)
+    shot.shot_grid_free(g)
+    ref = sk.divergence(og, p64, q64, eps, tau, T=T, delta=0.0, C=10)
+    assert np.all(r["status"] == ref["status"])
+    ot_pq = ref["runs"]["ot"][:2]
+    assert np.all(s_err_prec(r["S"], ref["S"], ot_pq, TOL, "bf16x3") <= 1.0)
