@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "tf32x3", "fp32"])
+    ap.add_argument("--workload", default="divergence", choices=["divergence", "multi", "grad"],
+                    help="divergence: the headline (720x1440, 24 problems); multi: 4 grids x 3 tau x 8 pairs "
+                         "in one shot_divergence_multi solve; grad: shot_divergence_grad at 256x512, 16 pairs")
     ap.add_argument("--no-compare", action="store_true", help="skip the FP32 comparison pass")
     ap.add_argument("--legendre", default="table", choices=["table", "recurrence"])
     ap.add_argument("--tau", type=float, default=math.inf)
@@ -352,10 +355,96 @@ def cpu_baseline(args, x, w, a_ring):
                       f"grid/table set-up excluded", "seconds": dt}
 
 
+def timed_calls(torch, fn, warmup, steps, index):
+    """warm-up calls, then `steps` calls between CUDA events on the current stream with the
+    clocks sampled meanwhile; returns (ms per call, clocks)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(index)
+    clk.start()
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    return e0.elapsed_time(e1) / steps, clocks
+
+
+def run_multi(args):
+    """Many pair sets on uneven grids in one solve (shot_divergence_multi): grids 64x128, 96x192,
+    128x256, 180x360; tau in {0.1, 1, 10}; 8 pairs per (grid, tau) -> 96 pairs, 288 OT problems;
+    t = 2.5e-3; vMF mixtures with a zonal modulation and masses U[0.5, 2]; a fixed number of
+    iterations (no convergence stop).  One step = one Alg. 1 iteration of all 288 problems."""
+    import torch
+    from paper_2605_18389_gb300 import shot, inputs
+    prec = {"fp32": shot.SHOT_FP32, "bf16x3": shot.SHOT_BF16X3, "tf32x3": shot.SHOT_TF32X3}[args.precision]
+    t = 2.5e-3
+    eps = 4 * t
+    T = 200
+    grids, sets = [], []
+    for gi, nlat in enumerate((64, 96, 128, 180)):
+        g = shot.shot_grid_init(nlat, 2 * nlat, -1, prec)
+        grids.append(g)
+        x, w, a = shot.shot_grid_nodes(g)
+        for ti, tau in enumerate((0.1, 1.0, 10.0)):
+            p, q = inputs.pairs("vmf8_zonal", 3000 + 10 * gi + ti, 8, x, 2 * nlat, a, masses=True, dtype=np.float32)
+            sets.append(dict(grid=g, p=torch.from_numpy(p).cuda(), q=torch.from_numpy(q).cuda(), eps=eps, tau=tau))
+    ms, clocks = timed_calls(torch, lambda: shot.shot_divergence_multi(sets, max_iter=T, tol=0.0, check_every=10),
+                             1, max(1, args.steps // T), 0)
+    rc, outs = shot.shot_divergence_multi(sets, max_iter=T, tol=0.0, check_every=10)
+    for g in grids:
+        shot.shot_grid_free(g)
+    print(json.dumps({"metric": "multi-grid heat-Sinkhorn iters/s (288 problems on 4 grids, one solve)",
+                      "value": T / (ms / 1e3), "unit": "iters/s", "ms_per_solve": ms, "iterations_per_solve": T,
+                      "problem_iters_per_s": 288 * T / (ms / 1e3), "dtype": DTYPE[args.precision],
+                      "data": "synthetic", "config": {"workload": "multi: grids 64/96/128/180 (nlon = 2 nlat), "
+                                                                  "tau 0.1/1/10, 8 pairs each, t = 2.5e-3, vmf8_zonal"},
+                      "clocks": clocks, "status": {"rc": int(rc), "S_finite": bool(all(np.all(np.isfinite(o["S"]))
+                                                                                       for o in outs))}}))
+    return 0
+
+
+def run_grad(args):
+    """The gradient of the Sinkhorn divergence (shot_divergence_grad, unrolled through T = 400
+    iterations with checkpoints every 20) at 256x512 for 16 pairs (48 forward problems),
+    t = 1e-3, vMF mixtures of 8 components."""
+    import torch
+    from paper_2605_18389_gb300 import shot, inputs
+    prec = {"fp32": shot.SHOT_FP32, "bf16x3": shot.SHOT_BF16X3, "tf32x3": shot.SHOT_TF32X3}[args.precision]
+    nlat, T, ck = 256, 400, 20
+    g = shot.shot_grid_init(nlat, 2 * nlat, -1, prec)
+    x, w, a = shot.shot_grid_nodes(g)
+    p, q = inputs.pairs("vmf8", 4000, 16, x, 2 * nlat, a, dtype=np.float32)
+    pt, qt = torch.from_numpy(p).cuda(), torch.from_numpy(q).cuda()
+    res = {}
+
+    def call():
+        res["r"] = shot.shot_divergence_grad(g, pt, qt, 4e-3, max_iter=T, checkpoint_every=ck,
+                                             mode=shot.SHOT_GRAD_UNROLLED)
+    ms, clocks = timed_calls(torch, call, 1, max(1, min(args.steps, 5)), 0)
+    rc, r = res["r"]
+    ok = bool(np.all(np.isfinite(r["grad"].cpu().numpy())))
+    shot.shot_grid_free(g)
+    print(json.dumps({"metric": "divergence gradients/s (256x512, 16 pairs, T = 400 unrolled, checkpoints every 20)",
+                      "value": 1e3 / ms, "unit": "gradients/s", "ms_per_gradient": ms,
+                      "forward_iters_per_s": T / (ms / 1e3), "dtype": DTYPE[args.precision], "data": "synthetic",
+                      "config": {"workload": "grad: 256x512 GL, t = 1e-3, 16 pairs -> 48 forward problems, vmf8"},
+                      "clocks": clocks, "status": {"rc": int(rc), "grad_finite": ok}}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "multi":
+        return run_multi(args)
+    if args.workload == "grad":
+        return run_grad(args)
     import torch
     from paper_2605_18389_gb300 import shot, inputs
     from paper_2605_18389_gb300 import dist as sd
