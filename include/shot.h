@@ -67,6 +67,7 @@ extern "C" {
 /* ---- solver flags -------------------------------------------------------- */
 #define SHOT_FLAG_NORM_L1     0x1  /* check sum_i a_i|u_i(Kv)_i - p_i| / sum_i a_i p_i instead of the relative L2 */
 #define SHOT_FLAG_WARM_START  0x2  /* u and v hold the initial scalings instead of 1 */
+#define SHOT_FLAG_POTENTIALS  0x4  /* return the potentials phi = eps log u, psi = eps log v in u, v */
 
 typedef struct shot_grid_s* shot_grid;
 
@@ -180,7 +181,12 @@ int shot_sht_synthesis(shot_grid g, const float* coeffs, float* out, int nfields
  *               unbalanced branch with the translation-invariant step
  *   max_iter    T;  tol = delta;  check_every = C (0 disables the periodic check)
  *   flags       SHOT_FLAG_* ; WARM_START reads u, v as the initial scalings
- *   u, v        device [batch][nlat][nlon] float32 outputs (inputs with WARM_START)
+ *   u, v        device [batch][nlat][nlon] float32 outputs (inputs with WARM_START): the
+ *               scalings, or with SHOT_FLAG_POTENTIALS the potentials eps log u, eps log v.
+ *               The solver keeps each scaling as an FP32 buffer times an FP64 factor
+ *               e^{la}, so the iteration and ot/err/mass stay valid when eps log u lies
+ *               outside FP32's exponent range (unbalanced, large tau/eps, unequal masses);
+ *               only the returned scalings then saturate to 0 or inf.
  *   ot          host [batch] or NULL: Alg. 1's return (dual form of App. C.2)
  *   ot_dual     host [batch] or NULL: ot - eps * m(pi)
  *   mass_pi     host [batch] or NULL: m(pi) = sum_i a_i u_i (K v)_i

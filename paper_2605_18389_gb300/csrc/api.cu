@@ -5,9 +5,12 @@
 // then v likewise),  then the gauge (balanced: s = sum u, u/s, s v) or the
 // translation-invariant step (c = tau/2 (log sum a p u^{-eps/tau} - log sum a q v^{-eps/tau}),
 // u e^{c/eps}, v e^{-c/eps}).  The rescalings are never applied to the stored buffers
-// during the loop: each problem keeps u_true = alpha u_buf and v_true = beta v_buf, and
-// the forward ring DFT multiplies v_buf by beta on load.  Every C iterations the relative
-// marginal error of App. C.3 is evaluated on the device and problems below tol stop.
+// during the loop: each problem keeps u_true = e^{la} u_buf and v_true = e^{lb} v_buf with
+// la, lb in FP64, and every half-step transforms the unscaled buffer of the other side, so
+// that no FP32 quantity carries a factor e^{phi/eps}.  The update multiplies its ratio by
+// an FP32 factor (ru, rv) that holds the buffer's mean level near 1; its exact effect goes
+// into la or lb.  Every C iterations the relative marginal error of App. C.3 is evaluated
+// on the device and problems below tol stop.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -93,10 +96,11 @@ __device__ __forceinline__ double wsum(double v) {
 // problem; the last block to finish (ticket in dev_int[12], reset by that block) counts
 // the problems still active and advances the iteration counter.
 constexpr int kRedThreads = 128;
+constexpr double kLn2 = 0.69314718055994530942;
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int nh, const double* __restrict__ part,
                                                         ProbState* ps, int* dev_int, double eps, double tol,
-                                                        int norm_l1) {
+                                                        int norm_l1, double lnpix) {
   __shared__ double red[kRedThreads / 32][NPART];
   __shared__ int last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -120,7 +124,9 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int
 #pragma unroll
       for (int i = 0; i < NPART; ++i) red[wid][i] = s[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (wid == 0) {
+      // every lane of warp 0 forms the totals; the scalar step runs on its lanes so that the
+      // FP64 logarithms (and exponentials) of one step run side by side, one per lane
 #pragma unroll
       for (int i = 0; i < NPART; ++i) {
         double t = 0.0;
@@ -128,47 +134,88 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int
         s[i] = t;
       }
       if (mode == RED_U || mode == RED_V) {
-        if (s[2] > 0.0) {
-          P->status = SHOT_ERR_NONPOSITIVE;
-          P->active = 0;
-          P->iters = kdone + 1;
-        } else if (s[3] > 0.0) {
-          P->status = SHOT_ERR_NONFINITE;
-          P->active = 0;
-          P->iters = kdone + 1;
-        } else if (mode == RED_U) {
-          P->su = s[0];
-        } else {
-          double al, be;
-          if (P->balanced) {
-            al = 1.0 / P->su;
-            be = P->su;
-          } else {
-            const double c = 0.5 * P->tau * (log(P->su) - log(s[0]));
-            al = exp(c / eps);
-            be = exp(-c / eps);
+        const int bal = P->balanced;
+        int st = SHOT_OK;
+        if (s[2] > 0.0) st = SHOT_ERR_NONPOSITIVE;
+        else if (s[3] > 0.0) st = SHOT_ERR_NONFINITE;
+        // the new buffer w_buf = (r m / K x_buf)^gamma of this half-step relates to the true
+        // scaling (m / K x_true)^gamma, x_true = e^{lx} x_buf, by w_true = e^{lw} w_buf;
+        // r = 2^e, so log r is exact
+        const double lx = log(lane == 0 ? s[0] : (lane == 1 ? (bal ? s[0] : s[1]) : 1.0));
+        const double lsum = __shfl_sync(0xffffffffu, lx, 0), ltot = __shfl_sync(0xffffffffu, lx, 1);
+        const double gam = (double)P->gamma;
+        const int e = (mode == RED_U) ? P->eu : P->ev;
+        const double lw = -gam * ((mode == RED_U ? P->lb : P->la) + e * kLn2);
+        // log of the step's sum over true values: sum w_true (balanced gauge) or
+        // sum a m w_true^{-eps/tau} (translation-invariant step)
+        const double ls = bal ? lw + lsum : -(eps / P->tau) * lw + lsum;
+        // buffer level L = log mean w_buf.  The factors r only keep the FP32 buffers near
+        // level 0 (exactness comes from lw): a half-step's level is about
+        // gamma (log r + A - L_other) with A a slowly varying term of the marginal's and the
+        // kernel's shapes, so each half-step estimates A from what it just produced and the
+        // other side's factor is set as soon as the level it will divide by is known.
+        const double L = ltot - lnpix;
+        const double A = L / gam - e * kLn2 + (mode == RED_U ? P->lvv : P->lvu);
+        const double zr = ((mode == RED_U ? P->qv : P->qu) + L) / kLn2;
+        const int en = (int)fmin(fmax(rint(zr), -100.0), 100.0);
+        if (st == SHOT_OK && !(isfinite(lw) && isfinite(ls) && isfinite(L))) st = SHOT_ERR_NONFINITE;
+        double la = P->la, lb = lw;
+        if (mode == RED_V) {
+          if (bal) {   // u / sum u, v sum u
+            la -= P->lsu;
+            lb += P->lsu;
+          } else {     // c = tau/2 (log su - log sv): u e^{c/eps}, v e^{-c/eps}
+            const double c = 0.5 * P->tau * (P->lsu - ls);
+            la += c / eps;
+            lb -= c / eps;
           }
-          if (!(isfinite(al) && isfinite(be) && al > 0.0 && be > 0.0)) {
-            P->status = SHOT_ERR_NONFINITE;
+        }
+        // e^{la+lb}, e^{la}, e^{lb} side by side on lanes 0..2
+        const double ey = (mode == RED_V) ? exp(lane == 0 ? la + lb : (lane == 1 ? la : (lane == 2 ? lb : 0.0)))
+                                          : 0.0;
+        const double euv = __shfl_sync(0xffffffffu, ey, 0), eu = __shfl_sync(0xffffffffu, ey, 1),
+                     ev = __shfl_sync(0xffffffffu, ey, 2);
+        const float cuv = (float)euv;
+        if (mode == RED_V && st == SHOT_OK && !(isfinite(la) && isfinite(lb) && cuv > 0.f && cuv < INFINITY))
+          st = SHOT_ERR_NONFINITE;
+        if (lane == 0) {
+          if (st != SHOT_OK) {
+            P->status = st;
             P->active = 0;
             P->iters = kdone + 1;
+          } else if (mode == RED_U) {
+            P->la = lw;
+            P->lsu = ls;
+            P->qu = -A;      // next u-step: log ru = -A + (level of the v buffer it divides by)
+            P->lvu = L;
+            P->ev = en;      // this iteration's v-step divides by this u buffer
+            P->rv = ldexpf(1.f, en);
           } else {
-            P->alpha = al;
-            P->beta = be;
+            P->la = la;
+            P->lb = lb;
+            P->qv = -A;
+            P->lvv = L;
+            P->eu = en;
+            P->ru = ldexpf(1.f, en);
+            P->cuv = cuv;
+            P->cu = (float)eu;
+            P->cv = (float)ev;
           }
         }
-      } else if (mode == RED_CHECK) {
-        const double e = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
-        P->err = e;
-        if (e < tol) {
-          P->active = 0;
-          P->iters = kdone;
+      } else if (lane == 0) {
+        if (mode == RED_CHECK) {
+          const double e = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
+          P->err = e;
+          if (e < tol) {
+            P->active = 0;
+            P->iters = kdone;
+          }
+        } else {
+          P->err = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
+          P->mass = s[2];
+          P->ot = s[3];
+          P->ot_dual = s[3] - eps * s[2];
         }
-      } else {
-        P->err = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
-        P->mass = s[2];
-        P->ot = s[3];
-        P->ot_dual = s[3] - eps * s[2];
       }
     }
   }
@@ -200,9 +247,11 @@ __global__ void k_init_probs(int nprob, ProbState* ps, int* dev_int, const doubl
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f < nprob) {
     ProbState P;
-    P.alpha = 1.0;
+    P.la = P.lb = P.lsu = 0.0;
+    P.qu = P.qv = P.lvu = P.lvv = 0.0;
+    P.eu = P.ev = 0;
     P.beta = 1.0;
-    P.su = 0.0;
+    P.ru = P.rv = P.cuv = P.cu = P.cv = 1.f;
     P.err = nan("");
     P.ot = P.ot_dual = P.mass = nan("");
     const double tau = taus[f];
@@ -281,7 +330,7 @@ int reduce(Grid& g, int mode, int nprob, double eps, double tol, int norm_l1, cu
   ProfScope prof(PK_OTHER, st);
   count_launch();
   k_reduce<<<nprob, kRedThreads, 0, st>>>(mode, nprob, g.nh, g.ws.part, reinterpret_cast<ProbState*>(g.ws.probs),
-                              g.ws.dev_int, eps, tol, norm_l1);
+                              g.ws.dev_int, eps, tol, norm_l1, log((double)g.npix));
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }
@@ -297,7 +346,7 @@ struct Solve {
   Grid* g = nullptr;
   int nprob = 0;
   double eps = 0, tol = 0;
-  int C = 0, norm_l1 = 0;
+  int C = 0, norm_l1 = 0, potentials = 0;
   float *u = nullptr, *v = nullptr;
   cudaStream_t st = nullptr;
   int xs = 0;   // spectra kept as bf16 hi/lo (tensor-core operand format)
@@ -329,6 +378,7 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
   s.tol = tol;
   s.C = C;
   s.norm_l1 = (flags & SHOT_FLAG_NORM_L1) ? 1 : 0;
+  s.potentials = (flags & SHOT_FLAG_POTENTIALS) ? 1 : 0;
   s.u = u;
   s.v = v;
   s.st = w.stream;
@@ -361,7 +411,7 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
     if ((rc = autotune(g, nprob, s.st, &up))) return rc;
   }
   if ((rc = launch_heat_mult(g, eps / 4.0, s.st))) return rc;
-  // spectra of the starting v (unscaled; the analysis applies beta per column)
+  // spectra of the starting v
   return launch_dft_fwd(g, v, nprob, nullptr, 0, w.XY, w.ldc, s.st, s.xs);
 }
 
@@ -377,20 +427,19 @@ EpiParams base_ep(Solve& s) {
 }
 
 // nit iterations of Alg. 1, then (optionally) the marginal check; no host synchronisation.
-// X always holds the unscaled ring spectra of the scaling the next heat convolution needs:
-// each half-step's inverse DFT also transforms the scaling it has just produced (fused),
-// and the gauge factor beta of v is applied per column by the next Legendre analysis.
+// X always holds the ring spectra of the buffer the next heat convolution needs: each
+// half-step's inverse DFT also transforms the scaling it has just produced (fused); the
+// buffers' factors e^{la}, e^{lb} enter only the FP64 scalars of k_reduce.
 int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
   Grid& g = *s.g;
   Workspace& w = g.ws;
   const float* const* margP = w.marg;
   const float* const* margQ = w.marg + s.nprob;
-  ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   EpiParams ep = base_ep(s);
   int rc;
   for (int i = 0; i < nit; ++i) {
-    // u-step: u = (p / K(beta v))^gamma, and X := F(u)
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, ps, s.xs))) return rc;
+    // u-step: u = (ru p / K v)^gamma, and X := F(u)
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
     ep.mode = EPI_UPDATE;
     ep.out = s.u;
     ep.marg = margP;
@@ -406,8 +455,8 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
     if ((rc = reduce(g, RED_V, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
   }
-  if (check) {   // K(beta v) from the spectra X, which stay for the next u-step
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, ps, s.xs))) return rc;
+  if (check) {   // K v from the spectra X, which stay for the next u-step
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
     ep.mode = EPI_CHECK;
     ep.other = s.u;
     ep.marg = margP;
@@ -424,9 +473,10 @@ int solve_final_enqueue(Solve& s) {
   EpiParams ep = base_ep(s);
   ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   int rc;
-  // final K v_true for the objective, mass and marginal error; writes u_true, v_true
-  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st, ps, s.xs))) return rc;
+  // final K v for the objective, mass and marginal error; writes u_true, v_true
+  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st, nullptr, s.xs))) return rc;
   ep.mode = EPI_FINAL;
+  ep.potentials = s.potentials;
   ep.out = s.v;
   ep.other = s.u;
   ep.marg = w.marg;

@@ -6,12 +6,14 @@
 // of the given mode and reduces the per-field partial sums of the pair into
 // ep.part[f][jh][NPART]:
 //   EPI_PLAIN   out = K v
-//   EPI_UPDATE  u = p / Kv (balanced) or (p / Kv)^{tau/(tau+eps)}; sums: sum u (gauge) or
-//               sum a p u^{-eps/tau} (translation-invariant step), non-positive and
-//               non-finite counts; when ep.xout is set the new scaling is also written
-//               into `other` (u_j + i u_J) for the forward transform that follows
-//   EPI_CHECK   |u Kv - p| sums for the marginal error (L2 or L1, App. C.3)
-//   EPI_FINAL   u_true, v_true, the marginal error, m(pi) and the dual objective
+//   EPI_UPDATE  u = r p / Kv (balanced) or (r p / Kv)^{tau/(tau+eps)} with the problem's FP32
+//               buffer factor r (ProbState ru / rv); sums: sum u (gauge) or sum a p u^{-eps/tau}
+//               (translation-invariant step) and sum u (unbalanced buffer level),
+//               non-positive and non-finite counts; when ep.xout is set the new scaling is
+//               also written into `other` (u_j + i u_J) for the forward transform that follows
+//   EPI_CHECK   |u_true (K v_true) - p| sums for the marginal error (L2 or L1, App. C.3)
+//   EPI_FINAL   u_true, v_true (or the potentials), the marginal error, m(pi) and the dual
+//               objective
 // Field f occupies out[f * fstride ...]; rings j and J start at rj and rJ within a field.
 #pragma once
 #include "shot_internal.cuh"
@@ -26,6 +28,7 @@ struct EpiField {
   int live;            // EPI_FINAL: status >= 0; otherwise active
   int balanced;
   float gamma, et;
+  float r;             // EPI_UPDATE: the buffer factor inside the ratio (ru or rv)
 };
 
 // Threads 0..FG-1 fill fi[q] for the CTA's fields f0 + q (q < nfg).
@@ -40,6 +43,7 @@ __device__ __forceinline__ void epi_fields_load(const EpiParams& ep, int f0, int
     e.balanced = P->balanced;
     e.gamma = P->gamma;
     e.et = P->et;
+    e.r = ep.which ? P->rv : P->ru;
     fi[q] = e;
   }
 }
@@ -117,7 +121,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
       }
       const float* mg = F.marg;
       const int bal = F.balanced;
-      const float gam = F.gamma, et = F.et;
+      const float gam = F.gamma, et = F.et, rr = F.r;
       for (int k0 = threadIdx.x; k0 < N; k0 += kEpiBatch * NT) {
         // the marginal values of all this thread's longitudes first, then the arithmetic
         float pv[kEpiBatch][2];
@@ -138,7 +142,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
             if (r == 1 && !two) { u2[1] = 0.f; break; }
             const float kv = r ? zz.y : zz.x;
             const float pm = pv[b][r];
-            const float ratio = __fdividef(pm, kv);   // MUFU reciprocal + multiply, <= 2 ulp
+            const float ratio = __fdividef(pm, kv) * rr;   // MUFU reciprocal + multiply, <= 2 ulp
             float u;
             if (bal) {
               u = ratio;
@@ -150,6 +154,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
               const float l2 = __log2f(ratio);
               u = exp2f(gam * l2);
               if (pm > 0.f) acc[q][0] += aj * pm * exp2f(-et * l2);
+              acc[q][1] += u;
             }
             // one test on the common path: K v positive and finite, u finite (NaN fails each
             // comparison); the rare failures are sorted into non-positive (first in the status
@@ -167,7 +172,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
     } else if (ep.mode == EPI_CHECK) {
       if (!F.live) continue;
       const float* mg = F.marg;
-      const float al = (float)ep.ps[f].alpha;
+      const float cuv = ep.ps[f].cuv;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const float2 zz = z[q * ld + k];
 #pragma unroll
@@ -176,7 +181,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
           const float kv = r ? zz.y : zz.x;
           const size_t o = (r ? rJ : rj) + k;
           const float pm = __ldg(mg + o);
-          const float d = fmaf(al * othf[o], kv, -pm);
+          const float d = fmaf(cuv * othf[o], kv, -pm);
           if (ep.norm_l1) {
             acc[q][0] += aj * fabsf(d);
             acc[q][1] += aj * pm;
@@ -186,12 +191,15 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
           }
         }
       }
-    } else {  // EPI_FINAL: z = K v_true; ep.other = u buffer, ep.out = v buffer
+    } else {  // EPI_FINAL: z = K v_buf; ep.other = u buffer, ep.out = v buffer
       if (!F.live) continue;
       const ProbState* P = ep.ps + f;
       const float* pp = ep.marg[f];
       const float* qq = ep.marg2[f];
-      const float al = (float)P->alpha, be = (float)P->beta;
+      const float cu = P->cu, cv = P->cv, cuv = P->cuv;
+      // log u_true = la + log u_buf with la split into an FP32 head and a small remainder
+      const float la_hi = (float)P->la, lb_hi = (float)P->lb;
+      const float la_lo = (float)(P->la - (double)la_hi), lb_lo = (float)(P->lb - (double)lb_hi);
       const int bal = P->balanced;
       const float epsf = (float)ep.eps, tauf = (float)P->tau, et = bal ? 0.f : (float)(ep.eps / P->tau);
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
@@ -202,11 +210,17 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
           const float kv = r ? zz.y : zz.x;
           const size_t o = (r ? rJ : rj) + k;
           const float pm = __ldg(pp + o), qm = __ldg(qq + o);
-          const float uu = al * othf[o];
-          const float vv = be * outf[o];
-          othf[o] = uu;
-          outf[o] = vv;
-          const float d = fmaf(uu, kv, -pm);
+          const float ub = othf[o], vb = outf[o];
+          const float lu = la_hi + (logf(ub) + la_lo), lv = lb_hi + (logf(vb) + lb_lo);
+          if (ep.potentials) {
+            othf[o] = epsf * lu;
+            outf[o] = epsf * lv;
+          } else {
+            othf[o] = cu * ub;
+            outf[o] = cv * vb;
+          }
+          const float ukv = cuv * ub * kv;   // u_true (K v_true)
+          const float d = ukv - pm;
           if (ep.norm_l1) {
             acc[q][0] += aj * fabsf(d);
             acc[q][1] += aj * pm;
@@ -214,9 +228,8 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
             acc[q][0] += d * d;
             acc[q][1] += pm * pm;
           }
-          acc[q][2] += aj * uu * kv;
+          acc[q][2] += aj * ukv;
           // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
-          const float lu = logf(uu), lv = logf(vv);
           float t;
           if (bal) {
             t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);

@@ -117,7 +117,6 @@ __global__ void k_g_scalars(int nprob, int nlat, const double* __restrict__ part
 __global__ void k_g_init_state(int nprob, ProbState* ps) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b < nprob) {
-    ps[b].alpha = 1.0;
     ps[b].beta = 1.0;
   }
 }

@@ -194,14 +194,23 @@ struct Grid {
 // ---------------------------------------------------------------------------------
 // Per-problem solver state (device), see sinkhorn.cu.
 struct ProbState {
-  double alpha;     // u_true = alpha * u_buf
-  double beta;      // v_true = beta  * v_buf
-  double su;        // pending reduction of the u-step (sum u or sum a p u^{-eps/tau})
+  // The solver's buffers hold scalings up to factors kept as FP64 logarithms:
+  // u_true = e^{la} u_buf, v_true = e^{lb} v_buf (unbalanced potentials eps log u reach
+  // tau |log m(p)/m(q)| / 2, far outside the FP32 exponent range when tau/eps is large).
+  double la, lb;
+  double lsu;       // pending log of the u-step's sum (sum u_true or sum a p u_true^{-eps/tau})
+  double lvu, lvv;  // levels log mean u_buf, log mean v_buf of the latest half-steps
+  double qu, qv;    // log ru (resp. rv) minus the level of the buffer that step divides by
+  double beta;      // factor the forward ring DFT applies with scale_which 1 (gradient sweeps)
   double err;       // last marginal error
   double ot, ot_dual, mass;
   double tau;       // marginal penalty of this problem (INFINITY: balanced)
   float gamma;      // tau/(tau+eps), 1 when balanced
   float et;         // eps/(tau+eps), 0 when balanced
+  float ru, rv;     // FP32 factors inside the update ratio: u_buf = (ru p / K v_buf)^gamma
+  int eu, ev;       // ru = 2^eu, rv = 2^ev
+  float cuv;        // e^{la+lb}: u_true (K v_true) = cuv u_buf (K v_buf)
+  float cu, cv;     // e^{la}, e^{lb} in FP32 (saturate for extreme potentials)
   int balanced;
   int active;
   int status;
@@ -226,6 +235,7 @@ struct EpiParams {
   float* xout;                // EPI_UPDATE: when set, the CTA also ring-transforms the new
                               // scaling (unscaled) into the folded spectra xout[.][jh][ldc]
   int xsplit;                 // xout as bf16 hi/lo arrays (tensor-core operand) instead of FP32
+  int potentials;             // EPI_FINAL: write eps log u, eps log v instead of u, v
 };
 bool profiling_on();
 

@@ -34,6 +34,7 @@ SHOT_QUAD_CLENSHAW_CURTIS = 1
 SHOT_QUAD_HEALPIX = 2
 SHOT_FLAG_NORM_L1 = 0x1
 SHOT_FLAG_WARM_START = 0x2
+SHOT_FLAG_POTENTIALS = 0x4
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libshot.so")
 

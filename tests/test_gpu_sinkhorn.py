@@ -7,7 +7,7 @@ import pytest
 from oracle.grid import Grid as OGrid
 from oracle import sinkhorn as sk
 from paper_2605_18389_gb300 import inputs
-from tests.gpu_util import rel_max, f32, s_err, potentials_err
+from tests.gpu_util import rel_max, f32, s_err, potentials_err, UNIT
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -193,3 +193,54 @@ def test_sinkhorn_on_ring_length_with_prime_13(prec):
         assert potentials_err(og, eps, u, v, ref["phi"], ref["psi"]) < (TOL_PHI if prec == "fp32" else 1e-4)
     finally:
         shot.shot_grid_free(g)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_unbalanced_potentials_beyond_fp32_exponent_range(prec):
+    """tau/eps = 1000 with masses 0.63 and 1.58 (App. C.2's unbalanced branch): the
+    potentials settle near -+tau log(m(q)/m(p))/2, so eps log u ~ -4.6 and u ~ e^{-460},
+    far outside FP32.  The solver keeps each scaling as an FP32 buffer times an FP64
+    factor; ot, m(pi), the potentials (SHOT_FLAG_POTENTIALS) and S still match the FP64
+    oracle, whose scalings stay inside the FP64 range."""
+    nlat, eps, tau, T = 64, 0.01, 10.0, 40
+    og = OGrid(nlat)
+    g = shot.shot_grid_init(nlat, None, -1, shot.SHOT_FP32 if prec == "fp32" else shot.SHOT_BF16X3)
+    tol = TOL_PHI if prec == "fp32" else 1e-4
+    try:
+        p, q = inputs.pairs("paper_uniform", 6400, 2, og.x, og.nlon, og.a_ring)
+        p32, p64 = f32(p * np.array([0.63, 1.58])[:, None, None])
+        q32, q64 = f32(q * np.array([1.58, 0.63])[:, None, None])
+        pt, qt = torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda()
+        rc, r = shot.shot_sinkhorn(g, pt, qt, eps, tau, max_iter=T, tol=0.0, check_every=10,
+                                   flags=shot.SHOT_FLAG_POTENTIALS)
+        ref = sk.sinkhorn(og, p64, q64, eps, tau, T=T, delta=0.0, C=10)
+        assert np.all(ref["status"] == 0)
+        assert np.max(np.abs(ref["phi"])) / eps > 200.0   # e^{phi/eps} is outside FP32
+        assert rc == 0 and np.all(r["status"] == 0)
+        phi, psi = r["u"].cpu().numpy(), r["v"].cpu().numpy()
+        assert rel_max(phi, ref["phi"]) < tol and rel_max(psi, ref["psi"]) < tol
+        np.testing.assert_allclose(r["ot"], ref["ot"], rtol=tol)
+        # m(pi) = sum a u (K v) moves by |d(phi + psi)| / eps (relative) when the potentials
+        # move by d: one unit roundoff of potentials of size ~4.7 is ~3e-5 of m(pi) at eps = 0.01
+        tol_m = max(tol, UNIT[prec] * (np.max(np.abs(ref["phi"])) + np.max(np.abs(ref["psi"]))) / eps)
+        np.testing.assert_allclose(r["mass_pi"], ref["mass_pi"], rtol=tol_m)
+        rc, rd = shot.shot_divergence(g, pt, qt, eps, tau, max_iter=T, tol=0.0, check_every=10)
+        refd = sk.divergence(og, p64, q64, eps, tau, T=T, delta=0.0, C=10)
+        assert rc == 0 and np.all(rd["status"] == 0)
+        assert np.all(s_err(rd["S"], refd["S"], refd["runs"]["ot"][:2], tol) <= 1.0)
+    finally:
+        shot.shot_grid_free(g)
+
+
+def test_potentials_flag_returns_eps_log_scalings(grid_cache):
+    g, og = grid_cache(32)
+    pt, qt, p, q = _fields(og, "paper_uniform", 81, 2, masses=True)
+    for tau in (math.inf, 1.0):
+        rc, r = shot.shot_sinkhorn(g, pt, qt, 0.1, tau, max_iter=30, tol=0.0, check_every=10)
+        rc2, r2 = shot.shot_sinkhorn(g, pt, qt, 0.1, tau, max_iter=30, tol=0.0, check_every=10,
+                                     flags=shot.SHOT_FLAG_POTENTIALS)
+        assert rc == rc2 == 0
+        np.testing.assert_array_equal(r["ot"], r2["ot"])
+        u, v = r["u"].cpu().double().numpy(), r["v"].cpu().double().numpy()
+        assert rel_max(r2["u"].cpu().numpy(), 0.1 * np.log(u)) < 1e-6
+        assert rel_max(r2["v"].cpu().numpy(), 0.1 * np.log(v)) < 1e-6
