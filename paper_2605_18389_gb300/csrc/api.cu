@@ -358,6 +358,9 @@ int ensure_stream(Grid& g) {
     SHOT_CUDA(cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
     SHOT_CUDA(cudaEventCreateWithFlags(&w.ev0, cudaEventDisableTiming));
     SHOT_CUDA(cudaEventCreateWithFlags(&w.ev1, cudaEventDisableTiming));
+    SHOT_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
+    SHOT_CUDA(cudaEventCreateWithFlags(&w.evf, cudaEventDisableTiming));
+    SHOT_CUDA(cudaEventCreateWithFlags(&w.evj, cudaEventDisableTiming));
   }
   return SHOT_OK;
 }
@@ -437,6 +440,23 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
   const float* const* margQ = w.marg + s.nprob;
   EpiParams ep = base_ep(s);
   int rc;
+  // Each half-step's reduction runs on the side stream beside the next heat convolution's
+  // Legendre stages (which read no per-problem state); the next update waits for it.
+  bool pending = false;
+  auto fork_reduce = [&](int mode) -> int {
+    SHOT_CUDA(cudaEventRecord(w.evf, st));
+    SHOT_CUDA(cudaStreamWaitEvent(w.side, w.evf, 0));
+    const int r = reduce(g, mode, s.nprob, s.eps, s.tol, s.norm_l1, w.side);
+    if (r) return r;
+    SHOT_CUDA(cudaEventRecord(w.evj, w.side));
+    pending = true;
+    return SHOT_OK;
+  };
+  auto join = [&]() -> int {
+    if (pending) SHOT_CUDA(cudaStreamWaitEvent(st, w.evj, 0));
+    pending = false;
+    return SHOT_OK;
+  };
   for (int i = 0; i < nit; ++i) {
     // u-step: u = (ru p / K v)^gamma, and X := F(u)
     if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
@@ -445,15 +465,15 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     ep.marg = margP;
     ep.which = 0;
     ep.xout = w.XY;
-    if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
-    if ((rc = reduce(g, RED_U, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
-    // v-step: v = (q / K u)^gamma, X := F(v); then the gauge / translation-invariant scalars
+    if ((rc = join()) || (rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
+    if ((rc = fork_reduce(RED_U))) return rc;
+    // v-step: v = (rv q / K u)^gamma, X := F(v); then the gauge / translation-invariant scalars
     if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
     ep.out = s.v;
     ep.marg = margQ;
     ep.which = 1;
-    if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
-    if ((rc = reduce(g, RED_V, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
+    if ((rc = join()) || (rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
+    if ((rc = fork_reduce(RED_V))) return rc;
   }
   if (check) {   // K v from the spectra X, which stay for the next u-step
     if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
@@ -461,10 +481,10 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     ep.other = s.u;
     ep.marg = margP;
     ep.xout = nullptr;
-    if ((rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
-    if ((rc = reduce(g, RED_CHECK, s.nprob, s.eps, s.tol, s.norm_l1, st))) return rc;
+    if ((rc = join()) || (rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
+    if ((rc = fork_reduce(RED_CHECK))) return rc;
   }
-  return SHOT_OK;
+  return join();
 }
 
 int solve_final_enqueue(Solve& s) {
@@ -812,6 +832,9 @@ int shot_grid_free(shot_grid gh) {
   if (g->ws.stream) cudaStreamDestroy(g->ws.stream);
   if (g->ws.ev0) cudaEventDestroy(g->ws.ev0);
   if (g->ws.ev1) cudaEventDestroy(g->ws.ev1);
+  if (g->ws.side) cudaStreamDestroy(g->ws.side);
+  if (g->ws.evf) cudaEventDestroy(g->ws.evf);
+  if (g->ws.evj) cudaEventDestroy(g->ws.evj);
   if (g->ws.host_int) cudaFreeHost(g->ws.host_int);
   if (g->ws.host_probs) cudaFreeHost(g->ws.host_probs);
   delete g;

@@ -109,6 +109,8 @@ struct Workspace {
   double* taus = nullptr;      // per-problem tau (device) [nf]
   cudaStream_t stream = nullptr;   // internal solver stream (capturable)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaStream_t side = nullptr;     // the solver's per-problem reductions (overlap the next analysis)
+  cudaEvent_t evf = nullptr, evj = nullptr;
 };
 
 // Tunable launch shapes for one field count (0 = the built-in default).
