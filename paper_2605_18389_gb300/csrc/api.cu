@@ -35,8 +35,7 @@ int cuda_status(cudaError_t e, const char* what) {
   return e == cudaErrorMemoryAllocation ? SHOT_ERR_OOM : SHOT_ERR_CUDA;
 }
 
-int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
-                         const ProbState* colscale);
+int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
 int launch_analysis_simt(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h, cudaStream_t st);
 int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st);
 
@@ -46,19 +45,19 @@ int spectra_split(const Grid& g, int nf, int ldc) {
 }
 
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
-                    const ProbState* colscale, int xsplit) {
-  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st, colscale);
-  if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st, colscale);
-  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st, colscale);
+                    int xsplit) {
+  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st);
+  if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st);
+  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st);
   if (g.merged_heat && !xsplit) {
-    const int rc = launch_heat_merged(g, nf, X, Y, ldc, st, colscale);
+    const int rc = launch_heat_merged(g, nf, X, Y, ldc, st);
     if (rc != SHOT_ERR_UNSUPPORTED) return rc;
   }
   if (g.fused_heat) {
-    const int rc = launch_heat_tc(g, nf, X, Y, ldc, st, colscale, xsplit);
+    const int rc = launch_heat_tc(g, nf, X, Y, ldc, st, xsplit);
     if (rc != SHOT_ERR_UNSUPPORTED) return rc;
   }
-  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st, colscale, xsplit);
+  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st, xsplit);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st) {
@@ -459,7 +458,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
   };
   for (int i = 0; i < nit; ++i) {
     // u-step: u = (ru p / K v)^gamma, and X := F(u)
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
     ep.mode = EPI_UPDATE;
     ep.out = s.u;
     ep.marg = margP;
@@ -468,7 +467,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     if ((rc = join()) || (rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
     if ((rc = fork_reduce(RED_U))) return rc;
     // v-step: v = (rv q / K u)^gamma, X := F(v); then the gauge / translation-invariant scalars
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
     ep.out = s.v;
     ep.marg = margQ;
     ep.which = 1;
@@ -476,7 +475,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     if ((rc = fork_reduce(RED_V))) return rc;
   }
   if (check) {   // K v from the spectra X, which stay for the next u-step
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, nullptr, s.xs))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
     ep.mode = EPI_CHECK;
     ep.other = s.u;
     ep.marg = margP;
@@ -494,7 +493,7 @@ int solve_final_enqueue(Solve& s) {
   ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   int rc;
   // final K v for the objective, mass and marginal error; writes u_true, v_true
-  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st, nullptr, s.xs))) return rc;
+  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st, s.xs))) return rc;
   ep.mode = EPI_FINAL;
   ep.potentials = s.potentials;
   ep.out = s.v;

@@ -70,8 +70,7 @@ __global__ void __launch_bounds__(kAnaThreads) k_ana_rec(int lmax, int nh, const
                                                          const int* __restrict__ Mrows,
                                                          const long long* __restrict__ row_off,
                                                          const float* __restrict__ X, int ldc, int ncols,
-                                                         const float* __restrict__ h, float* __restrict__ C,
-                                                         const ProbState* __restrict__ colscale) {
+                                                         const float* __restrict__ h, float* __restrict__ C) {
   extern __shared__ float sm[];
   const int blk = blockIdx.x;
   const int m = blk >> 1, p = blk & 1;
@@ -148,7 +147,7 @@ __global__ void __launch_bounds__(kAnaThreads) k_ana_rec(int lmax, int nh, const
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
         const int col = n0 + tc * 6 + c;
-        if (col < ncols) o[col] = acc[c] * sc * (colscale ? (float)colscale[col >> 1].beta : 1.f);
+        if (col < ncols) o[col] = acc[c] * sc;
       }
     }
   }
@@ -289,7 +288,7 @@ int build_recurrence(Grid& g, cudaStream_t st) {
 }
 
 int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
-                        bool apply_h, cudaStream_t st, const ProbState* colscale) {
+                        bool apply_h, cudaStream_t st) {
   const int ncols = 2 * nf;
   const int ncol_tiles = (ncols + kRN - 1) / kRN;
   if (g.nh > 6 * kAnaThreads) {
@@ -310,7 +309,7 @@ int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* 
     kern<<<dim3(g.nblk, ncol_tiles), kAnaThreads, smem, st>>>(
         g.lmax, g.nh, reinterpret_cast<const float2*>(g.rec_x), reinterpret_cast<const Seed*>(g.rec_seeds),
         reinterpret_cast<const float4*>(g.rec_coef), g.rec_coef_off, g.M_d, g.row_off_d, X, ldc, ncols,
-        apply_h ? g.h_d : nullptr, C, colscale);
+        apply_h ? g.h_d : nullptr, C);
     SHOT_CUDA(cudaGetLastError());
   }
   if (syn) {

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(NT) k_legendre_simt(
     const Tile* __restrict__ tiles, const float* __restrict__ tab, int ldt,
     const long long* __restrict__ row_off, const int* __restrict__ Mrows, int nh,
     const float* __restrict__ Bsrc, int ldc, int ncols, float* __restrict__ out,
-    const float* __restrict__ h, const ProbState* __restrict__ colscale) {
+    const float* __restrict__ h) {
   constexpr int TN = BN / 8;
   constexpr int BF4 = BK * BN / 4;                 // float4 per B chunk
   constexpr int BL = (BF4 + NT - 1) / NT;          // float4 loads per thread
@@ -165,15 +165,14 @@ __global__ void __launch_bounds__(NT) k_legendre_simt(
 #pragma unroll
     for (int c = 0; c < TN; ++c) {
       const int col = n0 + tn * TN + c;
-      // per-column factor: the gauge scale of the field whose spectra X holds unscaled
-      if (col < ncols) o[col] = acc[r][c] * sc * (colscale ? (float)colscale[col >> 1].beta : 1.f);
+      if (col < ncols) o[col] = acc[r][c] * sc;
     }
   }
 }
 
 template <int BN>
 int launch_pair(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
-                const float* h, cudaStream_t st, const ProbState* cs) {
+                const float* h, cudaStream_t st) {
   const int ncols = 2 * nf;
   const int ny = (ncols + BN - 1) / BN;
   if (ana) {
@@ -181,7 +180,7 @@ int launch_pair(const Grid& g, int nf, const float* X, float* C, float* Y, int l
     ProfScope prof(PK_ANALYSIS, st);
     count_launch();
     k_legendre_simt<BN, true><<<grid, NT, 0, st>>>(g.tiles_ana, g.tab, g.ldt, g.row_off_d, g.M_d, g.nh, X,
-                                                    ldc, ncols, C, h, cs);
+                                                    ldc, ncols, C, h);
     SHOT_CUDA(cudaGetLastError());
   }
   if (syn) {
@@ -189,30 +188,29 @@ int launch_pair(const Grid& g, int nf, const float* X, float* C, float* Y, int l
     ProfScope prof(PK_SYNTHESIS, st);
     count_launch();
     k_legendre_simt<BN, false><<<grid, NT, 0, st>>>(g.tiles_syn, g.tab, g.ldt, g.row_off_d, g.M_d, g.nh, C,
-                                                     ldc, ncols, Y, nullptr, nullptr);
+                                                     ldc, ncols, Y, nullptr);
     SHOT_CUDA(cudaGetLastError());
   }
   return SHOT_OK;
 }
 
 int dispatch(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
-             const float* h, cudaStream_t st, const ProbState* cs = nullptr) {
+             const float* h, cudaStream_t st) {
   const int ncols = 2 * nf;
   if (g.active.nf == nf && g.active.simt_bn > 0) {
-    if (g.active.simt_bn == 32) return launch_pair<32>(g, nf, X, C, Y, ldc, ana, syn, h, st, cs);
-    if (g.active.simt_bn == 48) return launch_pair<48>(g, nf, X, C, Y, ldc, ana, syn, h, st, cs);
-    return launch_pair<64>(g, nf, X, C, Y, ldc, ana, syn, h, st, cs);
+    if (g.active.simt_bn == 32) return launch_pair<32>(g, nf, X, C, Y, ldc, ana, syn, h, st);
+    if (g.active.simt_bn == 48) return launch_pair<48>(g, nf, X, C, Y, ldc, ana, syn, h, st);
+    return launch_pair<64>(g, nf, X, C, Y, ldc, ana, syn, h, st);
   }
-  if (ncols <= 32) return launch_pair<32>(g, nf, X, C, Y, ldc, ana, syn, h, st, cs);
-  if (ncols <= 48) return launch_pair<48>(g, nf, X, C, Y, ldc, ana, syn, h, st, cs);
-  return launch_pair<64>(g, nf, X, C, Y, ldc, ana, syn, h, st, cs);
+  if (ncols <= 32) return launch_pair<32>(g, nf, X, C, Y, ldc, ana, syn, h, st);
+  if (ncols <= 48) return launch_pair<48>(g, nf, X, C, Y, ldc, ana, syn, h, st);
+  return launch_pair<64>(g, nf, X, C, Y, ldc, ana, syn, h, st);
 }
 
 }  // namespace
 
-int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
-                         const ProbState* colscale) {
-  return dispatch(g, nf, X, C, Y, ldc, true, true, g.h_d, st, colscale);
+int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st) {
+  return dispatch(g, nf, X, C, Y, ldc, true, true, g.h_d, st);
 }
 
 int launch_analysis_simt(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,

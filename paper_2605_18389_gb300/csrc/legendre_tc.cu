@@ -147,7 +147,6 @@ struct AnaArgs {
   int nmma_cap, ldi;
   float* cf;           // optional FP32 [row_off + i][ldc]
   int* err;
-  const ProbState* colscale;   // per-field factor of unscaled spectra (or nullptr)
 };
 
 struct SynArgs {
@@ -187,12 +186,8 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
                                                                AnaArgs aa, SynArgs sa) {
   extern __shared__ uint8_t smraw[];
   __shared__ TcSmem ctl;
-  __shared__ float cscale[256];   // analysis: per-column factor (gauge beta) as FP32
   uint8_t* base = align1k(smraw);
   const int nmma = ANA ? aa.nmma : sa.nmma;
-  if (ANA)
-    for (int c = threadIdx.x; c < nmma; c += blockDim.x)
-      cscale[c] = (aa.colscale && c < aa.ncols) ? (float)aa.colscale[c >> 1].beta : 1.f;
   const int nh = ANA ? aa.nh : sa.nh;
   const int ntiles = ANA ? aa.ntiles : sa.ntiles;
   const Tile* tiles = ANA ? aa.tiles : sa.tiles;
@@ -407,7 +402,7 @@ __global__ void __launch_bounds__(tc_threads<ANA, XS>(), 1) k_legendre_tc(const 
             for (int e = 0; e < 16; ++e) {
               const int c = c0 + e;
               if (c < aa.ncols) {
-                const float val = v[e] * hl * cscale[c];
+                const float val = v[e] * hl;
                 const __nv_bfloat16 hi = __float2bfloat16_rn(val);
                 const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
                 const size_t o = ((size_t)blk * aa.nmma_cap + c) * aa.ldi + row;
@@ -472,7 +467,6 @@ struct AnaTArgs {
   const float* X;
   int ldc, ncols, nmma;
   const float* h;
-  const ProbState* colscale;
   __nv_bfloat16* ct_hi;
   __nv_bfloat16* ct_lo;
   int nmma_cap, ldi;
@@ -485,7 +479,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ana_tc_t(const __grid_constan
                                                             const __grid_constant__ CUtensorMap t_x, AnaTArgs aa) {
   extern __shared__ uint8_t smraw[];
   __shared__ TcSmem ctl;
-  __shared__ float cscale[256];
   uint8_t* base = align1k(smraw);
   const int nmma = aa.nmma, nh = aa.nh;
   constexpr int kBTile = 256 * kBK * 2;          // table tile (hi or lo), 256 rows
@@ -501,8 +494,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ana_tc_t(const __grid_constan
   constexpr uint32_t kAccCols = 256;
   const int nkb = (nh + kBK - 1) / kBK;
 
-  for (int c = threadIdx.x; c < 128; c += blockDim.x)
-    cscale[c] = (aa.colscale && c < aa.ncols) ? (float)aa.colscale[c >> 1].beta : 1.f;
   // the A atoms of columns 64..127 hold only zeros (2 nf <= 64): clear them once
   for (int s = 0; s < kStages; ++s)
     for (int o = threadIdx.x * 16; o < kXsBoxBytes; o += blockDim.x * 16) {
@@ -607,7 +598,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ana_tc_t(const __grid_constan
     const int q = warp - 4;
     const int c = q * 32 + lane;
     const bool qlive = q * 32 < aa.ncols;   // warp-uniform
-    const float cs = cscale[c];
     int lt = 0;
     for (int t = blockIdx.x; t < aa.ntiles; t += gridDim.x, ++lt) {
       const TileR tl = aa.tiles[t];
@@ -628,7 +618,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_ana_tc_t(const __grid_constan
               const int i = tl.r0 + i0 + e;   // rows past the tile (i0 + e >= rows) are not stored
               const float h0 = (aa.h && i0 + e < tl.rows) ? aa.h[m + p + 2 * i] : 1.f;
               const float h1 = (aa.h && i0 + e + 1 < tl.rows) ? aa.h[m + p + 2 * (i + 1)] : 1.f;
-              const float v0 = v[e] * h0 * cs, v1 = v[e + 1] * h1 * cs;
+              const float v0 = v[e] * h0, v1 = v[e + 1] * h1;
               const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
               const float2 hf = __bfloat1622float2(h2);
               const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - hf.x, v1 - hf.y);
@@ -698,7 +688,6 @@ struct HeatArgs {
   int nmt_max;        // 128-row tiles of the largest block
   int kc_max;         // 64-row chunks of the largest block
   const float* h;     // h_l or nullptr
-  const ProbState* colscale;
   float* Y;           // [blk][jh][ldc]
   int* err;
 };
@@ -712,11 +701,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
                                                            const __grid_constant__ CUtensorMap t_x2, HeatArgs ha) {
   extern __shared__ uint8_t smraw[];
   __shared__ HeatTcSmem ctl;
-  __shared__ float cscale[256];
   uint8_t* base = align1k(smraw);
   const int nmma = ha.nmma, nh = ha.nh;
-  for (int c = threadIdx.x; c < nmma; c += blockDim.x)
-    cscale[c] = (ha.colscale && c < ha.ncols) ? (float)ha.colscale[c >> 1].beta : 1.f;
   const int bbytes = mn_atoms(nmma) * kXsBoxBytes;   // analysis B, MN-major
   const int xbytes = XS ? 0 : nmma * kBK * 4;
   const int sbytes = 2 * kATileBytes + xbytes + 2 * bbytes;   // one pipeline stage
@@ -935,7 +921,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_heat_tc(const __grid_constant
             for (int e = 0; e < 16; ++e) {
               const int c = c0 + e;
               float val = 0.f;
-              if (c < ha.ncols) val = v[e] * hl * cscale[c];
+              if (c < ha.ncols) val = v[e] * hl;
               const __nv_bfloat16 hi = __float2bfloat16_rn(val);
               const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
               const uint32_t o = cb + sw128_offset(c, i & 63);
@@ -1007,7 +993,6 @@ struct MergedArgs {
   const long long* row_off;
   int nh, ldc, ncols, nmma;
   const float* h;                 // h_l
-  const ProbState* colscale;      // per-field factor of unscaled spectra, or nullptr
   __nv_bfloat16* ct_hi;           // C^T [blk][nmma_cap][ldi] (hi, lo)
   __nv_bfloat16* ct_lo;
   int nmma_cap, ldi;
@@ -1045,7 +1030,6 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_heat_merged(
     MergedArgs a) {
   extern __shared__ uint8_t smraw[];
   __shared__ MergedSmem ctl;
-  __shared__ float cscale[256];
   uint8_t* base = align1k(smraw);
   const int nmma = a.nmma, nh = a.nh;
   const int bbytes = mn_atoms(nmma) * kXsBoxBytes;   // analysis B atoms (hi or lo)
@@ -1070,8 +1054,6 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_heat_merged(
   const int nkbA = (nh + kBK - 1) / kBK;
   const int nnt = (nh + kBM - 1) / kBM;
 
-  for (int c = threadIdx.x; c < nmma; c += blockDim.x)
-    cscale[c] = (a.colscale && c < a.ncols) ? (float)a.colscale[c >> 1].beta : 1.f;
   for (int o = threadIdx.x * 16; o < kMgBR * 2 * bbytes; o += blockDim.x * 16)   // pad columns stay zero
     *reinterpret_cast<uint4*>(sB + o) = make_uint4(0, 0, 0, 0);
   fence_async_smem();
@@ -1257,7 +1239,7 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_heat_merged(
               for (int e = 0; e < 16; ++e) {
                 const int c = c0 + e;
                 if (c < a.ncols) {
-                  const float val = (v[e] + w[e]) * hl * cscale[c];
+                  const float val = (v[e] + w[e]) * hl;
                   const __nv_bfloat16 hi = __float2bfloat16_rn(val);
                   const __nv_bfloat16 lo = __float2bfloat16_rn(val - __bfloat162float(hi));
                   const size_t o = ((size_t)blk * a.nmma_cap + c) * a.ldi + row;
@@ -1343,7 +1325,7 @@ static int host_tmem_cols(int n) {
 int tc_supported_fields(int nf) { return tc_nmma(nf) <= 256; }
 
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                       bool apply_h, cudaStream_t st, const ProbState* colscale, int xsplit) {
+                       bool apply_h, cudaStream_t st, int xsplit) {
   const Workspace& w = g.ws;
   const int nmma = tc_nmma(nf);
   if (nmma > 256 || nmma > w.nmma_cap) {
@@ -1362,7 +1344,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kRowBox))) return rc;
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
     AnaTArgs ta{g.tiles_ana_t, g.ntiles_ana_t, g.row_off_d, g.M_d, g.nh, X, ldc, 2 * nf, nmma,
-                apply_h ? g.h_d : nullptr, colscale, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, w.dev_int + 4};
+                apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, w.dev_int + 4};
     SHOT_CUDA(cudaFuncSetAttribute(k_ana_tc_t<stages>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = g.ntiles_ana_t < g.num_sms ? g.ntiles_ana_t : g.num_sms;
     ProfScope prof(PK_ANALYSIS, st);
@@ -1385,7 +1367,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map(&xh, Xh, ldc, (uint64_t)g.nblk * g.nh, ldc, kBK))) return rc;
     if ((rc = make_map(&xl, Xl, ldc, (uint64_t)g.nblk * g.nh, ldc, kBK))) return rc;
     aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, nullptr, ldc, 2 * nf, nmma,
-                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4, colscale};
+                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4};
     auto kern = k_legendre_tc<stages, true, true>;
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int per_sm = (smem <= 113 * 1024 && 2 * 2 * host_tmem_cols(nmma) <= 512) ? 2 : 1;
@@ -1408,7 +1390,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kBM))) return rc;
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
     aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma,
-                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4, colscale};
+                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4};
     // [B_hi | B_lo] as one operand up to 128 columns (N = 2 x 64 x atoms <= 256)
     const bool bcat = 2 * 64 * mn_atoms(nmma) <= 256;
     auto kern = bcat ? (br == 3 ? (stages == 4   ? k_legendre_tc<4, true, false, 3, true>
@@ -1461,8 +1443,7 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
 // Fused analysis + synthesis (k_heat_tc) for the solver's heat applications.  Returns
 // SHOT_ERR_UNSUPPORTED (without launching) when the configuration does not fit: more than
 // 32 fields, TMEM slots, or shared memory; the caller then runs the two-kernel path.
-int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
-                   const ProbState* colscale, int xsplit) {
+int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st, int xsplit) {
   const Workspace& w = g.ws;
   const int nmma = tc_nmma(nf);
   if (nmma > 64 || g.nwork == 0) return SHOT_ERR_UNSUPPORTED;
@@ -1492,7 +1473,7 @@ int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cud
     mx2 = mx;
   }
   HeatArgs ha{g.blk_order_d, g.nwork, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma, g.nmt_max, g.kc_max,
-              g.h_d, colscale, Y, w.dev_int + 4};
+              g.h_d, Y, w.dev_int + 4};
   auto kern = xsplit ? (stages == 3 ? k_heat_tc<3, true> : k_heat_tc<2, true>)
                      : (stages == 3 ? k_heat_tc<3, false> : k_heat_tc<2, false>);
   SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1506,8 +1487,7 @@ int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cud
 
 // Merged heat kernel (k_heat_merged) for the BF16X3 heat applications, up to 32 fields with
 // FP32 spectra.  Returns SHOT_ERR_UNSUPPORTED (without launching) otherwise.
-int launch_heat_merged(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
-                       const ProbState* colscale) {
+int launch_heat_merged(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st) {
   const Workspace& w = g.ws;
   const int nmma = tc_nmma(nf);
   if (nmma > 64 || g.nwork == 0 || nmma > w.nmma_cap) return SHOT_ERR_UNSUPPORTED;
@@ -1526,7 +1506,7 @@ int launch_heat_merged(const Grid& g, int nf, const float* X, float* Y, int ldc,
   if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
   if ((rc = make_map(&ch, w.ct_hi, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
   if ((rc = make_map(&cl, w.ct_lo, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
-  MergedArgs ma{g.blk_order_d, g.nwork, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma, g.h_d, colscale,
+  MergedArgs ma{g.blk_order_d, g.nwork, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma, g.h_d,
                 w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Y, w.dev_int + 4};
   auto kern = stages == 4 ? k_heat_merged<4> : stages == 3 ? k_heat_merged<3> : k_heat_merged<2>;
   SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

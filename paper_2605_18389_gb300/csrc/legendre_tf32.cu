@@ -166,7 +166,6 @@ struct T32Args {
   const long long* row_off;
   int nh, ldc, ncols, nmma;
   const float* h;             // analysis: h_l, or nullptr
-  const ProbState* colscale;  // analysis: per-field factor (gauge beta) of unscaled spectra, or nullptr
   float* ct;                  // analysis output: C^T [blk][nmma_cap][ldi] FP32
   float* cf;                  // analysis output (optional): C [row_off + i][ldc] FP32
   int nmma_cap, ldi;
@@ -182,7 +181,6 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
                                                                   T32Args a) {
   extern __shared__ uint8_t smraw[];
   __shared__ TcSmem ctl;
-  __shared__ float cscale[256];
   uint8_t* base = align1k(smraw);
   const int nmma = a.nmma, nh = a.nh;
   const int bbytes = nmma * kTK * 4;   // one B tile (hi or lo); the analysis X tile has the same size
@@ -192,9 +190,6 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
   auto sB_hi = [&](int s) { return base + s * sbytes + 2 * kTTile; };
   auto sB_lo = [&](int s) { return base + s * sbytes + 2 * kTTile + bbytes; };
   auto sX = [&](int s) { return base + s * sbytes + 2 * kTTile + 2 * bbytes; };
-  if (ANA)
-    for (int c = threadIdx.x; c < nmma; c += blockDim.x)
-      cscale[c] = (a.colscale && c < a.ncols) ? (float)a.colscale[c >> 1].beta : 1.f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // BCAT (2 nmma <= 256): B hi and B lo are adjacent in shared memory and form one operand
   // of N = 2 nmma, so A_hi [B_hi | B_lo] and A_lo B_hi are two MMAs per K step instead of
@@ -342,7 +337,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
             for (int e = 0; e < 16; ++e) {
               const int c = c0 + e;
               if (c < a.ncols) {
-                const float val = v[e] * hl * cscale[c];
+                const float val = v[e] * hl;
                 a.ct[((size_t)blk * a.nmma_cap + c) * a.ldi + row] = val;
                 if (a.cf) a.cf[(size_t)(ro + row) * a.ldc + c] = val;
               }
@@ -408,7 +403,7 @@ size_t tf32_smem_bytes(int nmma, bool ana, int stages) {
 int tf32_nmma(int nf) { return (2 * nf + 15) / 16 * 16; }
 
 int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                         bool apply_h, cudaStream_t st, const ProbState* colscale) {
+                         bool apply_h, cudaStream_t st) {
   const Workspace& w = g.ws;
   const int nmma = tf32_nmma(nf);
   if (nmma > 256 || nmma > w.nmma_cap || !w.ct32 || !g.tab || !g.tabT) {
@@ -448,7 +443,7 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
     if ((rc = make_map_f32(&ma, g.tab, g.nh, g.rows_total, g.ldt, kTK, kBM, true))) return rc;
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kTK))) return rc;
     const T32Args args{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma,
-                       apply_h ? g.h_d : nullptr, colscale, w.ct32, Cf, w.nmma_cap, g.ldi, nullptr, w.dev_int + 4};
+                       apply_h ? g.h_d : nullptr, w.ct32, Cf, w.nmma_cap, g.ldi, nullptr, w.dev_int + 4};
     if ((rc = launch(true, ma, mx, args, g.ntiles_ana))) return rc;
   }
   if (syn) {
@@ -456,7 +451,7 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
     if ((rc = make_map_f32(&ma, g.tabT, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kTK, kBM, true))) return rc;
     if ((rc = make_map_f32(&mb, w.ct32, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, kTK, nmma, true))) return rc;
     const T32Args args{g.tiles_syn, g.ntiles_syn, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma,
-                       nullptr, nullptr, nullptr, nullptr, w.nmma_cap, g.ldi, Y, w.dev_int + 4};
+                       nullptr, nullptr, nullptr, w.nmma_cap, g.ldi, Y, w.dev_int + 4};
     if ((rc = launch(false, ma, mb, args, g.ntiles_syn))) return rc;
   }
   return SHOT_OK;

@@ -247,7 +247,7 @@ int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, 
                    float* X, int ldc, cudaStream_t st, int xsplit = 0);
 int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
-                    const ProbState* colscale = nullptr, int xsplit = 0);
+                    int xsplit = 0);
 // whether the solver keeps its spectra as bf16 hi/lo (BF16X3 table grids, <= 32 fields)
 int spectra_split(const Grid& g, int nf, int ldc);
 int launch_heat_mult(const Grid& g, double t, cudaStream_t st);
@@ -260,19 +260,17 @@ int build_grid_tables(Grid& g, cudaStream_t st);
 // selects g.active for nf (tunes on first use)
 int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd = nullptr);
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                       bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr, int xsplit = 0);
+                       bool apply_h, cudaStream_t st, int xsplit = 0);
 int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
-int launch_heat_merged(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
-                       const ProbState* colscale);
+int launch_heat_merged(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st);
 int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                         bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
+                         bool apply_h, cudaStream_t st);
 int launch_c_to_ct32(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
 int build_recurrence(Grid& g, cudaStream_t st);
 int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
-                        bool apply_h, cudaStream_t st, const ProbState* colscale = nullptr);
+                        bool apply_h, cudaStream_t st);
 int tc_nmma(int nf);
-int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st,
-                   const ProbState* colscale, int xsplit = 0);
+int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st, int xsplit = 0);
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
 // HEALPix
 void healpix_geometry(Grid& g, int nside);
