@@ -225,9 +225,9 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields):
 # captures of this file's 720 x 1440, 24-field runs (profiles/ncu_k_idft_720x1440.md,
 # ncu_k_legendre_tc_720x1440.md, ncu_k_legendre_tf32_720x1440.md); valid only for that workload,
 # precision and the kernels as captured.
-NCU_TRAFFIC = {("inverse_dft_epilogue", "bf16x3"): 316.6e6, ("legendre_analysis", "bf16x3"): 532.7e6,
-               ("legendre_synthesis", "bf16x3"): 521.7e6, ("inverse_dft_epilogue", "tf32x3"): 316.6e6,
-               ("legendre_analysis", "tf32x3"): 528.9e6, ("legendre_synthesis", "tf32x3"): 613.1e6}
+NCU_TRAFFIC = {("inverse_dft_epilogue", "bf16x3"): 311.4e6, ("legendre_analysis", "bf16x3"): 532.7e6,
+               ("legendre_synthesis", "bf16x3"): 521.7e6, ("inverse_dft_epilogue", "tf32x3"): 311.4e6,
+               ("legendre_analysis", "tf32x3"): 528.5e6, ("legendre_synthesis", "tf32x3"): 612.9e6}
 
 
 def roofline(kind, avg_ms, nlat, npix, lmax, nfields, prec):
