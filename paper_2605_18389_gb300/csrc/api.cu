@@ -440,9 +440,13 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
   EpiParams ep = base_ep(s);
   int rc;
   // Each half-step's reduction runs on the side stream beside the next heat convolution's
-  // Legendre stages (which read no per-problem state); the next update waits for it.
+  // Legendre stages (which read no per-problem state); the next update waits for it.  Profiled
+  // runs (a CUDA event pair around every launch) keep it on the solver's stream, so that each
+  // launch's time is its own.
   bool pending = false;
+  const bool side = !profiling_on();
   auto fork_reduce = [&](int mode) -> int {
+    if (!side) return reduce(g, mode, s.nprob, s.eps, s.tol, s.norm_l1, st);
     SHOT_CUDA(cudaEventRecord(w.evf, st));
     SHOT_CUDA(cudaStreamWaitEvent(w.side, w.evf, 0));
     const int r = reduce(g, mode, s.nprob, s.eps, s.tol, s.norm_l1, w.side);
