@@ -212,8 +212,11 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields):
     if kind == "ring_dft":
         return field + spec, 0.0
     if kind == "inverse_dft_epilogue":
-        # the fused half-step form: Y in, marginal in, new scaling out, its spectra X out
-        return 2 * spec + 2 * field, 0.0
+        # per block of C iterations: 2C fused half-steps (Y in, marginal in, spectra X of the new
+        # scaling out) of which the last two also store the scaling, and one marginal check
+        # (Y in, marginal in, u in); averaged over the block's 2C + 1 launches
+        C = CHECK_EVERY
+        return (2 * C * (2 * spec + field) + 2 * field + (spec + 2 * field)) / (2 * C + 1), 0.0
     if kind == "legendre_analysis":
         return table + spec + coef, legendre_flops_per_launch(nlat, lmax, nfields)
     if kind == "legendre_synthesis":
@@ -225,8 +228,7 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields):
 # captures of this file's 720 x 1440, 24-field runs (profiles/ncu_k_idft_720x1440.md,
 # ncu_k_legendre_tc_720x1440.md, ncu_k_legendre_tf32_720x1440.md); valid only for that workload,
 # precision and the kernels as captured.
-NCU_TRAFFIC = {("inverse_dft_epilogue", "bf16x3"): 311.4e6, ("legendre_analysis", "bf16x3"): 532.7e6,
-               ("legendre_synthesis", "bf16x3"): 521.7e6, ("inverse_dft_epilogue", "tf32x3"): 311.4e6,
+NCU_TRAFFIC = {("legendre_analysis", "bf16x3"): 532.7e6, ("legendre_synthesis", "bf16x3"): 521.7e6,
                ("legendre_analysis", "tf32x3"): 528.5e6, ("legendre_synthesis", "tf32x3"): 612.9e6}
 
 

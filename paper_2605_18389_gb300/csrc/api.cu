@@ -468,6 +468,9 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     ep.marg = margP;
     ep.which = 0;
     ep.xout = w.XY;
+    // only the block's last iteration leaves u and v in their buffers (the check and the final
+    // objective read them); the others feed the fused forward transforms alone
+    ep.skip_store = (i + 1 < nit) ? 1 : 0;
     if ((rc = join()) || (rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
     if ((rc = fork_reduce(RED_U))) return rc;
     // v-step: v = (rv q / K u)^gamma, X := F(v); then the gauge / translation-invariant scalars

@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
 
 // ---------------------------------------------------------------------------------
 // Persistent form of k_idft for the solver's update half-steps (EPI_UPDATE with the fused
-// forward transform of the new scaling).  A CTA walks over items (ring pair jh, field group)
+// forward transform of the new scaling) and its marginal checks (EPI_CHECK, no forward
+// transform).  A CTA walks over items (ring pair jh, field group)
 // item = blockIdx.x + i gridDim.x, consecutive items covering the field groups of one ring
 // pair.  Right after it has unpacked one item's spectra it starts the cp.async gather of the
 // next item's spectra rows into a staging area and asks L2 for the next item's marginal rows,
@@ -305,9 +306,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft_p(
     const bool two = (J != j);
     ring_pair_epilogue<FG, kThreads>(z, other, ld, N, nfg, f0, (size_t)nlat * nlon, (size_t)j * nlon,
                                      (size_t)J * nlon, two, aj, nh, jh, ep, red, fi[slot]);
-    __syncthreads();
-    const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw_g, pl, nfg);
-    unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc, ep.xsplit);
+    if (ep.xout) {   // the update's new scaling: its spectra for the next half-step
+      __syncthreads();
+      const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw_g, pl, nfg);
+      unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc, ep.xsplit);
+    }
     item = next;
     slot ^= 1;
   }
@@ -401,8 +404,9 @@ int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams&
     set_error("nlon too large for the shared-memory ring FFT");
     return SHOT_ERR_UNSUPPORTED;
   }
-  // the solver's update half-steps: persistent kernel with the next item's inputs prefetched
-  if (ep.mode == EPI_UPDATE && ep.xout && !g.idft_nonpersistent && nf >= 2 &&
+  // the solver's update half-steps and marginal checks: persistent kernel with the next item's
+  // inputs prefetched
+  if (((ep.mode == EPI_UPDATE && ep.xout) || ep.mode == EPI_CHECK) && !g.idft_nonpersistent && nf >= 2 &&
       idft_p_layout(2, g.nlon, g.lmax).total <= 74 * 1024) {
     if (plan_is<Plan1440>(g.plan)) return launch_idft_p_t<2, Plan1440>(g, Y, ldc, nf, ep, st);
     if (plan_is<Plan1024>(g.plan)) return launch_idft_p_t<2, Plan1024>(g, Y, ldc, nf, ep, st);

@@ -163,7 +163,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
               if (kv <= 0.f) acc[q][2] += 1.f;
               else acc[q][3] += 1.f;   // NaN or infinite K v, or u overflowed
             }
-            outf[(r ? rJ : rj) + k] = u;
+            if (!ep.skip_store) outf[(r ? rJ : rj) + k] = u;
             u2[r] = u;
           }
           if (ep.xout) other[q * ld + k] = make_float2(u2[0], u2[1]);

@@ -238,6 +238,8 @@ struct EpiParams {
                               // scaling (unscaled) into the folded spectra xout[.][jh][ldc]
   int xsplit;                 // xout as bf16 hi/lo arrays (tensor-core operand) instead of FP32
   int potentials;             // EPI_FINAL: write eps log u, eps log v instead of u, v
+  int skip_store;             // EPI_UPDATE: the new scaling feeds only the fused forward
+                              // transform (no later launch reads this iteration's buffer)
 };
 bool profiling_on();
 
