@@ -212,11 +212,12 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields):
     if kind == "ring_dft":
         return field + spec, 0.0
     if kind == "inverse_dft_epilogue":
-        # per block of C iterations: 2C fused half-steps (Y in, marginal in, spectra X of the new
-        # scaling out) of which the last two also store the scaling, and one marginal check
-        # (Y in, marginal in, u in); averaged over the block's 2C + 1 launches
-        C = CHECK_EVERY
-        return (2 * C * (2 * spec + field) + 2 * field + (spec + 2 * field)) / (2 * C + 1), 0.0
+        # the fused half-step: Y in, marginal in, spectra X of the new scaling out; the last two
+        # of a block's 2C half-steps also store the scaling (averaged over the block)
+        return 2 * spec + field + field / CHECK_EVERY, 0.0
+    if kind == "check_final":
+        # marginal check: Y in, marginal in, u in
+        return spec + 2 * field, 0.0
     if kind == "legendre_analysis":
         return table + spec + coef, legendre_flops_per_launch(nlat, lmax, nfields)
     if kind == "legendre_synthesis":
@@ -228,7 +229,8 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields):
 # captures of this file's 720 x 1440, 24-field runs (profiles/ncu_k_idft_720x1440.md,
 # ncu_k_legendre_tc_720x1440.md, ncu_k_legendre_tf32_720x1440.md); valid only for that workload,
 # precision and the kernels as captured.
-NCU_TRAFFIC = {("legendre_analysis", "bf16x3"): 532.7e6, ("legendre_synthesis", "bf16x3"): 521.7e6,
+NCU_TRAFFIC = {("inverse_dft_epilogue", "bf16x3"): (18 * 227.7e6 + 2 * 311.4e6) / 20,
+               ("legendre_analysis", "bf16x3"): 532.7e6, ("legendre_synthesis", "bf16x3"): 521.7e6,
                ("legendre_analysis", "tf32x3"): 528.5e6, ("legendre_synthesis", "tf32x3"): 612.9e6}
 
 

@@ -328,7 +328,8 @@ int shot_conv_compare(shot_grid g, double eps, const float* in, int nfields, dou
  * shot_profile_read: waits for the recorded events, then writes per kind the summed
  *   device time in ms and the number of launches, and clears the records.  Kinds:
  *   0 ring DFT (forward), 1 Legendre analysis, 2 Legendre synthesis,
- *   3 inverse ring DFT + Sinkhorn epilogue, 4 reductions and small kernels.
+ *   3 inverse ring DFT + Sinkhorn update (or a plain inverse transform), 4 reductions and
+ *   small kernels, 5 inverse ring DFT + marginal check or final objective.
  *   ms, launches: host arrays of nkinds entries. */
 int shot_launch_count(long long* n);
 int shot_profile_enable(int on);

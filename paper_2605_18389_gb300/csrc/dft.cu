@@ -343,7 +343,7 @@ int launch_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParam
   const size_t smem = (size_t)(fft_tw_len(g.plan) + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
   SHOT_CUDA(cudaFuncSetAttribute(k_idft<FG, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
-  ProfScope prof(PK_IDFT, st);
+  ProfScope prof(ep.mode == EPI_CHECK || ep.mode == EPI_FINAL ? PK_CHECK : PK_IDFT, st);
   count_launch();
   k_idft<FG, PL><<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, ep);
   SHOT_CUDA(cudaGetLastError());
@@ -357,7 +357,7 @@ int launch_idft_p_t(const Grid& g, const float* Y, int ldc, int nf, const EpiPar
   const int ngroups = (nf + FG - 1) / FG;
   const int nitems = ngroups * g.nh;
   const int grid = nitems < 3 * g.num_sms ? nitems : 3 * g.num_sms;
-  ProfScope prof(PK_IDFT, st);
+  ProfScope prof(ep.mode == EPI_CHECK || ep.mode == EPI_FINAL ? PK_CHECK : PK_IDFT, st);
   count_launch();
   k_idft_p<FG, PL><<<grid, kThreads, smem, st>>>(Y, ldc, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, g.plan, g.tw_d, ep,
                                                  ngroups);

@@ -247,7 +247,7 @@ template <int FG>
 int hp_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
   const size_t smem = hp_idft_smem(FG, g.nlon, g.lmax);
   SHOT_CUDA(cudaFuncSetAttribute(k_hp_idft<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  ProfScope prof(PK_IDFT, st);
+  ProfScope prof(ep.mode == EPI_CHECK || ep.mode == EPI_FINAL ? PK_CHECK : PK_IDFT, st);
   count_launch();
   k_hp_idft<FG><<<dim3((nf + FG - 1) / FG, g.nh), kHpThreads, smem, st>>>(
       Y, ldc, nf, g.npix, g.ring_len_d, g.ring_off_d, g.ring_phase_d, g.nlat, g.lmax, g.nh, (float)g.a_ring[0], ep,

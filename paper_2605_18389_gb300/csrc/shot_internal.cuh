@@ -23,7 +23,10 @@ int cuda_status(cudaError_t e, const char* what);   // SHOT_OK or SHOT_ERR_CUDA/
 
 // ---------------------------------------------------------------------------------
 // Launch accounting (prof.cu).  Kinds of shot_profile_read.
-enum ProfKind { PK_DFT = 0, PK_ANALYSIS = 1, PK_SYNTHESIS = 2, PK_IDFT = 3, PK_OTHER = 4, PK_NKINDS = 5 };
+// profiled launch kinds: ring DFT, Legendre analysis / synthesis, inverse DFT with the update
+// (or a plain inverse transform), other (reductions, set-up), inverse DFT with the marginal
+// check or the final objective
+enum ProfKind { PK_DFT = 0, PK_ANALYSIS = 1, PK_SYNTHESIS = 2, PK_IDFT = 3, PK_OTHER = 4, PK_CHECK = 5, PK_NKINDS = 6 };
 void count_launch(int n = 1);
 class ProfScope {
  public:

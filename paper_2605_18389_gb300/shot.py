@@ -80,7 +80,8 @@ SIGNATURES = {
     "shot_profile_read": [_c_dbl_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int],
 }
 
-PROFILE_KINDS = ("ring_dft", "legendre_analysis", "legendre_synthesis", "inverse_dft_epilogue", "other")
+PROFILE_KINDS = ("ring_dft", "legendre_analysis", "legendre_synthesis", "inverse_dft_epilogue", "other",
+                 "check_final")
 
 
 
