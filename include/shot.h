@@ -118,9 +118,9 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
  *   precision, legendre_mode as shot_grid_init.  shot_grid_info reports nlat = 4 nside - 1
  *   rings and nlon = 4 nside (the longest ring).
  * Supported on HEALPix grids: shot_heat_apply(_noalloc), shot_sht_analysis/synthesis,
- * shot_sinkhorn, shot_divergence(_multi), shot_gibbs_apply, shot_conv_compare; the gradient and
- * the regional attribution return SHOT_ERR_UNSUPPORTED.  Errors: INVALID_ARG, UNSUPPORTED,
- * OOM, CUDA.  Synchronises `stream`. */
+ * shot_sinkhorn, shot_divergence(_multi), shot_divergence_grad, shot_regional_rms,
+ * shot_gibbs_apply, shot_conv_compare.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ * Synchronises `stream`. */
 int shot_grid_init_healpix(shot_grid* out, int nside, int lmax, int precision, int legendre_mode, void* stream);
 
 /* Number of nodes of one field (nlat * nlon, or 12 nside^2 on HEALPix) into *npix. */

@@ -69,6 +69,11 @@ class HealpixGrid:
         return np.full((1, self.npix), self.area)
 
     @property
+    def lat_deg(self):
+        """Latitude of every pixel in degrees, shape [1, npix] (the rings are iso-latitude)."""
+        return (90.0 - np.degrees(np.arccos(self.z[self.ring_of])))[None]
+
+    @property
     def xyz(self):
         zz = self.z[self.ring_of]
         st = np.sqrt((1.0 - zz) * (1.0 + zz))

@@ -16,13 +16,14 @@ def band_masks(lat_deg):
 
 
 def regional_rms(grid, grad):
-    """grad: [..., nlat, nlon] dS/dp; returns [..., 5]."""
+    """grad: [..., nlat, nlon] dS/dp (HEALPix: [..., 1, npix]); returns [..., 5].  The band
+    masks come from the grid's latitudes, per ring ([nlat]) or per node (the node shape)."""
     a = grid.a
     g = np.asarray(grad, dtype=np.float64) / a
     mean = np.sum(a * g, axis=(-2, -1), keepdims=True) / np.sum(a)
     c = g - mean
     out = []
     for mask in band_masks(grid.lat_deg):
-        w = a * mask[:, None]
+        w = a * (mask if mask.shape == a.shape else mask[:, None])
         out.append(np.sqrt(np.sum(w * c * c, axis=(-2, -1)) / np.sum(w)))
     return np.stack(out, axis=-1)

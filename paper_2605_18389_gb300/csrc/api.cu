@@ -1160,10 +1160,6 @@ int shot_divergence_grad(shot_grid gh, const float* p, const float* q, int batch
     set_error("shot_divergence_grad: S, grad_p, status required; mode UNROLLED or ENVELOPE");
     return SHOT_ERR_INVALID_ARG;
   }
-  if (g->quad == SHOT_QUAD_HEALPIX) {
-    set_error("shot_divergence_grad: not built for HEALPix grids");
-    return SHOT_ERR_UNSUPPORTED;
-  }
   return divergence_grad(*g, p, q, batch, eps, tau, max_iter, checkpoint_every, mode, S, grad_p, status,
                          as_stream(stream));
 }

@@ -378,11 +378,11 @@ using Plan1024 = CtPlan<1024, 4, 16, 16>;   // 512 x 1024 grids
 int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
                    float* X, int ldc, cudaStream_t st, int xsplit) {
   if (g.quad == SHOT_QUAD_HEALPIX) {
-    if (scale_which || xsplit) {
-      set_error("HEALPix ring transform: no per-field scaling, FP32 spectra only");
+    if (xsplit || (scale_which && scale_which != 1)) {
+      set_error("HEALPix ring transform: FP32 spectra and the per-field factor beta only");
       return SHOT_ERR_UNSUPPORTED;
     }
-    return launch_hp_dft_fwd(g, in, nf, X, ldc, st);
+    return launch_hp_dft_fwd(g, in, nf, X, ldc, st, scale_which == 1 ? ps : nullptr);
   }
   if (g.nlon > kFftCap) {
     set_error("nlon too large for the shared-memory ring FFT");

@@ -46,6 +46,14 @@ namespace {
 
 constexpr int kEw = 256;
 
+// ring layout of a field: ring j holds len[j] nodes starting at off[j]; a field has npix nodes
+struct Rings {
+  const int* len;
+  const long long* off;
+  long long npix;
+  int nring;
+};
+
 __device__ __forceinline__ float block_sum_f(float v, float* red) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -66,16 +74,17 @@ struct GScal {      // per problem and iteration of a segment
 
 // forward half-step: out = (m / Kf)^g; partial sums per ring of
 //   balanced: sum out;  unbalanced: sum a m out^{-eps/tau}
-__global__ void k_g_update(int nlat, int nlon, const float* __restrict__ a_ring, const float* const* __restrict__ marg,
+__global__ void k_g_update(Rings R, const float* __restrict__ a_ring, const float* const* __restrict__ marg,
                            const float* __restrict__ Kf, float* __restrict__ out, int balanced, float gam, float et,
                            double* __restrict__ part) {
   __shared__ float red[32];
   const int j = blockIdx.x, b = blockIdx.y;
-  const size_t base = ((size_t)b * nlat + j) * nlon;
-  const float* m = marg[b] + (size_t)j * nlon;
+  const size_t base = (size_t)b * R.npix + R.off[j];
+  const int nk = R.len[j];
+  const float* m = marg[b] + R.off[j];
   const float aj = a_ring[j];
   float acc = 0.f;
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x) {
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
     const float mm = m[k];
     const float r = mm / Kf[base + k];
     const float u = balanced ? r : powf(r, gam);
@@ -83,7 +92,7 @@ __global__ void k_g_update(int nlat, int nlon, const float* __restrict__ a_ring,
     acc += balanced ? u : (mm > 0.f ? aj * mm * powf(u, -et) : 0.f);
   }
   const float t = block_sum_f(acc, red);
-  if (threadIdx.x == 0) part[(size_t)b * nlat + j] = (double)t;
+  if (threadIdx.x == 0) part[(size_t)b * R.nring + j] = (double)t;
 }
 
 // scalars of iteration k after both half-steps: (al, be) and the ProbState beta used by
@@ -127,16 +136,17 @@ __global__ void k_g_set_beta(int nprob, const GScal* __restrict__ sc, ProbState*
 }
 
 // initial adjoints from Alg. 1's return (T = last iteration): u~, v~, p~, q~
-__global__ void k_g_seed(int nlat, int nlon, const float* const* __restrict__ P, const float* const* __restrict__ Q,
+__global__ void k_g_seed(Rings R, const float* const* __restrict__ P, const float* const* __restrict__ Q,
                          const float* __restrict__ U, const float* __restrict__ V, const GScal* __restrict__ sc,
                          int balanced, float eps, float tau, float* __restrict__ ut, float* __restrict__ vt,
                          float* __restrict__ pt, float* __restrict__ qt) {
   const int j = blockIdx.x, b = blockIdx.y;
-  const size_t base = ((size_t)b * nlat + j) * nlon;
+  const size_t base = (size_t)b * R.npix + R.off[j];
+  const int nk = R.len[j];
   const float al = (float)sc[b].al, be = (float)sc[b].be;
   const float et = eps / tau;
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x) {
-    const float p = P[b][(size_t)j * nlon + k], q = Q[b][(size_t)j * nlon + k];
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    const float p = P[b][R.off[j] + k], q = Q[b][R.off[j] + k];
     const float u = al * U[base + k], v = be * V[base + k];
     if (balanced) {
       ut[base + k] = p > 0.f ? eps * p / u : 0.f;
@@ -154,14 +164,15 @@ __global__ void k_g_seed(int nlat, int nlon, const float* const* __restrict__ P,
 }
 
 // partial sums per ring of  sum a u~ u'  and  sum a v~ v'
-__global__ void k_g_rsum(int nlat, int nlon, const float* __restrict__ a_ring, const float* __restrict__ ut,
+__global__ void k_g_rsum(Rings R, const float* __restrict__ a_ring, const float* __restrict__ ut,
                          const float* __restrict__ vt, const float* __restrict__ U, const float* __restrict__ V,
                          double* __restrict__ p1, double* __restrict__ p2) {
   __shared__ float red[32];
   const int j = blockIdx.x, b = blockIdx.y;
-  const size_t base = ((size_t)b * nlat + j) * nlon;
+  const size_t base = (size_t)b * R.npix + R.off[j];
+  const int nk = R.len[j];
   float s1 = 0.f, s2 = 0.f;
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x) {
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
     s1 += ut[base + k] * U[base + k];
     s2 += vt[base + k] * V[base + k];
   }
@@ -169,8 +180,8 @@ __global__ void k_g_rsum(int nlat, int nlon, const float* __restrict__ a_ring, c
   const float t1 = block_sum_f(s1, red);
   const float t2 = block_sum_f(s2, red);
   if (threadIdx.x == 0) {
-    p1[(size_t)b * nlat + j] = (double)(aj * t1);
-    p2[(size_t)b * nlat + j] = (double)(aj * t2);
+    p1[(size_t)b * R.nring + j] = (double)(aj * t1);
+    p2[(size_t)b * R.nring + j] = (double)(aj * t2);
   }
 }
 
@@ -204,19 +215,20 @@ __global__ void k_g_rscal(int nprob, int nlat, const double* __restrict__ p1, co
 }
 
 // first pointwise reverse stage: u~' (before + K (Ku)~), (Ku)~, q~ updates
-__global__ void k_g_rev1(int nlat, int nlon, const float* __restrict__ a_ring, const float* const* __restrict__ P,
+__global__ void k_g_rev1(Rings R, const float* __restrict__ a_ring, const float* const* __restrict__ P,
                          const float* const* __restrict__ Q, const float* __restrict__ U, const float* __restrict__ V,
                          const GScal* __restrict__ sc, const RevScal* __restrict__ rs, int balanced, float gam, float et,
                          float* __restrict__ ut, const float* __restrict__ vt, float* __restrict__ qt,
                          float* __restrict__ kut, float* __restrict__ pt) {
   const int j = blockIdx.x, b = blockIdx.y;
-  const size_t base = ((size_t)b * nlat + j) * nlon;
+  const size_t base = (size_t)b * R.npix + R.off[j];
+  const int nk = R.len[j];
   const float aj = a_ring[j];
   const GScal s = sc[b];
   const RevScal r = rs[b];
   const float al = (float)s.al, be = (float)s.be;
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x) {
-    const float p = P[b][(size_t)j * nlon + k], q = Q[b][(size_t)j * nlon + k];
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    const float p = P[b][R.off[j] + k], q = Q[b][R.off[j] + k];
     const float u1 = U[base + k], v1 = V[base + k];
     float uu, vv;
     if (balanced) {
@@ -240,13 +252,14 @@ __global__ void k_g_rev1(int nlat, int nlon, const float* __restrict__ a_ring, c
 }
 
 // second pointwise reverse stage: u~' += K (Ku)~ ; (Kv)~ ; p~ update
-__global__ void k_g_rev2(int nlat, int nlon, const float* const* __restrict__ P, const float* __restrict__ U,
+__global__ void k_g_rev2(Rings R, const float* const* __restrict__ P, const float* __restrict__ U,
                          const float* __restrict__ kku, int balanced, float gam, float* __restrict__ ut,
                          float* __restrict__ kvt, float* __restrict__ pt) {
   const int j = blockIdx.x, b = blockIdx.y;
-  const size_t base = ((size_t)b * nlat + j) * nlon;
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x) {
-    const float p = P[b][(size_t)j * nlon + k];
+  const size_t base = (size_t)b * R.npix + R.off[j];
+  const int nk = R.len[j];
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    const float p = P[b][R.off[j] + k];
     const float u1 = U[base + k];
     const float uu = ut[base + k] + kku[base + k];
     if (p > 0.f) {
@@ -261,31 +274,33 @@ __global__ void k_g_rev2(int nlat, int nlon, const float* const* __restrict__ P,
 }
 
 // dS/dp for pair b from the (p,q) problem b and the (p,p) problem B + b
-__global__ void k_g_assemble(int nlat, int nlon, int batch, const float* __restrict__ a_ring,
+__global__ void k_g_assemble(Rings R, int batch, const float* __restrict__ a_ring,
                              const float* __restrict__ pt, const float* __restrict__ qt, const double* __restrict__ dm,
                              double eps, float* __restrict__ grad) {
   const int j = blockIdx.x, b = blockIdx.y;
-  const size_t n = (size_t)nlat * nlon;
-  const size_t o = (size_t)b * n + (size_t)j * nlon;
-  const size_t oA = (size_t)b * n + (size_t)j * nlon;
-  const size_t oB = (size_t)(batch + b) * n + (size_t)j * nlon;
+  const size_t n = (size_t)R.npix;
+  const size_t o = (size_t)b * n + R.off[j];
+  const size_t oA = o;
+  const size_t oB = (size_t)(batch + b) * n + R.off[j];
+  const int nk = R.len[j];
   const float aj = a_ring[j];
   const float mt = (float)(eps * dm[b]);
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x)
+  for (int k = threadIdx.x; k < nk; k += blockDim.x)
     grad[o + k] = aj * (pt[oA + k] - 0.5f * (pt[oB + k] + qt[oB + k]) + mt);
 }
 
 // envelope form from the converged scalings of all 3B problems (u3, v3 hold u_T, v_T)
-__global__ void k_g_envelope(int nlat, int nlon, int batch, const float* __restrict__ a_ring,
+__global__ void k_g_envelope(Rings R, int batch, const float* __restrict__ a_ring,
                              const float* __restrict__ u3, const float* __restrict__ v3, const double* __restrict__ dm,
                              int balanced, float eps, float tau, float* __restrict__ grad) {
   const int j = blockIdx.x, b = blockIdx.y;
-  const size_t n = (size_t)nlat * nlon;
-  const size_t o = (size_t)b * n + (size_t)j * nlon;
-  const size_t oB = (size_t)(batch + b) * n + (size_t)j * nlon;
+  const size_t n = (size_t)R.npix;
+  const size_t o = (size_t)b * n + R.off[j];
+  const size_t oB = (size_t)(batch + b) * n + R.off[j];
+  const int nk = R.len[j];
   const float aj = a_ring[j];
   const float et = eps / tau;
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x) {
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
     const float la = logf(u3[o + k]), lpp = logf(u3[oB + k]), lqp = logf(v3[oB + k]);
     float g;
     if (balanced) {
@@ -303,16 +318,18 @@ __global__ void k_g_fill_ones(float* __restrict__ a, size_t n) {
 }
 
 // m(p_b) - m(q_b) = sum_i a_i (p_b - q_b)_i in FP64, one block per pair
-__global__ void k_g_mass_diff(int nlat, int nlon, const float* __restrict__ p, const float* __restrict__ q,
+__global__ void k_g_mass_diff(Rings R, const float* __restrict__ p, const float* __restrict__ q,
                               const float* __restrict__ a_ring, double* __restrict__ dm) {
   __shared__ double red[32];
-  const size_t n = (size_t)nlat * nlon;
+  const size_t n = (size_t)R.npix;
   const float* pb = p + (size_t)blockIdx.x * n;
   const float* qb = q + (size_t)blockIdx.x * n;
   double s = 0.0;
-  for (int j = 0; j < nlat; ++j) {
+  for (int j = 0; j < R.nring; ++j) {
     float t = 0.f;
-    for (int k = threadIdx.x; k < nlon; k += blockDim.x) t += pb[(size_t)j * nlon + k] - qb[(size_t)j * nlon + k];
+    const float* pr = pb + R.off[j];
+    const float* qr = qb + R.off[j];
+    for (int k = threadIdx.x; k < R.len[j]; k += blockDim.x) t += pr[k] - qr[k];
     s += (double)a_ring[j] * (double)t;
   }
 #pragma unroll
@@ -342,7 +359,8 @@ static int heat_fields(Grid& g, const float* in, float* out, int nf, const ProbS
 
 int divergence_grad(Grid& g, const float* p, const float* q, int batch, double eps, double tau, int T, int ck,
                     int mode, double* S, float* grad, int* status, cudaStream_t st) {
-  const size_t n = (size_t)g.nlat * g.nlon;
+  const size_t n = (size_t)g.npix;
+  const Rings rings{g.ring_len_d, g.ring_off_d, (long long)g.npix, g.nlat};
   const int np3 = 3 * batch, np = 2 * batch;
   const bool balanced = isinf(tau);
   int rc;
@@ -372,7 +390,7 @@ int divergence_grad(Grid& g, const float* p, const float* q, int batch, double e
   // m(p_b) - m(q_b) (device, FP64)
   SHOT_CUDA(cudaMalloc(&dbufs, (size_t)batch * sizeof(double)));
   count_launch();
-  k_g_mass_diff<<<batch, 256, 0, st>>>(g.nlat, g.nlon, p, q, g.a_d, dbufs);
+  k_g_mass_diff<<<batch, 256, 0, st>>>(rings, p, q, g.a_d, dbufs);
   SHOT_CUDA(cudaGetLastError());
   std::vector<double> dm(batch);
   SHOT_CUDA(cudaMemcpyAsync(dm.data(), dbufs, batch * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -390,7 +408,7 @@ int divergence_grad(Grid& g, const float* p, const float* q, int batch, double e
   dim3 ew(g.nlat, batch);
   if (mode == SHOT_GRAD_ENVELOPE) {
     count_launch();
-    k_g_envelope<<<ew, kEw, 0, st>>>(g.nlat, g.nlon, batch, g.a_d, u3, v3, dbufs, balanced ? 1 : 0, (float)eps,
+    k_g_envelope<<<ew, kEw, 0, st>>>(rings, batch, g.a_d, u3, v3, dbufs, balanced ? 1 : 0, (float)eps,
                                      (float)tau, grad);
     SHOT_CUDA(cudaGetLastError());
     SHOT_CUDA(cudaStreamSynchronize(st));
@@ -463,10 +481,10 @@ int divergence_grad(Grid& g, const float* p, const float* q, int batch, double e
     int r;
     if ((r = heat_fields(g, vprev, kf, np, ps, st))) return r;
     count_launch();
-    k_g_update<<<ewp, kEw, 0, st>>>(g.nlat, g.nlon, g.a_d, Pl, kf, uo, bal, gam, et, partU);
+    k_g_update<<<ewp, kEw, 0, st>>>(rings, g.a_d, Pl, kf, uo, bal, gam, et, partU);
     if ((r = heat_fields(g, uo, kf, np, nullptr, st))) return r;
     count_launch(2);
-    k_g_update<<<ewp, kEw, 0, st>>>(g.nlat, g.nlon, g.a_d, Ql, kf, vo, bal, gam, et, partV);
+    k_g_update<<<ewp, kEw, 0, st>>>(rings, g.a_d, Ql, kf, vo, bal, gam, et, partV);
     k_g_scalars<<<nb, 128, 0, st>>>(np, g.nlat, partU, partV, bal, eps, tau, slot, ps);
     SHOT_CUDA(cudaGetLastError());
     return SHOT_OK;
@@ -516,17 +534,17 @@ int divergence_grad(Grid& g, const float* p, const float* q, int batch, double e
       const GScal* s_i = sc + (size_t)i * np;
       if (!seeded) {
         count_launch();
-        k_g_seed<<<ewp, kEw, 0, st>>>(g.nlat, g.nlon, Pl, Ql, U, V, s_i, bal, (float)eps, (float)tau, ut, vt, pt, qt);
+        k_g_seed<<<ewp, kEw, 0, st>>>(rings, Pl, Ql, U, V, s_i, bal, (float)eps, (float)tau, ut, vt, pt, qt);
         seeded = true;
       }
       count_launch(3);
-      k_g_rsum<<<ewp, kEw, 0, st>>>(g.nlat, g.nlon, g.a_d, ut, vt, U, V, partU, partV);
+      k_g_rsum<<<ewp, kEw, 0, st>>>(rings, g.a_d, ut, vt, U, V, partU, partV);
       k_g_rscal<<<nb, 128, 0, st>>>(np, g.nlat, partU, partV, s_i, bal, eps, tau, rs);
-      k_g_rev1<<<ewp, kEw, 0, st>>>(g.nlat, g.nlon, g.a_d, Pl, Ql, U, V, s_i, rs, bal, gam, et, ut, vt, qt, t1, pt);
+      k_g_rev1<<<ewp, kEw, 0, st>>>(rings, g.a_d, Pl, Ql, U, V, s_i, rs, bal, gam, et, ut, vt, qt, t1, pt);
       SHOT_CUDA(cudaGetLastError());
       if ((rc = heat_fields(g, t1, t2, np, nullptr, st))) { cleanup2(); return rc; }
       count_launch();
-      k_g_rev2<<<ewp, kEw, 0, st>>>(g.nlat, g.nlon, Pl, U, t2, bal, gam, ut, t1, pt);
+      k_g_rev2<<<ewp, kEw, 0, st>>>(rings, Pl, U, t2, bal, gam, ut, t1, pt);
       SHOT_CUDA(cudaGetLastError());
       if ((rc = heat_fields(g, t1, vt, np, nullptr, st))) { cleanup2(); return rc; }
     }
@@ -536,7 +554,7 @@ int divergence_grad(Grid& g, const float* p, const float* q, int batch, double e
     SHOT_CUDA(cudaMemsetAsync(qt, 0, fld * sizeof(float), st));
   }
   count_launch();
-  k_g_assemble<<<ew, kEw, 0, st>>>(g.nlat, g.nlon, batch, g.a_d, pt, qt, dbufs, eps, grad);
+  k_g_assemble<<<ew, kEw, 0, st>>>(rings, batch, g.a_d, pt, qt, dbufs, eps, grad);
   SHOT_CUDA(cudaGetLastError());
   SHOT_CUDA(cudaStreamSynchronize(st));
   cleanup2();

@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_fwd(const float* __restrict__
                                                        float area, float* __restrict__ X, int ldc,
                                                        const int* __restrict__ rplan, const FftPlan* __restrict__ plans,
                                                        const float2* __restrict__ tw_all,
-                                                       const int* __restrict__ tw_base) {
+                                                       const int* __restrict__ tw_base,
+                                                       const ProbState* __restrict__ ps) {
   extern __shared__ __align__(16) float2 sm[];
   const int jh = blockIdx.y, f0 = blockIdx.x * FG;
   const int nfg = min(FG, nf - f0);
@@ -138,7 +139,9 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_fwd(const float* __restrict__
   for (int q = 0; q < nfg; ++q) {
     const float* fj = in + (size_t)(f0 + q) * npix + roff[j];
     const float* fJ = in + (size_t)(f0 + q) * npix + roff[J];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) zb[q * ld + k] = make_float2(fj[k], J != j ? fJ[k] : 0.f);
+    const float sc = ps ? (float)ps[f0 + q].beta : 1.f;   // per-field factor (gradient sweeps)
+    for (int k = threadIdx.x; k < n; k += blockDim.x)
+      zb[q * ld + k] = make_float2(sc * fj[k], J != j ? sc * fJ[k] : 0.f);
   }
   __syncthreads();
   const float2* D = ring_transform<false>(zb, db, tw, n, nfg, pi, plans, tw_all, tw_base);
@@ -231,14 +234,14 @@ int hp_pick_fg(const Grid& g, int nf, bool inverse) {
 }
 
 template <int FG>
-int hp_fwd_t(const Grid& g, const float* in, int nf, float* X, int ldc, cudaStream_t st) {
+int hp_fwd_t(const Grid& g, const float* in, int nf, float* X, int ldc, cudaStream_t st, const ProbState* ps) {
   const size_t smem = hp_fwd_smem(FG, g.nlon, g.lmax);
   SHOT_CUDA(cudaFuncSetAttribute(k_hp_fwd<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   ProfScope prof(PK_DFT, st);
   count_launch();
   k_hp_fwd<FG><<<dim3((nf + FG - 1) / FG, g.nh), kHpThreads, smem, st>>>(
       in, nf, g.npix, g.ring_len_d, g.ring_off_d, g.ring_phase_d, g.nlat, g.lmax, g.nh, (float)g.a_ring[0], X, ldc,
-      g.ring_plan_d, g.hp_plan_d, g.hp_tw_d, g.hp_tw_base_d);
+      g.ring_plan_d, g.hp_plan_d, g.hp_tw_d, g.hp_tw_base_d, ps);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }
@@ -258,11 +261,12 @@ int hp_idft_t(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& e
 
 }  // namespace
 
-int launch_hp_dft_fwd(const Grid& g, const float* in, int nf, float* X, int ldc, cudaStream_t st) {
+int launch_hp_dft_fwd(const Grid& g, const float* in, int nf, float* X, int ldc, cudaStream_t st,
+                      const ProbState* ps) {
   switch (hp_pick_fg(g, nf, false)) {
-    case 4: return hp_fwd_t<4>(g, in, nf, X, ldc, st);
-    case 2: return hp_fwd_t<2>(g, in, nf, X, ldc, st);
-    default: return hp_fwd_t<1>(g, in, nf, X, ldc, st);
+    case 4: return hp_fwd_t<4>(g, in, nf, X, ldc, st, ps);
+    case 2: return hp_fwd_t<2>(g, in, nf, X, ldc, st, ps);
+    default: return hp_fwd_t<1>(g, in, nf, X, ldc, st, ps);
   }
 }
 

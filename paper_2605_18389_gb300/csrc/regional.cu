@@ -13,15 +13,19 @@ namespace shot {
 namespace {
 
 
-// per (ring, field): sum_k g and sum_k g^2 of the field form g = grad / a_j
-__global__ void k_ring_moments(int nlat, int nlon, const float* __restrict__ grad, const float* __restrict__ a_ring,
+// per (ring, field): sum_k g and sum_k g^2 of the field form g = grad / a_j; ring j holds
+// rlen[j] nodes from roff[j] of a field of npix nodes
+__global__ void k_ring_moments(int nring, const int* __restrict__ rlen, const long long* __restrict__ roff,
+                               long long npix, const float* __restrict__ grad, const float* __restrict__ a_ring,
                                double* __restrict__ mom) {
   __shared__ float r1[32], r2[32];
   const int j = blockIdx.x, b = blockIdx.y;
+  const int nlat = nring;
   const float inv_a = 1.f / a_ring[j];
-  const float* row = grad + ((size_t)b * nlat + j) * nlon;
+  const float* row = grad + (size_t)b * npix + roff[j];
+  const int nk = rlen[j];
   float s1 = 0.f, s2 = 0.f;
-  for (int k = threadIdx.x; k < nlon; k += blockDim.x) {
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
     const float g = row[k] * inv_a;
     s1 += g;
     s2 += g * g;
@@ -57,15 +61,12 @@ extern "C" int shot_regional_rms(shot_grid gh, const float* grad_p, int batch, d
     set_error("shot_regional_rms: bad argument");
     return SHOT_ERR_INVALID_ARG;
   }
-  if (g->quad == SHOT_QUAD_HEALPIX) {
-    set_error("shot_regional_rms: not built for HEALPix grids");
-    return SHOT_ERR_UNSUPPORTED;
-  }
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   double* mom = nullptr;
   SHOT_CUDA(cudaMalloc(&mom, (size_t)batch * g->nlat * 2 * sizeof(double)));
   count_launch();
-  k_ring_moments<<<dim3(g->nlat, batch), 256, 0, st>>>(g->nlat, g->nlon, grad_p, g->a_d, mom);
+  k_ring_moments<<<dim3(g->nlat, batch), 256, 0, st>>>(g->nlat, g->ring_len_d, g->ring_off_d, (long long)g->npix,
+                                                        grad_p, g->a_d, mom);
   cudaError_t e = cudaGetLastError();
   std::vector<double> h((size_t)batch * g->nlat * 2);
   if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), mom, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -78,7 +79,7 @@ extern "C" int shot_regional_rms(shot_grid gh, const float* grad_p, int batch, d
     double s1 = 0.0, area = 0.0;
     for (int j = 0; j < g->nlat; ++j) {
       s1 += g->a_ring[j] * h[((size_t)b * g->nlat + j) * 2];
-      area += g->a_ring[j] * g->nlon;
+      area += g->a_ring[j] * g->ring_len[j];
     }
     const double mean = s1 / area;   // area-weighted mean of the field form
     double S0[5] = {0}, S1[5] = {0}, S2[5] = {0};
@@ -90,7 +91,7 @@ extern "C" int shot_regional_rms(shot_grid gh, const float* grad_p, int batch, d
       const double m1 = h[((size_t)b * g->nlat + j) * 2], m2 = h[((size_t)b * g->nlat + j) * 2 + 1];
       for (int r = 0; r < 5; ++r)
         if (in[r]) {
-          S0[r] += a * g->nlon;
+          S0[r] += a * g->ring_len[j];
           S1[r] += a * m1;
           S2[r] += a * m2;
         }

@@ -279,7 +279,9 @@ int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cud
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
 // HEALPix
 void healpix_geometry(Grid& g, int nside);
-int launch_hp_dft_fwd(const Grid& g, const float* in, int nf, float* X, int ldc, cudaStream_t st);
+// ps != nullptr: every field is multiplied by its ProbState::beta on load
+int launch_hp_dft_fwd(const Grid& g, const float* in, int nf, float* X, int ldc, cudaStream_t st,
+                      const ProbState* ps = nullptr);
 int launch_hp_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
 
 }  // namespace shot

@@ -127,13 +127,49 @@ def test_gibbs_and_comparison_on_healpix():
     shot.shot_grid_free(g)
 
 
-def test_unsupported_calls_are_rejected():
-    g, og = _grid(4)
-    p = torch.full((1, og.npix), 1.0 / (4 * np.pi), device="cuda")
-    with pytest.raises(shot.ShotError):
-        shot.shot_divergence_grad(g, p, p, 0.1, max_iter=5)
-    with pytest.raises(shot.ShotError):
-        shot.shot_regional_rms(g, p)
+def test_bad_nside_is_rejected():
     with pytest.raises(shot.ShotError):
         shot.shot_grid_init_healpix(0)
-    shot.shot_grid_free(g)
+
+
+@pytest.mark.parametrize("nside,eps,tau,T,ck", [(4, 0.2, math.inf, 30, 7), (4, 0.2, 1.0, 30, 10)])
+def test_unrolled_gradient_matches_oracle_fd(nside, eps, tau, T, ck):
+    """The gradient of S (Sec. 4.2) on a HEALPix grid: directional derivatives of the unrolled
+    adjoint against central differences of the oracle's S after the same T iterations."""
+    from oracle.gradient import fd_directional
+    g, og = _grid(nside)
+    try:
+        bal = math.isinf(tau)
+        (p32, p), (q32, q) = _pairs(og, 300 + nside, 2, masses=not bal)
+        rc, r = shot.shot_divergence_grad(g, torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), eps, tau,
+                                          max_iter=T, checkpoint_every=ck, mode=shot.SHOT_GRAD_UNROLLED)
+        assert rc >= 0 and np.all(r["status"] >= 0)
+        grad = r["grad"].cpu().numpy().astype(np.float64)
+        rng = np.random.default_rng(17)
+        for b in range(2):
+            dirs = []
+            for _ in range(3):
+                d = p[b] * rng.normal(size=og.npix)
+                if bal:
+                    d -= np.mean(d)   # equal areas: keeps the mass
+                d *= np.sqrt(np.sum(p[b] * p[b]) / np.sum(d * d))
+                dirs.append(d[None, :])
+            dirs = np.array(dirs)
+            fd = fd_directional(og, p[b][None, :], q[b][None, :], eps, tau, T, dirs, h=1e-5)
+            got = np.array([np.sum(grad[b] * d[0]) for d in dirs])
+            assert np.max(np.abs(got - fd)) <= 1e-4 * np.max(np.abs(fd)), (got, fd)
+    finally:
+        shot.shot_grid_free(g)
+
+
+def test_regional_rms_matches_oracle():
+    from oracle.regional import regional_rms
+    g, og = _grid(16)
+    try:
+        rng = np.random.default_rng(16)
+        grad = (og.area * rng.normal(size=(3, og.npix))).astype(np.float32)
+        got = shot.shot_regional_rms(g, torch.from_numpy(grad).cuda())
+        ref = regional_rms(og, grad.astype(np.float64)[:, None, :])
+        np.testing.assert_allclose(got, ref, rtol=1e-5)
+    finally:
+        shot.shot_grid_free(g)

@@ -85,3 +85,31 @@ def test_sinkhorn_on_healpix():
     assert r["S"][0] > 0
     rpp = sk.divergence(g, p, p, 0.1, T=300, delta=1e-10, C=10)
     assert abs(rpp["S"][0]) < 1e-12
+
+
+def test_regional_bands_on_healpix():
+    """Sec. 4.2 / App. E on HEALPix: with equal-area pixels, a band's pixel fraction approaches
+    its exact area fraction (sin 23.5 deg for the Tropics, sin 10 deg for the ITCZ,
+    (sin 60 - sin 30)/2 for each mid-latitude band, (1 - sin 66.5)/2 for the Arctic) to
+    within the ring spacing; a constant field form has zero RMS everywhere, and the
+    hemisphere sign field (mean zero on the symmetric grid) has RMS 1 in every band."""
+    from oracle.regional import regional_rms, band_masks
+    og = HealpixGrid(32)
+    lat = og.lat_deg
+    s = lambda d: np.sin(np.radians(d))
+    exact = [s(23.5), s(10.0), (s(60.0) - s(30.0)) / 2, (s(60.0) - s(30.0)) / 2, (1 - s(66.5)) / 2]
+    for mask, e in zip(band_masks(lat), exact):
+        assert abs(mask.mean() - e) < 2.0 / og.nside
+    a = og.a
+    const = 3.0 * a[None]
+    np.testing.assert_allclose(regional_rms(og, const), 0.0, atol=1e-12)
+    # sign(lat) has mean zero (the grid is symmetric, the equator ring is 0): RMS 1 in the
+    # bands off the equator; in the two equatorial bands the equator ring's zeros leave
+    # sqrt(1 - n_eq / n_band)
+    sign = np.sign(lat)[None] * a[None]
+    got = regional_rms(og, sign)[0]
+    eq = np.abs(lat) < 1e-9
+    for r, mask in enumerate(band_masks(lat)):
+        want = np.sqrt(1.0 - np.sum(mask & eq) / np.sum(mask))
+        assert abs(got[r] - want) < 1e-12
+    assert np.sum(eq) == 4 * og.nside
