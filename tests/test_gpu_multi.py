@@ -71,3 +71,30 @@ def test_graph_replay_equals_profiled_eager_launches():
         np.testing.assert_array_equal(r_graph["S"], r_eager["S"])
     finally:
         shot.shot_grid_free(g)
+
+
+def test_configuration3_sets_with_scalings_beyond_fp32():
+    """Configuration 3's kind of batch at eps = 0.01 (t = 2.5e-3): tau in {0.1, 1, 10} with
+    masses far apart (0.6 vs 1.7 and 1.8 vs 0.55) on one grid in one solve.  At tau = 10 the
+    potentials reach ~6 = 600 eps, so the scalings leave FP32 (the solver carries them as FP32
+    buffers times FP64 factors); S matches the FP64 oracle for every set."""
+    eps, T = 0.01, 40
+    g, og = shot.shot_grid_init(64), OGrid(64)
+    try:
+        sets, refs = [], []
+        for i, tau in enumerate((0.1, 1.0, 10.0)):
+            p, q = inputs.pairs("paper_uniform", 3300 + i, 2, og.x, og.nlon, og.a_ring)
+            p32, p64 = f32(p * np.array([0.6, 1.8])[:, None, None])
+            q32, q64 = f32(q * np.array([1.7, 0.55])[:, None, None])
+            sets.append(dict(grid=g, p=torch.from_numpy(p32).cuda(), q=torch.from_numpy(q32).cuda(), eps=eps,
+                             tau=tau))
+            refs.append(sk.divergence(og, p64, q64, eps, tau, T=T, delta=0.0, C=10))
+        assert np.max(np.abs(refs[2]["runs"]["phi"])) / eps > 200.0
+        rc, outs = shot.shot_divergence_multi(sets, max_iter=T, tol=0.0, check_every=10)
+        assert rc >= 0
+        for o, ref in zip(outs, refs):
+            assert np.all(o["status"] == 0) and np.all(ref["status"] == 0)
+            ot_pq = ref["runs"]["ot"][: len(o["S"])]
+            assert np.all(s_err(o["S"], ref["S"], ot_pq, TOL_S) <= 1.0), (o["S"], ref["S"])
+    finally:
+        shot.shot_grid_free(g)
