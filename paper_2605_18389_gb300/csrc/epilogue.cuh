@@ -121,7 +121,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
       }
       const float* mg = F.marg;
       const int bal = F.balanced;
-      const float gam = F.gamma, et = F.et, rr = F.r;
+      const float gam = F.gamma, rr = F.r, rinv = 1.f / F.r;
       for (int k0 = threadIdx.x; k0 < N; k0 += kEpiBatch * NT) {
         // the marginal values of all this thread's longitudes first, then the arithmetic
         float pv[kEpiBatch][2];
@@ -148,12 +148,12 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
               u = ratio;
               acc[q][0] += u;
             } else {
-              // u = (p/Kv)^gamma;  p u^{-eps/tau} = p (p/Kv)^{-eps/(tau+eps)}: both powers from one
-              // base-2 logarithm of the ratio (hardware log2/exp2, ~2^-21 absolute in the exponent;
-              // ratio = 0 gives u = 0, and p = 0 contributes nothing to the sum)
-              const float l2 = __log2f(ratio);
-              u = exp2f(gam * l2);
-              if (pm > 0.f) acc[q][0] += aj * pm * exp2f(-et * l2);
+              // u = (r p/Kv)^gamma (hardware log2/exp2, ~2^-21 absolute in the exponent); the
+              // translation-invariant sum's p u^{-eps/tau} = p (r p/Kv)^{-eps/(tau+eps)} equals
+              // u (Kv) / r since gamma + eps/(tau+eps) = 1, so one power serves both (ratio = 0
+              // gives u = 0 and adds nothing)
+              u = exp2f(gam * __log2f(ratio));
+              acc[q][0] += aj * u * kv * rinv;
               acc[q][1] += u;
             }
             // one test on the common path: K v positive and finite, u finite (NaN fails each

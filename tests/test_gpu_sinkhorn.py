@@ -244,3 +244,43 @@ def test_potentials_flag_returns_eps_log_scalings(grid_cache):
         u, v = r["u"].cpu().double().numpy(), r["v"].cpu().double().numpy()
         assert rel_max(r2["u"].cpu().numpy(), 0.1 * np.log(u)) < 1e-6
         assert rel_max(r2["v"].cpu().numpy(), 0.1 * np.log(v)) < 1e-6
+
+
+@pytest.mark.parametrize("prec,tau", [("fp32", math.inf), ("bf16x3", math.inf), ("fp32", 1.0)])
+def test_full_size_first_iteration_matches_oracle(prec, tau):
+    """GL 720 x 1440 (the headline grid, t = 1e-4) through the solver's own launch path
+    (persistent update kernel, graph-free single block, final pass): after one iteration of
+    Alg. 1 the returned u, v equal the oracle's first iteration (u' = (p / K 1)^g,
+    v' = (q / K u')^g, then the gauge or the translation-invariant step) at every node."""
+    from oracle.sht import heat_apply
+    nlat, eps = 720, 4e-4
+    og = OGrid(nlat)
+    g = shot.shot_grid_init(nlat, None, -1, shot.SHOT_FP32 if prec == "fp32" else shot.SHOT_BF16X3)
+    try:
+        unb = not math.isinf(tau)
+        # unit masses also for tau = 1: with masses U[0.5, 2] the translation-invariant constant
+        # at eps = 4e-4 is e^{+-c/eps} ~ e^{+-800}, beyond FP64 (and so beyond the oracle)
+        p, q = inputs.pairs("paper_uniform", 7201, 2, og.x, og.nlon, og.a_ring)
+        p32, p64 = f32(p)
+        q32, q64 = f32(q)
+        rc, r = shot.shot_sinkhorn(g, torch.from_numpy(p32).cuda(), torch.from_numpy(q32).cuda(), eps, tau,
+                                   max_iter=1, tol=0.0, check_every=0)
+        assert rc == 0 and np.all(r["status"] == 0)
+        gam = 1.0 if not unb else tau / (tau + eps)
+        u1 = (p64 / heat_apply(og, np.ones_like(p64), eps / 4)) ** gam
+        v1 = (q64 / heat_apply(og, u1, eps / 4)) ** gam
+        if not unb:
+            s = np.sum(u1, axis=(1, 2))[:, None, None]
+            u1, v1 = u1 / s, v1 * s
+        else:
+            a = og.a
+            A = np.sum(a * p64 * u1 ** (-eps / tau), axis=(1, 2))
+            B = np.sum(a * q64 * v1 ** (-eps / tau), axis=(1, 2))
+            c = (0.5 * tau * (np.log(A) - np.log(B)))[:, None, None]
+            u1, v1 = u1 * np.exp(c / eps), v1 * np.exp(-c / eps)
+        tol = TOL_PHI if prec == "fp32" else 1e-4
+        for b in range(2):
+            assert rel_max(r["u"][b].cpu().numpy(), u1[b]) < tol
+            assert rel_max(r["v"][b].cpu().numpy(), v1[b]) < tol
+    finally:
+        shot.shot_grid_free(g)
