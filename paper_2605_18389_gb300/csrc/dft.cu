@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
     for (int k = threadIdx.x; k < nz; k += blockDim.x) buf[q * ld + lmax + 1 + k] = make_float2(0.f, 0.f);
   cp_async_wait_all();
   __syncthreads();
-  epi_prefetch_marginals<FG>(ep, fi, nfg, (size_t)j * nlon, (size_t)(nlat - 1 - jh) * nlon, nlat - 1 - jh != jh, N);
+  epi_prefetch_marginals<FG>(ep, fi, nfg, (size_t)j * nlon, (size_t)(nlat - 1 - jh) * nlon, nlat - 1 - jh != jh, N, f0,
+                             (size_t)nlat * nlon);
   const int nm = lmax + 1;
   for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft_p(
     int jh, f0, nfg;
     item_geom(item, jh, f0, nfg);
     epi_prefetch_marginals<FG>(ep, fi[0], nfg, (size_t)jh * nlon, (size_t)(nlat - 1 - jh) * nlon,
-                               nlat - 1 - jh != jh, N);
+                               nlat - 1 - jh != jh, N, f0, (size_t)nlat * nlon);
   }
   while (item < nitems) {
     const int next = item + gridDim.x;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft_p(
       int jn, fn, nn;
       item_geom(next, jn, fn, nn);
       epi_prefetch_marginals<FG>(ep, fi[slot ^ 1], nn, (size_t)jn * nlon, (size_t)(nlat - 1 - jn) * nlon,
-                                 nlat - 1 - jn != jn, N);
+                                 nlat - 1 - jn != jn, N, fn, (size_t)nlat * nlon);
     }
     const float aj = a_ring[j];
     const bool two = (J != j);

@@ -49,20 +49,24 @@ __device__ __forceinline__ void epi_fields_load(const EpiParams& ep, int f0, int
 }
 
 // After fi is visible to the block: asks L2 for the marginal rows j and J of the CTA's live
-// fields (UPDATE and CHECK modes), one 128-byte line per thread, so that the epilogue's loads
-// hit L2 instead of waiting on DRAM after the inverse transform.
+// fields (UPDATE and CHECK modes) and, for the check, the rows of the u buffer it reads (fields
+// f0 + q at stride fstride in ep.other), one 128-byte line per thread, so that the epilogue's
+// loads hit L2 instead of waiting on DRAM after the inverse transform.
 template <int FG>
 __device__ __forceinline__ void epi_prefetch_marginals(const EpiParams& ep, const EpiField* fi, int nfg, size_t rj,
-                                                       size_t rJ, bool two, int N) {
+                                                       size_t rJ, bool two, int N, int f0 = 0, size_t fstride = 0) {
   if (ep.mode != EPI_UPDATE && ep.mode != EPI_CHECK) return;
+  const int nsrc = (ep.mode == EPI_CHECK && ep.other && fstride) ? 2 : 1;   // marginal (+ u buffer)
   const int lines = (N + 31) / 32 + 1;   // a row of N floats spans at most this many 128-byte lines
-  const int per_field = 2 * lines;
+  const int per_field = 2 * nsrc * lines;
   for (int t = threadIdx.x; t < nfg * per_field; t += blockDim.x) {
     const int q = t / per_field, r = t - q * per_field;
     if (!fi[q].live) continue;
-    const int ring = r / lines, l = r - ring * lines;
+    const int src = r / (2 * lines), rr = r - src * 2 * lines;
+    const int ring = rr / lines, l = rr - ring * lines;
     if (ring == 1 && !two) continue;
-    const float* row = fi[q].marg + (ring ? rJ : rj);
+    const float* base = src ? ep.other + (size_t)(f0 + q) * fstride : fi[q].marg;
+    const float* row = base + (ring ? rJ : rj);
     const uintptr_t a0 = reinterpret_cast<uintptr_t>(row) & ~uintptr_t(127);
     const uintptr_t a = a0 + (uintptr_t)l * 128;
     if (a < reinterpret_cast<uintptr_t>(row + N))
@@ -173,21 +177,35 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
       if (!F.live) continue;
       const float* mg = F.marg;
       const float cuv = ep.ps[f].cuv;
-      for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const float2 zz = z[q * ld + k];
+      for (int k0 = threadIdx.x; k0 < N; k0 += kEpiBatch * NT) {
+        // the marginal and u values of all this thread's longitudes first, then the arithmetic
+        float pv[kEpiBatch][2], uv[kEpiBatch][2];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-          if (r == 1 && !two) break;
-          const float kv = r ? zz.y : zz.x;
-          const size_t o = (r ? rJ : rj) + k;
-          const float pm = __ldg(mg + o);
-          const float d = fmaf(cuv * othf[o], kv, -pm);
-          if (ep.norm_l1) {
-            acc[q][0] += aj * fabsf(d);
-            acc[q][1] += aj * pm;
-          } else {
-            acc[q][0] += d * d;
-            acc[q][1] += pm * pm;
+        for (int b = 0; b < kEpiBatch; ++b) {
+          const int k = k0 + b * NT;
+          pv[b][0] = (k < N) ? __ldg(mg + rj + k) : 0.f;
+          pv[b][1] = (k < N && two) ? __ldg(mg + rJ + k) : 0.f;
+          uv[b][0] = (k < N) ? __ldg(othf + rj + k) : 0.f;
+          uv[b][1] = (k < N && two) ? __ldg(othf + rJ + k) : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < kEpiBatch; ++b) {
+          const int k = k0 + b * NT;
+          if (k >= N) break;
+          const float2 zz = z[q * ld + k];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            if (r == 1 && !two) break;
+            const float kv = r ? zz.y : zz.x;
+            const float pm = pv[b][r];
+            const float d = fmaf(cuv * uv[b][r], kv, -pm);
+            if (ep.norm_l1) {
+              acc[q][0] += aj * fabsf(d);
+              acc[q][1] += aj * pm;
+            } else {
+              acc[q][0] += d * d;
+              acc[q][1] += pm * pm;
+            }
           }
         }
       }
