@@ -284,3 +284,27 @@ def test_full_size_first_iteration_matches_oracle(prec, tau):
             assert rel_max(r["v"][b].cpu().numpy(), v1[b]) < tol
     finally:
         shot.shot_grid_free(g)
+
+
+@pytest.mark.parametrize("tau", [math.inf, 1.0])
+def test_warm_start_continues_the_iteration(grid_cache, tau):
+    """SHOT_FLAG_WARM_START: T1 iterations, then T2 more from the returned (u, v), equal the
+    oracle's T1 + T2 iterations (Alg. 1's next u-step reads v only; the stored pair carries the
+    gauge / translation-invariant state)."""
+    g, og = grid_cache(32)
+    unb = not math.isinf(tau)
+    pt, qt, p, q = _fields(og, "paper_uniform", 515, 2, masses=unb)
+    rc, r1 = shot.shot_sinkhorn(g, pt, qt, 0.1, tau, max_iter=20, tol=0.0, check_every=10)
+    assert rc == 0
+    rc, r2 = shot.shot_sinkhorn(g, pt, qt, 0.1, tau, max_iter=25, tol=0.0, check_every=10,
+                                flags=shot.SHOT_FLAG_WARM_START, u=r1["u"], v=r1["v"])
+    assert rc == 0 and np.all(r2["iters"] == 25)
+    ref = sk.sinkhorn(og, p, q, 0.1, tau, T=45, delta=0.0, C=10)
+    u, v = r2["u"].cpu().numpy(), r2["v"].cpu().numpy()
+    if unb:
+        for b in range(2):
+            assert rel_max(0.1 * np.log(u[b]), ref["phi"][b]) < TOL_PHI
+            assert rel_max(0.1 * np.log(v[b]), ref["psi"][b]) < TOL_PHI
+    else:
+        assert potentials_err(og, 0.1, u, v, ref["phi"], ref["psi"]) < TOL_PHI
+    np.testing.assert_allclose(r2["ot"], ref["ot"], rtol=TOL_PHI)
