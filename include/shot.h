@@ -68,6 +68,10 @@ extern "C" {
 #define SHOT_FLAG_NORM_L1     0x1  /* check sum_i a_i|u_i(Kv)_i - p_i| / sum_i a_i p_i instead of the relative L2 */
 #define SHOT_FLAG_WARM_START  0x2  /* u and v hold the initial scalings instead of 1 */
 #define SHOT_FLAG_POTENTIALS  0x4  /* return the potentials phi = eps log u, psi = eps log v in u, v */
+#define SHOT_FLAG_SYMMETRIC_SELF 0x8  /* shot_divergence: self terms OT(p,p), OT(q,q) by the symmetric
+                                        averaged update u <- sqrt(u (p/Ku)^gamma) (Feydy et al.,
+                                        2019), one heat convolution per iteration, instead of
+                                        Alg. 1 with q := p; same fixed point */
 
 typedef struct shot_grid_s* shot_grid;
 

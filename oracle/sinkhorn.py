@@ -186,3 +186,80 @@ def gauge_fixed(grid, phi, psi):
     """phi - <a,phi>/4pi and psi + <a,phi>/4pi (removes the (phi+c, psi-c) freedom)."""
     c = np.sum(grid.a * phi, axis=(-2, -1), keepdims=True) / (4.0 * np.pi)
     return phi - c, psi + c
+
+
+def sinkhorn_symmetric(grid, p, eps, tau=np.inf, T=500, delta=0.0, C=10, norm="l2", kernel="sht"):
+    """The self term OT(p, p) through the symmetric form of Alg. 1's fixed point.  With q = p
+    the scalings of the converged Alg. 1 satisfy u = v = (p / K u)^gamma (gamma = 1 balanced,
+    tau/(tau+eps) otherwise; the translation-invariant constant vanishes); the averaged update
+    u <- sqrt(u (p / K u)^gamma) of Feydy et al. (2019) reaches that point with one heat
+    convolution per iteration.  u = 1 initially; the check of App. C.3 every C iterations on
+    || u (.) K u - p ||; breakdowns as in `sinkhorn`.  Returns the Alg. 1 objective with
+    phi = psi = eps log u (so OT = 2 sum a phi p balanced, 2 sum a tau (1 - e^{-phi/tau}) p
+    unbalanced) and the plan mass m(pi) = sum a u (K u)."""
+    p = np.asarray(p, dtype=np.float64)
+    if p.ndim == 2:
+        p = p[None]
+    B = p.shape[0]
+    K = _kernel(grid, eps, kernel)
+    a = grid.a
+    balanced = not np.isfinite(tau)
+    gamma = 1.0 if balanced else tau / (tau + eps)
+    u = np.ones_like(p)
+    active = np.ones(B, dtype=bool)
+    status = np.full(B, OK)
+    iters = np.full(B, T)
+    for k in range(1, T + 1):
+        idx = np.nonzero(active)[0]
+        if idx.size == 0:
+            break
+        ku = K(u[idx])
+        with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+            un = np.sqrt(u[idx] * (p[idx] / ku) ** gamma)
+        bad = _bad(ku, un)
+        for b, i in enumerate(idx):
+            if bad[b] == OK:
+                u[i] = un[b]
+            else:
+                status[i], iters[i], active[i] = bad[b], k, False
+        if C > 0 and k % C == 0:
+            idx2 = np.nonzero(active)[0]
+            if idx2.size:
+                e = marginal_error(grid, u[idx2], K(u[idx2]), p[idx2], norm)
+                for b, i in enumerate(idx2):
+                    if e[b] < delta:
+                        active[i], iters[i] = False, k
+    if delta > 0:
+        status[(status == OK) & active] = NOT_CONVERGED
+    ku = K(u)
+    err = marginal_error(grid, u, ku, p, norm)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        mass = np.sum(a * u * ku, axis=(1, 2))
+        phi = eps * np.log(u)
+        t = phi * p if balanced else tau * (1.0 - np.exp(-phi / tau)) * p
+        ot = 2.0 * np.sum(a * np.where(p > 0, t, 0.0), axis=(1, 2))
+    broke = status < 0
+    for arr in (err, mass, ot):
+        arr[broke] = np.nan
+    return dict(u=u, phi=phi, iters=iters, status=status, err=err, mass_pi=mass, ot=ot,
+                ot_dual=ot - eps * mass, eps=eps, tau=tau)
+
+
+def divergence_symmetric_self(grid, p, q, eps, tau=np.inf, T=500, delta=0.0, C=10, norm="l2", kernel="sht"):
+    """eq. (sinkhorn-divergence) with OT(p, q) from Alg. 1 and the self terms OT(p, p), OT(q, q)
+    from `sinkhorn_symmetric` (same T, delta, C); S and S_dual as in `divergence`."""
+    p = np.asarray(p, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    if p.ndim == 2:
+        p, q = p[None], q[None]
+    B = p.shape[0]
+    r = sinkhorn(grid, p, q, eps, tau, T, delta, C, norm, kernel)
+    s = sinkhorn_symmetric(grid, np.concatenate([p, q]), eps, tau, T, delta, C, norm, kernel)
+    a = grid.a
+    mp = np.sum(a * p, axis=(1, 2))
+    mq = np.sum(a * q, axis=(1, 2))
+    S = r["ot"] - 0.5 * (s["ot"][:B] + s["ot"][B:]) + 0.5 * eps * (mp - mq) ** 2
+    Sd = r["ot_dual"] - 0.5 * (s["ot_dual"][:B] + s["ot_dual"][B:])
+    st = np.stack([r["status"], s["status"][:B], s["status"][B:]])
+    status = np.where((st < 0).any(0), st.min(0), st.max(0))
+    return dict(S=S, S_dual=Sd, status=status, pq=r, self=s, m_p=mp, m_q=mq)

@@ -82,7 +82,7 @@ int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int l
 
 namespace {
 
-enum RedMode { RED_U = 0, RED_V = 1, RED_CHECK = 2, RED_FINAL = 3 };
+enum RedMode { RED_U = 0, RED_V = 1, RED_CHECK = 2, RED_FINAL = 3, RED_S = 4 };
 
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
@@ -132,7 +132,13 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int
         for (int w = 0; w < kRedThreads / 32; ++w) t += red[w][i];
         s[i] = t;
       }
-      if (mode == RED_U || mode == RED_V) {
+      if (mode == RED_S) {   // symmetric self-term step: breakdown flags only (no gauge)
+        if (lane == 0 && (s[2] > 0.0 || s[3] > 0.0)) {
+          P->status = s[2] > 0.0 ? SHOT_ERR_NONPOSITIVE : SHOT_ERR_NONFINITE;
+          P->active = 0;
+          P->iters = kdone + 1;
+        }
+      } else if (mode == RED_U || mode == RED_V) {
         const int bal = P->balanced;
         int st = SHOT_OK;
         if (s[2] > 0.0) st = SHOT_ERR_NONPOSITIVE;
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int
   if (threadIdx.x == 0) {
     int t = 0;
     for (int w = 0; w < kRedThreads / 32; ++w) t += wna[w];
-    if (mode == RED_V) dev_int[0] = kdone + 1;
+    if (mode == RED_V || mode == RED_S) dev_int[0] = kdone + 1;
     dev_int[1] = t;
     dev_int[12] = 0;
   }
@@ -346,6 +352,7 @@ struct Solve {
   int nprob = 0;
   double eps = 0, tol = 0;
   int C = 0, norm_l1 = 0, potentials = 0;
+  int symmetric = 0;   // self terms by the symmetric update (u and v are one buffer)
   float *u = nullptr, *v = nullptr;
   cudaStream_t st = nullptr;
   int xs = 0;   // spectra kept as bf16 hi/lo (tensor-core operand format)
@@ -381,6 +388,7 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
   s.C = C;
   s.norm_l1 = (flags & SHOT_FLAG_NORM_L1) ? 1 : 0;
   s.potentials = (flags & SHOT_FLAG_POTENTIALS) ? 1 : 0;
+  s.symmetric = (flags & kFlagSymmetricSolve) ? 1 : 0;
   s.u = u;
   s.v = v;
   s.st = w.stream;
@@ -460,7 +468,18 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     pending = false;
     return SHOT_OK;
   };
-  for (int i = 0; i < nit; ++i) {
+  for (int i = 0; s.symmetric && i < nit; ++i) {
+    // self term: u = sqrt(u (p / K u)^gamma) in place, and X := F(u)
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
+    ep.mode = EPI_SYM;
+    ep.out = s.u;
+    ep.marg = margP;
+    ep.which = 0;
+    ep.xout = w.XY;
+    if ((rc = join()) || (rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
+    if ((rc = fork_reduce(RED_S))) return rc;
+  }
+  for (int i = 0; !s.symmetric && i < nit; ++i) {
     // u-step: u = (ru p / K v)^gamma, and X := F(u)
     if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
     ep.mode = EPI_UPDATE;
@@ -1017,8 +1036,26 @@ int shot_divergence(shot_grid gh, const float* p, const float* q, int batch, dou
   SHOT_CUDA(cudaStreamSynchronize(st));
 
   SolveOut so;
-  rc = run_sinkhorn(*g, P, Q, eps, tau, max_iter, tol, check_every, flags, u3, v3, st, so);
-  if (rc) return rc;
+  if (flags & SHOT_FLAG_SYMMETRIC_SELF) {
+    // (p_b, q_b) by Alg. 1, then the 2B self terms by the symmetric update in one solve
+    const int f1 = flags & ~SHOT_FLAG_SYMMETRIC_SELF;
+    std::vector<const float*> P1(P.begin(), P.begin() + batch), Q1(Q.begin(), Q.begin() + batch);
+    std::vector<const float*> P2(P.begin() + batch, P.end());
+    SolveOut s1, s2;
+    if ((rc = run_sinkhorn(*g, P1, Q1, eps, tau, max_iter, tol, check_every, f1, u3, v3, st, s1))) return rc;
+    float* us = u3 + (size_t)batch * n;
+    if ((rc = run_sinkhorn(*g, P2, P2, eps, tau, max_iter, tol, check_every, f1 | kFlagSymmetricSolve, us, us, st,
+                           s2)))
+      return rc;
+    // v = u for the self terms
+    SHOT_CUDA(cudaMemcpyAsync(v3 + (size_t)batch * n, us, (size_t)2 * batch * n * sizeof(float),
+                              cudaMemcpyDeviceToDevice, st));
+    so.ps = s1.ps;
+    so.ps.insert(so.ps.end(), s2.ps.begin(), s2.ps.end());
+  } else {
+    rc = run_sinkhorn(*g, P, Q, eps, tau, max_iter, tol, check_every, flags, u3, v3, st, so);
+    if (rc) return rc;
+  }
   for (int b = 0; b < batch; ++b) {
     const ProbState &a = so.ps[b], &pp = so.ps[batch + b], &qq = so.ps[2 * batch + b];
     const double dm = masses[b] - masses[batch + b];

@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
   ring_pair_epilogue<FG, kThreads>(z, other, ld, N, nfg, f0, (size_t)nlat * nlon, (size_t)j * nlon,
                                    (size_t)J * nlon, two, aj, nh, jh, ep, red, fi);
   if (ep.mode == EPI_PLAIN) return;
-  if (ep.mode == EPI_UPDATE && ep.xout) {
+  if ((ep.mode == EPI_UPDATE || ep.mode == EPI_SYM) && ep.xout) {
     // the new scaling of this ring pair is in `other`: transform it for the next half-step
     __syncthreads();
     const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw, pl, nfg);
@@ -407,7 +407,8 @@ int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams&
   }
   // the solver's update half-steps and marginal checks: persistent kernel with the next item's
   // inputs prefetched
-  if (((ep.mode == EPI_UPDATE && ep.xout) || ep.mode == EPI_CHECK) && !g.idft_nonpersistent && nf >= 2 &&
+  if ((((ep.mode == EPI_UPDATE || ep.mode == EPI_SYM) && ep.xout) || ep.mode == EPI_CHECK) && !g.idft_nonpersistent &&
+      nf >= 2 &&
       idft_p_layout(2, g.nlon, g.lmax).total <= 74 * 1024) {
     if (plan_is<Plan1440>(g.plan)) return launch_idft_p_t<2, Plan1440>(g, Y, ldc, nf, ep, st);
     if (plan_is<Plan1024>(g.plan)) return launch_idft_p_t<2, Plan1024>(g, Y, ldc, nf, ep, st);

@@ -14,6 +14,8 @@
 //   EPI_CHECK   |u_true (K v_true) - p| sums for the marginal error (L2 or L1, App. C.3)
 //   EPI_FINAL   u_true, v_true (or the potentials), the marginal error, m(pi) and the dual
 //               objective
+//   EPI_SYM     self term (q = p): u = sqrt(u_old (p / Ku)^gamma) in place (ep.out holds u_old),
+//               breakdown counts; with ep.xout the new u is also written into `other`
 // Field f occupies out[f * fstride ...]; rings j and J start at rj and rJ within a field.
 #pragma once
 #include "shot_internal.cuh"
@@ -55,8 +57,9 @@ __device__ __forceinline__ void epi_fields_load(const EpiParams& ep, int f0, int
 template <int FG>
 __device__ __forceinline__ void epi_prefetch_marginals(const EpiParams& ep, const EpiField* fi, int nfg, size_t rj,
                                                        size_t rJ, bool two, int N, int f0 = 0, size_t fstride = 0) {
-  if (ep.mode != EPI_UPDATE && ep.mode != EPI_CHECK) return;
-  const int nsrc = (ep.mode == EPI_CHECK && ep.other && fstride) ? 2 : 1;   // marginal (+ u buffer)
+  if (ep.mode != EPI_UPDATE && ep.mode != EPI_CHECK && ep.mode != EPI_SYM) return;
+  const float* second = ep.mode == EPI_CHECK ? ep.other : (ep.mode == EPI_SYM ? ep.out : nullptr);
+  const int nsrc = (second && fstride) ? 2 : 1;   // marginal (+ the u buffer the epilogue reads)
   const int lines = (N + 31) / 32 + 1;   // a row of N floats spans at most this many 128-byte lines
   const int per_field = 2 * nsrc * lines;
   for (int t = threadIdx.x; t < nfg * per_field; t += blockDim.x) {
@@ -65,7 +68,7 @@ __device__ __forceinline__ void epi_prefetch_marginals(const EpiParams& ep, cons
     const int src = r / (2 * lines), rr = r - src * 2 * lines;
     const int ring = rr / lines, l = rr - ring * lines;
     if (ring == 1 && !two) continue;
-    const float* base = src ? ep.other + (size_t)(f0 + q) * fstride : fi[q].marg;
+    const float* base = src ? second + (size_t)(f0 + q) * fstride : fi[q].marg;
     const float* row = base + (ring ? rJ : rj);
     const uintptr_t a0 = reinterpret_cast<uintptr_t>(row) & ~uintptr_t(127);
     const uintptr_t a = a0 + (uintptr_t)l * 128;
@@ -168,6 +171,51 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
               else acc[q][3] += 1.f;   // NaN or infinite K v, or u overflowed
             }
             if (!ep.skip_store) outf[(r ? rJ : rj) + k] = u;
+            u2[r] = u;
+          }
+          if (ep.xout) other[q * ld + k] = make_float2(u2[0], u2[1]);
+        }
+      }
+    } else if (ep.mode == EPI_SYM) {
+      if (!F.live) {
+        if (ep.xout) {   // frozen problem: transform the stored scaling
+          for (int k = threadIdx.x; k < N; k += blockDim.x)
+            other[q * ld + k] = make_float2(outf[rj + k], two ? outf[rJ + k] : 0.f);
+        }
+        continue;
+      }
+      const float* mg = F.marg;
+      const int bal = F.balanced;
+      const float gam = F.gamma;
+      for (int k0 = threadIdx.x; k0 < N; k0 += kEpiBatch * NT) {
+        // the marginal and old-scaling values of this thread's longitudes first, then the arithmetic
+        float pv[kEpiBatch][2], uo[kEpiBatch][2];
+#pragma unroll
+        for (int b = 0; b < kEpiBatch; ++b) {
+          const int k = k0 + b * NT;
+          pv[b][0] = (k < N) ? __ldg(mg + rj + k) : 0.f;
+          pv[b][1] = (k < N && two) ? __ldg(mg + rJ + k) : 0.f;
+          uo[b][0] = (k < N) ? outf[rj + k] : 0.f;
+          uo[b][1] = (k < N && two) ? outf[rJ + k] : 0.f;
+        }
+#pragma unroll
+        for (int b = 0; b < kEpiBatch; ++b) {
+          const int k = k0 + b * NT;
+          if (k >= N) break;
+          const float2 zz = z[q * ld + k];
+          float u2[2];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            if (r == 1 && !two) { u2[1] = 0.f; break; }
+            const float kv = r ? zz.y : zz.x;
+            const float ratio = __fdividef(pv[b][r], kv);
+            const float t = bal ? ratio : exp2f(gam * __log2f(ratio));
+            const float u = sqrtf(uo[b][r] * t);
+            if (!(kv > 0.f && kv < INFINITY && fabsf(u) < INFINITY)) {
+              if (kv <= 0.f) acc[q][2] += 1.f;
+              else acc[q][3] += 1.f;
+            }
+            outf[(r ? rJ : rj) + k] = u;
             u2[r] = u;
           }
           if (ep.xout) other[q * ld + k] = make_float2(u2[0], u2[1]);

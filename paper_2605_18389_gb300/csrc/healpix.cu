@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kHpThreads) k_hp_idft(const float* __restrict_
   ring_pair_epilogue<FG, kHpThreads>(z, other, ld, n, nfg, f0, npix, (size_t)roff[j], (size_t)roff[J], two, area,
                                      nh, jh, ep, red, fi);
   if (ep.mode == EPI_PLAIN) return;
-  if (ep.mode == EPI_UPDATE && ep.xout) {   // transform the new scaling
+  if ((ep.mode == EPI_UPDATE || ep.mode == EPI_SYM) && ep.xout) {   // transform the new scaling
     __syncthreads();
     const float2* D = ring_transform<false>(other, z, tw, n, nfg, pi, plans, tw_all, tw_base);
     hp_unpack_store<FG>(D, ph, n, nfg, f0, lmax, nh, jh, area, ep.xout, ldc);

@@ -223,7 +223,10 @@ struct ProbState {
 };
 
 // Epilogue modes of the inverse DFT kernel
-enum EpiMode { EPI_PLAIN = 0, EPI_UPDATE = 1, EPI_CHECK = 2, EPI_FINAL = 3 };
+enum EpiMode { EPI_PLAIN = 0, EPI_UPDATE = 1, EPI_CHECK = 2, EPI_FINAL = 3, EPI_SYM = 4 };
+// solve_prepare flag (internal, above the public SHOT_FLAG_* bits): the problems are self terms
+// (q = p) solved by the symmetric averaged update u <- sqrt(u (p / K u)^gamma)
+constexpr int kFlagSymmetricSolve = 1 << 30;
 constexpr int NPART = 4;   // partial sums per (field, ring pair)
 
 struct EpiParams {

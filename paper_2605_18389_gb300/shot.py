@@ -35,6 +35,7 @@ SHOT_QUAD_HEALPIX = 2
 SHOT_FLAG_NORM_L1 = 0x1
 SHOT_FLAG_WARM_START = 0x2
 SHOT_FLAG_POTENTIALS = 0x4
+SHOT_FLAG_SYMMETRIC_SELF = 0x8
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libshot.so")
 

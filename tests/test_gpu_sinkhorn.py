@@ -7,7 +7,7 @@ import pytest
 from oracle.grid import Grid as OGrid
 from oracle import sinkhorn as sk
 from paper_2605_18389_gb300 import inputs
-from tests.gpu_util import rel_max, f32, s_err, potentials_err, UNIT
+from tests.gpu_util import rel_max, f32, s_err, s_err_prec, potentials_err, UNIT
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -308,3 +308,41 @@ def test_warm_start_continues_the_iteration(grid_cache, tau):
     else:
         assert potentials_err(og, 0.1, u, v, ref["phi"], ref["psi"]) < TOL_PHI
     np.testing.assert_allclose(r2["ot"], ref["ot"], rtol=TOL_PHI)
+
+
+@pytest.mark.parametrize("prec,tau", [("fp32", math.inf), ("fp32", 1.0), ("bf16x3", math.inf)])
+def test_symmetric_self_terms_match_oracle(prec, tau):
+    """SHOT_FLAG_SYMMETRIC_SELF: the self terms by the symmetric averaged update, T fixed
+    iterations on both sides, against the oracle's same iteration; S and the self terms' OT."""
+    nlat, eps, T = 32, 0.1, 40
+    og = OGrid(nlat)
+    g = shot.shot_grid_init(nlat, None, -1, shot.SHOT_FP32 if prec == "fp32" else shot.SHOT_BF16X3)
+    tol = TOL_S if prec == "fp32" else 1e-4
+    try:
+        unb = not math.isinf(tau)
+        pt, qt, p, q = _fields(og, "paper_uniform", 8080, 2, masses=unb)
+        rc, r = shot.shot_divergence(g, pt, qt, eps, tau, max_iter=T, tol=0.0, check_every=10,
+                                     flags=shot.SHOT_FLAG_SYMMETRIC_SELF)
+        ref = sk.divergence_symmetric_self(og, p, q, eps, tau, T=T, delta=0.0, C=10)
+        assert rc == 0 and np.all(r["status"] == 0) and np.all(ref["status"] == 0)
+        np.testing.assert_allclose(r["ot3"][2:], ref["self"]["ot"], rtol=tol)
+        np.testing.assert_allclose(r["ot3"][:2], ref["pq"]["ot"], rtol=tol)
+        # S cancels: its error floor is the precision's unit roundoff times OT(p, q)
+        assert np.all(s_err_prec(r["S"], ref["S"], ref["pq"]["ot"], tol, prec) <= 1.0), (r["S"], ref["S"])
+    finally:
+        shot.shot_grid_free(g)
+
+
+def test_symmetric_self_terms_reach_the_same_divergence(grid_cache):
+    """Converged, the symmetric self terms give Alg. 1's divergence (same fixed point) and stop
+    earlier."""
+    g, og = grid_cache(32)
+    pt, qt, p, q = _fields(og, "paper_uniform", 8181, 2)
+    rc, a = shot.shot_divergence(g, pt, qt, 0.1, max_iter=2000, tol=1e-6, check_every=10)
+    rc2, b = shot.shot_divergence(g, pt, qt, 0.1, max_iter=2000, tol=1e-6, check_every=10,
+                                  flags=shot.SHOT_FLAG_SYMMETRIC_SELF)
+    assert rc == 0 and rc2 == 0
+    ref = sk.divergence(og, p, q, 0.1, T=2000, delta=1e-9, C=10)
+    assert np.all(s_err(b["S"], ref["S"], ref["runs"]["ot"][:2], 1e-4) <= 1.0), (b["S"], ref["S"])
+    assert np.all(s_err(a["S"], ref["S"], ref["runs"]["ot"][:2], 1e-4) <= 1.0)
+    assert np.all(b["iters3"][2:] <= a["iters3"][2:])
