@@ -57,7 +57,7 @@ __device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity) {
     if (clock64() - t0 > kWaitCycles) return;
 }
 
-// Warp-uniform bounded wait: lane 0 waits, the verdict is broadcast to the warp (the
+// Warp-uniform bounded wait: lane 0 waits, the outcome is broadcast to the warp (the
 // epilogue's tcgen05.ld is .sync.aligned and must be reached by all lanes or none).
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort);
 
