@@ -90,43 +90,103 @@ def test_wrong_gauge_direction_caught(monkeypatch):
     assert abs(r["u"].sum() - 1.0) > 1e-3
 
 
-def test_cc_endpoint_halving_dropped_caught():
-    # Clenshaw-Curtis without halving the end terms of the cosine sums: the pins'
-    # exactness check (int x^2 = 2/3 on 9 nodes) must fail
-    from oracle.grid import clenshaw_curtis
-    x, _ = clenshaw_curtis(9)
-    N = 8
-    j = np.arange(N + 1)
-    w = np.zeros(N + 1)
-    for k in range(0, N + 1, 2):
-        w += (2.0 / N) * np.cos(np.pi * k * j / N) * (2.0 / (1.0 - k * k)) * (0.5 if k in (0, N) else 1.0)
-    assert abs(np.sum(w * x ** 2) - 2.0 / 3.0) > 1e-3
+def _fails(pin, *args):
+    """True when the pin test function fails (raises AssertionError) on the mutated oracle."""
+    try:
+        pin(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def test_cc_endpoint_halving_dropped_caught(monkeypatch):
+    # Clenshaw-Curtis weights without halving the end terms of the cosine sums, planted in
+    # the oracle; the exactness pin of tests/test_oracle_cc.py must fail
+    from oracle import grid as ogrid
+    from tests import test_oracle_cc as pins
+    good = ogrid.clenshaw_curtis
+
+    def bad(nlat):
+        x, _ = good(nlat)
+        N = nlat - 1
+        j = np.arange(N + 1)
+        w = np.zeros(N + 1)
+        for k in range(0, N + 1, 2):
+            w += (2.0 / N) * np.cos(np.pi * k * j / N) * (2.0 / (1.0 - k * k)) * (0.5 if k in (0, N) else 1.0)
+        return x, w
+    monkeypatch.setattr(ogrid, "clenshaw_curtis", bad)
+    monkeypatch.setattr(pins, "clenshaw_curtis", bad)
+    assert _fails(pins.test_cc_exactness_symmetry_positivity, 7)
+    assert _fails(pins.test_cc_textbook_closed_forms)
 
 
 def test_normaliser_without_jacobian_caught(monkeypatch):
-    # C(eps) integrated without the sin(theta) surface element: the small-eps series pin
-    # (C = pi eps - pi eps^2 / 6 + ...) must fail
+    # C(eps) integrated without the sin(theta) surface element, planted in the oracle; the
+    # small-eps series pin and the large-eps limit pin must fail
     from scipy import integrate
-    eps = 1e-2
-    bad = 2 * np.pi * integrate.quad(lambda th: np.exp(-th * th / eps), 0.0, np.pi)[0]
-    series = 2 * np.pi * (eps / 2 - eps ** 2 / 12 + eps ** 3 / 120)
-    assert abs(bad - series) > 1e-3
-
-
-def test_gibbs_without_area_weights_caught():
-    # matrix convolution that forgets a_j: its row sums no longer approach C(eps)
     from oracle import convolution as cv
-    g = Grid(24, quadrature="cc")
-    X = g.xyz.reshape(-1, 3)
-    d = cv.geodesic(X[:1, None, :], X[None, :, :])[0]
-    bad_rowsum = np.exp(-d * d / 0.5).sum()
-    assert abs(bad_rowsum / cv.gibbs_normaliser(0.5) - 1.0) > 1e-2
+    from tests import test_oracle_convolution as pins
+
+    def bad(eps):
+        return 2 * np.pi * integrate.quad(lambda th: np.exp(-th * th / eps), 0.0, np.pi, limit=200)[0]
+    monkeypatch.setattr(cv, "gibbs_normaliser", bad)
+    assert _fails(pins.test_normaliser_small_eps_series, 1e-2)
+    assert _fails(pins.test_normaliser_large_eps_limit)
 
 
-def test_healpix_longitude_offset_dropped_caught():
-    # rings without their half-pixel longitude offset: the base-resolution pin fails
-    from oracle.healpix import HealpixGrid
-    g = HealpixGrid(1)
-    bad = 2 * np.pi * (np.arange(g.npix) - g.off[g.ring_of]) / g.npx[g.ring_of]
-    ph = np.sort(bad.reshape(3, 4) % (2 * np.pi), axis=1)
-    assert np.abs(ph[0] - (np.pi / 4 + np.pi / 2 * np.arange(4))).max() > 0.5
+def test_gibbs_without_area_weights_caught(monkeypatch):
+    # matrix convolution that forgets a_j, planted in the oracle; the row-sum pin must fail
+    from oracle import convolution as cv
+    from tests import test_oracle_convolution as pins
+
+    def bad(grid, f, eps, rows=1024):
+        X = grid.xyz.reshape(-1, 3)
+        F = np.asarray(f, dtype=np.float64).reshape(-1, X.shape[0])
+        d = cv.geodesic(X[:, None, :], X[None, :, :])
+        return (F @ np.exp(-d * d / eps).T).reshape(f.shape)
+    monkeypatch.setattr(cv, "gibbs_apply", bad)
+    assert _fails(pins.test_row_sums_match_normaliser_on_fine_grid, 0.5)
+
+
+def test_healpix_longitude_offset_dropped_caught(monkeypatch):
+    # rings without their half-pixel longitude offset, planted in the oracle; the
+    # base-resolution geometry pin must fail
+    from oracle import healpix as ohp
+    from tests import test_oracle_healpix as pins
+    good = ohp.ring_geometry
+
+    def bad(nside):
+        z, npx, phi0 = good(nside)
+        return z, npx, np.zeros_like(phi0)
+    monkeypatch.setattr(ohp, "ring_geometry", bad)
+    monkeypatch.setattr(pins, "ring_geometry", bad)
+    assert _fails(pins.test_base_resolution_geometry)
+
+
+def test_unweighted_l1_marginal_error_caught(monkeypatch):
+    # the L1 check without the area weights, planted in the oracle; the hand-computed pin
+    # of tests/test_oracle_sinkhorn.py must fail
+    from tests import test_oracle_sinkhorn as pins
+
+    def bad(grid, u, kv, p, norm="l2"):
+        ax = tuple(range(1, p.ndim))
+        r = u * kv - p
+        if norm == "l2":
+            return np.sqrt(np.sum(r * r, axis=ax)) / np.sqrt(np.sum(p * p, axis=ax))
+        return np.sum(np.abs(r), axis=ax) / np.sum(p, axis=ax)
+    monkeypatch.setattr(sk, "marginal_error", bad)
+    assert _fails(pins.test_l1_marginal_error_hand_computed)
+    assert _fails(pins.test_l1_marginal_error_on_a_grid_equals_the_weighted_sum)
+
+
+def test_mutation_helpers_pass_unmutated():
+    # the same pins pass on the oracle as committed (so a failure above is the mutation's)
+    from tests import test_oracle_cc, test_oracle_convolution, test_oracle_healpix, test_oracle_sinkhorn
+    assert not _fails(test_oracle_cc.test_cc_exactness_symmetry_positivity, 7)
+    assert not _fails(test_oracle_cc.test_cc_textbook_closed_forms)
+    assert not _fails(test_oracle_convolution.test_normaliser_small_eps_series, 1e-2)
+    assert not _fails(test_oracle_convolution.test_normaliser_large_eps_limit)
+    assert not _fails(test_oracle_convolution.test_row_sums_match_normaliser_on_fine_grid, 0.5)
+    assert not _fails(test_oracle_healpix.test_base_resolution_geometry)
+    assert not _fails(test_oracle_sinkhorn.test_l1_marginal_error_hand_computed)
+    assert not _fails(test_oracle_sinkhorn.test_l1_marginal_error_on_a_grid_equals_the_weighted_sum)

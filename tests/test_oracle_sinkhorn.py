@@ -246,3 +246,44 @@ def test_symmetric_self_term_reaches_alg1_fixed_point(tau):
         assert np.max(np.abs(sym["phi"] - ref["psi"])) < 1e-9
     if np.isinf(tau):   # fewer iterations than Alg. 1 for the same tolerance
         assert sym["iters"][0] < ref["iters"][0]
+
+
+class _TwoNodes:
+    """A two-node 'grid' with unequal area weights: enough for the marginal-error norms."""
+    a = np.array([[1.0, 3.0]])
+
+
+def test_l1_marginal_error_hand_computed():
+    # App. C.3 / reading R4: L1 = sum_i a_i |u_i (Kv)_i - p_i| / sum_i a_i p_i.
+    # u (.) Kv - p = (1, -1), a = (1, 3), p = (1, 2): L1 = (1 + 3) / (1 + 6) = 4/7.
+    # Unweighted it would be 2/3, with the weights on the numerator only 4/3: both fail.
+    u = np.array([[[2.0, 1.0]]])
+    kv = np.array([[[1.0, 1.0]]])
+    p = np.array([[[1.0, 2.0]]])
+    e = sk.marginal_error(_TwoNodes, u, kv, p, norm="l1")
+    assert e.shape == (1,)
+    assert abs(e[0] - 4.0 / 7.0) < 1e-15
+
+
+def test_l2_marginal_error_hand_computed():
+    # App. C.3: e = ||u (.) Kv - p||_2 / ||p||_2, unweighted: sqrt(1 + 1) / sqrt(1 + 4).
+    u = np.array([[[2.0, 1.0]]])
+    kv = np.array([[[1.0, 1.0]]])
+    p = np.array([[[1.0, 2.0]]])
+    e = sk.marginal_error(_TwoNodes, u, kv, p)
+    assert abs(e[0] - np.sqrt(2.0 / 5.0)) < 1e-15
+
+
+def test_l1_marginal_error_on_a_grid_equals_the_weighted_sum():
+    # the same definition summed node by node in plain Python on a real grid, batch of 2
+    g = Grid(6)
+    rng = np.random.default_rng(3)
+    u, kv, p = rng.uniform(0.5, 2.0, size=(3, 2, g.nlat, g.nlon))
+    e = sk.marginal_error(g, u, kv, p, norm="l1")
+    for b in range(2):
+        num = den = 0.0
+        for j in range(g.nlat):
+            for k in range(g.nlon):
+                num += g.a_ring[j] * abs(u[b, j, k] * kv[b, j, k] - p[b, j, k])
+                den += g.a_ring[j] * p[b, j, k]
+        assert abs(e[b] - num / den) < 1e-14
