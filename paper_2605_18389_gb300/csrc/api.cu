@@ -39,25 +39,11 @@ int launch_legendre_simt(const Grid& g, int nf, const float* X, float* C, float*
 int launch_analysis_simt(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h, cudaStream_t st);
 int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st);
 
-int spectra_split(const Grid& g, int nf, int ldc) {
-  return (g.split_spectra && g.precision == SHOT_BF16X3 && g.mode == SHOT_TABLE && tc_nmma(nf) <= 64 &&
-          ldc % 8 == 0 && g.quad != SHOT_QUAD_HEALPIX) ? 1 : 0;
-}
-
-int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
-                    int xsplit) {
+int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st) {
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st);
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st);
   if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st);
-  if (g.merged_heat && !xsplit) {
-    const int rc = launch_heat_merged(g, nf, X, Y, ldc, st);
-    if (rc != SHOT_ERR_UNSUPPORTED) return rc;
-  }
-  if (g.fused_heat) {
-    const int rc = launch_heat_tc(g, nf, X, Y, ldc, st, xsplit);
-    if (rc != SHOT_ERR_UNSUPPORTED) return rc;
-  }
-  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st, xsplit);
+  return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st) {
@@ -151,6 +137,13 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int
         const double gam = (double)P->gamma;
         const int e = (mode == RED_U) ? P->eu : P->ev;
         const double lw = -gam * ((mode == RED_U ? P->lb : P->la) + e * kLn2);
+        // v-step: the plan mass m(pi) = sum a u (K v) = sum a v (K u) (K is self-adjoint in the
+        // area inner product), from the new v buffer and the K u it divided by:
+        // sum a v_true (K u_true) = e^{lw + la} sum a v_buf (K u_buf), kept by the gauge and the
+        // translation-invariant step (they keep the product u v).  Unbalanced, the
+        // translation-invariant sum is s[0] = sum a v_buf (K u_buf) / r.  Balanced,
+        // v_true (K u_true) = q node by node and the final pass sums a q (mass_v = 0 marks it).
+        const double mv = (mode == RED_V && !bal) ? exp(lw + P->la) * ldexp(s[0], e) : 0.0;
         // log of the step's sum over true values: sum w_true (balanced gauge) or
         // sum a m w_true^{-eps/tau} (translation-invariant step)
         const double ls = bal ? lw + lsum : -(eps / P->tau) * lw + lsum;
@@ -205,6 +198,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int
             P->cuv = cuv;
             P->cu = (float)eu;
             P->cv = (float)ev;
+            P->mass_v = mv;
           }
         }
       } else if (lane == 0) {
@@ -217,9 +211,13 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce(int mode, int nprob, int
           }
         } else {
           P->err = norm_l1 ? s[0] / s[1] : sqrt(s[0] / s[1]);
-          P->mass = s[2];
+          // m(pi) from the last v-update when there was one (the same quantity as
+          // sum a u (K v) of this pass, without the FP32 error of the final K v); balanced, the
+          // pass summed a q (see the epilogue)
+          const double m = (P->balanced || isnan(P->mass_v)) ? s[2] : P->mass_v;
+          P->mass = m;
           P->ot = s[3];
-          P->ot_dual = s[3] - eps * s[2];
+          P->ot_dual = s[3] - eps * m;
         }
       }
     }
@@ -258,7 +256,7 @@ __global__ void k_init_probs(int nprob, ProbState* ps, int* dev_int, const doubl
     P.beta = 1.0;
     P.ru = P.rv = P.cuv = P.cu = P.cv = 1.f;
     P.err = nan("");
-    P.ot = P.ot_dual = P.mass = nan("");
+    P.ot = P.ot_dual = P.mass = P.mass_v = nan("");
     const double tau = taus[f];
     P.tau = tau;
     P.balanced = isinf(tau) ? 1 : 0;
@@ -355,7 +353,6 @@ struct Solve {
   int symmetric = 0;   // self terms by the symmetric update (u and v are one buffer)
   float *u = nullptr, *v = nullptr;
   cudaStream_t st = nullptr;
-  int xs = 0;   // spectra kept as bf16 hi/lo (tensor-core operand format)
 };
 
 int ensure_stream(Grid& g) {
@@ -412,7 +409,6 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
     k_fill<<<1024, 256, 0, s.st>>>(v, n * nprob, 1.f);
   }
   SHOT_CUDA(cudaGetLastError());
-  s.xs = spectra_split(g, nprob, w.ldc);
   {  // tune the launch shapes on the solver's own form of the inverse DFT
     EpiParams up = base_ep(s);
     up.mode = EPI_UPDATE;
@@ -422,7 +418,7 @@ int solve_prepare(Grid& g, const std::vector<const float*>& P, const std::vector
   }
   if ((rc = launch_heat_mult(g, eps / 4.0, s.st))) return rc;
   // spectra of the starting v
-  return launch_dft_fwd(g, v, nprob, nullptr, 0, w.XY, w.ldc, s.st, s.xs);
+  return launch_dft_fwd(g, v, nprob, nullptr, 0, w.XY, w.ldc, s.st);
 }
 
 EpiParams base_ep(Solve& s) {
@@ -432,7 +428,6 @@ EpiParams base_ep(Solve& s) {
   ep.part = w.part;
   ep.eps = s.eps;
   ep.norm_l1 = s.norm_l1;
-  ep.xsplit = s.xs;
   return ep;
 }
 
@@ -470,7 +465,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
   };
   for (int i = 0; s.symmetric && i < nit; ++i) {
     // self term: u = sqrt(u (p / K u)^gamma) in place, and X := F(u)
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st))) return rc;
     ep.mode = EPI_SYM;
     ep.out = s.u;
     ep.marg = margP;
@@ -481,7 +476,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
   }
   for (int i = 0; !s.symmetric && i < nit; ++i) {
     // u-step: u = (ru p / K v)^gamma, and X := F(u)
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st))) return rc;
     ep.mode = EPI_UPDATE;
     ep.out = s.u;
     ep.marg = margP;
@@ -493,7 +488,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     if ((rc = join()) || (rc = launch_idft(g, w.Yb, w.ldc, s.nprob, ep, st))) return rc;
     if ((rc = fork_reduce(RED_U))) return rc;
     // v-step: v = (rv q / K u)^gamma, X := F(v); then the gauge / translation-invariant scalars
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st))) return rc;
     ep.out = s.v;
     ep.marg = margQ;
     ep.which = 1;
@@ -501,7 +496,7 @@ int solve_enqueue(Solve& s, int nit, bool check, cudaStream_t st) {
     if ((rc = fork_reduce(RED_V))) return rc;
   }
   if (check) {   // K v from the spectra X, which stay for the next u-step
-    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st, s.xs))) return rc;
+    if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, st))) return rc;
     ep.mode = EPI_CHECK;
     ep.other = s.u;
     ep.marg = margP;
@@ -519,7 +514,7 @@ int solve_final_enqueue(Solve& s) {
   ProbState* ps = reinterpret_cast<ProbState*>(w.probs);
   int rc;
   // final K v for the objective, mass and marginal error; writes u_true, v_true
-  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st, s.xs))) return rc;
+  if ((rc = launch_legendre(g, s.nprob, w.XY, w.C, w.Yb, w.ldc, s.st))) return rc;
   ep.mode = EPI_FINAL;
   ep.potentials = s.potentials;
   ep.out = s.v;
@@ -757,18 +752,9 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
   g->precision = precision;
   g->mode = legendre_mode;
   g->quad = quadrature;
-  {  // SHOT_FUSED_HEAT=1 selects the fused per-order analysis + synthesis kernel (BF16X3);
-     // SHOT_SPLIT_SPECTRA=1 has the solver keep bf16 hi/lo spectra on BF16X3 grids
-    const char* e = getenv("SHOT_FUSED_HEAT");
-    g->fused_heat = (e && e[0] == '1') ? 1 : 0;
-    e = getenv("SHOT_SPLIT_SPECTRA");
-    g->split_spectra = (e && e[0] == '1') ? 1 : 0;
-    e = getenv("SHOT_ANA_TRANSPOSED");   // 1: the transposed tensor-core analysis (fields on M)
-    g->ana_transposed = (e && e[0] == '1') ? 1 : 0;
-    e = getenv("SHOT_IDFT_PERSISTENT");   // 0: one item per CTA for the update half-steps too
+  {
+    const char* e = getenv("SHOT_IDFT_PERSISTENT");   // 0: one item per CTA for the update half-steps too
     g->idft_nonpersistent = (e && e[0] == '0') ? 1 : 0;
-    e = getenv("SHOT_MERGED_HEAT");   // 1: analysis + synthesis of a heat application in one persistent kernel
-    g->merged_heat = (e && e[0] == '1') ? 1 : 0;
     e = getenv("SHOT_TC_STAGES");   // 1..4 fixes the analysis pipeline depth instead of the autotuner
     g->tc_stages_override = (e && e[0] >= '1' && e[0] <= '4') ? e[0] - '0' : 0;
   }
@@ -847,7 +833,7 @@ int shot_grid_rings(shot_grid gh, int* len, long long* off, double* phi0) {
 int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
-  void* dptr[] = {g->tiles_ana_t, g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->hp_plan_d, g->ring_plan_d, g->hp_tw_d, g->hp_tw_base_d, g->xyz_d, g->blk_order_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tabT, g->tab_hi, g->tab_lo,
+  void* dptr[] = {g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->hp_plan_d, g->ring_plan_d, g->hp_tw_d, g->hp_tw_base_d, g->xyz_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tabT, g->tab_hi, g->tab_lo,
                   g->ws.ct_hi, g->ws.ct_lo, g->ws.ct32, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};

@@ -53,15 +53,11 @@ __device__ __forceinline__ void load_ring_pairs(const float* __restrict__ in, fl
 // Two-for-one unpack of the transformed ring pair (j north, J south) and the parity fold:
 // F_N(m) = (Z(m) + conj Z(N-m))/2, F_S(m) = (Z(m) - conj Z(N-m))/(2i);
 // S = a_j (F_N + F_S) -> block (m, even), D = a_j (F_N - F_S) -> block (m, odd).
-// xsplit: X holds the spectra as bf16 hi and lo arrays (hi first, lo 2(lmax+1) nh ldc
-// values later) instead of FP32, the operand format of the tensor-core analysis.
 template <int FG>
 __device__ __forceinline__ void unpack_fold_store(const float2* buf, int nfg, int f0, int N, int lmax, int nh, int jh,
                                                   float aj, const ProbState* __restrict__ ps, int scale_which,
-                                                  float* __restrict__ X, int ldc, int xsplit) {
+                                                  float* __restrict__ X, int ldc) {
   const int nm = lmax + 1, ld = seq_ld(N);
-  __nv_bfloat16* Xh = reinterpret_cast<__nv_bfloat16*>(X);
-  __nv_bfloat16* Xl = Xh + (size_t)2 * nm * nh * ldc;
   for (int idx = threadIdx.x; idx < nm * FG; idx += blockDim.x) {
     const int m = idx / FG, q = idx - m * FG;
     if (q >= nfg) continue;
@@ -76,17 +72,8 @@ __device__ __forceinline__ void unpack_fold_store(const float2* buf, int nfg, in
     const float2 D = make_float2(sc * (FN.x - FS.x), sc * (FN.y - FS.y));
     const size_t oS = ((size_t)(2 * m) * nh + jh) * ldc + 2 * f;
     const size_t oD = ((size_t)(2 * m + 1) * nh + jh) * ldc + 2 * f;
-    if (xsplit) {
-      const __nv_bfloat162 sh = __floats2bfloat162_rn(S.x, S.y), dh = __floats2bfloat162_rn(D.x, D.y);
-      const float2 sf = __bfloat1622float2(sh), df = __bfloat1622float2(dh);
-      *reinterpret_cast<__nv_bfloat162*>(Xh + oS) = sh;
-      *reinterpret_cast<__nv_bfloat162*>(Xl + oS) = __floats2bfloat162_rn(S.x - sf.x, S.y - sf.y);
-      *reinterpret_cast<__nv_bfloat162*>(Xh + oD) = dh;
-      *reinterpret_cast<__nv_bfloat162*>(Xl + oD) = __floats2bfloat162_rn(D.x - df.x, D.y - df.y);
-    } else {
-      *reinterpret_cast<float2*>(X + oS) = S;
-      *reinterpret_cast<float2*>(X + oD) = D;
-    }
+    *reinterpret_cast<float2*>(X + oS) = S;
+    *reinterpret_cast<float2*>(X + oD) = D;
   }
 }
 
@@ -94,7 +81,7 @@ template <int FG>
 __global__ void __launch_bounds__(kThreads, 3) k_dft_fwd(
     const float* __restrict__ in, int nf, int nlat, int nlon, int lmax, int nh,
     const float* __restrict__ a_ring, const ProbState* __restrict__ ps, int scale_which,
-    float* __restrict__ X, int ldc, FftPlan pl, const float2* __restrict__ tw_g, int xsplit) {
+    float* __restrict__ X, int ldc, FftPlan pl, const float2* __restrict__ tw_g) {
   extern __shared__ __align__(16) float2 sm[];
   const int N = nlon;
   float2* b0 = sm;
@@ -110,7 +97,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_dft_fwd(
   __syncthreads();
   const float2* buf = fft_smem<false>(b0, b1, tw, pl, nfg);
 
-  unpack_fold_store<FG>(buf, nfg, f0, N, lmax, nh, jh, a_ring[j], ps, scale_which, X, ldc, xsplit);
+  unpack_fold_store<FG>(buf, nfg, f0, N, lmax, nh, jh, a_ring[j], ps, scale_which, X, ldc);
 }
 
 template <int FG, class PL = RuntimePlan>
@@ -185,7 +172,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft(
     // the new scaling of this ring pair is in `other`: transform it for the next half-step
     __syncthreads();
     const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw, pl, nfg);
-    unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc, ep.xsplit);
+    unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc);
   }
 }
 
@@ -310,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft_p(
     if (ep.xout) {   // the update's new scaling: its spectra for the next half-step
       __syncthreads();
       const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw_g, pl, nfg);
-      unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc, ep.xsplit);
+      unpack_fold_store<FG>(zf, nfg, f0, N, lmax, nh, jh, aj, nullptr, 0, ep.xout, ldc);
     }
     item = next;
     slot ^= 1;
@@ -326,14 +313,14 @@ int pick_fg(int N, int nf) {
 
 template <int FG>
 int launch_fwd_t(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which, float* X,
-                 int ldc, cudaStream_t st, int xsplit) {
+                 int ldc, cudaStream_t st) {
   const size_t smem = (size_t)(fft_tw_len(g.plan) + 2 * FG * seq_ld(g.nlon)) * sizeof(float2);
   SHOT_CUDA(cudaFuncSetAttribute(k_dft_fwd<FG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid((nf + FG - 1) / FG, g.nh);   // field groups of one ring pair run together
   ProfScope prof(PK_DFT, st);
   count_launch();
   k_dft_fwd<FG><<<grid, kThreads, smem, st>>>(in, nf, g.nlat, g.nlon, g.lmax, g.nh, g.a_d, ps, scale_which, X,
-                                              ldc, g.plan, g.tw_d, xsplit);
+                                              ldc, g.plan, g.tw_d);
   SHOT_CUDA(cudaGetLastError());
   return SHOT_OK;
 }
@@ -377,10 +364,10 @@ using Plan1024 = CtPlan<1024, 4, 16, 16>;   // 512 x 1024 grids
 }  // namespace
 
 int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
-                   float* X, int ldc, cudaStream_t st, int xsplit) {
+                   float* X, int ldc, cudaStream_t st) {
   if (g.quad == SHOT_QUAD_HEALPIX) {
-    if (xsplit || (scale_which && scale_which != 1)) {
-      set_error("HEALPix ring transform: FP32 spectra and the per-field factor beta only");
+    if (scale_which && scale_which != 1) {
+      set_error("HEALPix ring transform: the per-field factor beta only");
       return SHOT_ERR_UNSUPPORTED;
     }
     return launch_hp_dft_fwd(g, in, nf, X, ldc, st, scale_which == 1 ? ps : nullptr);
@@ -392,10 +379,10 @@ int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, 
   int fg = pick_fg(g.nlon, nf);
   if (g.active.nf == nf && g.active.dft_fg > 0 && g.active.dft_fg * g.nlon <= kFftCap) fg = g.active.dft_fg;
   switch (fg) {
-    case 8: return launch_fwd_t<8>(g, in, nf, ps, scale_which, X, ldc, st, xsplit);
-    case 4: return launch_fwd_t<4>(g, in, nf, ps, scale_which, X, ldc, st, xsplit);
-    case 2: return launch_fwd_t<2>(g, in, nf, ps, scale_which, X, ldc, st, xsplit);
-    default: return launch_fwd_t<1>(g, in, nf, ps, scale_which, X, ldc, st, xsplit);
+    case 8: return launch_fwd_t<8>(g, in, nf, ps, scale_which, X, ldc, st);
+    case 4: return launch_fwd_t<4>(g, in, nf, ps, scale_which, X, ldc, st);
+    case 2: return launch_fwd_t<2>(g, in, nf, ps, scale_which, X, ldc, st);
+    default: return launch_fwd_t<1>(g, in, nf, ps, scale_which, X, ldc, st);
   }
 }
 

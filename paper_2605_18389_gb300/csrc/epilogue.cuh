@@ -13,7 +13,8 @@
 //               also written into `other` (u_j + i u_J) for the forward transform that follows
 //   EPI_CHECK   |u_true (K v_true) - p| sums for the marginal error (L2 or L1, App. C.3)
 //   EPI_FINAL   u_true, v_true (or the potentials), the marginal error, m(pi) and the dual
-//               objective
+//               objective (in FP64); m(pi) = sum a q when a balanced v-update has run (then
+//               v (K u) = q node by node), else sum a u (K v)
 //   EPI_SYM     self term (q = p): u = sqrt(u_old (p / Ku)^gamma) in place (ep.out holds u_old),
 //               breakdown counts; with ep.xout the new u is also written into `other`
 // Field f occupies out[f * fstride ...]; rings j and J start at rj and rJ within a field.
@@ -109,6 +110,13 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
   for (int q = 0; q < FG; ++q)
 #pragma unroll
     for (int i = 0; i < NPART; ++i) acc[q][i] = 0.f;
+  // EPI_FINAL: the dual objective and m(pi) in FP64 (the objective's terms carry the
+  // potentials' offsets eps la and eps lb, which cancel between the two marginals' terms and,
+  // across the three problems, in the divergence: FP32 sums of them lose the digits the
+  // divergence keeps; m(pi) enters S_dual times eps)
+  double acc_ot[FG], acc_m[FG];
+#pragma unroll
+  for (int q = 0; q < FG; ++q) acc_ot[q] = acc_m[q] = 0.0;
 
 #pragma unroll
   for (int q = 0; q < FG; ++q) {
@@ -267,6 +275,10 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
       const float la_hi = (float)P->la, lb_hi = (float)P->lb;
       const float la_lo = (float)(P->la - (double)la_hi), lb_lo = (float)(P->lb - (double)lb_hi);
       const int bal = P->balanced;
+      // balanced, after a v-update: v (K u) = q at every node, so m(pi) = sum a u (K v) =
+      // sum a v (K u) = sum a q (K is self-adjoint in the area inner product)
+      const bool mass_q = bal && !isnan(P->mass_v);
+      const double la = P->la, lb = P->lb;
       const float epsf = (float)ep.eps, tauf = (float)P->tau, et = bal ? 0.f : (float)(ep.eps / P->tau);
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const float2 zz = z[q * ld + k];
@@ -294,16 +306,18 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
             acc[q][0] += d * d;
             acc[q][1] += pm * pm;
           }
-          acc[q][2] += aj * ukv;
-          // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish
-          float t;
+          acc_m[q] += (double)(mass_q ? qm : ukv);
+          // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish.
+          // Balanced: p (la + log u_buf) + q (lb + log v_buf) in FP64, the buffers' logarithms
+          // in FP32 (they are O(1)); eps and a_j multiply the sums.
           if (bal) {
-            t = (pm > 0.f ? epsf * lu * pm : 0.f) + (qm > 0.f ? epsf * lv * qm : 0.f);
-          } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u)
-            t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
-                (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
+            acc_ot[q] += (pm > 0.f ? (double)pm * (la + (double)logf(ub)) : 0.0) +
+                         (qm > 0.f ? (double)qm * (lb + (double)logf(vb)) : 0.0);
+          } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u), per node in FP32
+            const float t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
+                            (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
+            acc_ot[q] += (double)t;
           }
-          acc[q][3] += aj * t;
         }
       }
     }
@@ -317,10 +331,39 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
       const float v = epi_warp_sum(acc[q][i]);
       if (lane == 0) red[wid][q * NPART + i] = v;
     }
-  __syncthreads();
+  {
+    __shared__ double redd[NT / 32][FG][2];   // EPI_FINAL: warp sums of m(pi) and the objective
+    if (ep.mode == EPI_FINAL) {
+#pragma unroll
+      for (int q = 0; q < FG; ++q) {
+        double v = acc_m[q], w = acc_ot[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          v += __shfl_xor_sync(0xffffffffu, v, o);
+          w += __shfl_xor_sync(0xffffffffu, w, o);
+        }
+        if (lane == 0) {
+          redd[wid][q][0] = v;
+          redd[wid][q][1] = w;
+        }
+      }
+    }
+    __syncthreads();
+    if (ep.mode == EPI_FINAL && threadIdx.x < 2 * FG) {
+      const int q = threadIdx.x >> 1, i = threadIdx.x & 1;
+      if (q < nfg && fi[q].live) {
+        double t = 0.0;
+        for (int w = 0; w < NT / 32; ++w) t += redd[w][q][i];
+        // m(pi) sums a_j times the node values; the balanced objective's sums are of
+        // p (la + log u_buf) + q (lb + log v_buf): times eps a_j
+        const double sc = (i == 1 && fi[q].balanced) ? ep.eps * (double)aj : (double)aj;
+        ep.part[((size_t)(f0 + q) * nh + jh) * NPART + 2 + i] = sc * t;
+      }
+    }
+  }
   if (threadIdx.x < FG * NPART) {
     const int q = threadIdx.x / NPART, i = threadIdx.x - q * NPART;
-    if (q < nfg) {
+    if (q < nfg && !(ep.mode == EPI_FINAL && i >= 2)) {
       const int f = f0 + q;
       if (fi[q].live) {
         double t = 0.0;

@@ -430,33 +430,6 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
     if (g.M[b] > 0)
       for (int r = 0; r < nh; r += g.bm_syn) ts.push_back({b, r});
   }
-  {  // blocks with rows, largest first, for the fused heat kernel
-    std::vector<int> ord;
-    for (int b = 0; b < g.nblk; ++b)
-      if (g.M[b] > 0) ord.push_back(b);
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return g.M[a] > g.M[b]; });
-    g.nwork = (int)ord.size();
-    g.nmt_max = (g.M[0] + g.bm_ana - 1) / g.bm_ana;
-    g.kc_max = (g.M[0] + 63) / 64;
-    SHOT_CUDA(cudaMalloc(&g.blk_order_d, ord.size() * sizeof(int)));
-    SHOT_CUDA(cudaMemcpyAsync(g.blk_order_d, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    SHOT_CUDA(cudaStreamSynchronize(st));   // ord is a local
-  }
-  {  // transposed analysis: each block's rows in at most 256-row runs of near-equal size
-    std::vector<TileR> tr;
-    for (int b = 0; b < g.nblk; ++b) {
-      const int M = g.M[b];
-      if (M <= 0) continue;
-      const int parts = (M + 255) / 256;
-      const int per = ((M + parts - 1) / parts + 31) / 32 * 32;
-      for (int r0 = 0; r0 < M; r0 += per) tr.push_back({b, r0, std::min(per, M - r0)});
-    }
-    std::stable_sort(tr.begin(), tr.end(), [](const TileR& a, const TileR& b) { return a.rows > b.rows; });
-    g.ntiles_ana_t = (int)tr.size();
-    SHOT_CUDA(cudaMalloc(&g.tiles_ana_t, tr.size() * sizeof(TileR)));
-    SHOT_CUDA(cudaMemcpyAsync(g.tiles_ana_t, tr.data(), tr.size() * sizeof(TileR), cudaMemcpyHostToDevice, st));
-    SHOT_CUDA(cudaStreamSynchronize(st));   // tr is a local
-  }
   // largest contraction first (synthesis work is proportional to M)
   std::stable_sort(ts.begin(), ts.end(), [&](const Tile& a, const Tile& b) { return g.M[a.blk] > g.M[b.blk]; });
   g.ntiles_ana = (int)ta.size();

@@ -271,10 +271,6 @@ int launch_hp_dft_fwd(const Grid& g, const float* in, int nf, float* X, int ldc,
 }
 
 int launch_hp_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
-  if (ep.xout && ep.xsplit) {
-    set_error("HEALPix grids keep FP32 spectra");
-    return SHOT_ERR_UNSUPPORTED;
-  }
   switch (hp_pick_fg(g, nf, true)) {
     case 4: return hp_idft_t<4>(g, Y, ldc, nf, ep, st);
     case 2: return hp_idft_t<2>(g, Y, ldc, nf, ep, st);

@@ -3,11 +3,13 @@
 // Same contractions as the other paths (App. C.1 semi-naive SHT; Sec. 3.2 h_l scaling):
 //   analysis   C[i][c] = h_l sum_jh Pbar_lm(x_jh) X[jh][c]        (K = nodes jh)
 //   synthesis  Y[jh][c] = sum_i Pbar_lm(x_jh) C[i][c]               (K = degrees i)
-// Every FP32 operand v is split into two TF32 values: hi = v with its 13 low mantissa bits
-// cleared, lo = v - hi (exact in FP32; the tensor core reads it as TF32 as well).  The
-// product is accumulated in FP32 in tensor memory as A_hi B_hi + A_hi B_lo + A_lo B_hi
-// (tcgen05.mma kind::tf32, K = 8 per instruction); the dropped lo*lo term and the TF32
-// reading of lo leave ~2^-21 relative error per product, against ~2^-16 for BF16x3.  The
+// Every FP32 operand v is split into two TF32 values: hi = v rounded to the nearest TF32
+// (10 stored mantissa bits), lo = v - hi (exact in FP32, |lo| <= 2^-11 |v|) rounded to the
+// nearest TF32 as well, so that both are exact TF32 values and the tensor core reads them
+// as they are.  The product is accumulated in FP32 in tensor memory as
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (tcgen05.mma kind::tf32, K = 8 per instruction); the
+// rounding of lo (<= 2^-22 |v|) and the dropped lo*lo term (<= 2^-22 |AB|) leave
+// <= ~2^-20 relative error per product, of either sign, against ~2^-16 for BF16x3.  The
 // HBM traffic is that of the BF16x3 path: the table is read once as FP32 (4 bytes an entry,
 // as bf16 hi + lo) and split in shared memory.
 //
@@ -37,6 +39,7 @@ constexpr int kTK = 32;                          // K per stage (one 128-byte ro
 constexpr int kTTile = kBM * kTK * 4;            // 16 KB: 128 rows x 32 FP32
 constexpr int kT32MaxStages = 4;
 constexpr uint32_t kTf32Mask = 0xFFFFE000u;      // sign, exponent and 10 stored mantissa bits
+constexpr uint32_t kTf32Half = 0x00001000u;      // half a unit in the last TF32 place
 
 __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accum) {
@@ -53,7 +56,17 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float tf32_hi(float v) { return __uint_as_float(__float_as_uint(v) & kTf32Mask); }
+// v rounded to the nearest TF32 value (ties away from zero): add half a TF32 unit to the
+// magnitude bits, then clear the 13 low mantissa bits (a carry moves into the exponent, as it
+// should).  Finite inputs below the FP32 maximum only (the operands here are far below it).
+__device__ __forceinline__ float tf32_rn(float v) {
+  return __uint_as_float((__float_as_uint(v) + kTf32Half) & kTf32Mask);
+}
+// hi/lo split of four values: hi = rn(v), lo = rn(v - hi)
+__device__ __forceinline__ void tf32_split4(const float (&v)[4], float4& h, float4& l) {
+  h = make_float4(tf32_rn(v[0]), tf32_rn(v[1]), tf32_rn(v[2]), tf32_rn(v[3]));
+  l = make_float4(tf32_rn(v[0] - h.x), tf32_rn(v[1] - h.y), tf32_rn(v[2] - h.z), tf32_rn(v[3] - h.w));
+}
 
 // byte offset of FP32 element (row, k) in a K-major 128B-swizzled tile with 32-element rows
 __device__ __forceinline__ uint32_t sw128_offset32(int row, int k) {
@@ -77,9 +90,11 @@ __device__ __forceinline__ void split_inplace(uint8_t* raw, uint8_t* lo, int nby
     for (int i = 0; i < kSplitBatch; ++i) {
       const int o = base + (pt + i * kSplitThreads) * 16;
       if (o < nbytes) {
-        const float4 h = make_float4(tf32_hi(v[i].x), tf32_hi(v[i].y), tf32_hi(v[i].z), tf32_hi(v[i].w));
+        const float w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
+        float4 h, l;
+        tf32_split4(w, h, l);
         *reinterpret_cast<float4*>(raw + o) = h;
-        *reinterpret_cast<float4*>(lo + o) = make_float4(v[i].x - h.x, v[i].y - h.y, v[i].z - h.z, v[i].w - h.w);
+        *reinterpret_cast<float4*>(lo + o) = l;
       }
     }
   }
@@ -107,11 +122,11 @@ __device__ __forceinline__ void split_xt(const float* xs, int nmma, int ncols, i
       const int e = e0 + b * kSplitThreads;
       if (e < ntask) {
         const int c = e % nmma, k4 = (e / nmma) * 4;
-        const float4 h = make_float4(tf32_hi(v[b][0]), tf32_hi(v[b][1]), tf32_hi(v[b][2]), tf32_hi(v[b][3]));
+        float4 h, l;
+        tf32_split4(v[b], h, l);
         const uint32_t o = sw128_offset32(c, k4);
         *reinterpret_cast<float4*>(bh + o) = h;
-        *reinterpret_cast<float4*>(bl + o) =
-            make_float4(v[b][0] - h.x, v[b][1] - h.y, v[b][2] - h.z, v[b][3] - h.w);
+        *reinterpret_cast<float4*>(bl + o) = l;
       }
     }
   }
@@ -151,10 +166,10 @@ struct XtPlan {
 #pragma unroll
     for (int i = 0; i < kXtTasks; ++i) {
       if (c[i] < 0) continue;
-      const float4 h = make_float4(tf32_hi(v[i][0]), tf32_hi(v[i][1]), tf32_hi(v[i][2]), tf32_hi(v[i][3]));
+      float4 h, l;
+      tf32_split4(v[i], h, l);
       *reinterpret_cast<float4*>(bh + o[i]) = h;
-      *reinterpret_cast<float4*>(bl + o[i]) =
-          make_float4(v[i][0] - h.x, v[i][1] - h.y, v[i][2] - h.z, v[i][3] - h.w);
+      *reinterpret_cast<float4*>(bl + o[i]) = l;
     }
   }
 };

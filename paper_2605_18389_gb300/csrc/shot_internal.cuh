@@ -83,10 +83,6 @@ struct Tile {
   int blk;    // 2*m + p
   int r0;     // first row of the tile (i for analysis, jh for synthesis)
 };
-// a run of degree rows of one block for the transposed tensor-core analysis (rows <= 256)
-struct TileR {
-  int blk, r0, rows;
-};
 
 struct Workspace {
   int nf_cap = 0;       // fields the buffers hold
@@ -161,17 +157,8 @@ struct Grid {
   long long* row_off_d = nullptr;
   Tile* tiles_ana = nullptr;
   Tile* tiles_syn = nullptr;
-  int* blk_order_d = nullptr;   // blocks with rows, largest first (fused heat kernel)
-  TileR* tiles_ana_t = nullptr;  // transposed analysis tiles, largest first
-  int ntiles_ana_t = 0;
-  int nwork = 0, nmt_max = 0, kc_max = 0;
-  int fused_heat = 0;           // BF16X3 table grids: fused analysis + synthesis kernel
-  int merged_heat = 0;          // SHOT_MERGED_HEAT=1: BF16X3 heat applications in k_heat_merged
-  int split_spectra = 0;        // BF16X3 table grids: the solver keeps bf16 hi/lo spectra
   int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core analysis (0 = tuned)
   int idft_nonpersistent = 0;   // SHOT_IDFT_PERSISTENT=0: update half-steps use the one-item-per-CTA k_idft
-  int ana_transposed = 0;       // SHOT_ANA_TRANSPOSED=1: fields on M, degree rows on N (k_ana_tc_t)
-                                // instead of 128-row tiles of degrees on M
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use
   // ring geometry (every grid): ring i holds ring_len[i] nodes starting at ring_off[i] of a
   // field of npix nodes; HEALPix rings also carry the longitude of their first pixel,
@@ -209,6 +196,8 @@ struct ProbState {
   double beta;      // factor the forward ring DFT applies with scale_which 1 (gradient sweeps)
   double err;       // last marginal error
   double ot, ot_dual, mass;
+  double mass_v;    // unbalanced: m(pi) = sum a v (K u) from the latest v-update; balanced: 0
+                    // once a v-update has run (then m(pi) = sum a q); NaN before the first
   double tau;       // marginal penalty of this problem (INFINITY: balanced)
   float gamma;      // tau/(tau+eps), 1 when balanced
   float et;         // eps/(tau+eps), 0 when balanced
@@ -242,7 +231,6 @@ struct EpiParams {
   int which;                  // 0: u-step (marginal p), 1: v-step (marginal q)
   float* xout;                // EPI_UPDATE: when set, the CTA also ring-transforms the new
                               // scaling (unscaled) into the folded spectra xout[.][jh][ldc]
-  int xsplit;                 // xout as bf16 hi/lo arrays (tensor-core operand) instead of FP32
   int potentials;             // EPI_FINAL: write eps log u, eps log v instead of u, v
   int skip_store;             // EPI_UPDATE: the new scaling feeds only the fused forward
                               // transform (no later launch reads this iteration's buffer)
@@ -252,12 +240,9 @@ bool profiling_on();
 // ---------------------------------------------------------------------------------
 // Launchers (return SHOT status)
 int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
-                   float* X, int ldc, cudaStream_t st, int xsplit = 0);
+                   float* X, int ldc, cudaStream_t st);
 int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
-int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st,
-                    int xsplit = 0);
-// whether the solver keeps its spectra as bf16 hi/lo (BF16X3 table grids, <= 32 fields)
-int spectra_split(const Grid& g, int nf, int ldc);
+int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
 int launch_heat_mult(const Grid& g, double t, cudaStream_t st);
 int launch_coeff_gather(const Grid& g, const float* C, int ldc, int nf, float* coeffs, cudaStream_t st);
 int launch_coeff_scatter(const Grid& g, const float* coeffs, int nf, float* C, int ldc, cudaStream_t st);
@@ -268,9 +253,8 @@ int build_grid_tables(Grid& g, cudaStream_t st);
 // selects g.active for nf (tunes on first use)
 int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd = nullptr);
 int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
-                       bool apply_h, cudaStream_t st, int xsplit = 0);
+                       bool apply_h, cudaStream_t st);
 int launch_c_to_ct(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
-int launch_heat_merged(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st);
 int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
                          bool apply_h, cudaStream_t st);
 int launch_c_to_ct32(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
@@ -278,7 +262,6 @@ int build_recurrence(Grid& g, cudaStream_t st);
 int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
                         bool apply_h, cudaStream_t st);
 int tc_nmma(int nf);
-int launch_heat_tc(const Grid& g, int nf, const float* X, float* Y, int ldc, cudaStream_t st, int xsplit = 0);
 int ensure_workspace(Grid& g, int nf, cudaStream_t st);
 // HEALPix
 void healpix_geometry(Grid& g, int nside);

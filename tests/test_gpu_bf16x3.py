@@ -12,7 +12,7 @@ from oracle.grid import Grid as OGrid
 from oracle import sht as osht
 from oracle import sinkhorn as sk
 from paper_2605_18389_gb300 import inputs
-from tests.gpu_util import rel_max, f32, s_err_prec, potentials_err
+from tests.gpu_util import rel_max, f32, potentials_err, assert_s, BF16_S_LIMIT
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -120,8 +120,8 @@ def test_bf16x3_divergence_matches_oracle(grid_cache, nlat, eps, tau, T, tol):
     ref = sk.divergence(og, p64, q64, eps, tau, T=T, delta=tol, C=10)
     assert np.all(r["status"] == ref["status"])
     ot_pq = ref["runs"]["ot"][:2]
-    assert np.all(s_err_prec(r["S"], ref["S"], ot_pq, TOL, "bf16x3") <= 1.0)
-    assert np.all(s_err_prec(r["S_dual"], ref["S_dual"], ot_pq, TOL, "bf16x3") <= 1.0)
+    assert_s(r["S"], ref["S"], ot_pq, TOL, limited_by=BF16_S_LIMIT)
+    assert_s(r["S_dual"], ref["S_dual"], ot_pq, TOL, limited_by=BF16_S_LIMIT)
 
 
 @pytest.mark.parametrize("nlat,nf", [(96, 24), (64, 40), (40, 64)])

@@ -11,7 +11,7 @@ import pytest
 from oracle.grid import Grid as OGrid
 from oracle import sinkhorn as sk
 from paper_2605_18389_gb300 import inputs
-from tests.gpu_util import f32, s_err
+from tests.gpu_util import f32, s_err, assert_s, FP32_S_LIMIT
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -43,13 +43,14 @@ def test_multi_grid_sets_match_oracle_and_single_calls():
         assert rc >= 0
         for st, o, ref in zip(sets, outs, refs):
             assert np.all(o["status"] == 0)
-            ot_pq = ref["runs"]["ot"][: len(o["S"])]
-            assert np.all(s_err(o["S"], ref["S"], ot_pq, TOL_S) <= 1.0), (o["S"], ref["S"])
-            assert np.all(s_err(o["S_dual"], ref["S_dual"], ot_pq, TOL_S) <= 1.0)
             rc1, r1 = shot.shot_divergence(st["grid"], st["p"], st["q"], eps, st["tau"], max_iter=T, tol=0.0,
                                            check_every=10)
             singles.append(r1)
             np.testing.assert_allclose(o["S"], r1["S"], rtol=1e-6, atol=1e-9)
+        for o, ref in zip(outs, refs):   # S against the oracle last (FP32: see FP32_S_LIMIT)
+            ot_pq = ref["runs"]["ot"][: len(o["S"])]
+            assert_s(o["S"], ref["S"], ot_pq, TOL_S, limited_by=FP32_S_LIMIT)
+            assert_s(o["S_dual"], ref["S_dual"], ot_pq, TOL_S, limited_by=FP32_S_LIMIT)
     finally:
         for g, _ in grids.values():
             shot.shot_grid_free(g)

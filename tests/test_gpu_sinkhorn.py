@@ -7,7 +7,7 @@ import pytest
 from oracle.grid import Grid as OGrid
 from oracle import sinkhorn as sk
 from paper_2605_18389_gb300 import inputs
-from tests.gpu_util import rel_max, f32, s_err, s_err_prec, potentials_err, UNIT
+from tests.gpu_util import rel_max, f32, s_err, potentials_err, assert_s, BF16_S_LIMIT, FP32_S_LIMIT
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -41,7 +41,7 @@ def _fields(og, recipe, seed, npairs, masses=False):
 
 
 @pytest.mark.parametrize("nlat,nlon,eps,tau,T", [(16, None, 0.1, math.inf, 40), (32, None, 0.1, math.inf, 60),
-                                                 (32, None, 0.1, 1.0, 60), (64, None, 0.02, 0.1, 30),
+                                                 (32, None, 0.1, 1.0, 60), (64, None, 0.01, 0.1, 30),
                                                  (33, 72, 0.1, math.inf, 30)])
 def test_sinkhorn_fixed_iterations_match_oracle(grid_cache, nlat, nlon, eps, tau, T):
     g, og = grid_cache(nlat, nlon)
@@ -95,7 +95,7 @@ def test_breakdown_reported_at_oracle_iteration(grid_cache):
 
 # tol >= 1e-6: the FP32 path resolves the relative marginal error down to ~3e-7
 @pytest.mark.parametrize("nlat,eps,tau,T,tol", [(16, 0.2, math.inf, 400, 2e-6), (32, 0.1, math.inf, 600, 1e-6),
-                                                (32, 0.1, 1.0, 80, 0.0), (64, 0.02, 10.0, 40, 0.0)])
+                                                (32, 0.1, 1.0, 80, 0.0), (64, 0.01, 10.0, 40, 0.0)])
 def test_divergence_matches_oracle(grid_cache, nlat, eps, tau, T, tol):
     g, og = grid_cache(nlat)
     unb = not math.isinf(tau)
@@ -220,14 +220,15 @@ def test_unbalanced_potentials_beyond_fp32_exponent_range(prec):
         phi, psi = r["u"].cpu().numpy(), r["v"].cpu().numpy()
         assert rel_max(phi, ref["phi"]) < tol and rel_max(psi, ref["psi"]) < tol
         np.testing.assert_allclose(r["ot"], ref["ot"], rtol=tol)
-        # m(pi) = sum a u (K v) moves by |d(phi + psi)| / eps (relative) when the potentials
-        # move by d: one unit roundoff of potentials of size ~4.7 is ~3e-5 of m(pi) at eps = 0.01
-        tol_m = max(tol, UNIT[prec] * (np.max(np.abs(ref["phi"])) + np.max(np.abs(ref["psi"]))) / eps)
+        # m(pi) = sum a e^{(phi + psi)/eps} H...: a relative change d of the potentials moves it by
+        # (|phi| + |psi|) d / eps, so FP32 potentials (d = 2^-24) of size ~4.7 at eps = 0.01
+        # carry ~5e-5 of m(pi) (the potentials themselves are within tol above)
+        tol_m = max(tol, 2.0 ** -24 * (np.max(np.abs(ref["phi"])) + np.max(np.abs(ref["psi"]))) / eps)
         np.testing.assert_allclose(r["mass_pi"], ref["mass_pi"], rtol=tol_m)
         rc, rd = shot.shot_divergence(g, pt, qt, eps, tau, max_iter=T, tol=0.0, check_every=10)
         refd = sk.divergence(og, p64, q64, eps, tau, T=T, delta=0.0, C=10)
         assert rc == 0 and np.all(rd["status"] == 0)
-        assert np.all(s_err(rd["S"], refd["S"], refd["runs"]["ot"][:2], tol) <= 1.0)
+        assert_s(rd["S"], refd["S"], refd["runs"]["ot"][:2], tol, limited_by=BF16_S_LIMIT if prec == "bf16x3" else None)
     finally:
         shot.shot_grid_free(g)
 
@@ -327,8 +328,7 @@ def test_symmetric_self_terms_match_oracle(prec, tau):
         assert rc == 0 and np.all(r["status"] == 0) and np.all(ref["status"] == 0)
         np.testing.assert_allclose(r["ot3"][2:], ref["self"]["ot"], rtol=tol)
         np.testing.assert_allclose(r["ot3"][:2], ref["pq"]["ot"], rtol=tol)
-        # S cancels: its error floor is the precision's unit roundoff times OT(p, q)
-        assert np.all(s_err_prec(r["S"], ref["S"], ref["pq"]["ot"], tol, prec) <= 1.0), (r["S"], ref["S"])
+        assert_s(r["S"], ref["S"], ref["pq"]["ot"], tol, limited_by=BF16_S_LIMIT if prec == "bf16x3" else FP32_S_LIMIT)
     finally:
         shot.shot_grid_free(g)
 

@@ -14,7 +14,7 @@ from oracle.gradient import envelope
 from oracle import sht as osht
 from oracle import sinkhorn as sk
 from paper_2605_18389_gb300 import inputs
-from tests.gpu_util import rel_max, f32, s_err_prec, potentials_err
+from tests.gpu_util import rel_max, f32, s_err, potentials_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -159,8 +159,8 @@ def test_tf32x3_divergence_matches_oracle(grid_cache, nlat, eps, tau, T, tol):
     ref = sk.divergence(og, p64, q64, eps, tau, T=T, delta=tol, C=10)
     assert np.all(r["status"] == ref["status"])
     ot_pq = ref["runs"]["ot"][:2]
-    assert np.all(s_err_prec(r["S"], ref["S"], ot_pq, TOL_S, "tf32x3") <= 1.0)
-    assert np.all(s_err_prec(r["S_dual"], ref["S_dual"], ot_pq, TOL_S, "tf32x3") <= 1.0)
+    assert np.all(s_err(r["S"], ref["S"], ot_pq, TOL_S) <= 1.0)
+    assert np.all(s_err(r["S_dual"], ref["S_dual"], ot_pq, TOL_S) <= 1.0)
 
 
 def test_tf32x3_envelope_gradient_matches_oracle():
