@@ -361,8 +361,10 @@ def make_grid(shot, args, prec, mode):
     return shot.shot_grid_init_quad(quad, args.nlat, 2 * args.nlat, -1, prec, mode)
 
 
-PRECS = ("fp32", "tf32x3", "bf16x3")
-TARGET = {"fp32": 1e-5, "tf32x3": 1e-4, "bf16x3": 1e-4}
+# the timed and accuracy-checked forms: (precision of the Legendre contractions, Legendre mode)
+FORMS = {"fp32": ("fp32", "table"), "tf32x3": ("tf32x3", "table"), "tf32x3_rec": ("tf32x3", "recurrence"),
+         "bf16x3": ("bf16x3", "table")}
+TARGET = {"fp32": 1e-5, "tf32x3": 1e-4, "tf32x3_rec": 1e-4, "bf16x3": 1e-4}
 ACC_ITERS = 20   # iterations of the accuracy sample (one pair, the oracle's bounded sample)
 
 
@@ -370,9 +372,22 @@ def prec_code(shot, prec):
     return {"fp32": shot.SHOT_FP32, "bf16x3": shot.SHOT_BF16X3, "tf32x3": shot.SHOT_TF32X3}[prec]
 
 
-def time_form(args, shot, torch, prec, mode, pt, qt):
-    """Another precision on the same fields and steps (graph path, CUDA events): iters/s."""
-    g = make_grid(shot, args, prec_code(shot, prec), mode)
+def mode_code(shot, legendre):
+    return shot.SHOT_TABLE if legendre == "table" else shot.SHOT_RECURRENCE
+
+
+def form_name(precision, legendre):
+    return precision + ("_rec" if legendre == "recurrence" else "")
+
+
+def form_grid(shot, args, form):
+    prec, leg = FORMS[form]
+    return make_grid(shot, args, prec_code(shot, prec), mode_code(shot, leg))
+
+
+def time_form(args, shot, torch, form, pt, qt):
+    """Another form on the same fields and steps (graph path, CUDA events): iters/s."""
+    g = form_grid(shot, args, form)
     shot.shot_grid_reserve(g, 3 * PAIRS)
     u3 = torch.empty((3 * PAIRS,) + tuple(pt.shape[1:]), device="cuda")
     v3 = torch.empty_like(u3)
@@ -390,14 +405,14 @@ def time_form(args, shot, torch, prec, mode, pt, qt):
     return {"value": args.steps / (ms / 1e3), "unit": "iters/s", "ms_per_step": ms / args.steps}
 
 
-def accuracy_sample_gpu(args, shot, torch, mode, p, q):
-    """Every precision on the accuracy sample: the first pair of the batch (3 problems),
-    ACC_ITERS iterations; returns S, S_dual, OT and the scalings per precision (host)."""
+def accuracy_sample_gpu(args, shot, torch, p, q):
+    """Every form on the accuracy sample: the first pair of the batch (3 problems),
+    ACC_ITERS iterations; returns S, S_dual, OT and the scalings per form (host)."""
     out = {}
     pt = torch.from_numpy(np.ascontiguousarray(p[:1])).cuda()
     qt = torch.from_numpy(np.ascontiguousarray(q[:1])).cuda()
-    for prec in PRECS:
-        g = make_grid(shot, args, prec_code(shot, prec), mode)
+    for prec in FORMS:
+        g = form_grid(shot, args, prec)
         u3 = torch.empty((3,) + tuple(pt.shape[1:]), device="cuda")
         v3 = torch.empty_like(u3)
         rc, r = shot.shot_divergence(g, pt, qt, EPS, args.tau, max_iter=ACC_ITERS, tol=0.0, check_every=CHECK_EVERY,
@@ -722,11 +737,12 @@ def main():
     share = {k: round(v[0] / sum(x[0] for x in kinds.values()), 4) for k, v in kinds.items()}
     per_kind = {k: {"avg_launch_ms": round(v[0] / v[1], 5), "launches": v[1]} for k, v in kinds.items()}
 
-    forms = {args.precision: {"value": value, "unit": "iters/s", "ms_per_step": ms / args.steps}}
+    head = form_name(args.precision, args.legendre)
+    forms = {head: {"value": value, "unit": "iters/s", "ms_per_step": ms / args.steps}}
     if not args.no_compare and ws == 1:
-        for prec in PRECS:
-            if prec != args.precision:
-                forms[prec] = time_form(args, shot, torch, prec, mode, pt, qt)
+        for f in FORMS:
+            if f != head:
+                forms[f] = time_form(args, shot, torch, f, pt, qt)
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -737,19 +753,20 @@ def main():
             "status": {"rc": int(rc), "S_finite": bool(np.all(np.isfinite(res["S"])))},
             "forms": forms}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        sample = accuracy_sample_gpu(args, shot, torch, mode, p, q)
+        sample = accuracy_sample_gpu(args, shot, torch, p, q)
         line["cpu_baseline"], acc = cpu_baseline(args, sample)
         line["accuracy"] = {"vs_oracle": acc}
         # the speedup of a split form over FP32 counts only where the split form meets its bar
+        for f in forms:
+            if f in acc:
+                forms[f]["meets_target"] = acc[f]["meets_target"]
         if "fp32" in forms:
-            for prec in ("tf32x3", "bf16x3"):
-                if prec in forms and prec in acc:
-                    forms[prec]["speedup_over_fp32"] = forms[prec]["value"] / forms["fp32"]["value"]
-                    forms[prec]["meets_target"] = acc[prec]["meets_target"]
-            hp = args.precision
-            if hp != "fp32" and hp in acc:
-                line["split_speedup"] = (forms[hp]["value"] / forms["fp32"]["value"]
-                                         if acc[hp]["meets_target"] else None)
+            for f in forms:
+                if f != "fp32":
+                    forms[f]["speedup_over_fp32"] = forms[f]["value"] / forms["fp32"]["value"]
+            if head != "fp32" and head in acc:
+                line["split_speedup"] = (forms[head]["value"] / forms["fp32"]["value"]
+                                         if acc[head]["meets_target"] else None)
     shot.shot_grid_free(g)
     if rank == 0:
         print(json.dumps(line))

@@ -40,27 +40,28 @@ int launch_analysis_simt(const Grid& g, int nf, const float* X, float* C, int ld
 int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st);
 
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st) {
+  // TF32X3 grids run the tensor-core kernels in both Legendre modes (table or checkpoints)
+  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st);
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st);
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st);
-  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st);
   return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st) {
+  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
   if (g.precision == SHOT_FP32) return launch_analysis_simt(g, nf, X, C, ldc, apply_h, st);
-  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
   return launch_legendre_tc(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
 }
 int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st) {
-  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, nullptr, const_cast<float*>(C), Y, ldc, false, true,
-                                                            false, st);
-  if (g.precision == SHOT_FP32) return launch_synthesis_simt(g, nf, C, Y, ldc, st);
   if (g.precision == SHOT_TF32X3) {
     const int rc = launch_c_to_ct32(g, nf, C, ldc, st);
     if (rc) return rc;
     return launch_legendre_tf32(g, nf, nullptr, nullptr, Y, ldc, false, true, false, st);
   }
+  if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, nullptr, const_cast<float*>(C), Y, ldc, false, true,
+                                                            false, st);
+  if (g.precision == SHOT_FP32) return launch_synthesis_simt(g, nf, C, Y, ldc, st);
   int rc = launch_c_to_ct(g, nf, C, ldc, st);
   if (rc) return rc;
   return launch_legendre_tc(g, nf, nullptr, nullptr, Y, ldc, false, true, false, st);
@@ -735,8 +736,8 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     set_error("unknown legendre_mode");
     return SHOT_ERR_INVALID_ARG;
   }
-  if (legendre_mode == SHOT_RECURRENCE && precision != SHOT_FP32) {
-    set_error("SHOT_RECURRENCE is built for SHOT_FP32 grids");
+  if (legendre_mode == SHOT_RECURRENCE && precision == SHOT_BF16X3) {
+    set_error("SHOT_RECURRENCE is built for SHOT_FP32 and SHOT_TF32X3 grids");
     return SHOT_ERR_UNSUPPORTED;
   }
   FftPlan plan;
@@ -785,8 +786,8 @@ int shot_grid_init_healpix(shot_grid* out, int nside, int lmax, int precision, i
     set_error("unknown legendre_mode");
     return SHOT_ERR_INVALID_ARG;
   }
-  if (legendre_mode == SHOT_RECURRENCE && precision != SHOT_FP32) {
-    set_error("SHOT_RECURRENCE is built for SHOT_FP32 grids");
+  if (legendre_mode == SHOT_RECURRENCE && precision == SHOT_BF16X3) {
+    set_error("SHOT_RECURRENCE is built for SHOT_FP32 and SHOT_TF32X3 grids");
     return SHOT_ERR_UNSUPPORTED;
   }
   Grid* g = new Grid;
@@ -834,7 +835,7 @@ int shot_grid_free(shot_grid gh) {
   Grid* g = as_grid(gh);
   if (!g) return SHOT_OK;
   void* dptr[] = {g->ring_len_d, g->ring_off_d, g->ring_phase_d, g->hp_plan_d, g->ring_plan_d, g->hp_tw_d, g->hp_tw_base_d, g->xyz_d, g->ws.Yb, g->x_d, g->w_d, g->a_d, g->tw_d, g->h_d, g->tab, g->tabT, g->tab_hi, g->tab_lo,
-                  g->ws.ct_hi, g->ws.ct_lo, g->ws.ct32, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->M_d,
+                  g->ws.ct_hi, g->ws.ct_lo, g->ws.ct32, g->rec_seeds, g->rec_coef, g->rec_coef_off, g->rec_x, g->ck, g->ck_off_d, g->M_d,
                   g->row_off_d, g->tiles_ana, g->tiles_syn, g->ws.XY, g->ws.C, g->ws.part, g->ws.probs,
                   g->ws.marg, g->ws.ubuf, g->ws.vbuf, g->ws.dev_int};
   for (void* p : dptr)

@@ -395,7 +395,7 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   __nv_bfloat16 *hi = nullptr, *lo = nullptr;
   g.ldi = (g.M[0] + 7) / 8 * 8;
   if (g.mode == SHOT_RECURRENCE) {
-    int rc = build_recurrence(g, st);
+    int rc = g.precision == SHOT_TF32X3 ? build_tf32_recurrence(g, st) : build_recurrence(g, st);
     if (rc) return rc;
   } else {
   float* tabT = nullptr;

@@ -3,13 +3,14 @@
 // Same contractions as the other paths (App. C.1 semi-naive SHT; Sec. 3.2 h_l scaling):
 //   analysis   C[i][c] = h_l sum_jh Pbar_lm(x_jh) X[jh][c]        (K = nodes jh)
 //   synthesis  Y[jh][c] = sum_i Pbar_lm(x_jh) C[i][c]               (K = degrees i)
-// Every FP32 operand v is split into two TF32 values: hi = v rounded to the nearest TF32
-// (10 stored mantissa bits), lo = v - hi (exact in FP32, |lo| <= 2^-11 |v|) rounded to the
-// nearest TF32 as well, so that both are exact TF32 values and the tensor core reads them
-// as they are.  The product is accumulated in FP32 in tensor memory as
-// A_hi B_hi + A_hi B_lo + A_lo B_hi (tcgen05.mma kind::tf32, K = 8 per instruction); the
-// rounding of lo (<= 2^-22 |v|) and the dropped lo*lo term (<= 2^-22 |AB|) leave
-// <= ~2^-20 relative error per product, of either sign, against ~2^-16 for BF16x3.  The
+// Every FP32 operand v is split into two TF32 values, hi = v rounded to the nearest TF32 and
+// lo = v - hi rounded likewise (|lo| <= 2^-11 |v|, either sign), both written to shared memory
+// as exact TF32 values (the tensor core reads a 32-bit kind::tf32 operand by ignoring its 13
+// low mantissa bits, checked bit for bit against operands written with the bits cleared, so a
+// value that is not exact TF32 would be truncated).  The product is accumulated in FP32 in
+// tensor memory as A_hi B_hi + A_hi B_lo + A_lo B_hi (tcgen05.mma kind::tf32, K = 8 per
+// instruction); the rounding of lo (<= 2^-22 |v|) and the dropped lo*lo term (<= 2^-22 |AB|)
+// leave ~2^-21 relative error per product, of either sign, against ~2^-16 for BF16x3.  The
 // HBM traffic is that of the BF16x3 path: the table is read once as FP32 (4 bytes an entry,
 // as bf16 hi + lo) and split in shared memory.
 //
@@ -23,6 +24,22 @@
 //              B = C^T [columns][32 degrees]                      (TMA, FP32 C^T written by
 //                                                                  the analysis epilogue)
 // kind::tf32 is used with K-major operands only, hence the transposed table copy.
+//
+// Recurrence mode (SHOT_RECURRENCE, O(n) memory): no table.  The grid keeps checkpoints,
+// Pbar at the degree pairs (m + 16 s, m + 16 s + 1) of every order m and north-hemisphere node
+// (FP64 recurrence of App. B, rounded to FP32; about a sixteenth of the table), and the
+// recurrence coefficients a_lm, b_lm in FP32.  A stage's checkpoint box comes by TMA with the
+// spectra (analysis) or C^T (synthesis) tile, and the split warps regenerate the stage's A tile
+// by the three-term recurrence Pbar_lm = a_lm (x Pbar_{l-1,m} - b_lm Pbar_{l-2,m}) in FP32
+// (x as an FP32 pair), at most 14 steps from a checkpoint, writing the values' TF32 hi and lo
+// straight into the swizzled K-major operand:
+//   analysis  A = [128 degree rows of block (m, p)][32 nodes]: a thread per (node, 16-degree
+//             segment), 16 segments per tile, a warp's 32 lanes the 32 nodes of one row;
+//   synthesis A = [128 nodes][32 degree rows]: a thread per (node, segment), 4 segments per
+//             stage, each segment's 8 rows of the block's parity stored as two 16-byte chunks.
+// The FP32 recurrence over at most 14 steps from FP32-rounded checkpoints carries ~1e-7 rms
+// relative error (a few 1e-6 at worst near the turning degrees), the level of the FP32 table
+// it replaces.
 // Warp roles: 0 TMA producer, 1 MMA issuer, 2-9 split (eight warps, two per SM sub-partition:
 // the table tile alone is 16 KB per stage), 10-13 epilogue over a double-buffered accumulator
 // (a warp reads the TMEM lane quadrant warp % 4).  Every mbarrier wait
@@ -39,7 +56,6 @@ constexpr int kTK = 32;                          // K per stage (one 128-byte ro
 constexpr int kTTile = kBM * kTK * 4;            // 16 KB: 128 rows x 32 FP32
 constexpr int kT32MaxStages = 4;
 constexpr uint32_t kTf32Mask = 0xFFFFE000u;      // sign, exponent and 10 stored mantissa bits
-constexpr uint32_t kTf32Half = 0x00001000u;      // half a unit in the last TF32 place
 
 __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accum) {
@@ -59,10 +75,11 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 // v rounded to the nearest TF32 value (ties away from zero): add half a TF32 unit to the
 // magnitude bits, then clear the 13 low mantissa bits (a carry moves into the exponent, as it
 // should).  Finite inputs below the FP32 maximum only (the operands here are far below it).
+constexpr uint32_t kTf32Half = 0x00001000u;
 __device__ __forceinline__ float tf32_rn(float v) {
   return __uint_as_float((__float_as_uint(v) + kTf32Half) & kTf32Mask);
 }
-// hi/lo split of four values: hi = rn(v), lo = rn(v - hi)
+// hi = rn(v), lo = rn(v - hi)
 __device__ __forceinline__ void tf32_split4(const float (&v)[4], float4& h, float4& l) {
   h = make_float4(tf32_rn(v[0]), tf32_rn(v[1]), tf32_rn(v[2]), tf32_rn(v[3]));
   l = make_float4(tf32_rn(v[0] - h.x), tf32_rn(v[1] - h.y), tf32_rn(v[2] - h.z), tf32_rn(v[3] - h.w));
@@ -75,8 +92,9 @@ __device__ __forceinline__ uint32_t sw128_offset32(int row, int k) {
          (uint32_t)(k & 3) * 4u;
 }
 
-// Element-wise split of a tile (the swizzle does not matter): raw -> hi (in place), lo.
-// Each thread loads kSplitBatch chunks before it stores any, so the loads overlap.
+// Element-wise split of a tile (the swizzle does not matter): hi = rn(v) over the raw values,
+// lo = rn(v - hi) beside them.  Each thread loads kSplitBatch chunks before it stores any, so
+// the loads overlap.
 constexpr int kSplitBatch = 4;   // 16 KB / (256 threads x 16 B) = 4 chunks per thread
 __device__ __forceinline__ void split_inplace(uint8_t* raw, uint8_t* lo, int nbytes, int pt) {
   for (int base = 0; base < nbytes; base += kSplitBatch * kSplitThreads * 16) {
@@ -186,11 +204,58 @@ struct T32Args {
   int nmma_cap, ldi;
   float* Y;                   // synthesis output [blk][jh][ldc]
   int* err;
+  // recurrence mode
+  const long long* ck_off;    // first checkpoint row of order m
+  const float2* coef;         // (a_lm, b_lm) at m * cstride + (l - m), zero past l = lmax
+  int cstride;
+  const float2* xnode;        // node cosines x_jh as FP32 pairs (hi, lo)
+  int lmax;
 };
 
+// Recurrence mode: checkpoint segments of 16 degrees; per stage a checkpoint box and the
+// stage's coefficient slice arrive with the spectra / C^T tile.
+constexpr int kSeg = 16;
+constexpr int kAnaSegs = 2 * kBM / kSeg;             // 16 segments cover a 128-row tile of one parity
+constexpr int kSynSegs = 2 * kTK / kSeg;             // 4 segments cover a 32-row K chunk
+constexpr int kCkBytes = kAnaSegs * kTK * 8;         // analysis box: 16 segments x 32 nodes x (P0, P1)
+static_assert(kCkBytes == kSynSegs * kBM * 8, "both checkpoint boxes are 4 KB");
+constexpr int kCfAna = 2 * kBM;                      // coefficients per analysis stage (its tile's degrees)
+constexpr int kCfSyn = 2 * kTK;                      // coefficients per synthesis stage (its K chunk's degrees)
+constexpr int kCfBytes = kCfAna * 8;                 // room for either slice
+
+// Two 16-degree segments of the recurrence side by side (independent chains).  Segment h
+// starts from its checkpoint (P_{d0}, P_{d0+1}) and takes coefficients cf[cb_h + j] for its
+// degree d0 + j; the coefficients are zero past the order's last degree, so the values there
+// come out zero and no step needs a bounds test.  emit(h, k, value) receives the values of
+// parity par (k = 0 .. 7: degree d0 + 2k + par); the other parity only feeds the recurrence.
+template <class F>
+__device__ __forceinline__ void rec_two_segments(float2 ck0, float2 ck1, float xh, float xl, const float2* cf,
+                                                 int cb0, int cb1, int par, F&& emit) {
+  float a0 = ck0.x, b0 = ck0.y, a1 = ck1.x, b1 = ck1.y;
+  emit(0, 0, par ? b0 : a0);
+  emit(1, 0, par ? b1 : a1);
+#pragma unroll
+  for (int j = 2; j < kSeg; j += 2) {
+    // degrees d0 + j (even offset) and d0 + j + 1 (odd offset) of both chains
+    const float2 e0 = cf[cb0 + j], o0 = cf[cb0 + j + 1], e1 = cf[cb1 + j], o1 = cf[cb1 + j + 1];
+    const float c0 = e0.x * fmaf(-e0.y, a0, fmaf(xh, b0, xl * b0));
+    const float c1 = e1.x * fmaf(-e1.y, a1, fmaf(xh, b1, xl * b1));
+    const float d0v = o0.x * fmaf(-o0.y, b0, fmaf(xh, c0, xl * c0));
+    const float d1v = o1.x * fmaf(-o1.y, b1, fmaf(xh, c1, xl * c1));
+    emit(0, j >> 1, par ? d0v : c0);
+    emit(1, j >> 1, par ? d1v : c1);
+    a0 = c0;
+    b0 = d0v;
+    a1 = c1;
+    b1 = d1v;
+  }
+}
+
 // Persistent, warp-specialised TF32x3 Legendre GEMM (roles in the file header).  Stage s
-// holds [A hi (TMA'd raw, split in place)][A lo][B hi][B lo][X raw (analysis)].
-template <int kStages, bool ANA, bool BCAT>
+// holds [A hi][A lo][B hi][B lo][X raw (analysis)][checkpoint box (REC)]; A hi is the raw
+// table tile by TMA, or (REC) the values the split warps regenerate.  REC adds, after the
+// stages, the node cosines and two coefficient buffers (by tile parity).
+template <int kStages, bool ANA, bool BCAT, bool REC = false>
 __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_constant__ CUtensorMap ta,
                                                                   const __grid_constant__ CUtensorMap tb,
                                                                   T32Args a) {
@@ -199,12 +264,19 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
   uint8_t* base = align1k(smraw);
   const int nmma = a.nmma, nh = a.nh;
   const int bbytes = nmma * kTK * 4;   // one B tile (hi or lo); the analysis X tile has the same size
-  const int sbytes = 2 * kTTile + (ANA ? 3 : 2) * bbytes;
+  const int sbytes = 2 * kTTile + (ANA ? 3 : 2) * bbytes + (REC ? kCkBytes + kCfBytes : 0);
   auto sA_hi = [&](int s) { return base + s * sbytes; };
   auto sA_lo = [&](int s) { return base + s * sbytes + kTTile; };
   auto sB_hi = [&](int s) { return base + s * sbytes + 2 * kTTile; };
   auto sB_lo = [&](int s) { return base + s * sbytes + 2 * kTTile + bbytes; };
   auto sX = [&](int s) { return base + s * sbytes + 2 * kTTile + 2 * bbytes; };
+  auto sCk = [&](int s) {
+    return reinterpret_cast<const float2*>(base + s * sbytes + 2 * kTTile + (ANA ? 3 : 2) * bbytes);
+  };
+  auto sCf = [&](int s) {   // REC: the stage's coefficient slice
+    return reinterpret_cast<const float2*>(base + s * sbytes + 2 * kTTile + (ANA ? 3 : 2) * bbytes + kCkBytes);
+  };
+  float2* sXn = reinterpret_cast<float2*>(base + kStages * sbytes);   // REC: node cosines [nh]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // BCAT (2 nmma <= 256): B hi and B lo are adjacent in shared memory and form one operand
   // of N = 2 nmma, so A_hi [B_hi | B_lo] and A_lo B_hi are two MMAs per K step instead of
@@ -227,6 +299,8 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
     ctl.abort = 0;
     fence_mbar_init();
   }
+  if (REC)
+    for (int j = threadIdx.x; j < nh; j += blockDim.x) sXn[j] = a.xnode[j];
   if (warp == 1) tmem_alloc(&ctl.tmem, 2 * ncols_alloc);
   tc_fence_before();
   __syncthreads();
@@ -242,17 +316,32 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const Tile tl = a.tiles[t];
         const int nkb = nkb_of(tl.blk);
+        const long long ck_base = REC ? a.ck_off[tl.blk >> 1] : 0;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
           if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
-          mbar_arrive_expect_tx(&ctl.fullA[s], kTTile + bbytes);
-          if (ANA) {   // table rows i of the tile x nodes of this K-chunk; spectra rows = nodes
+          mbar_arrive_expect_tx(&ctl.fullA[s],
+                                (REC ? kCkBytes + (ANA ? kCfAna : kCfSyn) * 8 : kTTile) + bbytes);
+          if (REC) {   // checkpoint box of the stage (segments x nodes), FP32 pairs, and coefficients
+            const int m = tl.blk >> 1;
+            uint8_t* ck = reinterpret_cast<uint8_t*>(const_cast<float2*>(sCk(s)));
+            uint8_t* cf = reinterpret_cast<uint8_t*>(const_cast<float2*>(sCf(s)));
+            if (ANA) {   // 16 segments of the tile's degrees 2 r0 .. 2 r0 + 255 x the 32 nodes of this chunk
+              tma_load_2d(ck, &ta, &ctl.fullA[s], 2 * kb * kTK, (int)(ck_base + tl.r0 / 8));
+              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * tl.r0, kCfAna * 8, &ctl.fullA[s]);
+            } else {     // the 4 segments of this K chunk's degrees 64 kb .. 64 kb + 63 x the tile's 128 nodes
+              tma_load_2d(ck, &ta, &ctl.fullA[s], 2 * tl.r0, (int)(ck_base + kb * kSynSegs));
+              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * kb * kTK, kCfSyn * 8, &ctl.fullA[s]);
+            }
+          } else if (ANA) {   // table rows i of the tile x nodes of this K-chunk
             tma_load_2d(sA_hi(s), &ta, &ctl.fullA[s], kb * kTK, (int)(a.row_off[tl.blk] + tl.r0));
-            tma_load_2d(sX(s), &tb, &ctl.fullA[s], 0, tl.blk * nh + kb * kTK);
-          } else {     // transposed table: nodes of the tile x degrees of this K-chunk; C^T rows = columns
+          } else {     // transposed table: nodes of the tile x degrees of this K-chunk
             tma_load_2d(sA_hi(s), &ta, &ctl.fullA[s], kb * kTK, tl.blk * nh + tl.r0);
-            tma_load_2d(sB_hi(s), &tb, &ctl.fullA[s], kb * kTK, tl.blk * a.nmma_cap);
           }
+          if (ANA)     // spectra rows = nodes of this K chunk
+            tma_load_2d(sX(s), &tb, &ctl.fullA[s], 0, tl.blk * nh + kb * kTK);
+          else         // C^T rows = columns, degrees of this K chunk
+            tma_load_2d(sB_hi(s), &tb, &ctl.fullA[s], kb * kTK, tl.blk * a.nmma_cap);
         }
       }
       // let this CTA's copies land before it can exit
@@ -260,7 +349,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         mbar_drain(&ctl.fullA[k % kStages], (k / kStages) & 1);
     }
   } else if (warp == 1) {
-    if (lane == 0) {  // MMA issuer: every operand it reads was written by the split warps
+    if (lane == 0) {  // MMA issuer: waits until the split warps have written the stage's lo parts
       const uint32_t idesc = idesc_tf32(kBM, nmma), idesc2 = idesc_tf32(kBM, nacc);
       int it = 0, lt = 0;
       bool ok = true;
@@ -298,20 +387,74 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
       }
     }
   } else if (warp < 2 + kSplitWarps) {
-    // split warps: table tile in place -> hi, lo; analysis: X -> X^T hi/lo; synthesis: C^T in place
+    // split warps: table tile -> lo (the raw tile is hi); analysis: X -> X^T hi/lo; synthesis: C^T -> hi/lo in place
     const int pt = threadIdx.x - 64;
     const bool pre = ANA && nmma * (kTK / 4) <= kXtTasks * kSplitThreads;
     XtPlan xp;
     xp.init(pre ? nmma : 0, pt);
+    const int gw = pt >> 5;   // generator warp 0..7
     int it = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
       const Tile tl = a.tiles[t];
       const int nkb = nkb_of(tl.blk);
+      const int m = tl.blk >> 1, par = tl.blk & 1;
+      const int dmax = a.lmax - m;   // largest relative degree of order m
       for (int kb = 0; kb < nkb; ++kb, ++it) {
         const int s = it % kStages, n = it / kStages;
         if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
-        split_inplace(sA_hi(s), sA_lo(s), kTTile, pt);
+        if (REC && ANA) {
+          // lane = node of the K chunk; warp gw runs segments gw and gw + 8 of the tile (degrees
+          // 2 r0 + 16 sr ..); the degree of parity par, 2 r0 + 16 sr + 2 k + par, is tile row 8 sr + k
+          const int node = kb * kTK + lane;
+          const float2 xx = node < nh ? sXn[node] : make_float2(0.f, 0.f);
+          const int d00 = 2 * tl.r0 + kSeg * gw, d01 = d00 + kSeg * 8;
+          const float2 z = make_float2(0.f, 0.f);
+          const float2 c0 = d00 <= dmax ? sCk(s)[gw * kTK + lane] : z;
+          const float2 c1 = d01 <= dmax ? sCk(s)[(gw + 8) * kTK + lane] : z;
+          uint8_t* ah = sA_hi(s);
+          uint8_t* al = sA_lo(s);
+          rec_two_segments(c0, c1, xx.x, xx.y, sCf(s), kSeg * gw, kSeg * (gw + 8), par,
+                           [&](int h, int k, float v) {
+                             const uint32_t o = sw128_offset32(kSeg / 2 * (gw + 8 * h) + k, lane);
+                             const float hv = tf32_rn(v);
+                             *reinterpret_cast<float*>(ah + o) = hv;
+                             *reinterpret_cast<float*>(al + o) = tf32_rn(v - hv);
+                           });
+        } else if (REC) {
+          // node tl.r0 + 32 (gw & 3) + lane (tile row); segments (gw >> 2) + {0, 2} of the K chunk
+          // (degrees 64 kb + 16 sr ..): the 8 degrees of parity par of a segment are K positions
+          // 8 sr .. 8 sr + 7, stored as two 16-byte chunks (zero past the order's last degree)
+          const int row = 32 * (gw & 3) + lane;
+          const int node = tl.r0 + row;
+          const float2 xx = node < nh ? sXn[node] : make_float2(0.f, 0.f);
+          const int s0 = gw >> 2, s1 = s0 + 2;
+          const int d00 = 2 * kb * kTK + kSeg * s0, d01 = 2 * kb * kTK + kSeg * s1;
+          const float2 z = make_float2(0.f, 0.f);
+          const float2 c0 = d00 <= dmax ? sCk(s)[s0 * kBM + row] : z;
+          const float2 c1 = d01 <= dmax ? sCk(s)[s1 * kBM + row] : z;
+          float v[2][8];
+          rec_two_segments(c0, c1, xx.x, xx.y, sCf(s), kSeg * s0, kSeg * s1, par,
+                           [&](int h, int k, float val) { v[h][k] = val; });
+          uint8_t* ah = sA_hi(s);
+          uint8_t* al = sA_lo(s);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int sr = h ? s1 : s0;
+            const float w0[4] = {v[h][0], v[h][1], v[h][2], v[h][3]};
+            const float w1[4] = {v[h][4], v[h][5], v[h][6], v[h][7]};
+            const uint32_t o0 = sw128_offset32(row, 8 * sr), o1 = sw128_offset32(row, 8 * sr + 4);
+            float4 h0, l0, h1, l1;
+            tf32_split4(w0, h0, l0);
+            tf32_split4(w1, h1, l1);
+            *reinterpret_cast<float4*>(ah + o0) = h0;
+            *reinterpret_cast<float4*>(ah + o1) = h1;
+            *reinterpret_cast<float4*>(al + o0) = l0;
+            *reinterpret_cast<float4*>(al + o1) = l1;
+          }
+        } else {
+          split_inplace(sA_hi(s), sA_lo(s), kTTile, pt);
+        }
         if (ANA && pre)
           xp.run(reinterpret_cast<const float*>(sX(s)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s));
         else if (ANA)
@@ -409,64 +552,198 @@ __global__ void k_c_to_ct32(const int* __restrict__ Mrows, const long long* __re
   }
 }
 
-size_t tf32_smem_bytes(int nmma, bool ana, int stages) {
-  return 1024 + (size_t)stages * (2 * kTTile + (ana ? 3 : 2) * (size_t)nmma * kTK * 4);
+// Recurrence mode, grid set-up: checkpoints Pbar_{m+16s, m}, Pbar_{m+16s+1, m} at every node of
+// the north hemisphere by the FP64 recurrences of App. B (k_pbar's), rounded to FP32, at
+// ck[(ck_off[m] + s) * ckld + 2 jh + {0, 1}] (nodes past nh stay zero), and x_jh as FP32 pairs.
+__global__ void k_ck_build(int lmax, int nh, const double* __restrict__ x, const long long* __restrict__ ck_off,
+                           int ckld, float* __restrict__ ck, float2* __restrict__ xnode) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (j >= nh) return;
+  const double xj = x[j];
+  if (m == 0) {
+    const float h = (float)xj;
+    xnode[j] = make_float2(h, (float)(xj - (double)h));
+  }
+  const double st = sqrt((1.0 - xj) * (1.0 + xj));
+  double pmm = 0.28209479177387814;   // 1/sqrt(4 pi)
+  for (int k = 1; k <= m; ++k) pmm *= -sqrt((2.0 * k + 1.0) / (2.0 * k)) * st;
+  float* row = ck + (size_t)ck_off[m] * ckld + 2 * j;
+  double p2 = pmm, p1 = (m < lmax) ? sqrt(2.0 * m + 3.0) * xj * pmm : 0.0;   // degrees m, m + 1
+  for (int l = m; l <= lmax; ++l) {
+    const int d = l - m;
+    if (d % kSeg == 0) {   // checkpoint s = d / 16: (Pbar_l, Pbar_{l+1})
+      float* c = row + (size_t)(d / kSeg) * ckld;
+      c[0] = (float)p2;
+      c[1] = (float)p1;
+    }
+    const int ln = l + 2;   // advance (p2, p1) from degrees (l, l + 1) to (l + 1, l + 2)
+    double pn = 0.0;
+    if (ln <= lmax) {
+      const double ll = (double)ln * ln, mm = (double)m * m, l1 = (double)(ln - 1) * (ln - 1);
+      pn = sqrt((4.0 * ll - 1.0) / (ll - mm)) * (xj * p1 - sqrt((l1 - mm) / (4.0 * l1 - 1.0)) * p2);
+    }
+    p2 = p1;
+    p1 = pn;
+  }
+}
+
+// (a_lm, b_lm) of App. B in FP32 at m * cstride + (l - m) for m + 2 <= l <= lmax; the rest of
+// the row stays zero (the buffer is cleared first), so that the recurrence run past lmax
+// gives zeros
+__global__ void k_coef32_build(int lmax, int cstride, float2* __restrict__ coef) {
+  const int m = blockIdx.x;
+  for (int l = m + 2 + threadIdx.x; l <= lmax; l += blockDim.x) {
+    const double ll = (double)l * l, mm = (double)m * m, l1 = (double)(l - 1) * (l - 1);
+    coef[(size_t)m * cstride + (l - m)] =
+        make_float2((float)sqrt((4.0 * ll - 1.0) / (ll - mm)), (float)sqrt((l1 - mm) / (4.0 * l1 - 1.0)));
+  }
+}
+
+size_t tf32_smem_bytes(int nmma, bool ana, int stages, bool rec, int nh) {
+  size_t b = 1024 + (size_t)stages * (2 * kTTile + (ana ? 3 : 2) * (size_t)nmma * kTK * 4 +
+                                      (rec ? kCkBytes + kCfBytes : 0));
+  if (rec) b += (size_t)((nh + 1) & ~1) * 8;
+  return b;
+}
+
+template <bool REC>
+void* tf32_kernel(bool ana, bool bc, int stages) {
+#define SHOT_T32K(S, A, B) reinterpret_cast<void*>(k_legendre_tf32<S, A, B, REC>)
+  if (bc) {
+    if (ana) return stages == 4 ? SHOT_T32K(4, true, true) : stages == 3 ? SHOT_T32K(3, true, true)
+                  : stages == 2 ? SHOT_T32K(2, true, true) : SHOT_T32K(1, true, true);
+    return stages == 4 ? SHOT_T32K(4, false, true) : stages == 3 ? SHOT_T32K(3, false, true)
+         : stages == 2 ? SHOT_T32K(2, false, true) : SHOT_T32K(1, false, true);
+  }
+  if (ana) return stages == 4 ? SHOT_T32K(4, true, false) : stages == 3 ? SHOT_T32K(3, true, false)
+                : stages == 2 ? SHOT_T32K(2, true, false) : SHOT_T32K(1, true, false);
+  return stages == 4 ? SHOT_T32K(4, false, false) : stages == 3 ? SHOT_T32K(3, false, false)
+       : stages == 2 ? SHOT_T32K(2, false, false) : SHOT_T32K(1, false, false);
+#undef SHOT_T32K
 }
 
 }  // namespace
 
 int tf32_nmma(int nf) { return (2 * nf + 15) / 16 * 16; }
 
+int build_tf32_recurrence(Grid& g, cudaStream_t st) {
+  const int L = g.lmax + 1, nh = g.nh;
+  std::vector<long long> ckoff(L + 1, 0);
+  for (int m = 0; m < L; ++m) ckoff[m + 1] = ckoff[m] + (L - m + kSeg - 1) / kSeg;
+  g.ck_ld = 2 * ((nh + 3) / 4 * 4);   // floats per checkpoint row (16-byte multiple)
+  g.ck_rows = ckoff[L];
+  // coefficient rows: every stage's slice (up to 2 r0 + 256 <= lmax + 256 degrees) stays in its row
+  g.cstride = (L + 255) / 256 * 256 + 256;
+  SHOT_CUDA(cudaMalloc(&g.ck_off_d, (L + 1) * sizeof(long long)));
+  SHOT_CUDA(cudaMemcpyAsync(g.ck_off_d, ckoff.data(), (L + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
+  g.ck_off = ckoff;
+  SHOT_CUDA(cudaMalloc(&g.rec_coef, (size_t)L * g.cstride * sizeof(float2)));
+  SHOT_CUDA(cudaMemsetAsync(g.rec_coef, 0, (size_t)L * g.cstride * sizeof(float2), st));
+  SHOT_CUDA(cudaMalloc(&g.rec_x, (size_t)nh * sizeof(float2)));
+  SHOT_CUDA(cudaMalloc(&g.ck, (size_t)g.ck_rows * g.ck_ld * sizeof(float)));
+  SHOT_CUDA(cudaMemsetAsync(g.ck, 0, (size_t)g.ck_rows * g.ck_ld * sizeof(float), st));
+  count_launch(2);
+  k_coef32_build<<<L, 256, 0, st>>>(g.lmax, g.cstride, reinterpret_cast<float2*>(g.rec_coef));
+  k_ck_build<<<dim3((nh + 127) / 128, L), 128, 0, st>>>(g.lmax, nh, g.x_d, g.ck_off_d, g.ck_ld, g.ck,
+                                                        reinterpret_cast<float2*>(g.rec_x));
+  SHOT_CUDA(cudaGetLastError());
+  SHOT_CUDA(cudaStreamSynchronize(st));   // ckoff is a local
+  return SHOT_OK;
+}
+
 int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float* Y, int ldc, bool ana, bool syn,
                          bool apply_h, cudaStream_t st) {
   const Workspace& w = g.ws;
   const int nmma = tf32_nmma(nf);
-  if (nmma > 256 || nmma > w.nmma_cap || !w.ct32 || !g.tab || !g.tabT) {
+  const bool rec = g.mode == SHOT_RECURRENCE;
+  if (nmma > 256 || nmma > w.nmma_cap || !w.ct32 || (rec ? !g.ck : (!g.tab || !g.tabT))) {
     set_error("TF32X3 path supports at most 128 fields per call");
     return SHOT_ERR_UNSUPPORTED;
   }
   int rc;
   // deepest pipeline (<= 4 stages) whose tiles fit in one CTA's shared memory, with 2 KB
   // left for the static control block
+  auto bytes = [&](bool a_, int s) { return tf32_smem_bytes(nmma, a_, s, rec, g.nh); };
   auto pick = [&](bool a_) {
     int s = kT32MaxStages;
-    while (s > 1 && tf32_smem_bytes(nmma, a_, s) + 2048 > 227 * 1024) --s;
+    while (s > 1 && bytes(a_, s) + 2048 > 227 * 1024) --s;
     return s;
   };
   auto launch = [&](bool a_, const CUtensorMap& ma, const CUtensorMap& mb, const T32Args& args, int ntiles) -> int {
     const int stages = pick(a_);
-    const size_t smem = tf32_smem_bytes(nmma, a_, stages);
+    const size_t smem = bytes(a_, stages);
+    if (smem + 2048 > 227 * 1024) {
+      set_error("TF32X3: the grid's recurrence buffers do not fit in shared memory");
+      return SHOT_ERR_UNSUPPORTED;
+    }
     const bool bc = 2 * nmma <= 256;
-    auto kern = bc ? (a_ ? (stages == 4 ? k_legendre_tf32<4, true, true> : stages == 3 ? k_legendre_tf32<3, true, true>
-                            : stages == 2 ? k_legendre_tf32<2, true, true> : k_legendre_tf32<1, true, true>)
-                         : (stages == 4 ? k_legendre_tf32<4, false, true> : stages == 3 ? k_legendre_tf32<3, false, true>
-                            : stages == 2 ? k_legendre_tf32<2, false, true> : k_legendre_tf32<1, false, true>))
-                   : (a_ ? (stages == 4 ? k_legendre_tf32<4, true, false> : stages == 3 ? k_legendre_tf32<3, true, false>
-                            : stages == 2 ? k_legendre_tf32<2, true, false> : k_legendre_tf32<1, true, false>)
-                         : (stages == 4 ? k_legendre_tf32<4, false, false> : stages == 3 ? k_legendre_tf32<3, false, false>
-                            : stages == 2 ? k_legendre_tf32<2, false, false> : k_legendre_tf32<1, false, false>));
+    void* kern = rec ? tf32_kernel<true>(a_, bc, stages) : tf32_kernel<false>(a_, bc, stages);
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = ntiles < g.num_sms ? ntiles : g.num_sms;
     ProfScope prof(a_ ? PK_ANALYSIS : PK_SYNTHESIS, st);
     count_launch();
-    kern<<<grid, kT32Threads, smem, st>>>(ma, mb, args);
-    SHOT_CUDA(cudaGetLastError());
+    void* params[] = {const_cast<CUtensorMap*>(&ma), const_cast<CUtensorMap*>(&mb), const_cast<T32Args*>(&args)};
+    SHOT_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(kT32Threads), params, smem, st));
     return SHOT_OK;
   };
+  T32Args rx{};
+  CUtensorMap mck_a, mck_s;
+  if (rec) {
+    rx.ck_off = g.ck_off_d;
+    rx.coef = reinterpret_cast<const float2*>(g.rec_coef);
+    rx.cstride = g.cstride;
+    rx.xnode = reinterpret_cast<const float2*>(g.rec_x);
+    rx.lmax = g.lmax;
+    // checkpoint rows (segments) of ck_ld floats: boxes of 16 segments x 32 nodes (analysis)
+    // and 4 segments x 128 nodes (synthesis)
+    if ((rc = make_map_f32(&mck_a, g.ck, g.ck_ld, (uint64_t)g.ck_rows, g.ck_ld, 2 * kTK, kAnaSegs))) return rc;
+    if ((rc = make_map_f32(&mck_s, g.ck, g.ck_ld, (uint64_t)g.ck_rows, g.ck_ld, 2 * kBM, kSynSegs))) return rc;
+  }
   if (ana) {
     CUtensorMap ma, mx;
-    if ((rc = make_map_f32(&ma, g.tab, g.nh, g.rows_total, g.ldt, kTK, kBM, true))) return rc;
+    if (rec) ma = mck_a;
+    else if ((rc = make_map_f32(&ma, g.tab, g.nh, g.rows_total, g.ldt, kTK, kBM, true))) return rc;
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kTK))) return rc;
-    const T32Args args{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma,
-                       apply_h ? g.h_d : nullptr, w.ct32, Cf, w.nmma_cap, g.ldi, nullptr, w.dev_int + 4};
+    T32Args args = rx;
+    args.tiles = g.tiles_ana;
+    args.ntiles = g.ntiles_ana;
+    args.M = g.M_d;
+    args.row_off = g.row_off_d;
+    args.nh = g.nh;
+    args.ldc = ldc;
+    args.ncols = 2 * nf;
+    args.nmma = nmma;
+    args.h = apply_h ? g.h_d : nullptr;
+    args.ct = w.ct32;
+    args.cf = Cf;
+    args.nmma_cap = w.nmma_cap;
+    args.ldi = g.ldi;
+    args.Y = nullptr;
+    args.err = w.dev_int + 4;
     if ((rc = launch(true, ma, mx, args, g.ntiles_ana))) return rc;
   }
   if (syn) {
     CUtensorMap ma, mb;
-    if ((rc = make_map_f32(&ma, g.tabT, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kTK, kBM, true))) return rc;
+    if (rec) ma = mck_s;
+    else if ((rc = make_map_f32(&ma, g.tabT, g.ldi, (uint64_t)g.nblk * g.nh, g.ldi, kTK, kBM, true))) return rc;
     if ((rc = make_map_f32(&mb, w.ct32, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, kTK, nmma, true))) return rc;
-    const T32Args args{g.tiles_syn, g.ntiles_syn, g.M_d, g.row_off_d, g.nh, ldc, 2 * nf, nmma,
-                       nullptr, nullptr, nullptr, w.nmma_cap, g.ldi, Y, w.dev_int + 4};
+    T32Args args = rx;
+    args.tiles = g.tiles_syn;
+    args.ntiles = g.ntiles_syn;
+    args.M = g.M_d;
+    args.row_off = g.row_off_d;
+    args.nh = g.nh;
+    args.ldc = ldc;
+    args.ncols = 2 * nf;
+    args.nmma = nmma;
+    args.h = nullptr;
+    args.ct = nullptr;
+    args.cf = nullptr;
+    args.nmma_cap = w.nmma_cap;
+    args.ldi = g.ldi;
+    args.Y = Y;
+    args.err = w.dev_int + 4;
     if ((rc = launch(false, ma, mb, args, g.ntiles_syn))) return rc;
   }
   return SHOT_OK;

@@ -153,6 +153,15 @@ struct Grid {
   void* rec_coef = nullptr;
   long long* rec_coef_off = nullptr;
   float* rec_x = nullptr;
+  // SHOT_RECURRENCE on TF32X3 grids: FP32 checkpoints (Pbar at degrees m + 16 s, m + 16 s + 1)
+  // [ck_off[m] + s][ck_ld floats: 2 per node], recurrence coefficients (a, b) as FP32 pairs in
+  // rec_coef, node cosines as FP32 pairs in rec_x
+  float* ck = nullptr;
+  long long* ck_off_d = nullptr;
+  std::vector<long long> ck_off;
+  long long ck_rows = 0;
+  int ck_ld = 0;
+  int cstride = 0;              // TF32X3 recurrence: coefficient row stride ((a, b) pairs per order)
   int* M_d = nullptr;
   long long* row_off_d = nullptr;
   Tile* tiles_ana = nullptr;
@@ -259,6 +268,7 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
                          bool apply_h, cudaStream_t st);
 int launch_c_to_ct32(const Grid& g, int nf, const float* C, int ldc, cudaStream_t st);
 int build_recurrence(Grid& g, cudaStream_t st);
+int build_tf32_recurrence(Grid& g, cudaStream_t st);
 int launch_legendre_rec(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, bool ana, bool syn,
                         bool apply_h, cudaStream_t st);
 int tc_nmma(int nf);

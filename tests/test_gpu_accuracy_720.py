@@ -33,8 +33,12 @@ from paper_2605_18389_gb300 import shot  # noqa: E402
 
 NLAT, T_HEAT, T_ITERS, SEED = 720, 1e-4, 20, 5000
 EPS = 4.0 * T_HEAT
-TOL = {"fp32": 1e-5, "tf32x3": 1e-4, "bf16x3": 1e-4}
-PREC = {"fp32": shot.SHOT_FP32, "tf32x3": shot.SHOT_TF32X3, "bf16x3": shot.SHOT_BF16X3}
+TOL = {"fp32": 1e-5, "tf32x3": 1e-4, "bf16x3": 1e-4, "tf32x3_rec": 1e-4}
+PREC = {"fp32": (shot.SHOT_FP32, shot.SHOT_TABLE), "tf32x3": (shot.SHOT_TF32X3, shot.SHOT_TABLE),
+        "bf16x3": (shot.SHOT_BF16X3, shot.SHOT_TABLE),
+        # TF32x3 contractions on P regenerated from checkpoints (recurrence mode, no table)
+        "tf32x3_rec": (shot.SHOT_TF32X3, shot.SHOT_RECURRENCE)}
+ALL = ["fp32", "tf32x3", "tf32x3_rec", "bf16x3"]
 BF16_MISS = pytest.mark.xfail(strict=True, reason="bf16 hi/lo operands: ~2^-17 per table entry; the element-wise "
                                                   "scalings miss 1e-4 at 720 (measured 3.2e-4)")
 
@@ -54,7 +58,7 @@ def ref720():
 def _gpu(ref720, prec):
     """One shot_divergence solve per precision (cached for the module's tests)."""
     if prec not in ref720["gpu"]:
-        g = shot.shot_grid_init(NLAT, 2 * NLAT, -1, PREC[prec])
+        g = shot.shot_grid_init(NLAT, 2 * NLAT, -1, *PREC[prec])
         try:
             pt = torch.from_numpy(ref720["p32"]).cuda()
             qt = torch.from_numpy(ref720["q32"]).cuda()
@@ -70,7 +74,7 @@ def _gpu(ref720, prec):
     return ref720["gpu"][prec]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ALL)
 def test_potentials_and_marginals_match_oracle_at_720(ref720, prec):
     r, ref, og = _gpu(ref720, prec), ref720["ref"], ref720["og"]
     runs = ref["runs"]
@@ -85,7 +89,7 @@ def test_potentials_and_marginals_match_oracle_at_720(ref720, prec):
     np.testing.assert_allclose(r["ot3"], runs["ot"], rtol=tol)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", pytest.param("bf16x3", marks=BF16_MISS)])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "tf32x3_rec", pytest.param("bf16x3", marks=BF16_MISS)])
 def test_scalings_elementwise_match_oracle_at_720(ref720, prec):
     r, runs = _gpu(ref720, prec), ref720["ref"]["runs"]
     for name in ("u", "v"):
@@ -93,7 +97,7 @@ def test_scalings_elementwise_match_oracle_at_720(ref720, prec):
         assert e <= TOL[prec], f"{prec}: {name} element-wise {e:.3e} > {TOL[prec]:g}"
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ALL)
 def test_divergence_matches_oracle_at_720(ref720, prec):
     r, ref = _gpu(ref720, prec), ref720["ref"]
     ot_pq = ref["runs"]["ot"][:1]
