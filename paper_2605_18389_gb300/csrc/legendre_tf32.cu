@@ -25,21 +25,22 @@
 //                                                                  the analysis epilogue)
 // kind::tf32 is used with K-major operands only, hence the transposed table copy.
 //
-// Recurrence mode (SHOT_RECURRENCE, O(n) memory): no table.  The grid keeps checkpoints,
-// Pbar at the degree pairs (m + 16 s, m + 16 s + 1) of every order m and north-hemisphere node
-// (FP64 recurrence of App. B, rounded to FP32; about a sixteenth of the table), and the
-// recurrence coefficients a_lm, b_lm in FP32.  A stage's checkpoint box comes by TMA with the
+// Recurrence mode (SHOT_RECURRENCE, O(n) memory): no table.  The grid keeps checkpoints, for
+// each parity par, Pbar at the degrees (m + 16 s + par, m + 16 s + par + 2) of every order m and
+// north-hemisphere node (FP64 recurrence of App. B, rounded to FP32; about an eighth of the
+// table), and the same-parity two-step form of App. B's recurrence,
+// P_{l+2} = (A x^2 + B) P_l + C P_{l-2}, as FP32 coefficients (A, B, C) per degree.  A stage's
+// checkpoint box (of its parity) comes by TMA and its coefficient slice by a bulk copy with the
 // spectra (analysis) or C^T (synthesis) tile, and the split warps regenerate the stage's A tile
-// by the three-term recurrence Pbar_lm = a_lm (x Pbar_{l-1,m} - b_lm Pbar_{l-2,m}) in FP32
-// (x as an FP32 pair), at most 14 steps from a checkpoint, writing the values' TF32 hi and lo
+// in FP32, at most 6 two-degree steps from a checkpoint, writing the values' TF32 hi and lo
 // straight into the swizzled K-major operand:
-//   analysis  A = [128 degree rows of block (m, p)][32 nodes]: a thread per (node, 16-degree
-//             segment), 16 segments per tile, a warp's 32 lanes the 32 nodes of one row;
+//   analysis  A = [128 degree rows of block (m, p)][32 nodes]: a thread per (node pair, 16-degree
+//             segment), 16 segments per tile, a half-warp's 16 lanes the 32 nodes of one row;
 //   synthesis A = [128 nodes][32 degree rows]: a thread per (node, segment), 4 segments per
 //             stage, each segment's 8 rows of the block's parity stored as two 16-byte chunks.
-// The FP32 recurrence over at most 14 steps from FP32-rounded checkpoints carries ~1e-7 rms
-// relative error (a few 1e-6 at worst near the turning degrees), the level of the FP32 table
-// it replaces.
+// The FP32 two-step recurrence over at most 6 steps from FP32-rounded checkpoints carries
+// ~1e-7 rms error relative to each order's largest value (6e-6 at worst near the turning
+// degrees), the level of the FP32 table it replaces.
 // Warp roles: 0 TMA producer, 1 MMA issuer, 2-9 split (eight warps, two per SM sub-partition:
 // the table tile alone is 16 KB per stage), 10-13 epilogue over a double-buffered accumulator
 // (a warp reads the TMEM lane quadrant warp % 4).  Every mbarrier wait
@@ -205,10 +206,12 @@ struct T32Args {
   float* Y;                   // synthesis output [blk][jh][ldc]
   int* err;
   // recurrence mode
-  const long long* ck_off;    // first checkpoint row of order m
-  const float2* coef;         // (a_lm, b_lm) at m * cstride + (l - m), zero past l = lmax
+  const long long* ck_off;    // first checkpoint row of order m (in either parity plane)
+  long long ck_rows;          // rows per parity plane
+  const float4* coef;         // two-step coefficients (A, B, C, 0) of degree l at m * cstride + (l - m),
+                              // zero past l = lmax
   int cstride;
-  const float2* xnode;        // node cosines x_jh as FP32 pairs (hi, lo)
+  const float* xnode;         // x_jh^2 in FP32
   int lmax;
 };
 
@@ -217,37 +220,62 @@ struct T32Args {
 constexpr int kSeg = 16;
 constexpr int kAnaSegs = 2 * kBM / kSeg;             // 16 segments cover a 128-row tile of one parity
 constexpr int kSynSegs = 2 * kTK / kSeg;             // 4 segments cover a 32-row K chunk
-constexpr int kCkBytes = kAnaSegs * kTK * 8;         // analysis box: 16 segments x 32 nodes x (P0, P1)
+constexpr int kCkBytes = kAnaSegs * kTK * 8;         // analysis box: 16 segments x 32 nodes x 2 values
 static_assert(kCkBytes == kSynSegs * kBM * 8, "both checkpoint boxes are 4 KB");
 constexpr int kCfAna = 2 * kBM;                      // coefficients per analysis stage (its tile's degrees)
 constexpr int kCfSyn = 2 * kTK;                      // coefficients per synthesis stage (its K chunk's degrees)
-constexpr int kCfBytes = kCfAna * 8;                 // room for either slice
+constexpr int kCfBytes = kCfAna * 16;                // room for either slice
 
-// Two 16-degree segments of the recurrence side by side (independent chains).  Segment h
-// starts from its checkpoint (P_{d0}, P_{d0+1}) and takes coefficients cf[cb_h + j] for its
-// degree d0 + j; the coefficients are zero past the order's last degree, so the values there
-// come out zero and no step needs a bounds test.  emit(h, k, value) receives the values of
-// parity par (k = 0 .. 7: degree d0 + 2k + par); the other parity only feeds the recurrence.
+// Two 16-degree segments of the recurrence side by side (independent chains), both of the
+// parity par: chain h starts from its checkpoint (P_{d0+par}, P_{d0+par+2}) and steps two
+// degrees at a time by the same-parity form of App. B's recurrence,
+//   P_{l+2} = (A x^2 + B) P_l + C P_{l-2},
+//   A = a_{l+2} a_{l+1},  B = -a_{l+2} (a_{l+1} b_{l+1} / a_l + b_{l+2}),  C = -a_{l+2} a_{l+1} b_{l+1} b_l
+// (eliminate P_{l+1} and P_{l-1} from three consecutive steps), with (A, B, C) of the new degree
+// at cf[cb_h + (its degree - d0)].  The coefficients are zero past the order's last degree, so
+// the values there come out zero and no step needs a bounds test.  emit(h, k, value) receives
+// P_{d0 + par + 2k}, k = 0 .. 7.
 template <class F>
-__device__ __forceinline__ void rec_two_segments(float2 ck0, float2 ck1, float xh, float xl, const float2* cf,
-                                                 int cb0, int cb1, int par, F&& emit) {
+__device__ __forceinline__ void rec_two_segments(float2 ck0, float2 ck1, float x2, const float4* cf, int cb0,
+                                                 int cb1, int par, F&& emit) {
   float a0 = ck0.x, b0 = ck0.y, a1 = ck1.x, b1 = ck1.y;
-  emit(0, 0, par ? b0 : a0);
-  emit(1, 0, par ? b1 : a1);
+  emit(0, 0, a0);
+  emit(1, 0, a1);
+  emit(0, 1, b0);
+  emit(1, 1, b1);
 #pragma unroll
-  for (int j = 2; j < kSeg; j += 2) {
-    // degrees d0 + j (even offset) and d0 + j + 1 (odd offset) of both chains
-    const float2 e0 = cf[cb0 + j], o0 = cf[cb0 + j + 1], e1 = cf[cb1 + j], o1 = cf[cb1 + j + 1];
-    const float c0 = e0.x * fmaf(-e0.y, a0, fmaf(xh, b0, xl * b0));
-    const float c1 = e1.x * fmaf(-e1.y, a1, fmaf(xh, b1, xl * b1));
-    const float d0v = o0.x * fmaf(-o0.y, b0, fmaf(xh, c0, xl * c0));
-    const float d1v = o1.x * fmaf(-o1.y, b1, fmaf(xh, c1, xl * c1));
-    emit(0, j >> 1, par ? d0v : c0);
-    emit(1, j >> 1, par ? d1v : c1);
-    a0 = c0;
-    b0 = d0v;
-    a1 = c1;
-    b1 = d1v;
+  for (int k = 2; k < kSeg / 2; ++k) {
+    const float4 e0 = cf[cb0 + par + 2 * k], e1 = cf[cb1 + par + 2 * k];
+    const float c0 = fmaf(fmaf(e0.x, x2, e0.y), b0, e0.z * a0);
+    const float c1 = fmaf(fmaf(e1.x, x2, e1.y), b1, e1.z * a1);
+    emit(0, k, c0);
+    emit(1, k, c1);
+    a0 = b0;
+    b0 = c0;
+    a1 = b1;
+    b1 = c1;
+  }
+}
+
+// One 16-degree segment at two nodes side by side (same coefficients, independent chains):
+// ck = (P_{d0+par}, P_{d0+par+2}) at node 0, then at node 1; x2 = (x0^2, x1^2); cf[cb + 2k] holds
+// (A, B, C) of degree d0 + par + 2k (cb = d0 + par relative to the slice).  emit(k, v0, v1)
+// receives P_{d0 + par + 2k} at both nodes, k = 0 .. 7.
+template <class F>
+__device__ __forceinline__ void rec_node_pair(float4 ck, float2 x2, const float4* cf, int cb, F&& emit) {
+  float a0 = ck.x, b0 = ck.y, a1 = ck.z, b1 = ck.w;
+  emit(0, a0, a1);
+  emit(1, b0, b1);
+#pragma unroll
+  for (int k = 2; k < kSeg / 2; ++k) {
+    const float4 e = cf[cb + 2 * k];
+    const float c0 = fmaf(fmaf(e.x, x2.x, e.y), b0, e.z * a0);
+    const float c1 = fmaf(fmaf(e.x, x2.y, e.y), b1, e.z * a1);
+    emit(k, c0, c1);
+    a0 = b0;
+    b0 = c0;
+    a1 = b1;
+    b1 = c1;
   }
 }
 
@@ -274,9 +302,9 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
     return reinterpret_cast<const float2*>(base + s * sbytes + 2 * kTTile + (ANA ? 3 : 2) * bbytes);
   };
   auto sCf = [&](int s) {   // REC: the stage's coefficient slice
-    return reinterpret_cast<const float2*>(base + s * sbytes + 2 * kTTile + (ANA ? 3 : 2) * bbytes + kCkBytes);
+    return reinterpret_cast<const float4*>(base + s * sbytes + 2 * kTTile + (ANA ? 3 : 2) * bbytes + kCkBytes);
   };
-  float2* sXn = reinterpret_cast<float2*>(base + kStages * sbytes);   // REC: node cosines [nh]
+  float* sXn = reinterpret_cast<float*>(base + kStages * sbytes);   // REC: x^2 of the nodes [nh]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // BCAT (2 nmma <= 256): B hi and B lo are adjacent in shared memory and form one operand
   // of N = 2 nmma, so A_hi [B_hi | B_lo] and A_lo B_hi are two MMAs per K step instead of
@@ -316,22 +344,24 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const Tile tl = a.tiles[t];
         const int nkb = nkb_of(tl.blk);
-        const long long ck_base = REC ? a.ck_off[tl.blk >> 1] : 0;
+        // checkpoint rows of order m in the plane of the tile's parity (planes of ck_rows rows)
+        const long long ck_base = REC ? (tl.blk & 1) * a.ck_rows + a.ck_off[tl.blk >> 1] : 0;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
           if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
           mbar_arrive_expect_tx(&ctl.fullA[s],
-                                (REC ? kCkBytes + (ANA ? kCfAna : kCfSyn) * 8 : kTTile) + bbytes);
+                                (REC ? kCkBytes + (ANA ? kCfAna : kCfSyn) * 16 : kTTile) + bbytes);
           if (REC) {   // checkpoint box of the stage (segments x nodes), FP32 pairs, and coefficients
             const int m = tl.blk >> 1;
             uint8_t* ck = reinterpret_cast<uint8_t*>(const_cast<float2*>(sCk(s)));
-            uint8_t* cf = reinterpret_cast<uint8_t*>(const_cast<float2*>(sCf(s)));
+            uint8_t* cf = reinterpret_cast<uint8_t*>(const_cast<float4*>(sCf(s)));
+            // checkpoint plane of the tile's parity: rows ck_base (see the producer's tile set-up)
             if (ANA) {   // 16 segments of the tile's degrees 2 r0 .. 2 r0 + 255 x the 32 nodes of this chunk
               tma_load_2d(ck, &ta, &ctl.fullA[s], 2 * kb * kTK, (int)(ck_base + tl.r0 / 8));
-              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * tl.r0, kCfAna * 8, &ctl.fullA[s]);
+              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * tl.r0, kCfAna * 16, &ctl.fullA[s]);
             } else {     // the 4 segments of this K chunk's degrees 64 kb .. 64 kb + 63 x the tile's 128 nodes
               tma_load_2d(ck, &ta, &ctl.fullA[s], 2 * tl.r0, (int)(ck_base + kb * kSynSegs));
-              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * kb * kTK, kCfSyn * 8, &ctl.fullA[s]);
+              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * kb * kTK, kCfSyn * 16, &ctl.fullA[s]);
             }
           } else if (ANA) {   // table rows i of the tile x nodes of this K-chunk
             tma_load_2d(sA_hi(s), &ta, &ctl.fullA[s], kb * kTK, (int)(a.row_off[tl.blk] + tl.r0));
@@ -404,37 +434,37 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         const int s = it % kStages, n = it / kStages;
         if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
         if (REC && ANA) {
-          // lane = node of the K chunk; warp gw runs segments gw and gw + 8 of the tile (degrees
-          // 2 r0 + 16 sr ..); the degree of parity par, 2 r0 + 16 sr + 2 k + par, is tile row 8 sr + k
-          const int node = kb * kTK + lane;
-          const float2 xx = node < nh ? sXn[node] : make_float2(0.f, 0.f);
-          const int d00 = 2 * tl.r0 + kSeg * gw, d01 = d00 + kSeg * 8;
-          const float2 z = make_float2(0.f, 0.f);
-          const float2 c0 = d00 <= dmax ? sCk(s)[gw * kTK + lane] : z;
-          const float2 c1 = d01 <= dmax ? sCk(s)[(gw + 8) * kTK + lane] : z;
+          // thread = (node pair np of the K chunk, segment sr of the tile): nodes 2 np, 2 np + 1
+          // run as two chains on the same coefficients; the degree of parity par
+          // 2 r0 + 16 sr + 2 k + par is tile row 8 sr + k, the pair's columns one 8-byte store
+          const int np = pt & 15, sr = pt >> 4;
+          const int node = kb * kTK + 2 * np;
+          const float2 x2 = make_float2(node < nh ? sXn[node] : 0.f, node + 1 < nh ? sXn[node + 1] : 0.f);
+          const int d0 = 2 * tl.r0 + kSeg * sr;
+          const float4 ck = d0 <= dmax ? reinterpret_cast<const float4*>(sCk(s))[(sr * kTK) / 2 + np]
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
           uint8_t* ah = sA_hi(s);
           uint8_t* al = sA_lo(s);
-          rec_two_segments(c0, c1, xx.x, xx.y, sCf(s), kSeg * gw, kSeg * (gw + 8), par,
-                           [&](int h, int k, float v) {
-                             const uint32_t o = sw128_offset32(kSeg / 2 * (gw + 8 * h) + k, lane);
-                             const float hv = tf32_rn(v);
-                             *reinterpret_cast<float*>(ah + o) = hv;
-                             *reinterpret_cast<float*>(al + o) = tf32_rn(v - hv);
-                           });
+          rec_node_pair(ck, x2, sCf(s), kSeg * sr + par, [&](int k, float v0, float v1) {
+            const uint32_t o = sw128_offset32(kSeg / 2 * sr + k, 2 * np);
+            const float h0 = tf32_rn(v0), h1 = tf32_rn(v1);
+            *reinterpret_cast<float2*>(ah + o) = make_float2(h0, h1);
+            *reinterpret_cast<float2*>(al + o) = make_float2(tf32_rn(v0 - h0), tf32_rn(v1 - h1));
+          });
         } else if (REC) {
           // node tl.r0 + 32 (gw & 3) + lane (tile row); segments (gw >> 2) + {0, 2} of the K chunk
           // (degrees 64 kb + 16 sr ..): the 8 degrees of parity par of a segment are K positions
           // 8 sr .. 8 sr + 7, stored as two 16-byte chunks (zero past the order's last degree)
           const int row = 32 * (gw & 3) + lane;
           const int node = tl.r0 + row;
-          const float2 xx = node < nh ? sXn[node] : make_float2(0.f, 0.f);
+          const float x2 = node < nh ? sXn[node] : 0.f;
           const int s0 = gw >> 2, s1 = s0 + 2;
           const int d00 = 2 * kb * kTK + kSeg * s0, d01 = 2 * kb * kTK + kSeg * s1;
           const float2 z = make_float2(0.f, 0.f);
           const float2 c0 = d00 <= dmax ? sCk(s)[s0 * kBM + row] : z;
           const float2 c1 = d01 <= dmax ? sCk(s)[s1 * kBM + row] : z;
           float v[2][8];
-          rec_two_segments(c0, c1, xx.x, xx.y, sCf(s), kSeg * s0, kSeg * s1, par,
+          rec_two_segments(c0, c1, x2, sCf(s), kSeg * s0, kSeg * s1, par,
                            [&](int h, int k, float val) { v[h][k] = val; });
           uint8_t* ah = sA_hi(s);
           uint8_t* al = sA_lo(s);
@@ -552,51 +582,64 @@ __global__ void k_c_to_ct32(const int* __restrict__ Mrows, const long long* __re
   }
 }
 
-// Recurrence mode, grid set-up: checkpoints Pbar_{m+16s, m}, Pbar_{m+16s+1, m} at every node of
-// the north hemisphere by the FP64 recurrences of App. B (k_pbar's), rounded to FP32, at
-// ck[(ck_off[m] + s) * ckld + 2 jh + {0, 1}] (nodes past nh stay zero), and x_jh as FP32 pairs.
+// Recurrence mode, grid set-up: checkpoints of every order m, 16-degree segment s and
+// north-hemisphere node, one plane per parity par: (Pbar_{m+16s+par}, Pbar_{m+16s+par+2}) by the
+// FP64 recurrences of App. B (k_pbar's), rounded to FP32, at
+// ck[(par * ck_rows + ck_off[m] + s) * ckld + 2 jh + {0, 1}]; degrees past lmax and nodes past nh
+// stay zero (the buffer is cleared first).  Also x_jh^2 in FP32.
 __global__ void k_ck_build(int lmax, int nh, const double* __restrict__ x, const long long* __restrict__ ck_off,
-                           int ckld, float* __restrict__ ck, float2* __restrict__ xnode) {
+                           long long ck_rows, int ckld, float* __restrict__ ck, float* __restrict__ x2) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (j >= nh) return;
   const double xj = x[j];
-  if (m == 0) {
-    const float h = (float)xj;
-    xnode[j] = make_float2(h, (float)(xj - (double)h));
-  }
+  if (m == 0) x2[j] = (float)(xj * xj);
   const double st = sqrt((1.0 - xj) * (1.0 + xj));
   double pmm = 0.28209479177387814;   // 1/sqrt(4 pi)
   for (int k = 1; k <= m; ++k) pmm *= -sqrt((2.0 * k + 1.0) / (2.0 * k)) * st;
-  float* row = ck + (size_t)ck_off[m] * ckld + 2 * j;
-  double p2 = pmm, p1 = (m < lmax) ? sqrt(2.0 * m + 3.0) * xj * pmm : 0.0;   // degrees m, m + 1
+  double p2 = 0.0, p1 = pmm;   // Pbar_{l-2}, Pbar_{l-1} entering degree l = m + 1
   for (int l = m; l <= lmax; ++l) {
-    const int d = l - m;
-    if (d % kSeg == 0) {   // checkpoint s = d / 16: (Pbar_l, Pbar_{l+1})
-      float* c = row + (size_t)(d / kSeg) * ckld;
-      c[0] = (float)p2;
-      c[1] = (float)p1;
+    double pl;
+    if (l == m) {
+      pl = pmm;
+    } else if (l == m + 1) {
+      pl = sqrt(2.0 * m + 3.0) * xj * pmm;
+    } else {
+      const double ll = (double)l * l, mm = (double)m * m, l1 = (double)(l - 1) * (l - 1);
+      pl = sqrt((4.0 * ll - 1.0) / (ll - mm)) * (xj * p1 - sqrt((l1 - mm) / (4.0 * l1 - 1.0)) * p2);
     }
-    const int ln = l + 2;   // advance (p2, p1) from degrees (l, l + 1) to (l + 1, l + 2)
-    double pn = 0.0;
-    if (ln <= lmax) {
-      const double ll = (double)ln * ln, mm = (double)m * m, l1 = (double)(ln - 1) * (ln - 1);
-      pn = sqrt((4.0 * ll - 1.0) / (ll - mm)) * (xj * p1 - sqrt((l1 - mm) / (4.0 * l1 - 1.0)) * p2);
+    if (l > m) {
+      p2 = p1;
+      p1 = pl;
     }
-    p2 = p1;
-    p1 = pn;
+    const int d = l - m, r = d % kSeg;
+    if (r < 4) {   // offsets 0, 2 -> plane 0; 1, 3 -> plane 1; first or second value by r / 2
+      const int par = r & 1;
+      ck[((size_t)par * ck_rows + ck_off[m] + d / kSeg) * ckld + 2 * j + (r >> 1)] = (float)pl;
+    }
   }
 }
 
-// (a_lm, b_lm) of App. B in FP32 at m * cstride + (l - m) for m + 2 <= l <= lmax; the rest of
-// the row stays zero (the buffer is cleared first), so that the recurrence run past lmax
-// gives zeros
-__global__ void k_coef32_build(int lmax, int cstride, float2* __restrict__ coef) {
+// Two-step coefficients (A, B, C, 0) of degree l (from l - 2 and l - 4) for m + 4 <= l <= lmax at
+// m * cstride + (l - m), in FP64 from a_lm = sqrt((4l^2-1)/(l^2-m^2)), b_lm =
+// sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)), rounded to FP32; the rest of the row stays zero (cleared
+// first), so that the recurrence run past lmax gives zeros
+__global__ void k_coef32_build(int lmax, int cstride, float4* __restrict__ coef) {
   const int m = blockIdx.x;
-  for (int l = m + 2 + threadIdx.x; l <= lmax; l += blockDim.x) {
-    const double ll = (double)l * l, mm = (double)m * m, l1 = (double)(l - 1) * (l - 1);
-    coef[(size_t)m * cstride + (l - m)] =
-        make_float2((float)sqrt((4.0 * ll - 1.0) / (ll - mm)), (float)sqrt((l1 - mm) / (4.0 * l1 - 1.0)));
+  auto al = [&](int l) {
+    const double ll = (double)l * l, mm = (double)m * m;
+    return sqrt((4.0 * ll - 1.0) / (ll - mm));
+  };
+  auto be = [&](int l) {
+    const double mm = (double)m * m, l1 = (double)(l - 1) * (l - 1);
+    return sqrt((l1 - mm) / (4.0 * l1 - 1.0));
+  };
+  for (int t = m + 4 + threadIdx.x; t <= lmax; t += blockDim.x) {
+    const int l = t - 2;   // P_t = (A x^2 + B) P_l + C P_{l-2}
+    const double A = al(l + 2) * al(l + 1);
+    const double B = -al(l + 2) * (al(l + 1) * be(l + 1) / al(l) + be(l + 2));
+    const double C = -al(l + 2) * al(l + 1) * be(l + 1) * be(l);
+    coef[(size_t)m * cstride + (t - m)] = make_float4((float)A, (float)B, (float)C, 0.f);
   }
 }
 
@@ -638,15 +681,15 @@ int build_tf32_recurrence(Grid& g, cudaStream_t st) {
   SHOT_CUDA(cudaMalloc(&g.ck_off_d, (L + 1) * sizeof(long long)));
   SHOT_CUDA(cudaMemcpyAsync(g.ck_off_d, ckoff.data(), (L + 1) * sizeof(long long), cudaMemcpyHostToDevice, st));
   g.ck_off = ckoff;
-  SHOT_CUDA(cudaMalloc(&g.rec_coef, (size_t)L * g.cstride * sizeof(float2)));
-  SHOT_CUDA(cudaMemsetAsync(g.rec_coef, 0, (size_t)L * g.cstride * sizeof(float2), st));
-  SHOT_CUDA(cudaMalloc(&g.rec_x, (size_t)nh * sizeof(float2)));
-  SHOT_CUDA(cudaMalloc(&g.ck, (size_t)g.ck_rows * g.ck_ld * sizeof(float)));
-  SHOT_CUDA(cudaMemsetAsync(g.ck, 0, (size_t)g.ck_rows * g.ck_ld * sizeof(float), st));
+  SHOT_CUDA(cudaMalloc(&g.rec_coef, (size_t)L * g.cstride * sizeof(float4)));
+  SHOT_CUDA(cudaMemsetAsync(g.rec_coef, 0, (size_t)L * g.cstride * sizeof(float4), st));
+  SHOT_CUDA(cudaMalloc(&g.rec_x, (size_t)nh * sizeof(float)));
+  SHOT_CUDA(cudaMalloc(&g.ck, (size_t)2 * g.ck_rows * g.ck_ld * sizeof(float)));   // two parity planes
+  SHOT_CUDA(cudaMemsetAsync(g.ck, 0, (size_t)2 * g.ck_rows * g.ck_ld * sizeof(float), st));
   count_launch(2);
-  k_coef32_build<<<L, 256, 0, st>>>(g.lmax, g.cstride, reinterpret_cast<float2*>(g.rec_coef));
-  k_ck_build<<<dim3((nh + 127) / 128, L), 128, 0, st>>>(g.lmax, nh, g.x_d, g.ck_off_d, g.ck_ld, g.ck,
-                                                        reinterpret_cast<float2*>(g.rec_x));
+  k_coef32_build<<<L, 256, 0, st>>>(g.lmax, g.cstride, reinterpret_cast<float4*>(g.rec_coef));
+  k_ck_build<<<dim3((nh + 127) / 128, L), 128, 0, st>>>(g.lmax, nh, g.x_d, g.ck_off_d, g.ck_rows, g.ck_ld, g.ck,
+                                                        g.rec_x);
   SHOT_CUDA(cudaGetLastError());
   SHOT_CUDA(cudaStreamSynchronize(st));   // ckoff is a local
   return SHOT_OK;
@@ -691,14 +734,15 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
   CUtensorMap mck_a, mck_s;
   if (rec) {
     rx.ck_off = g.ck_off_d;
-    rx.coef = reinterpret_cast<const float2*>(g.rec_coef);
+    rx.coef = reinterpret_cast<const float4*>(g.rec_coef);
     rx.cstride = g.cstride;
-    rx.xnode = reinterpret_cast<const float2*>(g.rec_x);
+    rx.xnode = g.rec_x;
+    rx.ck_rows = g.ck_rows;
     rx.lmax = g.lmax;
     // checkpoint rows (segments) of ck_ld floats: boxes of 16 segments x 32 nodes (analysis)
     // and 4 segments x 128 nodes (synthesis)
-    if ((rc = make_map_f32(&mck_a, g.ck, g.ck_ld, (uint64_t)g.ck_rows, g.ck_ld, 2 * kTK, kAnaSegs))) return rc;
-    if ((rc = make_map_f32(&mck_s, g.ck, g.ck_ld, (uint64_t)g.ck_rows, g.ck_ld, 2 * kBM, kSynSegs))) return rc;
+    if ((rc = make_map_f32(&mck_a, g.ck, g.ck_ld, (uint64_t)2 * g.ck_rows, g.ck_ld, 2 * kTK, kAnaSegs))) return rc;
+    if ((rc = make_map_f32(&mck_s, g.ck, g.ck_ld, (uint64_t)2 * g.ck_rows, g.ck_ld, 2 * kBM, kSynSegs))) return rc;
   }
   if (ana) {
     CUtensorMap ma, mx;

@@ -153,15 +153,16 @@ struct Grid {
   void* rec_coef = nullptr;
   long long* rec_coef_off = nullptr;
   float* rec_x = nullptr;
-  // SHOT_RECURRENCE on TF32X3 grids: FP32 checkpoints (Pbar at degrees m + 16 s, m + 16 s + 1)
-  // [ck_off[m] + s][ck_ld floats: 2 per node], recurrence coefficients (a, b) as FP32 pairs in
-  // rec_coef, node cosines as FP32 pairs in rec_x
+  // SHOT_RECURRENCE on TF32X3 grids: FP32 checkpoints, per parity plane par, Pbar at degrees
+  // (m + 16 s + par, m + 16 s + par + 2) at [par ck_rows + ck_off[m] + s][ck_ld floats: 2 per node];
+  // two-step coefficients (A, B, C, 0) per degree in rec_coef (row stride cstride); x^2 of the
+  // nodes in rec_x
   float* ck = nullptr;
   long long* ck_off_d = nullptr;
   std::vector<long long> ck_off;
-  long long ck_rows = 0;
+  long long ck_rows = 0;       // rows per parity plane
   int ck_ld = 0;
-  int cstride = 0;              // TF32X3 recurrence: coefficient row stride ((a, b) pairs per order)
+  int cstride = 0;              // TF32X3 recurrence: coefficient row stride (entries per order)
   int* M_d = nullptr;
   long long* row_off_d = nullptr;
   Tile* tiles_ana = nullptr;
