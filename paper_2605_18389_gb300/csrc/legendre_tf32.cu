@@ -31,18 +31,21 @@
 // table), and the same-parity two-step form of App. B's recurrence,
 // P_{l+2} = (A x^2 + B) P_l + C P_{l-2}, as FP32 coefficients (A, B, C) per degree.  A stage's
 // checkpoint box (of its parity) comes by TMA and its coefficient slice by a bulk copy with the
-// spectra (analysis) or C^T (synthesis) tile, and the split warps regenerate the stage's A tile
+// spectra (analysis) or C^T (synthesis) tile into the input ring, and the split warps regenerate
+// the A tile of a stage of generated operands
 // in FP32, at most 6 two-degree steps from a checkpoint, writing the values' TF32 hi and lo
 // straight into the swizzled K-major operand:
-//   analysis  A = [128 degree rows of block (m, p)][32 nodes]: a thread per (node pair, 16-degree
-//             segment), 16 segments per tile, a half-warp's 16 lanes the 32 nodes of one row;
+//   analysis  A = [128 degree rows of block (m, p)][32 nodes]: eight of the split warps, a thread
+//             per (node pair, 16-degree segment), 16 segments per tile, a half-warp's 16 lanes
+//             the 32 nodes of one row; the other eight split X^T meanwhile;
 //   synthesis A = [128 nodes][32 degree rows]: a thread per (node, segment), 4 segments per
 //             stage, each segment's 8 rows of the block's parity stored as two 16-byte chunks.
 // The FP32 two-step recurrence over at most 6 steps from FP32-rounded checkpoints carries
 // ~1e-7 rms error relative to each order's largest value (6e-6 at worst near the turning
 // degrees), the level of the FP32 table it replaces.
-// Warp roles: 0 TMA producer, 1 MMA issuer, 2-9 split (eight warps, two per SM sub-partition:
-// the table tile alone is 16 KB per stage), 10-13 epilogue over a double-buffered accumulator
+// Warp roles: 0 TMA producer, 1 MMA issuer, 2-17 split (sixteen warps, four per SM
+// sub-partition, so that the split and recurrence arithmetic, which bounds the kernel, hides
+// its latencies), 18-21 epilogue over a double-buffered accumulator
 // (a warp reads the TMEM lane quadrant warp % 4).  Every mbarrier wait
 // is bounded; on expiry the CTA records SHOT_ERR_TIMEOUT and still frees its tensor memory.
 #include "tc_ptx.cuh"
@@ -50,7 +53,7 @@
 namespace shot {
 namespace {
 
-constexpr int kSplitWarps = 8;                   // warps 2..9 (two per SM sub-partition)
+constexpr int kSplitWarps = 16;                  // warps 2..17 (four per SM sub-partition)
 constexpr int kSplitThreads = 32 * kSplitWarps;
 constexpr int kT32Threads = 32 * (2 + kSplitWarps + 4);   // + TMA, MMA and four epilogue warps
 constexpr int kTK = 32;                          // K per stage (one 128-byte row of FP32)
@@ -93,11 +96,11 @@ __device__ __forceinline__ uint32_t sw128_offset32(int row, int k) {
          (uint32_t)(k & 3) * 4u;
 }
 
-// Element-wise split of a tile (the swizzle does not matter): hi = rn(v) over the raw values,
-// lo = rn(v - hi) beside them.  Each thread loads kSplitBatch chunks before it stores any, so
-// the loads overlap.
-constexpr int kSplitBatch = 4;   // 16 KB / (256 threads x 16 B) = 4 chunks per thread
-__device__ __forceinline__ void split_inplace(uint8_t* raw, uint8_t* lo, int nbytes, int pt) {
+// Element-wise split of a tile (the swizzle does not matter as long as the three tiles share
+// their 1024-byte phase): hi = rn(v), lo = rn(v - hi); hi may be the raw tile itself.  Each
+// thread loads kSplitBatch chunks before it stores any, so the loads overlap.
+constexpr int kSplitBatch = 2;   // 16 KB / (512 threads x 16 B) = 2 chunks per thread
+__device__ __forceinline__ void split_tile(const uint8_t* raw, uint8_t* hi, uint8_t* lo, int nbytes, int pt) {
   for (int base = 0; base < nbytes; base += kSplitBatch * kSplitThreads * 16) {
     float4 v[kSplitBatch];
 #pragma unroll
@@ -112,7 +115,7 @@ __device__ __forceinline__ void split_inplace(uint8_t* raw, uint8_t* lo, int nby
         const float w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
         float4 h, l;
         tf32_split4(w, h, l);
-        *reinterpret_cast<float4*>(raw + o) = h;
+        *reinterpret_cast<float4*>(hi + o) = h;
         *reinterpret_cast<float4*>(lo + o) = l;
       }
     }
@@ -124,13 +127,13 @@ __device__ __forceinline__ void split_inplace(uint8_t* raw, uint8_t* lo, int nby
 // block (jh0 + k >= nh) and columns past the fields are zero.
 // Two tasks per thread are loaded before either is stored.
 __device__ __forceinline__ void split_xt(const float* xs, int nmma, int ncols, int jh0, int nh, uint8_t* bh,
-                                         uint8_t* bl, int pt) {
+                                         uint8_t* bl, int pt, int nthr) {
   const int ntask = nmma * (kTK / 4);
-  for (int e0 = pt; e0 < ntask; e0 += 2 * kSplitThreads) {
+  for (int e0 = pt; e0 < ntask; e0 += 2 * nthr) {
     float v[2][4];
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      const int e = e0 + b * kSplitThreads;
+      const int e = e0 + b * nthr;
       const int c = e % nmma, k4 = (e / nmma) * 4;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
@@ -138,7 +141,7 @@ __device__ __forceinline__ void split_xt(const float* xs, int nmma, int ncols, i
     }
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      const int e = e0 + b * kSplitThreads;
+      const int e = e0 + b * nthr;
       if (e < ntask) {
         const int c = e % nmma, k4 = (e / nmma) * 4;
         float4 h, l;
@@ -154,16 +157,16 @@ __device__ __forceinline__ void split_xt(const float* xs, int nmma, int ncols, i
 // The X^T split with each thread's tasks fixed for the whole kernel (they are the same at every
 // stage): the tile offsets of the four node values, the chunk's offset in the swizzled B tile and
 // whether the column is a field column; a stage then only loads, splits and stores.
-constexpr int kXtTasks = 4;   // nmma x 8 tasks <= 4 x 256 threads (nmma <= 128)
+constexpr int kXtTasks = 2;   // nmma x 8 tasks <= 2 x threads (wider batches take split_xt's loop)
 struct XtPlan {
   int c[kXtTasks];         // column (-1: no task)
   int k4[kXtTasks];        // first of the task's four nodes within the 32-node chunk
   uint32_t o[kXtTasks];    // byte offset of the 16-byte chunk in the hi (and lo) tile
-  __device__ __forceinline__ void init(int nmma, int pt) {
+  __device__ __forceinline__ void init(int nmma, int pt, int nthr) {
     const int ntask = nmma * (kTK / 4);
 #pragma unroll
     for (int i = 0; i < kXtTasks; ++i) {
-      const int e = pt + i * kSplitThreads;
+      const int e = pt + i * nthr;
       c[i] = -1;
       k4[i] = 0;
       o[i] = 0;
@@ -212,6 +215,7 @@ struct T32Args {
                               // zero past l = lmax
   int cstride;
   const float* xnode;         // x_jh^2 in FP32
+  int nin;                    // input ring depth (REC)
   int lmax;
 };
 
@@ -225,42 +229,36 @@ static_assert(kCkBytes == kSynSegs * kBM * 8, "both checkpoint boxes are 4 KB");
 constexpr int kCfAna = 2 * kBM;                      // coefficients per analysis stage (its tile's degrees)
 constexpr int kCfSyn = 2 * kTK;                      // coefficients per synthesis stage (its K chunk's degrees)
 constexpr int kCfBytes = kCfAna * 16;                // room for either slice
+constexpr int kMaxIn = 8;                            // deepest input ring
+static_assert(kMaxIn <= (int)(sizeof(TcSmem::infull) / sizeof(uint64_t)), "input ring barriers");
 
-// Two 16-degree segments of the recurrence side by side (independent chains), both of the
-// parity par: chain h starts from its checkpoint (P_{d0+par}, P_{d0+par+2}) and steps two
-// degrees at a time by the same-parity form of App. B's recurrence,
+// One 16-degree segment of the recurrence at one node, all of the parity par: it starts from
+// its checkpoint ck = (P_{d0+par}, P_{d0+par+2}) and steps two degrees at a time by the
+// same-parity form of App. B's recurrence,
 //   P_{l+2} = (A x^2 + B) P_l + C P_{l-2},
 //   A = a_{l+2} a_{l+1},  B = -a_{l+2} (a_{l+1} b_{l+1} / a_l + b_{l+2}),  C = -a_{l+2} a_{l+1} b_{l+1} b_l
-// (eliminate P_{l+1} and P_{l-1} from three consecutive steps), with (A, B, C) of the new degree
-// at cf[cb_h + (its degree - d0)].  The coefficients are zero past the order's last degree, so
-// the values there come out zero and no step needs a bounds test.  emit(h, k, value) receives
-// P_{d0 + par + 2k}, k = 0 .. 7.
+// (eliminate P_{l+1} and P_{l-1} from three consecutive steps), with (A, B, C) of degree
+// d0 + par + 2k at cf[cb + 2k] (cb = d0 + par relative to the stage's coefficient slice).  The
+// coefficients are zero past the order's last degree, so the values there come out zero and no
+// step needs a bounds test.  emit(k, value) receives P_{d0 + par + 2k}, k = 0 .. 7.
 template <class F>
-__device__ __forceinline__ void rec_two_segments(float2 ck0, float2 ck1, float x2, const float4* cf, int cb0,
-                                                 int cb1, int par, F&& emit) {
-  float a0 = ck0.x, b0 = ck0.y, a1 = ck1.x, b1 = ck1.y;
-  emit(0, 0, a0);
-  emit(1, 0, a1);
-  emit(0, 1, b0);
-  emit(1, 1, b1);
+__device__ __forceinline__ void rec_segment(float2 ck, float x2, const float4* cf, int cb, F&& emit) {
+  float a0 = ck.x, b0 = ck.y;
+  emit(0, a0);
+  emit(1, b0);
 #pragma unroll
   for (int k = 2; k < kSeg / 2; ++k) {
-    const float4 e0 = cf[cb0 + par + 2 * k], e1 = cf[cb1 + par + 2 * k];
-    const float c0 = fmaf(fmaf(e0.x, x2, e0.y), b0, e0.z * a0);
-    const float c1 = fmaf(fmaf(e1.x, x2, e1.y), b1, e1.z * a1);
-    emit(0, k, c0);
-    emit(1, k, c1);
+    const float4 e = cf[cb + 2 * k];
+    const float c0 = fmaf(fmaf(e.x, x2, e.y), b0, e.z * a0);
+    emit(k, c0);
     a0 = b0;
     b0 = c0;
-    a1 = b1;
-    b1 = c1;
   }
 }
 
-// One 16-degree segment at two nodes side by side (same coefficients, independent chains):
-// ck = (P_{d0+par}, P_{d0+par+2}) at node 0, then at node 1; x2 = (x0^2, x1^2); cf[cb + 2k] holds
-// (A, B, C) of degree d0 + par + 2k (cb = d0 + par relative to the slice).  emit(k, v0, v1)
-// receives P_{d0 + par + 2k} at both nodes, k = 0 .. 7.
+// The same segment at two nodes side by side (independent chains on the same coefficients):
+// ck = (P_{d0+par}, P_{d0+par+2}) at node 0, then at node 1; x2 = (x0^2, x1^2); emit(k, v0, v1)
+// receives P_{d0 + par + 2k} at both nodes.
 template <class F>
 __device__ __forceinline__ void rec_node_pair(float4 ck, float2 x2, const float4* cf, int cb, F&& emit) {
   float a0 = ck.x, b0 = ck.y, a1 = ck.z, b1 = ck.w;
@@ -279,10 +277,13 @@ __device__ __forceinline__ void rec_node_pair(float4 ck, float2 x2, const float4
   }
 }
 
-// Persistent, warp-specialised TF32x3 Legendre GEMM (roles in the file header).  Stage s
-// holds [A hi][A lo][B hi][B lo][X raw (analysis)][checkpoint box (REC)]; A hi is the raw
-// table tile by TMA, or (REC) the values the split warps regenerate.  REC adds, after the
-// stages, the node cosines and two coefficient buffers (by tile parity).
+// Persistent, warp-specialised TF32x3 Legendre GEMM (roles in the file header).  Table mode:
+// stage s holds [A hi][A lo][B hi][B lo][X raw (analysis)], A hi the raw table tile by TMA.
+// Recurrence mode (REC) runs two rings, so that the TMA latency hides behind a deep ring of
+// the small inputs while the large generated operands need only a few stages: kStages output
+// stages [A hi][A lo][B hi][B lo] (written by the split warps, read by the MMAs) and a.nin
+// input stages [X or C^T raw][checkpoint box][coefficient slice] (written by TMA, read by the
+// split warps, released as soon as they are read), then x^2 of the nodes.
 template <int kStages, bool ANA, bool BCAT, bool REC = false>
 __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_constant__ CUtensorMap ta,
                                                                   const __grid_constant__ CUtensorMap tb,
@@ -292,19 +293,20 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
   uint8_t* base = align1k(smraw);
   const int nmma = a.nmma, nh = a.nh;
   const int bbytes = nmma * kTK * 4;   // one B tile (hi or lo); the analysis X tile has the same size
-  const int sbytes = 2 * kTTile + (ANA ? 3 : 2) * bbytes + (REC ? kCkBytes + kCfBytes : 0);
+  const int sbytes = 2 * kTTile + (REC ? 2 : (ANA ? 3 : 2)) * bbytes;   // one (output) stage
+  const int ibytes = bbytes + kCkBytes + kCfBytes;                         // one REC input stage
+  uint8_t* ibase = base + kStages * sbytes;
   auto sA_hi = [&](int s) { return base + s * sbytes; };
   auto sA_lo = [&](int s) { return base + s * sbytes + kTTile; };
   auto sB_hi = [&](int s) { return base + s * sbytes + 2 * kTTile; };
   auto sB_lo = [&](int s) { return base + s * sbytes + 2 * kTTile + bbytes; };
-  auto sX = [&](int s) { return base + s * sbytes + 2 * kTTile + 2 * bbytes; };
-  auto sCk = [&](int s) {
-    return reinterpret_cast<const float2*>(base + s * sbytes + 2 * kTTile + (ANA ? 3 : 2) * bbytes);
-  };
-  auto sCf = [&](int s) {   // REC: the stage's coefficient slice
-    return reinterpret_cast<const float4*>(base + s * sbytes + 2 * kTTile + (ANA ? 3 : 2) * bbytes + kCkBytes);
-  };
-  float* sXn = reinterpret_cast<float*>(base + kStages * sbytes);   // REC: x^2 of the nodes [nh]
+  // analysis X raw: the table-mode stage's fifth tile, or the REC input stage's first
+  auto sIn = [&](int i) { return ibase + i * ibytes; };   // REC: the input stage's X or C^T raw tile
+  auto sX = [&](int s) { return REC ? sIn(s) : base + s * sbytes + 2 * kTTile + 2 * bbytes; };
+  auto sCk = [&](int i) { return reinterpret_cast<const float2*>(ibase + i * ibytes + bbytes); };
+  auto sCf = [&](int i) { return reinterpret_cast<const float4*>(ibase + i * ibytes + bbytes + kCkBytes); };
+  const int nin = REC ? a.nin : 1;
+  float* sXn = reinterpret_cast<float*>(ibase + (REC ? nin * ibytes : 0));   // REC: x^2 of the nodes [nh]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // BCAT (2 nmma <= 256): B hi and B lo are adjacent in shared memory and form one operand
   // of N = 2 nmma, so A_hi [B_hi | B_lo] and A_lo B_hi are two MMAs per K step instead of
@@ -317,12 +319,16 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl.fullA[s], 1);
-      mbar_init(&ctl.fullB[s], kSplitThreads);
+      mbar_init(&ctl.fullB[s], kSplitWarps);   // one arrival per split warp
       mbar_init(&ctl.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&ctl.tfull[b], 1);
-      mbar_init(&ctl.tempty[b], 128);
+      mbar_init(&ctl.tempty[b], 4);   // one arrival per epilogue warp
+    }
+    for (int i = 0; REC && i < nin; ++i) {
+      mbar_init(&ctl.infull[i], 1);
+      mbar_init(&ctl.inempty[i], kSplitWarps);
     }
     ctl.abort = 0;
     fence_mbar_init();
@@ -339,7 +345,8 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
 
   if (warp == 0) {
     if (lane == 0) {  // TMA producer, runs ahead across tiles
-      int it = 0;
+      const int depth = REC ? nin : kStages;
+      int it = 0, s = 0, ph = 0;   // slot of the ring and its phase parity, advanced by counting
       bool ok = true;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const Tile tl = a.tiles[t];
@@ -347,41 +354,46 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         // checkpoint rows of order m in the plane of the tile's parity (planes of ck_rows rows)
         const long long ck_base = REC ? (tl.blk & 1) * a.ck_rows + a.ck_off[tl.blk >> 1] : 0;
         for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int s = it % kStages, n = it / kStages;
-          if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
-          mbar_arrive_expect_tx(&ctl.fullA[s],
-                                (REC ? kCkBytes + (ANA ? kCfAna : kCfSyn) * 16 : kTTile) + bbytes);
+          // REC fills the input ring (freed by the split warps), the table mode the stages (freed
+          // by the MMAs)
+          uint64_t* full = REC ? &ctl.infull[s] : &ctl.fullA[s];
+          if (it >= depth && !(ok = mbar_wait(REC ? &ctl.inempty[s] : &ctl.empty[s], ph ^ 1, abort))) break;
+          mbar_arrive_expect_tx(full, (REC ? kCkBytes + (ANA ? kCfAna : kCfSyn) * 16 : kTTile) + bbytes);
           if (REC) {   // checkpoint box of the stage (segments x nodes), FP32 pairs, and coefficients
             const int m = tl.blk >> 1;
             uint8_t* ck = reinterpret_cast<uint8_t*>(const_cast<float2*>(sCk(s)));
             uint8_t* cf = reinterpret_cast<uint8_t*>(const_cast<float4*>(sCf(s)));
             // checkpoint plane of the tile's parity: rows ck_base (see the producer's tile set-up)
             if (ANA) {   // 16 segments of the tile's degrees 2 r0 .. 2 r0 + 255 x the 32 nodes of this chunk
-              tma_load_2d(ck, &ta, &ctl.fullA[s], 2 * kb * kTK, (int)(ck_base + tl.r0 / 8));
-              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * tl.r0, kCfAna * 16, &ctl.fullA[s]);
+              tma_load_2d(ck, &ta, full, 2 * kb * kTK, (int)(ck_base + tl.r0 / 8));
+              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * tl.r0, kCfAna * 16, full);
             } else {     // the 4 segments of this K chunk's degrees 64 kb .. 64 kb + 63 x the tile's 128 nodes
-              tma_load_2d(ck, &ta, &ctl.fullA[s], 2 * tl.r0, (int)(ck_base + kb * kSynSegs));
-              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * kb * kTK, kCfSyn * 16, &ctl.fullA[s]);
+              tma_load_2d(ck, &ta, full, 2 * tl.r0, (int)(ck_base + kb * kSynSegs));
+              bulk_load(cf, a.coef + (size_t)m * a.cstride + 2 * kb * kTK, kCfSyn * 16, full);
             }
           } else if (ANA) {   // table rows i of the tile x nodes of this K-chunk
-            tma_load_2d(sA_hi(s), &ta, &ctl.fullA[s], kb * kTK, (int)(a.row_off[tl.blk] + tl.r0));
+            tma_load_2d(sA_hi(s), &ta, full, kb * kTK, (int)(a.row_off[tl.blk] + tl.r0));
           } else {     // transposed table: nodes of the tile x degrees of this K-chunk
-            tma_load_2d(sA_hi(s), &ta, &ctl.fullA[s], kb * kTK, tl.blk * nh + tl.r0);
+            tma_load_2d(sA_hi(s), &ta, full, kb * kTK, tl.blk * nh + tl.r0);
           }
           if (ANA)     // spectra rows = nodes of this K chunk
-            tma_load_2d(sX(s), &tb, &ctl.fullA[s], 0, tl.blk * nh + kb * kTK);
+            tma_load_2d(sX(s), &tb, full, 0, tl.blk * nh + kb * kTK);
           else         // C^T rows = columns, degrees of this K chunk
-            tma_load_2d(sB_hi(s), &tb, &ctl.fullA[s], kb * kTK, tl.blk * a.nmma_cap);
+            tma_load_2d(REC ? sIn(s) : sB_hi(s), &tb, full, kb * kTK, tl.blk * a.nmma_cap);
+          if (++s == depth) {
+            s = 0;
+            ph ^= 1;
+          }
         }
       }
       // let this CTA's copies land before it can exit
-      for (int k = it > kStages ? it - kStages : 0; k < it; ++k)
-        mbar_drain(&ctl.fullA[k % kStages], (k / kStages) & 1);
+      for (int k = it > depth ? it - depth : 0; k < it; ++k)
+        mbar_drain(REC ? &ctl.infull[k % depth] : &ctl.fullA[k % depth], (k / depth) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer: waits until the split warps have written the stage's lo parts
       const uint32_t idesc = idesc_tf32(kBM, nmma), idesc2 = idesc_tf32(kBM, nacc);
-      int it = 0, lt = 0;
+      int lt = 0, s = 0, ph = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++lt) {
         const Tile tl = a.tiles[t];
@@ -390,9 +402,8 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (u - 1) & 1, abort))) break;
         tc_fence_after();
         const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
-        for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int s = it % kStages, n = it / kStages;
-          if (!(ok = mbar_wait(&ctl.fullB[s], n & 1, abort))) break;
+        for (int kb = 0; kb < nkb; ++kb) {
+          if (!(ok = mbar_wait(&ctl.fullB[s], ph, abort))) break;
           tc_fence_after();
           const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
           const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
@@ -411,19 +422,32 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
             }
           }
           umma_commit(&ctl.empty[s]);
+          if (++s == kStages) {
+            s = 0;
+            ph ^= 1;
+          }
         }
         if (!ok) break;
         umma_commit(&ctl.tfull[acc]);
       }
     }
   } else if (warp < 2 + kSplitWarps) {
-    // split warps: table tile -> lo (the raw tile is hi); analysis: X -> X^T hi/lo; synthesis: C^T -> hi/lo in place
+    // split warps: table tile -> lo (the raw tile is hi) or (REC) the regenerated A tile hi/lo;
+    // analysis: X -> X^T hi/lo; synthesis: C^T -> hi/lo (in place in table mode)
     const int pt = threadIdx.x - 64;
-    const bool pre = ANA && nmma * (kTK / 4) <= kXtTasks * kSplitThreads;
+    // REC analysis: split warps 0-7 regenerate A (node pairs), 8-15 split X^T; otherwise every
+    // split warp does both parts.  bt / nbt: this thread among the X^T threads.
+    constexpr bool kRoles = REC && ANA;
+    constexpr int nbt = kRoles ? kSplitThreads / 2 : kSplitThreads;
+    const bool agen = !kRoles || pt < kSplitThreads / 2, bsplit = !kRoles || pt >= kSplitThreads / 2;
+    const int bt = kRoles ? pt - kSplitThreads / 2 : pt;
+    const bool pre = ANA && nmma * (kTK / 4) <= kXtTasks * nbt;
     XtPlan xp;
-    xp.init(pre ? nmma : 0, pt);
-    const int gw = pt >> 5;   // generator warp 0..7
-    int it = 0;
+    xp.init(pre && bsplit ? nmma : 0, bt, nbt);
+    const int gw = pt >> 5;   // split warp 0..15
+    // it counts stages; s / ph: the stage written and its phase parity; i / iph: the REC input
+    // slot and its phase (table mode: the stage itself), advanced by counting
+    int it = 0, s = 0, ph = 0, i = 0, iph = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
       const Tile tl = a.tiles[t];
@@ -431,72 +455,87 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
       const int m = tl.blk >> 1, par = tl.blk & 1;
       const int dmax = a.lmax - m;   // largest relative degree of order m
       for (int kb = 0; kb < nkb; ++kb, ++it) {
-        const int s = it % kStages, n = it / kStages;
-        if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
+        // REC: the inputs are in slot i of the input ring, and stage s must also be free (its
+        // previous MMAs done).  Every thread waits (each must observe the copies' phase
+        // itself); the outcome is made warp-uniform so that a warp leaves together and its
+        // single arrivals below stay valid.
+        if (!REC) i = s;
+        bool w = REC ? mbar_wait(&ctl.infull[i], iph, abort) : mbar_wait(&ctl.fullA[s], ph, abort);
+        if (REC && w && it >= kStages) w = mbar_wait(&ctl.empty[s], ph ^ 1, abort);
+        if (!(ok = __all_sync(0xffffffffu, w))) break;
         if (REC && ANA) {
-          // thread = (node pair np of the K chunk, segment sr of the tile): nodes 2 np, 2 np + 1
-          // run as two chains on the same coefficients; the degree of parity par
-          // 2 r0 + 16 sr + 2 k + par is tile row 8 sr + k, the pair's columns one 8-byte store
-          const int np = pt & 15, sr = pt >> 4;
-          const int node = kb * kTK + 2 * np;
-          const float2 x2 = make_float2(node < nh ? sXn[node] : 0.f, node + 1 < nh ? sXn[node + 1] : 0.f);
-          const int d0 = 2 * tl.r0 + kSeg * sr;
-          const float4 ck = d0 <= dmax ? reinterpret_cast<const float4*>(sCk(s))[(sr * kTK) / 2 + np]
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-          uint8_t* ah = sA_hi(s);
-          uint8_t* al = sA_lo(s);
-          rec_node_pair(ck, x2, sCf(s), kSeg * sr + par, [&](int k, float v0, float v1) {
-            const uint32_t o = sw128_offset32(kSeg / 2 * sr + k, 2 * np);
-            const float h0 = tf32_rn(v0), h1 = tf32_rn(v1);
-            *reinterpret_cast<float2*>(ah + o) = make_float2(h0, h1);
-            *reinterpret_cast<float2*>(al + o) = make_float2(tf32_rn(v0 - h0), tf32_rn(v1 - h1));
-          });
+          if (agen) {
+            // thread = (node pair np of the K chunk, segment sr of the tile): nodes 2 np, 2 np + 1
+            // run as two chains on the same coefficients; the degree of parity par
+            // 2 r0 + 16 sr + 2 k + par is tile row 8 sr + k, the pair's columns one 8-byte store
+            const int np = pt & 15, sr = pt >> 4;
+            const int node = kb * kTK + 2 * np;
+            const float2 x2 = make_float2(node < nh ? sXn[node] : 0.f, node + 1 < nh ? sXn[node + 1] : 0.f);
+            const int d0 = 2 * tl.r0 + kSeg * sr;
+            const float4 ck = d0 <= dmax ? reinterpret_cast<const float4*>(sCk(i))[(sr * kTK) / 2 + np]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            uint8_t* ah = sA_hi(s);
+            uint8_t* al = sA_lo(s);
+            rec_node_pair(ck, x2, sCf(i), kSeg * sr + par, [&](int k, float v0, float v1) {
+              const uint32_t o = sw128_offset32(kSeg / 2 * sr + k, 2 * np);
+              const float h0 = tf32_rn(v0), h1 = tf32_rn(v1);
+              *reinterpret_cast<float2*>(ah + o) = make_float2(h0, h1);
+              *reinterpret_cast<float2*>(al + o) = make_float2(tf32_rn(v0 - h0), tf32_rn(v1 - h1));
+            });
+          }
         } else if (REC) {
-          // node tl.r0 + 32 (gw & 3) + lane (tile row); segments (gw >> 2) + {0, 2} of the K chunk
-          // (degrees 64 kb + 16 sr ..): the 8 degrees of parity par of a segment are K positions
-          // 8 sr .. 8 sr + 7, stored as two 16-byte chunks (zero past the order's last degree)
+          // node tl.r0 + 32 (gw & 3) + lane (tile row); segment gw >> 2 of the K chunk (degrees
+          // 64 kb + 16 sr ..): its 8 degrees of parity par are K positions 8 sr .. 8 sr + 7,
+          // stored as two 16-byte chunks (zero past the order's last degree)
           const int row = 32 * (gw & 3) + lane;
           const int node = tl.r0 + row;
           const float x2 = node < nh ? sXn[node] : 0.f;
-          const int s0 = gw >> 2, s1 = s0 + 2;
-          const int d00 = 2 * kb * kTK + kSeg * s0, d01 = 2 * kb * kTK + kSeg * s1;
-          const float2 z = make_float2(0.f, 0.f);
-          const float2 c0 = d00 <= dmax ? sCk(s)[s0 * kBM + row] : z;
-          const float2 c1 = d01 <= dmax ? sCk(s)[s1 * kBM + row] : z;
-          float v[2][8];
-          rec_two_segments(c0, c1, x2, sCf(s), kSeg * s0, kSeg * s1, par,
-                           [&](int h, int k, float val) { v[h][k] = val; });
+          const int sr = gw >> 2;
+          const int d0 = 2 * kb * kTK + kSeg * sr;
+          const float2 c = d0 <= dmax ? sCk(i)[sr * kBM + row] : make_float2(0.f, 0.f);
+          float v[8];
+          rec_segment(c, x2, sCf(i), kSeg * sr + par, [&](int k, float val) { v[k] = val; });
           uint8_t* ah = sA_hi(s);
           uint8_t* al = sA_lo(s);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int sr = h ? s1 : s0;
-            const float w0[4] = {v[h][0], v[h][1], v[h][2], v[h][3]};
-            const float w1[4] = {v[h][4], v[h][5], v[h][6], v[h][7]};
-            const uint32_t o0 = sw128_offset32(row, 8 * sr), o1 = sw128_offset32(row, 8 * sr + 4);
-            float4 h0, l0, h1, l1;
-            tf32_split4(w0, h0, l0);
-            tf32_split4(w1, h1, l1);
-            *reinterpret_cast<float4*>(ah + o0) = h0;
-            *reinterpret_cast<float4*>(ah + o1) = h1;
-            *reinterpret_cast<float4*>(al + o0) = l0;
-            *reinterpret_cast<float4*>(al + o1) = l1;
-          }
+          const float w0[4] = {v[0], v[1], v[2], v[3]};
+          const float w1[4] = {v[4], v[5], v[6], v[7]};
+          const uint32_t o0 = sw128_offset32(row, 8 * sr), o1 = sw128_offset32(row, 8 * sr + 4);
+          float4 h0, l0, h1, l1;
+          tf32_split4(w0, h0, l0);
+          tf32_split4(w1, h1, l1);
+          *reinterpret_cast<float4*>(ah + o0) = h0;
+          *reinterpret_cast<float4*>(ah + o1) = h1;
+          *reinterpret_cast<float4*>(al + o0) = l0;
+          *reinterpret_cast<float4*>(al + o1) = l1;
         } else {
-          split_inplace(sA_hi(s), sA_lo(s), kTTile, pt);
+          split_tile(sA_hi(s), sA_hi(s), sA_lo(s), kTTile, pt);
         }
-        if (ANA && pre)
-          xp.run(reinterpret_cast<const float*>(sX(s)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s));
-        else if (ANA)
-          split_xt(reinterpret_cast<const float*>(sX(s)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s), pt);
-        else
-          split_inplace(sB_hi(s), sB_lo(s), bbytes, pt);
-        fence_async_smem();
-        mbar_arrive(&ctl.fullB[s]);
+        if (ANA && pre && bsplit)
+          xp.run(reinterpret_cast<const float*>(sX(i)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s));
+        else if (ANA && bsplit)
+          split_xt(reinterpret_cast<const float*>(sX(i)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s), bt, nbt);
+        else if (!ANA)
+          split_tile(REC ? sIn(i) : sB_hi(s), sB_hi(s), sB_lo(s), bbytes, pt);
+        // one arrival per warp, after __syncwarp has ordered all its lanes' accesses before it
+        if (REC) {   // inputs read: the producer may refill the slot
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&ctl.inempty[i]);
+        }
+        fence_async_smem();   // this thread's operand writes, made visible to the tensor core
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ctl.fullB[s]);
+        if (++s == kStages) {
+          s = 0;
+          ph ^= 1;
+        }
+        if (REC && ++i == nin) {
+          i = 0;
+          iph ^= 1;
+        }
       }
     }
   } else {
-    // epilogue: drain the accumulator of every tile of this CTA (warp 8 + q reads lanes 32q..)
+    // epilogue: drain the accumulator of every tile of this CTA (a warp reads the TMEM lanes of its quadrant warp % 4)
     const int q = warp & 3;   // a warp reaches only TMEM lanes 32 (warp % 4) ..
     int lt = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
@@ -557,7 +596,8 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         }
       }
       tc_fence_before();
-      mbar_arrive(&ctl.tempty[acc]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ctl.tempty[acc]);
     }
   }
   tc_fence_before();
@@ -643,11 +683,13 @@ __global__ void k_coef32_build(int lmax, int cstride, float4* __restrict__ coef)
   }
 }
 
-size_t tf32_smem_bytes(int nmma, bool ana, int stages, bool rec, int nh) {
-  size_t b = 1024 + (size_t)stages * (2 * kTTile + (ana ? 3 : 2) * (size_t)nmma * kTK * 4 +
-                                      (rec ? kCkBytes + kCfBytes : 0));
-  if (rec) b += (size_t)((nh + 1) & ~1) * 8;
-  return b;
+// dynamic shared memory of k_legendre_tf32: 1 KB alignment slack, the stages, and in recurrence
+// mode the input ring and x^2 of the nodes
+size_t tf32_smem_bytes(int nmma, bool ana, int stages, bool rec, int nin, int nh) {
+  const size_t bb = (size_t)nmma * kTK * 4;
+  if (!rec) return 1024 + (size_t)stages * (2 * kTTile + (ana ? 3 : 2) * bb);
+  return 1024 + (size_t)stages * (2 * kTTile + 2 * bb) + (size_t)nin * (bb + kCkBytes + kCfBytes) +
+         (size_t)((nh + 3) & ~3) * 4;
 }
 
 template <bool REC>
@@ -705,21 +747,36 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
     return SHOT_ERR_UNSUPPORTED;
   }
   int rc;
-  // deepest pipeline (<= 4 stages) whose tiles fit in one CTA's shared memory, with 2 KB
-  // left for the static control block
-  auto bytes = [&](bool a_, int s) { return tf32_smem_bytes(nmma, a_, s, rec, g.nh); };
-  auto pick = [&](bool a_) {
-    int s = kT32MaxStages;
-    while (s > 1 && bytes(a_, s) + 2048 > 227 * 1024) --s;
-    return s;
+  // Table mode: the deepest pipeline (<= 4 stages) whose tiles fit in one CTA's shared memory,
+  // with 2 KB left for the static control block.  Recurrence mode: 3 stages of generated
+  // operands (2, then 1, where the fields leave no room) and the deepest input ring (<= 8)
+  // beside them; SHOT_TC_STAGES / SHOT_T32_INRING fix either depth.
+  constexpr size_t kSmemCap = 227 * 1024 - 2048;
+  auto bytes = [&](bool a_, int s, int in) { return tf32_smem_bytes(nmma, a_, s, rec, in, g.nh); };
+  auto pick = [&](bool a_, int& s, int& in) {
+    if (!rec) {
+      in = 0;
+      s = g.tc_stages_override > 0 ? g.tc_stages_override : kT32MaxStages;
+      while (s > 1 && bytes(a_, s, 0) > kSmemCap) --s;
+      return;
+    }
+    const size_t ib = bytes(a_, 1, 1) - bytes(a_, 1, 0);
+    for (s = g.tc_stages_override > 0 ? g.tc_stages_override : 3; s >= 1; --s) {
+      const size_t fixed = bytes(a_, s, 0);
+      in = fixed < kSmemCap ? (int)std::min<size_t>(kMaxIn, (kSmemCap - fixed) / ib) : 0;
+      if (g.t32_in_override > 0 && g.t32_in_override < in) in = g.t32_in_override;
+      if (in >= (s > 2 ? 4 : s) || s == 1) return;
+    }
   };
-  auto launch = [&](bool a_, const CUtensorMap& ma, const CUtensorMap& mb, const T32Args& args, int ntiles) -> int {
-    const int stages = pick(a_);
-    const size_t smem = bytes(a_, stages);
-    if (smem + 2048 > 227 * 1024) {
+  auto launch = [&](bool a_, const CUtensorMap& ma, const CUtensorMap& mb, T32Args args, int ntiles) -> int {
+    int stages, nin;
+    pick(a_, stages, nin);
+    const size_t smem = bytes(a_, stages, nin);
+    if (smem > kSmemCap || (rec && nin < 1)) {
       set_error("TF32X3: the grid's recurrence buffers do not fit in shared memory");
       return SHOT_ERR_UNSUPPORTED;
     }
+    args.nin = nin;
     const bool bc = 2 * nmma <= 256;
     void* kern = rec ? tf32_kernel<true>(a_, bc, stages) : tf32_kernel<false>(a_, bc, stages);
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -167,7 +167,8 @@ struct Grid {
   long long* row_off_d = nullptr;
   Tile* tiles_ana = nullptr;
   Tile* tiles_syn = nullptr;
-  int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core analysis (0 = tuned)
+  int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core kernels (0 = tuned)
+  int t32_in_override = 0;      // SHOT_T32_INRING: input ring depth of the TF32 recurrence kernels (0 = deepest)
   int idft_nonpersistent = 0;   // SHOT_IDFT_PERSISTENT=0: update half-steps use the one-item-per-CTA k_idft
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use
   // ring geometry (every grid): ring i holds ring_len[i] nodes starting at ring_off[i] of a

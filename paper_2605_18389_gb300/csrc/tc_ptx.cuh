@@ -34,17 +34,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* b, uint32_t byte
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
 }
-// One potentially blocking probe: mbarrier.try_wait suspends the thread in hardware for a
-// bounded, system-dependent time, so waiting roles do not take issue slots from the working
-// ones the way a test_wait spin does.
+// One potentially blocking probe: mbarrier.try_wait suspends the thread in hardware until the
+// phase completes or the suspend-time hint (ns) runs out, so a waiting role costs a few
+// instructions per wake-up instead of a polling loop's issue slots on the working warps.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
-      : "r"(smem_u32(b)), "r"(parity)
+      : "r"(smem_u32(b)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -193,6 +194,8 @@ struct TcSmem {
   uint64_t tfull[2];    // accumulator buffer ready for the epilogue
   uint64_t tempty[2];   // accumulator buffer drained by the epilogue
   uint64_t bempty[3];   // analysis B buffer read by the MMAs (B ring of up to three)
+  uint64_t infull[8];   // TF32 recurrence mode: input ring (TMA landed / read by the split warps)
+  uint64_t inempty[8];
   uint32_t tmem;
   int abort;
 };
