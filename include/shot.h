@@ -159,6 +159,15 @@ int shot_grid_reserve(shot_grid g, int nfields);
  * Errors: INVALID_ARG (NULL grid), CUDA, TIMEOUT. */
 int shot_grid_check(shot_grid g, void* stream);
 
+/* Limit of the bounded device-side waits in this grid's tensor-core kernels, in SM clock
+ * cycles, for the launches that follow (cycles <= 0 restores the default 2^30, about 0.5 s).
+ * A limit below 2^20 makes every wait probe without blocking and read the clock after each
+ * probe, so that it expires on time: a way to exercise the timeout path (status
+ * SHOT_ERR_TIMEOUT from shot_grid_check, tensor memory released, the grid usable again).
+ * The waits that only let a CTA's own copies and MMAs finish before it exits keep the
+ * default.  Not part of the paper's method.  Errors: INVALID_ARG (NULL grid). */
+int shot_grid_set_wait_limit(shot_grid g, long long cycles);
+
 /* Heat convolution, Sec. 3.2: out = HeatConv(in; h), h_l = exp(-t l(l+1)), for
  * nfields fields:  ring real-DFT -> per-order Legendre analysis with area weights ->
  * scaling by h_l -> Legendre synthesis -> inverse ring DFT.

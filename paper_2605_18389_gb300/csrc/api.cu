@@ -899,6 +899,13 @@ int shot_grid_check(shot_grid gh, void* stream) {
   return SHOT_OK;
 }
 
+int shot_grid_set_wait_limit(shot_grid gh, long long cycles) {
+  Grid* g = as_grid(gh);
+  if (!g) { set_error("shot_grid_set_wait_limit: bad grid"); return SHOT_ERR_INVALID_ARG; }
+  g->wait_cycles = cycles > 0 ? cycles : kDefaultWaitCycles;
+  return SHOT_OK;
+}
+
 int shot_heat_apply(shot_grid gh, double t, const float* in, float* out, int nfields, void* stream) {
   Grid* g = as_grid(gh);
   if (!g || !in || !out || nfields < 1 || !(t >= 0.0) || in == out) {

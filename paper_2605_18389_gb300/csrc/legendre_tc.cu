@@ -147,6 +147,7 @@ struct AnaArgs {
   int nmma_cap, ldi;
   float* cf;           // optional FP32 [row_off + i][ldc]
   int* err;
+  long long wait;      // limit of every bounded wait (SM clock cycles)
 };
 
 struct SynArgs {
@@ -158,6 +159,7 @@ struct SynArgs {
   int nmma, nmma_cap, ncols, ldc;
   float* Y;   // [blk][jh][ldc]
   int* err;
+  long long wait;
 };
 
 // Persistent, warp-specialised Legendre GEMM.  Warp 0: TMA producer (runs ahead across
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(tc_threads<ANA>(), 1) k_legendre_tc(const __gr
       mbar_init(&ctl.tempty[b], 128);
     }
     for (int b = 0; b < kBR; ++b) mbar_init(&ctl.bempty[b], 1);
+    mbar_init(&ctl.drain, 1);
     ctl.abort = 0;
     fence_mbar_init();
   }
@@ -239,6 +242,7 @@ __global__ void __launch_bounds__(tc_threads<ANA>(), 1) k_legendre_tc(const __gr
   tc_fence_after();
   const uint32_t taddr = ctl.tmem;
   volatile int* abort = &ctl.abort;
+  const long long wl = (ANA ? aa.wait : sa.wait);   // wait limit (cycles)
   auto nkb_of = [&](int blk) { return ANA ? (nh + kBK - 1) / kBK : (Mr[blk] + kBK - 1) / kBK; };
 
   if (warp == 0) {
@@ -250,7 +254,7 @@ __global__ void __launch_bounds__(tc_threads<ANA>(), 1) k_legendre_tc(const __gr
         const int nkb = nkb_of(tl.blk);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
-          if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort))) break;
+          if (it >= kStages && !(ok = mbar_wait(&ctl.empty[s], (n - 1) & 1, abort, wl))) break;
           if (ANA) {
             mbar_arrive_expect_tx(&ctl.fullA[s], 2 * kATileBytes + xbytes);
             const int y = (int)(aa.row_off[tl.blk] + tl.r0);
@@ -287,14 +291,14 @@ __global__ void __launch_bounds__(tc_threads<ANA>(), 1) k_legendre_tc(const __gr
         const Tile tl = tiles[t];
         const int nkb = nkb_of(tl.blk);
         const int acc = lt & 1, u = lt >> 1;
-        if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (u - 1) & 1, abort))) break;
+        if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (u - 1) & 1, abort, wl))) break;
         tc_fence_after();
         const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
           const int sb = kBRing ? (it % kBR) : s;   // B buffer of this iteration
-          ok = mbar_wait(&ctl.fullA[s], n & 1, abort);
-          if (ok && kBRing) ok = mbar_wait(&ctl.fullB[sb], (it / kBR) & 1, abort);
+          ok = mbar_wait(&ctl.fullA[s], n & 1, abort, wl);
+          if (ok && kBRing) ok = mbar_wait(&ctl.fullB[sb], (it / kBR) & 1, abort, wl);
           if (!ok) break;
           tc_fence_after();
           const uint32_t ah = smem_u32(sA_hi + s * kATileBytes), al = smem_u32(sA_lo + s * kATileBytes);
@@ -332,6 +336,9 @@ __global__ void __launch_bounds__(tc_threads<ANA>(), 1) k_legendre_tc(const __gr
         }
         umma_commit(&ctl.tfull[acc]);
       }
+      // every MMA issued here completes before the CTA frees its tensor memory (after an abort too)
+      umma_commit(&ctl.drain);
+      mbar_drain(&ctl.drain, 0);
     }
   } else if (warp < kEpiWarp0) {
     if (ANA) {
@@ -348,9 +355,9 @@ __global__ void __launch_bounds__(tc_threads<ANA>(), 1) k_legendre_tc(const __gr
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % kStages, n = it / kStages;
           const int sb = it % kBR, nb = it / kBR;
-          if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort))) break;
+          if (!(ok = mbar_wait(&ctl.fullA[s], n & 1, abort, wl))) break;
           // the MMAs of iteration it - kBR have finished reading this B buffer
-          if (nb > 0 && !(ok = mbar_wait(&ctl.bempty[sb], (nb - 1) & 1, abort))) break;
+          if (nb > 0 && !(ok = mbar_wait(&ctl.bempty[sb], (nb - 1) & 1, abort, wl))) break;
           if (pre)
             xc.run(reinterpret_cast<const float*>(sX + s * xbytes), kb * kBK, nh, sB_hi + sb * bstride,
                    sB_lo + sb * bstride);
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(tc_threads<ANA>(), 1) k_legendre_tc(const __gr
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
       const Tile tl = tiles[t];
       const int acc = lt & 1, u = lt >> 1;
-      if (!mbar_wait_warp(&ctl.tfull[acc], u & 1, abort)) break;
+      if (!mbar_wait_warp(&ctl.tfull[acc], u & 1, abort, wl)) break;
       tc_fence_after();
       const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc) + ((uint32_t)(q * 32) << 16);
       const int row = tl.r0 + q * 32 + lane;
@@ -497,7 +504,8 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map(&ml, g.tab_lo, g.nh, g.rows_total, g.ldt, kBM))) return rc;
     if ((rc = make_map_f32(&mx, X, ldc, (uint64_t)g.nblk * g.nh, ldc, nmma, kBK))) return rc;
     aa = AnaArgs{g.tiles_ana, g.ntiles_ana, g.M_d, g.row_off_d, g.nh, X, ldc, 2 * nf, nmma,
-                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4};
+                 apply_h ? g.h_d : nullptr, w.ct_hi, w.ct_lo, w.nmma_cap, g.ldi, Cf, w.dev_int + 4,
+                 g.wait_cycles};
     // [B_hi | B_lo] as one operand up to 128 columns (N = 2 x 64 x atoms <= 256)
     const bool bcat = 2 * 64 * mn_atoms(nmma) <= 256;
     auto kern = bcat ? (br == 3 ? (stages == 4   ? k_legendre_tc<4, true, 3, true>
@@ -533,7 +541,8 @@ int launch_legendre_tc(const Grid& g, int nf, const float* X, float* Cf, float* 
     if ((rc = make_map(&al, g.tab_lo, g.nh, g.rows_total, g.ldt, 64))) return rc;
     if ((rc = make_map(&bh, w.ct_hi, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
     if ((rc = make_map(&bl, w.ct_lo, g.ldi, (uint64_t)g.nblk * w.nmma_cap, g.ldi, nmma))) return rc;
-    sa = SynArgs{g.tiles_syn, g.ntiles_syn, g.M_d, g.row_off_d, g.nh, nmma, w.nmma_cap, 2 * nf, ldc, Y, w.dev_int + 4};
+    sa = SynArgs{g.tiles_syn, g.ntiles_syn, g.M_d, g.row_off_d, g.nh, nmma, w.nmma_cap, 2 * nf, ldc, Y, w.dev_int + 4,
+                 g.wait_cycles};
     auto kern = k_legendre_tc<kStagesSyn, false>;
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     // CTAs per SM: both shared memory and the 512 TMEM columns (two accumulators each) must fit

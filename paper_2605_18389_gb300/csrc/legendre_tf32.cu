@@ -208,6 +208,7 @@ struct T32Args {
   int nmma_cap, ldi;
   float* Y;                   // synthesis output [blk][jh][ldc]
   int* err;
+  long long wait;             // limit of every bounded wait (SM clock cycles)
   // recurrence mode
   const long long* ck_off;    // first checkpoint row of order m (in either parity plane)
   long long ck_rows;          // rows per parity plane
@@ -330,6 +331,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
       mbar_init(&ctl.infull[i], 1);
       mbar_init(&ctl.inempty[i], kSplitWarps);
     }
+    mbar_init(&ctl.drain, 1);
     ctl.abort = 0;
     fence_mbar_init();
   }
@@ -341,6 +343,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
   tc_fence_after();
   const uint32_t taddr = ctl.tmem;
   volatile int* abort = &ctl.abort;
+  const long long wl = a.wait;   // wait limit (cycles)
   auto nkb_of = [&](int blk) { return ANA ? (nh + kTK - 1) / kTK : (a.M[blk] + kTK - 1) / kTK; };
 
   if (warp == 0) {
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
           // REC fills the input ring (freed by the split warps), the table mode the stages (freed
           // by the MMAs)
           uint64_t* full = REC ? &ctl.infull[s] : &ctl.fullA[s];
-          if (it >= depth && !(ok = mbar_wait(REC ? &ctl.inempty[s] : &ctl.empty[s], ph ^ 1, abort))) break;
+          if (it >= depth && !(ok = mbar_wait(REC ? &ctl.inempty[s] : &ctl.empty[s], ph ^ 1, abort, wl))) break;
           mbar_arrive_expect_tx(full, (REC ? kCkBytes + (ANA ? kCfAna : kCfSyn) * 16 : kTTile) + bbytes);
           if (REC) {   // checkpoint box of the stage (segments x nodes), FP32 pairs, and coefficients
             const int m = tl.blk >> 1;
@@ -399,11 +402,11 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         const Tile tl = a.tiles[t];
         const int nkb = nkb_of(tl.blk);
         const int acc = lt & 1, u = lt >> 1;
-        if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (u - 1) & 1, abort))) break;
+        if (lt >= 2 && !(ok = mbar_wait(&ctl.tempty[acc], (u - 1) & 1, abort, wl))) break;
         tc_fence_after();
         const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc);
         for (int kb = 0; kb < nkb; ++kb) {
-          if (!(ok = mbar_wait(&ctl.fullB[s], ph, abort))) break;
+          if (!(ok = mbar_wait(&ctl.fullB[s], ph, abort, wl))) break;
           tc_fence_after();
           const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
           const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
@@ -430,6 +433,9 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         if (!ok) break;
         umma_commit(&ctl.tfull[acc]);
       }
+      // every MMA issued here completes before the CTA frees its tensor memory (after an abort too)
+      umma_commit(&ctl.drain);
+      mbar_drain(&ctl.drain, 0);
     }
   } else if (warp < 2 + kSplitWarps) {
     // split warps: table tile -> lo (the raw tile is hi) or (REC) the regenerated A tile hi/lo;
@@ -460,8 +466,8 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         // itself); the outcome is made warp-uniform so that a warp leaves together and its
         // single arrivals below stay valid.
         if (!REC) i = s;
-        bool w = REC ? mbar_wait(&ctl.infull[i], iph, abort) : mbar_wait(&ctl.fullA[s], ph, abort);
-        if (REC && w && it >= kStages) w = mbar_wait(&ctl.empty[s], ph ^ 1, abort);
+        bool w = REC ? mbar_wait(&ctl.infull[i], iph, abort, wl) : mbar_wait(&ctl.fullA[s], ph, abort, wl);
+        if (REC && w && it >= kStages) w = mbar_wait(&ctl.empty[s], ph ^ 1, abort, wl);
         if (!(ok = __all_sync(0xffffffffu, w))) break;
         if (REC && ANA) {
           if (agen) {
@@ -541,7 +547,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++lt) {
       const Tile tl = a.tiles[t];
       const int acc = lt & 1, u = lt >> 1;
-      if (!mbar_wait_warp(&ctl.tfull[acc], u & 1, abort)) break;
+      if (!mbar_wait_warp(&ctl.tfull[acc], u & 1, abort, wl)) break;
       tc_fence_after();
       const uint32_t d = taddr + (uint32_t)(acc * ncols_alloc) + ((uint32_t)(q * 32) << 16);
       const int row = tl.r0 + q * 32 + lane;
@@ -822,6 +828,7 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
     args.ldi = g.ldi;
     args.Y = nullptr;
     args.err = w.dev_int + 4;
+    args.wait = g.wait_cycles;
     if ((rc = launch(true, ma, mx, args, g.ntiles_ana))) return rc;
   }
   if (syn) {
@@ -845,6 +852,7 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
     args.ldi = g.ldi;
     args.Y = Y;
     args.err = w.dev_int + 4;
+    args.wait = g.wait_cycles;
     if ((rc = launch(false, ma, mb, args, g.ntiles_syn))) return rc;
   }
   return SHOT_OK;

@@ -11,6 +11,9 @@
 
 namespace shot {
 
+// Default limit of the bounded device-side waits of the tensor-core kernels (SM clock cycles).
+constexpr long long kDefaultWaitCycles = 1LL << 30;
+
 // ---------------------------------------------------------------------------------
 // Error reporting (thread-local message, status codes of shot.h)
 void set_error(const std::string& msg);
@@ -168,6 +171,7 @@ struct Grid {
   Tile* tiles_ana = nullptr;
   Tile* tiles_syn = nullptr;
   int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core kernels (0 = tuned)
+  long long wait_cycles = kDefaultWaitCycles;   // limit of the tensor-core kernels' waits (cycles)
   int t32_in_override = 0;      // SHOT_T32_INRING: input ring depth of the TF32 recurrence kernels (0 = deepest)
   int idft_nonpersistent = 0;   // SHOT_IDFT_PERSISTENT=0: update half-steps use the one-item-per-CTA k_idft
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use

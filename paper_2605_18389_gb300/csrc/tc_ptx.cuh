@@ -18,8 +18,13 @@ constexpr int kBK = 64;           // K elements per pipeline stage (one 128-byte
 constexpr int kMaxStages = 4;
 constexpr int kStagesAna = 4;   // one CTA per SM (table + X tiles per stage, B in its own ring)
 constexpr int kStagesSyn = 2;   // two CTAs per SM
-// Every wait is bounded by the SM clock: after ~2^30 cycles (~0.5 s at 2 GHz) it gives up.
-constexpr long long kWaitCycles = 1LL << 30;
+// Every wait is bounded by the SM clock: after a limit passed in the kernel's arguments (by
+// default kDefaultWaitCycles, ~0.5 s at 2 GHz) it gives up.  The waits that only let this
+// CTA's own copies and MMAs finish use the default.
+constexpr long long kWaitCycles = kDefaultWaitCycles;
+// Limits below this probe with test_wait (never blocks) and read the clock after every probe,
+// so that a short limit expires on time.
+constexpr long long kShortWait = 1LL << 20;
 constexpr int kATileBytes = kBM * kBK * 2;   // 16 KB
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -50,8 +55,21 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
   return ok != 0;
 }
 
+// Non-blocking probe.
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
 // Bounded wait that ignores the abort flag: used to let this CTA's own TMA copies land
-// before it exits.
+// (and its MMAs finish) before it exits.
 __device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity) {
   const long long t0 = clock64();
   while (!mbar_try(b, parity))
@@ -60,27 +78,29 @@ __device__ __forceinline__ void mbar_drain(uint64_t* b, uint32_t parity) {
 
 // Warp-uniform bounded wait: lane 0 waits, the outcome is broadcast to the warp (the
 // epilogue's tcgen05.ld is .sync.aligned and must be reached by all lanes or none).
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort);
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort, long long limit);
 
 // Bounded wait for the phase of the given parity.  Returns false (and raises the CTA's
-// abort flag) when the clock limit expires or another role already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort) {
-  if (mbar_try(b, parity)) return true;
+// abort flag) when `limit` cycles have passed or another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort, long long limit) {
+  const bool shortw = limit < kShortWait;
+  auto probe = [&] { return shortw ? mbar_test(b, parity) : mbar_try(b, parity); };
+  if (probe()) return true;
   const long long t0 = clock64();
   for (uint32_t it = 1;; ++it) {
-    if (mbar_try(b, parity)) return true;
-    if ((it & 15u) == 0) {
+    if (probe()) return true;
+    if (shortw || (it & 15u) == 0) {
       if (*abort) return false;
-      if (clock64() - t0 > kWaitCycles) break;
+      if (clock64() - t0 > limit) break;
     }
   }
   *abort = 1;
   return false;
 }
 
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort) {
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* b, uint32_t parity, volatile int* abort, long long limit) {
   int ok = 0;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait(b, parity, abort) ? 1 : 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(b, parity, abort, limit) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   return ok != 0;
 }
@@ -196,6 +216,7 @@ struct TcSmem {
   uint64_t bempty[3];   // analysis B buffer read by the MMAs (B ring of up to three)
   uint64_t infull[8];   // TF32 recurrence mode: input ring (TMA landed / read by the split warps)
   uint64_t inempty[8];
+  uint64_t drain;       // the MMA issuer's last commit: its MMAs are done before TMEM is freed
   uint32_t tmem;
   int abort;
 };

@@ -62,6 +62,7 @@ SIGNATURES = {
     "shot_grid_nodes": [_vp, _c_dbl_p, _c_dbl_p, _c_dbl_p],
     "shot_grid_reserve": [_vp, ctypes.c_int],
     "shot_grid_check": [_vp, _vp],
+    "shot_grid_set_wait_limit": [_vp, ctypes.c_longlong],
     "shot_heat_apply": [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int, _vp],
     "shot_sht_analysis": [_vp, _vp, _vp, ctypes.c_int, _vp],
     "shot_sht_synthesis": [_vp, _vp, _vp, ctypes.c_int, _vp],
@@ -241,6 +242,12 @@ def shot_grid_check(g, stream=None):
     """Synchronises the stream; raises ShotError(SHOT_ERR_TIMEOUT) if a bounded device-side
     wait expired in a kernel on this grid since the last check."""
     return _check(lib().shot_grid_check(g, _stream(stream)))
+
+
+def shot_grid_set_wait_limit(g, cycles):
+    """Limit (SM clock cycles) of the tensor-core kernels' bounded waits for later launches on
+    this grid; cycles <= 0 restores the default 2^30."""
+    return _check(lib().shot_grid_set_wait_limit(g, int(cycles)))
 
 
 def shot_heat_apply(g, t, inp, out, stream=None):
