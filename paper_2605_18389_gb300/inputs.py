@@ -83,3 +83,21 @@ def pairs(recipe, base_seed, npairs, x, nlon, a_ring, masses=False, dtype=np.flo
         p *= rng.uniform(0.5, 2.0, size=npairs)[:, None, None]
         q *= rng.uniform(0.5, 2.0, size=npairs)[:, None, None]
     return p.astype(dtype), q.astype(dtype)
+
+
+def fd_directions(p, a, k, seed, balanced=True):
+    """k directions [k, nlat, nlon] for finite-difference checks of a gradient in p: delta =
+    p * xi with xi ~ N(0, 1) per node (numpy default_rng(seed), one direction after the other);
+    when `balanced`, a constant is subtracted so that sum(a delta) = 0 (p + h delta keeps the
+    mass of p); then delta is scaled so that ||delta||_a = ||p||_a (a: node area weights)."""
+    p = np.asarray(p, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(k):
+        d = p * rng.normal(size=p.shape)
+        if balanced:
+            d -= np.sum(a * d) / np.sum(a)
+        d *= np.sqrt(np.sum(a * p * p) / np.sum(a * d * d))
+        out.append(d)
+    return np.array(out)
