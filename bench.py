@@ -197,12 +197,13 @@ def fp32_simt_peak_tflops():
     return 152 * 128 * 2 * 2.070e9 / 1e12
 
 
-def algorithmic_work(kind, nlat, npix, lmax, nfields):
+def algorithmic_work(kind, nlat, npix, lmax, nfields, legendre="table"):
     """(bytes, flops) one launch of a kernel kind must move / compute at minimum.
 
     npix nodes per field, nh = ceil(nlat/2) ring pairs, T = (lmax+1)(lmax+2)/2 degrees
     and orders; the folded table holds T*nh entries (4 B in FP32 and TF32x3, 2+2 B as bf16
-    hi/lo), read once per launch in every precision.
+    hi/lo), read once per launch in every precision.  In recurrence mode the TF32x3 kernels
+    read the checkpoints instead (4 FP32 values per 16 degrees and node: T*nh/4 entries).
     """
     n = npix
     nh = (nlat + 1) // 2
@@ -211,7 +212,7 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields):
     field = nfields * n * 4.0                     # one FP32 field batch
     spec = 2 * L * nh * 2 * nfields * 4.0         # folded ring spectra X or Y (FP32)
     coef = T * 2 * nfields * 4.0                  # coefficients (FP32, or bf16 hi+lo)
-    table = T * nh * 4.0
+    table = T * nh * 4.0 if legendre == "table" else T * nh * 4.0 / 4
     if kind == "ring_dft":
         return field + spec, 0.0
     if kind == "inverse_dft_epilogue":
@@ -230,15 +231,18 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields):
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from ncu --set full
 # captures of this file's 720 x 1440, 24-field runs (profiles/ncu_k_idft_720x1440.md,
-# ncu_k_legendre_tc_720x1440.md, ncu_k_legendre_tf32_720x1440.md); valid only for that workload,
+# ncu_k_legendre_tc_720x1440.md, ncu_k_legendre_tf32_720x1440.md, ncu_k_legendre_tf32_rec_720x1440.md);
+# valid only for that workload,
 # precision and the kernels as captured.
-NCU_TRAFFIC = {("inverse_dft_epilogue", "bf16x3"): (18 * 227.7e6 + 2 * 311.4e6) / 20,
-               ("legendre_analysis", "bf16x3"): 532.7e6, ("legendre_synthesis", "bf16x3"): 521.7e6,
-               ("legendre_analysis", "tf32x3"): 528.5e6, ("legendre_synthesis", "tf32x3"): 612.9e6}
+NCU_TRAFFIC = {("inverse_dft_epilogue", "*", "*"): (18 * 227.7e6 + 2 * 311.4e6) / 20,   # same kernel in every form
+               ("legendre_analysis", "bf16x3", "table"): 532.7e6, ("legendre_synthesis", "bf16x3", "table"): 521.7e6,
+               ("legendre_analysis", "tf32x3", "table"): 528.8e6, ("legendre_synthesis", "tf32x3", "table"): 613.1e6,
+               ("legendre_analysis", "tf32x3", "recurrence"): 241.9e6,
+               ("legendre_synthesis", "tf32x3", "recurrence"): 211.7e6}
 
 
-def roofline(kind, avg_ms, nlat, npix, lmax, nfields, prec):
-    by, fl = algorithmic_work(kind, nlat, npix, lmax, nfields)
+def roofline(kind, avg_ms, nlat, npix, lmax, nfields, prec, legendre="table"):
+    by, fl = algorithmic_work(kind, nlat, npix, lmax, nfields, legendre)
     fp32 = prec == "fp32"
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
@@ -254,7 +258,8 @@ def roofline(kind, avg_ms, nlat, npix, lmax, nfields, prec):
                 "peak_source": "FP32 FFMA, derived: 152 SMs x 128 lanes x 2 FLOP x 2.070 GHz",
                 "algorithmic_per_launch": fl, "avg_launch_ms": avg_ms}
     ach = by / s / 1e9
-    traffic = NCU_TRAFFIC.get((kind, prec)) if (nlat, npix, nfields) == (720, 720 * 1440, 24) else None
+    traffic = (NCU_TRAFFIC.get((kind, prec, legendre), NCU_TRAFFIC.get((kind, "*", "*")))
+               if (nlat, npix, nfields) == (720, 720 * 1440, 24) else None)
     out = {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
            "traffic": traffic, "peak_source": src, "algorithmic_per_launch": by, "avg_launch_ms": avg_ms}
     if kind.startswith("legendre"):
@@ -730,7 +735,7 @@ def main():
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
     lmax = 3 * args.nside - 1 if args.quadrature == "healpix" else nlat - 1
-    roof = roofline(dom, dom_ms / dom_n, nlat, npix, lmax, 3 * PAIRS, args.precision)
+    roof = roofline(dom, dom_ms / dom_n, nlat, npix, lmax, 3 * PAIRS, args.precision, args.legendre)
     roof["launches"] = dom_n
     roof["timing"] = ("CUDA events around every launch on the solver's stream, over a second "
                       "pass of the timed K steps")

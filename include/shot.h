@@ -54,8 +54,12 @@ extern "C" {
 /* ---- source of the associated Legendre values ---------------------------- */
 #define SHOT_TABLE       0   /* precomputed parity-folded table, O(nlat^3) memory */
 #define SHOT_RECURRENCE  1   /* values regenerated on the fly by the normalised three-term
-                                recurrence from per-(m, node) seeds: O(nlat^2) memory
-                                (SHOT_FP32 grids) */
+                                recurrence (App. B): SHOT_FP32 grids from per-(m, node) seeds,
+                                O(nlat^2) memory; SHOT_TF32X3 grids on the tensor cores from
+                                FP32 checkpoints, four values per 16 degrees (a quarter of
+                                the table's entries), by the two-step same-parity form;
+                                SHOT_BF16X3 grids run the same TF32x3 recurrence kernels (the
+                                generation, not the operand width, bounds them) */
 
 /* ---- latitudinal quadrature (App. C.1) ----------------------------------- */
 #define SHOT_QUAD_GAUSS_LEGENDRE  0  /* nodes = roots of P_nlat; exact to degree 2 nlat - 1 */
@@ -86,9 +90,12 @@ int shot_last_error(char* buf, int len);
  *   nlat >= 2; 2*lmax+1 <= nlon <= 6400 (any factorisation: prime factors above 5 run generic
  *              O(p)-per-output FFT stages, so 2,3,5-smooth nlon are fastest); lmax = -1 means nlat-1,
  *              else 0 <= lmax <= nlat-1
- *   precision  SHOT_FP32, SHOT_BF16X3 or SHOT_TF32X3; legendre_mode SHOT_TABLE or SHOT_RECURRENCE (FP32)
+ *   precision  SHOT_FP32, SHOT_BF16X3 or SHOT_TF32X3; legendre_mode SHOT_TABLE or SHOT_RECURRENCE
  * Memory: about 2*(lmax+1)(lmax+2)/2 * ceil(nlat/2) * 4 bytes of table (0.37 GB at 720);
  *   SHOT_TF32X3 adds the transposed copy, 2(lmax+1) ceil(nlat/2) ceil(M_max/8)*8 * 4 bytes (0.75 GB at 720).
+ *   SHOT_RECURRENCE keeps no table: FP32 grids ~(lmax+1) ceil(nlat/2) * 20 bytes of seeds; TF32X3
+ *   grids the checkpoints, ~(lmax+1)(lmax+2)/32 rows of 2 ceil(nlat/2) floats in each of two parity
+ *   planes (95 MB at 720, a quarter of the FP32 table; TF32X3's table mode keeps two tables).
  * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.  Synchronises `stream`. */
 int shot_grid_init(shot_grid* out, int nlat, int nlon, int lmax, int precision,
                    int legendre_mode, void* stream);

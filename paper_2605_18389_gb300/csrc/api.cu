@@ -40,21 +40,22 @@ int launch_analysis_simt(const Grid& g, int nf, const float* X, float* C, int ld
 int launch_synthesis_simt(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st);
 
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st) {
-  // TF32X3 grids run the tensor-core kernels in both Legendre modes (table or checkpoints)
-  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st);
+  // TF32X3 grids run the tensor-core kernels in both Legendre modes (table or checkpoints), and
+  // BF16X3 grids in recurrence mode run the same recurrence kernels
+  if (tf32_kernels(g)) return launch_legendre_tf32(g, nf, X, nullptr, Y, ldc, true, true, true, st);
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, Y, ldc, true, true, true, st);
   if (g.precision == SHOT_FP32) return launch_legendre_simt(g, nf, X, C, Y, ldc, st);
   return launch_legendre_tc(g, nf, X, nullptr, Y, ldc, true, true, true, st);
 }
 int launch_analysis_only(const Grid& g, int nf, const float* X, float* C, int ldc, bool apply_h,
                          cudaStream_t st) {
-  if (g.precision == SHOT_TF32X3) return launch_legendre_tf32(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
+  if (tf32_kernels(g)) return launch_legendre_tf32(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
   if (g.mode == SHOT_RECURRENCE) return launch_legendre_rec(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
   if (g.precision == SHOT_FP32) return launch_analysis_simt(g, nf, X, C, ldc, apply_h, st);
   return launch_legendre_tc(g, nf, X, C, nullptr, ldc, true, false, apply_h, st);
 }
 int launch_synthesis_only(const Grid& g, int nf, const float* C, float* Y, int ldc, cudaStream_t st) {
-  if (g.precision == SHOT_TF32X3) {
+  if (tf32_kernels(g)) {
     const int rc = launch_c_to_ct32(g, nf, C, ldc, st);
     if (rc) return rc;
     return launch_legendre_tf32(g, nf, nullptr, nullptr, Y, ldc, false, true, false, st);
@@ -736,10 +737,6 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     set_error("unknown legendre_mode");
     return SHOT_ERR_INVALID_ARG;
   }
-  if (legendre_mode == SHOT_RECURRENCE && precision == SHOT_BF16X3) {
-    set_error("SHOT_RECURRENCE is built for SHOT_FP32 and SHOT_TF32X3 grids");
-    return SHOT_ERR_UNSUPPORTED;
-  }
   FftPlan plan;
   if (nlon > kFftCap || !make_fft_plan(nlon, &plan)) {
     set_error("nlon above the shared-memory ring FFT's 6400 longitudes");
@@ -787,10 +784,6 @@ int shot_grid_init_healpix(shot_grid* out, int nside, int lmax, int precision, i
   if (legendre_mode != SHOT_TABLE && legendre_mode != SHOT_RECURRENCE) {
     set_error("unknown legendre_mode");
     return SHOT_ERR_INVALID_ARG;
-  }
-  if (legendre_mode == SHOT_RECURRENCE && precision == SHOT_BF16X3) {
-    set_error("SHOT_RECURRENCE is built for SHOT_FP32 and SHOT_TF32X3 grids");
-    return SHOT_ERR_UNSUPPORTED;
   }
   Grid* g = new Grid;
   g->nlat = nr;

@@ -92,7 +92,10 @@ int autotune(Grid& g, int nf, cudaStream_t st, const EpiParams* upd) {
     ep_upd = *upd;
     ep_upd.out = fld;
   }
-  auto run_inv = [&]() { return launch_idft(g, w.XY, w.ldc, nf, upd ? ep_upd : ep, st); };
+  // the field group only matters for the non-persistent inverse DFT (plain transforms, the final
+  // objective, and the update where the persistent kernel does not apply): tune on that
+  const bool inv_upd = upd && !idft_is_persistent(g, nf, ep_upd);
+  auto run_inv = [&]() { return launch_idft(g, w.XY, w.ldc, nf, inv_upd ? ep_upd : ep, st); };
   auto run_leg = [&]() { return launch_legendre(g, nf, w.XY, w.C, w.XY, w.ldc, st); };
   auto pick_vec = [&](int* slot, const std::vector<int>& c, const std::function<int()>& fn) -> int {
     float best = FLT_MAX;

@@ -292,8 +292,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_idft_p(
     }
     const float aj = a_ring[j];
     const bool two = (J != j);
-    ring_pair_epilogue<FG, kThreads>(z, other, ld, N, nfg, f0, (size_t)nlat * nlon, (size_t)j * nlon,
-                                     (size_t)J * nlon, two, aj, nh, jh, ep, red, fi[slot]);
+    // the persistent kernel runs updates and checks only: no final-objective branch
+    ring_pair_epilogue<FG, kThreads, false>(z, other, ld, N, nfg, f0, (size_t)nlat * nlon, (size_t)j * nlon,
+                                            (size_t)J * nlon, two, aj, nh, jh, ep, red, fi[slot]);
     if (ep.xout) {   // the update's new scaling: its spectra for the next half-step
       __syncthreads();
       const float2* zf = fft_smem_plan<false, PL>(other, const_cast<float2*>(z), tw_g, pl, nfg);
@@ -386,6 +387,13 @@ int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, 
   }
 }
 
+// whether launch_idft runs the persistent kernel (fixed field group of 2) for this epilogue
+bool idft_is_persistent(const Grid& g, int nf, const EpiParams& ep) {
+  return g.quad != SHOT_QUAD_HEALPIX && g.nlon <= kFftCap &&
+         (((ep.mode == EPI_UPDATE || ep.mode == EPI_SYM) && ep.xout) || ep.mode == EPI_CHECK) &&
+         !g.idft_nonpersistent && nf >= 2 && idft_p_layout(2, g.nlon, g.lmax).total <= 74 * 1024;
+}
+
 int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st) {
   if (g.quad == SHOT_QUAD_HEALPIX) return launch_hp_idft(g, Y, ldc, nf, ep, st);
   if (g.nlon > kFftCap) {
@@ -394,9 +402,7 @@ int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams&
   }
   // the solver's update half-steps and marginal checks: persistent kernel with the next item's
   // inputs prefetched
-  if ((((ep.mode == EPI_UPDATE || ep.mode == EPI_SYM) && ep.xout) || ep.mode == EPI_CHECK) && !g.idft_nonpersistent &&
-      nf >= 2 &&
-      idft_p_layout(2, g.nlon, g.lmax).total <= 74 * 1024) {
+  if (idft_is_persistent(g, nf, ep)) {
     if (plan_is<Plan1440>(g.plan)) return launch_idft_p_t<2, Plan1440>(g, Y, ldc, nf, ep, st);
     if (plan_is<Plan1024>(g.plan)) return launch_idft_p_t<2, Plan1024>(g, Y, ldc, nf, ep, st);
     return launch_idft_p_t<2>(g, Y, ldc, nf, ep, st);

@@ -84,7 +84,8 @@ __device__ __forceinline__ float epi_warp_sum(float v) {
   return v;
 }
 
-template <int FG, int NT>
+// kFinal = false compiles the EPI_FINAL branch out (kernels never launched with it)
+template <int FG, int NT, bool kFinal = true>
 __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* other, int ld, int N, int nfg, int f0,
                                                    size_t fstride, size_t rj, size_t rJ, bool two, float aj,
                                                    int nh, int jh, const EpiParams& ep,
@@ -110,13 +111,13 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
   for (int q = 0; q < FG; ++q)
 #pragma unroll
     for (int i = 0; i < NPART; ++i) acc[q][i] = 0.f;
-  // EPI_FINAL: the dual objective and m(pi) in FP64 (the objective's terms carry the
-  // potentials' offsets eps la and eps lb, which cancel between the two marginals' terms and,
-  // across the three problems, in the divergence: FP32 sums of them lose the digits the
-  // divergence keeps; m(pi) enters S_dual times eps)
-  double acc_ot[FG], acc_m[FG];
-#pragma unroll
-  for (int q = 0; q < FG; ++q) acc_ot[q] = acc_m[q] = 0.0;
+  // EPI_FINAL: the dual objective and m(pi) reach the block's FP64 sums through per-thread
+  // partials: the potentials' offsets eps la and eps lb cancel between the two marginals' terms
+  // and, across the three problems, in the divergence, so the balanced objective is formed per
+  // thread as la sum p + lb sum q + sum (p log u_buf + q log v_buf), with the sums of p and q
+  // (and the masses) compensated (Kahan) in FP32 and the offsets applied in FP64; per element
+  // the work stays FP32.  m(pi) enters S_dual times eps.
+  __shared__ double redd[NT / 32][FG][2];   // EPI_FINAL: warp sums of m(pi) and the objective
 
 #pragma unroll
   for (int q = 0; q < FG; ++q) {
@@ -265,7 +266,7 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
           }
         }
       }
-    } else {  // EPI_FINAL: z = K v_buf; ep.other = u buffer, ep.out = v buffer
+    } else if constexpr (kFinal) {  // EPI_FINAL: z = K v_buf; ep.other = u buffer, ep.out = v buffer
       if (!F.live) continue;
       const ProbState* P = ep.ps + f;
       const float* pp = ep.marg[f];
@@ -278,8 +279,15 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
       // balanced, after a v-update: v (K u) = q at every node, so m(pi) = sum a u (K v) =
       // sum a v (K u) = sum a q (K is self-adjoint in the area inner product)
       const bool mass_q = bal && !isnan(P->mass_v);
-      const double la = P->la, lb = P->lb;
       const float epsf = (float)ep.eps, tauf = (float)P->tau, et = bal ? 0.f : (float)(ep.eps / P->tau);
+      // balanced: A = sum p, B = sum q (compensated), C = sum p log u_buf + q log v_buf, D = sum
+      // u (K v) (m(pi) before any v-update); unbalanced: A = sum u (K v), B = the objective's terms
+      float A = 0.f, Ac = 0.f, B = 0.f, Bc = 0.f, C = 0.f, D = 0.f;
+      auto kahan = [](float& s, float& c, float x) {
+        const float y = x - c, t = s + y;
+        c = (t - s) - y;
+        s = t;
+      };
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
         const float2 zz = z[q * ld + k];
 #pragma unroll
@@ -306,19 +314,38 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
             acc[q][0] += d * d;
             acc[q][1] += pm * pm;
           }
-          acc_m[q] += (double)(mass_q ? qm : ukv);
           // phi = eps log u, psi = eps log v (App. C.2); terms with a zero marginal vanish.
-          // Balanced: p (la + log u_buf) + q (lb + log v_buf) in FP64, the buffers' logarithms
-          // in FP32 (they are O(1)); eps and a_j multiply the sums.
+          // Balanced: p (la + log u_buf) + q (lb + log v_buf), the offsets applied per thread
+          // below; eps and a_j multiply the sums.
           if (bal) {
-            acc_ot[q] += (pm > 0.f ? (double)pm * (la + (double)logf(ub)) : 0.0) +
-                         (qm > 0.f ? (double)qm * (lb + (double)logf(vb)) : 0.0);
+            kahan(A, Ac, pm);
+            kahan(B, Bc, qm);
+            C += (pm > 0.f ? pm * logf(ub) : 0.f) + (qm > 0.f ? qm * logf(vb) : 0.f);
+            D += ukv;
           } else {  // tau (1 - e^{-phi/tau}) = -tau expm1(-(eps/tau) log u), per node in FP32
-            const float t = (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
-                            (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f);
-            acc_ot[q] += (double)t;
+            kahan(A, Ac, ukv);
+            kahan(B, Bc, (pm > 0.f ? -tauf * expm1f(-et * lu) * pm : 0.f) +
+                             (qm > 0.f ? -tauf * expm1f(-et * lv) * qm : 0.f));
           }
         }
+      }
+      // this thread's m(pi) and objective in FP64, then the warp's sums
+      double vm, vo;
+      if (bal) {
+        vm = mass_q ? (double)B - (double)Bc : (double)D;
+        vo = P->la * ((double)A - (double)Ac) + P->lb * ((double)B - (double)Bc) + (double)C;
+      } else {
+        vm = (double)A - (double)Ac;
+        vo = (double)B - (double)Bc;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        vm += __shfl_xor_sync(0xffffffffu, vm, o);
+        vo += __shfl_xor_sync(0xffffffffu, vo, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        redd[threadIdx.x >> 5][q][0] = vm;
+        redd[threadIdx.x >> 5][q][1] = vo;
       }
     }
   }
@@ -331,24 +358,8 @@ __device__ __forceinline__ void ring_pair_epilogue(const float2* z, float2* othe
       const float v = epi_warp_sum(acc[q][i]);
       if (lane == 0) red[wid][q * NPART + i] = v;
     }
-  {
-    __shared__ double redd[NT / 32][FG][2];   // EPI_FINAL: warp sums of m(pi) and the objective
-    if (ep.mode == EPI_FINAL) {
-#pragma unroll
-      for (int q = 0; q < FG; ++q) {
-        double v = acc_m[q], w = acc_ot[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          v += __shfl_xor_sync(0xffffffffu, v, o);
-          w += __shfl_xor_sync(0xffffffffu, w, o);
-        }
-        if (lane == 0) {
-          redd[wid][q][0] = v;
-          redd[wid][q][1] = w;
-        }
-      }
-    }
-    __syncthreads();
+  __syncthreads();
+  if constexpr (kFinal) {
     if (ep.mode == EPI_FINAL && threadIdx.x < 2 * FG) {
       const int q = threadIdx.x >> 1, i = threadIdx.x & 1;
       if (q < nfg && fi[q].live) {

@@ -395,7 +395,7 @@ int build_grid_tables(Grid& g, cudaStream_t st) {
   __nv_bfloat16 *hi = nullptr, *lo = nullptr;
   g.ldi = (g.M[0] + 7) / 8 * 8;
   if (g.mode == SHOT_RECURRENCE) {
-    int rc = g.precision == SHOT_TF32X3 ? build_tf32_recurrence(g, st) : build_recurrence(g, st);
+    int rc = tf32_kernels(g) ? build_tf32_recurrence(g, st) : build_recurrence(g, st);
     if (rc) return rc;
   } else {
   float* tabT = nullptr;
@@ -520,7 +520,7 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
   // X and C are never read before written except padding columns; keep them finite
   SHOT_CUDA(cudaMemsetAsync(w.XY, 0, xy * sizeof(float), st));
   SHOT_CUDA(cudaMemsetAsync(w.C, 0, cc * sizeof(float), st));
-  if (g.precision == SHOT_BF16X3) {
+  if (g.precision == SHOT_BF16X3 && !tf32_kernels(g)) {
     w.nmma_cap = tc_nmma(nf);
     const size_t ct = (size_t)g.nblk * w.nmma_cap * g.ldi;
     SHOT_CUDA(cudaMalloc(&w.ct_hi, ct * sizeof(__nv_bfloat16)));
@@ -528,7 +528,7 @@ int ensure_workspace(Grid& g, int nf, cudaStream_t st) {
     SHOT_CUDA(cudaMemsetAsync(w.ct_hi, 0, ct * sizeof(__nv_bfloat16), st));
     SHOT_CUDA(cudaMemsetAsync(w.ct_lo, 0, ct * sizeof(__nv_bfloat16), st));
   }
-  if (g.precision == SHOT_TF32X3) {
+  if (tf32_kernels(g)) {
     w.nmma_cap = tc_nmma(nf);
     const size_t ct = (size_t)g.nblk * w.nmma_cap * g.ldi;
     SHOT_CUDA(cudaMalloc(&w.ct32, ct * sizeof(float)));

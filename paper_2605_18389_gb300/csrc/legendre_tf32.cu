@@ -25,10 +25,11 @@
 //                                                                  the analysis epilogue)
 // kind::tf32 is used with K-major operands only, hence the transposed table copy.
 //
-// Recurrence mode (SHOT_RECURRENCE, O(n) memory): no table.  The grid keeps checkpoints, for
+// Recurrence mode (SHOT_RECURRENCE): no table.  The grid keeps checkpoints (a quarter of one
+// table's entries: O(n^{3/2}) memory with a small constant, not the FP32 path's O(n)), for
 // each parity par, Pbar at the degrees (m + 16 s + par, m + 16 s + par + 2) of every order m and
-// north-hemisphere node (FP64 recurrence of App. B, rounded to FP32; about an eighth of the
-// table), and the same-parity two-step form of App. B's recurrence,
+// north-hemisphere node (FP64 recurrence of App. B, rounded to FP32; four values per 16 degrees),
+// and the same-parity two-step form of App. B's recurrence,
 // P_{l+2} = (A x^2 + B) P_l + C P_{l-2}, as FP32 coefficients (A, B, C) per degree.  A stage's
 // checkpoint box (of its parity) comes by TMA and its coefficient slice by a bulk copy with the
 // spectra (analysis) or C^T (synthesis) tile into the input ring, and the split warps regenerate

@@ -257,6 +257,14 @@ bool profiling_on();
 int launch_dft_fwd(const Grid& g, const float* in, int nf, const ProbState* ps, int scale_which,
                    float* X, int ldc, cudaStream_t st);
 int launch_idft(const Grid& g, const float* Y, int ldc, int nf, const EpiParams& ep, cudaStream_t st);
+bool idft_is_persistent(const Grid& g, int nf, const EpiParams& ep);
+// Grids whose Legendre contractions run the TF32x3 tensor-core kernels: TF32X3 grids, and BF16X3
+// grids in recurrence mode (the recurrence kernels are bound by generating the A operand, not by
+// the MMA's operand width, so a bf16 split of the generated values would gain nothing; TF32x3
+// is also the more accurate)
+inline bool tf32_kernels(const Grid& g) {
+  return g.precision == SHOT_TF32X3 || (g.precision == SHOT_BF16X3 && g.mode == SHOT_RECURRENCE);
+}
 int launch_legendre(const Grid& g, int nf, const float* X, float* C, float* Y, int ldc, cudaStream_t st);
 int launch_heat_mult(const Grid& g, double t, cudaStream_t st);
 int launch_coeff_gather(const Grid& g, const float* C, int ldc, int nf, float* coeffs, cudaStream_t st);
