@@ -306,7 +306,9 @@ int shot_regional_rms(shot_grid g, const float* grad_p, int batch, double* rms, 
  *   The first call on a device resolves the array's device address
  *   (cudaGetSymbolAddress) with that device current; make it before any stream capture.
  *   All calls share the array: calls whose kernels may overlap on the GPU race and must
- *   be serialised by the caller.  Asynchronous on `stream`. */
+ *   be serialised by the caller.  A call also writes the grid's heat multipliers h_l for its
+ *   t, so it races too with any overlapping call on the same grid (shot_heat_apply, a solve),
+ *   which reads them.  Asynchronous on `stream`. */
 #define SHOT_NOALLOC_SCRATCH_BYTES (8u << 20)
 int shot_heat_apply_noalloc(shot_grid g, double t, const float* in, float* out, int nfields, void* stream);
 

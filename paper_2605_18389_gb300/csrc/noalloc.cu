@@ -17,7 +17,9 @@
 // before any stream capture that includes this entry point.
 //
 // All calls share the one array: two calls whose kernels overlap on the GPU (different
-// streams, or different host threads) race on it and must be serialised by the caller.
+// streams, or different host threads) race on it and must be serialised by the caller.  A call
+// also writes the grid's heat multipliers h_l for its t (launch_heat_mult), so it races as well
+// with any overlapping call on the same grid (shot_heat_apply, a solve), which reads them.
 // Every call writes the scratch it reads before reading it (the padding columns of the
 // spectra are never read into a stored output), so nothing needs clearing between calls.
 #include <mutex>

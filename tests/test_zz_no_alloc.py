@@ -46,6 +46,43 @@ def test_noalloc_matches_heat_apply_twice():
         shot.shot_grid_free(g)
 
 
+# a Gauss-Legendre FP32 grid in table and recurrence mode, and a HEALPix grid: (make, field shape)
+GRIDS = {
+    "gl_table": (lambda: shot.shot_grid_init(48), (3, 48, 96)),
+    "gl_recurrence": (lambda: shot.shot_grid_init(48, None, -1, shot.SHOT_FP32, shot.SHOT_RECURRENCE), (3, 48, 96)),
+    "healpix": (lambda: shot.shot_grid_init_healpix(8, -1, shot.SHOT_FP32, shot.SHOT_TABLE), (3, 12 * 8 * 8)),
+}
+
+
+@pytest.mark.parametrize("kind", list(GRIDS))
+def test_noalloc_first_on_fresh_grid_allocates_nothing(kind):
+    """On a grid that has never run a transform (no workspace yet) the allocation-free call
+    comes first; after the first call has resolved the scratch array's device address, a
+    second call leaves the device's free memory unchanged.  Only then does shot_heat_apply
+    (which creates the grid's workspace) run, for the comparison."""
+    make, shape = GRIDS[kind]
+    g = make()
+    try:
+        t = 1e-2
+        f = torch.from_numpy(np.random.default_rng(8).uniform(size=shape).astype(np.float32)).cuda()
+        out = torch.full_like(f, float("nan"))
+        ref = torch.empty_like(f)
+        torch.cuda.synchronize()
+        assert _call_abi(g, t, f, out) == shot.SHOT_OK, shot.last_error()
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        out.fill_(float("nan"))
+        assert _call_abi(g, t, f, out) == shot.SHOT_OK, shot.last_error()
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0 - free1)
+        shot.shot_heat_apply(g, t, f, ref)
+        torch.cuda.synchronize()
+        assert rel_max(out.cpu().numpy(), ref.cpu().numpy()) <= TOL_SHT
+    finally:
+        shot.shot_grid_free(g)
+
+
 def test_noalloc_rejects_requests_beyond_its_scratch():
     g = shot.shot_grid_init(180)
     try:
