@@ -99,3 +99,35 @@ def test_configuration3_sets_with_scalings_beyond_fp32():
             assert np.all(s_err(o["S"], ref["S"], ot_pq, TOL_S) <= 1.0), (o["S"], ref["S"])
     finally:
         shot.shot_grid_free(g)
+
+
+def test_configuration3_grids_in_one_solve_match_oracle():
+    """Configuration 3's own grids, 64/96/128/180 rings (nlon = 2 nlat), in one
+    shot_divergence_multi solve: one set per grid, tau cycling through {0.1, 1, 10} plus a
+    balanced set, masses U[0.5, 2] per field, eps = 0.01 (t = 2.5e-3), 20 iterations.  Each set's
+    S and S_dual against the FP64 oracle, and against the same set solved alone."""
+    eps, T = 0.01, 20
+    specs = [(64, 0.1), (96, 1.0), (128, 10.0), (180, math.inf)]
+    grids = {n: (shot.shot_grid_init(n), OGrid(n)) for n, _ in specs}
+    try:
+        sets, refs = [], []
+        for i, (n, tau) in enumerate(specs):
+            g, og = grids[n]
+            pt, qt, p64, q64 = _set(og, 3900 + i, 1, not math.isinf(tau))
+            sets.append(dict(grid=g, p=pt, q=qt, eps=eps, tau=tau))
+            refs.append(sk.divergence(og, p64, q64, eps, tau, T=T, delta=0.0, C=10))
+        rc, outs = shot.shot_divergence_multi(sets, max_iter=T, tol=0.0, check_every=10)
+        assert rc >= 0
+        for st, o in zip(sets, outs):
+            assert np.all(o["status"] == 0)
+            rc1, r1 = shot.shot_divergence(st["grid"], st["p"], st["q"], eps, st["tau"], max_iter=T, tol=0.0,
+                                           check_every=10)
+            np.testing.assert_allclose(o["S"], r1["S"], rtol=1e-6, atol=1e-9)
+        for o, ref in zip(outs, refs):
+            assert np.all(ref["status"] == 0)
+            ot_pq = ref["runs"]["ot"][: len(o["S"])]
+            assert_s(o["S"], ref["S"], ot_pq, TOL_S, limited_by=FP32_S_LIMIT)
+            assert_s(o["S_dual"], ref["S_dual"], ot_pq, TOL_S, limited_by=FP32_S_LIMIT)
+    finally:
+        for g, _ in grids.values():
+            shot.shot_grid_free(g)
