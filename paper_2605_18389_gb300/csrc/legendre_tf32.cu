@@ -397,7 +397,15 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer: waits until the split warps have written the stage's lo parts
       const uint32_t idesc = idesc_tf32(kBM, nmma), idesc2 = idesc_tf32(kBM, nacc);
+      // operand descriptors: the start-address field is (address >> 4) in the low 14 bits (all
+      // of shared memory fits), so every descriptor is the first stage's A hi descriptor plus
+      // a constant: stage s at s sbytes, A lo / B hi / B lo at fixed offsets, K step k at 32 k
+      // bytes; the issuer spends a few adds per MMA instead of rebuilding descriptors
+      const uint64_t dbase = desc_sw128_kmajor(smem_u32(sA_hi(0)));
+      const uint64_t d_al = (uint64_t)(kTTile >> 4), d_bh = (uint64_t)((2 * kTTile) >> 4);
+      const uint64_t d_bl = d_bh + (uint64_t)(bbytes >> 4), d_stage = (uint64_t)(sbytes >> 4);
       int lt = 0, s = 0, ph = 0;
+      uint64_t dstage = dbase;   // descriptor of stage s's A hi
       bool ok = true;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++lt) {
         const Tile tl = a.tiles[t];
@@ -409,13 +417,10 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
         for (int kb = 0; kb < nkb; ++kb) {
           if (!(ok = mbar_wait(&ctl.fullB[s], ph, abort, wl))) break;
           tc_fence_after();
-          const uint32_t ah = smem_u32(sA_hi(s)), al = smem_u32(sA_lo(s));
-          const uint32_t bh = smem_u32(sB_hi(s)), bl = smem_u32(sB_lo(s));
 #pragma unroll
           for (int k = 0; k < kTK / 8; ++k) {   // 8 TF32 = 32 bytes per instruction
-            const uint32_t off = k * 32;
-            const uint64_t a_h = desc_sw128_kmajor(ah + off), a_l = desc_sw128_kmajor(al + off);
-            const uint64_t b_h = desc_sw128_kmajor(bh + off), b_l = desc_sw128_kmajor(bl + off);
+            const uint64_t off = dstage + (uint64_t)(2 * k);
+            const uint64_t a_h = off, a_l = off + d_al, b_h = off + d_bh, b_l = off + d_bl;
             if constexpr (BCAT) {   // b_h spans B_hi and B_lo (2 nmma rows)
               umma_tf32(d, a_h, b_h, idesc2, (kb | k) != 0);
               umma_tf32(d, a_l, b_h, idesc, 1);
@@ -426,9 +431,11 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
             }
           }
           umma_commit(&ctl.empty[s]);
+          dstage += d_stage;
           if (++s == kStages) {
             s = 0;
             ph ^= 1;
+            dstage = dbase;
           }
         }
         if (!ok) break;
