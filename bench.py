@@ -229,16 +229,13 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields, legendre="table"):
     return 0.0, 0.0
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from ncu --set full
-# captures of this file's 720 x 1440, 24-field runs (profiles/ncu_k_idft_720x1440.md,
-# ncu_k_legendre_tc_720x1440.md, ncu_k_legendre_tf32_720x1440.md, ncu_k_legendre_tf32_rec_720x1440.md);
-# valid only for that workload,
-# precision and the kernels as captured.
-NCU_TRAFFIC = {("inverse_dft_epilogue", "*", "*"): (18 * 227.7e6 + 2 * 311.4e6) / 20,   # same kernel in every form
-               ("legendre_analysis", "bf16x3", "table"): 532.7e6, ("legendre_synthesis", "bf16x3", "table"): 521.7e6,
-               ("legendre_analysis", "tf32x3", "table"): 528.8e6, ("legendre_synthesis", "tf32x3", "table"): 613.1e6,
-               ("legendre_analysis", "tf32x3", "recurrence"): 241.9e6,
-               ("legendre_synthesis", "tf32x3", "recurrence"): 211.7e6}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from ncu captures of
+# this file's 720 x 1440, 24-field TF32x3 runs of the kernels as they are (profiles/
+# ncu_k_idft_720x1440.md, ncu_k_legendre_tf32_720x1440.md); valid only for that workload and those
+# kernels.  The update kernel stores the scaling in 2 of a block's 20 half-steps.  Forms whose
+# kernels changed since their last capture (BF16x3, the recurrence mode) report null.
+NCU_TRAFFIC = {("inverse_dft_epilogue", "*", "*"): (18 * 223.2e6 + 2 * 313.5e6) / 20,   # same kernel in every form
+               ("legendre_analysis", "tf32x3", "table"): 525.3e6, ("legendre_synthesis", "tf32x3", "table"): 612.6e6}
 
 
 def roofline(kind, avg_ms, nlat, npix, lmax, nfields, prec, legendre="table"):
