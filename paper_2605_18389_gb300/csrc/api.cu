@@ -1,6 +1,6 @@
-// C ABI of the SHOT library (declared in include/shot.h) and the Sinkhorn driver.
+// C ABI of the SHOT library (declared in include/shot.h) and the host side of the Sinkhorn solver.
 //
-// The driver runs Algorithm 1 (App. C) for a batch of independent problems.  One
+// The host-side solver runs Algorithm 1 (App. C) for a batch of independent problems.  One
 // iteration is:  u-step (K v, then u = p/Kv or (p/Kv)^{tau/(tau+eps)}),  v-step (K u,
 // then v likewise),  then the gauge (balanced: s = sum u, u/s, s v) or the
 // translation-invariant step (c = tau/2 (log sum a p u^{-eps/tau} - log sum a q v^{-eps/tau}),
