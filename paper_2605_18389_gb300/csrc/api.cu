@@ -755,6 +755,8 @@ int shot_grid_init_quad(shot_grid* out, int quadrature, int nlat, int nlon, int 
     g->idft_nonpersistent = (e && e[0] == '0') ? 1 : 0;
     e = getenv("SHOT_TC_STAGES");   // 1..4 fixes the analysis pipeline depth instead of the autotuner
     g->tc_stages_override = (e && e[0] >= '1' && e[0] <= '4') ? e[0] - '0' : 0;
+    e = getenv("SHOT_T32_2CTA");   // 0: one CTA of 16 split warps per SM in the TF32 table kernels
+    g->t32_two_cta_off = (e && e[0] == '0') ? 1 : 0;
     e = getenv("SHOT_T32_INRING");   // 1..8 caps the input ring of the TF32 recurrence kernels
     g->t32_in_override = (e && e[0] >= '1' && e[0] <= '8') ? e[0] - '0' : 0;
   }

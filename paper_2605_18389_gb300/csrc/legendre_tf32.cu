@@ -56,7 +56,7 @@ namespace {
 
 constexpr int kSplitWarps = 16;                  // warps 2..17 (four per SM sub-partition)
 constexpr int kSplitThreads = 32 * kSplitWarps;
-constexpr int kT32Threads = 32 * (2 + kSplitWarps + 4);   // + TMA, MMA and four epilogue warps
+// (one CTA of 16 split warps: 32 * (2 + 16 + 4) threads, the TMA, MMA and four epilogue warps besides)
 constexpr int kTK = 32;                          // K per stage (one 128-byte row of FP32)
 constexpr int kTTile = kBM * kTK * 4;            // 16 KB: 128 rows x 32 FP32
 constexpr int kT32MaxStages = 4;
@@ -101,17 +101,18 @@ __device__ __forceinline__ uint32_t sw128_offset32(int row, int k) {
 // their 1024-byte phase): hi = rn(v), lo = rn(v - hi); hi may be the raw tile itself.  Each
 // thread loads kSplitBatch chunks before it stores any, so the loads overlap.
 constexpr int kSplitBatch = 2;   // 16 KB / (512 threads x 16 B) = 2 chunks per thread
+template <int NT = kSplitThreads>   // split threads
 __device__ __forceinline__ void split_tile(const uint8_t* raw, uint8_t* hi, uint8_t* lo, int nbytes, int pt) {
-  for (int base = 0; base < nbytes; base += kSplitBatch * kSplitThreads * 16) {
+  for (int base = 0; base < nbytes; base += kSplitBatch * NT * 16) {
     float4 v[kSplitBatch];
 #pragma unroll
     for (int i = 0; i < kSplitBatch; ++i) {
-      const int o = base + (pt + i * kSplitThreads) * 16;
+      const int o = base + (pt + i * NT) * 16;
       if (o < nbytes) v[i] = *reinterpret_cast<const float4*>(raw + o);
     }
 #pragma unroll
     for (int i = 0; i < kSplitBatch; ++i) {
-      const int o = base + (pt + i * kSplitThreads) * 16;
+      const int o = base + (pt + i * NT) * 16;
       if (o < nbytes) {
         const float w[4] = {v[i].x, v[i].y, v[i].z, v[i].w};
         float4 h, l;
@@ -286,10 +287,13 @@ __device__ __forceinline__ void rec_node_pair(float4 ck, float2 x2, const float4
 // stages [A hi][A lo][B hi][B lo] (written by the split warps, read by the MMAs) and a.nin
 // input stages [X or C^T raw][checkpoint box][coefficient slice] (written by TMA, read by the
 // split warps, released as soon as they are read), then x^2 of the nodes.
-template <int kStages, bool ANA, bool BCAT, bool REC = false>
-__global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_constant__ CUtensorMap ta,
-                                                                  const __grid_constant__ CUtensorMap tb,
-                                                                  T32Args a) {
+// SW split warps: 16 with one CTA per SM; 8 (table mode) with two CTAs per SM, whose independent
+// pipelines hide each other's handshake and copy latencies.
+template <int kStages, bool ANA, bool BCAT, bool REC = false, int SW = kSplitWarps>
+__global__ void __launch_bounds__(32 * (2 + SW + 4), SW == 8 ? 2 : 1)
+    k_legendre_tf32(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, T32Args a) {
+  static_assert(SW == 16 || (SW == 8 && !REC), "the recurrence generators are laid out for 16 split warps");
+  constexpr int kSW = SW, kST = 32 * SW;   // split warps, split threads
   extern __shared__ uint8_t smraw[];
   __shared__ TcSmem ctl;
   uint8_t* base = align1k(smraw);
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&ctl.fullA[s], 1);
-      mbar_init(&ctl.fullB[s], kSplitWarps);   // one arrival per split warp
+      mbar_init(&ctl.fullB[s], kSW);   // one arrival per split warp
       mbar_init(&ctl.empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -330,7 +334,7 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
     }
     for (int i = 0; REC && i < nin; ++i) {
       mbar_init(&ctl.infull[i], 1);
-      mbar_init(&ctl.inempty[i], kSplitWarps);
+      mbar_init(&ctl.inempty[i], kSW);
     }
     mbar_init(&ctl.drain, 1);
     ctl.abort = 0;
@@ -445,16 +449,16 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
       umma_commit(&ctl.drain);
       mbar_drain(&ctl.drain, 0);
     }
-  } else if (warp < 2 + kSplitWarps) {
+  } else if (warp < 2 + kSW) {
     // split warps: table tile -> lo (the raw tile is hi) or (REC) the regenerated A tile hi/lo;
     // analysis: X -> X^T hi/lo; synthesis: C^T -> hi/lo (in place in table mode)
     const int pt = threadIdx.x - 64;
     // REC analysis: split warps 0-7 regenerate A (node pairs), 8-15 split X^T; otherwise every
     // split warp does both parts.  bt / nbt: this thread among the X^T threads.
     constexpr bool kRoles = REC && ANA;
-    constexpr int nbt = kRoles ? kSplitThreads / 2 : kSplitThreads;
-    const bool agen = !kRoles || pt < kSplitThreads / 2, bsplit = !kRoles || pt >= kSplitThreads / 2;
-    const int bt = kRoles ? pt - kSplitThreads / 2 : pt;
+    constexpr int nbt = kRoles ? kST / 2 : kST;
+    const bool agen = !kRoles || pt < kST / 2, bsplit = !kRoles || pt >= kST / 2;
+    const int bt = kRoles ? pt - kST / 2 : pt;
     const bool pre = ANA && nmma * (kTK / 4) <= kXtTasks * nbt;
     XtPlan xp;
     xp.init(pre && bsplit ? nmma : 0, bt, nbt);
@@ -522,14 +526,14 @@ __global__ void __launch_bounds__(kT32Threads, 1) k_legendre_tf32(const __grid_c
           *reinterpret_cast<float4*>(al + o0) = l0;
           *reinterpret_cast<float4*>(al + o1) = l1;
         } else {
-          split_tile(sA_hi(s), sA_hi(s), sA_lo(s), kTTile, pt);
+          split_tile<kST>(sA_hi(s), sA_hi(s), sA_lo(s), kTTile, pt);
         }
         if (ANA && pre && bsplit)
           xp.run(reinterpret_cast<const float*>(sX(i)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s));
         else if (ANA && bsplit)
           split_xt(reinterpret_cast<const float*>(sX(i)), nmma, a.ncols, kb * kTK, nh, sB_hi(s), sB_lo(s), bt, nbt);
         else if (!ANA)
-          split_tile(REC ? sIn(i) : sB_hi(s), sB_hi(s), sB_lo(s), bbytes, pt);
+          split_tile<kST>(REC ? sIn(i) : sB_hi(s), sB_hi(s), sB_lo(s), bbytes, pt);
         // one arrival per warp, after __syncwarp has ordered all its lanes' accesses before it
         if (REC) {   // inputs read: the producer may refill the slot
           __syncwarp();
@@ -707,7 +711,19 @@ size_t tf32_smem_bytes(int nmma, bool ana, int stages, bool rec, int nin, int nh
 }
 
 template <bool REC>
-void* tf32_kernel(bool ana, bool bc, int stages) {
+void* tf32_kernel(bool ana, bool bc, int stages, bool two_cta) {
+  if constexpr (!REC) {
+    if (two_cta) {   // 8 split warps, two CTAs per SM
+#define SHOT_T32K8(S, A, B) reinterpret_cast<void*>(k_legendre_tf32<S, A, B, false, 8>)
+      if (bc) {
+        if (ana) return stages == 2 ? SHOT_T32K8(2, true, true) : SHOT_T32K8(1, true, true);
+        return stages == 2 ? SHOT_T32K8(2, false, true) : SHOT_T32K8(1, false, true);
+      }
+      if (ana) return stages == 2 ? SHOT_T32K8(2, true, false) : SHOT_T32K8(1, true, false);
+      return stages == 2 ? SHOT_T32K8(2, false, false) : SHOT_T32K8(1, false, false);
+#undef SHOT_T32K8
+    }
+  }
 #define SHOT_T32K(S, A, B) reinterpret_cast<void*>(k_legendre_tf32<S, A, B, REC>)
   if (bc) {
     if (ana) return stages == 4 ? SHOT_T32K(4, true, true) : stages == 3 ? SHOT_T32K(3, true, true)
@@ -767,9 +783,22 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
   // beside them; SHOT_TC_STAGES / SHOT_T32_INRING fix either depth.
   constexpr size_t kSmemCap = 227 * 1024 - 2048;
   auto bytes = [&](bool a_, int s, int in) { return tf32_smem_bytes(nmma, a_, s, rec, in, g.nh); };
+  // Table mode: two CTAs per SM (8 split warps each, two stages) where each CTA's tensor memory
+  // (two accumulators of at most 128 columns) and two stages in half the SM's shared memory fit;
+  // SHOT_T32_2CTA=0 keeps one CTA of 16 split warps.
+  const int nacc_h = 2 * nmma <= 256 ? 2 * nmma : nmma;
+  int tcols = 32;
+  while (tcols < nacc_h) tcols <<= 1;
+  constexpr size_t kSmemHalf = 112 * 1024 - 2048;
+  bool two_cta = false;
   auto pick = [&](bool a_, int& s, int& in) {
     if (!rec) {
       in = 0;
+      two_cta = !g.t32_two_cta_off && tcols <= 128 && bytes(a_, 2, 0) <= kSmemHalf;
+      if (two_cta) {
+        s = 2;
+        return;
+      }
       s = g.tc_stages_override > 0 ? g.tc_stages_override : kT32MaxStages;
       while (s > 1 && bytes(a_, s, 0) > kSmemCap) --s;
       return;
@@ -792,13 +821,15 @@ int launch_legendre_tf32(const Grid& g, int nf, const float* X, float* Cf, float
     }
     args.nin = nin;
     const bool bc = 2 * nmma <= 256;
-    void* kern = rec ? tf32_kernel<true>(a_, bc, stages) : tf32_kernel<false>(a_, bc, stages);
+    void* kern = rec ? tf32_kernel<true>(a_, bc, stages, false) : tf32_kernel<false>(a_, bc, stages, two_cta);
     SHOT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int grid = ntiles < g.num_sms ? ntiles : g.num_sms;
+    const int nthreads = 32 * (2 + (two_cta ? 8 : kSplitWarps) + 4);
+    const int ctas = (two_cta ? 2 : 1) * g.num_sms;   // persistent: one or two CTAs per SM
+    const int grid = ntiles < ctas ? ntiles : ctas;
     ProfScope prof(a_ ? PK_ANALYSIS : PK_SYNTHESIS, st);
     count_launch();
     void* params[] = {const_cast<CUtensorMap*>(&ma), const_cast<CUtensorMap*>(&mb), const_cast<T32Args*>(&args)};
-    SHOT_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(kT32Threads), params, smem, st));
+    SHOT_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(nthreads), params, smem, st));
     return SHOT_OK;
   };
   T32Args rx{};

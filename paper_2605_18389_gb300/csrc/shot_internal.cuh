@@ -172,7 +172,8 @@ struct Grid {
   Tile* tiles_syn = nullptr;
   int tc_stages_override = 0;   // SHOT_TC_STAGES: pipeline depth of the tensor-core kernels (0 = tuned)
   long long wait_cycles = kDefaultWaitCycles;   // limit of the tensor-core kernels' waits (cycles)
-  int t32_in_override = 0;      // SHOT_T32_INRING: input ring depth of the TF32 recurrence kernels (0 = deepest)
+  int t32_in_override = 0;
+  int t32_two_cta_off = 0;      // SHOT_T32_2CTA=0: TF32 table kernels with one CTA of 16 split warps per SM      // SHOT_T32_INRING: input ring depth of the TF32 recurrence kernels (0 = deepest)
   int idft_nonpersistent = 0;   // SHOT_IDFT_PERSISTENT=0: update half-steps use the one-item-per-CTA k_idft
   void* xyz_d = nullptr;        // node unit vectors (float4), made on first use
   // ring geometry (every grid): ring i holds ring_len[i] nodes starting at ring_off[i] of a
