@@ -235,7 +235,7 @@ def algorithmic_work(kind, nlat, npix, lmax, nfields, legendre="table"):
 # kernels.  The update kernel stores the scaling in 2 of a block's 20 half-steps.  Forms whose
 # kernels changed since their last capture (BF16x3, the recurrence mode) report null.
 NCU_TRAFFIC = {("inverse_dft_epilogue", "*", "*"): (18 * 223.2e6 + 2 * 313.5e6) / 20,   # same kernel in every form
-               ("legendre_analysis", "tf32x3", "table"): 525.3e6, ("legendre_synthesis", "tf32x3", "table"): 612.6e6}
+               ("legendre_analysis", "tf32x3", "table"): 524.6e6, ("legendre_synthesis", "tf32x3", "table"): 611.5e6}
 
 
 def roofline(kind, avg_ms, nlat, npix, lmax, nfields, prec, legendre="table"):
